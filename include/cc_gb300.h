@@ -1,0 +1,188 @@
+/*
+ * cc_gb300.h - C ABI of the GB300 connected-components engine.
+ *
+ * The engine labels every vertex of an undirected graph G(V, E) with the
+ * smallest vertex id of its connected component (Section 1, problem
+ * statement; Section 3.1.1 and the Figure 1(b) caption: at termination every
+ * tuple of a component carries the partition min(u, v1, v2)). It follows the
+ * hybrid route of Algorithm 2 (Section 3.2):
+ *   1. degree distribution of G,
+ *   2. power-law fit + Kolmogorov-Smirnov statistic D; BFS runs iff D < tau,
+ *   3. if so, a direction-optimizing BFS from the max-degree vertex claims
+ *      its component and the visited pairs are filtered out,
+ *   4. Shiloach-Vishkin iterations (Section 3.1, Algorithm 1 semantics: every
+ *      partition joins its minimum neighbour, pointer doubling, completed
+ *      partitions are excluded, Section 3.1.4) label the rest.
+ * Labels are identical for every route; the route only changes the time.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA
+ *    memory); pointers named *_host are host pointers. The caller owns all of
+ *    them; the library never frees or retains them past the call and never
+ *    writes to its inputs.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Work is enqueued on it in order. Unless noted otherwise the
+ *    call returns after enqueueing; results are valid once the stream has
+ *    reached that point.
+ *  - Edge lists are [m][2] interleaved (u, v) pairs, row-major, of
+ *    `id_bytes` (4: int32, 8: int64) each, vertex ids dense in [0, n).
+ *    Self-loops and duplicate pairs are allowed. n must be < 2^32 - 1.
+ *    Edge arrays must be 16-byte aligned (the kernels read them with 128-bit
+ *    loads); labels are written with the same id width as the edges.
+ *  - Errors: argument errors are returned immediately and nothing is
+ *    enqueued. Errors the device detects (an id outside [0, n), a run that
+ *    exceeds the iteration cap) are recorded in the context and returned by
+ *    the next cc_get_stats() or, with debug_checks set, by the call itself;
+ *    the contents of the outputs are then unspecified.
+ *  - A context is not thread safe: use one context per host thread/stream.
+ */
+#ifndef CC_GB300_H
+#define CC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cc_ctx cc_ctx;
+
+typedef enum {
+    CC_OK = 0,
+    CC_ERR_INVALID_ARG = 1,     /* bad pointer, size, option or alignment */
+    CC_ERR_INVALID_EDGE = 2,    /* an edge id lies outside [0, n) */
+    CC_ERR_OOM = 3,             /* device workspace allocation failed */
+    CC_ERR_NO_CONVERGENCE = 4,  /* SV iteration cap or BFS level cap exceeded */
+    CC_ERR_TIMEOUT = 5,         /* a bounded device wait ran out */
+    CC_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+    CC_ERR_UNSUPPORTED = 7      /* size outside the engine's limits */
+} cc_status;
+
+/* Route policies (Algorithm 2 and its variants). */
+enum {
+    CC_ROUTE_AUTO = 0,      /* K-S heuristic of Section 3.2: BFS iff D < ks_tau */
+    CC_ROUTE_LEARNED = 1,   /* learned predictor (needs cc_set_predictor); K-S decides when unsure */
+    CC_ROUTE_FORCE_BFS = 2, /* always BFS first (the "opposite decision" experiment of Section 5) */
+    CC_ROUTE_FORCE_SV = 3   /* SV only, no prediction */
+};
+
+/* Host-side fault injection bits (tests only; no GPU fault is ever caused). */
+enum {
+    CC_FAULT_NONE = 0,
+    CC_FAULT_ALLOC = 1,      /* the next workspace allocation fails -> CC_ERR_OOM */
+    CC_FAULT_ITER_CAP = 2    /* SV iteration cap forced to 1 -> CC_ERR_NO_CONVERGENCE on any graph needing more */
+};
+
+typedef struct {
+    int id_bytes;           /* 4 or 8; default 4 */
+    int route_policy;       /* CC_ROUTE_*; default CC_ROUTE_AUTO */
+    double ks_tau;          /* default 0.05 (Section 5, Table 2) */
+    int ks_min_tail;        /* smallest tail (vertices) an xmin candidate may have; default 50 */
+    int ks_min_distinct;    /* fewest distinct degrees in a candidate tail; default 3 */
+    int max_iters;          /* SV iteration cap; 0 = default 64 + 4*ceil(log2 n) */
+    int bfs_cutoff_levels;  /* stop BFS after this many levels; 0 = run to completion */
+    int debug_checks;       /* 1: synchronise the stream at the end of every call and return device errors */
+    int fault_inject;       /* CC_FAULT_* bits */
+    int reserved[7];
+} cc_options;
+
+#define CC_MAX_SV_ITERS_RECORDED 64
+
+typedef struct {
+    int status;             /* cc_status of the last call's device work */
+    int route;              /* 1 = BFS then SV, 0 = SV only */
+    int route_source;       /* 0 = K-S heuristic, 1 = learned predictor, 2 = forced */
+    int bfs_levels;         /* BFS levels run */
+    int sv_iters;           /* SV iterations run */
+    int pad0;
+    double ks_d;            /* K-S statistic (min over xmin); 1.0 if no candidate */
+    double ks_alpha;        /* power-law exponent at the chosen xmin */
+    int64_t ks_xmin;        /* chosen xmin; 0 if no candidate */
+    int64_t ks_ntail;       /* vertices in the chosen tail */
+    int64_t ks_ncand;       /* number of xmin candidates */
+    int64_t n, m;           /* problem size of the last call */
+    int64_t max_degree;     /* largest vertex degree */
+    int64_t seed_vertex;    /* BFS seed: max-degree vertex, ties to the smallest id */
+    int64_t bfs_visited;    /* vertices claimed by BFS */
+    int64_t comp_min;       /* smallest id among the BFS-visited vertices */
+    int64_t bfs_edges_inspected; /* adjacency entries the BFS read */
+    int64_t m_active[CC_MAX_SV_ITERS_RECORDED]; /* active pairs entering each SV iteration */
+    float ms_degree, ms_predict, ms_csr, ms_bfs, ms_sv, ms_finalize, ms_total; /* device stage times */
+    float pad1;
+} cc_stats;
+
+/* Fills *opt with the defaults listed above. */
+cc_status cc_default_options(cc_options *opt);
+
+/*
+ * Creates a context bound to CUDA device `device`. opt == NULL takes the
+ * defaults. The context owns a device workspace that grows on demand (the
+ * first call at a new size allocates; later calls at that size or below do
+ * not) and is freed by cc_destroy.
+ */
+cc_status cc_create(cc_ctx **out, const cc_options *opt, int device);
+
+/* Replaces the context's options (same meaning as in cc_create). */
+cc_status cc_set_options(cc_ctx *ctx, const cc_options *opt);
+
+/* Frees the workspace and the context. NULL is accepted. */
+cc_status cc_destroy(cc_ctx *ctx);
+
+/*
+ * Connected-component labels of one graph (Algorithm 2, Section 3.2).
+ *   edges_dev      [m][2] pairs of id_bytes each (device, 16-byte aligned)
+ *   n              vertices, 0 <= n < 2^32 - 1
+ *   m              pairs, m >= 0 (m = 0 gives labels_out[v] = v)
+ *   labels_out_dev [n] ids of id_bytes each (device); labels_out[v] = min id of v's component
+ * The call synchronises `stream` internally a few times (to read the route
+ * and the active-pair counts); everything else is enqueued. On return the
+ * labels are complete on `stream`.
+ */
+cc_status cc_labels(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, void *labels_out_dev, void *stream);
+
+/*
+ * Labels of G independent graphs in one call (the batched form).
+ *   edges_dev          concatenated int32 pairs with ids local to each graph
+ *   edge_offsets_dev   [G+1] int64 (device): graph g owns pairs [eo[g], eo[g+1])
+ *   vertex_offsets_dev [G+1] int64 (device): graph g owns vertices [vo[g], vo[g+1]) of labels_out
+ *   labels_out_dev     [vo[G]] int32 (device): local labels, min local id of each component
+ * edge_offsets_host / vertex_offsets_host must hold the same offsets on the
+ * host (they drive the schedule; the device copies drive the kernels).
+ * Works for id_bytes = 4 only; sum of vertices < 2^31.
+ */
+cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *edge_offsets_dev,
+                            const int64_t *vertex_offsets_dev, const int64_t *edge_offsets_host,
+                            const int64_t *vertex_offsets_host, int G, void *labels_out_dev, void *stream);
+
+/*
+ * Degree pass and degree distribution (Section 3.2, Algorithm 2 line 1):
+ *   deg_out_dev  [n] uint32 (device): number of pair endpoints equal to v
+ *                (a self-loop adds 2, duplicates count)
+ *   hist_out_dev [hist_len] uint64 (device): hist[d] = #{v : deg[v] = d} for d < hist_len
+ *                (degrees >= hist_len are not counted; pass NULL to skip)
+ * Either output may be NULL. Returns CC_ERR_INVALID_EDGE (after a stream
+ * synchronisation) if an id is outside [0, n).
+ */
+cc_status cc_degree_distribution(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, uint32_t *deg_out_dev,
+                                 uint64_t *hist_out_dev, int64_t hist_len, void *stream);
+
+/*
+ * Power-law fit + K-S statistic of a degree histogram (Section 3.2, Table 2),
+ * computed on the device:
+ *   hist_dev [hist_len] uint64 (device) counts per degree
+ *   out_host [5] doubles (host): D, alpha, xmin, tail size, candidates
+ * Synchronises `stream`.
+ */
+cc_status cc_ks_statistic(cc_ctx *ctx, const uint64_t *hist_dev, int64_t hist_len, double *out_host, void *stream);
+
+/* Statistics of the last cc_labels call; synchronises its stream. Returns the recorded device status. */
+cc_status cc_get_stats(cc_ctx *ctx, cc_stats *out);
+
+/* Static, human-readable description of a status. */
+const char *cc_strerror(cc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CC_GB300_H */

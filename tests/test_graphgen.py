@@ -1,0 +1,56 @@
+"""Input generators: determinism, sizes and planted structure (CPU only)."""
+import numpy as np
+
+import graphgen as gg
+
+
+def test_permutation_is_a_bijection():
+    for n in (1, 2, 3, 17, 1000, 4096, 12345):
+        x = np.arange(n, dtype=np.uint64)
+        y = gg.permute(n, 99, 7, x)
+        assert np.array_equal(np.sort(y), x)
+
+
+def test_deterministic_and_seed_sensitive():
+    a = gg.rmat(seed=3, scale=12, edge_factor=4)
+    b = gg.rmat(seed=3, scale=12, edge_factor=4)
+    c = gg.rmat(seed=4, scale=12, edge_factor=4)
+    assert np.array_equal(a.edges, b.edges)
+    assert not np.array_equal(a.edges, c.edges)
+    assert a.edges.min() >= 0 and a.edges.max() < a.n
+
+
+def test_planted_sizes_and_counts():
+    g = gg.planted(seed=1)
+    s = g.meta["sizes"]
+    assert s.sum() == g.n == 65536 and s.size == 512 and s.min() >= 1
+    assert np.array_equal(np.bincount(g.meta["comp"], minlength=512), s)
+    # each component: spanning tree (s-1) + round(1.5 s) extra pairs (halves round up)
+    assert g.m == int(np.sum(s - 1 + np.floor(1.5 * s + 0.5)))  # round half away from zero
+    # pairs never cross components
+    comp = g.meta["comp"]
+    assert (comp[g.edges[:, 0]] == comp[g.edges[:, 1]]).all()
+
+
+def test_grid_chains_shape():
+    W, nch = 64, 500
+    g = gg.grid_chains(seed=2, W=W, p=0.55, nchains=nch, id_bytes=8)
+    off = g.meta["chain_off"]
+    assert g.n == W * W + off[-1]
+    assert g.edges.dtype == np.int64 and g.edges.min() >= 0 and g.edges.max() < g.n
+    bonds = 2 * W * (W - 1)
+    chain_edges = off[-1] - nch
+    extra = g.m - chain_edges
+    assert 0.45 * bonds < extra < 0.65 * bonds + 0.05 * off[-1]
+
+
+def test_batch_offsets_and_local_ids():
+    b = gg.batch(seed=1, G=12, nmin=1000, nmax=20000)
+    assert b.edge_offsets[0] == 0 and b.edge_offsets[-1] == b.edges.shape[0]
+    for g in range(b.G):
+        gr = b.graph(g)
+        assert 1000 <= gr.n <= 20000
+        if gr.m:
+            assert gr.edges.min() >= 0 and gr.edges.max() < gr.n
+        if g % 3 == 0:
+            assert gr.m == 8 * gr.n
