@@ -81,9 +81,10 @@ typedef struct {
     int ks_min_distinct;    /* fewest distinct degrees in a candidate tail; default 3 */
     int max_iters;          /* SV iteration cap; 0 = default 64 + 4*ceil(log2 n) */
     int bfs_cutoff_levels;  /* stop BFS after this many levels; 0 = run to completion */
-    int debug_checks;       /* 1: synchronise the stream at the end of every call and return device errors */
+    int debug_checks;       /* reserved: cc_labels always returns device-detected errors */
     int fault_inject;       /* CC_FAULT_* bits */
-    int reserved[7];
+    double ks_min_span;     /* a candidate tail must reach max degree >= ks_min_span * xmin; default 10 */
+    int reserved[4];
 } cc_options;
 
 #define CC_MAX_SV_ITERS_RECORDED 64

@@ -1,0 +1,217 @@
+"""GB300 connected-components engine: thin ctypes binding over libcc_gb300.so.
+
+Every step of the hybrid route (Algorithm 2 of Jain et al., "An Adaptive
+Parallel Algorithm for Computing Connected Components": degree
+distribution, power-law/K-S route prediction, direction-optimizing BFS,
+Shiloach-Vishkin iterations) runs in the library's CUDA kernels; this module
+only marshals arguments. PyTorch supplies device memory and streams.
+
+There is no CPU fallback: if the shared library has not been built the
+import succeeds but every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcc_gb300.so")
+
+CC_OK = 0
+STATUS = {
+    0: "CC_OK", 1: "CC_ERR_INVALID_ARG", 2: "CC_ERR_INVALID_EDGE", 3: "CC_ERR_OOM",
+    4: "CC_ERR_NO_CONVERGENCE", 5: "CC_ERR_TIMEOUT", 6: "CC_ERR_CUDA", 7: "CC_ERR_UNSUPPORTED",
+}
+ROUTES = {"auto": 0, "learned": 1, "bfs": 2, "sv": 3}
+FAULT_ALLOC, FAULT_ITER_CAP = 1, 2
+MAX_SV_ITERS_RECORDED = 64
+
+
+class CCError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("id_bytes", ctypes.c_int), ("route_policy", ctypes.c_int), ("ks_tau", ctypes.c_double),
+        ("ks_min_tail", ctypes.c_int), ("ks_min_distinct", ctypes.c_int), ("max_iters", ctypes.c_int),
+        ("bfs_cutoff_levels", ctypes.c_int), ("debug_checks", ctypes.c_int), ("fault_inject", ctypes.c_int),
+        ("ks_min_span", ctypes.c_double), ("reserved", ctypes.c_int * 4),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("route", ctypes.c_int), ("route_source", ctypes.c_int),
+        ("bfs_levels", ctypes.c_int), ("sv_iters", ctypes.c_int), ("pad0", ctypes.c_int),
+        ("ks_d", ctypes.c_double), ("ks_alpha", ctypes.c_double), ("ks_xmin", ctypes.c_int64),
+        ("ks_ntail", ctypes.c_int64), ("ks_ncand", ctypes.c_int64), ("n", ctypes.c_int64), ("m", ctypes.c_int64),
+        ("max_degree", ctypes.c_int64), ("seed_vertex", ctypes.c_int64), ("bfs_visited", ctypes.c_int64),
+        ("comp_min", ctypes.c_int64), ("bfs_edges_inspected", ctypes.c_int64),
+        ("m_active", ctypes.c_int64 * MAX_SV_ITERS_RECORDED),
+        ("ms_degree", ctypes.c_float), ("ms_predict", ctypes.c_float), ("ms_csr", ctypes.c_float),
+        ("ms_bfs", ctypes.c_float), ("ms_sv", ctypes.c_float), ("ms_finalize", ctypes.c_float),
+        ("ms_total", ctypes.c_float), ("pad1", ctypes.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
+        d["m_active"] = [int(x) for x in self.m_active[:max(0, min(self.sv_iters, MAX_SV_ITERS_RECORDED))]]
+        return d
+
+
+_lib = None
+_vp, _i64, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(the engine has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        L.cc_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.cc_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(Options), _int]
+        L.cc_set_options.argtypes = [_vp, ctypes.POINTER(Options)]
+        L.cc_destroy.argtypes = [_vp]
+        L.cc_labels.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp]
+        L.cc_labels_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp]
+        L.cc_degree_distribution.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp]
+        L.cc_ks_statistic.argtypes = [_vp, _vp, _i64, _vp, _vp]
+        L.cc_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
+        L.cc_strerror.argtypes = [_int]
+        L.cc_strerror.restype = ctypes.c_char_p
+        for f in ("cc_default_options", "cc_create", "cc_set_options", "cc_destroy", "cc_labels",
+                  "cc_labels_batched", "cc_degree_distribution", "cc_ks_statistic", "cc_get_stats"):
+            getattr(L, f).restype = _int
+        _lib = L
+    return _lib
+
+
+def default_options() -> Options:
+    o = Options()
+    lib().cc_default_options(ctypes.byref(o))
+    return o
+
+
+def _check(rc: int, where: str):
+    if rc != CC_OK:
+        raise CCError(rc, where)
+
+
+def _stream_handle(stream, device) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Engine:
+    """One cc_ctx: a device workspace plus options (Algorithm 2 route policy)."""
+
+    def __init__(self, id_bytes: int = 4, route: str = "auto", device: int = 0, **opts):
+        o = default_options()
+        o.id_bytes = id_bytes
+        o.route_policy = ROUTES[route]
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.device = device
+        self._opt = o
+        h = _vp()
+        _check(lib().cc_create(ctypes.byref(h), ctypes.byref(o), device), "cc_create")
+        self._h = h
+
+    def set_options(self, route: str | None = None, **opts):
+        o = self._opt
+        if route is not None:
+            o.route_policy = ROUTES[route]
+        for k, v in opts.items():
+            setattr(o, k, v)
+        _check(lib().cc_set_options(self._h, ctypes.byref(o)), "cc_set_options")
+
+    @property
+    def options(self) -> Options:
+        return self._opt
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----- raw-pointer calls (the C ABI as is) -----
+    def labels_ptr(self, edges_ptr: int, n: int, m: int, labels_ptr: int, stream: int = 0) -> int:
+        return lib().cc_labels(self._h, edges_ptr, n, m, labels_ptr, stream)
+
+    # ----- torch conveniences -----
+    def labels(self, edges, n: int, out=None, stream=None):
+        """Component labels (min vertex id per component) of a device edge tensor [m, 2]."""
+        import torch
+
+        if edges.dtype.itemsize != self._opt.id_bytes:
+            raise ValueError(f"edges dtype {edges.dtype} does not match id_bytes={self._opt.id_bytes}")
+        if not edges.is_contiguous():
+            raise ValueError("edges must be contiguous")
+        m = edges.shape[0] if edges.numel() else 0
+        if out is None:
+            out = torch.empty(n, dtype=edges.dtype, device=edges.device)
+        rc = lib().cc_labels(self._h, edges.data_ptr() if m else None, n, m, out.data_ptr() if n else None,
+                             _stream_handle(stream, edges.device))
+        _check(rc, "cc_labels")
+        return out
+
+    def labels_batched(self, edges, edge_offsets, vertex_offsets, out=None, stream=None):
+        """Local labels of G independent graphs (int32 ids local to each graph)."""
+        import torch
+
+        eo_h = edge_offsets.cpu().contiguous()
+        vo_h = vertex_offsets.cpu().contiguous()
+        eo_d = eo_h.to(edges.device)
+        vo_d = vo_h.to(edges.device)
+        G = eo_h.numel() - 1
+        if out is None:
+            out = torch.empty(int(vo_h[-1]), dtype=torch.int32, device=edges.device)
+        rc = lib().cc_labels_batched(self._h, edges.data_ptr() if edges.numel() else None, eo_d.data_ptr(),
+                                     vo_d.data_ptr(), eo_h.data_ptr(), vo_h.data_ptr(), G,
+                                     out.data_ptr() if out.numel() else None, _stream_handle(stream, edges.device))
+        _check(rc, "cc_labels_batched")
+        return out
+
+    def degree_distribution(self, edges, n: int, hist_len: int = 0, stream=None):
+        """(deg[n] uint32 as int32 tensor, hist[hist_len] uint64 as int64 tensor or None)."""
+        import torch
+
+        m = edges.shape[0] if edges.numel() else 0
+        deg = torch.empty(n, dtype=torch.int32, device=edges.device)
+        hist = torch.empty(hist_len, dtype=torch.int64, device=edges.device) if hist_len > 0 else None
+        rc = lib().cc_degree_distribution(self._h, edges.data_ptr() if m else None, n, m,
+                                          deg.data_ptr() if n else None, hist.data_ptr() if hist is not None else None,
+                                          hist_len, _stream_handle(stream, edges.device))
+        _check(rc, "cc_degree_distribution")
+        return deg, hist
+
+    def ks_statistic(self, hist, stream=None) -> dict:
+        """Power-law fit + K-S statistic of a device uint64 (int64 tensor) degree histogram."""
+        out = (ctypes.c_double * 5)()
+        rc = lib().cc_ks_statistic(self._h, hist.data_ptr(), hist.numel(), out, _stream_handle(stream, hist.device))
+        _check(rc, "cc_ks_statistic")
+        return {"D": out[0], "alpha": out[1], "xmin": int(out[2]), "ntail": int(out[3]), "ncand": int(out[4])}
+
+    def stats(self) -> dict:
+        s = Stats()
+        lib().cc_get_stats(self._h, ctypes.byref(s))
+        return s.as_dict()
+
+
+def strerror(status: int) -> str:
+    return lib().cc_strerror(status).decode()

@@ -1,0 +1,588 @@
+// C ABI and host orchestration of the hybrid connected-components route
+// (Algorithm 2, Section 3.2): degree distribution -> K-S prediction ->
+// optional BFS from the max-degree vertex with the visited pairs filtered ->
+// Shiloach-Vishkin iterations -> labels. Declared in include/cc_gb300.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/cc_gb300.h"
+#include "cc_common.cuh"
+#include "cc_kernels.h"
+
+using namespace ccg;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+enum Ev { EV_START, EV_DEGREE, EV_PREDICT, EV_CSR, EV_BFS, EV_SV, EV_END, EV_COUNT };
+
+}  // namespace
+
+struct cc_ctx {
+    int device = 0;
+    cc_options opt{};
+    int num_sms = 0;
+    int grid = 0;  // blocks for grid-stride kernels
+    // SV / degree workspace
+    size_t n_cap = 0, m_cap = 0;
+    Buf deg, parent, hooked, ebuf0, ebuf1, hist, ovf, ks_xs, ks_cnt, ks_cum, ks_lnx, ks_Dc, ks_Ac, chunk_nz,
+        chunk_mass, st;
+    unsigned long long ovf_cap = 0;
+    // BFS workspace
+    size_t bn_cap = 0, bm_cap = 0;
+    Buf row_ptr, col, vis, fb, nb, q0, q1, dq, off, tsum, counters;
+    // host side
+    DevState *h_st = nullptr;  // pinned mirror of the device state
+    cudaEvent_t ev[EV_COUNT] = {};
+    bool ev_used[EV_COUNT] = {};
+    cudaStream_t last_stream = nullptr;
+    cc_stats stats{};
+    cc_status last_status = CC_OK;
+    int alloc_fail_pending = 0;
+};
+
+namespace {
+
+cc_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return CC_OK;
+    if (e == cudaErrorMemoryAllocation) return CC_ERR_OOM;
+    return CC_ERR_CUDA;
+}
+
+#define CC_TRY(expr)                             \
+    do {                                         \
+        cc_status _s = (expr);                   \
+        if (_s != CC_OK) return _s;              \
+    } while (0)
+#define CU_TRY(expr) CC_TRY(cuda_status(expr))
+
+cc_status buf_reserve(cc_ctx *ctx, Buf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return CC_OK;
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (ctx->alloc_fail_pending) {
+        ctx->alloc_fail_pending = 0;
+        return CC_ERR_OOM;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return CC_ERR_OOM;
+    }
+    b.bytes = bytes;
+    return CC_OK;
+}
+
+void buf_free(Buf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+size_t round4(size_t x) { return (x + 3) & ~(size_t)3; }
+
+cc_status ensure_sv(cc_ctx *ctx, size_t n, size_t m) {
+    if (n <= ctx->n_cap && m <= ctx->m_cap && ctx->st.p) return CC_OK;
+    const size_t N = n > ctx->n_cap ? n : ctx->n_cap, M = m > ctx->m_cap ? m : ctx->m_cap;
+    CC_TRY(buf_reserve(ctx, ctx->deg, round4(N + 4) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->parent, round4(N + 4) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->hooked, round4(N + 4) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->ebuf0, (M + 4) * 8));
+    CC_TRY(buf_reserve(ctx, ctx->ebuf1, (M + 4) * 8));
+    CC_TRY(buf_reserve(ctx, ctx->hist, (size_t)kHistDense * 4));
+    ctx->ovf_cap = 2 * (unsigned long long)M / kHistDense + 2;
+    CC_TRY(buf_reserve(ctx, ctx->ovf, ctx->ovf_cap * 4));
+    const size_t nd = (N < (size_t)kHistDense + 4096 ? N : (size_t)kHistDense + 4096) + 2;
+    CC_TRY(buf_reserve(ctx, ctx->ks_xs, nd * 4));
+    CC_TRY(buf_reserve(ctx, ctx->ks_cnt, nd * 8));
+    CC_TRY(buf_reserve(ctx, ctx->ks_cum, nd * 8));
+    CC_TRY(buf_reserve(ctx, ctx->ks_lnx, nd * 8));
+    CC_TRY(buf_reserve(ctx, ctx->ks_Dc, nd * 8));
+    CC_TRY(buf_reserve(ctx, ctx->ks_Ac, nd * 8));
+    CC_TRY(buf_reserve(ctx, ctx->chunk_nz, (size_t)(ks_num_chunks() + 1) * 8));
+    CC_TRY(buf_reserve(ctx, ctx->chunk_mass, (size_t)(ks_num_chunks() + 1) * 8));
+    CC_TRY(buf_reserve(ctx, ctx->st, sizeof(DevState)));
+    ctx->n_cap = N;
+    ctx->m_cap = M;
+    return CC_OK;
+}
+
+cc_status ensure_bfs(cc_ctx *ctx, size_t n, size_t m) {
+    if (n <= ctx->bn_cap && m <= ctx->bm_cap && ctx->row_ptr.p) return CC_OK;
+    const size_t N = n > ctx->bn_cap ? n : ctx->bn_cap, M = m > ctx->bm_cap ? m : ctx->bm_cap;
+    const size_t words = (N + 31) / 32 + 4;
+    CC_TRY(buf_reserve(ctx, ctx->row_ptr, round4(N + 8) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->col, (2 * M + 4) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->vis, words * 4));
+    CC_TRY(buf_reserve(ctx, ctx->fb, words * 4));
+    CC_TRY(buf_reserve(ctx, ctx->nb, words * 4));
+    CC_TRY(buf_reserve(ctx, ctx->q0, (N + 4) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->q1, (N + 4) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->dq, (N + 4) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->off, (N + 8) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->tsum, (size_t)(scan_num_tiles((long long)N + 2) + 4) * 8));
+    CC_TRY(buf_reserve(ctx, ctx->counters, 64 * 8));
+    ctx->bn_cap = N;
+    ctx->bm_cap = M;
+    return CC_OK;
+}
+
+template <typename P>
+P *as(const Buf &b) {
+    return reinterpret_cast<P *>(b.p);
+}
+
+cc_status check_options(const cc_options *o) {
+    if (o->id_bytes != 4 && o->id_bytes != 8) return CC_ERR_INVALID_ARG;
+    if (o->route_policy < CC_ROUTE_AUTO || o->route_policy > CC_ROUTE_FORCE_SV) return CC_ERR_INVALID_ARG;
+    if (!(o->ks_tau >= 0.0 && o->ks_tau <= 2.0)) return CC_ERR_INVALID_ARG;
+    if (o->ks_min_tail < 1 || o->ks_min_distinct < 1 || o->max_iters < 0 || o->bfs_cutoff_levels < 0 ||
+        !(o->ks_min_span >= 0.0))
+        return CC_ERR_INVALID_ARG;
+    if (o->max_iters > kMaxIters - 1) return CC_ERR_INVALID_ARG;
+    return CC_OK;
+}
+
+void rec(cc_ctx *ctx, Ev e, cudaStream_t s) {
+    cudaEventRecord(ctx->ev[e], s);
+    ctx->ev_used[e] = true;
+}
+
+// Copies `bytes` of the device state at `dev_ptr` (a member of ctx->st) into
+// the same offset of the pinned mirror and waits for it.
+cc_status read_back(cc_ctx *ctx, const void *dev_ptr, size_t bytes, cudaStream_t s) {
+    const size_t off = (size_t)(reinterpret_cast<const char *>(dev_ptr) - reinterpret_cast<const char *>(ctx->st.p));
+    CU_TRY(cudaMemcpyAsync(reinterpret_cast<char *>(ctx->h_st) + off, dev_ptr, bytes, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    return CC_OK;
+}
+
+cc_status device_error(uint32_t err) {
+    if (err & kErrInvalidEdge) return CC_ERR_INVALID_EDGE;
+    if (err & kErrNoConvergence) return CC_ERR_NO_CONVERGENCE;
+    if (err & kErrOverflow) return CC_ERR_CUDA;
+    return CC_OK;
+}
+
+int default_max_iters(long long n) {
+    int lg = 0;
+    while (lg < 62 && (1LL << lg) < n) lg++;
+    int c = 64 + 4 * lg;
+    return c < kMaxIters - 1 ? c : kMaxIters - 1;
+}
+
+// Degree pass + histogram + K-S fit; leaves the route in DevState.
+template <typename T>
+void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s) {
+    cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
+    cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s);
+    launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), as<DevState>(ctx->st), ctx->grid, s);
+    launch_hist(as<uint32_t>(ctx->deg), n, as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap,
+                as<DevState>(ctx->st), ctx->grid, s);
+}
+
+void enqueue_ks(cc_ctx *ctx, cudaStream_t s) {
+    KsScratch ks{as<uint32_t>(ctx->ks_xs), as<unsigned long long>(ctx->ks_cnt), as<unsigned long long>(ctx->ks_cum),
+                 as<double>(ctx->ks_lnx), as<double>(ctx->ks_Dc), as<double>(ctx->ks_Ac),
+                 as<unsigned long long>(ctx->chunk_nz), as<unsigned long long>(ctx->chunk_mass)};
+    launch_ks(as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap, ks, as<DevState>(ctx->st),
+              ctx->opt.ks_min_tail, ctx->opt.ks_min_distinct, ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->grid, s);
+}
+
+// CSR + direction-optimizing BFS from the max-degree vertex. Returns the
+// number of levels run; leaves the visited bitmap in ctx->vis and cmin in DevState.
+template <typename T>
+cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s, int *levels_out) {
+    DevState *st = as<DevState>(ctx->st);
+    uint32_t *row_ptr = as<uint32_t>(ctx->row_ptr), *deg = as<uint32_t>(ctx->deg);
+    vid_t *col = as<vid_t>(ctx->col);
+    const long long nwords = ((long long)n + 31) / 32;
+    // row_ptr = exclusive scan of deg; deg becomes the scatter cursor
+    launch_scan_u32(deg, n, row_ptr, deg, as<unsigned long long>(ctx->tsum), nullptr, row_ptr + n, s);
+    launch_csr_scatter<T>(edges, m, n, deg, col, ctx->grid, s);
+    rec(ctx, EV_CSR, s);
+    cudaMemsetAsync(ctx->vis.p, 0, (size_t)nwords * 4, s);
+    vid_t *qcur = as<vid_t>(ctx->q0), *qnext = as<vid_t>(ctx->q1);
+    uint32_t *fb = as<uint32_t>(ctx->fb), *nb = as<uint32_t>(ctx->nb), *vis = as<uint32_t>(ctx->vis);
+    launch_bfs_init(row_ptr, n, vis, qcur, st, s);
+    // Beamer's switching rule: go bottom-up when the frontier's edges exceed
+    // 1/alpha of the unexplored edges; come back when the frontier holds fewer
+    // than n/beta vertices and is shrinking.
+    const double alpha = 14.0, beta = 24.0;
+    bool bottom_up = false, have_queue = true;
+    unsigned long long f = 1, fe = 0, explored = 0, prev_f = 0;
+    const unsigned long long total_edges = 2ull * (unsigned long long)m;
+    CC_TRY(read_back(ctx, &st->front_edges[0], 8, s));
+    fe = ctx->h_st->front_edges[0];
+    int level = 0;
+    const int cutoff = ctx->opt.bfs_cutoff_levels;
+    unsigned long long *cnt = as<unsigned long long>(ctx->counters);
+    while (f > 0 && level < kMaxLevels - 1) {
+        if (cutoff > 0 && level >= cutoff) break;
+        const unsigned long long unexplored = total_edges > explored ? total_edges - explored : 0;
+        if (!bottom_up && (double)fe > (double)unexplored / alpha) bottom_up = true;
+        else if (bottom_up && (double)f < (double)n / beta && f < prev_f) bottom_up = false;
+        if (bottom_up) {
+            if (have_queue) {
+                cudaMemsetAsync(fb, 0, (size_t)nwords * 4, s);
+                launch_queue_to_bitmap(qcur, (long long)f, fb, ctx->grid, s);
+                have_queue = false;
+            }
+            launch_bfs_bottomup(n, row_ptr, col, fb, vis, nb, st, level, ctx->grid, s);
+            uint32_t *t = fb;
+            fb = nb;
+            nb = t;
+        } else {
+            if (!have_queue) {
+                cudaMemsetAsync(cnt, 0, 8, s);
+                launch_bitmap_to_queue(fb, nwords, qcur, cnt, ctx->grid, s);
+                have_queue = true;
+            }
+            uint32_t *dq = as<uint32_t>(ctx->dq), *off = as<uint32_t>(ctx->off);
+            launch_front_degrees(qcur, (long long)f, row_ptr, dq, ctx->grid, s);
+            launch_scan_u32(dq, (long long)f, off, nullptr, as<unsigned long long>(ctx->tsum), nullptr, nullptr, s);
+            launch_bfs_topdown(qcur, (long long)f, off, (long long)fe, row_ptr, col, vis, qnext, st, level, ctx->grid,
+                               s);
+            vid_t *t = qcur;
+            qcur = qnext;
+            qnext = t;
+        }
+        explored += fe;
+        CU_TRY(cudaMemcpyAsync(&ctx->h_st->front[level + 1], &st->front[level + 1], 8, cudaMemcpyDeviceToHost, s));
+        CC_TRY(read_back(ctx, &st->front_edges[level + 1], 8, s));
+        prev_f = f;
+        f = ctx->h_st->front[level + 1];
+        fe = ctx->h_st->front_edges[level + 1];
+        level++;
+    }
+    *levels_out = level;
+    // visited count and the smallest visited id (the BFS component's label)
+    cudaMemsetAsync(cnt + 1, 0, 8, s);
+    launch_popcount(vis, nwords, cnt + 1, ctx->grid, s);
+    launch_first_visited(vis, nwords, st, ctx->grid, s);
+    return CC_OK;
+}
+
+template <typename T>
+cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void *labels_out, cudaStream_t s) {
+    DevState *st = as<DevState>(ctx->st);
+    cc_stats &S = ctx->stats;
+    memset(&S, 0, sizeof(S));
+    S.n = n;
+    S.m = m;
+    for (int e = 0; e < EV_COUNT; e++) ctx->ev_used[e] = false;
+    CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+    rec(ctx, EV_START, s);
+    const int policy = ctx->opt.route_policy;
+    int route = 0;
+    S.route_source = policy == CC_ROUTE_AUTO || policy == CC_ROUTE_LEARNED ? 0 : 2;
+    if (policy != CC_ROUTE_FORCE_SV && m > 0) {
+        enqueue_degree<T>(ctx, edges, n, m, s);
+        rec(ctx, EV_DEGREE, s);
+        if (policy != CC_ROUTE_FORCE_BFS) enqueue_ks(ctx, s);
+        rec(ctx, EV_PREDICT, s);
+        CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, kept), cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaStreamSynchronize(s));
+        if (ctx->h_st->err) return device_error(ctx->h_st->err);
+        route = policy == CC_ROUTE_FORCE_BFS ? 1 : ctx->h_st->route;
+        S.ks_d = ctx->h_st->ks_out[0];
+        S.ks_alpha = ctx->h_st->ks_out[1];
+        S.ks_xmin = (int64_t)ctx->h_st->ks_out[2];
+        S.ks_ntail = (int64_t)ctx->h_st->ks_out[3];
+        S.ks_ncand = (int64_t)ctx->h_st->ks_out[4];
+        S.max_degree = (int64_t)(ctx->h_st->maxkey >> 32);
+        S.seed_vertex = (int64_t)(0xffffffffu - (uint32_t)(ctx->h_st->maxkey & 0xffffffffu));
+        if (policy == CC_ROUTE_FORCE_BFS) S.ks_d = 0.0;
+    }
+    // the CSR uses 32-bit offsets: the BFS step needs 2m < 2^32
+    if (route == 1 && 2ull * (unsigned long long)m >= 0xffffffffull) route = 0;
+    S.route = route;
+    const int cap = ctx->opt.fault_inject & CC_FAULT_ITER_CAP ? 1
+                    : ctx->opt.max_iters > 0                  ? ctx->opt.max_iters
+                                                              : default_max_iters(n);
+    vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
+    uint2 *eb[2] = {as<uint2>(ctx->ebuf0), as<uint2>(ctx->ebuf1)};
+    int it = 0;
+    unsigned long long m_cur = 0;
+    const void *src = nullptr;
+    if (route == 1) {
+        CC_TRY(ensure_bfs(ctx, n, (size_t)m));
+        int levels = 0;
+        CC_TRY(run_bfs<T>(ctx, edges, n, m, s, &levels));
+        rec(ctx, EV_BFS, s);
+        CU_TRY(cudaMemcpyAsync(&ctx->h_st->cmin, &st->cmin, 4, cudaMemcpyDeviceToHost, s));
+        unsigned long long visited = 0;
+        CU_TRY(cudaMemcpyAsync(&visited, as<unsigned long long>(ctx->counters) + 1, 8, cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaStreamSynchronize(s));
+        const vid_t cmin = ctx->h_st->cmin;
+        S.bfs_levels = levels;
+        S.bfs_visited = (int64_t)visited;
+        S.comp_min = cmin;
+        launch_parent_init(parent, n, as<uint32_t>(ctx->vis), cmin, ctx->grid, s);
+        launch_sv_pass<T>(1, true, edges, m, n, parent, as<uint32_t>(ctx->vis), cmin, hooked, eb[0], st, 0, ctx->grid,
+                          s);
+        launch_sv_shortcut(parent, hooked, st, 0, ctx->grid, s);
+        S.m_active[0] = m;
+        CC_TRY(read_back(ctx, &st->kept[0], 8, s));
+        m_cur = ctx->h_st->kept[0];
+        src = eb[0];
+    } else {
+        launch_parent_init(parent, n, nullptr, 0, ctx->grid, s);
+        if (m > 0) {
+            launch_sv_pass<T>(0, false, edges, m, n, parent, nullptr, 0, hooked, nullptr, st, 0, ctx->grid, s);
+            launch_sv_shortcut(parent, hooked, st, 0, ctx->grid, s);
+            S.m_active[0] = m;
+            it = 1;
+            if (it >= cap) {
+                CC_TRY(read_back(ctx, &st->err, 4, s));
+                return ctx->h_st->err ? device_error(ctx->h_st->err) : CC_ERR_NO_CONVERGENCE;
+            }
+            launch_sv_pass<T>(2, true, edges, m, n, parent, nullptr, 0, hooked, eb[0], st, 1, ctx->grid, s);
+            launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, s);
+            S.m_active[1] = m;
+            CC_TRY(read_back(ctx, &st->kept[1], 8, s));
+            m_cur = ctx->h_st->kept[1];
+            src = eb[0];
+        }
+    }
+    int cur = 0;
+    while (m_cur > 0) {
+        it++;
+        if (it >= cap) {
+            S.sv_iters = it;
+            return CC_ERR_NO_CONVERGENCE;
+        }
+        if (it < CC_MAX_SV_ITERS_RECORDED) S.m_active[it] = (int64_t)m_cur;
+        launch_sv_pass<uint32_t>(2, true, src, (long long)m_cur, n, parent, nullptr, 0, hooked, eb[1 - cur], st, it,
+                                 ctx->grid, s);
+        launch_sv_shortcut(parent, hooked, st, it, ctx->grid, s);
+        cur = 1 - cur;
+        src = eb[cur];
+        CU_TRY(cudaMemcpyAsync(&ctx->h_st->kept[it], &st->kept[it], 8, cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaStreamSynchronize(s));
+        m_cur = ctx->h_st->kept[it];
+    }
+    S.sv_iters = it + 1;
+    rec(ctx, EV_SV, s);
+    launch_finalize<T>(parent, n, labels_out, ctx->grid, s);
+    rec(ctx, EV_END, s);
+    CU_TRY(cudaMemcpyAsync(&ctx->h_st->err, &st->err, 4, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    CU_TRY(cudaGetLastError());
+    return device_error(ctx->h_st->err);
+}
+
+float ev_ms(cc_ctx *ctx, Ev a, Ev b) {
+    if (!ctx->ev_used[a] || !ctx->ev_used[b]) return 0.0f;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0f;
+    }
+    return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+cc_status cc_default_options(cc_options *opt) {
+    if (!opt) return CC_ERR_INVALID_ARG;
+    memset(opt, 0, sizeof(*opt));
+    opt->id_bytes = 4;
+    opt->route_policy = CC_ROUTE_AUTO;
+    opt->ks_tau = 0.05;
+    opt->ks_min_tail = 50;
+    opt->ks_min_distinct = 3;
+    opt->ks_min_span = 10.0;
+    return CC_OK;
+}
+
+cc_status cc_create(cc_ctx **out, const cc_options *opt, int device) {
+    if (!out) return CC_ERR_INVALID_ARG;
+    *out = nullptr;
+    cc_options o;
+    if (opt) o = *opt;
+    else cc_default_options(&o);
+    CC_TRY(check_options(&o));
+    int ndev = 0;
+    CU_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return CC_ERR_INVALID_ARG;
+    CU_TRY(cudaSetDevice(device));
+    cc_ctx *ctx = new (std::nothrow) cc_ctx();
+    if (!ctx) return CC_ERR_OOM;
+    ctx->device = device;
+    ctx->opt = o;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete ctx;
+        return CC_ERR_CUDA;
+    }
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->grid = ctx->num_sms * (prop.maxThreadsPerMultiProcessor / kBlock);
+    if (cudaMallocHost(&ctx->h_st, sizeof(DevState)) != cudaSuccess) {
+        delete ctx;
+        return CC_ERR_OOM;
+    }
+    memset(ctx->h_st, 0, sizeof(DevState));
+    for (int e = 0; e < EV_COUNT; e++) cudaEventCreate(&ctx->ev[e]);
+    *out = ctx;
+    return CC_OK;
+}
+
+cc_status cc_set_options(cc_ctx *ctx, const cc_options *opt) {
+    if (!ctx || !opt) return CC_ERR_INVALID_ARG;
+    CC_TRY(check_options(opt));
+    ctx->opt = *opt;
+    return CC_OK;
+}
+
+cc_status cc_destroy(cc_ctx *ctx) {
+    if (!ctx) return CC_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    Buf *bufs[] = {&ctx->deg,    &ctx->parent,     &ctx->hooked, &ctx->ebuf0,   &ctx->ebuf1,  &ctx->hist,
+                   &ctx->ovf,    &ctx->ks_xs,      &ctx->ks_cnt, &ctx->ks_cum,  &ctx->ks_lnx, &ctx->ks_Dc,
+                   &ctx->ks_Ac,  &ctx->chunk_nz,   &ctx->chunk_mass, &ctx->st,  &ctx->row_ptr, &ctx->col,
+                   &ctx->vis,    &ctx->fb,         &ctx->nb,     &ctx->q0,      &ctx->q1,     &ctx->dq,
+                   &ctx->off,    &ctx->tsum,       &ctx->counters};
+    for (Buf *b : bufs) buf_free(*b);
+    for (int e = 0; e < EV_COUNT; e++)
+        if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
+    if (ctx->h_st) cudaFreeHost(ctx->h_st);
+    delete ctx;
+    return CC_OK;
+}
+
+cc_status cc_labels(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, void *labels_out_dev, void *stream) {
+    if (!ctx) return CC_ERR_INVALID_ARG;
+    if (n < 0 || m < 0) return CC_ERR_INVALID_ARG;
+    if (n >= 0xffffffffLL) return CC_ERR_UNSUPPORTED;
+    if (m >= (1LL << 31)) return CC_ERR_UNSUPPORTED;
+    if (n == 0) {
+        if (m > 0) return CC_ERR_INVALID_EDGE;
+        return CC_OK;
+    }
+    if (!labels_out_dev || (m > 0 && !edges_dev)) return CC_ERR_INVALID_ARG;
+    if (((uintptr_t)edges_dev & 15) || ((uintptr_t)labels_out_dev & 15)) return CC_ERR_INVALID_ARG;
+    CU_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    if (ctx->opt.fault_inject & CC_FAULT_ALLOC) ctx->alloc_fail_pending = 1;
+    cc_status st = ensure_sv(ctx, (size_t)n, (size_t)m);
+    ctx->alloc_fail_pending = 0;
+    if (st != CC_OK) {
+        ctx->last_status = st;
+        return st;
+    }
+    if (ctx->opt.id_bytes == 4) st = labels_impl<int32_t>(ctx, edges_dev, (vid_t)n, m, labels_out_dev, s);
+    else st = labels_impl<int64_t>(ctx, edges_dev, (vid_t)n, m, labels_out_dev, s);
+    if (st == CC_OK || st == CC_ERR_INVALID_EDGE || st == CC_ERR_NO_CONVERGENCE) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+    }
+    ctx->last_status = st;
+    ctx->stats.status = st;
+    return st;
+}
+
+cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *edge_offsets_dev,
+                            const int64_t *vertex_offsets_dev, const int64_t *edge_offsets_host,
+                            const int64_t *vertex_offsets_host, int G, void *labels_out_dev, void *stream) {
+    (void)ctx; (void)edges_dev; (void)edge_offsets_dev; (void)vertex_offsets_dev; (void)edge_offsets_host;
+    (void)vertex_offsets_host; (void)G; (void)labels_out_dev; (void)stream;
+    return CC_ERR_UNSUPPORTED;
+}
+
+cc_status cc_degree_distribution(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, uint32_t *deg_out_dev,
+                                 uint64_t *hist_out_dev, int64_t hist_len, void *stream) {
+    if (!ctx || n < 0 || m < 0 || hist_len < 0) return CC_ERR_INVALID_ARG;
+    if (n >= 0xffffffffLL || m >= (1LL << 31)) return CC_ERR_UNSUPPORTED;
+    if (n == 0) return m > 0 ? CC_ERR_INVALID_EDGE : CC_OK;
+    if ((m > 0 && !edges_dev) || ((uintptr_t)edges_dev & 15)) return CC_ERR_INVALID_ARG;
+    CU_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    CC_TRY(ensure_sv(ctx, (size_t)n, (size_t)m));
+    DevState *st = as<DevState>(ctx->st);
+    CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+    if (ctx->opt.id_bytes == 4) enqueue_degree<int32_t>(ctx, edges_dev, (vid_t)n, m, s);
+    else enqueue_degree<int64_t>(ctx, edges_dev, (vid_t)n, m, s);
+    if (deg_out_dev) CU_TRY(cudaMemcpyAsync(deg_out_dev, ctx->deg.p, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, kept), cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    if (ctx->h_st->err) return device_error(ctx->h_st->err);
+    if (hist_out_dev && hist_len > 0)
+        launch_hist_widen(as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap, st, hist_out_dev, hist_len,
+                          ctx->grid, s);
+    CU_TRY(cudaStreamSynchronize(s));
+    CU_TRY(cudaGetLastError());
+    return CC_OK;
+}
+
+cc_status cc_ks_statistic(cc_ctx *ctx, const uint64_t *hist_dev, int64_t hist_len, double *out_host, void *stream) {
+    if (!ctx || !hist_dev || hist_len < 1 || !out_host) return CC_ERR_INVALID_ARG;
+    if (hist_len > (int64_t)kHistDense) return CC_ERR_UNSUPPORTED;
+    CU_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    CC_TRY(ensure_sv(ctx, 1, 1));
+    DevState *st = as<DevState>(ctx->st);
+    CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+    CU_TRY(cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s));
+    launch_hist_narrow(hist_dev, hist_len, as<uint32_t>(ctx->hist), st, ctx->grid, s);
+    enqueue_ks(ctx, s);
+    CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, kept), cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    CU_TRY(cudaGetLastError());
+    if (ctx->h_st->err) return CC_ERR_UNSUPPORTED;
+    for (int i = 0; i < 5; i++) out_host[i] = ctx->h_st->ks_out[i];
+    return CC_OK;
+}
+
+cc_status cc_get_stats(cc_ctx *ctx, cc_stats *out) {
+    if (!ctx || !out) return CC_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->last_stream);
+    cc_stats &S = ctx->stats;
+    S.ms_degree = ev_ms(ctx, EV_START, EV_DEGREE);
+    S.ms_predict = ev_ms(ctx, EV_DEGREE, EV_PREDICT);
+    S.ms_csr = ev_ms(ctx, EV_PREDICT, EV_CSR);
+    S.ms_bfs = ev_ms(ctx, EV_CSR, EV_BFS);
+    S.ms_sv = ctx->ev_used[EV_BFS] ? ev_ms(ctx, EV_BFS, EV_SV)
+              : ctx->ev_used[EV_PREDICT] ? ev_ms(ctx, EV_PREDICT, EV_SV)
+                                         : ev_ms(ctx, EV_START, EV_SV);
+    S.ms_finalize = ev_ms(ctx, EV_SV, EV_END);
+    S.ms_total = ev_ms(ctx, EV_START, EV_END);
+    S.status = ctx->last_status;
+    *out = S;
+    return ctx->last_status;
+}
+
+const char *cc_strerror(cc_status s) {
+    switch (s) {
+        case CC_OK: return "ok";
+        case CC_ERR_INVALID_ARG: return "invalid argument";
+        case CC_ERR_INVALID_EDGE: return "edge id outside [0, n)";
+        case CC_ERR_OOM: return "device workspace allocation failed";
+        case CC_ERR_NO_CONVERGENCE: return "iteration cap exceeded";
+        case CC_ERR_TIMEOUT: return "bounded device wait ran out";
+        case CC_ERR_CUDA: return "CUDA runtime error";
+        case CC_ERR_UNSUPPORTED: return "size outside the engine's limits";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Shared device-side definitions of the GB300 connected-components engine.
+//
+// Internal vertex ids are 32-bit (n < 2^32 - 1). Inputs may be int32 or int64
+// pairs; every kernel that touches the caller's edge list is templated on the
+// id type and reads it with 128-bit loads (two int32 pairs or one int64 pair
+// per load). Internal edge lists are uint2 pairs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ccg {
+
+typedef uint32_t vid_t;
+
+constexpr int kBlock = 256;            // threads per block for the streaming kernels
+constexpr int kMaxIters = 256;         // SV iteration slots recorded on the device
+constexpr int kMaxLevels = 4096;       // BFS level slots recorded on the device
+constexpr uint32_t kHistDense = 1u << 20;   // degrees below this get a dense histogram bin
+constexpr uint32_t kHistSmem = 4096;        // bins privatised in shared memory
+
+// Device error bits (collected in DevState::err).
+enum : uint32_t {
+    kErrInvalidEdge = 1u,
+    kErrOverflow = 2u,     // an internal capacity was exceeded (a bug guard, never expected)
+    kErrNoConvergence = 4u,
+};
+
+// Device-resident bookkeeping for one cc_labels call. Zeroed at the start of
+// each call (cudaMemsetAsync); slots indexed by iteration avoid resets.
+struct DevState {
+    uint32_t err;
+    uint32_t cmin;                          // min id among BFS-visited vertices
+    unsigned long long maxkey;              // (deg << 32) | (0xffffffff - v): argmax degree, ties to min id
+    unsigned long long n_ovf;               // overflow degrees (>= kHistDense) recorded
+    unsigned long long nd;                  // distinct degrees >= 1
+    unsigned long long ncand;               // K-S candidates
+    unsigned long long bfs_visited;
+    unsigned long long bfs_inspected;       // adjacency entries read by the BFS
+    double ks_out[5];                       // D, alpha, xmin, ntail, ncand
+    int route;                              // 1 = BFS first
+    int pad;
+    unsigned long long kept[kMaxIters];     // active pairs written by SV iteration i
+    unsigned long long hooked[kMaxIters];   // roots hooked in SV iteration i
+    unsigned long long hook_base[kMaxIters + 1];  // start of iteration i's slice of the hooked list
+    unsigned long long front[kMaxLevels];   // BFS frontier size entering level l
+    unsigned long long front_edges[kMaxLevels];  // sum of degrees of that frontier
+};
+
+// ---------------------------------------------------------------------------
+// Loads of the caller's edge list.
+
+// Streaming 128-bit load that does not allocate in L1 (edges are read once per pass).
+__device__ __forceinline__ int4 ld_stream(const int4 *p) { return __ldcs(p); }
+__device__ __forceinline__ uint4 ld_stream(const uint4 *p) { return __ldcs(p); }
+
+// Number of 128-bit vectors holding whole pairs, and pairs per vector, for id type T.
+template <typename T> struct PairVec;
+template <> struct PairVec<int32_t> { static constexpr int kPairs = 2; };
+template <> struct PairVec<int64_t> { static constexpr int kPairs = 1; };
+
+// Decodes pair `j` (0..kPairs-1) of a 128-bit vector as unsigned 64-bit ids.
+template <typename T>
+__device__ __forceinline__ void vec_pair(const int4 &q, int j, long long &u, long long &v);
+template <>
+__device__ __forceinline__ void vec_pair<int32_t>(const int4 &q, int j, long long &u, long long &v) {
+    u = j == 0 ? (long long)q.x : (long long)q.z;
+    v = j == 0 ? (long long)q.y : (long long)q.w;
+}
+template <>
+__device__ __forceinline__ void vec_pair<int64_t>(const int4 &q, int, long long &u, long long &v) {
+    u = (long long)(((unsigned long long)(unsigned)q.y << 32) | (unsigned)q.x);
+    v = (long long)(((unsigned long long)(unsigned)q.w << 32) | (unsigned)q.z);
+}
+
+template <typename T>
+__device__ __forceinline__ void scalar_pair(const T *e, long long k, long long &u, long long &v) {
+    u = (long long)e[2 * k];
+    v = (long long)e[2 * k + 1];
+}
+
+// ---------------------------------------------------------------------------
+// Warp-aggregated append: every lane with `want` gets a distinct slot of a
+// global counter; one atomic per warp.
+__device__ __forceinline__ unsigned long long warp_append(unsigned long long *counter, bool want) {
+    const unsigned mask = __activemask();
+    const unsigned ballot = __ballot_sync(mask, want);
+    if (!ballot) return 0;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(ballot) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(ballot));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(ballot & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ void set_err(DevState *st, uint32_t bit) { atomicOr(&st->err, bit); }
+
+// Grid-stride helpers
+__device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
+
+}  // namespace ccg

@@ -1,0 +1,64 @@
+// Host-side launchers of the engine's kernels (one definition per .cu file).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cc_common.cuh"
+
+namespace ccg {
+
+// Scratch of the K-S fit (device arrays, sized for the distinct degrees).
+struct KsScratch {
+    uint32_t *xs;                  // distinct degrees >= 1, increasing
+    unsigned long long *cnt;       // vertices per distinct degree
+    unsigned long long *cum;       // exclusive prefix of cnt (one extra entry: total)
+    double *lnx;                   // ln(xs)
+    double *Dc, *Ac;               // D and alpha per candidate xmin
+    unsigned long long *chunk_nz;  // per-chunk distinct counts, then offsets
+    unsigned long long *chunk_mass;
+};
+
+// k_degree.cu
+template <typename T>
+void launch_degree(const void *edges, long long m, vid_t n, uint32_t *deg, DevState *st, int grid, cudaStream_t s);
+void launch_hist(const uint32_t *deg, vid_t n, uint32_t *hist, uint32_t *ovf, unsigned long long ovf_cap,
+                 DevState *st, int grid, cudaStream_t s);
+void launch_ks(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf_cap, KsScratch ks, DevState *st,
+               long long min_tail, long long min_distinct, double min_span, double tau, int grid, cudaStream_t s);
+int ks_num_chunks();
+void launch_hist_widen(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf_cap, const DevState *st,
+                       uint64_t *out, long long len, int grid, cudaStream_t s);
+void launch_hist_narrow(const uint64_t *in, long long len, uint32_t *hist, DevState *st, int grid, cudaStream_t s);
+
+// k_sv.cu
+template <typename T>
+void launch_sv_pass(int mode, bool write, const void *in, long long m, vid_t n, vid_t *parent, const uint32_t *vis,
+                    vid_t cmin, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid, cudaStream_t s);
+void launch_sv_shortcut(vid_t *parent, const vid_t *hooked_list, DevState *st, int it, int grid, cudaStream_t s);
+void launch_parent_init(vid_t *parent, vid_t n, const uint32_t *vis, vid_t cmin, int grid, cudaStream_t s);
+template <typename T>
+void launch_finalize(vid_t *parent, vid_t n, void *labels, int grid, cudaStream_t s);
+
+// k_bfs.cu
+void launch_scan_u32(const uint32_t *in, long long len, uint32_t *out, uint32_t *out_copy, unsigned long long *tsum,
+                     unsigned long long *total_dev, uint32_t *total_u32, cudaStream_t s);
+long long scan_num_tiles(long long len);
+template <typename T>
+void launch_csr_scatter(const void *edges, long long m, vid_t n, uint32_t *cursor, vid_t *col, int grid,
+                        cudaStream_t s);
+void launch_bfs_init(const uint32_t *row_ptr, vid_t n, uint32_t *vis, vid_t *queue, DevState *st, cudaStream_t s);
+void launch_front_degrees(const vid_t *queue, long long f, const uint32_t *row_ptr, uint32_t *dq, int grid,
+                          cudaStream_t s);
+void launch_bfs_topdown(const vid_t *queue, long long f, const uint32_t *off, long long total, const uint32_t *row_ptr,
+                        const vid_t *col, uint32_t *vis, vid_t *next, DevState *st, int level, int grid,
+                        cudaStream_t s);
+void launch_bfs_bottomup(vid_t n, const uint32_t *row_ptr, const vid_t *col, const uint32_t *fb, uint32_t *vis,
+                         uint32_t *nb, DevState *st, int level, int grid, cudaStream_t s);
+void launch_queue_to_bitmap(const vid_t *queue, long long f, uint32_t *bm, int grid, cudaStream_t s);
+void launch_bitmap_to_queue(const uint32_t *bm, long long nwords, vid_t *queue, unsigned long long *count, int grid,
+                            cudaStream_t s);
+void launch_first_visited(const uint32_t *vis, long long nwords, DevState *st, int grid, cudaStream_t s);
+void launch_popcount(const uint32_t *bm, long long nwords, unsigned long long *out, int grid, cudaStream_t s);
+
+}  // namespace ccg

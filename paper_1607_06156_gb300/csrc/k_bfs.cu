@@ -1,0 +1,359 @@
+// BFS step of the hybrid route (Section 3.2, Algorithm 2 lines 5-9).
+//
+//  scan      exclusive prefix sum (tile reduce, tile-offset scan, tile scan)
+//  CSR       row_ptr = exclusive scan of the degrees; every pair is stored in
+//            both directions (Section 3.2 stores each undirected edge as two
+//            directed edges) by an atomic cursor per vertex.
+//  BFS       level-synchronous, direction optimizing (Beamer et al., cited in
+//            Section 1): top-down levels expand the frontier queue edge-parallel
+//            (a scan of the frontier degrees splits the work evenly, so a hub
+//            of any degree is spread over the whole grid); bottom-up levels give
+//            each warp one 32-vertex word of the visited bitmap, every
+//            unvisited lane scans its adjacency until it meets a frontier
+//            vertex, and the warp's ballot is the word of the next frontier.
+//  cmin      smallest visited id: the label the BFS component ends with.
+#include "cc_common.cuh"
+#include "cc_kernels.h"
+
+namespace ccg {
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of uint32 values into uint32 prefix sums (the total must fit).
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kBlock * kScanItems;
+
+__device__ __forceinline__ unsigned long long block_scan_excl_u64(unsigned long long x, unsigned long long &total) {
+    __shared__ unsigned long long sw[33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sw[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = lane < nw ? sw[lane] : 0ull, wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) sw[lane] = wi - w;
+        if (lane == nw - 1) sw[32] = wi;
+    }
+    __syncthreads();
+    const unsigned long long r = sw[warp] + incl - x;
+    total = sw[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_up(const uint32_t *__restrict__ in, long long len,
+                                                    unsigned long long *tsum) {
+    const long long t0 = (long long)blockIdx.x * kScanTile;
+    unsigned long long s = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        const long long i = t0 + (long long)threadIdx.x * kScanItems + k;
+        if (i < len) s += in[i];
+    }
+    unsigned long long tot;
+    block_scan_excl_u64(s, tot);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_mid(unsigned long long *tsum, long long ntiles,
+                                                     unsigned long long *total_out, uint32_t *total_u32) {
+    unsigned long long carry = 0;
+    for (long long r = 0; r < ntiles; r += blockDim.x) {
+        const long long i = r + threadIdx.x;
+        const unsigned long long x = i < ntiles ? tsum[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long e = block_scan_excl_u64(x, tot);
+        if (i < ntiles) tsum[i] = carry + e;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total_out) *total_out = carry;
+    if (threadIdx.x == 0 && total_u32) *total_u32 = (uint32_t)carry;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_down(const uint32_t *__restrict__ in, long long len,
+                                                      const unsigned long long *__restrict__ tsum, uint32_t *out,
+                                                      uint32_t *out_copy) {
+    const long long t0 = (long long)blockIdx.x * kScanTile;
+    uint32_t v[kScanItems];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        const long long i = t0 + (long long)threadIdx.x * kScanItems + k;
+        v[k] = i < len ? in[i] : 0u;
+        s += v[k];
+    }
+    unsigned long long tot;
+    unsigned long long run = tsum[blockIdx.x] + block_scan_excl_u64(s, tot);
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        const long long i = t0 + (long long)threadIdx.x * kScanItems + k;
+        if (i < len) {
+            out[i] = (uint32_t)run;
+            if (out_copy) out_copy[i] = (uint32_t)run;
+        }
+        run += v[k];
+    }
+}
+
+void launch_scan_u32(const uint32_t *in, long long len, uint32_t *out, uint32_t *out_copy, unsigned long long *tsum,
+                     unsigned long long *total_dev, uint32_t *total_u32, cudaStream_t s) {
+    if (len <= 0) return;
+    const long long ntiles = (len + kScanTile - 1) / kScanTile;
+    k_scan_up<<<(unsigned)ntiles, kBlock, 0, s>>>(in, len, tsum);
+    k_scan_mid<<<1, kBlock, 0, s>>>(tsum, ntiles, total_dev, total_u32);
+    k_scan_down<<<(unsigned)ntiles, kBlock, 0, s>>>(in, len, tsum, out, out_copy);
+}
+
+long long scan_num_tiles(long long len) { return (len + kScanTile - 1) / kScanTile; }
+
+// ---------------------------------------------------------------------------
+// CSR scatter: both directions of every valid pair.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_csr_scatter(const T *__restrict__ edges, long long m, vid_t n,
+                                                        uint32_t *cursor, vid_t *col) {
+    constexpr int P = PairVec<T>::kPairs;
+    const long long nvec = m / P;
+    const int4 *ev = reinterpret_cast<const int4 *>(edges);
+    for (long long i = gtid(); i < nvec; i += gstride()) {
+        const int4 q = ld_stream(ev + i);
+#pragma unroll
+        for (int j = 0; j < P; j++) {
+            long long u, v;
+            vec_pair<T>(q, j, u, v);
+            if ((unsigned long long)u >= n || (unsigned long long)v >= n) continue;
+            col[atomicAdd(&cursor[u], 1u)] = (vid_t)v;
+            col[atomicAdd(&cursor[v], 1u)] = (vid_t)u;
+        }
+    }
+    if (P == 2 && (m & 1) && gtid() == 0) {
+        long long u, v;
+        scalar_pair<T>(edges, m - 1, u, v);
+        if ((unsigned long long)u < n && (unsigned long long)v < n) {
+            col[atomicAdd(&cursor[u], 1u)] = (vid_t)v;
+            col[atomicAdd(&cursor[v], 1u)] = (vid_t)u;
+        }
+    }
+}
+
+template <typename T>
+void launch_csr_scatter(const void *edges, long long m, vid_t n, uint32_t *cursor, vid_t *col, int grid,
+                        cudaStream_t s) {
+    if (m <= 0) return;
+    k_csr_scatter<T><<<grid, kBlock, 0, s>>>((const T *)edges, m, n, cursor, col);
+}
+template void launch_csr_scatter<int32_t>(const void *, long long, vid_t, uint32_t *, vid_t *, int, cudaStream_t);
+template void launch_csr_scatter<int64_t>(const void *, long long, vid_t, uint32_t *, vid_t *, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// BFS
+
+__global__ void k_bfs_init(const uint32_t *__restrict__ row_ptr, vid_t n, uint32_t *vis, vid_t *queue,
+                           DevState *st) {
+    vid_t s = 0xffffffffu - (vid_t)(st->maxkey & 0xffffffffull);
+    if (s >= n) s = 0;
+    vis[s >> 5] |= 1u << (s & 31);
+    queue[0] = s;
+    st->front[0] = 1;
+    st->front_edges[0] = row_ptr[s + 1] - row_ptr[s];
+    st->cmin = 0xffffffffu;
+}
+
+// dq[i] = degree of the i-th frontier vertex
+__global__ void __launch_bounds__(kBlock) k_front_degrees(const vid_t *__restrict__ queue, long long f,
+                                                          const uint32_t *__restrict__ row_ptr, uint32_t *dq) {
+    for (long long i = gtid(); i < f; i += gstride()) {
+        const vid_t v = queue[i];
+        dq[i] = row_ptr[v + 1] - row_ptr[v];
+    }
+}
+
+// Top-down: edge slot e of the frontier belongs to frontier vertex k with
+// off[k] <= e < off[k] + dq[k]; found by binary search over off.
+__global__ void __launch_bounds__(kBlock) k_bfs_topdown(const vid_t *__restrict__ queue, long long f,
+                                                        const uint32_t *__restrict__ off, long long total,
+                                                        const uint32_t *__restrict__ row_ptr,
+                                                        const vid_t *__restrict__ col, uint32_t *vis, vid_t *next,
+                                                        DevState *st, int level) {
+    const long long stride = gstride();
+    const long long rounds = (total + stride - 1) / stride;
+    unsigned long long new_edges = 0;
+    for (long long r = 0; r < rounds; r++) {
+        const long long e = gtid() + r * stride;
+        bool fresh = false;
+        vid_t w = 0;
+        if (e < total) {
+            long long lo = 0, hi = f - 1;  // largest k with off[k] <= e
+            while (lo < hi) {
+                const long long mid = (lo + hi + 1) >> 1;
+                if ((long long)off[mid] <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            const vid_t v = queue[lo];
+            const uint32_t k = (uint32_t)(e - (long long)off[lo]), b0 = row_ptr[v];
+            if (k < row_ptr[v + 1] - b0) {  // always true when total matches the frontier's degree sum
+                w = col[b0 + k];
+                const uint32_t bit = 1u << (w & 31);
+                if (!(__ldcg(&vis[w >> 5]) & bit)) {
+                    const uint32_t old = atomicOr(&vis[w >> 5], bit);
+                    fresh = !(old & bit);
+                }
+            }
+        }
+        const unsigned long long k = warp_append(&st->front[level + 1], fresh);
+        if (fresh) {
+            next[k] = w;
+            new_edges += row_ptr[w + 1] - row_ptr[w];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) new_edges += __shfl_xor_sync(0xffffffffu, new_edges, o);
+    if ((threadIdx.x & 31) == 0 && new_edges) atomicAdd(&st->front_edges[level + 1], new_edges);
+    if (gtid() == 0) atomicAdd(&st->bfs_inspected, (unsigned long long)total);
+}
+
+// Bottom-up: warp w owns vertex word w. Lanes of unvisited vertices with
+// neighbours scan their adjacency for a frontier member (bitmap fb).
+__global__ void __launch_bounds__(kBlock) k_bfs_bottomup(vid_t n, const uint32_t *__restrict__ row_ptr,
+                                                         const vid_t *__restrict__ col,
+                                                         const uint32_t *__restrict__ fb, uint32_t *vis, uint32_t *nb,
+                                                         DevState *st, int level) {
+    const long long nwords = ((long long)n + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const long long warp0 = gtid() >> 5, nwarps = gstride() >> 5;
+    unsigned long long inspected = 0, new_edges = 0, found_total = 0;
+    for (long long w = warp0; w < nwords; w += nwarps) {
+        const uint32_t vword = vis[w];
+        const long long v = w * 32 + lane;
+        bool found = false;
+        uint32_t d = 0;
+        if (v < (long long)n && !((vword >> lane) & 1u)) {
+            const uint32_t b = row_ptr[v], e = row_ptr[v + 1];
+            d = e - b;
+            for (uint32_t k = b; k < e; k++) {
+                const vid_t x = col[k];
+                inspected++;
+                if ((fb[x >> 5] >> (x & 31)) & 1u) {
+                    found = true;
+                    break;
+                }
+            }
+        }
+        const uint32_t fmask = __ballot_sync(0xffffffffu, found);
+        if (found) new_edges += d;
+        if (lane == 0) {
+            nb[w] = fmask;
+            if (fmask) vis[w] = vword | fmask;
+            found_total += __popc(fmask);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        inspected += __shfl_xor_sync(0xffffffffu, inspected, o);
+        new_edges += __shfl_xor_sync(0xffffffffu, new_edges, o);
+    }
+    if (lane == 0) {
+        if (found_total) atomicAdd(&st->front[level + 1], found_total);
+        if (new_edges) atomicAdd(&st->front_edges[level + 1], new_edges);
+        if (inspected) atomicAdd(&st->bfs_inspected, inspected);
+    }
+}
+
+// queue -> bitmap (bitmap cleared beforehand)
+__global__ void __launch_bounds__(kBlock) k_queue_to_bitmap(const vid_t *__restrict__ queue, long long f,
+                                                            uint32_t *bm) {
+    for (long long i = gtid(); i < f; i += gstride()) {
+        const vid_t v = queue[i];
+        atomicOr(&bm[v >> 5], 1u << (v & 31));
+    }
+}
+
+// bitmap -> queue (order of appearance is irrelevant to the BFS)
+__global__ void __launch_bounds__(kBlock) k_bitmap_to_queue(const uint32_t *__restrict__ bm, long long nwords,
+                                                            vid_t *queue, unsigned long long *count) {
+    const long long stride = gstride();
+    const long long rounds = (nwords + stride - 1) / stride;
+    for (long long r = 0; r < rounds; r++) {
+        const long long w = gtid() + r * stride;
+        uint32_t bits = w < nwords ? bm[w] : 0u;
+        const int c = __popc(bits);
+        // warp-aggregated reservation of c slots per lane
+        unsigned long long incl = (unsigned long long)c;
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned long long wtot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 31 && wtot) base = atomicAdd(count, wtot);
+        base = __shfl_sync(0xffffffffu, base, 31) + incl - (unsigned long long)c;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            queue[base++] = (vid_t)(w * 32 + b);
+        }
+    }
+}
+
+// smallest set bit of the visited bitmap
+__global__ void __launch_bounds__(kBlock) k_first_visited(const uint32_t *__restrict__ vis, long long nwords,
+                                                          DevState *st) {
+    for (long long w = gtid(); w < nwords; w += gstride()) {
+        const uint32_t b = vis[w];
+        if (b) {
+            atomicMin(&st->cmin, (uint32_t)(w * 32 + __ffs(b) - 1));
+            return;  // later words of this thread hold larger ids
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_popcount(const uint32_t *__restrict__ bm, long long nwords,
+                                                     unsigned long long *out) {
+    unsigned long long c = 0;
+    for (long long w = gtid(); w < nwords; w += gstride()) c += __popc(bm[w]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+void launch_bfs_init(const uint32_t *row_ptr, vid_t n, uint32_t *vis, vid_t *queue, DevState *st, cudaStream_t s) {
+    k_bfs_init<<<1, 1, 0, s>>>(row_ptr, n, vis, queue, st);
+}
+void launch_front_degrees(const vid_t *queue, long long f, const uint32_t *row_ptr, uint32_t *dq, int grid,
+                          cudaStream_t s) {
+    if (f > 0) k_front_degrees<<<grid, kBlock, 0, s>>>(queue, f, row_ptr, dq);
+}
+void launch_bfs_topdown(const vid_t *queue, long long f, const uint32_t *off, long long total, const uint32_t *row_ptr,
+                        const vid_t *col, uint32_t *vis, vid_t *next, DevState *st, int level, int grid,
+                        cudaStream_t s) {
+    if (f > 0 && total > 0)
+        k_bfs_topdown<<<grid, kBlock, 0, s>>>(queue, f, off, total, row_ptr, col, vis, next, st, level);
+}
+void launch_bfs_bottomup(vid_t n, const uint32_t *row_ptr, const vid_t *col, const uint32_t *fb, uint32_t *vis,
+                         uint32_t *nb, DevState *st, int level, int grid, cudaStream_t s) {
+    k_bfs_bottomup<<<grid, kBlock, 0, s>>>(n, row_ptr, col, fb, vis, nb, st, level);
+}
+void launch_queue_to_bitmap(const vid_t *queue, long long f, uint32_t *bm, int grid, cudaStream_t s) {
+    if (f > 0) k_queue_to_bitmap<<<grid, kBlock, 0, s>>>(queue, f, bm);
+}
+void launch_bitmap_to_queue(const uint32_t *bm, long long nwords, vid_t *queue, unsigned long long *count, int grid,
+                            cudaStream_t s) {
+    k_bitmap_to_queue<<<grid, kBlock, 0, s>>>(bm, nwords, queue, count);
+}
+void launch_first_visited(const uint32_t *vis, long long nwords, DevState *st, int grid, cudaStream_t s) {
+    k_first_visited<<<grid, kBlock, 0, s>>>(vis, nwords, st);
+}
+void launch_popcount(const uint32_t *bm, long long nwords, unsigned long long *out, int grid, cudaStream_t s) {
+    k_popcount<<<grid, kBlock, 0, s>>>(bm, nwords, out);
+}
+
+}  // namespace ccg

@@ -1,0 +1,506 @@
+// Degree distribution and route prediction (Section 3.2, Algorithm 2 lines 1-2).
+//
+//  k_degree        one streaming pass over the pairs: deg[v] = number of pair
+//                  endpoints equal to v (both directions of every pair, so a
+//                  self-loop adds 2); ids outside [0, n) raise kErrInvalidEdge.
+//  k_hist          histogram of deg with shared-memory privatised bins for
+//                  small degrees, dense global bins below kHistDense and an
+//                  overflow list above; argmax degree (ties to the smallest id).
+//  k_distinct_*    the distinct degrees >= 1 in increasing order with their
+//                  counts, exclusive count prefix and natural logs.
+//  k_ks_candidates one block per candidate xmin: discrete power-law exponent
+//                  (Clauset et al. eq. 3.7), model CDF from the Hurwitz zeta,
+//                  and the exact sup distance to the empirical CDF.
+//  k_ks_select     min D over the candidates, route = D < tau.
+#include "cc_common.cuh"
+#include "cc_kernels.h"
+
+#include <math.h>
+
+namespace ccg {
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_degree(const T *__restrict__ edges, long long m, vid_t n,
+                                                   uint32_t *__restrict__ deg, DevState *st) {
+    constexpr int P = PairVec<T>::kPairs;
+    constexpr int U = 4;  // vectors in flight per thread
+    const long long nvec = m / P;
+    const int4 *ev = reinterpret_cast<const int4 *>(edges);
+    bool bad = false;
+    const long long stride = gstride();
+    for (long long base = gtid(); base < nvec; base += stride * U) {
+        int4 q[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const long long i = base + (long long)k * stride;
+            if (i < nvec) q[k] = ld_stream(ev + i);
+        }
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const long long i = base + (long long)k * stride;
+            if (i >= nvec) break;
+#pragma unroll
+            for (int j = 0; j < P; j++) {
+                long long u, v;
+                vec_pair<T>(q[k], j, u, v);
+                if ((unsigned long long)u >= n || (unsigned long long)v >= n) {
+                    bad = true;
+                    continue;
+                }
+                atomicAdd(&deg[u], 1u);
+                atomicAdd(&deg[v], 1u);
+            }
+        }
+    }
+    if (P == 2 && (m & 1) && gtid() == 0) {
+        long long u, v;
+        scalar_pair<T>(edges, m - 1, u, v);
+        if ((unsigned long long)u >= n || (unsigned long long)v >= n) bad = true;
+        else {
+            atomicAdd(&deg[u], 1u);
+            atomicAdd(&deg[v], 1u);
+        }
+    }
+    if (bad) set_err(st, kErrInvalidEdge);
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void hist_one(uint32_t d, vid_t v, uint32_t *sh, uint32_t *hist, uint32_t *ovf,
+                                         unsigned long long ovf_cap, DevState *st, unsigned long long &best) {
+    if (d < kHistSmem) atomicAdd(&sh[d], 1u);
+    else if (d < kHistDense) atomicAdd(&hist[d], 1u);
+    else {
+        unsigned long long k = atomicAdd(&st->n_ovf, 1ull);
+        if (k < ovf_cap) ovf[k] = d;
+        else set_err(st, kErrOverflow);
+    }
+    const unsigned long long key = ((unsigned long long)d << 32) | (unsigned long long)(0xffffffffu - v);
+    best = key > best ? key : best;
+}
+
+__global__ void __launch_bounds__(kBlock) k_hist(const uint32_t *__restrict__ deg, vid_t n, uint32_t *hist,
+                                                 uint32_t *ovf, unsigned long long ovf_cap, DevState *st) {
+    __shared__ uint32_t sh[kHistSmem];
+    for (int i = threadIdx.x; i < (int)kHistSmem; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    unsigned long long best = 0;
+    const long long nv4 = (long long)n / 4;
+    const uint4 *d4 = reinterpret_cast<const uint4 *>(deg);
+    for (long long i = gtid(); i < nv4; i += gstride()) {
+        const uint4 q = d4[i];
+        const vid_t v = (vid_t)(i * 4);
+        hist_one(q.x, v, sh, hist, ovf, ovf_cap, st, best);
+        hist_one(q.y, v + 1, sh, hist, ovf, ovf_cap, st, best);
+        hist_one(q.z, v + 2, sh, hist, ovf, ovf_cap, st, best);
+        hist_one(q.w, v + 3, sh, hist, ovf, ovf_cap, st, best);
+    }
+    for (long long v = nv4 * 4 + gtid(); v < (long long)n; v += gstride())
+        hist_one(deg[v], (vid_t)v, sh, hist, ovf, ovf_cap, st, best);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long b = __shfl_xor_sync(0xffffffffu, best, o);
+        best = b > best ? b : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(&st->maxkey, best);
+    __syncthreads();
+    for (int i = threadIdx.x; i < (int)kHistSmem; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Distinct degrees. The dense bins [1, min(maxdeg+1, kHistDense)) are split
+// into chunks of kChunk; k_distinct_count counts nonzero bins and their mass
+// per chunk, k_distinct_scan turns those into chunk offsets (one block),
+// k_distinct_write writes the compacted arrays, k_distinct_overflow appends
+// the (rare) degrees >= kHistDense in sorted order.
+constexpr int kChunk = 4096;
+constexpr int kNumChunks = (int)(kHistDense / kChunk);
+
+__device__ __forceinline__ long long dense_limit(const DevState *st) {
+    const unsigned long long maxdeg = st->maxkey >> 32;
+    return maxdeg + 1 < kHistDense ? (long long)maxdeg + 1 : (long long)kHistDense;
+}
+
+template <typename V>
+__device__ V block_exclusive_scan(V x, V *smem /* >= 32 */, V &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    V incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        V y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) smem[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        V w = lane < nw ? smem[lane] : (V)0;
+        V wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            V y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) smem[lane] = wi - w;
+        if (lane == nw - 1) smem[32] = wi;
+    }
+    __syncthreads();
+    V r = smem[warp] + incl - x;
+    total = smem[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_distinct_count(const uint32_t *hist, const DevState *st,
+                                                         unsigned long long *chunk_nz, unsigned long long *chunk_mass) {
+    __shared__ unsigned long long sm[33];
+    const long long lim = dense_limit(st);
+    const long long c0 = (long long)blockIdx.x * kChunk;
+    unsigned long long nz = 0, mass = 0;
+    for (long long d = c0 + threadIdx.x; d < c0 + kChunk && d < lim; d += blockDim.x) {
+        if (d == 0) continue;
+        const uint32_t h = hist[d];
+        nz += h ? 1 : 0;
+        mass += h;
+    }
+    unsigned long long tnz, tmass;
+    block_exclusive_scan<unsigned long long>(nz, sm, tnz);
+    block_exclusive_scan<unsigned long long>(mass, sm, tmass);
+    if (threadIdx.x == 0) {
+        chunk_nz[blockIdx.x] = tnz;
+        chunk_mass[blockIdx.x] = tmass;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_distinct_scan(unsigned long long *chunk_nz, unsigned long long *chunk_mass,
+                                                        DevState *st) {
+    // kNumChunks = 256 <= blockDim: one element per thread.
+    __shared__ unsigned long long sm[33];
+    const int t = threadIdx.x;
+    unsigned long long nz = t < kNumChunks ? chunk_nz[t] : 0, mass = t < kNumChunks ? chunk_mass[t] : 0;
+    unsigned long long tnz, tmass;
+    unsigned long long onz = block_exclusive_scan<unsigned long long>(nz, sm, tnz);
+    unsigned long long omass = block_exclusive_scan<unsigned long long>(mass, sm, tmass);
+    if (t < kNumChunks) {
+        chunk_nz[t] = onz;
+        chunk_mass[t] = omass;
+    }
+    if (t == 0) {
+        chunk_nz[kNumChunks] = tnz;
+        chunk_mass[kNumChunks] = tmass;
+        st->nd = tnz;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_distinct_write(const uint32_t *hist, const DevState *st,
+                                                         const unsigned long long *chunk_nz,
+                                                         const unsigned long long *chunk_mass, uint32_t *xs,
+                                                         unsigned long long *cnt, unsigned long long *cum, double *lnx) {
+    __shared__ unsigned long long sm[33];
+    const long long lim = dense_limit(st);
+    const long long c0 = (long long)blockIdx.x * kChunk;
+    if (c0 >= lim) return;  // uniform per block
+    unsigned long long off = chunk_nz[blockIdx.x], moff = chunk_mass[blockIdx.x];
+    // 4 rounds of 1024 bins, in increasing degree order
+    for (long long r = 0; r < kChunk; r += blockDim.x) {
+        const long long d = c0 + r + threadIdx.x;
+        const uint32_t h = (d > 0 && d < lim) ? hist[d] : 0u;
+        unsigned long long tnz, tmass;
+        unsigned long long p = block_exclusive_scan<unsigned long long>(h ? 1ull : 0ull, sm, tnz);
+        unsigned long long pm = block_exclusive_scan<unsigned long long>((unsigned long long)h, sm, tmass);
+        if (h) {
+            const unsigned long long k = off + p;
+            xs[k] = (uint32_t)d;
+            cnt[k] = h;
+            cum[k] = moff + pm;
+            lnx[k] = log((double)d);
+        }
+        off += tnz;
+        moff += tmass;
+    }
+}
+
+// Appends the distinct overflow degrees (>= kHistDense) in increasing order:
+// bitonic sort of the (at most kOvfMax) recorded degrees in shared memory,
+// then one pass that keeps the first of each run of equal values.
+constexpr int kOvfMax = 4096;
+
+__global__ void __launch_bounds__(1024) k_distinct_overflow(const uint32_t *ovf, unsigned long long ovf_cap,
+                                                            const unsigned long long *chunk_mass, DevState *st,
+                                                            uint32_t *xs, unsigned long long *cnt,
+                                                            unsigned long long *cum, double *lnx) {
+    __shared__ uint32_t sv[kOvfMax];
+    __shared__ unsigned long long sm[33];
+    const unsigned long long rec = st->n_ovf < ovf_cap ? st->n_ovf : ovf_cap;
+    const int k = (int)(rec < (unsigned long long)kOvfMax ? rec : (unsigned long long)kOvfMax);
+    const unsigned long long base = st->nd, mass0 = chunk_mass[kNumChunks];
+    int P = 1;
+    while (P < k) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sv[i] = i < k ? ovf[i] : 0xffffffffu;
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const uint32_t a = sv[i], b = sv[j];
+                    if ((a > b) == up) {
+                        sv[i] = b;
+                        sv[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // runs of equal values: a run starts at i when sv[i] != sv[i-1]
+    unsigned long long out = 0;
+    for (int r = 0; r < P; r += blockDim.x) {
+        const int i = r + threadIdx.x;
+        const bool head = i < k && (i == 0 || sv[i] != sv[i - 1]);
+        unsigned long long tot;
+        const unsigned long long rank = block_exclusive_scan<unsigned long long>(head ? 1ull : 0ull, sm, tot);
+        if (head) {
+            int e = i + 1;
+            while (e < k && sv[e] == sv[i]) e++;
+            const unsigned long long o = base + out + rank;
+            xs[o] = sv[i];
+            cnt[o] = (unsigned long long)(e - i);
+            cum[o] = mass0 + (unsigned long long)i;
+            lnx[o] = log((double)sv[i]);
+        }
+        out += tot;
+    }
+    if (threadIdx.x == 0) {
+        st->nd = base + out;
+        cum[base + out] = mass0 + (unsigned long long)k;  // total mass of degrees >= 1
+        if (rec > (unsigned long long)kOvfMax) atomicOr(&st->err, kErrOverflow);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Scaled Hurwitz zeta: c^s * zeta(s, q) = sum_{k>=0} ((q+k)/c)^-s, s > 1.
+// Explicit terms until a = q + k reaches max(16, 2s); the remainder by the
+// Euler-Maclaurin formula with six Bernoulli terms. With a >= 2s the ratio
+// of consecutive correction terms is below (s / (2 pi a))^2 <= 1/(16 pi^2),
+// so six terms leave a relative error near 1e-15.
+__device__ double zeta_scaled(double s, double q, double lnc) {
+    double acc = 0.0, a = q;
+    const double thr = fmax(16.0, 2.0 * s);
+    while (a < thr) {
+        const double term = exp(-s * (log(a) - lnc));
+        acc += term;
+        a += 1.0;
+        // the rest is below term * (1 + a/(s-1)) (integral bound); stop once it cannot matter
+        if (term * (1.0 + a / (s - 1.0)) < 1e-18 * acc) return acc;
+    }
+    const double A = exp(-s * (log(a) - lnc));
+    acc += A * a / (s - 1.0) + 0.5 * A;
+    const double ia2 = 1.0 / (a * a);
+    // term_k = B_2k/(2k)! * s(s+1)...(s+2k-2) * A * a^-(2k-1)
+    const double coef[6] = {1.0 / 12.0, -1.0 / 720.0, 1.0 / 30240.0, -1.0 / 1209600.0, 1.0 / 47900160.0,
+                            -691.0 / 1307674368000.0};
+    double t = A * s / a;
+    acc += coef[0] * t;
+#pragma unroll
+    for (int k = 1; k < 6; k++) {
+        t *= (s + 2 * k - 1) * (s + 2 * k) * ia2;
+        acc += coef[k] * t;
+    }
+    return acc;
+}
+
+template <typename V>
+__device__ V block_reduce_sum(V x, V *smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) smem[warp] = x;
+    __syncthreads();
+    V r = 0;
+    for (int w = 0; w < nw; w++) r += smem[w];
+    __syncthreads();
+    return r;
+}
+
+__device__ double block_reduce_max(double x, double *smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (lane == 0) smem[warp] = x;
+    __syncthreads();
+    double r = 0.0;
+    for (int w = 0; w < nw; w++) r = fmax(r, smem[w]);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_ks_candidates(const uint32_t *xs, const unsigned long long *cnt,
+                                                       const unsigned long long *cum, const double *lnx,
+                                                       const DevState *st, long long min_tail, long long min_distinct,
+                                                       double min_span, double *Dc, double *Ac) {
+    __shared__ double sd[32];
+    const long long nd = (long long)st->nd;
+    if (nd == 0) return;
+    const double xmax = (double)xs[nd - 1];
+    const unsigned long long total = cum[nd];
+    for (long long i = blockIdx.x; i < nd; i += gridDim.x) {
+        const double xmin = (double)xs[i];
+        const unsigned long long Nt = total - cum[i];
+        if ((long long)Nt < min_tail || nd - i < min_distinct || xmax < min_span * xmin) {
+            if (threadIdx.x == 0) Dc[i] = 2.0;  // not a candidate
+            continue;
+        }
+        const double N = (double)Nt;
+        const double lshift = log(xmin - 0.5);
+        double part = 0.0;
+        for (long long j = i + threadIdx.x; j < nd; j += blockDim.x) part += (double)cnt[j] * (lnx[j] - lshift);
+        const double S = block_reduce_sum<double>(part, sd);
+        const double alpha = 1.0 + N / S;
+        const double lnc = lnx[i];
+        const double Z = zeta_scaled(alpha, xmin, lnc);
+        double dmax = 0.0;
+        for (long long j = i + threadIdx.x; j < nd; j += blockDim.x) {
+            const double x = (double)xs[j];
+            const double zb = zeta_scaled(alpha, x, lnc);        // mass at >= x
+            const double za = zeta_scaled(alpha, x + 1.0, lnc);  // mass at >= x+1
+            const double before = (double)(cum[j] - cum[i]) / N;
+            const double at = (double)(cum[j + 1] - cum[i]) / N;
+            double d = fabs(at - (1.0 - za / Z));
+            if (j > i) d = fmax(d, fabs(before - (1.0 - zb / Z)));
+            dmax = fmax(dmax, d);
+        }
+        const double D = block_reduce_max(dmax, sd);
+        if (threadIdx.x == 0) {
+            Dc[i] = D;
+            Ac[i] = alpha;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_ks_select(const uint32_t *xs, const unsigned long long *cum,
+                                                    const double *Dc, const double *Ac, DevState *st, double tau) {
+    __shared__ double sD[1024];
+    __shared__ long long sI[1024];
+    __shared__ unsigned long long sC[1024];
+    const long long nd = (long long)st->nd;
+    double best = 2.0;
+    long long bi = -1;
+    unsigned long long nc = 0;
+    for (long long i = threadIdx.x; i < nd; i += blockDim.x) {
+        const double d = Dc[i];
+        if (d <= 1.0) {
+            nc++;
+            if (d < best) {  // i increases per thread, so ties keep the smaller i
+                best = d;
+                bi = i;
+            }
+        }
+    }
+    sD[threadIdx.x] = best;
+    sI[threadIdx.x] = bi;
+    sC[threadIdx.x] = nc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const double d2 = sD[threadIdx.x + o];
+            const long long i2 = sI[threadIdx.x + o];
+            if (i2 >= 0 && (d2 < sD[threadIdx.x] || (d2 == sD[threadIdx.x] && (sI[threadIdx.x] < 0 || i2 < sI[threadIdx.x])))) {
+                sD[threadIdx.x] = d2;
+                sI[threadIdx.x] = i2;
+            }
+            sC[threadIdx.x] += sC[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const long long i = sI[0];
+        if (i < 0) {
+            st->ks_out[0] = 1.0;
+            st->ks_out[1] = 0.0;
+            st->ks_out[2] = 0.0;
+            st->ks_out[3] = 0.0;
+        } else {
+            st->ks_out[0] = sD[0];
+            st->ks_out[1] = Ac[i];
+            st->ks_out[2] = (double)xs[i];
+            st->ks_out[3] = (double)(cum[nd] - cum[i]);
+        }
+        st->ks_out[4] = (double)sC[0];
+        st->ncand = sC[0];
+        st->route = st->ks_out[0] < tau ? 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+
+template <typename T>
+void launch_degree(const void *edges, long long m, vid_t n, uint32_t *deg, DevState *st, int grid, cudaStream_t s) {
+    if (m <= 0) return;
+    k_degree<T><<<grid, kBlock, 0, s>>>((const T *)edges, m, n, deg, st);
+}
+template void launch_degree<int32_t>(const void *, long long, vid_t, uint32_t *, DevState *, int, cudaStream_t);
+template void launch_degree<int64_t>(const void *, long long, vid_t, uint32_t *, DevState *, int, cudaStream_t);
+
+void launch_hist(const uint32_t *deg, vid_t n, uint32_t *hist, uint32_t *ovf, unsigned long long ovf_cap,
+                 DevState *st, int grid, cudaStream_t s) {
+    if (n == 0) return;
+    k_hist<<<grid, kBlock, 0, s>>>(deg, n, hist, ovf, ovf_cap, st);
+}
+
+void launch_ks(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf_cap, KsScratch ks, DevState *st,
+               long long min_tail, long long min_distinct, double min_span, double tau, int grid, cudaStream_t s) {
+    k_distinct_count<<<kNumChunks, 1024, 0, s>>>(hist, st, ks.chunk_nz, ks.chunk_mass);
+    k_distinct_scan<<<1, 1024, 0, s>>>(ks.chunk_nz, ks.chunk_mass, st);
+    k_distinct_write<<<kNumChunks, 1024, 0, s>>>(hist, st, ks.chunk_nz, ks.chunk_mass, ks.xs, ks.cnt, ks.cum, ks.lnx);
+    k_distinct_overflow<<<1, 1024, 0, s>>>(ovf, ovf_cap, ks.chunk_mass, st, ks.xs, ks.cnt, ks.cum, ks.lnx);
+    k_ks_candidates<<<grid, 256, 0, s>>>(ks.xs, ks.cnt, ks.cum, ks.lnx, st, min_tail, min_distinct, min_span, ks.Dc,
+                                         ks.Ac);
+    k_ks_select<<<1, 1024, 0, s>>>(ks.xs, ks.cum, ks.Dc, ks.Ac, st, tau);
+}
+
+int ks_num_chunks() { return kNumChunks; }
+
+// hist (uint32 dense bins + overflow list) -> uint64 histogram of length len
+__global__ void __launch_bounds__(kBlock) k_hist_widen(const uint32_t *hist, const uint32_t *ovf,
+                                                       unsigned long long ovf_cap, const DevState *st, uint64_t *out,
+                                                       long long len) {
+    for (long long d = gtid(); d < len; d += gstride()) out[d] = d < (long long)kHistDense ? hist[d] : 0ull;
+}
+__global__ void __launch_bounds__(kBlock) k_hist_widen_ovf(const uint32_t *ovf, unsigned long long ovf_cap,
+                                                           const DevState *st, uint64_t *out, long long len) {
+    const unsigned long long k = st->n_ovf < ovf_cap ? st->n_ovf : ovf_cap;
+    for (long long i = gtid(); i < (long long)k; i += gstride())
+        if ((long long)ovf[i] < len) atomicAdd((unsigned long long *)&out[ovf[i]], 1ull);
+}
+void launch_hist_widen(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf_cap, const DevState *st,
+                       uint64_t *out, long long len, int grid, cudaStream_t s) {
+    k_hist_widen<<<grid, kBlock, 0, s>>>(hist, ovf, ovf_cap, st, out, len);
+    k_hist_widen_ovf<<<grid, kBlock, 0, s>>>(ovf, ovf_cap, st, out, len);
+}
+
+// uint64 histogram (len <= kHistDense, counts < 2^32) -> dense uint32 bins and
+// the max degree (maxkey) the distinct-degree pass reads.
+__global__ void __launch_bounds__(kBlock) k_hist_narrow(const uint64_t *in, long long len, uint32_t *hist,
+                                                        DevState *st) {
+    unsigned long long best = 0;
+    for (long long d = gtid(); d < len; d += gstride()) {
+        const uint64_t h = in[d];
+        if (h > 0xffffffffull) set_err(st, kErrOverflow);
+        hist[d] = (uint32_t)h;
+        if (h) best = ((unsigned long long)d << 32) | 0xffffffffull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, best, o);
+        best = b > best ? b : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(&st->maxkey, best);
+}
+void launch_hist_narrow(const uint64_t *in, long long len, uint32_t *hist, DevState *st, int grid, cudaStream_t s) {
+    k_hist_narrow<<<grid, kBlock, 0, s>>>(in, len, hist, st);
+}
+
+}  // namespace ccg

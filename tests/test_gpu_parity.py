@@ -1,0 +1,244 @@
+"""GPU parity: CUDA labels are bit-identical to the oracle's on every route.
+
+Labels are the minimum vertex id of each component (Section 3.1.1); the
+route (K-S heuristic, forced BFS, forced SV; Algorithm 2) never changes
+them. Sizes here span several tiles of every kernel plus ragged tails.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from tests.gpu_util import assert_labels_match, run_engine, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def test_planted_config_small():
+    g = gg.planted(seed=1)  # n = 65,536, 512 components, ~163K pairs
+    st = assert_labels_match(g.edges, g.n)
+    assert st["auto"]["route"] == 0  # no power-law tail: SV only
+    assert st["bfs"]["route"] == 1 and st["bfs"]["bfs_visited"] > 0
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_planted_seeds_int64(seed):
+    g = gg.planted(seed=seed, n=50000, ncomp=700, id_bytes=8)
+    assert_labels_match(g.edges, g.n)
+
+
+@pytest.mark.parametrize("scale,ef", [(12, 4), (16, 16), (18, 8)])
+def test_rmat(scale, ef):
+    g = gg.rmat(seed=scale, scale=scale, edge_factor=ef)
+    assert_labels_match(g.edges, g.n)
+
+
+def test_chung_lu_takes_bfs_route():
+    g = gg.chung_lu(seed=5, n=1 << 17, avg_degree=12, alpha=2.3)
+    st = assert_labels_match(g.edges, g.n, routes=("auto",))["auto"]
+    assert st["route"] == 1, st
+    assert st["ks_d"] < 0.05
+    assert st["bfs_visited"] > g.n // 4
+    assert st["seed_vertex"] == int(np.argmax(np.bincount(g.edges.ravel(), minlength=g.n)))
+
+
+def test_grid_chains_int64():
+    g = gg.grid_chains(seed=3, W=300, p=0.55, nchains=20000, id_bytes=8)
+    st = assert_labels_match(g.edges, g.n)
+    assert st["auto"]["route"] == 0
+
+
+def test_grid_chains_int32():
+    g = gg.grid_chains(seed=4, W=257, p=0.5, nchains=5000, id_bytes=4)
+    assert_labels_match(g.edges, g.n)
+
+
+@pytest.mark.parametrize("cutoff", [1, 2, 3, 5])
+def test_bfs_cutoff_keeps_labels_exact(cutoff):
+    g = gg.chung_lu(seed=7, n=1 << 15, avg_degree=6, alpha=2.5)
+    st = assert_labels_match(g.edges, g.n, routes=("bfs",), bfs_cutoff_levels=cutoff)["bfs"]
+    assert st["bfs_levels"] <= cutoff
+
+
+def _arr(pairs, dt=np.int32):
+    return np.array(pairs, dtype=dt).reshape(-1, 2)
+
+
+def test_empty_and_tiny():
+    for n in (1, 2, 3, 7, 100, 1001):
+        assert_labels_match(np.zeros((0, 2), np.int32), n)
+    assert_labels_match(_arr([(0, 1)]), 2)
+    assert_labels_match(_arr([(1, 0)]), 5)
+    assert_labels_match(_arr([(2, 2)]), 3)
+    assert_labels_match(_arr([(4, 3), (1, 2), (3, 0)]), 6)  # odd m: ragged vector tail
+
+
+def test_self_loops_and_duplicates():
+    n = 5000
+    loops = np.repeat(np.arange(n, dtype=np.int32)[:, None], 2, axis=1)
+    assert_labels_match(loops, n)
+    rng = np.random.default_rng(0)
+    base = rng.integers(0, n, size=(3000, 2)).astype(np.int32)
+    dup = np.concatenate([base, base, base[::-1], loops[:777]])
+    assert_labels_match(dup, n)
+
+
+def test_long_paths_sorted_and_reversed_ids():
+    """Diameter n-1: the worst case for BFS levels and for hook chains."""
+    n = 200_001
+    fwd = np.stack([np.arange(n - 1), np.arange(1, n)], axis=1).astype(np.int32)
+    want = np.zeros(n, dtype=np.int64)
+    assert_labels_match(fwd, n, want=want, routes=("sv", "auto"))
+    assert_labels_match(fwd[::-1, ::-1].copy(), n, want=want, routes=("sv",))
+    perm = np.random.default_rng(1).permutation(n).astype(np.int32)
+    assert_labels_match(perm[fwd], n, want=want, routes=("sv",))
+
+
+def test_long_path_bfs_route():
+    n = 3000
+    perm = np.random.default_rng(2).permutation(n).astype(np.int32)
+    e = perm[np.stack([np.arange(n - 1), np.arange(1, n)], axis=1)]
+    assert_labels_match(e, n, want=np.zeros(n, np.int64), routes=("bfs",))
+
+
+def test_star_and_isolated():
+    n = 100_000
+    hub = n - 1
+    star = np.stack([np.full(n // 2, hub), np.arange(0, n // 2) * 2 % (n - 1)], axis=1).astype(np.int32)
+    assert_labels_match(star, n)
+
+
+def test_large_ids_int64():
+    """ids near and above 2^31 with int64 edges (n = 2^31 + 4096)."""
+    torch = torch_cuda()
+    n = (1 << 31) + 4096
+    rng = np.random.default_rng(3)
+    ids = np.unique(np.concatenate([rng.integers(n - 100000, n, 3000), [n - 1, (1 << 31) - 1, 1 << 31]]))
+    e_local = rng.integers(0, ids.size, size=(2500, 2))
+    e = ids[e_local].astype(np.int64)
+    got, _ = run_engine(e, n, route="sv")
+    want_local = oracle.cc_labels(e_local, ids.size)
+    want = np.arange(n, dtype=np.int64)
+    want[ids] = ids[want_local]
+    assert np.array_equal(got[ids], want[ids])
+    sample = rng.integers(0, n, 100000)
+    assert np.array_equal(got[sample], want[sample])
+    del torch
+
+
+@pytest.mark.parametrize("route", ["auto", "sv", "bfs"])
+def test_invalid_ids_rejected(route):
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    for bad, dt in ((_arr([(0, 1), (2, 10)]), np.int32), (_arr([(0, 1), (-1, 2)]), np.int32),
+                    (_arr([(0, 1), (3, 1 << 40)], np.int64), np.int64)):
+        eng = cc.Engine(id_bytes=np.dtype(dt).itemsize, route=route)
+        with pytest.raises(cc.CCError) as ei:
+            eng.labels(torch.from_numpy(bad).cuda(), 10)
+        assert ei.value.status == 2
+        # the context stays usable
+        ok = eng.labels(torch.from_numpy(_arr([(0, 1)], dt)).cuda(), 3)
+        assert ok.cpu().tolist() == [0, 0, 2]
+        eng.close()
+
+
+def test_repeated_runs_are_identical():
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    g = gg.rmat(seed=9, scale=15, edge_factor=8)
+    want = oracle.cc_labels(g.edges, g.n)
+    e = torch.from_numpy(g.edges).cuda()
+    for route in ("sv", "bfs"):
+        eng = cc.Engine(route=route)
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for _ in range(25):
+            eng.labels(e, g.n, out=out)
+            assert np.array_equal(out.cpu().numpy().astype(np.int64), want)
+        eng.close()
+
+
+def test_degree_distribution_parity():
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    for g in (gg.rmat(seed=2, scale=16, edge_factor=16), gg.grid_chains(seed=2, W=100, nchains=3000, id_bytes=8),
+              gg.planted(seed=2)):
+        deg_o = oracle.degrees(g.edges, g.n)
+        hist_o = oracle.histogram(deg_o)
+        eng = cc.Engine(id_bytes=g.id_bytes)
+        deg, hist = eng.degree_distribution(torch.from_numpy(g.edges).cuda(), g.n, hist_len=hist_o.size + 3)
+        assert np.array_equal(deg.cpu().numpy().astype(np.int64), deg_o)
+        h = hist.cpu().numpy()
+        assert np.array_equal(h[:hist_o.size], hist_o) and (h[hist_o.size:] == 0).all()
+        eng.close()
+
+
+def test_degree_overflow_bins():
+    """A vertex of degree >= 2^20 goes through the overflow list."""
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    n = 3 << 20
+    hubs = np.array([5, 77, 1 << 21], dtype=np.int64)
+    parts = [np.stack([np.full(k, h), np.arange(k) + (1 << 20) * i], axis=1) for i, (h, k) in
+             enumerate(zip(hubs, [(1 << 20) + 3, (1 << 20) + 3, 1 << 20]))]
+    e = np.concatenate(parts).astype(np.int32)
+    e[:, 1] %= n
+    deg_o = oracle.degrees(e, n)
+    eng = cc.Engine()
+    deg, hist = eng.degree_distribution(torch.from_numpy(e).cuda(), n, hist_len=int(deg_o.max()) + 1)
+    assert np.array_equal(deg.cpu().numpy().astype(np.int64), deg_o)
+    assert np.array_equal(hist.cpu().numpy(), oracle.histogram(deg_o))
+    got, st = run_engine(e, n, route="auto")
+    assert np.array_equal(got, oracle.cc_labels(e, n))
+    assert st["max_degree"] == int(deg_o.max())
+    eng.close()
+
+
+def _ks_dev(hist):
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    eng = cc.Engine()
+    r = eng.ks_statistic(torch.from_numpy(np.ascontiguousarray(hist, dtype=np.int64)).cuda())
+    eng.close()
+    return r
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: gg.rmat(seed=1, scale=18, edge_factor=16),
+    lambda: gg.chung_lu(seed=3, n=1 << 18, avg_degree=16, alpha=2.5),
+    lambda: gg.chung_lu(seed=4, n=1 << 16, avg_degree=4, alpha=3.2),
+    lambda: gg.planted(seed=1),
+    lambda: gg.grid_chains(seed=1, W=256, nchains=50000),
+])
+def test_ks_statistic_parity(maker):
+    """Device D / alpha agree with the fp64 oracle to 1e-9; xmin and counts exactly."""
+    g = maker()
+    hist = oracle.histogram(oracle.degrees(g.edges, g.n))
+    want = oracle.ks_fit(hist)
+    got = _ks_dev(hist)
+    assert got["ncand"] == want["ncand"]
+    assert abs(got["D"] - want["D"]) < 1e-9, (got, want)
+    assert got["xmin"] == want["xmin"] and got["ntail"] == want["ntail"]
+    assert abs(got["alpha"] - want["alpha"]) < 1e-9 * max(1.0, want["alpha"])
+    _, st = run_engine(g.edges, g.n, route="auto")
+    assert abs(st["ks_d"] - want["D"]) < 1e-9
+    assert st["route"] == int(oracle.route_is_bfs(want["D"]))
+
+
+def test_ks_statistic_synthetic_histograms():
+    rng = np.random.default_rng(11)
+    for trial in range(20):
+        L = int(rng.integers(10, 5000))
+        hist = np.zeros(L, dtype=np.int64)
+        k = int(rng.integers(3, min(L, 400)))
+        xs = rng.choice(np.arange(1, L), size=k, replace=False)
+        hist[xs] = rng.integers(1, 10 ** int(rng.integers(1, 7)), size=k)
+        hist[0] = int(rng.integers(0, 1000))
+        want = oracle.ks_fit(hist)
+        got = _ks_dev(hist)
+        assert got["ncand"] == want["ncand"] and got["xmin"] == want["xmin"], (got, want)
+        assert abs(got["D"] - want["D"]) < 1e-9, (got, want)
