@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the hybrid connected-components route on one GB300 per rank.
+
+Workload (default): R-MAT scale 24, edge factor 16 (n = 16,777,216 vertices,
+m = 268,435,456 undirected int32 pairs, a=0.57 b=c=0.19, ids permuted,
+duplicates and self-loops kept), generated from a fixed seed. One step is
+one cc_labels call (degree pass -> K-S prediction -> BFS if chosen -> SV
+iterations -> labels) with the edges already resident in HBM; the metric is
+m / device time (CC edges/s). The 2.15 GB edge list is larger than L2, so no
+flush is done between steps.
+
+Extra keys: roofline of the dominant kernel (algorithmic bytes per launch /
+its average event-timed duration, against the measured HBM copy bandwidth),
+e2e (the same metric with pinned host buffers and both copies inside the
+timed region), cpu_baseline (the CPU oracle on a bounded prefix sample),
+clocks sampled during the timed region, and route_compare (the forced BFS
+and forced SV routes on the same graph).
+
+`--impl reference` times the CPU oracle (sequential union-find) instead.
+Under torchrun with N > 1 ranks every rank runs an independent replica
+(the single-graph path does not shard); value = all ranks' pairs / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CC edges/s (m / device time to exact labels)"
+UNIT = "edges/s"
+WORKLOADS = {
+    "rmat24": dict(kind="rmat", scale=24, edge_factor=16, seed=1),
+    "rmat20": dict(kind="rmat", scale=20, edge_factor=16, seed=1),
+    "planted": dict(kind="planted", seed=1),
+    "grid_chains": dict(kind="grid_chains", seed=1, W=8192, nchains=10_000_000),
+}
+KERNEL_FILES = ["cc_common.cuh", "k_degree.cu", "k_sv.cu", "k_bfs.cu", "cc_api.cu"]
+
+
+def make_graph(name: str):
+    import graphgen as gg
+
+    w = dict(WORKLOADS[name])
+    kind = w.pop("kind")
+    if kind == "rmat":
+        return gg.rmat(**w)
+    if kind == "planted":
+        return gg.planted(**w)
+    return gg.grid_chains(**w)
+
+
+def workload_config(name: str, g) -> dict:
+    w = WORKLOADS[name]
+    cfg = {"workload": name, "n": int(g.n), "m": int(g.m), "id_bytes": int(g.id_bytes),
+           "l2": "inputs larger than L2 (no flush)" if g.m * 2 * g.id_bytes > 129e6 else "L2-resident inputs"}
+    if w["kind"] == "rmat":
+        cfg.update({"graph": f"R-MAT scale {w['scale']} edge factor {w['edge_factor']} (a=0.57,b=0.19,c=0.19)",
+                    "seed": w["seed"]})
+    else:
+        cfg.update({"graph": g.name})
+    return cfg
+
+
+def alg_bytes(cls: str, st: dict, w: int) -> float:
+    """Algorithmic bytes one call moves in a kernel class (element-size accesses)."""
+    n, m = st["n"], st["m"]
+    act, hooks = st["m_active"], st["sv_hooks"]
+    if cls == "degree":
+        return 2 * w * m + 4 * n
+    if cls == "hist":
+        return 4 * n
+    if cls == "parent_init":
+        return 4 * n
+    if cls == "finalize":
+        return 4 * n + w * n
+    if cls == "sv_first":
+        return 2 * w * m + 4 * m
+    if cls == "sv_gather_input":
+        # read pairs, gather both parents, atomicMin per surviving pair, write survivors
+        kept = act[2] if len(act) > 2 else 0
+        return 2 * w * m + 8 * m + 4 * kept + 8 * kept
+    if cls == "sv_gather_list":
+        tot = 0
+        for i in range(2, len(act)):
+            mi = act[i]
+            kept = act[i + 1] if i + 1 < len(act) else 0
+            tot += 16 * mi + 12 * kept
+        return tot
+    if cls == "sv_shortcut":
+        return 12 * sum(hooks)
+    if cls == "csr":
+        return 2 * w * m + 16 * m
+    if cls in ("bfs_bottomup", "bfs_topdown"):
+        return 4 * st["bfs_edges_inspected"] / 2 + n / 8 * 3
+    return 0.0
+
+
+def sources_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_FILES:
+        with open(os.path.join(ROOT, "paper_1607_06156_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_cls: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("sources_hash") != sources_hash():
+        return None
+    return d.get("traffic", {}).get(workload, {}).get(kernel_cls)
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling in the background (200 ms period)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+        self.t_start = self.t_end = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def mark(self, which: str):
+        setattr(self, "t_" + which, time.time())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip().lower() == "active"})
+        # under load: samples at or above half the maximum clock seen
+        load = [x for x in sm if sm and x >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(load)) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_oracle_rate(edges: np.ndarray, n: int, budget_pairs: int) -> tuple[float, int, float]:
+    """The oracle's union-find on the first `budget_pairs` pairs (full n); pairs/s, pairs, seconds."""
+    import oracle
+
+    k = min(budget_pairs, edges.shape[0])
+    sample = np.ascontiguousarray(edges[:k])
+    t = time.perf_counter()
+    oracle.labels_uf(sample, n)
+    dt = time.perf_counter() - t
+    return k / dt, k, dt
+
+
+def run_reference(args, world: int, rank: int):
+    if rank != 0:
+        return 0
+    g = make_graph(args.workload)
+    sample = args.ref_pairs
+    cfg = workload_config(args.workload, g)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(g.edges, g.n, sample)
+    times = []
+    for _ in range(args.steps):
+        _, k, dt = cpu_oracle_rate(g.edges, g.n, sample)
+        times.append(dt)
+    tot = sum(times)
+    value = k * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {k} of {g.m} pairs of the same graph, full n, sequential union-find"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def check_labels(torch, edges_d, lab, n):
+    """Cheap device-side invariants of min-id labels (outside the timed region)."""
+    l = lab.long()
+    e = edges_d.long()
+    ok = bool((l[e[:, 0]] == l[e[:, 1]]).all())
+    v = torch.arange(n, device=lab.device)
+    ok = ok and bool((l <= v).all()) and bool((l[l] == l).all())
+    return ok
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
+    ap.add_argument("--route", default="auto", choices=["auto", "sv", "bfs"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the forced-route comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ref-pairs", type=int, default=1 << 24, help="pairs per step of the CPU oracle")
+    ap.add_argument("--cpu-pairs", type=int, default=1 << 25, help="pairs in the cpu_baseline sample")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+
+    import paper_1607_06156_gb300 as cc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    g = make_graph(args.workload)
+    cfg = workload_config(args.workload, g)
+    w = g.id_bytes
+    n, m = g.n, g.m
+    edges_d = torch.from_numpy(g.edges).to(dev)
+    lab = torch.empty(n, dtype=edges_d.dtype, device=dev)
+    eng = cc.Engine(id_bytes=w, route=args.route, device=local, profile=1)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(max(args.warmup, 1)):
+        eng.labels(edges_d, n, out=lab)
+    torch.cuda.synchronize(dev)
+    if not check_labels(torch, edges_d, lab, n):
+        raise SystemExit("label invariants violated after warm-up")
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms, kla, launches = {}, {}, 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        eng.labels(edges_d, n, out=lab)
+        st = eng.stats()
+        launches += st["launches"]
+        for k, v in st["kernel_ms"].items():
+            kms[k] = kms.get(k, 0.0) + v
+            kla[k] = kla.get(k, 0) + st["kernel_launches"][k]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop() if sampler else None
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * m * args.steps / (ms / 1e3)
+    last = st
+
+    # roofline of the dominant kernel class
+    dom = max(kms, key=lambda k: kms[k])
+    per_call_bytes = alg_bytes(dom, last, w)
+    per_launch_ms = kms[dom] / max(kla[dom], 1)
+    launches_per_call = kla[dom] / args.steps
+    achieved = per_call_bytes / launches_per_call / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+    pk = peaks()
+    peak = pk.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    if not peak:
+        peak = 6800.0
+    traffic = ncu_traffic(dom, args.workload)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "alg_bytes_per_launch": per_call_bytes / launches_per_call, "avg_launch_ms": per_launch_ms,
+                "traffic": traffic}
+    kernels = {k: {"ms_per_step": kms[k] / args.steps, "launches_per_step": kla[k] / args.steps,
+                   "gbs": (alg_bytes(k, last, w) / (kms[k] / args.steps / 1e3) / 1e9) if kms[k] > 0 else None}
+               for k in kms if kla[k]}
+
+    # end to end through host buffers: H2D of the pairs, labels, D2H of the labels
+    e2e = None
+    if rank == 0 or world > 1:
+        h_edges = torch.from_numpy(g.edges).pin_memory()
+        h_lab = torch.empty(n, dtype=lab.dtype).pin_memory()
+        d_edges = torch.empty_like(edges_d)
+        eng.set_options(profile=0)
+        steps_e2e = max(3, min(args.steps, 10))
+        for _ in range(2):
+            d_edges.copy_(h_edges, non_blocking=True)
+            eng.labels(d_edges, n, out=lab)
+            h_lab.copy_(lab, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps_e2e):
+            d_edges.copy_(h_edges, non_blocking=True)
+            eng.labels(d_edges, n, out=lab)
+            h_lab.copy_(lab, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        t_e2e = a.elapsed_time(b) / steps_e2e
+        e2e = {"value": world * m / (t_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(g.edges.nbytes),
+               "d2h_bytes_per_step": int(n * lab.element_size()), "ms_per_step": t_e2e}
+        del d_edges
+        eng.set_options(profile=1)
+
+    # the forced routes on the same graph (the paper's dynamic-vs-opposite comparison)
+    route_compare = None
+    if not args.no_compare and rank == 0:
+        route_compare = {}
+        for r in ("sv", "bfs"):
+            e = cc.Engine(id_bytes=w, route=r, device=local)
+            e.labels(edges_d, n, out=lab)
+            torch.cuda.synchronize(dev)
+            k = max(3, min(args.steps, 5))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(k):
+                e.labels(edges_d, n, out=lab)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            t = a.elapsed_time(b) / k
+            sd = e.stats()
+            route_compare[r] = {"value": m / (t / 1e3), "ms_per_step": t, "route": sd["route"],
+                                "stage_ms": {k2: sd[k2] for k2 in ("ms_degree", "ms_predict", "ms_csr", "ms_bfs",
+                                                                   "ms_sv", "ms_finalize")}}
+            e.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, k, dt = cpu_oracle_rate(g.edges, n, args.cpu_pairs)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {k} of {m} pairs of the same graph, full n ({dt:.1f} s of sequential union-find)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32" if w == 4 else "int64", "data": "synthetic",
+                "config": cfg | {"route_policy": args.route, "route_taken": "bfs+sv" if last["route"] else "sv",
+                                 "ks_d": last["ks_d"], "sv_iters": last["sv_iters"],
+                                 "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches, "kernels": kernels, "route_compare": route_compare,
+                "stage_ms": {k: last[k] for k in ("ms_degree", "ms_predict", "ms_csr", "ms_bfs", "ms_sv",
+                                                  "ms_finalize", "ms_total")},
+                "m_active": last["m_active"]}
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

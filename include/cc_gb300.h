@@ -84,8 +84,28 @@ typedef struct {
     int debug_checks;       /* reserved: cc_labels always returns device-detected errors */
     int fault_inject;       /* CC_FAULT_* bits */
     double ks_min_span;     /* a candidate tail must reach max degree >= ks_min_span * xmin; default 10 */
-    int reserved[4];
+    int profile;            /* 1: time every kernel class with CUDA events (cc_stats.kernel_ms) */
+    int reserved[3];
 } cc_options;
+
+/* Kernel classes reported in cc_stats.kernel_ms / kernel_launches. */
+enum {
+    CC_K_DEGREE = 0,        /* degree pass over the pairs */
+    CC_K_HIST = 1,          /* degree histogram + argmax */
+    CC_K_KS = 2,            /* distinct degrees + power-law fit + K-S (six small kernels) */
+    CC_K_SCAN = 3,          /* prefix sums (CSR offsets, frontier offsets) */
+    CC_K_CSR = 4,           /* CSR scatter */
+    CC_K_BFS_TOPDOWN = 5,
+    CC_K_BFS_BOTTOMUP = 6,
+    CC_K_BFS_AUX = 7,       /* frontier conversions, degrees, visited count / minimum */
+    CC_K_PARENT_INIT = 8,
+    CC_K_SV_FIRST = 9,      /* first SV pass over the caller's pairs (no gathers) */
+    CC_K_SV_GATHER_INPUT = 10, /* SV pass with parent gathers over the caller's pairs */
+    CC_K_SV_GATHER_LIST = 11,  /* SV pass over the compacted active list */
+    CC_K_SV_SHORTCUT = 12,
+    CC_K_FINALIZE = 13,
+    CC_K_COUNT = 16
+};
 
 #define CC_MAX_SV_ITERS_RECORDED 64
 
@@ -110,6 +130,10 @@ typedef struct {
     int64_t m_active[CC_MAX_SV_ITERS_RECORDED]; /* active pairs entering each SV iteration */
     float ms_degree, ms_predict, ms_csr, ms_bfs, ms_sv, ms_finalize, ms_total; /* device stage times */
     float pad1;
+    int64_t launches;                   /* kernels this library launched in the call */
+    float kernel_ms[CC_K_COUNT];        /* summed device time per kernel class (options.profile = 1) */
+    int32_t kernel_launches[CC_K_COUNT];/* launches per kernel class (options.profile = 1) */
+    int64_t sv_hooks[CC_MAX_SV_ITERS_RECORDED]; /* roots hooked in each SV iteration */
 } cc_stats;
 
 /* Fills *opt with the defaults listed above. */

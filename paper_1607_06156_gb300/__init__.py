@@ -25,6 +25,10 @@ STATUS = {
 ROUTES = {"auto": 0, "learned": 1, "bfs": 2, "sv": 3}
 FAULT_ALLOC, FAULT_ITER_CAP = 1, 2
 MAX_SV_ITERS_RECORDED = 64
+K_COUNT = 16
+# kernel classes of cc_stats.kernel_ms (CC_K_* in the header)
+KERNELS = ["degree", "hist", "ks", "scan", "csr", "bfs_topdown", "bfs_bottomup", "bfs_aux", "parent_init",
+           "sv_first", "sv_gather_input", "sv_gather_list", "sv_shortcut", "finalize"]
 
 
 class CCError(RuntimeError):
@@ -38,7 +42,7 @@ class Options(ctypes.Structure):
         ("id_bytes", ctypes.c_int), ("route_policy", ctypes.c_int), ("ks_tau", ctypes.c_double),
         ("ks_min_tail", ctypes.c_int), ("ks_min_distinct", ctypes.c_int), ("max_iters", ctypes.c_int),
         ("bfs_cutoff_levels", ctypes.c_int), ("debug_checks", ctypes.c_int), ("fault_inject", ctypes.c_int),
-        ("ks_min_span", ctypes.c_double), ("reserved", ctypes.c_int * 4),
+        ("ks_min_span", ctypes.c_double), ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 3),
     ]
 
 
@@ -53,12 +57,18 @@ class Stats(ctypes.Structure):
         ("m_active", ctypes.c_int64 * MAX_SV_ITERS_RECORDED),
         ("ms_degree", ctypes.c_float), ("ms_predict", ctypes.c_float), ("ms_csr", ctypes.c_float),
         ("ms_bfs", ctypes.c_float), ("ms_sv", ctypes.c_float), ("ms_finalize", ctypes.c_float),
-        ("ms_total", ctypes.c_float), ("pad1", ctypes.c_float),
+        ("ms_total", ctypes.c_float), ("pad1", ctypes.c_float), ("launches", ctypes.c_int64),
+        ("kernel_ms", ctypes.c_float * K_COUNT), ("kernel_launches", ctypes.c_int32 * K_COUNT),
+        ("sv_hooks", ctypes.c_int64 * MAX_SV_ITERS_RECORDED),
     ]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
-        d["m_active"] = [int(x) for x in self.m_active[:max(0, min(self.sv_iters, MAX_SV_ITERS_RECORDED))]]
+        it = max(0, min(self.sv_iters, MAX_SV_ITERS_RECORDED))
+        d["m_active"] = [int(x) for x in self.m_active[:it]]
+        d["sv_hooks"] = [int(x) for x in self.sv_hooks[:it]]
+        d["kernel_ms"] = {KERNELS[i]: float(self.kernel_ms[i]) for i in range(len(KERNELS))}
+        d["kernel_launches"] = {KERNELS[i]: int(self.kernel_launches[i]) for i in range(len(KERNELS))}
         return d
 
 

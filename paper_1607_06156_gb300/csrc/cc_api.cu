@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "../../include/cc_gb300.h"
 #include "cc_common.cuh"
@@ -36,7 +37,7 @@ struct cc_ctx {
     size_t n_cap = 0, m_cap = 0;
     Buf deg, parent, hooked, ebuf0, ebuf1, hist, ovf, ks_xs, ks_cnt, ks_cum, ks_lnx, ks_Dc, ks_Ac, chunk_nz,
         chunk_mass, st;
-    unsigned long long ovf_cap = 0;
+    unsigned long long ovf_cap = 0, ks_cap = 0;
     // BFS workspace
     size_t bn_cap = 0, bm_cap = 0;
     Buf row_ptr, col, vis, fb, nb, q0, q1, dq, off, tsum, counters;
@@ -48,6 +49,14 @@ struct cc_ctx {
     cc_stats stats{};
     cc_status last_status = CC_OK;
     int alloc_fail_pending = 0;
+    // per-kernel-class event timing (options.profile)
+    struct ProfRec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> evpool;
+    size_t evpool_used = 0;
+    std::vector<ProfRec> prof;
 };
 
 namespace {
@@ -107,6 +116,7 @@ cc_status ensure_sv(cc_ctx *ctx, size_t n, size_t m) {
     ctx->ovf_cap = 2 * (unsigned long long)M / kHistDense + 2;
     CC_TRY(buf_reserve(ctx, ctx->ovf, ctx->ovf_cap * 4));
     const size_t nd = (N < (size_t)kHistDense + 4096 ? N : (size_t)kHistDense + 4096) + 2;
+    ctx->ks_cap = nd - 1;
     CC_TRY(buf_reserve(ctx, ctx->ks_xs, nd * 4));
     CC_TRY(buf_reserve(ctx, ctx->ks_cnt, nd * 8));
     CC_TRY(buf_reserve(ctx, ctx->ks_cum, nd * 8));
@@ -157,6 +167,60 @@ cc_status check_options(const cc_options *o) {
     return CC_OK;
 }
 
+cudaEvent_t pool_event(cc_ctx *ctx) {
+    if (ctx->evpool_used < ctx->evpool.size()) return ctx->evpool[ctx->evpool_used++];
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    ctx->evpool.push_back(e);
+    ctx->evpool_used++;
+    return e;
+}
+
+// Counts the launches of one kernel class and, with options.profile, brackets
+// them with a pair of events on the launching stream.
+struct Scope {
+    cc_ctx *ctx;
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    Scope(cc_ctx *c, int k, cudaStream_t st, int nlaunch) : ctx(c), cls(k), s(st) {
+        ctx->stats.launches += nlaunch;
+        if (ctx->opt.profile && ctx->prof.size() < 100000) {
+            a = pool_event(ctx);
+            if (a) cudaEventRecord(a, s);
+        }
+    }
+    ~Scope() {
+        if (!a) return;
+        cudaEvent_t b = pool_event(ctx);
+        if (!b) return;
+        cudaEventRecord(b, s);
+        ctx->prof.push_back({cls, a, b});
+    }
+};
+
+void prof_reset(cc_ctx *ctx) {
+    ctx->prof.clear();
+    ctx->evpool_used = 0;
+}
+
+// Resolves the recorded event pairs (the stream has been synchronised).
+void prof_collect(cc_ctx *ctx) {
+    for (const auto &r : ctx->prof) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            ctx->stats.kernel_ms[r.cls] += ms;
+            ctx->stats.kernel_launches[r.cls] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    ctx->prof.clear();
+}
+
 void rec(cc_ctx *ctx, Ev e, cudaStream_t s) {
     cudaEventRecord(ctx->ev[e], s);
     ctx->ev_used[e] = true;
@@ -190,15 +254,22 @@ template <typename T>
 void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s) {
     cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
     cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s);
-    launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), as<DevState>(ctx->st), ctx->grid, s);
-    launch_hist(as<uint32_t>(ctx->deg), n, as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap,
-                as<DevState>(ctx->st), ctx->grid, s);
+    {
+        Scope sc(ctx, CC_K_DEGREE, s, m > 0);
+        launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), as<DevState>(ctx->st), ctx->grid, s);
+    }
+    {
+        Scope sc(ctx, CC_K_HIST, s, 1);
+        launch_hist(as<uint32_t>(ctx->deg), n, as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap,
+                    as<DevState>(ctx->st), ctx->grid, s);
+    }
 }
 
 void enqueue_ks(cc_ctx *ctx, cudaStream_t s) {
     KsScratch ks{as<uint32_t>(ctx->ks_xs), as<unsigned long long>(ctx->ks_cnt), as<unsigned long long>(ctx->ks_cum),
                  as<double>(ctx->ks_lnx), as<double>(ctx->ks_Dc), as<double>(ctx->ks_Ac),
-                 as<unsigned long long>(ctx->chunk_nz), as<unsigned long long>(ctx->chunk_mass)};
+                 as<unsigned long long>(ctx->chunk_nz), as<unsigned long long>(ctx->chunk_mass), ctx->ks_cap};
+    Scope sc(ctx, CC_K_KS, s, 6);
     launch_ks(as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap, ks, as<DevState>(ctx->st),
               ctx->opt.ks_min_tail, ctx->opt.ks_min_distinct, ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->grid, s);
 }
@@ -212,13 +283,22 @@ cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStre
     vid_t *col = as<vid_t>(ctx->col);
     const long long nwords = ((long long)n + 31) / 32;
     // row_ptr = exclusive scan of deg; deg becomes the scatter cursor
-    launch_scan_u32(deg, n, row_ptr, deg, as<unsigned long long>(ctx->tsum), nullptr, row_ptr + n, s);
-    launch_csr_scatter<T>(edges, m, n, deg, col, ctx->grid, s);
+    {
+        Scope sc(ctx, CC_K_SCAN, s, 3);
+        launch_scan_u32(deg, n, row_ptr, deg, as<unsigned long long>(ctx->tsum), nullptr, row_ptr + n, s);
+    }
+    {
+        Scope sc(ctx, CC_K_CSR, s, 1);
+        launch_csr_scatter<T>(edges, m, n, deg, col, ctx->grid, s);
+    }
     rec(ctx, EV_CSR, s);
     cudaMemsetAsync(ctx->vis.p, 0, (size_t)nwords * 4, s);
     vid_t *qcur = as<vid_t>(ctx->q0), *qnext = as<vid_t>(ctx->q1);
     uint32_t *fb = as<uint32_t>(ctx->fb), *nb = as<uint32_t>(ctx->nb), *vis = as<uint32_t>(ctx->vis);
-    launch_bfs_init(row_ptr, n, vis, qcur, st, s);
+    {
+        Scope sc(ctx, CC_K_BFS_AUX, s, 1);
+        launch_bfs_init(row_ptr, n, vis, qcur, st, s);
+    }
     // Beamer's switching rule: go bottom-up when the frontier's edges exceed
     // 1/alpha of the unexplored edges; come back when the frontier holds fewer
     // than n/beta vertices and is shrinking.
@@ -239,24 +319,39 @@ cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStre
         if (bottom_up) {
             if (have_queue) {
                 cudaMemsetAsync(fb, 0, (size_t)nwords * 4, s);
+                Scope sc(ctx, CC_K_BFS_AUX, s, 1);
                 launch_queue_to_bitmap(qcur, (long long)f, fb, ctx->grid, s);
                 have_queue = false;
             }
-            launch_bfs_bottomup(n, row_ptr, col, fb, vis, nb, st, level, ctx->grid, s);
+            {
+                Scope sc(ctx, CC_K_BFS_BOTTOMUP, s, 1);
+                launch_bfs_bottomup(n, row_ptr, col, fb, vis, nb, st, level, ctx->grid, s);
+            }
             uint32_t *t = fb;
             fb = nb;
             nb = t;
         } else {
             if (!have_queue) {
                 cudaMemsetAsync(cnt, 0, 8, s);
+                Scope sc(ctx, CC_K_BFS_AUX, s, 1);
                 launch_bitmap_to_queue(fb, nwords, qcur, cnt, ctx->grid, s);
                 have_queue = true;
             }
             uint32_t *dq = as<uint32_t>(ctx->dq), *off = as<uint32_t>(ctx->off);
-            launch_front_degrees(qcur, (long long)f, row_ptr, dq, ctx->grid, s);
-            launch_scan_u32(dq, (long long)f, off, nullptr, as<unsigned long long>(ctx->tsum), nullptr, nullptr, s);
-            launch_bfs_topdown(qcur, (long long)f, off, (long long)fe, row_ptr, col, vis, qnext, st, level, ctx->grid,
-                               s);
+            {
+                Scope sc(ctx, CC_K_BFS_AUX, s, 1);
+                launch_front_degrees(qcur, (long long)f, row_ptr, dq, ctx->grid, s);
+            }
+            {
+                Scope sc(ctx, CC_K_SCAN, s, 3);
+                launch_scan_u32(dq, (long long)f, off, nullptr, as<unsigned long long>(ctx->tsum), nullptr, nullptr,
+                                s);
+            }
+            {
+                Scope sc(ctx, CC_K_BFS_TOPDOWN, s, 1);
+                launch_bfs_topdown(qcur, (long long)f, off, (long long)fe, row_ptr, col, vis, qnext, st, level,
+                                   ctx->grid, s);
+            }
             vid_t *t = qcur;
             qcur = qnext;
             qnext = t;
@@ -272,6 +367,7 @@ cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStre
     *levels_out = level;
     // visited count and the smallest visited id (the BFS component's label)
     cudaMemsetAsync(cnt + 1, 0, 8, s);
+    Scope sc(ctx, CC_K_BFS_AUX, s, 2);
     launch_popcount(vis, nwords, cnt + 1, ctx->grid, s);
     launch_first_visited(vis, nwords, st, ctx->grid, s);
     return CC_OK;
@@ -282,6 +378,7 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     DevState *st = as<DevState>(ctx->st);
     cc_stats &S = ctx->stats;
     memset(&S, 0, sizeof(S));
+    prof_reset(ctx);
     S.n = n;
     S.m = m;
     for (int e = 0; e < EV_COUNT; e++) ctx->ev_used[e] = false;
@@ -332,27 +429,53 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         S.bfs_levels = levels;
         S.bfs_visited = (int64_t)visited;
         S.comp_min = cmin;
-        launch_parent_init(parent, n, as<uint32_t>(ctx->vis), cmin, ctx->grid, s);
-        launch_sv_pass<T>(1, true, edges, m, n, parent, as<uint32_t>(ctx->vis), cmin, hooked, eb[0], st, 0, ctx->grid,
-                          s);
-        launch_sv_shortcut(parent, hooked, st, 0, ctx->grid, s);
+        {
+            Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
+            launch_parent_init(parent, n, as<uint32_t>(ctx->vis), cmin, ctx->grid, s);
+        }
+        {
+            Scope sc(ctx, CC_K_SV_FIRST, s, 1);
+            launch_sv_pass<T>(1, true, true, edges, m, n, parent, as<uint32_t>(ctx->vis), cmin, hooked, eb[0], st,
+                              0, ctx->grid, s);
+        }
+        {
+            Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
+            launch_sv_shortcut(parent, hooked, st, 0, ctx->grid, s);
+        }
         S.m_active[0] = m;
         CC_TRY(read_back(ctx, &st->kept[0], 8, s));
         m_cur = ctx->h_st->kept[0];
         src = eb[0];
     } else {
-        launch_parent_init(parent, n, nullptr, 0, ctx->grid, s);
+        {
+            Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
+            launch_parent_init(parent, n, nullptr, 0, ctx->grid, s);
+        }
         if (m > 0) {
-            launch_sv_pass<T>(0, false, edges, m, n, parent, nullptr, 0, hooked, nullptr, st, 0, ctx->grid, s);
-            launch_sv_shortcut(parent, hooked, st, 0, ctx->grid, s);
+            // every vertex is a root here: hook without recording, then shortcut all vertices
+            {
+                Scope sc(ctx, CC_K_SV_FIRST, s, 1);
+                launch_sv_pass<T>(0, false, false, edges, m, n, parent, nullptr, 0, hooked, nullptr, st, 0, ctx->grid,
+                                  s);
+            }
+            {
+                Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
+                launch_shortcut_all(parent, n, st, 0, ctx->grid, s);
+            }
             S.m_active[0] = m;
             it = 1;
             if (it >= cap) {
                 CC_TRY(read_back(ctx, &st->err, 4, s));
                 return ctx->h_st->err ? device_error(ctx->h_st->err) : CC_ERR_NO_CONVERGENCE;
             }
-            launch_sv_pass<T>(2, true, edges, m, n, parent, nullptr, 0, hooked, eb[0], st, 1, ctx->grid, s);
-            launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, s);
+            {
+                Scope sc(ctx, CC_K_SV_GATHER_INPUT, s, 1);
+                launch_sv_pass<T>(2, true, true, edges, m, n, parent, nullptr, 0, hooked, eb[0], st, 1, ctx->grid, s);
+            }
+            {
+                Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
+                launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, s);
+            }
             S.m_active[1] = m;
             CC_TRY(read_back(ctx, &st->kept[1], 8, s));
             m_cur = ctx->h_st->kept[1];
@@ -367,9 +490,15 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
             return CC_ERR_NO_CONVERGENCE;
         }
         if (it < CC_MAX_SV_ITERS_RECORDED) S.m_active[it] = (int64_t)m_cur;
-        launch_sv_pass<uint32_t>(2, true, src, (long long)m_cur, n, parent, nullptr, 0, hooked, eb[1 - cur], st, it,
-                                 ctx->grid, s);
-        launch_sv_shortcut(parent, hooked, st, it, ctx->grid, s);
+        {
+            Scope sc(ctx, CC_K_SV_GATHER_LIST, s, 1);
+            launch_sv_pass<uint32_t>(2, true, true, src, (long long)m_cur, n, parent, nullptr, 0, hooked, eb[1 - cur],
+                                     st, it, ctx->grid, s);
+        }
+        {
+            Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
+            launch_sv_shortcut(parent, hooked, st, it, ctx->grid, s);
+        }
         cur = 1 - cur;
         src = eb[cur];
         CU_TRY(cudaMemcpyAsync(&ctx->h_st->kept[it], &st->kept[it], 8, cudaMemcpyDeviceToHost, s));
@@ -378,11 +507,17 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     }
     S.sv_iters = it + 1;
     rec(ctx, EV_SV, s);
-    launch_finalize<T>(parent, n, labels_out, ctx->grid, s);
+    {
+        Scope sc(ctx, CC_K_FINALIZE, s, 1);
+        launch_finalize<T>(parent, n, labels_out, ctx->grid, s);
+    }
     rec(ctx, EV_END, s);
     CU_TRY(cudaMemcpyAsync(&ctx->h_st->err, &st->err, 4, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaMemcpyAsync(ctx->h_st->hooked, st->hooked, sizeof(ctx->h_st->hooked), cudaMemcpyDeviceToHost, s));
     CU_TRY(cudaStreamSynchronize(s));
     CU_TRY(cudaGetLastError());
+    for (int i = 0; i < CC_MAX_SV_ITERS_RECORDED && i <= it; i++) S.sv_hooks[i] = (int64_t)ctx->h_st->hooked[i];
+    prof_collect(ctx);
     return device_error(ctx->h_st->err);
 }
 
@@ -463,6 +598,7 @@ cc_status cc_destroy(cc_ctx *ctx) {
     for (Buf *b : bufs) buf_free(*b);
     for (int e = 0; e < EV_COUNT; e++)
         if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
+    for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     delete ctx;
     return CC_OK;
@@ -538,7 +674,8 @@ cc_status cc_ks_statistic(cc_ctx *ctx, const uint64_t *hist_dev, int64_t hist_le
     if (hist_len > (int64_t)kHistDense) return CC_ERR_UNSUPPORTED;
     CU_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
-    CC_TRY(ensure_sv(ctx, 1, 1));
+    // the distinct-degree scratch holds at most hist_len entries
+    CC_TRY(ensure_sv(ctx, (size_t)hist_len, 1));
     DevState *st = as<DevState>(ctx->st);
     CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
     CU_TRY(cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s));

@@ -17,6 +17,7 @@ struct KsScratch {
     double *Dc, *Ac;               // D and alpha per candidate xmin
     unsigned long long *chunk_nz;  // per-chunk distinct counts, then offsets
     unsigned long long *chunk_mass;
+    unsigned long long cap;        // entries of xs/cnt/lnx/Dc/Ac (cum holds cap + 1)
 };
 
 // k_degree.cu
@@ -33,8 +34,10 @@ void launch_hist_narrow(const uint64_t *in, long long len, uint32_t *hist, DevSt
 
 // k_sv.cu
 template <typename T>
-void launch_sv_pass(int mode, bool write, const void *in, long long m, vid_t n, vid_t *parent, const uint32_t *vis,
-                    vid_t cmin, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid, cudaStream_t s);
+void launch_sv_pass(int mode, bool write, bool record, const void *in, long long m, vid_t n, vid_t *parent,
+                    const uint32_t *vis, vid_t cmin, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
+                    cudaStream_t s);
+void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid, cudaStream_t s);
 void launch_sv_shortcut(vid_t *parent, const vid_t *hooked_list, DevState *st, int it, int grid, cudaStream_t s);
 void launch_parent_init(vid_t *parent, vid_t n, const uint32_t *vis, vid_t cmin, int grid, cudaStream_t s);
 template <typename T>

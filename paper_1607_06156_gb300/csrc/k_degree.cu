@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(1024) k_distinct_count(const uint32_t *hist, c
 }
 
 __global__ void __launch_bounds__(1024) k_distinct_scan(unsigned long long *chunk_nz, unsigned long long *chunk_mass,
-                                                        DevState *st) {
+                                                        DevState *st, unsigned long long cap) {
     // kNumChunks = 256 <= blockDim: one element per thread.
     __shared__ unsigned long long sm[33];
     const int t = threadIdx.x;
@@ -188,14 +188,16 @@ __global__ void __launch_bounds__(1024) k_distinct_scan(unsigned long long *chun
     if (t == 0) {
         chunk_nz[kNumChunks] = tnz;
         chunk_mass[kNumChunks] = tmass;
-        st->nd = tnz;
+        st->nd = tnz < cap ? tnz : cap;
+        if (tnz > cap) atomicOr(&st->err, kErrOverflow);
     }
 }
 
 __global__ void __launch_bounds__(1024) k_distinct_write(const uint32_t *hist, const DevState *st,
                                                          const unsigned long long *chunk_nz,
                                                          const unsigned long long *chunk_mass, uint32_t *xs,
-                                                         unsigned long long *cnt, unsigned long long *cum, double *lnx) {
+                                                         unsigned long long *cnt, unsigned long long *cum, double *lnx,
+                                                         unsigned long long cap) {
     __shared__ unsigned long long sm[33];
     const long long lim = dense_limit(st);
     const long long c0 = (long long)blockIdx.x * kChunk;
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(1024) k_distinct_write(const uint32_t *hist, c
         unsigned long long tnz, tmass;
         unsigned long long p = block_exclusive_scan<unsigned long long>(h ? 1ull : 0ull, sm, tnz);
         unsigned long long pm = block_exclusive_scan<unsigned long long>((unsigned long long)h, sm, tmass);
-        if (h) {
+        if (h && off + p < cap) {
             const unsigned long long k = off + p;
             xs[k] = (uint32_t)d;
             cnt[k] = h;
@@ -228,7 +230,8 @@ constexpr int kOvfMax = 4096;
 __global__ void __launch_bounds__(1024) k_distinct_overflow(const uint32_t *ovf, unsigned long long ovf_cap,
                                                             const unsigned long long *chunk_mass, DevState *st,
                                                             uint32_t *xs, unsigned long long *cnt,
-                                                            unsigned long long *cum, double *lnx) {
+                                                            unsigned long long *cum, double *lnx,
+                                                            unsigned long long cap) {
     __shared__ uint32_t sv[kOvfMax];
     __shared__ unsigned long long sm[33];
     const unsigned long long rec = st->n_ovf < ovf_cap ? st->n_ovf : ovf_cap;
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(1024) k_distinct_overflow(const uint32_t *ovf,
         const bool head = i < k && (i == 0 || sv[i] != sv[i - 1]);
         unsigned long long tot;
         const unsigned long long rank = block_exclusive_scan<unsigned long long>(head ? 1ull : 0ull, sm, tot);
-        if (head) {
+        if (head && base + out + rank < cap) {
             int e = i + 1;
             while (e < k && sv[e] == sv[i]) e++;
             const unsigned long long o = base + out + rank;
@@ -273,8 +276,10 @@ __global__ void __launch_bounds__(1024) k_distinct_overflow(const uint32_t *ovf,
         out += tot;
     }
     if (threadIdx.x == 0) {
-        st->nd = base + out;
-        cum[base + out] = mass0 + (unsigned long long)k;  // total mass of degrees >= 1
+        const unsigned long long nd = base + out < cap ? base + out : cap;
+        if (base + out > cap) atomicOr(&st->err, kErrOverflow);
+        st->nd = nd;
+        cum[nd] = mass0 + (unsigned long long)k;  // total mass of degrees >= 1
         if (rec > (unsigned long long)kOvfMax) atomicOr(&st->err, kErrOverflow);
     }
 }
@@ -285,18 +290,10 @@ __global__ void __launch_bounds__(1024) k_distinct_overflow(const uint32_t *ovf,
 // Euler-Maclaurin formula with six Bernoulli terms. With a >= 2s the ratio
 // of consecutive correction terms is below (s / (2 pi a))^2 <= 1/(16 pi^2),
 // so six terms leave a relative error near 1e-15.
-__device__ double zeta_scaled(double s, double q, double lnc) {
-    double acc = 0.0, a = q;
-    const double thr = fmax(16.0, 2.0 * s);
-    while (a < thr) {
-        const double term = exp(-s * (log(a) - lnc));
-        acc += term;
-        a += 1.0;
-        // the rest is below term * (1 + a/(s-1)) (integral bound); stop once it cannot matter
-        if (term * (1.0 + a / (s - 1.0)) < 1e-18 * acc) return acc;
-    }
-    const double A = exp(-s * (log(a) - lnc));
-    acc += A * a / (s - 1.0) + 0.5 * A;
+// Euler-Maclaurin remainder sum_{k>=0} ((a+k)/c)^-s for a >= max(16, 2s),
+// given A = (a/c)^-s.
+__device__ __forceinline__ double zeta_tail(double s, double a, double A) {
+    double acc = A * a / (s - 1.0) + 0.5 * A;
     const double ia2 = 1.0 / (a * a);
     // term_k = B_2k/(2k)! * s(s+1)...(s+2k-2) * A * a^-(2k-1)
     const double coef[6] = {1.0 / 12.0, -1.0 / 720.0, 1.0 / 30240.0, -1.0 / 1209600.0, 1.0 / 47900160.0,
@@ -309,6 +306,34 @@ __device__ double zeta_scaled(double s, double q, double lnc) {
         acc += coef[k] * t;
     }
     return acc;
+}
+
+__device__ double zeta_scaled(double s, double q, double lnc) {
+    double acc = 0.0, a = q;
+    const double thr = fmax(16.0, 2.0 * s);
+    while (a < thr) {
+        const double term = exp(-s * (log(a) - lnc));
+        acc += term;
+        a += 1.0;
+        // the rest is below term * (1 + a/(s-1)) (integral bound); stop once it cannot matter
+        if (term * (1.0 + a / (s - 1.0)) < 1e-18 * acc) return acc;
+    }
+    return acc + zeta_tail(s, a, exp(-s * (log(a) - lnc)));
+}
+
+// zeta_scaled at x and at x+1 for an observed degree x with ln x known.
+// For x >= max(16, 2s) one evaluation serves both: the x+1 value is the x
+// value minus its first term (x/c)^-s, and the tail is at least twice that
+// term, so the subtraction loses under two bits.
+__device__ __forceinline__ void zeta_pair(double s, double x, double lnx, double lnc, double &zx, double &zx1) {
+    if (x >= fmax(16.0, 2.0 * s)) {
+        const double A = exp(-s * (lnx - lnc));
+        zx = zeta_tail(s, x, A);
+        zx1 = zx - A;
+    } else {
+        zx = zeta_scaled(s, x, lnc);
+        zx1 = zeta_scaled(s, x + 1.0, lnc);
+    }
 }
 
 template <typename V>
@@ -363,8 +388,8 @@ __global__ void __launch_bounds__(256) k_ks_candidates(const uint32_t *xs, const
         double dmax = 0.0;
         for (long long j = i + threadIdx.x; j < nd; j += blockDim.x) {
             const double x = (double)xs[j];
-            const double zb = zeta_scaled(alpha, x, lnc);        // mass at >= x
-            const double za = zeta_scaled(alpha, x + 1.0, lnc);  // mass at >= x+1
+            double zb, za;  // model mass at >= x and at >= x+1 (scaled by xmin^alpha)
+            zeta_pair(alpha, x, lnx[j], lnc, zb, za);
             const double before = (double)(cum[j] - cum[i]) / N;
             const double at = (double)(cum[j + 1] - cum[i]) / N;
             double d = fabs(at - (1.0 - za / Z));
@@ -453,9 +478,10 @@ void launch_hist(const uint32_t *deg, vid_t n, uint32_t *hist, uint32_t *ovf, un
 void launch_ks(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf_cap, KsScratch ks, DevState *st,
                long long min_tail, long long min_distinct, double min_span, double tau, int grid, cudaStream_t s) {
     k_distinct_count<<<kNumChunks, 1024, 0, s>>>(hist, st, ks.chunk_nz, ks.chunk_mass);
-    k_distinct_scan<<<1, 1024, 0, s>>>(ks.chunk_nz, ks.chunk_mass, st);
-    k_distinct_write<<<kNumChunks, 1024, 0, s>>>(hist, st, ks.chunk_nz, ks.chunk_mass, ks.xs, ks.cnt, ks.cum, ks.lnx);
-    k_distinct_overflow<<<1, 1024, 0, s>>>(ovf, ovf_cap, ks.chunk_mass, st, ks.xs, ks.cnt, ks.cum, ks.lnx);
+    k_distinct_scan<<<1, 1024, 0, s>>>(ks.chunk_nz, ks.chunk_mass, st, ks.cap);
+    k_distinct_write<<<kNumChunks, 1024, 0, s>>>(hist, st, ks.chunk_nz, ks.chunk_mass, ks.xs, ks.cnt, ks.cum, ks.lnx,
+                                                 ks.cap);
+    k_distinct_overflow<<<1, 1024, 0, s>>>(ovf, ovf_cap, ks.chunk_mass, st, ks.xs, ks.cnt, ks.cum, ks.lnx, ks.cap);
     k_ks_candidates<<<grid, 256, 0, s>>>(ks.xs, ks.cnt, ks.cum, ks.lnx, st, min_tail, min_distinct, min_span, ks.Dc,
                                          ks.Ac);
     k_ks_select<<<1, 1024, 0, s>>>(ks.xs, ks.cum, ks.Dc, ks.Ac, st, tau);

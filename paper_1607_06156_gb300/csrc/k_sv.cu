@@ -51,83 +51,163 @@ __device__ __forceinline__ bool vis_test(const uint32_t *vis, long long v) {
     return (vis[v >> 5] >> (v & 31)) & 1u;
 }
 
-template <int MODE, bool WRITE>
-__device__ __forceinline__ void sv_pair(long long u, long long v, bool valid, vid_t n, vid_t *parent,
-                                        const uint32_t *vis, vid_t cmin, vid_t *hooked_list, unsigned long long hbase,
-                                        uint2 *out, DevState *st, int it, bool &bad) {
-    bool keep = false, first = false;
-    vid_t ru = 0, rv = 0, hi = 0;
-    if (valid) {
-        if ((unsigned long long)u >= n || (unsigned long long)v >= n) {
-            bad = true;
-        } else {
-            if (MODE == 0) {
-                ru = (vid_t)u;
-                rv = (vid_t)v;
-            } else if (MODE == 1) {
-                const bool ok = cmin < n;
-                const bool a = ok && vis_test(vis, u), b = ok && vis_test(vis, v);
-                ru = a ? cmin : (vid_t)u;
-                rv = b ? cmin : (vid_t)v;
-            } else {
-                ru = parent[u];
-                rv = parent[v];
-            }
-            if (ru != rv) {
-                hi = ru > rv ? ru : rv;
-                const vid_t lo = ru > rv ? rv : ru;
-                const vid_t old = atomicMin(&parent[hi], lo);
-                first = old == hi;
-                keep = true;
-            }
+// Block-wide exclusive scan of small per-thread counts; thread 0 reserves
+// the block's total from `counter` with one atomic. Returns this thread's
+// first slot. Called by every thread of the block.
+__device__ __forceinline__ unsigned long long block_reserve(unsigned long long *counter, int c, int *sw,
+                                                            unsigned long long *sbase) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sw[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int w = lane < nw ? sw[lane] : 0, wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
         }
+        if (lane < nw) sw[lane] = wi - w;
+        if (lane == nw - 1) *sbase = wi ? atomicAdd(counter, (unsigned long long)wi) : 0ull;
     }
-    const unsigned long long h = warp_append(&st->hooked[it], first);
-    if (first) hooked_list[hbase + h] = hi;
-    if (WRITE) {
-        const unsigned long long k = warp_append(&st->kept[it], keep);
-        if (keep) out[k] = make_uint2(ru, rv);
-    }
+    __syncthreads();
+    const unsigned long long r = *sbase + (unsigned long long)(sw[warp] + incl - c);
+    __syncthreads();
+    return r;
 }
 
-template <typename T, int MODE, bool WRITE>
+// One pair of an SV pass. Returns true if the pair stays active; `hooked`
+// is set when this pair's atomicMin turned a root into a non-root (only
+// tracked when RECORD). The plain read before the atomic skips hooks that
+// cannot lower parent[hi] (parents only decrease, so a stale read is an
+// upper bound of the current value).
+template <int MODE, bool RECORD>
+__device__ __forceinline__ bool sv_pair(long long u, long long v, vid_t n, vid_t *parent, const uint32_t *vis,
+                                        vid_t cmin, vid_t &ru, vid_t &rv, bool &hooked, bool &bad) {
+    hooked = false;
+    if ((unsigned long long)u >= n || (unsigned long long)v >= n) {
+        bad = true;
+        return false;
+    }
+    if (MODE == 0) {
+        ru = (vid_t)u;
+        rv = (vid_t)v;
+    } else if (MODE == 1) {
+        const bool ok = cmin < n;
+        const bool a = ok && vis_test(vis, u), b = ok && vis_test(vis, v);
+        ru = a ? cmin : (vid_t)u;
+        rv = b ? cmin : (vid_t)v;
+    } else {
+        ru = parent[u];
+        rv = parent[v];
+    }
+    if (ru == rv) return false;
+    const vid_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
+    if (parent[hi] > lo) {
+        if (RECORD) hooked = atomicMin(&parent[hi], lo) == hi;
+        else atomicMin(&parent[hi], lo);
+    }
+    return true;
+}
+
+template <typename T> struct PassUnroll { static constexpr int U = 2; };
+template <> struct PassUnroll<int64_t> { static constexpr int U = 4; };
+
+template <typename T, int MODE, bool WRITE, bool RECORD>
 __global__ void __launch_bounds__(kBlock) k_sv_pass(const T *__restrict__ in, long long m, vid_t n, vid_t *parent,
                                                     const uint32_t *__restrict__ vis, vid_t cmin, vid_t *hooked_list,
                                                     uint2 *__restrict__ out, DevState *st, int it) {
     constexpr int P = PairVec<T>::kPairs;
-    constexpr int U = 2;
+    constexpr int U = PassUnroll<T>::U;
+    constexpr int K = P * U;  // pairs per thread per round
+    __shared__ int sw[32];
+    __shared__ unsigned long long sbase;
     const long long nvec = m / P;
     const int4 *ev = reinterpret_cast<const int4 *>(in);
-    const unsigned long long hbase = st->hook_base[it];
+    const unsigned long long hbase = RECORD ? st->hook_base[it] : 0ull;
     bool bad = false;
-    const long long stride = gstride();
-    // every lane runs the same number of rounds so the warp-aggregated appends stay converged
-    const long long rounds = (nvec + stride * U - 1) / (stride * U);
-    for (long long r = 0; r < rounds; r++) {
-        const long long base = gtid() + r * stride * U;
-        int4 q[U];
+    // block-contiguous tiles of kBlock * U vectors, so the block's rounds are uniform
+    const long long tile = (long long)kBlock * U;
+    const long long ntiles = (nvec + tile - 1) / tile;
+    for (long long t = blockIdx.x; t < ntiles + (P == 2 && (m & 1) ? 1 : 0); t += gridDim.x) {
+        vid_t ru[K], rv[K];
+        bool keep[K], hk[K];
+        if (t < ntiles) {
+            int4 q[U];
 #pragma unroll
-        for (int k = 0; k < U; k++) {
-            const long long i = base + (long long)k * stride;
-            q[k] = i < nvec ? ld_stream(ev + i) : make_int4(0, 0, 0, 0);
-        }
+            for (int k = 0; k < U; k++) {
+                const long long i = t * tile + (long long)k * kBlock + threadIdx.x;
+                q[k] = i < nvec ? ld_stream(ev + i) : make_int4(0, 0, 0, 0);
+            }
 #pragma unroll
-        for (int k = 0; k < U; k++) {
-            const long long i = base + (long long)k * stride;
+            for (int k = 0; k < U; k++) {
+                const long long i = t * tile + (long long)k * kBlock + threadIdx.x;
 #pragma unroll
-            for (int j = 0; j < P; j++) {
+                for (int j = 0; j < P; j++) {
+                    long long u, v;
+                    vec_pair<T>(q[k], j, u, v);
+                    keep[k * P + j] = i < nvec && sv_pair<MODE, RECORD>(u, v, n, parent, vis, cmin, ru[k * P + j],
+                                                                        rv[k * P + j], hk[k * P + j], bad);
+                    if (i >= nvec) hk[k * P + j] = false;
+                }
+            }
+        } else {  // the odd last pair of an int32 / internal list
+#pragma unroll
+            for (int k = 0; k < K; k++) keep[k] = hk[k] = false;
+            if (threadIdx.x == 0) {
                 long long u, v;
-                vec_pair<T>(q[k], j, u, v);
-                sv_pair<MODE, WRITE>(u, v, i < nvec, n, parent, vis, cmin, hooked_list, hbase, out, st, it, bad);
+                scalar_pair<T>(in, m - 1, u, v);
+                keep[0] = sv_pair<MODE, RECORD>(u, v, n, parent, vis, cmin, ru[0], rv[0], hk[0], bad);
             }
         }
-    }
-    if (P == 2 && (m & 1) && blockIdx.x == 0 && threadIdx.x < 32) {
-        long long u = 0, v = 0;
-        if (threadIdx.x == 0) scalar_pair<T>(in, m - 1, u, v);
-        sv_pair<MODE, WRITE>(u, v, threadIdx.x == 0, n, parent, vis, cmin, hooked_list, hbase, out, st, it, bad);
+        if (WRITE) {
+            int c = 0;
+#pragma unroll
+            for (int k = 0; k < K; k++) c += keep[k];
+            unsigned long long o = block_reserve(&st->kept[it], c, sw, &sbase);
+#pragma unroll
+            for (int k = 0; k < K; k++)
+                if (keep[k]) out[o++] = make_uint2(ru[k], rv[k]);
+        }
+        if (RECORD) {
+            int c = 0;
+#pragma unroll
+            for (int k = 0; k < K; k++) c += hk[k];
+            unsigned long long o = block_reserve(&st->hooked[it], c, sw, &sbase);
+#pragma unroll
+            for (int k = 0; k < K; k++)
+                if (hk[k]) hooked_list[hbase + o++] = ru[k] > rv[k] ? ru[k] : rv[k];
+        }
     }
     if (bad) set_err(st, kErrInvalidEdge);
+}
+
+// Pointer jumping with path halving for every vertex (used after a pass that
+// did not record its hooks). Only shortcuts happen while it runs.
+__global__ void __launch_bounds__(kBlock) k_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it) {
+    for (long long v = gtid(); v < (long long)n; v += gstride()) {
+        vid_t y = parent[v];
+        if (y == (vid_t)v) continue;
+        while (true) {
+            const vid_t p = parent[y];
+            if (p == y) break;
+            const vid_t g = parent[p];
+            if (g == p) {
+                y = p;
+                break;
+            }
+            parent[y] = g;
+            y = g;
+        }
+        parent[v] = y;
+    }
+    if (gtid() == 0) st->hook_base[it + 1] = st->hook_base[it] + st->hooked[it];
 }
 
 // Path-halving shortcut of the roots hooked in iteration `it`. Only
@@ -199,24 +279,32 @@ __global__ void __launch_bounds__(kBlock) k_finalize(vid_t *parent, vid_t n, T *
 // Host launchers
 
 template <typename T>
-void launch_sv_pass(int mode, bool write, const void *in, long long m, vid_t n, vid_t *parent, const uint32_t *vis,
-                    vid_t cmin, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid, cudaStream_t s) {
+void launch_sv_pass(int mode, bool write, bool record, const void *in, long long m, vid_t n, vid_t *parent,
+                    const uint32_t *vis, vid_t cmin, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
+                    cudaStream_t s) {
     const T *e = (const T *)in;
+#define SVP(M, W, R) k_sv_pass<T, M, W, R><<<grid, kBlock, 0, s>>>(e, m, n, parent, vis, cmin, hooked_list, out, st, it)
     if (mode == 0) {
-        if (write) k_sv_pass<T, 0, true><<<grid, kBlock, 0, s>>>(e, m, n, parent, vis, cmin, hooked_list, out, st, it);
-        else k_sv_pass<T, 0, false><<<grid, kBlock, 0, s>>>(e, m, n, parent, vis, cmin, hooked_list, out, st, it);
+        if (write) SVP(0, true, false);
+        else SVP(0, false, false);
     } else if (mode == 1) {
-        k_sv_pass<T, 1, true><<<grid, kBlock, 0, s>>>(e, m, n, parent, vis, cmin, hooked_list, out, st, it);
+        SVP(1, true, true);
     } else {
-        k_sv_pass<T, 2, true><<<grid, kBlock, 0, s>>>(e, m, n, parent, vis, cmin, hooked_list, out, st, it);
+        if (record) SVP(2, true, true);
+        else SVP(2, true, false);
     }
+#undef SVP
 }
-template void launch_sv_pass<int32_t>(int, bool, const void *, long long, vid_t, vid_t *, const uint32_t *, vid_t,
-                                      vid_t *, uint2 *, DevState *, int, int, cudaStream_t);
-template void launch_sv_pass<int64_t>(int, bool, const void *, long long, vid_t, vid_t *, const uint32_t *, vid_t,
-                                      vid_t *, uint2 *, DevState *, int, int, cudaStream_t);
-template void launch_sv_pass<uint32_t>(int, bool, const void *, long long, vid_t, vid_t *, const uint32_t *, vid_t,
-                                       vid_t *, uint2 *, DevState *, int, int, cudaStream_t);
+template void launch_sv_pass<int32_t>(int, bool, bool, const void *, long long, vid_t, vid_t *, const uint32_t *,
+                                      vid_t, vid_t *, uint2 *, DevState *, int, int, cudaStream_t);
+template void launch_sv_pass<int64_t>(int, bool, bool, const void *, long long, vid_t, vid_t *, const uint32_t *,
+                                      vid_t, vid_t *, uint2 *, DevState *, int, int, cudaStream_t);
+template void launch_sv_pass<uint32_t>(int, bool, bool, const void *, long long, vid_t, vid_t *, const uint32_t *,
+                                       vid_t, vid_t *, uint2 *, DevState *, int, int, cudaStream_t);
+
+void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid, cudaStream_t s) {
+    k_shortcut_all<<<grid, kBlock, 0, s>>>(parent, n, st, it);
+}
 
 void launch_sv_shortcut(vid_t *parent, const vid_t *hooked_list, DevState *st, int it, int grid, cudaStream_t s) {
     k_sv_shortcut<<<grid, kBlock, 0, s>>>(parent, hooked_list, st, it);
