@@ -200,6 +200,40 @@ cc_status cc_degree_distribution(cc_ctx *ctx, const void *edges_dev, int64_t n, 
  */
 cc_status cc_ks_statistic(cc_ctx *ctx, const uint64_t *hist_dev, int64_t hist_len, double *out_host, void *stream);
 
+/* Size limits of cc_labels_static: its scratch is compiled into the library. */
+#define CC_STATIC_MAX_VERTICES (1 << 20)
+#define CC_STATIC_MAX_PAIRS (1 << 21)
+
+/*
+ * Connected-component labels without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that may not allocate
+ * device memory themselves - a plugin inside an application whose memory
+ * pool owns the whole device, or a latency-critical loop where cudaMalloc /
+ * cudaFree (which can synchronise the device) are not allowed.
+ *
+ * It runs the SV-only route of cc_labels (no degree pass, no prediction, no
+ * BFS; the labels are the same: min id of each component) on a scratch area
+ * that is a file-scope __device__ array of the library, about 40 MB, held
+ * by every GPU that loads the library until the process exits. It calls no
+ * cudaMalloc, cudaFree or allocating library routine, and needs no context.
+ *   edges_dev      [m][2] pairs of id_bytes (4 or 8) each, device, 16-byte aligned
+ *   n, m           at most CC_STATIC_MAX_VERTICES vertices and CC_STATIC_MAX_PAIRS
+ *                  pairs; larger sizes return CC_ERR_UNSUPPORTED before any work
+ *   labels_out_dev [n] ids of id_bytes each, device, 16-byte aligned
+ *   stream         cudaStream_t as void*
+ * Errors as cc_labels (CC_ERR_INVALID_EDGE for an id outside [0, n)). The
+ * call synchronises `stream` once per SV iteration and returns with the
+ * labels complete.
+ * The first call on each device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. Every call on a device shares the one
+ * scratch area and clears the parts that must start at zero; calls that
+ * overlap on the GPU (other streams or host threads) race and must be
+ * serialised by the caller.
+ */
+cc_status cc_labels_static(const void *edges_dev, int id_bytes, int64_t n, int64_t m, void *labels_out_dev,
+                           void *stream);
+
 /* Statistics of the last cc_labels call; synchronises its stream. Returns the recorded device status. */
 cc_status cc_get_stats(cc_ctx *ctx, cc_stats *out);
 

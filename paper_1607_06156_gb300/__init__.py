@@ -93,10 +93,12 @@ def lib() -> ctypes.CDLL:
         L.cc_degree_distribution.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp]
         L.cc_ks_statistic.argtypes = [_vp, _vp, _i64, _vp, _vp]
         L.cc_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
+        L.cc_labels_static.argtypes = [_vp, _int, _i64, _i64, _vp, _vp]
         L.cc_strerror.argtypes = [_int]
         L.cc_strerror.restype = ctypes.c_char_p
         for f in ("cc_default_options", "cc_create", "cc_set_options", "cc_destroy", "cc_labels",
-                  "cc_labels_batched", "cc_degree_distribution", "cc_ks_statistic", "cc_get_stats"):
+                  "cc_labels_batched", "cc_degree_distribution", "cc_ks_statistic", "cc_get_stats",
+                  "cc_labels_static"):
             getattr(L, f).restype = _int
         _lib = L
     return _lib
@@ -221,6 +223,23 @@ class Engine:
         s = Stats()
         lib().cc_get_stats(self._h, ctypes.byref(s))
         return s.as_dict()
+
+
+STATIC_MAX_VERTICES = 1 << 20
+STATIC_MAX_PAIRS = 1 << 21
+
+
+def labels_static(edges, n: int, out=None, stream=None):
+    """cc_labels_static: labels with the library's built-in scratch (no device allocation by the library)."""
+    import torch
+
+    m = edges.shape[0] if edges.numel() else 0
+    if out is None:
+        out = torch.empty(n, dtype=edges.dtype, device=edges.device)
+    rc = lib().cc_labels_static(edges.data_ptr() if m else None, edges.element_size(), n, m,
+                                out.data_ptr() if n else None, _stream_handle(stream, edges.device))
+    _check(rc, "cc_labels_static")
+    return out
 
 
 def strerror(status: int) -> str:
