@@ -44,7 +44,7 @@ WORKLOADS = {
     "planted": dict(kind="planted", seed=1),
     "grid_chains": dict(kind="grid_chains", seed=1, W=8192, nchains=10_000_000),
 }
-KERNEL_FILES = ["cc_common.cuh", "k_degree.cu", "k_sv.cu", "k_bfs.cu", "cc_api.cu"]
+KERNEL_FILES = ["cc_common.cuh", "k_degree.cu", "k_sv.cu", "k_bfs.cu", "k_bucket.cu", "cc_api.cu"]
 
 
 def make_graph(name: str):

@@ -35,12 +35,12 @@ struct cc_ctx {
     int grid = 0;  // blocks for grid-stride kernels
     // SV / degree workspace
     size_t n_cap = 0, m_cap = 0;
-    Buf deg, parent, hooked, ebuf0, ebuf1, hist, ovf, ks_xs, ks_cnt, ks_cum, ks_lnx, ks_Dc, ks_Ac, chunk_nz,
-        chunk_mass, st;
+    Buf deg, parent, hooked, ebuf0, ebuf1, hist, ovf, ks_xs, ks_cnt, ks_cum, ks_lnx, ks_Dc, ks_Ac, ks_Zc, ks_Df, chunk_nz,
+        chunk_mass, st, bk_count, bk_off, bk_cursor;
     unsigned long long ovf_cap = 0, ks_cap = 0;
     // BFS workspace
     size_t bn_cap = 0, bm_cap = 0;
-    Buf row_ptr, col, vis, fb, nb, q0, q1, dq, off, tsum, counters;
+    Buf row_ptr, col, vis, fb, nb, q0, q1, dq, off, tsum, counters, csr_entries;
     // host side
     DevState *h_st = nullptr;  // pinned mirror of the device state
     cudaEvent_t ev[EV_COUNT] = {};
@@ -104,6 +104,13 @@ void buf_free(Buf &b) {
 
 size_t round4(size_t x) { return (x + 3) & ~(size_t)3; }
 
+// The vertex-block partitioned CSR build handles up to 1024 blocks of 2^15
+// vertices; small inputs keep the direct scatter.
+bool bucketed_ok(size_t n, size_t m) {
+    return n > 0 && bucket_count_for((vid_t)(n < 0xffffffffULL ? n : 0xfffffffeULL)) <= bucket_max() &&
+           m >= ((size_t)1 << 20);
+}
+
 cc_status ensure_sv(cc_ctx *ctx, size_t n, size_t m) {
     if (n <= ctx->n_cap && m <= ctx->m_cap && ctx->st.p) return CC_OK;
     const size_t N = n > ctx->n_cap ? n : ctx->n_cap, M = m > ctx->m_cap ? m : ctx->m_cap;
@@ -123,9 +130,14 @@ cc_status ensure_sv(cc_ctx *ctx, size_t n, size_t m) {
     CC_TRY(buf_reserve(ctx, ctx->ks_lnx, nd * 8));
     CC_TRY(buf_reserve(ctx, ctx->ks_Dc, nd * 8));
     CC_TRY(buf_reserve(ctx, ctx->ks_Ac, nd * 8));
+    CC_TRY(buf_reserve(ctx, ctx->ks_Zc, nd * 8));
+    CC_TRY(buf_reserve(ctx, ctx->ks_Df, nd * 4));
     CC_TRY(buf_reserve(ctx, ctx->chunk_nz, (size_t)(ks_num_chunks() + 1) * 8));
     CC_TRY(buf_reserve(ctx, ctx->chunk_mass, (size_t)(ks_num_chunks() + 1) * 8));
     CC_TRY(buf_reserve(ctx, ctx->st, sizeof(DevState)));
+    CC_TRY(buf_reserve(ctx, ctx->bk_count, (size_t)ctx->grid * (bucket_max() + 2) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->bk_cursor, (size_t)ctx->grid * (bucket_max() + 2) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->bk_off, (size_t)(bucket_max() + 2) * 8));
     ctx->n_cap = N;
     ctx->m_cap = M;
     return CC_OK;
@@ -146,6 +158,7 @@ cc_status ensure_bfs(cc_ctx *ctx, size_t n, size_t m) {
     CC_TRY(buf_reserve(ctx, ctx->off, (N + 8) * 4));
     CC_TRY(buf_reserve(ctx, ctx->tsum, (size_t)(scan_num_tiles((long long)N + 2) + 4) * 8));
     CC_TRY(buf_reserve(ctx, ctx->counters, 64 * 8));
+    if (bucketed_ok(N, M)) CC_TRY(buf_reserve(ctx, ctx->csr_entries, (2 * M + 4) * 8));
     ctx->bn_cap = N;
     ctx->bm_cap = M;
     return CC_OK;
@@ -249,11 +262,15 @@ int default_max_iters(long long n) {
     return c < kMaxIters - 1 ? c : kMaxIters - 1;
 }
 
-// Degree pass + histogram + K-S fit; leaves the route in DevState.
+BucketScratch bucket_scratch(cc_ctx *ctx) {
+    return BucketScratch{as<uint32_t>(ctx->bk_count), as<uint32_t>(ctx->bk_cursor), as<unsigned long long>(ctx->bk_off)};
+}
+
+// Degree pass + histogram (Algorithm 2 line 1).
 template <typename T>
 void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s) {
-    cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
     cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s);
+    cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
     {
         Scope sc(ctx, CC_K_DEGREE, s, m > 0);
         launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), as<DevState>(ctx->st), ctx->grid, s);
@@ -267,9 +284,10 @@ void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaSt
 
 void enqueue_ks(cc_ctx *ctx, cudaStream_t s) {
     KsScratch ks{as<uint32_t>(ctx->ks_xs), as<unsigned long long>(ctx->ks_cnt), as<unsigned long long>(ctx->ks_cum),
-                 as<double>(ctx->ks_lnx), as<double>(ctx->ks_Dc), as<double>(ctx->ks_Ac),
+                 as<double>(ctx->ks_lnx), as<double>(ctx->ks_Dc), as<double>(ctx->ks_Ac), as<double>(ctx->ks_Zc),
+                 as<float>(ctx->ks_Df),
                  as<unsigned long long>(ctx->chunk_nz), as<unsigned long long>(ctx->chunk_mass), ctx->ks_cap};
-    Scope sc(ctx, CC_K_KS, s, 6);
+    Scope sc(ctx, CC_K_KS, s, 7);
     launch_ks(as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap, ks, as<DevState>(ctx->st),
               ctx->opt.ks_min_tail, ctx->opt.ks_min_distinct, ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->grid, s);
 }
@@ -282,12 +300,19 @@ cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStre
     uint32_t *row_ptr = as<uint32_t>(ctx->row_ptr), *deg = as<uint32_t>(ctx->deg);
     vid_t *col = as<vid_t>(ctx->col);
     const long long nwords = ((long long)n + 31) / 32;
-    // row_ptr = exclusive scan of deg; deg becomes the scatter cursor
+    // row_ptr = exclusive scan of deg
+    const bool bucketed = bucketed_ok(n, (size_t)m) && ctx->csr_entries.p;
     {
         Scope sc(ctx, CC_K_SCAN, s, 3);
-        launch_scan_u32(deg, n, row_ptr, deg, as<unsigned long long>(ctx->tsum), nullptr, row_ptr + n, s);
+        // the direct scatter uses deg as its cursor
+        launch_scan_u32(deg, n, row_ptr, bucketed ? nullptr : deg, as<unsigned long long>(ctx->tsum), nullptr,
+                        row_ptr + n, s);
     }
-    {
+    if (bucketed) {
+        Scope sc(ctx, CC_K_CSR, s, 4);
+        launch_csr_bucketed<T>(edges, m, n, row_ptr, col, bucket_scratch(ctx), as<unsigned long long>(ctx->csr_entries),
+                               st, ctx->grid, s);
+    } else {
         Scope sc(ctx, CC_K_CSR, s, 1);
         launch_csr_scatter<T>(edges, m, n, deg, col, ctx->grid, s);
     }
@@ -387,6 +412,7 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     const int policy = ctx->opt.route_policy;
     int route = 0;
     S.route_source = policy == CC_ROUTE_AUTO || policy == CC_ROUTE_LEARNED ? 0 : 2;
+    vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
     if (policy != CC_ROUTE_FORCE_SV && m > 0) {
         enqueue_degree<T>(ctx, edges, n, m, s);
         rec(ctx, EV_DEGREE, s);
@@ -411,7 +437,6 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     const int cap = ctx->opt.fault_inject & CC_FAULT_ITER_CAP ? 1
                     : ctx->opt.max_iters > 0                  ? ctx->opt.max_iters
                                                               : default_max_iters(n);
-    vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
     uint2 *eb[2] = {as<uint2>(ctx->ebuf0), as<uint2>(ctx->ebuf1)};
     int it = 0;
     unsigned long long m_cur = 0;
@@ -568,6 +593,11 @@ cc_status cc_create(cc_ctx **out, const cc_options *opt, int device) {
         return CC_ERR_CUDA;
     }
     ctx->num_sms = prop.multiProcessorCount;
+    if (bucket_kernels_setup() != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return CC_ERR_CUDA;
+    }
     ctx->grid = ctx->num_sms * (prop.maxThreadsPerMultiProcessor / kBlock);
     if (cudaMallocHost(&ctx->h_st, sizeof(DevState)) != cudaSuccess) {
         delete ctx;
@@ -592,9 +622,10 @@ cc_status cc_destroy(cc_ctx *ctx) {
     cudaDeviceSynchronize();
     Buf *bufs[] = {&ctx->deg,    &ctx->parent,     &ctx->hooked, &ctx->ebuf0,   &ctx->ebuf1,  &ctx->hist,
                    &ctx->ovf,    &ctx->ks_xs,      &ctx->ks_cnt, &ctx->ks_cum,  &ctx->ks_lnx, &ctx->ks_Dc,
-                   &ctx->ks_Ac,  &ctx->chunk_nz,   &ctx->chunk_mass, &ctx->st,  &ctx->row_ptr, &ctx->col,
+                   &ctx->ks_Ac,  &ctx->ks_Zc, &ctx->ks_Df, &ctx->chunk_nz,   &ctx->chunk_mass, &ctx->st,  &ctx->row_ptr, &ctx->col,
                    &ctx->vis,    &ctx->fb,         &ctx->nb,     &ctx->q0,      &ctx->q1,     &ctx->dq,
-                   &ctx->off,    &ctx->tsum,       &ctx->counters};
+                   &ctx->off,    &ctx->tsum,       &ctx->counters, &ctx->bk_count, &ctx->bk_off,
+                   &ctx->bk_cursor, &ctx->csr_entries};
     for (Buf *b : bufs) buf_free(*b);
     for (int e = 0; e < EV_COUNT; e++)
         if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);

@@ -14,11 +14,27 @@ struct KsScratch {
     unsigned long long *cnt;       // vertices per distinct degree
     unsigned long long *cum;       // exclusive prefix of cnt (one extra entry: total)
     double *lnx;                   // ln(xs)
-    double *Dc, *Ac;               // D and alpha per candidate xmin
+    double *Dc, *Ac, *Zc;          // D, alpha and scaled zeta(alpha, xmin) per candidate xmin
+    float *Df;                     // fp32 screen maximum per candidate
     unsigned long long *chunk_nz;  // per-chunk distinct counts, then offsets
     unsigned long long *chunk_mass;
     unsigned long long cap;        // entries of xs/cnt/lnx/Dc/Ac (cum holds cap + 1)
 };
+
+// Scratch of the vertex-block partitioned CSR build (k_bucket.cu).
+struct BucketScratch {
+    uint32_t *counts;             // [grid][buckets] entries of each grid block's chunks per vertex block
+    uint32_t *off;                // [grid][buckets] private write offsets
+    unsigned long long *boff;     // [buckets + 1] (unused by the CSR build)
+};
+
+// k_bucket.cu
+int bucket_count_for(vid_t n);
+int bucket_max();
+template <typename T>
+void launch_csr_bucketed(const void *edges, long long m, vid_t n, const uint32_t *row_ptr, vid_t *col,
+                         BucketScratch bs, unsigned long long *entries, DevState *st, int grid, cudaStream_t s);
+cudaError_t bucket_kernels_setup();
 
 // k_degree.cu
 template <typename T>
@@ -38,6 +54,7 @@ void launch_sv_pass(int mode, bool write, bool record, const void *in, long long
                     const uint32_t *vis, vid_t cmin, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
                     cudaStream_t s);
 void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid, cudaStream_t s);
+
 void launch_sv_shortcut(vid_t *parent, const vid_t *hooked_list, DevState *st, int it, int grid, cudaStream_t s);
 void launch_parent_init(vid_t *parent, vid_t n, const uint32_t *vis, vid_t cmin, int grid, cudaStream_t s);
 template <typename T>

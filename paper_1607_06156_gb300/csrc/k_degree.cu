@@ -361,46 +361,145 @@ __device__ double block_reduce_max(double x, double *smem) {
     return r;
 }
 
-__global__ void __launch_bounds__(256) k_ks_candidates(const uint32_t *xs, const unsigned long long *cnt,
-                                                       const unsigned long long *cum, const double *lnx,
-                                                       const DevState *st, long long min_tail, long long min_distinct,
-                                                       double min_span, double *Dc, double *Ac) {
-    __shared__ double sd[32];
+// Candidate setup, one warp per candidate xmin: the tail rules, the
+// exponent alpha (Clauset et al. eq. 3.7) and the normaliser Z = scaled
+// zeta(alpha, xmin). Non-candidates get D = 2 (never selected).
+__global__ void __launch_bounds__(256) k_ks_prep(const uint32_t *xs, const unsigned long long *cnt,
+                                                 const unsigned long long *cum, const double *lnx, const DevState *st,
+                                                 long long min_tail, long long min_distinct, double min_span,
+                                                 double *Dc, double *Ac, double *Zc) {
     const long long nd = (long long)st->nd;
     if (nd == 0) return;
+    const int lane = threadIdx.x & 31;
+    const long long warp = gtid() >> 5, nwarps = gstride() >> 5;
     const double xmax = (double)xs[nd - 1];
     const unsigned long long total = cum[nd];
-    for (long long i = blockIdx.x; i < nd; i += gridDim.x) {
+    for (long long i = warp; i < nd; i += nwarps) {
         const double xmin = (double)xs[i];
         const unsigned long long Nt = total - cum[i];
         if ((long long)Nt < min_tail || nd - i < min_distinct || xmax < min_span * xmin) {
-            if (threadIdx.x == 0) Dc[i] = 2.0;  // not a candidate
+            if (lane == 0) Dc[i] = 2.0;
             continue;
         }
-        const double N = (double)Nt;
         const double lshift = log(xmin - 0.5);
-        double part = 0.0;
-        for (long long j = i + threadIdx.x; j < nd; j += blockDim.x) part += (double)cnt[j] * (lnx[j] - lshift);
-        const double S = block_reduce_sum<double>(part, sd);
-        const double alpha = 1.0 + N / S;
-        const double lnc = lnx[i];
-        const double Z = zeta_scaled(alpha, xmin, lnc);
-        double dmax = 0.0;
-        for (long long j = i + threadIdx.x; j < nd; j += blockDim.x) {
-            const double x = (double)xs[j];
-            double zb, za;  // model mass at >= x and at >= x+1 (scaled by xmin^alpha)
-            zeta_pair(alpha, x, lnx[j], lnc, zb, za);
-            const double before = (double)(cum[j] - cum[i]) / N;
-            const double at = (double)(cum[j + 1] - cum[i]) / N;
-            double d = fabs(at - (1.0 - za / Z));
-            if (j > i) d = fmax(d, fabs(before - (1.0 - zb / Z)));
-            dmax = fmax(dmax, d);
-        }
-        const double D = block_reduce_max(dmax, sd);
-        if (threadIdx.x == 0) {
-            Dc[i] = D;
+        double S = 0.0;
+        for (long long j = i + lane; j < nd; j += 32) S += (double)cnt[j] * (lnx[j] - lshift);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+        if (lane == 0) {
+            const double alpha = 1.0 + (double)Nt / S;
             Ac[i] = alpha;
+            Zc[i] = zeta_scaled(alpha, xmin, lnx[i]);
+            Dc[i] = 0.0;
         }
+    }
+}
+
+// The sup distance is taken in two passes over (candidate, chunk of
+// kKsTerms terms) blocks. The screen evaluates every term in fp32 and keeps
+// each candidate's fp32 maximum; the refine pass re-evaluates in fp64 only
+// the terms whose fp32 value is within kScreenSlack of that maximum and
+// folds them into D[i] (atomicMax on the bit pattern: non-negative doubles
+// and floats order like their bits). The fp32 terms are within ~3e-6 of the
+// fp64 ones (a few ulp on S, on the zeta ratio and on 1 - ratio), far inside
+// the 1e-4 slack, so the term that attains the fp64 maximum always passes
+// the screen and D[i] is the fp64 sup.
+constexpr int kKsTerms = 1024;
+constexpr float kScreenSlack = 1e-4f;
+
+__device__ __forceinline__ float zeta_tail_f(float s, float a, float A) {
+    float acc = A * a / (s - 1.0f) + 0.5f * A;
+    const float ia2 = 1.0f / (a * a);
+    float t = A * s / a;
+    acc += t * (1.0f / 12.0f);
+    t *= (s + 1.0f) * (s + 2.0f) * ia2;
+    acc -= t * (1.0f / 720.0f);
+    t *= (s + 3.0f) * (s + 4.0f) * ia2;
+    acc += t * (1.0f / 30240.0f);
+    return acc;
+}
+
+__device__ float zeta_scaled_f(float s, float q, float lnc) {
+    float acc = 0.0f, a = q;
+    const float thr = fmaxf(16.0f, 2.0f * s);
+    while (a < thr) {
+        const float term = __expf(-s * (__logf(a) - lnc));
+        acc += term;
+        a += 1.0f;
+        if (term * (1.0f + a / (s - 1.0f)) < 1e-9f * acc) return acc;
+    }
+    return acc + zeta_tail_f(s, a, __expf(-s * (__logf(a) - lnc)));
+}
+
+// fp32 distance of term j of candidate i
+__device__ __forceinline__ float ks_term_f(float alpha, float Z, float lnc, float x, float lnxj, float before,
+                                           float at, bool first) {
+    float zb, za;
+    if (x >= fmaxf(16.0f, 2.0f * alpha)) {
+        const float A = __expf(-alpha * (lnxj - lnc));
+        zb = zeta_tail_f(alpha, x, A);
+        za = zb - A;
+    } else {
+        zb = zeta_scaled_f(alpha, x, lnc);
+        za = zeta_scaled_f(alpha, x + 1.0f, lnc);
+    }
+    float d = fabsf(at - (1.0f - za / Z));
+    if (!first) d = fmaxf(d, fabsf(before - (1.0f - zb / Z)));
+    return d;
+}
+
+template <bool REFINE>
+__global__ void __launch_bounds__(256) k_ks_terms(const uint32_t *xs, const unsigned long long *cum,
+                                                  const double *lnx, const DevState *st, double *Dc, const double *Ac,
+                                                  const double *Zc, float *Df) {
+    __shared__ float sf[8];
+    __shared__ double sd[8];
+    const long long nd = (long long)st->nd;
+    for (long long i = blockIdx.y; i < nd; i += gridDim.y)
+    for (long long j0 = i + (long long)blockIdx.x * kKsTerms; j0 < nd; j0 += (long long)gridDim.x * kKsTerms) {
+        if (Dc[i] > 1.0) break;  // not a candidate (block-uniform)
+        const double alpha = Ac[i], Z = Zc[i], lnc = lnx[i];
+        const float alpha_f = (float)alpha, Z_f = (float)Z, lnc_f = (float)lnc;
+        const unsigned long long ci = cum[i];
+        const double N = (double)(cum[nd] - ci);
+        const float cut = REFINE ? Df[i] - kScreenSlack : 0.0f;
+        float fmax_ = 0.0f;
+        double dmax = 0.0;
+        for (long long j = j0 + threadIdx.x; j < nd && j < j0 + kKsTerms; j += blockDim.x) {
+            const double x = (double)xs[j];
+            const double before = (double)(cum[j] - ci) / N;
+            const double at = (double)(cum[j + 1] - ci) / N;
+            const float d32 = ks_term_f(alpha_f, Z_f, lnc_f, (float)x, (float)lnx[j], (float)before, (float)at, j == i);
+            fmax_ = fmaxf(fmax_, d32);
+            if (REFINE && d32 >= cut) {
+                double zb, za;  // model mass at >= x and at >= x+1 (scaled by xmin^alpha)
+                zeta_pair(alpha, x, lnx[j], lnc, zb, za);
+                double d = fabs(at - (1.0 - za / Z));
+                if (j > i) d = fmax(d, fabs(before - (1.0 - zb / Z)));
+                dmax = fmax(dmax, d);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fmax_ = fmaxf(fmax_, __shfl_xor_sync(0xffffffffu, fmax_, o));
+            dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sf[threadIdx.x >> 5] = fmax_;
+            sd[threadIdx.x >> 5] = dmax;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float bf = 0.0f;
+            double bd = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+                bf = fmaxf(bf, sf[w]);
+                bd = fmax(bd, sd[w]);
+            }
+            if (REFINE) atomicMax(reinterpret_cast<unsigned long long *>(&Dc[i]), (unsigned long long)__double_as_longlong(bd));
+            else atomicMax(reinterpret_cast<unsigned int *>(&Df[i]), __float_as_uint(bf));
+        }
+        __syncthreads();
     }
 }
 
@@ -482,8 +581,13 @@ void launch_ks(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf
     k_distinct_write<<<kNumChunks, 1024, 0, s>>>(hist, st, ks.chunk_nz, ks.chunk_mass, ks.xs, ks.cnt, ks.cum, ks.lnx,
                                                  ks.cap);
     k_distinct_overflow<<<1, 1024, 0, s>>>(ovf, ovf_cap, ks.chunk_mass, st, ks.xs, ks.cnt, ks.cum, ks.lnx, ks.cap);
-    k_ks_candidates<<<grid, 256, 0, s>>>(ks.xs, ks.cnt, ks.cum, ks.lnx, st, min_tail, min_distinct, min_span, ks.Dc,
-                                         ks.Ac);
+    k_ks_prep<<<grid, 256, 0, s>>>(ks.xs, ks.cnt, ks.cum, ks.lnx, st, min_tail, min_distinct, min_span, ks.Dc,
+                                   ks.Ac, ks.Zc);
+    // blocks stride over candidates (y) and over chunks of kKsTerms terms (x)
+    const dim3 tg(4, 2048);
+    cudaMemsetAsync(ks.Df, 0, sizeof(float) * (ks.cap + 1), s);
+    k_ks_terms<false><<<tg, 256, 0, s>>>(ks.xs, ks.cum, ks.lnx, st, ks.Dc, ks.Ac, ks.Zc, ks.Df);
+    k_ks_terms<true><<<tg, 256, 0, s>>>(ks.xs, ks.cum, ks.lnx, st, ks.Dc, ks.Ac, ks.Zc, ks.Df);
     k_ks_select<<<1, 1024, 0, s>>>(ks.xs, ks.cum, ks.Dc, ks.Ac, st, tau);
 }
 

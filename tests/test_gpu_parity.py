@@ -242,3 +242,30 @@ def test_ks_statistic_synthetic_histograms():
         got = _ks_dev(hist)
         assert got["ncand"] == want["ncand"] and got["xmin"] == want["xmin"], (got, want)
         assert abs(got["D"] - want["D"]) < 1e-9, (got, want)
+
+
+@pytest.mark.parametrize("id_bytes", [4, 8])
+def test_partitioned_degree_and_csr_paths(id_bytes):
+    """m >= 2^20 takes the vertex-block partitioned degree pass and CSR build;
+    an odd m exercises the ragged last pair, a hub the merged smem atomics."""
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    g = gg.rmat(seed=21, scale=16, edge_factor=16, m=(1 << 20) + 7, id_bytes=id_bytes)
+    hub = np.stack([np.full(70000, 12345), np.arange(70000) * 3 % g.n], axis=1).astype(g.edges.dtype)
+    e = np.concatenate([g.edges, hub])
+    deg_o = oracle.degrees(e, g.n)
+    eng = cc.Engine(id_bytes=id_bytes)
+    deg, hist = eng.degree_distribution(torch.from_numpy(e).cuda(), g.n, hist_len=int(deg_o.max()) + 2)
+    assert np.array_equal(deg.cpu().numpy().astype(np.int64), deg_o)
+    assert np.array_equal(hist.cpu().numpy()[:-1], oracle.histogram(deg_o))
+    eng.close()
+    assert_labels_match(e, g.n, routes=("auto", "bfs"))
+
+
+def test_partitioned_paths_many_vertex_blocks():
+    """n close to the partition limit (1024 blocks of 2^15 vertices)."""
+    n = (1 << 25) - 5
+    rng = np.random.default_rng(8)
+    e = rng.integers(0, n, size=((1 << 21) + 1, 2)).astype(np.int32)
+    assert_labels_match(e, n, routes=("bfs",))
