@@ -43,6 +43,8 @@ WORKLOADS = {
     "rmat20": dict(kind="rmat", scale=20, edge_factor=16, seed=1),
     "planted": dict(kind="planted", seed=1),
     "grid_chains": dict(kind="grid_chains", seed=1, W=8192, nchains=10_000_000),
+    "batch4096": dict(kind="batch", seed=1, G=4096, nmin=1000, nmax=1_000_000),
+    "batch512": dict(kind="batch", seed=1, G=512, nmin=1000, nmax=1_000_000),
 }
 KERNEL_FILES = ["cc_common.cuh", "k_degree.cu", "k_sv.cu", "k_bfs.cu", "k_bucket.cu", "cc_api.cu"]
 
@@ -220,6 +222,85 @@ def run_reference(args, world: int, rank: int):
     return 0
 
 
+def run_batch(args, world: int, rank: int, local: int) -> int:
+    """Batched form: one cc_labels_batched call per step over G graphs, against
+    a loop of per-graph cc_labels calls on the same GPU (labels compared)."""
+    import torch
+
+    import graphgen as gg
+    import paper_1607_06156_gb300 as cc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = dict(WORKLOADS[args.workload])
+    w.pop("kind")
+    b = gg.batch(**w)
+    m, n = int(b.edge_offsets[-1]), int(b.vertex_offsets[-1])
+    edges_d = torch.from_numpy(b.edges).to(dev)
+    eo_h = torch.from_numpy(b.edge_offsets)
+    vo_h = torch.from_numpy(b.vertex_offsets)
+    eo_d, vo_d = eo_h.to(dev), vo_h.to(dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    eng = cc.Engine(id_bytes=4, device=local, profile=1)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 1)):
+        eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches, kms, kla = 0, {}, {}
+    e0.record(stream)
+    for _ in range(args.steps):
+        eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
+        st = eng.stats()
+        launches += st["launches"]
+        for k, v in st["kernel_ms"].items():
+            kms[k] = kms.get(k, 0.0) + v
+            kla[k] = kla.get(k, 0) + st["kernel_launches"][k]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = sampler.stop()
+    # the same graphs one cc_labels call at a time (each graph in its own aligned buffer)
+    per = [edges_d[b.edge_offsets[g]:b.edge_offsets[g + 1]].clone() for g in range(b.G)]
+    outs = [torch.empty(int(b.vertex_offsets[g + 1] - b.vertex_offsets[g]), dtype=torch.int32, device=dev)
+            for g in range(b.G)]
+    one = cc.Engine(id_bytes=4, device=local)
+    for g in range(b.G):
+        one.labels(per[g], outs[g].numel(), out=outs[g])
+    torch.cuda.synchronize(dev)
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    loops = max(1, min(args.steps, 2))
+    a.record(stream)
+    for _ in range(loops):
+        for g in range(b.G):
+            one.labels(per[g], outs[g].numel(), out=outs[g])
+    c.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_loop = a.elapsed_time(c) / loops
+    same = all(torch.equal(outs[g], out[b.vertex_offsets[g]:b.vertex_offsets[g + 1]]) for g in range(b.G))
+    if not same:
+        raise SystemExit("batched labels differ from the per-graph calls")
+    dom = max(kms, key=lambda k: kms[k])
+    kernels = {k: {"ms_per_step": kms[k] / args.steps, "launches_per_step": kla[k] / args.steps} for k in kms if kla[k]}
+    line = {"metric": METRIC + " [batched form]", "value": m / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "graphs": b.G, "n": n, "m": m,
+                       "graph": "log-uniform n_g in [1K, 1M], cycling R-MAT ef 8 / grid p=0.55 / chain forest",
+                       "l2": "inputs larger than L2 (no flush)"},
+            "vs_per_graph_loop": {"value": m / (ms_loop / 1e3), "ms_per_step": ms_loop,
+                                  "speedup": ms_loop / ms, "labels_identical": same},
+            "dominant_kernel": dom, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
+            "sv_iters": st["sv_iters"], "m_active": st["m_active"]}
+    print(json.dumps(line), flush=True)
+    eng.close()
+    one.close()
+    return 0
+
+
 def check_labels(torch, edges_d, lab, n):
     """Cheap device-side invariants of min-id labels (outside the timed region)."""
     l = lab.long()
@@ -248,6 +329,8 @@ def main() -> int:
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if WORKLOADS[args.workload]["kind"] == "batch":
+        return run_batch(args, world, rank, local)
 
     import torch
 

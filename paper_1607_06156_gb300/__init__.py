@@ -199,6 +199,15 @@ class Engine:
         _check(rc, "cc_labels_batched")
         return out
 
+    def labels_batched_dev(self, edges, eo_dev, vo_dev, eo_host, vo_host, out, stream=None):
+        """cc_labels_batched with offsets already on the device and on the host (no copies)."""
+        G = eo_host.numel() - 1
+        rc = lib().cc_labels_batched(self._h, edges.data_ptr() if edges.numel() else None, eo_dev.data_ptr(),
+                                     vo_dev.data_ptr(), eo_host.data_ptr(), vo_host.data_ptr(), G,
+                                     out.data_ptr() if out.numel() else None, _stream_handle(stream, edges.device))
+        _check(rc, "cc_labels_batched")
+        return out
+
     def degree_distribution(self, edges, n: int, hist_len: int = 0, stream=None):
         """(deg[n] uint32 as int32 tensor, hist[hist_len] uint64 as int64 tensor or None)."""
         import torch

@@ -398,6 +398,42 @@ cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStre
     return CC_OK;
 }
 
+// SV iterations over the compacted active list until no pair is active
+// (Section 3.1.4: completed partitions leave the working set). `src` holds
+// m_cur pairs in ebuf0; `it` is the last iteration run so far.
+cc_status sv_list_loop(cc_ctx *ctx, vid_t n, const void *src, unsigned long long m_cur, int it, int cap,
+                       cudaStream_t s) {
+    DevState *st = as<DevState>(ctx->st);
+    cc_stats &S = ctx->stats;
+    vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
+    uint2 *eb[2] = {as<uint2>(ctx->ebuf0), as<uint2>(ctx->ebuf1)};
+    int cur = 0;
+    while (m_cur > 0) {
+        it++;
+        if (it >= cap) {
+            S.sv_iters = it;
+            return CC_ERR_NO_CONVERGENCE;
+        }
+        if (it < CC_MAX_SV_ITERS_RECORDED) S.m_active[it] = (int64_t)m_cur;
+        {
+            Scope sc(ctx, CC_K_SV_GATHER_LIST, s, 1);
+            launch_sv_pass<uint32_t>(2, true, true, src, (long long)m_cur, n, parent, nullptr, 0, hooked, eb[1 - cur],
+                                     st, it, ctx->grid, s);
+        }
+        {
+            Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
+            launch_sv_shortcut(parent, hooked, st, it, ctx->grid, s);
+        }
+        cur = 1 - cur;
+        src = eb[cur];
+        CU_TRY(cudaMemcpyAsync(&ctx->h_st->kept[it], &st->kept[it], 8, cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaStreamSynchronize(s));
+        m_cur = ctx->h_st->kept[it];
+    }
+    S.sv_iters = it + 1;
+    return CC_OK;
+}
+
 template <typename T>
 cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void *labels_out, cudaStream_t s) {
     DevState *st = as<DevState>(ctx->st);
@@ -507,30 +543,7 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
             src = eb[0];
         }
     }
-    int cur = 0;
-    while (m_cur > 0) {
-        it++;
-        if (it >= cap) {
-            S.sv_iters = it;
-            return CC_ERR_NO_CONVERGENCE;
-        }
-        if (it < CC_MAX_SV_ITERS_RECORDED) S.m_active[it] = (int64_t)m_cur;
-        {
-            Scope sc(ctx, CC_K_SV_GATHER_LIST, s, 1);
-            launch_sv_pass<uint32_t>(2, true, true, src, (long long)m_cur, n, parent, nullptr, 0, hooked, eb[1 - cur],
-                                     st, it, ctx->grid, s);
-        }
-        {
-            Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
-            launch_sv_shortcut(parent, hooked, st, it, ctx->grid, s);
-        }
-        cur = 1 - cur;
-        src = eb[cur];
-        CU_TRY(cudaMemcpyAsync(&ctx->h_st->kept[it], &st->kept[it], 8, cudaMemcpyDeviceToHost, s));
-        CU_TRY(cudaStreamSynchronize(s));
-        m_cur = ctx->h_st->kept[it];
-    }
-    S.sv_iters = it + 1;
+    CC_TRY(sv_list_loop(ctx, n, src, m_cur, it, cap, s));
     rec(ctx, EV_SV, s);
     {
         Scope sc(ctx, CC_K_FINALIZE, s, 1);
@@ -670,9 +683,91 @@ cc_status cc_labels(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, vo
 cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *edge_offsets_dev,
                             const int64_t *vertex_offsets_dev, const int64_t *edge_offsets_host,
                             const int64_t *vertex_offsets_host, int G, void *labels_out_dev, void *stream) {
-    (void)ctx; (void)edges_dev; (void)edge_offsets_dev; (void)vertex_offsets_dev; (void)edge_offsets_host;
-    (void)vertex_offsets_host; (void)G; (void)labels_out_dev; (void)stream;
-    return CC_ERR_UNSUPPORTED;
+    if (!ctx || G < 0) return CC_ERR_INVALID_ARG;
+    if (G == 0) return CC_OK;
+    if (!edge_offsets_dev || !vertex_offsets_dev || !edge_offsets_host || !vertex_offsets_host)
+        return CC_ERR_INVALID_ARG;
+    if (edge_offsets_host[0] != 0 || vertex_offsets_host[0] != 0) return CC_ERR_INVALID_ARG;
+    for (int g = 0; g < G; g++)
+        if (edge_offsets_host[g + 1] < edge_offsets_host[g] || vertex_offsets_host[g + 1] < vertex_offsets_host[g])
+            return CC_ERR_INVALID_ARG;
+    const long long m = edge_offsets_host[G], n = vertex_offsets_host[G];
+    if (n >= (1LL << 31) || m >= (1LL << 31)) return CC_ERR_UNSUPPORTED;
+    for (int g = 0; g < G; g++)  // pairs in a graph without vertices cannot be valid
+        if (vertex_offsets_host[g + 1] == vertex_offsets_host[g] && edge_offsets_host[g + 1] > edge_offsets_host[g])
+            return CC_ERR_INVALID_EDGE;
+    if (n == 0) return CC_OK;
+    if (!labels_out_dev || (m > 0 && !edges_dev) || ((uintptr_t)edges_dev & 15)) return CC_ERR_INVALID_ARG;
+    CU_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    CC_TRY(ensure_sv(ctx, (size_t)n, (size_t)m));
+    DevState *st = as<DevState>(ctx->st);
+    cc_stats &S = ctx->stats;
+    memset(&S, 0, sizeof(S));
+    prof_reset(ctx);
+    for (int e = 0; e < EV_COUNT; e++) ctx->ev_used[e] = false;
+    S.n = n;
+    S.m = m;
+    S.route_source = 2;
+    CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+    rec(ctx, EV_START, s);
+    vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
+    const vid_t nt = (vid_t)n;
+    const int cap = ctx->opt.max_iters > 0 ? ctx->opt.max_iters : default_max_iters(n);
+    {
+        Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
+        launch_parent_init(parent, nt, nullptr, 0, ctx->grid, s);
+    }
+    unsigned long long m_cur = 0;
+    int it = 0;
+    if (m > 0) {
+        {
+            Scope sc(ctx, CC_K_SV_FIRST, s, 1);
+            launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,
+                                 hooked, nullptr, st, 0, ctx->grid, s);
+        }
+        {
+            Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
+            launch_shortcut_all(parent, nt, st, 0, ctx->grid, s);
+        }
+        S.m_active[0] = m;
+        it = 1;
+        {
+            Scope sc(ctx, CC_K_SV_GATHER_INPUT, s, 1);
+            launch_sv_pass_batch(2, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,
+                                 hooked, as<uint2>(ctx->ebuf0), st, 1, ctx->grid, s);
+        }
+        {
+            Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
+            launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, s);
+        }
+        S.m_active[1] = m;
+        CC_TRY(read_back(ctx, &st->err, 4, s));
+        if (ctx->h_st->err) {
+            ctx->last_status = device_error(ctx->h_st->err);
+            return ctx->last_status;
+        }
+        CC_TRY(read_back(ctx, &st->kept[1], 8, s));
+        m_cur = ctx->h_st->kept[1];
+    }
+    cc_status stt = sv_list_loop(ctx, nt, ctx->ebuf0.p, m_cur, it, cap, s);
+    if (stt == CC_OK) {
+        rec(ctx, EV_SV, s);
+        {
+            Scope sc(ctx, CC_K_FINALIZE, s, 1);
+            launch_finalize_batch(parent, nt, vertex_offsets_dev, G, (int32_t *)labels_out_dev, ctx->grid, s);
+        }
+        rec(ctx, EV_END, s);
+        CU_TRY(cudaMemcpyAsync(&ctx->h_st->err, &st->err, 4, cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaStreamSynchronize(s));
+        CU_TRY(cudaGetLastError());
+        prof_collect(ctx);
+        stt = device_error(ctx->h_st->err);
+    }
+    ctx->last_status = stt;
+    S.status = stt;
+    return stt;
 }
 
 cc_status cc_degree_distribution(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, uint32_t *deg_out_dev,

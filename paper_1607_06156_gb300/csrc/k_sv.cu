@@ -18,7 +18,9 @@
 //           atomicMin that sees the old value equal to the root itself).
 //  shortcut pointer jumping with path halving over the roots hooked in this
 //           iteration, so each of them points at the root at the end of the
-//           iteration (the paper's pointer doubling).
+//           iteration (the paper's pointer doubling); parent writes are
+//           atomicMin so concurrent chases cannot leave a vertex one level
+//           short of its root.
 //
 // Parents only ever decrease and always point at a smaller id, so the
 // structure stays a forest; trees only merge, so a dropped pair (equal
@@ -188,50 +190,42 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass(const T *__restrict__ in, lo
     if (bad) set_err(st, kErrInvalidEdge);
 }
 
-// Pointer jumping with path halving for every vertex (used after a pass that
-// did not record its hooks). Only shortcuts happen while it runs.
-__global__ void __launch_bounds__(kBlock) k_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it) {
-    for (long long v = gtid(); v < (long long)n; v += gstride()) {
-        vid_t y = parent[v];
-        if (y == (vid_t)v) continue;
-        while (true) {
-            const vid_t p = parent[y];
-            if (p == y) break;
-            const vid_t g = parent[p];
-            if (g == p) {
-                y = p;
-                break;
-            }
-            parent[y] = g;
-            y = g;
+// Chase from x to its root with path halving. No hook runs while a shortcut
+// kernel runs, so every value written is an ancestor of the vertex it is
+// written to; the writes are atomicMin, so a stale halving write of one
+// thread (a grandparent read before another thread pointed the vertex at
+// its root) can never undo a later, smaller value: the root is the smallest
+// ancestor, and a vertex set to its root stays there. After the kernel every
+// vertex it processed points at its root, which the next hook pass relies on
+// (its one-jump parent reads are then roots).
+__device__ __forceinline__ void shortcut_to_root(vid_t *parent, vid_t x) {
+    vid_t y = x;
+    while (true) {
+        const vid_t p = parent[y];
+        if (p == y) break;
+        const vid_t g = parent[p];
+        if (g == p) {
+            y = p;
+            break;
         }
-        parent[v] = y;
+        atomicMin(&parent[y], g);
+        y = g;
     }
+    if (y != x) atomicMin(&parent[x], y);
+}
+
+// Shortcut of every vertex (used after a pass that did not record its hooks).
+__global__ void __launch_bounds__(kBlock) k_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it) {
+    for (long long v = gtid(); v < (long long)n; v += gstride())
+        if (parent[v] != (vid_t)v) shortcut_to_root(parent, (vid_t)v);
     if (gtid() == 0) st->hook_base[it + 1] = st->hook_base[it] + st->hooked[it];
 }
 
-// Path-halving shortcut of the roots hooked in iteration `it`. Only
-// shortcuts happen while it runs (no hooks), so every write replaces a
-// parent by one of its ancestors and concurrent chases stay consistent.
+// Shortcut of the roots hooked in iteration `it`.
 __global__ void __launch_bounds__(kBlock) k_sv_shortcut(vid_t *parent, const vid_t *__restrict__ hooked_list,
                                                         DevState *st, int it) {
     const unsigned long long base = st->hook_base[it], cnt = st->hooked[it];
-    for (long long i = gtid(); i < (long long)cnt; i += gstride()) {
-        const vid_t x = hooked_list[base + i];
-        vid_t y = x;
-        while (true) {
-            const vid_t p = parent[y];
-            if (p == y) break;
-            const vid_t g = parent[p];
-            if (g == p) {
-                y = p;
-                break;
-            }
-            parent[y] = g;
-            y = g;
-        }
-        parent[x] = y;
-    }
+    for (long long i = gtid(); i < (long long)cnt; i += gstride()) shortcut_to_root(parent, hooked_list[base + i]);
     if (gtid() == 0) st->hook_base[it + 1] = base + cnt;
 }
 
@@ -273,6 +267,145 @@ __global__ void __launch_bounds__(kBlock) k_finalize(vid_t *parent, vid_t n, T *
         }
     }
     for (long long v = n4 * 4 + gtid(); v < (long long)n; v += gstride()) labels[v] = (T)find_root(parent, (vid_t)v);
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: G independent graphs as one disjoint union. Graph g owns
+// pairs [eo[g], eo[g+1]) with ids local to it and vertices [vo[g], vo[g+1])
+// of the union; the union's components are exactly the graphs' components,
+// and a component's minimum union id is vo[g] plus its minimum local id.
+
+// largest g in [0, G) with off[g] <= k (skips empty graphs)
+__device__ __forceinline__ int graph_search(const int64_t *off, int G, long long k) {
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int graph_advance(const int64_t *off, int G, long long k, int g) {
+    while (g + 1 < G && off[g + 1] <= k) g++;
+    return g;
+}
+
+template <int MODE, bool WRITE, bool RECORD>
+__global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restrict__ in, long long m,
+                                                          const int64_t *__restrict__ eo,
+                                                          const int64_t *__restrict__ vo, int G, vid_t ntot,
+                                                          vid_t *parent, vid_t *hooked_list, uint2 *__restrict__ out,
+                                                          DevState *st, int it) {
+    constexpr int U = 2, K = 2 * U;
+    __shared__ int sw[32];
+    __shared__ unsigned long long sbase;
+    __shared__ int sg;
+    const long long nvec = m / 2;
+    const int4 *ev = reinterpret_cast<const int4 *>(in);
+    const unsigned long long hbase = RECORD ? st->hook_base[it] : 0ull;
+    bool bad = false;
+    const long long tile = (long long)kBlock * U;
+    const long long ntiles = (nvec + tile - 1) / tile;
+    for (long long t = blockIdx.x; t < ntiles + ((m & 1) ? 1 : 0); t += gridDim.x) {
+        const long long k0 = t < ntiles ? t * tile * 2 : m - 1;  // first pair of the tile
+        if (threadIdx.x == 0) sg = graph_search(eo, G, k0);
+        __syncthreads();
+        const int g0 = sg;
+        long long u[K], v[K], k[K];
+        bool valid[K];
+        if (t < ntiles) {
+#pragma unroll
+            for (int r = 0; r < U; r++) {
+                const long long i = t * tile + (long long)r * kBlock + threadIdx.x;
+                const int4 q = i < nvec ? ld_stream(ev + i) : make_int4(0, 0, 0, 0);
+                u[2 * r] = q.x; v[2 * r] = q.y; k[2 * r] = 2 * i;
+                u[2 * r + 1] = q.z; v[2 * r + 1] = q.w; k[2 * r + 1] = 2 * i + 1;
+                valid[2 * r] = valid[2 * r + 1] = i < nvec;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < K; r++) {
+                u[r] = v[r] = 0;
+                k[r] = m - 1;
+                valid[r] = false;
+            }
+            if (threadIdx.x == 0) {
+                u[0] = in[2 * (m - 1)];
+                v[0] = in[2 * (m - 1) + 1];
+                valid[0] = true;
+            }
+        }
+        vid_t ru[K], rv[K];
+        bool keep[K], hk[K];
+#pragma unroll
+        for (int r = 0; r < K; r++) {
+            keep[r] = hk[r] = false;
+            if (!valid[r]) continue;
+            const int g = graph_advance(eo, G, k[r], g0);
+            const long long base = vo[g], ng = vo[g + 1] - base;
+            if (u[r] < 0 || v[r] < 0 || u[r] >= ng || v[r] >= ng) {
+                bad = true;
+                continue;
+            }
+            keep[r] = sv_pair<MODE, RECORD>(base + u[r], base + v[r], ntot, parent, nullptr, 0, ru[r], rv[r], hk[r],
+                                            bad);
+        }
+        if (WRITE) {
+            int c = 0;
+#pragma unroll
+            for (int r = 0; r < K; r++) c += keep[r];
+            unsigned long long o = block_reserve(&st->kept[it], c, sw, &sbase);
+#pragma unroll
+            for (int r = 0; r < K; r++)
+                if (keep[r]) out[o++] = make_uint2(ru[r], rv[r]);
+        }
+        if (RECORD) {
+            int c = 0;
+#pragma unroll
+            for (int r = 0; r < K; r++) c += hk[r];
+            unsigned long long o = block_reserve(&st->hooked[it], c, sw, &sbase);
+#pragma unroll
+            for (int r = 0; r < K; r++)
+                if (hk[r]) hooked_list[hbase + o++] = ru[r] > rv[r] ? ru[r] : rv[r];
+        }
+        __syncthreads();  // sg is rewritten by the next tile
+    }
+    if (bad) set_err(st, kErrInvalidEdge);
+}
+
+// labels[v] = root(v) - vo[g(v)]: the minimum local id of v's component
+__global__ void __launch_bounds__(kBlock) k_finalize_batch(vid_t *parent, vid_t ntot, const int64_t *__restrict__ vo,
+                                                           int G, int32_t *__restrict__ labels) {
+    __shared__ int sg;
+    const long long tile = kBlock;
+    const long long ntiles = ((long long)ntot + tile - 1) / tile;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (threadIdx.x == 0) sg = graph_search(vo, G, t * tile);
+        __syncthreads();
+        const long long v = t * tile + threadIdx.x;
+        if (v < (long long)ntot) {
+            const int g = graph_advance(vo, G, v, sg);
+            labels[v] = (int32_t)((long long)find_root(parent, (vid_t)v) - vo[g]);
+        }
+        __syncthreads();
+    }
+}
+
+void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
+                          vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
+                          cudaStream_t s) {
+    if (m <= 0) return;
+    if (mode == 0)
+        k_sv_pass_batch<0, false, false><<<grid, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it);
+    else
+        k_sv_pass_batch<2, true, true><<<grid, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it);
+}
+
+void launch_finalize_batch(vid_t *parent, vid_t ntot, const int64_t *vo, int G, int32_t *labels, int grid,
+                           cudaStream_t s) {
+    if (ntot == 0) return;
+    k_finalize_batch<<<grid, kBlock, 0, s>>>(parent, ntot, vo, G, labels);
 }
 
 // ---------------------------------------------------------------------------

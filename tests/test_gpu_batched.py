@@ -1,0 +1,91 @@
+"""Batched form: G independent graphs in one cc_labels_batched call.
+
+Each graph's labels are local (the minimum local id of each component) and
+must equal the oracle's labels of that graph alone, and the labels a loop of
+per-graph cc_labels calls gives.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from tests.gpu_util import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_batched(torch, edges, eoff, voff, **opts):
+    import paper_1607_06156_gb300 as cc
+
+    eng = cc.Engine(id_bytes=4, **opts)
+    out = eng.labels_batched(torch.from_numpy(np.ascontiguousarray(edges)).cuda(), torch.from_numpy(eoff),
+                             torch.from_numpy(voff))
+    torch.cuda.synchronize()
+    st = eng.stats()
+    eng.close()
+    return out.cpu().numpy().astype(np.int64), st
+
+
+def _check_each(b, got, graphs=None):
+    for g in (range(b.G) if graphs is None else graphs):
+        gr = b.graph(g)
+        want = oracle.cc_labels(gr.edges, gr.n)
+        have = got[b.vertex_offsets[g]:b.vertex_offsets[g + 1]]
+        bad = np.nonzero(have != want)[0]
+        assert bad.size == 0, (g, gr.n, gr.m, bad[:5])
+
+
+def test_mixed_batch_matches_oracle_per_graph():
+    torch = torch_cuda()
+    b = gg.batch(seed=3, G=90, nmin=1000, nmax=60000)
+    got, st = _run_batched(torch, b.edges, b.edge_offsets, b.vertex_offsets)
+    _check_each(b, got)
+    assert st["sv_iters"] >= 2
+
+
+def test_batched_equals_per_graph_loop():
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    b = gg.batch(seed=4, G=24, nmin=2000, nmax=200000)
+    got, _ = _run_batched(torch, b.edges, b.edge_offsets, b.vertex_offsets)
+    eng = cc.Engine(id_bytes=4)
+    for g in range(b.G):
+        gr = b.graph(g)
+        one = eng.labels(torch.from_numpy(np.ascontiguousarray(gr.edges)).cuda(), gr.n).cpu().numpy()
+        assert np.array_equal(one, got[b.vertex_offsets[g]:b.vertex_offsets[g + 1]])
+    eng.close()
+
+
+def test_empty_tiny_and_ragged_graphs():
+    torch = torch_cuda()
+    rng = np.random.default_rng(5)
+    sizes = [1, 5, 1000, 1, 3, 777, 2, 40000, 1]
+    pairs = [0, 2, 3001, 0, 3, 1555, 1, 80001, 0]  # odd total; some graphs without pairs
+    parts = [rng.integers(0, n, size=(k, 2)) for n, k in zip(sizes, pairs)]
+    edges = np.concatenate(parts).astype(np.int32)
+    eoff = np.concatenate([[0], np.cumsum(pairs)]).astype(np.int64)
+    voff = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    got, _ = _run_batched(torch, edges, eoff, voff)
+    for g, (n, p) in enumerate(zip(sizes, parts)):
+        want = oracle.cc_labels(p.astype(np.int32), n)
+        assert np.array_equal(got[voff[g]:voff[g + 1]], want), g
+
+
+def test_local_id_out_of_its_graph_is_rejected():
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    edges = np.array([[0, 1], [1, 2], [0, 3]], dtype=np.int32)  # graph 1 has 3 vertices: id 3 is invalid there
+    eoff = np.array([0, 1, 3], dtype=np.int64)
+    voff = np.array([0, 10, 13], dtype=np.int64)
+    with pytest.raises(cc.CCError) as ei:
+        _run_batched(torch, edges, eoff, voff)
+    assert ei.value.status == 2
+
+
+def test_single_graph_batch_equals_cc_labels():
+    torch = torch_cuda()
+    g = gg.rmat(seed=6, scale=16, edge_factor=8)
+    got, _ = _run_batched(torch, g.edges, np.array([0, g.m], np.int64), np.array([0, g.n], np.int64))
+    assert np.array_equal(got, oracle.cc_labels(g.edges, g.n))

@@ -57,3 +57,28 @@ def test_grid_chains_full_size():
     assert bad.size == 0, (bad[:10], st)
     # every chain is its own component
     assert np.unique(want).size >= 10_000_000
+
+
+def test_batch4096_full_size():
+    """The 4,096-graph batch: sampled graphs against the oracle, every graph
+    against the label invariants (edge ends share a label, label <= id,
+    labels are fixed points)."""
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    b = gg.batch(seed=1, G=4096, nmin=1000, nmax=1_000_000)
+    eng = cc.Engine(id_bytes=4)
+    out = eng.labels_batched(torch.from_numpy(b.edges).cuda(), torch.from_numpy(b.edge_offsets),
+                             torch.from_numpy(b.vertex_offsets))
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    eng.close()
+    rng = np.random.default_rng(0)
+    sample = set(rng.choice(b.G, 24, replace=False).tolist()) | {0, 1, 2, b.G - 1}
+    for g in range(b.G):
+        lab = got[b.vertex_offsets[g]:b.vertex_offsets[g + 1]].astype(np.int64)
+        e = b.edges[b.edge_offsets[g]:b.edge_offsets[g + 1]]
+        assert (lab[e[:, 0]] == lab[e[:, 1]]).all(), g
+        assert (lab <= np.arange(lab.size)).all() and (lab[lab] == lab).all(), g
+        if g in sample:
+            assert np.array_equal(lab, oracle.cc_labels(e, lab.size)), g

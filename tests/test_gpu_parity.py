@@ -269,3 +269,11 @@ def test_partitioned_paths_many_vertex_blocks():
     rng = np.random.default_rng(8)
     e = rng.integers(0, n, size=((1 << 21) + 1, 2)).astype(np.int32)
     assert_labels_match(e, n, routes=("bfs",))
+
+
+@pytest.mark.parametrize("seed", list(range(12)))
+def test_stress_many_chains_sv(seed):
+    """Many short chains plus a percolated grid, forced SV: deep hook chains in
+    one iteration make concurrent shortcuts race; labels must stay exact."""
+    g = gg.grid_chains(seed=100 + seed, W=700, p=0.55, nchains=150_000, id_bytes=4)
+    assert_labels_match(g.edges, g.n, routes=("sv",))
