@@ -85,7 +85,10 @@ typedef struct {
     int fault_inject;       /* CC_FAULT_* bits */
     double ks_min_span;     /* a candidate tail must reach max degree >= ks_min_span * xmin; default 10 */
     int profile;            /* 1: time every kernel class with CUDA events (cc_stats.kernel_ms) */
-    int reserved[3];
+    int bfs_mode;           /* BFS engine: 0 = direction-optimizing BFS on a CSR (default),
+                               1 = edge-list BFS (each level one pass over the active pairs, no CSR);
+                               the learned route always uses 1 */
+    int reserved[2];
 } cc_options;
 
 /* Kernel classes reported in cc_stats.kernel_ms / kernel_launches. */
@@ -104,6 +107,7 @@ enum {
     CC_K_SV_GATHER_LIST = 11,  /* SV pass over the compacted active list */
     CC_K_SV_SHORTCUT = 12,
     CC_K_FINALIZE = 13,
+    CC_K_PREDICT = 14,      /* sampled route features + network inference */
     CC_K_COUNT = 16
 };
 
@@ -134,6 +138,10 @@ typedef struct {
     float kernel_ms[CC_K_COUNT];        /* summed device time per kernel class (options.profile = 1) */
     int32_t kernel_launches[CC_K_COUNT];/* launches per kernel class (options.profile = 1) */
     int64_t sv_hooks[CC_MAX_SV_ITERS_RECORDED]; /* roots hooked in each SV iteration */
+    float pred_confidence;              /* learned policy: probability of the predicted route */
+    int pred_route;                     /* learned policy: predicted route (-1 if none) */
+    int pred_cutoff;                    /* learned policy: predicted BFS cutoff (0 = none) */
+    float ms_features;                  /* learned policy: device time of features + inference */
 } cc_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -199,6 +207,67 @@ cc_status cc_degree_distribution(cc_ctx *ctx, const void *edges_dev, int64_t n, 
  * Synchronises `stream`.
  */
 cc_status cc_ks_statistic(cc_ctx *ctx, const uint64_t *hist_dev, int64_t hist_len, double *out_host, void *stream);
+
+/*
+ * Learned route predictor (the learned form of the route choice of Section
+ * 3.2: it replaces the K-S threshold only in choosing BFS first vs SV only
+ * and the BFS cutoff; labels never depend on it).
+ *
+ * Network 69 -> 128 (ReLU) -> 128 (ReLU) -> 3, parameters in one fp32 array
+ * of CC_MLP_PARAMS floats: [W1 (128 x 69, row-major) | b1 (128) |
+ * W2 (128 x 128) | b2 (128) | W3 (3 x 128) | b3 (3)]. Outputs: two route
+ * logits (0 = SV only, 1 = BFS first) and the natural log of the BFS cutoff
+ * in levels. Features (see cc_route_features) are CC_MLP_IN floats.
+ */
+#define CC_MLP_IN 69
+#define CC_MLP_HIDDEN 128
+#define CC_MLP_OUT 3
+#define CC_MLP_PARAMS (128 * 69 + 128 + 128 * 128 + 128 + 3 * 128 + 3)
+
+/*
+ * Route features of a graph, computed on the device from samples:
+ *   [0, 64)  log2-degree histogram (bucket 0: degree 0, bucket b: degrees in
+ *            [2^(b-1), 2^b)) of the vertices whose id is a multiple of 16, as
+ *            fractions of those vertices
+ *   64, 65   ln(n) / 20, ln(m + 1) / 20
+ *   66..68   ln(1 + vertices reached) / 20 at BFS levels 1, 2, 3 from the
+ *            sampled vertex of highest degree, over the pairs of every 16th
+ *            block of 256 pairs
+ *   edges_dev, n, m as in cc_labels; feat_out_dev [CC_MLP_IN] floats (device).
+ * Enqueued on `stream`; returns CC_ERR_INVALID_EDGE (after synchronising) for
+ * an id outside [0, n).
+ */
+cc_status cc_route_features(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, float *feat_out_dev,
+                            void *stream);
+
+/*
+ * Installs predictor parameters (host, CC_MLP_PARAMS floats) into the
+ * context, converted to bf16 weights with fp32 biases for inference. With
+ * route_policy CC_ROUTE_LEARNED, cc_labels then computes the features,
+ * runs the network, and takes its route (and cutoff) when the predicted
+ * route's softmax probability is at least min_confidence; otherwise the K-S
+ * heuristic decides. params_host == NULL removes the predictor (the learned
+ * policy then falls back to the heuristic on every call).
+ */
+cc_status cc_set_predictor(cc_ctx *ctx, const float *params_host, double min_confidence);
+
+/*
+ * Training kernels (fp32), all device pointers, nothing allocated:
+ *   cc_mlp_forward:  X [B][CC_MLP_IN] -> act [B * (2 * CC_MLP_HIDDEN + CC_MLP_OUT)]
+ *                    = [H1 (B x 128) | H2 (B x 128) | O (B x 3)]
+ *   cc_mlp_backward: gradients of the batch-mean loss
+ *                    CE(O[:, 0:2], y) + lambda * w * (O[:, 2] - t)^2
+ *                    into grad [CC_MLP_PARAMS]; scratch holds
+ *                    B * (3 + 2 * CC_MLP_HIDDEN) floats; the batch loss is
+ *                    added into *loss_dev (one float)
+ *   cc_mlp_adam:     one Adam step (step t >= 1, bias-corrected) on count floats
+ */
+cc_status cc_mlp_forward(const float *params_dev, const float *X_dev, int B, float *act_dev, void *stream);
+cc_status cc_mlp_backward(const float *params_dev, const float *X_dev, const int *y_dev, const float *t_dev,
+                          const float *w_dev, int B, float lambda, const float *act_dev, float *grad_dev,
+                          float *scratch_dev, float *loss_dev, void *stream);
+cc_status cc_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int count, float lr,
+                      float beta1, float beta2, float eps, int t, void *stream);
 
 /* Size limits of cc_labels_static: its scratch is compiled into the library. */
 #define CC_STATIC_MAX_VERTICES (1 << 20)

@@ -102,3 +102,46 @@ def predict(p: dict, X: np.ndarray) -> tuple[np.ndarray, np.ndarray, np.ndarray]
     sm = e / e.sum(axis=1, keepdims=True)
     r = sm.argmax(axis=1)
     return r, sm[np.arange(len(r)), r], o[:, 2]
+
+
+def route_features(edges: np.ndarray, n: int) -> np.ndarray:
+    """The predictor's 69 input features, by their plain definition.
+
+    [0, 64)  log2-degree histogram (bucket 0: degree 0, bucket b: degrees in
+             [2^(b-1), 2^b)) of the vertices whose id is a multiple of 16, as
+             fractions of those vertices (degrees count both pair ends)
+    64, 65   ln(n)/20, ln(m+1)/20
+    66..68   ln(1 + new vertices)/20 at BFS levels 1..3 from the sampled
+             vertex of highest degree (ties: smallest id), over the pairs in
+             every 16th block of 256 pairs (pair k is used iff (k // 256) % 16 == 0)
+    """
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    m = e.shape[0]
+    deg = np.bincount(e.ravel(), minlength=n)[:n] if m else np.zeros(n, dtype=np.int64)
+    sampled = np.arange(0, n, 16)
+    sd = deg[sampled]
+    x = np.zeros(IN, dtype=np.float64)
+    buckets = np.where(sd == 0, 0, np.floor(np.log2(np.maximum(sd, 1))).astype(np.int64) + 1)
+    buckets = np.minimum(buckets, 63)
+    x[:64] = np.bincount(buckets, minlength=64)[:64] / sampled.size
+    x[64] = np.log(n) / 20.0
+    x[65] = np.log(m + 1.0) / 20.0
+    seed = int(sampled[int(np.argmax(sd))]) if sampled.size else 0
+    k = np.arange(m)
+    sp = e[(k // 256) % 16 == 0]
+    adj = {}
+    for u, v in sp.tolist():
+        adj.setdefault(u, []).append(v)
+        adj.setdefault(v, []).append(u)
+    visited = {seed}
+    front = {seed}
+    for level in range(3):
+        nxt = set()
+        for u in front:
+            for v in adj.get(u, ()):
+                if v not in visited:
+                    visited.add(v)
+                    nxt.add(v)
+        x[66 + level] = np.log1p(len(nxt)) / 20.0
+        front = nxt
+    return x

@@ -28,7 +28,9 @@ MAX_SV_ITERS_RECORDED = 64
 K_COUNT = 16
 # kernel classes of cc_stats.kernel_ms (CC_K_* in the header)
 KERNELS = ["degree", "hist", "ks", "scan", "csr", "bfs_topdown", "bfs_bottomup", "bfs_aux", "parent_init",
-           "sv_first", "sv_gather_input", "sv_gather_list", "sv_shortcut", "finalize"]
+           "sv_first", "sv_gather_input", "sv_gather_list", "sv_shortcut", "finalize", "predict"]
+MLP_IN, MLP_HIDDEN, MLP_OUT = 69, 128, 3
+MLP_PARAMS = 128 * 69 + 128 + 128 * 128 + 128 + 3 * 128 + 3
 
 
 class CCError(RuntimeError):
@@ -42,7 +44,8 @@ class Options(ctypes.Structure):
         ("id_bytes", ctypes.c_int), ("route_policy", ctypes.c_int), ("ks_tau", ctypes.c_double),
         ("ks_min_tail", ctypes.c_int), ("ks_min_distinct", ctypes.c_int), ("max_iters", ctypes.c_int),
         ("bfs_cutoff_levels", ctypes.c_int), ("debug_checks", ctypes.c_int), ("fault_inject", ctypes.c_int),
-        ("ks_min_span", ctypes.c_double), ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 3),
+        ("ks_min_span", ctypes.c_double), ("profile", ctypes.c_int), ("bfs_mode", ctypes.c_int),
+        ("reserved", ctypes.c_int * 2),
     ]
 
 
@@ -60,6 +63,8 @@ class Stats(ctypes.Structure):
         ("ms_total", ctypes.c_float), ("pad1", ctypes.c_float), ("launches", ctypes.c_int64),
         ("kernel_ms", ctypes.c_float * K_COUNT), ("kernel_launches", ctypes.c_int32 * K_COUNT),
         ("sv_hooks", ctypes.c_int64 * MAX_SV_ITERS_RECORDED),
+        ("pred_confidence", ctypes.c_float), ("pred_route", ctypes.c_int), ("pred_cutoff", ctypes.c_int),
+        ("ms_features", ctypes.c_float),
     ]
 
     def as_dict(self) -> dict:
@@ -94,11 +99,18 @@ def lib() -> ctypes.CDLL:
         L.cc_ks_statistic.argtypes = [_vp, _vp, _i64, _vp, _vp]
         L.cc_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
         L.cc_labels_static.argtypes = [_vp, _int, _i64, _i64, _vp, _vp]
+        L.cc_route_features.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp]
+        L.cc_set_predictor.argtypes = [_vp, _vp, ctypes.c_double]
+        L.cc_mlp_forward.argtypes = [_vp, _vp, _int, _vp, _vp]
+        L.cc_mlp_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _int, ctypes.c_float, _vp, _vp, _vp, _vp, _vp]
+        L.cc_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, _int, _vp]
         L.cc_strerror.argtypes = [_int]
         L.cc_strerror.restype = ctypes.c_char_p
         for f in ("cc_default_options", "cc_create", "cc_set_options", "cc_destroy", "cc_labels",
                   "cc_labels_batched", "cc_degree_distribution", "cc_ks_statistic", "cc_get_stats",
-                  "cc_labels_static"):
+                  "cc_labels_static", "cc_route_features", "cc_set_predictor", "cc_mlp_forward",
+                  "cc_mlp_backward", "cc_mlp_adam"):
             getattr(L, f).restype = _int
         _lib = L
     return _lib
@@ -228,10 +240,53 @@ class Engine:
         _check(rc, "cc_ks_statistic")
         return {"D": out[0], "alpha": out[1], "xmin": int(out[2]), "ntail": int(out[3]), "ncand": int(out[4])}
 
+    def route_features(self, edges, n: int, stream=None):
+        """The predictor's CC_MLP_IN features of a device edge tensor (float32 tensor on its device)."""
+        import torch
+
+        m = edges.shape[0] if edges.numel() else 0
+        x = torch.empty(MLP_IN, dtype=torch.float32, device=edges.device)
+        rc = lib().cc_route_features(self._h, edges.data_ptr() if m else None, n, m, x.data_ptr(),
+                                     _stream_handle(stream, edges.device))
+        _check(rc, "cc_route_features")
+        return x
+
+    def set_predictor(self, params, min_confidence: float = 0.75):
+        """Installs fp32 predictor parameters (MLP_PARAMS floats) for route='learned'; None removes it."""
+        import numpy as np
+
+        if params is None:
+            _check(lib().cc_set_predictor(self._h, None, min_confidence), "cc_set_predictor")
+            return
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MLP_PARAMS:
+            raise ValueError(f"expected {MLP_PARAMS} parameters, got {p.size}")
+        _check(lib().cc_set_predictor(self._h, p.ctypes.data_as(ctypes.c_void_p), min_confidence),
+               "cc_set_predictor")
+
     def stats(self) -> dict:
         s = Stats()
         lib().cc_get_stats(self._h, ctypes.byref(s))
         return s.as_dict()
+
+
+def mlp_forward(params, X, act, stream=None):
+    """cc_mlp_forward on device float32 tensors; act holds B * (2*128 + 3) floats."""
+    _check(lib().cc_mlp_forward(params.data_ptr(), X.data_ptr(), X.shape[0], act.data_ptr(),
+                                _stream_handle(stream, X.device)), "cc_mlp_forward")
+
+
+def mlp_backward(params, X, y, t, w, lam, act, grad, scratch, loss, stream=None):
+    """cc_mlp_backward on device tensors (y int32, others float32); adds the batch loss into loss[0]."""
+    _check(lib().cc_mlp_backward(params.data_ptr(), X.data_ptr(), y.data_ptr(), t.data_ptr(), w.data_ptr(),
+                                 X.shape[0], lam, act.data_ptr(), grad.data_ptr(), scratch.data_ptr(),
+                                 loss.data_ptr(), _stream_handle(stream, X.device)), "cc_mlp_backward")
+
+
+def mlp_adam(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """cc_mlp_adam on device float32 tensors (step >= 1)."""
+    _check(lib().cc_mlp_adam(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), params.numel(), lr,
+                             beta1, beta2, eps, step, _stream_handle(stream, params.device)), "cc_mlp_adam")
 
 
 STATIC_MAX_VERTICES = 1 << 20

@@ -41,6 +41,11 @@ struct cc_ctx {
     // BFS workspace
     size_t bn_cap = 0, bm_cap = 0;
     Buf row_ptr, col, vis, fb, nb, q0, q1, dq, off, tsum, counters, csr_entries;
+    // learned route predictor
+    size_t f_cap = 0;
+    Buf f_sdeg, f_counts, f_vis, f_f0, f_f1, f_x, pred_wb, pred_bias, pred_tmp;
+    bool have_pred = false;
+    double pred_min_conf = 0.75;
     // host side
     DevState *h_st = nullptr;  // pinned mirror of the device state
     cudaEvent_t ev[EV_COUNT] = {};
@@ -135,6 +140,7 @@ cc_status ensure_sv(cc_ctx *ctx, size_t n, size_t m) {
     CC_TRY(buf_reserve(ctx, ctx->chunk_nz, (size_t)(ks_num_chunks() + 1) * 8));
     CC_TRY(buf_reserve(ctx, ctx->chunk_mass, (size_t)(ks_num_chunks() + 1) * 8));
     CC_TRY(buf_reserve(ctx, ctx->st, sizeof(DevState)));
+    CC_TRY(buf_reserve(ctx, ctx->counters, 64 * 8));  // both BFS engines count visited vertices here
     CC_TRY(buf_reserve(ctx, ctx->bk_count, (size_t)ctx->grid * (bucket_max() + 2) * 4));
     CC_TRY(buf_reserve(ctx, ctx->bk_cursor, (size_t)ctx->grid * (bucket_max() + 2) * 4));
     CC_TRY(buf_reserve(ctx, ctx->bk_off, (size_t)(bucket_max() + 2) * 8));
@@ -157,7 +163,6 @@ cc_status ensure_bfs(cc_ctx *ctx, size_t n, size_t m) {
     CC_TRY(buf_reserve(ctx, ctx->dq, (N + 4) * 4));
     CC_TRY(buf_reserve(ctx, ctx->off, (N + 8) * 4));
     CC_TRY(buf_reserve(ctx, ctx->tsum, (size_t)(scan_num_tiles((long long)N + 2) + 4) * 8));
-    CC_TRY(buf_reserve(ctx, ctx->counters, 64 * 8));
     if (bucketed_ok(N, M)) CC_TRY(buf_reserve(ctx, ctx->csr_entries, (2 * M + 4) * 8));
     ctx->bn_cap = N;
     ctx->bm_cap = M;
@@ -169,6 +174,25 @@ P *as(const Buf &b) {
     return reinterpret_cast<P *>(b.p);
 }
 
+cc_status ensure_feat(cc_ctx *ctx, size_t n) {
+    if (n <= ctx->f_cap && ctx->f_x.p) return CC_OK;
+    const size_t N = n > ctx->f_cap ? n : ctx->f_cap;
+    const size_t words = (N + 31) / 32 + 4;
+    CC_TRY(buf_reserve(ctx, ctx->f_sdeg, ((N + 15) / 16 + 4) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->f_counts, 64 * 4));
+    CC_TRY(buf_reserve(ctx, ctx->f_vis, words * 4));
+    CC_TRY(buf_reserve(ctx, ctx->f_f0, words * 4));
+    CC_TRY(buf_reserve(ctx, ctx->f_f1, words * 4));
+    CC_TRY(buf_reserve(ctx, ctx->f_x, 128 * 4));
+    ctx->f_cap = N;
+    return CC_OK;
+}
+
+FeatScratch feat_scratch(cc_ctx *ctx) {
+    return FeatScratch{as<uint32_t>(ctx->f_sdeg), as<unsigned>(ctx->f_counts), as<uint32_t>(ctx->f_vis),
+                       as<uint32_t>(ctx->f_f0), as<uint32_t>(ctx->f_f1)};
+}
+
 cc_status check_options(const cc_options *o) {
     if (o->id_bytes != 4 && o->id_bytes != 8) return CC_ERR_INVALID_ARG;
     if (o->route_policy < CC_ROUTE_AUTO || o->route_policy > CC_ROUTE_FORCE_SV) return CC_ERR_INVALID_ARG;
@@ -177,6 +201,7 @@ cc_status check_options(const cc_options *o) {
         !(o->ks_min_span >= 0.0))
         return CC_ERR_INVALID_ARG;
     if (o->max_iters > kMaxIters - 1) return CC_ERR_INVALID_ARG;
+    if (o->bfs_mode < 0 || o->bfs_mode > 1) return CC_ERR_INVALID_ARG;
     return CC_OK;
 }
 
@@ -266,6 +291,16 @@ BucketScratch bucket_scratch(cc_ctx *ctx) {
     return BucketScratch{as<uint32_t>(ctx->bk_count), as<uint32_t>(ctx->bk_cursor), as<unsigned long long>(ctx->bk_off)};
 }
 
+float ev_ms(cc_ctx *ctx, Ev a, Ev b) {
+    if (!ctx->ev_used[a] || !ctx->ev_used[b]) return 0.0f;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0f;
+    }
+    return ms;
+}
+
 // Degree pass + histogram (Algorithm 2 line 1).
 template <typename T>
 void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s) {
@@ -295,7 +330,7 @@ void enqueue_ks(cc_ctx *ctx, cudaStream_t s) {
 // CSR + direction-optimizing BFS from the max-degree vertex. Returns the
 // number of levels run; leaves the visited bitmap in ctx->vis and cmin in DevState.
 template <typename T>
-cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s, int *levels_out) {
+cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s, int cutoff, int *levels_out) {
     DevState *st = as<DevState>(ctx->st);
     uint32_t *row_ptr = as<uint32_t>(ctx->row_ptr), *deg = as<uint32_t>(ctx->deg);
     vid_t *col = as<vid_t>(ctx->col);
@@ -334,7 +369,6 @@ cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStre
     CC_TRY(read_back(ctx, &st->front_edges[0], 8, s));
     fe = ctx->h_st->front_edges[0];
     int level = 0;
-    const int cutoff = ctx->opt.bfs_cutoff_levels;
     unsigned long long *cnt = as<unsigned long long>(ctx->counters);
     while (f > 0 && level < kMaxLevels - 1) {
         if (cutoff > 0 && level >= cutoff) break;
@@ -400,14 +434,13 @@ cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStre
 
 // SV iterations over the compacted active list until no pair is active
 // (Section 3.1.4: completed partitions leave the working set). `src` holds
-// m_cur pairs in ebuf0; `it` is the last iteration run so far.
+// m_cur pairs in ebuf[cur]; `it` is the last iteration run so far.
 cc_status sv_list_loop(cc_ctx *ctx, vid_t n, const void *src, unsigned long long m_cur, int it, int cap,
-                       cudaStream_t s) {
+                       cudaStream_t s, int cur = 0) {
     DevState *st = as<DevState>(ctx->st);
     cc_stats &S = ctx->stats;
     vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
     uint2 *eb[2] = {as<uint2>(ctx->ebuf0), as<uint2>(ctx->ebuf1)};
-    int cur = 0;
     while (m_cur > 0) {
         it++;
         if (it >= cap) {
@@ -434,6 +467,67 @@ cc_status sv_list_loop(cc_ctx *ctx, vid_t n, const void *src, unsigned long long
     return CC_OK;
 }
 
+// Edge-list BFS from the vertex named by *key (Algorithm 2 lines 6-9 without
+// a CSR). On return the visited set is in ctx->f_vis, cmin in DevState, and
+// the pairs still active (those without both ends visited) are either the
+// caller's pairs (*list_buf < 0) or the compacted list in ebuf[*list_buf]
+// with *list_len pairs.
+template <typename T>
+cc_status run_bfs_edges(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s, int cutoff,
+                        const unsigned long long *key, int *levels_out, int *list_buf, unsigned long long *list_len) {
+    DevState *st = as<DevState>(ctx->st);
+    CC_TRY(ensure_feat(ctx, n));
+    if (!ctx->counters.p || !ctx->f_vis.p || !ctx->ebuf0.p || !ctx->ebuf1.p) return CC_ERR_CUDA;
+    const long long nwords = ((long long)n + 31) / 32;
+    uint32_t *vis = as<uint32_t>(ctx->f_vis), *cur = as<uint32_t>(ctx->f_f0), *next = as<uint32_t>(ctx->f_f1);
+    uint2 *eb[2] = {as<uint2>(ctx->ebuf0), as<uint2>(ctx->ebuf1)};
+    cudaMemsetAsync(vis, 0, (size_t)nwords * 4, s);
+    cudaMemsetAsync(cur, 0, (size_t)nwords * 4, s);
+    {
+        Scope sc(ctx, CC_K_BFS_AUX, s, 1);
+        launch_edge_bfs_seed(vis, cur, n, key, st, s);
+    }
+    const void *src = edges;
+    unsigned long long len = (unsigned long long)m, kept_prev = (unsigned long long)m;
+    int buf = -1, level = 0;
+    while (level < kMaxLevels - 1 && (cutoff <= 0 || level < cutoff)) {
+        cudaMemsetAsync(next, 0, (size_t)nwords * 4, s);
+        // compact once the surviving pairs fall to 70% of the active list
+        const bool write = level >= 1 && (double)kept_prev <= 0.7 * (double)len;
+        const int ob = buf == 0 ? 1 : 0;
+        {
+            Scope sc(ctx, CC_K_BFS_BOTTOMUP, s, 1);
+            if (buf < 0) launch_bfs_edges<T>(write, src, (long long)len, n, vis, cur, next, eb[ob], st, level, ctx->grid, s);
+            else
+                launch_bfs_edges<uint32_t>(write, src, (long long)len, n, vis, cur, next, eb[ob], st, level, ctx->grid,
+                                           s);
+        }
+        CU_TRY(cudaMemcpyAsync(&ctx->h_st->front[level + 1], &st->front[level + 1], 8, cudaMemcpyDeviceToHost, s));
+        CC_TRY(read_back(ctx, &st->front_edges[level + 1], 8, s));
+        const unsigned long long claimed = ctx->h_st->front[level + 1], kept = ctx->h_st->front_edges[level + 1];
+        if (write) {
+            src = eb[ob];
+            len = kept;
+            buf = ob;
+        }
+        kept_prev = kept;
+        uint32_t *t = cur;
+        cur = next;
+        next = t;
+        level++;
+        if (claimed == 0) break;
+    }
+    *levels_out = level;
+    *list_buf = buf;
+    *list_len = len;
+    unsigned long long *cnt = as<unsigned long long>(ctx->counters);
+    cudaMemsetAsync(cnt + 1, 0, 8, s);
+    Scope sc(ctx, CC_K_BFS_AUX, s, 2);
+    launch_popcount(vis, nwords, cnt + 1, ctx->grid, s);
+    launch_first_visited(vis, nwords, st, ctx->grid, s);
+    return CC_OK;
+}
+
 template <typename T>
 cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void *labels_out, cudaStream_t s) {
     DevState *st = as<DevState>(ctx->st);
@@ -449,7 +543,35 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     int route = 0;
     S.route_source = policy == CC_ROUTE_AUTO || policy == CC_ROUTE_LEARNED ? 0 : 2;
     vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
-    if (policy != CC_ROUTE_FORCE_SV && m > 0) {
+    int cutoff = ctx->opt.bfs_cutoff_levels;
+    // Learned route: sampled features + network; a confident prediction skips
+    // the exact degree pass and the K-S fit (its BFS is the edge-list BFS,
+    // seeded at the sampled hub).
+    bool learned = false;
+    S.pred_route = -1;
+    if (policy == CC_ROUTE_LEARNED && ctx->have_pred && m > 0) {
+        CC_TRY(ensure_feat(ctx, n));
+        {
+            Scope sc(ctx, CC_K_PREDICT, s, 12);
+            launch_route_features<T>(edges, m, n, feat_scratch(ctx), st, as<float>(ctx->f_x), ctx->grid, s);
+            mlp_infer(as<__nv_bfloat16>(ctx->pred_wb), as<float>(ctx->pred_bias), as<float>(ctx->f_x), st, s);
+        }
+        rec(ctx, EV_DEGREE, s);
+        CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, kept), cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaStreamSynchronize(s));
+        if (ctx->h_st->err) return device_error(ctx->h_st->err);
+        S.pred_route = ctx->h_st->pred_route;
+        S.pred_confidence = ctx->h_st->pred_conf;
+        S.pred_cutoff = ctx->h_st->pred_cutoff;
+        S.ms_features = ev_ms(ctx, EV_START, EV_DEGREE);
+        if (ctx->h_st->pred_conf >= ctx->pred_min_conf) {
+            learned = true;
+            route = ctx->h_st->pred_route;
+            if (route == 1 && cutoff == 0) cutoff = ctx->h_st->pred_cutoff;
+            S.route_source = 1;
+        }
+    }
+    if (!learned && policy != CC_ROUTE_FORCE_SV && m > 0) {
         enqueue_degree<T>(ctx, edges, n, m, s);
         rec(ctx, EV_DEGREE, s);
         if (policy != CC_ROUTE_FORCE_BFS) enqueue_ks(ctx, s);
@@ -467,20 +589,32 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         S.seed_vertex = (int64_t)(0xffffffffu - (uint32_t)(ctx->h_st->maxkey & 0xffffffffu));
         if (policy == CC_ROUTE_FORCE_BFS) S.ks_d = 0.0;
     }
-    // the CSR uses 32-bit offsets: the BFS step needs 2m < 2^32
-    if (route == 1 && 2ull * (unsigned long long)m >= 0xffffffffull) route = 0;
+    // the learned route always takes the edge-list BFS (it needs no exact
+    // degrees); the CSR uses 32-bit offsets, so the CSR BFS needs 2m < 2^32
+    const bool edge_bfs = learned || ctx->opt.bfs_mode == 1;
+    if (route == 1 && !edge_bfs && 2ull * (unsigned long long)m >= 0xffffffffull) route = 0;
     S.route = route;
     const int cap = ctx->opt.fault_inject & CC_FAULT_ITER_CAP ? 1
                     : ctx->opt.max_iters > 0                  ? ctx->opt.max_iters
                                                               : default_max_iters(n);
     uint2 *eb[2] = {as<uint2>(ctx->ebuf0), as<uint2>(ctx->ebuf1)};
-    int it = 0;
+    int it = 0, cur0 = 0;
     unsigned long long m_cur = 0;
     const void *src = nullptr;
     if (route == 1) {
-        CC_TRY(ensure_bfs(ctx, n, (size_t)m));
-        int levels = 0;
-        CC_TRY(run_bfs<T>(ctx, edges, n, m, s, &levels));
+        int levels = 0, list_buf = -1;
+        unsigned long long list_len = (unsigned long long)m;
+        const uint32_t *vis = nullptr;
+        if (edge_bfs) {
+            // seed: the exact max-degree vertex when the degree pass ran, else the sampled hub
+            const unsigned long long *key = learned ? &st->pred_seedkey : &st->maxkey;
+            CC_TRY(run_bfs_edges<T>(ctx, edges, n, m, s, cutoff, key, &levels, &list_buf, &list_len));
+            vis = as<uint32_t>(ctx->f_vis);
+        } else {
+            CC_TRY(ensure_bfs(ctx, n, (size_t)m));
+            CC_TRY(run_bfs<T>(ctx, edges, n, m, s, cutoff, &levels));
+            vis = as<uint32_t>(ctx->vis);
+        }
         rec(ctx, EV_BFS, s);
         CU_TRY(cudaMemcpyAsync(&ctx->h_st->cmin, &st->cmin, 4, cudaMemcpyDeviceToHost, s));
         unsigned long long visited = 0;
@@ -492,21 +626,27 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         S.comp_min = cmin;
         {
             Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
-            launch_parent_init(parent, n, as<uint32_t>(ctx->vis), cmin, ctx->grid, s);
+            launch_parent_init(parent, n, vis, cmin, ctx->grid, s);
         }
+        // first SV pass over the pairs the BFS left active (Algorithm 2 lines 8-9)
+        cur0 = list_buf == 0 ? 1 : 0;
         {
             Scope sc(ctx, CC_K_SV_FIRST, s, 1);
-            launch_sv_pass<T>(1, true, true, edges, m, n, parent, as<uint32_t>(ctx->vis), cmin, hooked, eb[0], st,
-                              0, ctx->grid, s);
+            if (list_buf < 0)
+                launch_sv_pass<T>(1, true, true, edges, m, n, parent, vis, cmin, hooked, eb[cur0], st, 0, ctx->grid,
+                                  s);
+            else
+                launch_sv_pass<uint32_t>(1, true, true, eb[list_buf], (long long)list_len, n, parent, vis, cmin, hooked,
+                                         eb[cur0], st, 0, ctx->grid, s);
         }
         {
             Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
             launch_sv_shortcut(parent, hooked, st, 0, ctx->grid, s);
         }
-        S.m_active[0] = m;
+        S.m_active[0] = (int64_t)list_len;
         CC_TRY(read_back(ctx, &st->kept[0], 8, s));
         m_cur = ctx->h_st->kept[0];
-        src = eb[0];
+        src = eb[cur0];
     } else {
         {
             Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
@@ -543,7 +683,7 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
             src = eb[0];
         }
     }
-    CC_TRY(sv_list_loop(ctx, n, src, m_cur, it, cap, s));
+    CC_TRY(sv_list_loop(ctx, n, src, m_cur, it, cap, s, cur0));
     rec(ctx, EV_SV, s);
     {
         Scope sc(ctx, CC_K_FINALIZE, s, 1);
@@ -559,15 +699,6 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     return device_error(ctx->h_st->err);
 }
 
-float ev_ms(cc_ctx *ctx, Ev a, Ev b) {
-    if (!ctx->ev_used[a] || !ctx->ev_used[b]) return 0.0f;
-    float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]) != cudaSuccess) {
-        cudaGetLastError();
-        return 0.0f;
-    }
-    return ms;
-}
 
 }  // namespace
 
@@ -638,7 +769,8 @@ cc_status cc_destroy(cc_ctx *ctx) {
                    &ctx->ks_Ac,  &ctx->ks_Zc, &ctx->ks_Df, &ctx->chunk_nz,   &ctx->chunk_mass, &ctx->st,  &ctx->row_ptr, &ctx->col,
                    &ctx->vis,    &ctx->fb,         &ctx->nb,     &ctx->q0,      &ctx->q1,     &ctx->dq,
                    &ctx->off,    &ctx->tsum,       &ctx->counters, &ctx->bk_count, &ctx->bk_off,
-                   &ctx->bk_cursor, &ctx->csr_entries};
+                   &ctx->bk_cursor, &ctx->csr_entries, &ctx->f_sdeg, &ctx->f_counts, &ctx->f_vis,
+                   &ctx->f_f0,   &ctx->f_f1,       &ctx->f_x,    &ctx->pred_wb, &ctx->pred_bias, &ctx->pred_tmp};
     for (Buf *b : bufs) buf_free(*b);
     for (int e = 0; e < EV_COUNT; e++)
         if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
@@ -813,6 +945,71 @@ cc_status cc_ks_statistic(cc_ctx *ctx, const uint64_t *hist_dev, int64_t hist_le
     if (ctx->h_st->err) return CC_ERR_UNSUPPORTED;
     for (int i = 0; i < 5; i++) out_host[i] = ctx->h_st->ks_out[i];
     return CC_OK;
+}
+
+cc_status cc_route_features(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, float *feat_out_dev,
+                            void *stream) {
+    if (!ctx || n <= 0 || m < 0 || !feat_out_dev) return CC_ERR_INVALID_ARG;
+    if (n >= 0xffffffffLL || m >= (1LL << 31)) return CC_ERR_UNSUPPORTED;
+    if ((m > 0 && !edges_dev) || ((uintptr_t)edges_dev & 15)) return CC_ERR_INVALID_ARG;
+    CU_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    CC_TRY(ensure_sv(ctx, (size_t)n, (size_t)m));
+    CC_TRY(ensure_feat(ctx, (size_t)n));
+    DevState *st = as<DevState>(ctx->st);
+    CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+    if (ctx->opt.id_bytes == 4)
+        launch_route_features<int32_t>(edges_dev, m, (vid_t)n, feat_scratch(ctx), st, feat_out_dev, ctx->grid, s);
+    else
+        launch_route_features<int64_t>(edges_dev, m, (vid_t)n, feat_scratch(ctx), st, feat_out_dev, ctx->grid, s);
+    CU_TRY(cudaMemcpyAsync(&ctx->h_st->err, &st->err, 4, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    CU_TRY(cudaGetLastError());
+    return device_error(ctx->h_st->err);
+}
+
+cc_status cc_set_predictor(cc_ctx *ctx, const float *params_host, double min_confidence) {
+    if (!ctx || !(min_confidence >= 0.0 && min_confidence <= 1.0)) return CC_ERR_INVALID_ARG;
+    if (!params_host) {
+        ctx->have_pred = false;
+        return CC_OK;
+    }
+    CU_TRY(cudaSetDevice(ctx->device));
+    const int np = mlp_num_params();
+    CC_TRY(buf_reserve(ctx, ctx->pred_tmp, (size_t)np * 4));
+    CC_TRY(buf_reserve(ctx, ctx->pred_wb, (size_t)np * 2));
+    CC_TRY(buf_reserve(ctx, ctx->pred_bias, 512 * 4));
+    CU_TRY(cudaMemcpy(ctx->pred_tmp.p, params_host, (size_t)np * 4, cudaMemcpyHostToDevice));
+    mlp_prepare_inference(as<float>(ctx->pred_tmp), as<__nv_bfloat16>(ctx->pred_wb), as<float>(ctx->pred_bias), 0);
+    CU_TRY(cudaDeviceSynchronize());
+    CU_TRY(cudaGetLastError());
+    ctx->have_pred = true;
+    ctx->pred_min_conf = min_confidence;
+    return CC_OK;
+}
+
+cc_status cc_mlp_forward(const float *params_dev, const float *X_dev, int B, float *act_dev, void *stream) {
+    if (!params_dev || !X_dev || !act_dev || B <= 0) return CC_ERR_INVALID_ARG;
+    mlp_forward(params_dev, X_dev, B, act_dev, (cudaStream_t)stream);
+    return cuda_status(cudaGetLastError());
+}
+
+cc_status cc_mlp_backward(const float *params_dev, const float *X_dev, const int *y_dev, const float *t_dev,
+                          const float *w_dev, int B, float lambda, const float *act_dev, float *grad_dev,
+                          float *scratch_dev, float *loss_dev, void *stream) {
+    if (!params_dev || !X_dev || !y_dev || !t_dev || !w_dev || !act_dev || !grad_dev || !scratch_dev || !loss_dev ||
+        B <= 0)
+        return CC_ERR_INVALID_ARG;
+    mlp_backward(params_dev, X_dev, y_dev, t_dev, w_dev, B, lambda, act_dev, grad_dev, scratch_dev, loss_dev,
+                 (cudaStream_t)stream);
+    return cuda_status(cudaGetLastError());
+}
+
+cc_status cc_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int count, float lr,
+                      float beta1, float beta2, float eps, int t, void *stream) {
+    if (!params_dev || !grad_dev || !m_dev || !v_dev || count <= 0 || t < 1) return CC_ERR_INVALID_ARG;
+    mlp_adam(params_dev, grad_dev, m_dev, v_dev, count, lr, beta1, beta2, eps, t, (cudaStream_t)stream);
+    return cuda_status(cudaGetLastError());
 }
 
 cc_status cc_get_stats(cc_ctx *ctx, cc_stats *out) {

@@ -40,6 +40,13 @@ struct DevState {
     double ks_out[5];                       // D, alpha, xmin, ntail, ncand
     int route;                              // 1 = BFS first
     int pad;
+    // learned route predictor
+    unsigned long long pred_seedkey;        // (sampled degree << 32) | (0xffffffff - v): probe seed
+    unsigned long long pred_probe[3];       // new vertices at probe levels 1..3
+    int pred_route;                         // 0 SV only, 1 BFS first
+    float pred_conf;                        // probability of the predicted route
+    int pred_cutoff;                        // BFS levels (0 = run to completion)
+    int pad2;
     unsigned long long kept[kMaxIters];     // active pairs written by SV iteration i
     unsigned long long hooked[kMaxIters];   // roots hooked in SV iteration i
     unsigned long long hook_base[kMaxIters + 1];  // start of iteration i's slice of the hooked list
@@ -58,6 +65,7 @@ __device__ __forceinline__ uint4 ld_stream(const uint4 *p) { return __ldcs(p); }
 template <typename T> struct PairVec;
 template <> struct PairVec<int32_t> { static constexpr int kPairs = 2; };
 template <> struct PairVec<int64_t> { static constexpr int kPairs = 1; };
+template <> struct PairVec<uint32_t> { static constexpr int kPairs = 2; };
 
 // Decodes pair `j` (0..kPairs-1) of a 128-bit vector as unsigned 64-bit ids.
 template <typename T>
@@ -71,6 +79,12 @@ template <>
 __device__ __forceinline__ void vec_pair<int64_t>(const int4 &q, int, long long &u, long long &v) {
     u = (long long)(((unsigned long long)(unsigned)q.y << 32) | (unsigned)q.x);
     v = (long long)(((unsigned long long)(unsigned)q.w << 32) | (unsigned)q.z);
+}
+
+template <>
+__device__ __forceinline__ void vec_pair<uint32_t>(const int4 &q, int j, long long &u, long long &v) {
+    u = j == 0 ? (long long)(unsigned)q.x : (long long)(unsigned)q.z;
+    v = j == 0 ? (long long)(unsigned)q.y : (long long)(unsigned)q.w;
 }
 
 template <typename T>
@@ -95,6 +109,38 @@ __device__ __forceinline__ unsigned long long warp_append(unsigned long long *co
 }
 
 __device__ __forceinline__ void set_err(DevState *st, uint32_t bit) { atomicOr(&st->err, bit); }
+
+// Block-wide exclusive scan of small per-thread counts; thread 0 reserves
+// the block's total from `counter` with one atomic. Returns this thread's
+// first slot. Called by every thread of the block.
+__device__ __forceinline__ unsigned long long block_reserve(unsigned long long *counter, int c, int *sw,
+                                                            unsigned long long *sbase) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sw[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int w = lane < nw ? sw[lane] : 0, wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) sw[lane] = wi - w;
+        if (lane == nw - 1) *sbase = wi ? atomicAdd(counter, (unsigned long long)wi) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long r = *sbase + (unsigned long long)(sw[warp] + incl - c);
+    __syncthreads();
+    return r;
+}
+
 
 // Grid-stride helpers
 __device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }

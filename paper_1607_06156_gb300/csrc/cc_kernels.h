@@ -36,6 +36,24 @@ void launch_csr_bucketed(const void *edges, long long m, vid_t n, const uint32_t
                          BucketScratch bs, unsigned long long *entries, DevState *st, int grid, cudaStream_t s);
 cudaError_t bucket_kernels_setup();
 
+// Scratch of the sampled route features (k_mlp.cu).
+struct FeatScratch {
+    uint32_t *sdeg;     // [n/16 + 1] degrees of the sampled vertices
+    unsigned *counts;   // [64] log2-bucket counts
+    uint32_t *vis, *f0, *f1;  // [n/32 + 1] probe bitmaps
+};
+
+// k_mlp.cu
+int mlp_num_params();
+void mlp_forward(const float *P, const float *X, int B, float *act, cudaStream_t s);
+void mlp_backward(const float *P, const float *X, const int *y, const float *t, const float *w, int B, float lam,
+                  const float *act, float *G, float *scratch, float *loss, cudaStream_t s);
+void mlp_adam(float *P, const float *G, float *M, float *V, int count, float lr, float b1, float b2, float eps, int t,
+              cudaStream_t s);
+template <typename T>
+void launch_route_features(const void *edges, long long m, vid_t n, FeatScratch fs, DevState *st, float *x, int grid,
+                           cudaStream_t s);
+
 // k_degree.cu
 template <typename T>
 void launch_degree(const void *edges, long long m, vid_t n, uint32_t *deg, DevState *st, int grid, cudaStream_t s);
@@ -85,5 +103,16 @@ void launch_bitmap_to_queue(const uint32_t *bm, long long nwords, vid_t *queue, 
                             cudaStream_t s);
 void launch_first_visited(const uint32_t *vis, long long nwords, DevState *st, int grid, cudaStream_t s);
 void launch_popcount(const uint32_t *bm, long long nwords, unsigned long long *out, int grid, cudaStream_t s);
+template <typename T>
+void launch_bfs_edges(bool write, const void *in, long long m, vid_t n, uint32_t *vis, const uint32_t *cur,
+                      uint32_t *next, uint2 *out, DevState *st, int level, int grid, cudaStream_t s);
+void launch_edge_bfs_seed(uint32_t *vis, uint32_t *cur, vid_t n, const unsigned long long *key, DevState *st,
+                          cudaStream_t s);
 
+}  // namespace ccg
+
+#include <cuda_bf16.h>
+namespace ccg {
+void mlp_prepare_inference(const float *P, __nv_bfloat16 *Wb, float *bias, cudaStream_t s);
+void mlp_infer(const __nv_bfloat16 *Wb, const float *bias, const float *x, DevState *st, cudaStream_t s);
 }  // namespace ccg

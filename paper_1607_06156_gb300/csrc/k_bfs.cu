@@ -304,6 +304,134 @@ __global__ void __launch_bounds__(kBlock) k_bitmap_to_queue(const uint32_t *__re
     }
 }
 
+// ---------------------------------------------------------------------------
+// Edge-list BFS (bfs_mode 1): one level is one streaming pass over the
+// active pairs, no CSR. A pair with one end in the frontier bitmap claims
+// the other end if it is unvisited (atomicOr on the visited bitmap decides
+// the single winner, which also enters the next frontier). A pair whose ends
+// are both visited after the level can never claim again (and the SV step
+// drops it anyway), so it leaves the active list; with WRITE the surviving
+// pairs are compacted into `out`. front[level + 1] counts the claimed
+// vertices, front_edges[level + 1] the surviving pairs.
+template <typename T> struct EdgeUnroll { static constexpr int U = 2; };
+template <> struct EdgeUnroll<int64_t> { static constexpr int U = 4; };
+
+__device__ __forceinline__ bool bit_test(const uint32_t *b, long long v) { return (b[v >> 5] >> (v & 31)) & 1u; }
+
+__device__ __forceinline__ bool claim(uint32_t *vis, uint32_t *next, long long v) {
+    const uint32_t bit = 1u << (v & 31);
+    if (__ldcg(&vis[v >> 5]) & bit) return false;
+    if (atomicOr(&vis[v >> 5], bit) & bit) return false;
+    atomicOr(&next[v >> 5], bit);
+    return true;
+}
+
+template <typename T, bool WRITE>
+__global__ void __launch_bounds__(kBlock) k_bfs_edges(const T *__restrict__ in, long long m, vid_t n, uint32_t *vis,
+                                                      const uint32_t *__restrict__ cur, uint32_t *next,
+                                                      uint2 *__restrict__ out, DevState *st, int level) {
+    constexpr int P = PairVec<T>::kPairs;
+    constexpr int U = EdgeUnroll<T>::U;
+    constexpr int K = P * U;
+    __shared__ int sw[32];
+    __shared__ unsigned long long sbase;
+    const long long nvec = m / P;
+    const int4 *ev = reinterpret_cast<const int4 *>(in);
+    const long long tile = (long long)kBlock * U;
+    const long long ntiles = (nvec + tile - 1) / tile;
+    unsigned long long claimed = 0, kept_total = 0;
+    for (long long t = blockIdx.x; t < ntiles + (P == 2 && (m & 1) ? 1 : 0); t += gridDim.x) {
+        long long u[K], v[K];
+        bool valid[K];
+        if (t < ntiles) {
+            int4 q[U];
+#pragma unroll
+            for (int k = 0; k < U; k++) {
+                const long long i = t * tile + (long long)k * kBlock + threadIdx.x;
+                q[k] = i < nvec ? ld_stream(ev + i) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int k = 0; k < U; k++) {
+                const long long i = t * tile + (long long)k * kBlock + threadIdx.x;
+#pragma unroll
+                for (int j = 0; j < P; j++) {
+                    vec_pair<T>(q[k], j, u[k * P + j], v[k * P + j]);
+                    valid[k * P + j] = i < nvec;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                u[k] = v[k] = 0;
+                valid[k] = false;
+            }
+            if (threadIdx.x == 0) {
+                scalar_pair<T>(in, m - 1, u[0], v[0]);
+                valid[0] = true;
+            }
+        }
+        bool keep[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            keep[k] = false;
+            if (!valid[k] || (unsigned long long)u[k] >= n || (unsigned long long)v[k] >= n) continue;
+            const bool fu = bit_test(cur, u[k]), fv = bit_test(cur, v[k]);
+            const bool vu0 = fu || bit_test(vis, u[k]), vv0 = fv || bit_test(vis, v[k]);
+            if (fu && !vv0 && claim(vis, next, v[k])) claimed++;
+            if (fv && !vu0 && claim(vis, next, u[k])) claimed++;
+            // after this pair's claims: u is visited if it was, or if v is in the frontier
+            keep[k] = !((vu0 || fv) && (vv0 || fu));
+        }
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) c += keep[k];
+        kept_total += (unsigned long long)c;
+        if (WRITE) {
+            unsigned long long o = block_reserve(&st->front_edges[level + 1], c, sw, &sbase);
+#pragma unroll
+            for (int k = 0; k < K; k++)
+                if (keep[k]) out[o++] = make_uint2((vid_t)u[k], (vid_t)v[k]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        claimed += __shfl_xor_sync(0xffffffffu, claimed, o);
+        kept_total += __shfl_xor_sync(0xffffffffu, kept_total, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (claimed) atomicAdd(&st->front[level + 1], claimed);
+        if (!WRITE && kept_total) atomicAdd(&st->front_edges[level + 1], kept_total);
+    }
+}
+
+__global__ void k_edge_bfs_seed(uint32_t *vis, uint32_t *cur, vid_t n, const unsigned long long *key, DevState *st) {
+    vid_t s = 0xffffffffu - (vid_t)(*key & 0xffffffffull);
+    if (s >= n) s = 0;
+    vis[s >> 5] |= 1u << (s & 31);
+    cur[s >> 5] |= 1u << (s & 31);
+    st->front[0] = 1;
+    st->cmin = 0xffffffffu;
+}
+
+template <typename T>
+void launch_bfs_edges(bool write, const void *in, long long m, vid_t n, uint32_t *vis, const uint32_t *cur,
+                      uint32_t *next, uint2 *out, DevState *st, int level, int grid, cudaStream_t s) {
+    if (m <= 0) return;
+    if (write) k_bfs_edges<T, true><<<grid, kBlock, 0, s>>>((const T *)in, m, n, vis, cur, next, out, st, level);
+    else k_bfs_edges<T, false><<<grid, kBlock, 0, s>>>((const T *)in, m, n, vis, cur, next, out, st, level);
+}
+template void launch_bfs_edges<int32_t>(bool, const void *, long long, vid_t, uint32_t *, const uint32_t *, uint32_t *,
+                                        uint2 *, DevState *, int, int, cudaStream_t);
+template void launch_bfs_edges<int64_t>(bool, const void *, long long, vid_t, uint32_t *, const uint32_t *, uint32_t *,
+                                        uint2 *, DevState *, int, int, cudaStream_t);
+template void launch_bfs_edges<uint32_t>(bool, const void *, long long, vid_t, uint32_t *, const uint32_t *,
+                                         uint32_t *, uint2 *, DevState *, int, int, cudaStream_t);
+
+void launch_edge_bfs_seed(uint32_t *vis, uint32_t *cur, vid_t n, const unsigned long long *key, DevState *st,
+                          cudaStream_t s) {
+    k_edge_bfs_seed<<<1, 1, 0, s>>>(vis, cur, n, key, st);
+}
+
 // smallest set bit of the visited bitmap
 __global__ void __launch_bounds__(kBlock) k_first_visited(const uint32_t *__restrict__ vis, long long nwords,
                                                           DevState *st) {

@@ -37,51 +37,9 @@
 
 namespace ccg {
 
-template <> struct PairVec<uint32_t> { static constexpr int kPairs = 2; };
-template <>
-__device__ __forceinline__ void vec_pair<uint32_t>(const int4 &q, int j, long long &u, long long &v) {
-    u = j == 0 ? (long long)(unsigned)q.x : (long long)(unsigned)q.z;
-    v = j == 0 ? (long long)(unsigned)q.y : (long long)(unsigned)q.w;
-}
-template <>
-__device__ __forceinline__ void scalar_pair<uint32_t>(const uint32_t *e, long long k, long long &u, long long &v) {
-    u = (long long)e[2 * k];
-    v = (long long)e[2 * k + 1];
-}
 
 __device__ __forceinline__ bool vis_test(const uint32_t *vis, long long v) {
     return (vis[v >> 5] >> (v & 31)) & 1u;
-}
-
-// Block-wide exclusive scan of small per-thread counts; thread 0 reserves
-// the block's total from `counter` with one atomic. Returns this thread's
-// first slot. Called by every thread of the block.
-__device__ __forceinline__ unsigned long long block_reserve(unsigned long long *counter, int c, int *sw,
-                                                            unsigned long long *sbase) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) sw[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        int w = lane < nw ? sw[lane] : 0, wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
-        }
-        if (lane < nw) sw[lane] = wi - w;
-        if (lane == nw - 1) *sbase = wi ? atomicAdd(counter, (unsigned long long)wi) : 0ull;
-    }
-    __syncthreads();
-    const unsigned long long r = *sbase + (unsigned long long)(sw[warp] + incl - c);
-    __syncthreads();
-    return r;
 }
 
 // One pair of an SV pass. Returns true if the pair stays active; `hooked`

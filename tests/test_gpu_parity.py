@@ -277,3 +277,21 @@ def test_stress_many_chains_sv(seed):
     one iteration make concurrent shortcuts race; labels must stay exact."""
     g = gg.grid_chains(seed=100 + seed, W=700, p=0.55, nchains=150_000, id_bytes=4)
     assert_labels_match(g.edges, g.n, routes=("sv",))
+
+
+@pytest.mark.parametrize("cutoff", [0, 1, 3])
+def test_edge_list_bfs_mode(cutoff):
+    """bfs_mode 1: BFS as streaming passes over the active pairs (no CSR)."""
+    for g in (gg.chung_lu(seed=9, n=1 << 16, avg_degree=8), gg.rmat(seed=10, scale=17, edge_factor=16),
+              gg.grid_chains(seed=11, W=200, nchains=5000, id_bytes=8), gg.planted(seed=12, n=40000, ncomp=100)):
+        st = assert_labels_match(g.edges, g.n, routes=("bfs",), bfs_mode=1, bfs_cutoff_levels=cutoff)["bfs"]
+        assert st["route"] == 1 and st["bfs_visited"] >= 1
+        if cutoff:
+            assert st["bfs_levels"] <= cutoff
+
+
+def test_edge_list_bfs_matches_csr_bfs_visited_set():
+    g = gg.chung_lu(seed=13, n=1 << 17, avg_degree=10)
+    a = assert_labels_match(g.edges, g.n, routes=("bfs",), bfs_mode=1)["bfs"]
+    b = assert_labels_match(g.edges, g.n, routes=("bfs",), bfs_mode=0)["bfs"]
+    assert a["bfs_visited"] == b["bfs_visited"] and a["comp_min"] == b["comp_min"]

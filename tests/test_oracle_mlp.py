@@ -62,3 +62,19 @@ def test_adam_decreases_the_loss():
     for _ in range(200):
         mlp.adam_step(p, mlp.backward(p, mlp.forward(p, X), y, t, w), st, lr=3e-3)
     assert mlp.loss(mlp.forward(p, X)["o"], y, t, w) < 0.2 * l0
+
+
+def test_route_features_hand_computed():
+    """A star on vertex 16 (degree 10), vertex 0 isolated, pair (32, 33):
+    sampled vertices 0, 16, 32 have degrees 0, 10, 1 -> buckets 0, 4, 1; the
+    probe from 16 reaches 10 vertices at level 1 and none after."""
+    import math
+
+    e = np.array([(16, i) for i in range(1, 11)] + [(32, 33)], dtype=np.int32)
+    x = mlp.route_features(e, 40)
+    want = np.zeros(69)
+    want[[0, 1, 4]] = 1.0 / 3.0
+    want[64] = math.log(40) / 20
+    want[65] = math.log(12) / 20
+    want[66] = math.log(11) / 20
+    assert np.allclose(x, want)
