@@ -435,12 +435,23 @@ def main() -> int:
         del d_edges
         eng.set_options(profile=1)
 
-    # the forced routes on the same graph (the paper's dynamic-vs-opposite comparison)
+    # the forced routes on the same graph (the paper's dynamic-vs-opposite
+    # comparison), the edge-list BFS engine, and the learned route with the
+    # committed predictor weights
     route_compare = None
     if not args.no_compare and rank == 0:
         route_compare = {}
-        for r in ("sv", "bfs"):
-            e = cc.Engine(id_bytes=w, route=r, device=local)
+        variants = [("sv", dict(route="sv")), ("bfs", dict(route="bfs")), ("bfs_edges", dict(route="bfs", bfs_mode=1))]
+        wpath = os.path.join(ROOT, "paper_1607_06156_gb300", "route_predictor.bin")
+        if os.path.exists(wpath):
+            variants.append(("learned", dict(route="learned")))
+        ref_lab = lab.clone()
+        for r, kw in variants:
+            e = cc.Engine(id_bytes=w, device=local, **kw)
+            if r == "learned":
+                from paper_1607_06156_gb300.train_predictor import load_params
+
+                e.set_predictor(load_params(wpath)[0])
             e.labels(edges_d, n, out=lab)
             torch.cuda.synchronize(dev)
             k = max(3, min(args.steps, 5))
@@ -452,7 +463,10 @@ def main() -> int:
             torch.cuda.synchronize(dev)
             t = a.elapsed_time(b) / k
             sd = e.stats()
+            if not torch.equal(lab, ref_lab):
+                raise SystemExit(f"route {r} changed the labels")
             route_compare[r] = {"value": m / (t / 1e3), "ms_per_step": t, "route": sd["route"],
+                                "route_source": sd["route_source"],
                                 "stage_ms": {k2: sd[k2] for k2 in ("ms_degree", "ms_predict", "ms_csr", "ms_bfs",
                                                                    "ms_sv", "ms_finalize")}}
             e.close()
