@@ -140,7 +140,8 @@ cc_status ensure_sv(cc_ctx *ctx, size_t n, size_t m) {
     CC_TRY(buf_reserve(ctx, ctx->chunk_nz, (size_t)(ks_num_chunks() + 1) * 8));
     CC_TRY(buf_reserve(ctx, ctx->chunk_mass, (size_t)(ks_num_chunks() + 1) * 8));
     CC_TRY(buf_reserve(ctx, ctx->st, sizeof(DevState)));
-    CC_TRY(buf_reserve(ctx, ctx->counters, 64 * 8));  // both BFS engines count visited vertices here
+    // BFS visited counts (words 0-1) and the hub-aware degree pass scratch (32-bit words 32..)
+    CC_TRY(buf_reserve(ctx, ctx->counters, 4096));
     CC_TRY(buf_reserve(ctx, ctx->bk_count, (size_t)ctx->grid * (bucket_max() + 2) * 4));
     CC_TRY(buf_reserve(ctx, ctx->bk_cursor, (size_t)ctx->grid * (bucket_max() + 2) * 4));
     CC_TRY(buf_reserve(ctx, ctx->bk_off, (size_t)(bucket_max() + 2) * 8));
@@ -306,7 +307,12 @@ template <typename T>
 void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s) {
     cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s);
     cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
-    {
+    if (degree_uses_hubs(m)) {
+        Scope sc(ctx, CC_K_DEGREE, s, 4);
+        unsigned *scr = as<unsigned>(ctx->counters) + 16;  // 34 words after the BFS counters
+        launch_degree_hubs<T>(edges, m, n, as<uint32_t>(ctx->deg), scr, scr + 40, as<DevState>(ctx->st), ctx->grid,
+                              s);
+    } else {
         Scope sc(ctx, CC_K_DEGREE, s, m > 0);
         launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), as<DevState>(ctx->st), ctx->grid, s);
     }
@@ -317,14 +323,27 @@ void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaSt
     }
 }
 
-void enqueue_ks(cc_ctx *ctx, cudaStream_t s) {
+// k distinct positive degrees sum to at least k(k+1)/2 <= 2m, so k <= sqrt(4m);
+// and k <= n. (`m` < 0: unknown, take the scratch capacity.)
+long long distinct_degree_bound(cc_ctx *ctx, long long n, long long m) {
+    long long b = (long long)ctx->ks_cap;
+    if (n > 0 && n < b) b = n;
+    if (m >= 0) {
+        const long long r = (long long)sqrt(4.0 * (double)m) + 2;
+        if (r < b) b = r;
+    }
+    return b;
+}
+
+void enqueue_ks(cc_ctx *ctx, cudaStream_t s, long long nd_bound) {
     KsScratch ks{as<uint32_t>(ctx->ks_xs), as<unsigned long long>(ctx->ks_cnt), as<unsigned long long>(ctx->ks_cum),
                  as<double>(ctx->ks_lnx), as<double>(ctx->ks_Dc), as<double>(ctx->ks_Ac), as<double>(ctx->ks_Zc),
                  as<float>(ctx->ks_Df),
                  as<unsigned long long>(ctx->chunk_nz), as<unsigned long long>(ctx->chunk_mass), ctx->ks_cap};
     Scope sc(ctx, CC_K_KS, s, 7);
     launch_ks(as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap, ks, as<DevState>(ctx->st),
-              ctx->opt.ks_min_tail, ctx->opt.ks_min_distinct, ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->grid, s);
+              ctx->opt.ks_min_tail, ctx->opt.ks_min_distinct, ctx->opt.ks_min_span, ctx->opt.ks_tau, nd_bound,
+              ctx->grid, s);
 }
 
 // CSR + direction-optimizing BFS from the max-degree vertex. Returns the
@@ -574,7 +593,7 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     if (!learned && policy != CC_ROUTE_FORCE_SV && m > 0) {
         enqueue_degree<T>(ctx, edges, n, m, s);
         rec(ctx, EV_DEGREE, s);
-        if (policy != CC_ROUTE_FORCE_BFS) enqueue_ks(ctx, s);
+        if (policy != CC_ROUTE_FORCE_BFS) enqueue_ks(ctx, s, distinct_degree_bound(ctx, n, m));
         rec(ctx, EV_PREDICT, s);
         CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, kept), cudaMemcpyDeviceToHost, s));
         CU_TRY(cudaStreamSynchronize(s));
@@ -938,7 +957,7 @@ cc_status cc_ks_statistic(cc_ctx *ctx, const uint64_t *hist_dev, int64_t hist_le
     CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
     CU_TRY(cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s));
     launch_hist_narrow(hist_dev, hist_len, as<uint32_t>(ctx->hist), st, ctx->grid, s);
-    enqueue_ks(ctx, s);
+    enqueue_ks(ctx, s, distinct_degree_bound(ctx, hist_len, -1));
     CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, kept), cudaMemcpyDeviceToHost, s));
     CU_TRY(cudaStreamSynchronize(s));
     CU_TRY(cudaGetLastError());

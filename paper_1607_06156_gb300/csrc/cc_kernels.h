@@ -57,10 +57,15 @@ void launch_route_features(const void *edges, long long m, vid_t n, FeatScratch 
 // k_degree.cu
 template <typename T>
 void launch_degree(const void *edges, long long m, vid_t n, uint32_t *deg, DevState *st, int grid, cudaStream_t s);
+bool degree_uses_hubs(long long m);
+template <typename T>
+void launch_degree_hubs(const void *edges, long long m, vid_t n, uint32_t *deg, unsigned *scratch, uint32_t *hubs,
+                        DevState *st, int grid, cudaStream_t s);
 void launch_hist(const uint32_t *deg, vid_t n, uint32_t *hist, uint32_t *ovf, unsigned long long ovf_cap,
                  DevState *st, int grid, cudaStream_t s);
 void launch_ks(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf_cap, KsScratch ks, DevState *st,
-               long long min_tail, long long min_distinct, double min_span, double tau, int grid, cudaStream_t s);
+               long long min_tail, long long min_distinct, double min_span, double tau, long long nd_bound, int grid,
+               cudaStream_t s);
 int ks_num_chunks();
 void launch_hist_widen(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf_cap, const DevState *st,
                        uint64_t *out, long long len, int grid, cudaStream_t s);

@@ -66,6 +66,135 @@ __global__ void __launch_bounds__(kBlock) k_degree(const T *__restrict__ edges, 
 }
 
 // ---------------------------------------------------------------------------
+// Hub-aware degree pass. The counts of a few high-degree vertices (hubs of
+// scale-free graphs) all land on a handful of L2 slices, which then bound
+// the whole pass. The pass is split: a prefix of the pairs is counted with
+// plain global atomics; the vertices whose prefix count clears a threshold
+// (at most kHubs, the threshold the smallest power of two that admits no
+// more) are hubs; the rest of the pairs is counted with the hubs in a
+// per-block shared-memory table, flushed once per block. Which vertices
+// become hubs only changes the speed, never the counts.
+constexpr int kHubs = 256;
+constexpr int kHubTable = 512;  // open addressing, load <= 1/2
+
+__device__ __forceinline__ int hub_hash(uint32_t v) { return (int)((v * 2654435761u) >> 23); }  // 9 bits
+
+// log2 histogram of the prefix counts (bucket b: counts in [2^b, 2^(b+1)))
+__global__ void __launch_bounds__(kBlock) k_hub_levels(const uint32_t *__restrict__ deg, vid_t n, unsigned *levels) {
+    __shared__ unsigned sh[33];
+    if (threadIdx.x < 33) sh[threadIdx.x] = 0;
+    __syncthreads();
+    for (long long v = gtid(); v < (long long)n; v += gstride()) {
+        const uint32_t d = deg[v];
+        if (d >= 16) atomicAdd(&sh[31 - __clz(d)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 33 && sh[threadIdx.x]) atomicAdd(&levels[threadIdx.x], sh[threadIdx.x]);
+}
+
+// hubs = vertices whose prefix count is >= 2^b for the smallest b >= 4 with
+// at most kHubs of them
+__global__ void __launch_bounds__(kBlock) k_hub_select(const uint32_t *__restrict__ deg, vid_t n,
+                                                       const unsigned *levels, uint32_t *hubs, unsigned *nhubs) {
+    __shared__ int sb;
+    if (threadIdx.x == 0) {
+        unsigned above = 0;
+        int b = 32;
+        for (int k = 31; k >= 4; k--) {
+            if (above + levels[k] > (unsigned)kHubs) break;
+            above += levels[k];
+            b = k;
+        }
+        sb = b;
+    }
+    __syncthreads();
+    if (sb >= 32) return;
+    const uint32_t thr = 1u << sb;
+    for (long long v = gtid(); v < (long long)n; v += gstride())
+        if (deg[v] >= thr) {
+            const unsigned k = atomicAdd(nhubs, 1u);
+            if (k < (unsigned)kHubs) hubs[k] = (uint32_t)v;
+        }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_degree_hubs(const T *__restrict__ edges, long long m, vid_t n,
+                                                        uint32_t *__restrict__ deg, const uint32_t *__restrict__ hubs,
+                                                        const unsigned *__restrict__ nhubs, DevState *st) {
+    __shared__ uint32_t key[kHubTable];
+    __shared__ unsigned cnt[kHubTable];
+    for (int i = threadIdx.x; i < kHubTable; i += blockDim.x) {
+        key[i] = 0xffffffffu;
+        cnt[i] = 0;
+    }
+    __syncthreads();
+    const unsigned nh = *nhubs < (unsigned)kHubs ? *nhubs : (unsigned)kHubs;
+    if (threadIdx.x == 0)
+        for (unsigned i = 0; i < nh; i++) {
+            int h = hub_hash(hubs[i]);
+            while (key[h] != 0xffffffffu) h = (h + 1) & (kHubTable - 1);
+            key[h] = hubs[i];
+        }
+    __syncthreads();
+    constexpr int P = PairVec<T>::kPairs;
+    constexpr int U = 4;
+    const long long nvec = m / P;
+    const int4 *ev = reinterpret_cast<const int4 *>(edges);
+    bool bad = false;
+    const long long stride = gstride();
+    auto count = [&](long long x) {
+        int h = hub_hash((uint32_t)x);
+        while (true) {
+            const uint32_t k = key[h];
+            if (k == (uint32_t)x) {
+                atomicAdd(&cnt[h], 1u);
+                return;
+            }
+            if (k == 0xffffffffu) break;
+            h = (h + 1) & (kHubTable - 1);
+        }
+        atomicAdd(&deg[x], 1u);
+    };
+    for (long long base = gtid(); base < nvec; base += stride * U) {
+        int4 q[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const long long i = base + (long long)k * stride;
+            if (i < nvec) q[k] = ld_stream(ev + i);
+        }
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const long long i = base + (long long)k * stride;
+            if (i >= nvec) break;
+#pragma unroll
+            for (int j = 0; j < P; j++) {
+                long long u, v;
+                vec_pair<T>(q[k], j, u, v);
+                if ((unsigned long long)u >= n || (unsigned long long)v >= n) {
+                    bad = true;
+                    continue;
+                }
+                count(u);
+                count(v);
+            }
+        }
+    }
+    if (P == 2 && (m & 1) && gtid() == 0) {
+        long long u, v;
+        scalar_pair<T>(edges, m - 1, u, v);
+        if ((unsigned long long)u >= n || (unsigned long long)v >= n) bad = true;
+        else {
+            count(u);
+            count(v);
+        }
+    }
+    if (bad) set_err(st, kErrInvalidEdge);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHubTable; i += blockDim.x)
+        if (cnt[i]) atomicAdd(&deg[key[i]], cnt[i]);
+}
+
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ void hist_one(uint32_t d, vid_t v, uint32_t *sh, uint32_t *hist, uint32_t *ovf,
                                          unsigned long long ovf_cap, DevState *st, unsigned long long &best) {
     if (d < kHistSmem) atomicAdd(&sh[d], 1u);
@@ -568,6 +697,28 @@ void launch_degree(const void *edges, long long m, vid_t n, uint32_t *deg, DevSt
 template void launch_degree<int32_t>(const void *, long long, vid_t, uint32_t *, DevState *, int, cudaStream_t);
 template void launch_degree<int64_t>(const void *, long long, vid_t, uint32_t *, DevState *, int, cudaStream_t);
 
+// prefix pairs counted plainly before the hubs are chosen
+constexpr long long kHubPrefix = 1LL << 22;
+
+bool degree_uses_hubs(long long m) { return m >= 4 * kHubPrefix; }
+
+// deg must be zeroed; scratch: levels[33] + nhubs (34 unsigned, zeroed here) and hubs[kHubs]
+template <typename T>
+void launch_degree_hubs(const void *edges, long long m, vid_t n, uint32_t *deg, unsigned *scratch, uint32_t *hubs,
+                        DevState *st, int grid, cudaStream_t s) {
+    cudaMemsetAsync(scratch, 0, 34 * sizeof(unsigned), s);
+    // the prefix must end on a 16-byte boundary of the pair array: kHubPrefix pairs of 8 or 16 bytes do
+    k_degree<T><<<grid, kBlock, 0, s>>>((const T *)edges, kHubPrefix, n, deg, st);
+    k_hub_levels<<<grid, kBlock, 0, s>>>(deg, n, scratch);
+    k_hub_select<<<grid, kBlock, 0, s>>>(deg, n, scratch, hubs, scratch + 33);
+    k_degree_hubs<T><<<grid, kBlock, 0, s>>>((const T *)edges + 2 * kHubPrefix, m - kHubPrefix, n, deg, hubs,
+                                             scratch + 33, st);
+}
+template void launch_degree_hubs<int32_t>(const void *, long long, vid_t, uint32_t *, unsigned *, uint32_t *,
+                                          DevState *, int, cudaStream_t);
+template void launch_degree_hubs<int64_t>(const void *, long long, vid_t, uint32_t *, unsigned *, uint32_t *,
+                                          DevState *, int, cudaStream_t);
+
 void launch_hist(const uint32_t *deg, vid_t n, uint32_t *hist, uint32_t *ovf, unsigned long long ovf_cap,
                  DevState *st, int grid, cudaStream_t s) {
     if (n == 0) return;
@@ -575,7 +726,8 @@ void launch_hist(const uint32_t *deg, vid_t n, uint32_t *hist, uint32_t *ovf, un
 }
 
 void launch_ks(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf_cap, KsScratch ks, DevState *st,
-               long long min_tail, long long min_distinct, double min_span, double tau, int grid, cudaStream_t s) {
+               long long min_tail, long long min_distinct, double min_span, double tau, long long nd_bound, int grid,
+               cudaStream_t s) {
     k_distinct_count<<<kNumChunks, 1024, 0, s>>>(hist, st, ks.chunk_nz, ks.chunk_mass);
     k_distinct_scan<<<1, 1024, 0, s>>>(ks.chunk_nz, ks.chunk_mass, st, ks.cap);
     k_distinct_write<<<kNumChunks, 1024, 0, s>>>(hist, st, ks.chunk_nz, ks.chunk_mass, ks.xs, ks.cnt, ks.cum, ks.lnx,
@@ -583,8 +735,11 @@ void launch_ks(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf
     k_distinct_overflow<<<1, 1024, 0, s>>>(ovf, ovf_cap, ks.chunk_mass, st, ks.xs, ks.cnt, ks.cum, ks.lnx, ks.cap);
     k_ks_prep<<<grid, 256, 0, s>>>(ks.xs, ks.cnt, ks.cum, ks.lnx, st, min_tail, min_distinct, min_span, ks.Dc,
                                    ks.Ac, ks.Zc);
-    // blocks stride over candidates (y) and over chunks of kKsTerms terms (x)
-    const dim3 tg(4, 2048);
+    // blocks stride over candidates (y) and over chunks of kKsTerms terms (x);
+    // nd_bound (an upper bound of the distinct degrees) keeps small graphs from
+    // launching thousands of idle blocks
+    const long long nb = nd_bound < 1 ? 1 : nd_bound;
+    const dim3 tg((unsigned)(nb < 4 * kKsTerms ? (nb + kKsTerms - 1) / kKsTerms : 4), (unsigned)(nb < 2048 ? nb : 2048));
     cudaMemsetAsync(ks.Df, 0, sizeof(float) * (ks.cap + 1), s);
     k_ks_terms<false><<<tg, 256, 0, s>>>(ks.xs, ks.cum, ks.lnx, st, ks.Dc, ks.Ac, ks.Zc, ks.Df);
     k_ks_terms<true><<<tg, 256, 0, s>>>(ks.xs, ks.cum, ks.lnx, st, ks.Dc, ks.Ac, ks.Zc, ks.Df);

@@ -295,3 +295,25 @@ def test_edge_list_bfs_matches_csr_bfs_visited_set():
     a = assert_labels_match(g.edges, g.n, routes=("bfs",), bfs_mode=1)["bfs"]
     b = assert_labels_match(g.edges, g.n, routes=("bfs",), bfs_mode=0)["bfs"]
     assert a["bfs_visited"] == b["bfs_visited"] and a["comp_min"] == b["comp_min"]
+
+
+@pytest.mark.parametrize("id_bytes,extra", [(4, 0), (4, 3), (8, 1)])
+def test_hub_aware_degree_pass(id_bytes, extra):
+    """m >= 2^24 takes the hub-aware degree pass (prefix counts pick the hubs,
+    the rest is counted with hubs in shared memory); counts stay exact."""
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    g = gg.rmat(seed=31, scale=20, edge_factor=16, m=(1 << 24) + extra, id_bytes=id_bytes)
+    # hubs whose pairs mostly come after the prefix
+    hub = np.stack([np.full(300000, 77), np.arange(300000) * 7 % g.n], axis=1).astype(g.edges.dtype)
+    e = np.concatenate([g.edges, hub])
+    deg_o = oracle.degrees(e, g.n)
+    eng = cc.Engine(id_bytes=id_bytes)
+    deg, hist = eng.degree_distribution(torch.from_numpy(e).cuda(), g.n, hist_len=int(deg_o.max()) + 1)
+    assert np.array_equal(deg.cpu().numpy().astype(np.int64), deg_o)
+    assert np.array_equal(hist.cpu().numpy(), oracle.histogram(deg_o))
+    eng.close()
+    got, st = run_engine(e, g.n, route="auto")
+    assert np.array_equal(got, oracle.cc_labels(e, g.n, cross_check=False))
+    assert st["max_degree"] == int(deg_o.max())
