@@ -11,6 +11,9 @@ flush is done between steps.
 
 Extra keys: roofline of the dominant kernel (algorithmic bytes per launch /
 its average event-timed duration, against the measured HBM copy bandwidth),
+l2_roofline (the same kernel's scattered 4-byte accesses per second against
+the L2 random-op rate measured in the same run: the degree and hook passes
+are bound by that rate, not by HBM),
 e2e (the same metric with pinned host buffers and both copies inside the
 timed region), cpu_baseline (the CPU oracle on a bounded prefix sample),
 clocks sampled during the timed region, and route_compare (the forced BFS
@@ -41,6 +44,7 @@ UNIT = "edges/s"
 WORKLOADS = {
     "rmat24": dict(kind="rmat", scale=24, edge_factor=16, seed=1),
     "rmat20": dict(kind="rmat", scale=20, edge_factor=16, seed=1),
+    "rmat22": dict(kind="rmat", scale=22, edge_factor=16, seed=1),
     "planted": dict(kind="planted", seed=1),
     "grid_chains": dict(kind="grid_chains", seed=1, W=8192, nchains=10_000_000),
     "batch4096": dict(kind="batch", seed=1, G=4096, nmin=1000, nmax=1_000_000),
@@ -107,6 +111,29 @@ def alg_bytes(cls: str, st: dict, w: int) -> float:
     return 0.0
 
 
+def l2_ops(cls: str, st: dict) -> tuple[float, str]:
+    """Scattered 4-byte accesses to L2-resident arrays one call makes in a
+    kernel class, and the probe rate that bounds them. A lower bound: the
+    hook atomics that follow a passing pre-check are not counted."""
+    n, m = st["n"], st["m"]
+    act = st["m_active"]
+    if cls == "degree":
+        return 2.0 * m, "red_add"            # one increment per pair endpoint
+    if cls == "sv_first":
+        return 1.0 * m, "gather"             # pre-check read of parent[max(u, v)]
+    if cls == "sv_gather_input":
+        kept = act[2] if len(act) > 2 else 0
+        return 2.0 * m + kept, "gather"      # both parents, then the pre-check of the pairs still crossing
+    if cls == "sv_gather_list":
+        tot = 0.0
+        for i in range(2, len(act)):
+            tot += 2.0 * act[i] + (act[i + 1] if i + 1 < len(act) else 0)
+        return tot, "gather"
+    if cls == "finalize":
+        return 1.0 * n, "gather"
+    return 0.0, "gather"
+
+
 def sources_hash() -> str:
     h = hashlib.sha256()
     for f in KERNEL_FILES:
@@ -116,7 +143,8 @@ def sources_hash() -> str:
 
 
 def ncu_traffic(kernel_cls: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current sources."""
+    """DRAM bytes per launch of a kernel class from the committed ncu summary,
+    if it matches the current sources (None otherwise)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(p))
@@ -124,7 +152,57 @@ def ncu_traffic(kernel_cls: str, workload: str):
         return None
     if d.get("sources_hash") != sources_hash():
         return None
-    return d.get("traffic", {}).get(workload, {}).get(kernel_cls)
+    return d.get("traffic_per_launch", {}).get(workload, {}).get(kernel_cls)
+
+
+def kernel_class(name: str):
+    """Kernel class (the engine's profiling scopes) of a kernel name in an ncu list."""
+    table = [("k_degree_hubs", "degree"), ("k_hub_", "degree"), ("k_degree<", "degree"), ("k_hist", "hist"),
+             ("k_distinct", "ks"), ("k_ks_", "ks"), ("k_parent_init", "parent_init"),
+             ("k_sv_pass<int, 0", "sv_first"), ("k_sv_pass<long, 0", "sv_first"),
+             ("k_sv_pass<int, 2", "sv_gather_input"), ("k_sv_pass<long, 2", "sv_gather_input"),
+             ("k_sv_pass<unsigned int, 2", "sv_gather_list"), ("k_shortcut_all", "sv_shortcut"),
+             ("k_sv_shortcut", "sv_shortcut"), ("k_finalize", "finalize")]
+    for key, cls in table:
+        if key in name:
+            return cls
+    return None
+
+
+def ncu_summary(csv_path: str, workload: str, scale_to: dict, command: str) -> dict:
+    """Mean DRAM bytes per launch of each kernel class from an ncu --csv
+    capture of gpu__time_duration.sum, dram__bytes_read.sum and
+    dram__bytes_write.sum (the same per-launch unit as the roofline's
+    algorithmic bytes: a class's bytes per call / its launches per call).
+    `scale_to` maps another workload to the ratio of its pairs to this one's
+    (the streamed pairs dominate the traffic)."""
+    import csv
+
+    rows = list(csv.reader(open(csv_path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hi]
+    ki, idi, mi, vi = h.index("Kernel Name"), h.index("ID"), h.index("Metric Name"), h.index("Metric Value")
+    launches = {}
+    for r in rows[hi + 1:]:
+        if len(r) <= vi:
+            continue
+        d = launches.setdefault(int(r[idi]), {"name": r[ki]})
+        d[r[mi]] = float(r[vi].replace(",", ""))
+    tot, cnt = {}, {}
+    for L in launches.values():
+        cls = kernel_class(L["name"])
+        if cls is None:
+            continue
+        tot[cls] = tot.get(cls, 0.0) + L.get("dram__bytes_read.sum", 0.0) + L.get("dram__bytes_write.sum", 0.0)
+        cnt[cls] = cnt.get(cls, 0) + 1
+    per = {k: tot[k] / cnt[k] for k in tot}
+    out = {"sources_hash": sources_hash(), "command": command, "launches": cnt,
+           "note": f"mean dram__bytes_read.sum + dram__bytes_write.sum per launch and kernel class, captured on "
+                   f"{workload}" + "".join(f"; {w}: scaled by the pair ratio x{f:g}" for w, f in scale_to.items()),
+           "traffic_per_launch": {workload: per}}
+    for w, f in scale_to.items():
+        out["traffic_per_launch"][w] = {k: v * f for k, v in per.items()}
+    return out
 
 
 class ClockSampler:
@@ -197,6 +275,22 @@ def cpu_oracle_rate(edges: np.ndarray, n: int, budget_pairs: int) -> tuple[float
     return k / dt, k, dt
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time (every rank gets it); `dist` None = one rank."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, m: int, steps: int, ms_total: float) -> float:
+    """Whole-job pairs/s: every rank labels its own replica of the m pairs per step."""
+    return world * m * steps / (ms_total / 1e3)
+
+
 def run_reference(args, world: int, rank: int):
     if rank != 0:
         return 0
@@ -241,7 +335,7 @@ def run_batch(args, world: int, rank: int, local: int) -> int:
     vo_h = torch.from_numpy(b.vertex_offsets)
     eo_d, vo_d = eo_h.to(dev), vo_h.to(dev)
     out = torch.empty(n, dtype=torch.int32, device=dev)
-    eng = cc.Engine(id_bytes=4, device=local, profile=1)
+    eng = cc.Engine(id_bytes=4, device=local, profile=0)  # SV loop as one captured graph
     stream = torch.cuda.current_stream(dev)
     for _ in range(max(args.warmup, 1)):
         eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
@@ -250,19 +344,26 @@ def run_batch(args, world: int, rank: int, local: int) -> int:
     sampler.start()
     time.sleep(0.5)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches, kms, kla = 0, {}, {}
+    launches = 0
     e0.record(stream)
     for _ in range(args.steps):
         eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
-        st = eng.stats()
-        launches += st["launches"]
-        for k, v in st["kernel_ms"].items():
-            kms[k] = kms.get(k, 0.0) + v
-            kla[k] = kla.get(k, 0) + st["kernel_launches"][k]
+        launches += eng.stats()["launches"]
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
+    # per-kernel CUDA events in a second region (profiling on: host-driven loop)
+    eng.set_options(profile=1)
+    eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
+    kms, kla = {}, {}
+    for _ in range(args.steps):
+        eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
+        st = eng.stats()
+        for k, v in st["kernel_ms"].items():
+            kms[k] = kms.get(k, 0.0) + v
+            kla[k] = kla.get(k, 0) + st["kernel_launches"][k]
     clocks = sampler.stop()
+    eng.set_options(profile=0)
     # the same graphs one cc_labels call at a time (each graph in its own aligned buffer)
     per = [edges_d[b.edge_offsets[g]:b.edge_offsets[g + 1]].clone() for g in range(b.G)]
     outs = [torch.empty(int(b.vertex_offsets[g + 1] - b.vertex_offsets[g]), dtype=torch.int32, device=dev)
@@ -323,7 +424,17 @@ def main() -> int:
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ref-pairs", type=int, default=1 << 24, help="pairs per step of the CPU oracle")
     ap.add_argument("--cpu-pairs", type=int, default=1 << 25, help="pairs in the cpu_baseline sample")
+    ap.add_argument("--ncu-summary", metavar="CSV",
+                    help="print the DRAM traffic summary of an ncu --csv capture of --workload and exit")
+    ap.add_argument("--ncu-command", default="", help="the command line of that capture (recorded)")
     args = ap.parse_args()
+    if args.ncu_summary:
+        w = WORKLOADS[args.workload]
+        scale = {}
+        if w["kind"] == "rmat" and w["scale"] < 24:
+            scale["rmat24"] = float(2 ** (24 - w["scale"]))
+        print(json.dumps(ncu_summary(args.ncu_summary, args.workload, scale, args.ncu_command), indent=1))
+        return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -349,7 +460,9 @@ def main() -> int:
     n, m = g.n, g.m
     edges_d = torch.from_numpy(g.edges).to(dev)
     lab = torch.empty(n, dtype=edges_d.dtype, device=dev)
-    eng = cc.Engine(id_bytes=w, route=args.route, device=local, profile=1)
+    # the product path: per-kernel profiling off, so the SV loop runs as one
+    # captured CUDA graph with a device-driven WHILE node
+    eng = cc.Engine(id_bytes=w, route=args.route, device=local, profile=0)
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(max(args.warmup, 1)):
@@ -366,26 +479,37 @@ def main() -> int:
         dist.barrier()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kms, kla, launches = {}, {}, 0
+    launches = 0
     e0.record(stream)
     for _ in range(args.steps):
         eng.labels(edges_d, n, out=lab)
-        st = eng.stats()
-        launches += st["launches"]
-        for k, v in st["kernel_ms"].items():
-            kms[k] = kms.get(k, 0.0) + v
-            kla[k] = kla.get(k, 0) + st["kernel_launches"][k]
+        launches += eng.stats()["launches"]
     e1.record(stream)
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    value = replica_value(world, m, args.steps, ms)
+
+    # second timed region: the same calls with per-kernel CUDA events on the
+    # launching stream (host-driven loop), for the kernel breakdown and roofline
+    eng.set_options(profile=1)
+    eng.labels(edges_d, n, out=lab)
+    torch.cuda.synchronize(dev)
+    kms, kla = {}, {}
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        eng.labels(edges_d, n, out=lab)
+        st = eng.stats()
+        for k, v in st["kernel_ms"].items():
+            kms[k] = kms.get(k, 0.0) + v
+            kla[k] = kla.get(k, 0) + st["kernel_launches"][k]
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_profiled = p0.elapsed_time(p1) / args.steps
     clocks = sampler.stop() if sampler else None
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * m * args.steps / (ms / 1e3)
+    eng.set_options(profile=0)
     last = st
 
     # roofline of the dominant kernel class
@@ -407,6 +531,22 @@ def main() -> int:
     kernels = {k: {"ms_per_step": kms[k] / args.steps, "launches_per_step": kla[k] / args.steps,
                    "gbs": (alg_bytes(k, last, w) / (kms[k] / args.steps / 1e3) / 1e9) if kms[k] > 0 else None}
                for k in kms if kla[k]}
+    # the scattered-access ceiling: measured L2 random-op rates of this GPU (outside the timed region)
+    rates = eng.l2_rates()
+    for k, kv in kernels.items():
+        ops, op = l2_ops(k, last)
+        if ops > 0 and kv["ms_per_step"] > 0:
+            kv["l2_gops"] = ops / (kv["ms_per_step"] / 1e3) / 1e9
+            kv["l2_frac"] = kv["l2_gops"] * 1e9 / rates[op]
+    ops, op = l2_ops(dom, last)
+    l2_roofline = {"bound": "l2_random_ops", "kernel": dom, "op": op,
+                   "ops_per_launch": ops / launches_per_call,
+                   "achieved": ops / launches_per_call / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0,
+                   "peak": rates[op] / 1e9, "unit": "Gop/s",
+                   "peak_source": "measured in this run: 2^28 random 4-byte ops over a 64 MiB table "
+                                  "(cc_measure_l2_rates, best of 3)",
+                   "rates_gops": {r: rates[r] / 1e9 for r in ("gather", "red_add", "red_min", "atom_min")}}
+    l2_roofline["frac"] = l2_roofline["achieved"] / l2_roofline["peak"] if l2_roofline["peak"] else None
 
     # end to end through host buffers: H2D of the pairs, labels, D2H of the labels
     e2e = None
@@ -484,8 +624,13 @@ def main() -> int:
                 "config": cfg | {"route_policy": args.route, "route_taken": "bfs+sv" if last["route"] else "sv",
                                  "ks_d": last["ks_d"], "sv_iters": last["sv_iters"],
                                  "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": launches, "kernels": kernels, "route_compare": route_compare,
+                "roofline": roofline, "l2_roofline": l2_roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks,
+                "gpu_launches": launches,
+                "kernels_note": "per-kernel CUDA events from a second timed region of the same calls with "
+                                "profiling on (host-driven SV loop), "
+                                f"{ms_profiled:.3f} ms/step there vs {ms / args.steps:.3f} ms/step in the main region",
+                "kernels": kernels, "route_compare": route_compare,
                 "stage_ms": {k: last[k] for k in ("ms_degree", "ms_predict", "ms_csr", "ms_bfs", "ms_sv",
                                                   "ms_finalize", "ms_total")},
                 "m_active": last["m_active"]}

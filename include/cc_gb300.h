@@ -303,6 +303,30 @@ cc_status cc_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, fl
 cc_status cc_labels_static(const void *edges_dev, int id_bytes, int64_t n, int64_t m, void *labels_out_dev,
                            void *stream);
 
+/* Measured L2 random-access rates of the context's device: the ceiling of
+ * the kernels whose cost is scattered 4-byte accesses to an L2-resident
+ * array rather than streamed bytes (the degree pass of Section 3.2 and the
+ * hook passes of Section 3.1, on the parent and degree arrays). Each rate is
+ * operations per second of one grid-stride kernel that issues `ops` accesses
+ * to a table of `table_words` 32-bit words at indices from a 64-bit mixing
+ * hash of the operation number; the best of `reps` timed launches (CUDA
+ * events on `stream`) counts.
+ *   out     host struct, written on success
+ *   stream  cudaStream_t as void*; the call synchronises it
+ * The probe allocates and frees its own table (4 * table_words bytes).
+ * Errors: CC_ERR_INVALID_ARG for a null pointer; CC_ERR_CUDA. */
+typedef struct cc_l2_rates {
+    double gather;       /* loads per second */
+    double red_add;      /* atomicAdd with the result unused (RED) */
+    double red_min;      /* atomicMin with the result unused (RED) */
+    double atom_min;     /* atomicMin with the result used (ATOM) */
+    int64_t table_words; /* 2^24 (64 MiB) */
+    int64_t ops;         /* 2^28 per launch */
+    int32_t reps;        /* 3 */
+    int32_t grid;        /* blocks of 256 threads */
+} cc_l2_rates;
+cc_status cc_measure_l2_rates(cc_ctx *ctx, cc_l2_rates *out, void *stream);
+
 /* Statistics of the last cc_labels call; synchronises its stream. Returns the recorded device status. */
 cc_status cc_get_stats(cc_ctx *ctx, cc_stats *out);
 

@@ -81,6 +81,13 @@ _lib = None
 _vp, _i64, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
 
 
+class L2Rates(ctypes.Structure):
+    """cc_l2_rates: measured L2 random-access rates (operations per second)."""
+    _fields_ = [("gather", ctypes.c_double), ("red_add", ctypes.c_double), ("red_min", ctypes.c_double),
+                ("atom_min", ctypes.c_double), ("table_words", ctypes.c_int64), ("ops", ctypes.c_int64),
+                ("reps", ctypes.c_int32), ("grid", ctypes.c_int32)]
+
+
 def lib() -> ctypes.CDLL:
     """The loaded shared library (raises if it has not been built)."""
     global _lib
@@ -105,12 +112,13 @@ def lib() -> ctypes.CDLL:
         L.cc_mlp_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _int, ctypes.c_float, _vp, _vp, _vp, _vp, _vp]
         L.cc_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                   ctypes.c_float, _int, _vp]
+        L.cc_measure_l2_rates.argtypes = [_vp, ctypes.POINTER(L2Rates), _vp]
         L.cc_strerror.argtypes = [_int]
         L.cc_strerror.restype = ctypes.c_char_p
         for f in ("cc_default_options", "cc_create", "cc_set_options", "cc_destroy", "cc_labels",
                   "cc_labels_batched", "cc_degree_distribution", "cc_ks_statistic", "cc_get_stats",
                   "cc_labels_static", "cc_route_features", "cc_set_predictor", "cc_mlp_forward",
-                  "cc_mlp_backward", "cc_mlp_adam"):
+                  "cc_mlp_backward", "cc_mlp_adam", "cc_measure_l2_rates"):
             getattr(L, f).restype = _int
         _lib = L
     return _lib
@@ -263,6 +271,13 @@ class Engine:
             raise ValueError(f"expected {MLP_PARAMS} parameters, got {p.size}")
         _check(lib().cc_set_predictor(self._h, p.ctypes.data_as(ctypes.c_void_p), min_confidence),
                "cc_set_predictor")
+
+    def l2_rates(self, stream=None) -> dict:
+        """Measured L2 random-access rates of this engine's device (cc_measure_l2_rates), in operations/s."""
+        r = L2Rates()
+        _check(lib().cc_measure_l2_rates(self._h, ctypes.byref(r), _stream_handle(stream, self.device)),
+               "cc_measure_l2_rates")
+        return {f: getattr(r, f) for f, _ in L2Rates._fields_}
 
     def stats(self) -> dict:
         s = Stats()

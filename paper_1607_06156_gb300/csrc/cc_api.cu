@@ -62,6 +62,21 @@ struct cc_ctx {
     std::vector<cudaEvent_t> evpool;
     size_t evpool_used = 0;
     std::vector<ProfRec> prof;
+    // captured SV graphs (device-driven loop), one per entry point, keyed by their arguments
+    struct GraphKey {
+        long long n, m, G;
+        const void *edges, *eo, *vo, *labels, *parent, *hooked, *eb0, *eb1, *st;
+        int kind, cap, grid, pad;
+    };
+    struct LoopGraph {
+        cudaGraphExec_t exec = nullptr;
+        GraphKey key{};
+    };
+    LoopGraph g_single, g_batch;
+    cudaStream_t cap_s = nullptr, cap_s2 = nullptr;  // private capture streams
+    // side stream of the speculative first SV pass, with its fork and join events
+    cudaStream_t side_s = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -140,7 +155,7 @@ cc_status ensure_sv(cc_ctx *ctx, size_t n, size_t m) {
     CC_TRY(buf_reserve(ctx, ctx->chunk_nz, (size_t)(ks_num_chunks() + 1) * 8));
     CC_TRY(buf_reserve(ctx, ctx->chunk_mass, (size_t)(ks_num_chunks() + 1) * 8));
     CC_TRY(buf_reserve(ctx, ctx->st, sizeof(DevState)));
-    // BFS visited counts (words 0-1) and the hub-aware degree pass scratch (32-bit words 32..)
+    // BFS visited counts (words 0-1)
     CC_TRY(buf_reserve(ctx, ctx->counters, 4096));
     CC_TRY(buf_reserve(ctx, ctx->bk_count, (size_t)ctx->grid * (bucket_max() + 2) * 4));
     CC_TRY(buf_reserve(ctx, ctx->bk_cursor, (size_t)ctx->grid * (bucket_max() + 2) * 4));
@@ -288,6 +303,140 @@ int default_max_iters(long long n) {
     return c < kMaxIters - 1 ? c : kMaxIters - 1;
 }
 
+// ---------------------------------------------------------------------------
+// SV as one CUDA graph: the fixed prefix (`pre`: parent init, the first two
+// passes and their shortcuts), a WHILE node whose body is one SV iteration
+// over the compacted list (k_sv_pass_loop, k_sv_shortcut, k_sv_loop_step:
+// the device decides whether another iteration runs), and the fixed suffix
+// (`post`: the labels). One graph launch replaces a host round trip per
+// iteration. Graphs are captured on private streams (the caller's stream
+// may be the legacy default stream, which cannot be captured) and cached
+// per entry point while their arguments stay the same.
+
+cc_ctx::GraphKey graph_key(cc_ctx *ctx, int kind, long long n, long long m, long long G, const void *edges,
+                           const void *eo, const void *vo, const void *labels, int cap) {
+    cc_ctx::GraphKey k;
+    memset(&k, 0, sizeof(k));
+    k.n = n;
+    k.m = m;
+    k.G = G;
+    k.edges = edges;
+    k.eo = eo;
+    k.vo = vo;
+    k.labels = labels;
+    k.parent = ctx->parent.p;
+    k.hooked = ctx->hooked.p;
+    k.eb0 = ctx->ebuf0.p;
+    k.eb1 = ctx->ebuf1.p;
+    k.st = ctx->st.p;
+    k.kind = kind;
+    k.cap = cap;
+    k.grid = ctx->grid;
+    return k;
+}
+
+void graph_drop(cc_ctx::LoopGraph &lg) {
+    if (lg.exec) cudaGraphExecDestroy(lg.exec);
+    lg.exec = nullptr;
+}
+
+template <typename Pre, typename Post>
+cc_status capture_sv_graph(cc_ctx *ctx, vid_t n, int it0, int cur0, int cap, Pre pre, Post post,
+                           cudaGraphExec_t *out) {
+    if (!ctx->cap_s) CU_TRY(cudaStreamCreateWithFlags(&ctx->cap_s, cudaStreamNonBlocking));
+    if (!ctx->cap_s2) CU_TRY(cudaStreamCreateWithFlags(&ctx->cap_s2, cudaStreamNonBlocking));
+    cudaStream_t cs = ctx->cap_s, cs2 = ctx->cap_s2;
+    DevState *st = as<DevState>(ctx->st);
+    CU_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    auto abort = [&](cudaError_t e) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(cs, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        const cc_status r = cuda_status(e);
+        return r == CC_OK ? CC_ERR_CUDA : r;
+    };
+    pre(cs);
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edata = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, &edata, &ndeps);
+    if (e != cudaSuccess || cst != cudaStreamCaptureStatusActive) return abort(e);
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return abort(e);
+    launch_sv_loop_init(st, it0, cur0, cap, h, cs);
+    if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, &edata, &ndeps)) != cudaSuccess)
+        return abort(e);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    if ((e = cudaGraphAddNode(&cnode, graph, deps, edata, ndeps, &cp)) != cudaSuccess) return abort(e);
+    if ((e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+        return abort(e);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+        cudaSuccess)
+        return abort(e);
+    launch_sv_loop_body(as<uint2>(ctx->ebuf0), as<uint2>(ctx->ebuf1), n, as<vid_t>(ctx->parent),
+                        as<vid_t>(ctx->hooked), st, h, ctx->grid, cs2);
+    cudaGraph_t body_out = nullptr;
+    if ((e = cudaStreamEndCapture(cs2, &body_out)) != cudaSuccess) return abort(e);
+    post(cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return CC_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return CC_ERR_CUDA;
+    }
+    return CC_OK;
+}
+
+// Launches the cached graph for `key` (capturing it first if the key changed).
+template <typename Pre, typename Post>
+cc_status launch_sv_graph(cc_ctx *ctx, cc_ctx::LoopGraph &lg, const cc_ctx::GraphKey &key, vid_t n, int it0,
+                          int cur0, int cap, Pre pre, Post post, cudaStream_t s) {
+    if (!lg.exec || memcmp(&lg.key, &key, sizeof(key)) != 0) {
+        graph_drop(lg);
+        CC_TRY(capture_sv_graph(ctx, n, it0, cur0, cap, pre, post, &lg.exec));
+        lg.key = key;
+    }
+    CU_TRY(cudaGraphLaunch(lg.exec, s));
+    return CC_OK;
+}
+
+// After a graph launch: waits, fills the iteration statistics (iteration it0
+// and those before it are the prefix's) and returns the device status.
+cc_status sv_graph_finish(cc_ctx *ctx, int it0, int prefix_launches, cudaStream_t s) {
+    DevState *st = as<DevState>(ctx->st);
+    cc_stats &S = ctx->stats;
+    CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, hook_base), cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    CU_TRY(cudaGetLastError());
+    const DevState *h = ctx->h_st;
+    const int done = h->loop_done > it0 ? h->loop_done : it0 + 1;
+    for (int i = it0 + 1; i < done && i < CC_MAX_SV_ITERS_RECORDED; i++) S.m_active[i] = (int64_t)h->kept[i - 1];
+    for (int i = 0; i < CC_MAX_SV_ITERS_RECORDED && i < done; i++) S.sv_hooks[i] = (int64_t)h->hooked[i];
+    S.sv_iters = done;
+    // prefix + loop init + 3 per loop iteration + the labels kernel
+    S.launches += prefix_launches + 1 + 3 * (done - 1 - it0) + 1;
+    return device_error(h->err);
+}
+
 BucketScratch bucket_scratch(cc_ctx *ctx) {
     return BucketScratch{as<uint32_t>(ctx->bk_count), as<uint32_t>(ctx->bk_cursor), as<unsigned long long>(ctx->bk_off)};
 }
@@ -307,11 +456,11 @@ template <typename T>
 void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s) {
     cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s);
     cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
-    if (degree_uses_hubs(m)) {
-        Scope sc(ctx, CC_K_DEGREE, s, 4);
-        unsigned *scr = as<unsigned>(ctx->counters) + 16;  // 34 words after the BFS counters
-        launch_degree_hubs<T>(edges, m, n, as<uint32_t>(ctx->deg), scr, scr + 40, as<DevState>(ctx->st), ctx->grid,
-                              s);
+    if (degree_uses_hubs(m) && ctx->ebuf0.bytes >= degree_hubs_scratch_bytes()) {
+        Scope sc(ctx, CC_K_DEGREE, s, 5);
+        // the pair buffers are idle until the first SV pass; m >= 2^24 makes ebuf0 far larger than the scratch
+        launch_degree_hubs<T>(edges, m, n, as<uint32_t>(ctx->deg), as<unsigned>(ctx->ebuf0), as<DevState>(ctx->st),
+                              ctx->grid, ctx->num_sms, s);
     } else {
         Scope sc(ctx, CC_K_DEGREE, s, m > 0);
         launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), as<DevState>(ctx->st), ctx->grid, s);
@@ -547,6 +696,26 @@ cc_status run_bfs_edges(cc_ctx *ctx, const void *edges, vid_t n, long long m, cu
     return CC_OK;
 }
 
+cc_status ensure_side(cc_ctx *ctx) {
+    if (!ctx->side_s) CU_TRY(cudaStreamCreateWithFlags(&ctx->side_s, cudaStreamNonBlocking));
+    if (!ctx->ev_fork) CU_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    if (!ctx->ev_join) CU_TRY(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    return CC_OK;
+}
+
+// Orders all later work on `s` after the side stream's speculative pass, on
+// every exit path (the next call must not reset state the side stream uses).
+struct JoinGuard {
+    cc_ctx *ctx;
+    cudaStream_t s;
+    bool armed = false;
+    void join() {
+        if (armed) cudaStreamWaitEvent(s, ctx->ev_join, 0);
+        armed = false;
+    }
+    ~JoinGuard() { join(); }
+};
+
 template <typename T>
 cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void *labels_out, cudaStream_t s) {
     DevState *st = as<DevState>(ctx->st);
@@ -562,6 +731,38 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     int route = 0;
     S.route_source = policy == CC_ROUTE_AUTO || policy == CC_ROUTE_LEARNED ? 0 : 2;
     vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
+    // Speculative first SV pass. On the SV route the first pass needs nothing
+    // the prediction computes (every vertex starts as its own root), so the
+    // parent init, the unrecorded hook pass and the full shortcut run on a
+    // side stream while the route prediction runs on `s`. It is forked after
+    // the degree pass (both are bound by scattered L2 operations, so running
+    // them together gains nothing) to overlap the K-S fit, or at the start
+    // of the learned route's sampled features. The BFS route re-initialises
+    // the parent array after its BFS, so the speculative work is then unused.
+    JoinGuard spec{ctx, s};
+    auto speculate = [&]() -> cc_status {
+        if (spec.armed || m <= 0) return CC_OK;
+        CC_TRY(ensure_side(ctx));
+        cudaStream_t side = ctx->side_s;
+        CU_TRY(cudaEventRecord(ctx->ev_fork, s));
+        CU_TRY(cudaStreamWaitEvent(side, ctx->ev_fork, 0));
+        {
+            Scope sc(ctx, CC_K_PARENT_INIT, side, 1);
+            launch_parent_init(parent, n, nullptr, 0, ctx->grid, side);
+        }
+        {
+            Scope sc(ctx, CC_K_SV_FIRST, side, 1);
+            launch_sv_pass<T>(0, false, false, edges, m, n, parent, nullptr, 0, hooked, nullptr, st, 0, ctx->grid,
+                              side);
+        }
+        {
+            Scope sc(ctx, CC_K_SV_SHORTCUT, side, 1);
+            launch_shortcut_all(parent, n, st, 0, ctx->grid, side);
+        }
+        CU_TRY(cudaEventRecord(ctx->ev_join, side));
+        spec.armed = true;
+        return CC_OK;
+    };
     int cutoff = ctx->opt.bfs_cutoff_levels;
     // Learned route: sampled features + network; a confident prediction skips
     // the exact degree pass and the K-S fit (its BFS is the edge-list BFS,
@@ -570,6 +771,7 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     S.pred_route = -1;
     if (policy == CC_ROUTE_LEARNED && ctx->have_pred && m > 0) {
         CC_TRY(ensure_feat(ctx, n));
+        CC_TRY(speculate());
         {
             Scope sc(ctx, CC_K_PREDICT, s, 12);
             launch_route_features<T>(edges, m, n, feat_scratch(ctx), st, as<float>(ctx->f_x), ctx->grid, s);
@@ -593,7 +795,10 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     if (!learned && policy != CC_ROUTE_FORCE_SV && m > 0) {
         enqueue_degree<T>(ctx, edges, n, m, s);
         rec(ctx, EV_DEGREE, s);
-        if (policy != CC_ROUTE_FORCE_BFS) enqueue_ks(ctx, s, distinct_degree_bound(ctx, n, m));
+        if (policy != CC_ROUTE_FORCE_BFS) {
+            CC_TRY(speculate());
+            enqueue_ks(ctx, s, distinct_degree_bound(ctx, n, m));
+        }
         rec(ctx, EV_PREDICT, s);
         CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, kept), cudaMemcpyDeviceToHost, s));
         CU_TRY(cudaStreamSynchronize(s));
@@ -608,6 +813,8 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         S.seed_vertex = (int64_t)(0xffffffffu - (uint32_t)(ctx->h_st->maxkey & 0xffffffffu));
         if (policy == CC_ROUTE_FORCE_BFS) S.ks_d = 0.0;
     }
+    const bool speculated = spec.armed;
+    spec.join();  // later work on `s` sees the speculative pass complete
     // the learned route always takes the edge-list BFS (it needs no exact
     // degrees); the CSR uses 32-bit offsets, so the CSR BFS needs 2m < 2^32
     const bool edge_bfs = learned || ctx->opt.bfs_mode == 1;
@@ -667,20 +874,44 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         m_cur = ctx->h_st->kept[0];
         src = eb[cur0];
     } else {
-        {
+        if (m > 0 && cap >= 2 && !ctx->opt.profile) {
+            // the whole SV route as one cached graph with a device-driven loop
+            auto pre = [&](cudaStream_t cs) {
+                if (!speculated) {
+                    launch_parent_init(parent, n, nullptr, 0, ctx->grid, cs);
+                    launch_sv_pass<T>(0, false, false, edges, m, n, parent, nullptr, 0, hooked, nullptr, st, 0,
+                                      ctx->grid, cs);
+                    launch_shortcut_all(parent, n, st, 0, ctx->grid, cs);
+                }
+                launch_sv_pass<T>(2, true, true, edges, m, n, parent, nullptr, 0, hooked, eb[0], st, 1, ctx->grid, cs);
+                launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, cs);
+            };
+            auto post = [&](cudaStream_t cs) { launch_finalize<T>(parent, n, labels_out, ctx->grid, cs); };
+            const cc_ctx::GraphKey key = graph_key(ctx, (sizeof(T) == 4 ? 0 : 1) | (speculated ? 4 : 0), n, m, 0,
+                                                   edges, nullptr, nullptr, labels_out, cap);
+            CC_TRY(launch_sv_graph(ctx, ctx->g_single, key, n, 1, 0, cap, pre, post, s));
+            rec(ctx, EV_SV, s);
+            rec(ctx, EV_END, s);
+            S.m_active[0] = m;
+            S.m_active[1] = m;
+            return sv_graph_finish(ctx, 1, speculated ? 2 : 5, s);
+        }
+        if (!speculated) {
             Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
             launch_parent_init(parent, n, nullptr, 0, ctx->grid, s);
         }
         if (m > 0) {
             // every vertex is a root here: hook without recording, then shortcut all vertices
-            {
-                Scope sc(ctx, CC_K_SV_FIRST, s, 1);
-                launch_sv_pass<T>(0, false, false, edges, m, n, parent, nullptr, 0, hooked, nullptr, st, 0, ctx->grid,
-                                  s);
-            }
-            {
-                Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
-                launch_shortcut_all(parent, n, st, 0, ctx->grid, s);
+            if (!speculated) {
+                {
+                    Scope sc(ctx, CC_K_SV_FIRST, s, 1);
+                    launch_sv_pass<T>(0, false, false, edges, m, n, parent, nullptr, 0, hooked, nullptr, st, 0,
+                                      ctx->grid, s);
+                }
+                {
+                    Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
+                    launch_shortcut_all(parent, n, st, 0, ctx->grid, s);
+                }
             }
             S.m_active[0] = m;
             it = 1;
@@ -794,6 +1025,13 @@ cc_status cc_destroy(cc_ctx *ctx) {
     for (int e = 0; e < EV_COUNT; e++)
         if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
     for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+    graph_drop(ctx->g_single);
+    graph_drop(ctx->g_batch);
+    if (ctx->side_s) cudaStreamDestroy(ctx->side_s);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->cap_s) cudaStreamDestroy(ctx->cap_s);
+    if (ctx->cap_s2) cudaStreamDestroy(ctx->cap_s2);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     delete ctx;
     return CC_OK;
@@ -869,6 +1107,34 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
     {
         Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
         launch_parent_init(parent, nt, nullptr, 0, ctx->grid, s);
+    }
+    if (m > 0 && cap >= 2 && !ctx->opt.profile) {
+        // one cached graph with a device-driven loop (the parent init above stays outside)
+        uint2 *eb0 = as<uint2>(ctx->ebuf0);
+        auto pre = [&](cudaStream_t cs) {
+            launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,
+                                 hooked, nullptr, st, 0, ctx->grid, cs);
+            launch_shortcut_all(parent, nt, st, 0, ctx->grid, cs);
+            launch_sv_pass_batch(2, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,
+                                 hooked, eb0, st, 1, ctx->grid, cs);
+            launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, cs);
+        };
+        auto post = [&](cudaStream_t cs) {
+            launch_finalize_batch(parent, nt, vertex_offsets_dev, G, (int32_t *)labels_out_dev, ctx->grid, cs);
+        };
+        const cc_ctx::GraphKey key =
+            graph_key(ctx, 2, n, m, G, edges_dev, edge_offsets_dev, vertex_offsets_dev, labels_out_dev, cap);
+        cc_status gs = launch_sv_graph(ctx, ctx->g_batch, key, nt, 1, 0, cap, pre, post, s);
+        if (gs == CC_OK) {
+            rec(ctx, EV_SV, s);
+            rec(ctx, EV_END, s);
+            S.m_active[0] = m;
+            S.m_active[1] = m;
+            gs = sv_graph_finish(ctx, 1, 4, s);
+        }
+        ctx->last_status = gs;
+        S.status = gs;
+        return gs;
     }
     unsigned long long m_cur = 0;
     int it = 0;
@@ -1029,6 +1295,49 @@ cc_status cc_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, fl
     if (!params_dev || !grad_dev || !m_dev || !v_dev || count <= 0 || t < 1) return CC_ERR_INVALID_ARG;
     mlp_adam(params_dev, grad_dev, m_dev, v_dev, count, lr, beta1, beta2, eps, t, (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
+}
+
+cc_status cc_measure_l2_rates(cc_ctx *ctx, cc_l2_rates *out, void *stream) {
+    if (!ctx || !out) return CC_ERR_INVALID_ARG;
+    CU_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long words = 1LL << 24, ops = 1LL << 28;
+    const int reps = 3, grid = ctx->num_sms * 16;
+    uint32_t *table = nullptr;
+    CU_TRY(cudaMalloc(&table, (size_t)words * 4 + 64));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cc_status rc = CC_OK;
+    double rate[4] = {0, 0, 0, 0};
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMemsetAsync(table, 0xff, (size_t)words * 4 + 64, s) != cudaSuccess)
+        rc = CC_ERR_CUDA;
+    for (int kind = 0; kind < 4 && rc == CC_OK; kind++) {
+        launch_l2_probe(kind, table, (uint32_t)(words - 1), ops, table + words, grid, s);  // warm-up
+        for (int r = 0; r < reps && rc == CC_OK; r++) {
+            float ms = 0.f;
+            if (cudaEventRecord(e0, s) != cudaSuccess) rc = CC_ERR_CUDA;
+            launch_l2_probe(kind, table, (uint32_t)(words - 1), ops, table + words, grid, s);
+            if (rc != CC_OK || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                rc = CC_ERR_CUDA;
+            else if (ms > 0.f && (double)ops / (ms * 1e-3) > rate[kind])
+                rate[kind] = (double)ops / (ms * 1e-3);
+        }
+    }
+    if (rc == CC_OK && cudaGetLastError() != cudaSuccess) rc = CC_ERR_CUDA;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(table);
+    if (rc != CC_OK) return rc;
+    out->gather = rate[0];
+    out->red_add = rate[1];
+    out->red_min = rate[2];
+    out->atom_min = rate[3];
+    out->table_words = words;
+    out->ops = ops;
+    out->reps = reps;
+    out->grid = grid;
+    return CC_OK;
 }
 
 cc_status cc_get_stats(cc_ctx *ctx, cc_stats *out) {

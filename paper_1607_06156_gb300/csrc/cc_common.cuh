@@ -47,6 +47,11 @@ struct DevState {
     float pred_conf;                        // probability of the predicted route
     int pred_cutoff;                        // BFS levels (0 = run to completion)
     int pad2;
+    // device-driven SV loop (CUDA graph WHILE node)
+    int loop_it;                            // iteration being run
+    int loop_cur;                           // active pairs of iteration loop_it are in ebuf[loop_cur]
+    int loop_cap;                           // iteration cap
+    int loop_done;                          // iterations run when the loop stopped (0 = not stopped)
     unsigned long long kept[kMaxIters];     // active pairs written by SV iteration i
     unsigned long long hooked[kMaxIters];   // roots hooked in SV iteration i
     unsigned long long hook_base[kMaxIters + 1];  // start of iteration i's slice of the hooked list

@@ -59,8 +59,9 @@ template <typename T>
 void launch_degree(const void *edges, long long m, vid_t n, uint32_t *deg, DevState *st, int grid, cudaStream_t s);
 bool degree_uses_hubs(long long m);
 template <typename T>
-void launch_degree_hubs(const void *edges, long long m, vid_t n, uint32_t *deg, unsigned *scratch, uint32_t *hubs,
-                        DevState *st, int grid, cudaStream_t s);
+void launch_degree_hubs(const void *edges, long long m, vid_t n, uint32_t *deg, unsigned *scratch, DevState *st,
+                        int grid, int num_sms, cudaStream_t s);
+size_t degree_hubs_scratch_bytes();
 void launch_hist(const uint32_t *deg, vid_t n, uint32_t *hist, uint32_t *ovf, unsigned long long ovf_cap,
                  DevState *st, int grid, cudaStream_t s);
 void launch_ks(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf_cap, KsScratch ks, DevState *st,
@@ -84,6 +85,10 @@ void launch_finalize_batch(vid_t *parent, vid_t ntot, const int64_t *vo, int G, 
                            cudaStream_t s);
 
 void launch_sv_shortcut(vid_t *parent, const vid_t *hooked_list, DevState *st, int it, int grid, cudaStream_t s);
+// device-driven loop: init before a WHILE node on handle h, body inside it
+void launch_sv_loop_init(DevState *st, int it0, int cur0, int cap, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_sv_loop_body(const uint2 *eb0, const uint2 *eb1, vid_t n, vid_t *parent, vid_t *hooked_list,
+                         DevState *st, cudaGraphConditionalHandle h, int grid, cudaStream_t s);
 void launch_parent_init(vid_t *parent, vid_t n, const uint32_t *vis, vid_t cmin, int grid, cudaStream_t s);
 template <typename T>
 void launch_finalize(vid_t *parent, vid_t n, void *labels, int grid, cudaStream_t s);
@@ -120,4 +125,8 @@ void launch_edge_bfs_seed(uint32_t *vis, uint32_t *cur, vid_t n, const unsigned 
 namespace ccg {
 void mlp_prepare_inference(const float *P, __nv_bfloat16 *Wb, float *bias, cudaStream_t s);
 void mlp_infer(const __nv_bfloat16 *Wb, const float *bias, const float *x, DevState *st, cudaStream_t s);
+// k_probe.cu
+void launch_l2_probe(int kind, uint32_t *table, uint32_t mask, long long ops, uint32_t *sink, int grid,
+                     cudaStream_t s);
+
 }  // namespace ccg

@@ -80,9 +80,9 @@ template <typename T> struct PassUnroll { static constexpr int U = 2; };
 template <> struct PassUnroll<int64_t> { static constexpr int U = 4; };
 
 template <typename T, int MODE, bool WRITE, bool RECORD>
-__global__ void __launch_bounds__(kBlock) k_sv_pass(const T *__restrict__ in, long long m, vid_t n, vid_t *parent,
-                                                    const uint32_t *__restrict__ vis, vid_t cmin, vid_t *hooked_list,
-                                                    uint2 *__restrict__ out, DevState *st, int it) {
+__device__ __forceinline__ void sv_pass_body(const T *__restrict__ in, long long m, vid_t n, vid_t *parent,
+                                             const uint32_t *__restrict__ vis, vid_t cmin, vid_t *hooked_list,
+                                             uint2 *__restrict__ out, DevState *st, int it) {
     constexpr int P = PairVec<T>::kPairs;
     constexpr int U = PassUnroll<T>::U;
     constexpr int K = P * U;  // pairs per thread per round
@@ -148,6 +148,62 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass(const T *__restrict__ in, lo
     if (bad) set_err(st, kErrInvalidEdge);
 }
 
+template <typename T, int MODE, bool WRITE, bool RECORD>
+__global__ void __launch_bounds__(kBlock) k_sv_pass(const T *__restrict__ in, long long m, vid_t n, vid_t *parent,
+                                                    const uint32_t *__restrict__ vis, vid_t cmin, vid_t *hooked_list,
+                                                    uint2 *__restrict__ out, DevState *st, int it) {
+    sv_pass_body<T, MODE, WRITE, RECORD>(in, m, n, parent, vis, cmin, hooked_list, out, st, it);
+}
+
+// ---------------------------------------------------------------------------
+// Device-driven SV loop (the body of a CUDA graph WHILE node). The iteration
+// number, the ping-pong buffer and the active-pair count live in DevState,
+// so the loop runs with no host round trip per iteration:
+//   k_sv_loop_init   after iteration it0 (whose pairs are in eb[cur0]): stop
+//                    if nothing stayed active, else start iteration it0 + 1
+//   k_sv_pass_loop   hook pass over the active list of iteration loop_it
+//   k_sv_shortcut_loop
+//   k_sv_loop_step   continue while pairs stayed active; past the iteration
+//                    cap the loop stops with kErrNoConvergence
+// The host loop it replaces ends identically (same iterations, same lists).
+
+__device__ __forceinline__ void sv_loop_decide(DevState *st, int it, cudaGraphConditionalHandle h) {
+    // `it` is the iteration just completed
+    if (st->kept[it] == 0) {
+        st->loop_done = it + 1;
+        cudaGraphSetConditional(h, 0u);
+    } else if (it + 1 >= st->loop_cap) {
+        set_err(st, kErrNoConvergence);
+        st->loop_done = it + 1;
+        cudaGraphSetConditional(h, 0u);
+    } else {
+        st->loop_it = it + 1;
+        cudaGraphSetConditional(h, 1u);
+    }
+}
+
+__global__ void k_sv_loop_init(DevState *st, int it0, int cur0, int cap, cudaGraphConditionalHandle h) {
+    st->loop_cap = cap < kMaxIters ? cap : kMaxIters;
+    st->loop_cur = cur0;
+    sv_loop_decide(st, it0, h);
+}
+
+__global__ void __launch_bounds__(kBlock) k_sv_pass_loop(const uint2 *eb0, const uint2 *eb1, vid_t n, vid_t *parent,
+                                                         vid_t *hooked_list, DevState *st) {
+    const int it = st->loop_it, cur = st->loop_cur;
+    const long long m = (long long)st->kept[it - 1];
+    const uint2 *in = cur ? eb1 : eb0;
+    uint2 *out = const_cast<uint2 *>(cur ? eb0 : eb1);
+    sv_pass_body<uint32_t, 2, true, true>(reinterpret_cast<const uint32_t *>(in), m, n, parent, nullptr, 0,
+                                          hooked_list, out, st, it);
+}
+
+__global__ void k_sv_loop_step(DevState *st, cudaGraphConditionalHandle h) {
+    const int it = st->loop_it;
+    st->loop_cur ^= 1;
+    sv_loop_decide(st, it, h);
+}
+
 // Chase from x to its root with path halving. No hook runs while a shortcut
 // kernel runs, so every value written is an ancestor of the vertex it is
 // written to; the writes are atomicMin, so a stale halving write of one
@@ -179,9 +235,10 @@ __global__ void __launch_bounds__(kBlock) k_shortcut_all(vid_t *parent, vid_t n,
     if (gtid() == 0) st->hook_base[it + 1] = st->hook_base[it] + st->hooked[it];
 }
 
-// Shortcut of the roots hooked in iteration `it`.
+// Shortcut of the roots hooked in iteration `it` (it < 0: DevState::loop_it).
 __global__ void __launch_bounds__(kBlock) k_sv_shortcut(vid_t *parent, const vid_t *__restrict__ hooked_list,
                                                         DevState *st, int it) {
+    if (it < 0) it = st->loop_it;
     const unsigned long long base = st->hook_base[it], cnt = st->hooked[it];
     for (long long i = gtid(); i < (long long)cnt; i += gstride()) shortcut_to_root(parent, hooked_list[base + i]);
     if (gtid() == 0) st->hook_base[it + 1] = base + cnt;
@@ -399,6 +456,17 @@ void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid,
 
 void launch_sv_shortcut(vid_t *parent, const vid_t *hooked_list, DevState *st, int it, int grid, cudaStream_t s) {
     k_sv_shortcut<<<grid, kBlock, 0, s>>>(parent, hooked_list, st, it);
+}
+
+void launch_sv_loop_init(DevState *st, int it0, int cur0, int cap, cudaGraphConditionalHandle h, cudaStream_t s) {
+    k_sv_loop_init<<<1, 1, 0, s>>>(st, it0, cur0, cap, h);
+}
+
+void launch_sv_loop_body(const uint2 *eb0, const uint2 *eb1, vid_t n, vid_t *parent, vid_t *hooked_list,
+                         DevState *st, cudaGraphConditionalHandle h, int grid, cudaStream_t s) {
+    k_sv_pass_loop<<<grid, kBlock, 0, s>>>(eb0, eb1, n, parent, hooked_list, st);
+    k_sv_shortcut<<<grid, kBlock, 0, s>>>(parent, hooked_list, st, -1);
+    k_sv_loop_step<<<1, 1, 0, s>>>(st, h);
 }
 
 void launch_parent_init(vid_t *parent, vid_t n, const uint32_t *vis, vid_t cmin, int grid, cudaStream_t s) {

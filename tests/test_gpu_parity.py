@@ -317,3 +317,28 @@ def test_hub_aware_degree_pass(id_bytes, extra):
     got, st = run_engine(e, g.n, route="auto")
     assert np.array_equal(got, oracle.cc_labels(e, g.n, cross_check=False))
     assert st["max_degree"] == int(deg_o.max())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["uniform", "star"])
+def test_hub_aware_degree_pass_extremes(kind):
+    """No vertex clears the hub threshold (uniform pairs: every prefix count
+    is small), or one vertex is an endpoint of every pair (its per-block
+    shared-memory count runs into the hundreds of thousands)."""
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    m = (1 << 24) + 5
+    rng = np.random.default_rng(41)
+    if kind == "uniform":
+        n = 1 << 23
+        e = rng.integers(0, n, size=(m, 2), dtype=np.int64).astype(np.int32)
+    else:
+        n = 1 << 20
+        e = np.stack([np.full(m, 12345), rng.integers(0, n, size=m)], axis=1).astype(np.int32)
+    deg_o = oracle.degrees(e, n)
+    eng = cc.Engine(id_bytes=4)
+    deg, hist = eng.degree_distribution(torch.from_numpy(e).cuda(), n, hist_len=int(deg_o.max()) + 1)
+    assert np.array_equal(deg.cpu().numpy().astype(np.int64), deg_o)
+    assert np.array_equal(hist.cpu().numpy(), oracle.histogram(deg_o))
+    eng.close()

@@ -122,3 +122,18 @@ def test_learned_route_labels_exact_and_fallback():
                 else:
                     assert st["route_source"] == 0
     del rng
+
+
+def test_trained_predictor_gains_over_the_heuristic():
+    """The committed network (trained on 20,000 seeded graphs) against the
+    K-S heuristic on graphs it was not trained on (another seed): labels
+    identical on every graph, and less total time. The learned route reads a
+    1/16 vertex sample instead of the exact degree pass and K-S fit."""
+    torch_cuda()
+    from paper_1607_06156_gb300.train_predictor import default_weights_path, evaluate, load_params
+
+    params, n_train = load_params(default_weights_path())
+    assert n_train >= 20000
+    summ = evaluate(params, count=30, seed=777, big=0, log=lambda *a, **k: None)
+    assert summ["labels_equal"]
+    assert summ["gain_learned_over_heuristic"] > 1.1, summ["gain_learned_over_heuristic"]

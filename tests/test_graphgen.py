@@ -54,3 +54,4 @@ def test_batch_offsets_and_local_ids():
             assert gr.edges.min() >= 0 and gr.edges.max() < gr.n
         if g % 3 == 0:
             assert gr.m == 8 * gr.n
+
