@@ -50,7 +50,8 @@ WORKLOADS = {
     "batch4096": dict(kind="batch", seed=1, G=4096, nmin=1000, nmax=1_000_000),
     "batch512": dict(kind="batch", seed=1, G=512, nmin=1000, nmax=1_000_000),
 }
-KERNEL_FILES = ["cc_common.cuh", "k_degree.cu", "k_sv.cu", "k_bfs.cu", "k_bucket.cu", "cc_api.cu"]
+KERNEL_FILES = ["cc_common.cuh", "ks_math.cuh", "k_degree.cu", "k_sv.cu", "k_bfs.cu", "k_bucket.cu", "k_batch_route.cu",
+                "cc_api.cu"]
 
 
 def make_graph(name: str):
@@ -386,6 +387,17 @@ def run_batch(args, world: int, rank: int, local: int) -> int:
         raise SystemExit("batched labels differ from the per-graph calls")
     dom = max(kms, key=lambda k: kms[k])
     kernels = {k: {"ms_per_step": kms[k] / args.steps, "launches_per_step": kla[k] / args.steps} for k in kms if kla[k]}
+    # the same batch with the route prediction skipped (every graph SV only)
+    sv = cc.Engine(id_bytes=4, device=local, route="sv")
+    sv.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    for _ in range(loops):
+        sv.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
+    c.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_sv = a.elapsed_time(c) / loops
+    sv.close()
     line = {"metric": METRIC + " [batched form]", "value": m / (ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -394,6 +406,10 @@ def run_batch(args, world: int, rank: int, local: int) -> int:
                        "l2": "inputs larger than L2 (no flush)"},
             "vs_per_graph_loop": {"value": m / (ms_loop / 1e3), "ms_per_step": ms_loop,
                                   "speedup": ms_loop / ms, "labels_identical": same},
+            "sv_only_batched": {"value": m / (ms_sv / 1e3), "ms_per_step": ms_sv,
+                                "note": "route prediction skipped (CC_ROUTE_FORCE_SV)"},
+            "route_policy": "auto (a K-S fit per graph)", "graphs_routed_bfs": st["route"],
+            "schedule": {"unroll": st["batch_unroll"], "grid_mult": st["batch_grid_mult"]},
             "dominant_kernel": dom, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
             "sv_iters": st["sv_iters"], "m_active": st["m_active"]}
     print(json.dumps(line), flush=True)
@@ -548,32 +564,30 @@ def main() -> int:
                    "rates_gops": {r: rates[r] / 1e9 for r in ("gather", "red_add", "red_min", "atom_min")}}
     l2_roofline["frac"] = l2_roofline["achieved"] / l2_roofline["peak"] if l2_roofline["peak"] else None
 
-    # end to end through host buffers: H2D of the pairs, labels, D2H of the labels
+    # end to end through host buffers with the public host-input call
+    # (cc_labels_host): the H2D copy of the pairs (chunked, overlapped with the
+    # passes that stream them) and the D2H copy of the labels are inside the
+    # timed region
     e2e = None
     if rank == 0 or world > 1:
         h_edges = torch.from_numpy(g.edges).pin_memory()
         h_lab = torch.empty(n, dtype=lab.dtype).pin_memory()
-        d_edges = torch.empty_like(edges_d)
-        eng.set_options(profile=0)
         steps_e2e = max(3, min(args.steps, 10))
         for _ in range(2):
-            d_edges.copy_(h_edges, non_blocking=True)
-            eng.labels(d_edges, n, out=lab)
-            h_lab.copy_(lab, non_blocking=True)
+            eng.labels_host(h_edges, n, out=h_lab)
+        if not torch.equal(h_lab, lab.cpu()):
+            raise SystemExit("cc_labels_host labels differ from cc_labels")
         torch.cuda.synchronize(dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(steps_e2e):
-            d_edges.copy_(h_edges, non_blocking=True)
-            eng.labels(d_edges, n, out=lab)
-            h_lab.copy_(lab, non_blocking=True)
+            eng.labels_host(h_edges, n, out=h_lab)
         b.record(stream)
         torch.cuda.synchronize(dev)
-        t_e2e = a.elapsed_time(b) / steps_e2e
+        t_e2e = max_over_ranks(a.elapsed_time(b) / steps_e2e, dist, dev)
         e2e = {"value": world * m / (t_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(g.edges.nbytes),
-               "d2h_bytes_per_step": int(n * lab.element_size()), "ms_per_step": t_e2e}
-        del d_edges
-        eng.set_options(profile=1)
+               "d2h_bytes_per_step": int(n * lab.element_size()), "ms_per_step": t_e2e,
+               "call": "cc_labels_host (pinned host buffers)"}
 
     # the forced routes on the same graph (the paper's dynamic-vs-opposite
     # comparison), the edge-list BFS engine, and the learned route with the

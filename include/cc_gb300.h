@@ -142,6 +142,8 @@ typedef struct {
     int pred_route;                     /* learned policy: predicted route (-1 if none) */
     int pred_cutoff;                    /* learned policy: predicted BFS cutoff (0 = none) */
     float ms_features;                  /* learned policy: device time of features + inference */
+    int32_t batch_unroll;               /* batched form: tuned 16-byte vectors per thread per tile of the hook passes */
+    int32_t batch_grid_mult;            /* batched form: tuned blocks per launch, in resident-grid multiples */
 } cc_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -174,7 +176,39 @@ cc_status cc_destroy(cc_ctx *ctx);
 cc_status cc_labels(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, void *labels_out_dev, void *stream);
 
 /*
- * Labels of G independent graphs in one call (the batched form).
+ * cc_labels for a graph whose pairs and labels are in host memory (Algorithm
+ * 2, Section 3.2). With the K-S route or forced SV, m >= 2^24 and no
+ * iteration cap or fault injection set, the pairs are copied to the device
+ * in at most 32 chunks (of at least 2^23 pairs) on a copy stream, and each
+ * chunk is consumed as it lands: its degrees are counted (Section 3.2) and
+ * one SV iteration (Section 3.1: hook on the current roots, shortcut)
+ * runs over its pairs, keeping the pairs that crossed roots. After the copy
+ * the route is predicted from the complete histogram; the SV route
+ * continues with the kept pairs, the BFS route starts over from the device
+ * copy. Otherwise the pairs are copied once and cc_labels runs.
+ *   edges_host      [m][2] pairs of id_bytes each, host memory; page-locked
+ *                   memory (cudaHostAlloc / cudaHostRegister) lets the copies
+ *                   overlap the passes, pageable memory works but is slower
+ *   n, m            as cc_labels
+ *   labels_out_host [n] ids of id_bytes each, host memory
+ *   stream          cudaStream_t as void*
+ * The context keeps device copies of the pairs and labels (grown on demand,
+ * freed by cc_destroy). The call returns with the labels in labels_out_host.
+ * Errors as cc_labels; on an error labels_out_host is not written.
+ */
+cc_status cc_labels_host(cc_ctx *ctx, const void *edges_host, int64_t n, int64_t m, void *labels_out_host,
+                         void *stream);
+
+/*
+ * Labels of G independent graphs in one call (the batched form). Under the
+ * K-S policy (and the learned one, which the batch treats the same way)
+ * every graph gets its own route prediction, as cc_ks_statistic_batched:
+ * the degree pass is fused into the first SV hook pass over all graphs, and
+ * each graph routed to BFS runs the BFS step on its own pairs; then the SV
+ * iterations run over the union of all graphs (one cached CUDA graph with a
+ * device-driven loop when per-kernel profiling is off). CC_ROUTE_FORCE_SV
+ * skips the prediction; CC_ROUTE_FORCE_BFS sends every graph to BFS.
+ * cc_get_stats: route = number of graphs that took the BFS step.
  *   edges_dev          concatenated int32 pairs with ids local to each graph
  *   edge_offsets_dev   [G+1] int64 (device): graph g owns pairs [eo[g], eo[g+1])
  *   vertex_offsets_dev [G+1] int64 (device): graph g owns vertices [vo[g], vo[g+1]) of labels_out
@@ -326,6 +360,25 @@ typedef struct cc_l2_rates {
     int32_t grid;        /* blocks of 256 threads */
 } cc_l2_rates;
 cc_status cc_measure_l2_rates(cc_ctx *ctx, cc_l2_rates *out, void *stream);
+
+/*
+ * Route prediction of every graph of a batch (Algorithm 2 lines 1-3 and the
+ * power-law fit of Section 3.2, per graph): the degrees of each graph, its
+ * degree histogram, the K-S statistic D (minimum over candidate xmin, as
+ * cc_ks_statistic), the route and the max-degree seed. cc_labels_batched
+ * makes the same prediction under the K-S policy. Arguments as
+ * cc_labels_batched, plus host output arrays of G entries each:
+ *   D_host, alpha_host   statistic and exponent at the selected xmin (1, 0 without a candidate)
+ *   xmin_host, ncand_host  selected xmin (0 without a candidate), number of candidates
+ *   route_host           1 = BFS first (D < ks_tau), 0 = SV only
+ *   seed_host            local id of the max-degree vertex (ties to the smallest id)
+ * The call synchronises `stream`. Errors as cc_labels_batched.
+ */
+cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *edge_offsets_dev,
+                                  const int64_t *vertex_offsets_dev, const int64_t *edge_offsets_host,
+                                  const int64_t *vertex_offsets_host, int G, double *D_host, double *alpha_host,
+                                  int64_t *xmin_host, int64_t *ncand_host, int32_t *route_host, int64_t *seed_host,
+                                  void *stream);
 
 /* Statistics of the last cc_labels call; synchronises its stream. Returns the recorded device status. */
 cc_status cc_get_stats(cc_ctx *ctx, cc_stats *out);

@@ -65,6 +65,8 @@ class Stats(ctypes.Structure):
         ("sv_hooks", ctypes.c_int64 * MAX_SV_ITERS_RECORDED),
         ("pred_confidence", ctypes.c_float), ("pred_route", ctypes.c_int), ("pred_cutoff", ctypes.c_int),
         ("ms_features", ctypes.c_float),
+        ("batch_unroll", ctypes.c_int32),
+        ("batch_grid_mult", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -101,6 +103,8 @@ def lib() -> ctypes.CDLL:
         L.cc_set_options.argtypes = [_vp, ctypes.POINTER(Options)]
         L.cc_destroy.argtypes = [_vp]
         L.cc_labels.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp]
+        L.cc_labels_host.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp]
+        L.cc_ks_statistic_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.cc_labels_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp]
         L.cc_degree_distribution.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp]
         L.cc_ks_statistic.argtypes = [_vp, _vp, _i64, _vp, _vp]
@@ -118,7 +122,8 @@ def lib() -> ctypes.CDLL:
         for f in ("cc_default_options", "cc_create", "cc_set_options", "cc_destroy", "cc_labels",
                   "cc_labels_batched", "cc_degree_distribution", "cc_ks_statistic", "cc_get_stats",
                   "cc_labels_static", "cc_route_features", "cc_set_predictor", "cc_mlp_forward",
-                  "cc_mlp_backward", "cc_mlp_adam", "cc_measure_l2_rates"):
+                  "cc_mlp_backward", "cc_mlp_adam", "cc_measure_l2_rates", "cc_labels_host",
+                  "cc_ks_statistic_batched"):
             getattr(L, f).restype = _int
         _lib = L
     return _lib
@@ -202,6 +207,24 @@ class Engine:
         _check(rc, "cc_labels")
         return out
 
+    def labels_host(self, edges, n: int, out=None, stream=None):
+        """Labels of a host (CPU) [m, 2] edge tensor into a host tensor (cc_labels_host).
+        Pin both tensors (`.pin_memory()`) for the copies to overlap the passes."""
+        import torch
+
+        if edges.device.type != "cpu" or not edges.is_contiguous():
+            raise ValueError("edges must be a contiguous CPU tensor")
+        m = edges.shape[0] if edges.numel() else 0
+        dt = torch.int32 if self._opt.id_bytes == 4 else torch.int64
+        if out is None:
+            out = torch.empty(n, dtype=dt)
+        if out.device.type != "cpu" or out.dtype != dt or out.numel() != n or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CPU tensor of n ids")
+        rc = lib().cc_labels_host(self._h, edges.data_ptr() if m else None, n, m, out.data_ptr(),
+                                  _stream_handle(stream, self.device))
+        _check(rc, "cc_labels_host")
+        return out
+
     def labels_batched(self, edges, edge_offsets, vertex_offsets, out=None, stream=None):
         """Local labels of G independent graphs (int32 ids local to each graph)."""
         import torch
@@ -217,6 +240,27 @@ class Engine:
                                      vo_d.data_ptr(), eo_h.data_ptr(), vo_h.data_ptr(), G,
                                      out.data_ptr() if out.numel() else None, _stream_handle(stream, edges.device))
         _check(rc, "cc_labels_batched")
+        return out
+
+    def ks_statistic_batched(self, edges, edge_offsets, vertex_offsets, stream=None) -> dict:
+        """Per-graph route prediction of a batch (cc_ks_statistic_batched): numpy arrays
+        D, alpha, xmin, ncand, route, seed of G entries each."""
+        import numpy as np
+        import torch
+
+        eo = torch.as_tensor(np.ascontiguousarray(edge_offsets, dtype=np.int64))
+        vo = torch.as_tensor(np.ascontiguousarray(vertex_offsets, dtype=np.int64))
+        G = eo.numel() - 1
+        eo_d, vo_d = eo.to(edges.device), vo.to(edges.device)
+        out = {k: np.zeros(G, dtype=dt) for k, dt in (("D", np.float64), ("alpha", np.float64), ("xmin", np.int64),
+                                                     ("ncand", np.int64), ("route", np.int32), ("seed", np.int64))}
+        m = edges.shape[0] if edges.numel() else 0
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        rc = lib().cc_ks_statistic_batched(self._h, edges.data_ptr() if m else None, eo_d.data_ptr(), vo_d.data_ptr(),
+                                           eo.data_ptr(), vo.data_ptr(), G, ptr(out["D"]), ptr(out["alpha"]),
+                                           ptr(out["xmin"]), ptr(out["ncand"]), ptr(out["route"]), ptr(out["seed"]),
+                                           _stream_handle(stream, edges.device))
+        _check(rc, "cc_ks_statistic_batched")
         return out
 
     def labels_batched_dev(self, edges, eo_dev, vo_dev, eo_host, vo_host, out, stream=None):

@@ -55,6 +55,7 @@ struct DevState {
     unsigned long long kept[kMaxIters];     // active pairs written by SV iteration i
     unsigned long long hooked[kMaxIters];   // roots hooked in SV iteration i
     unsigned long long hook_base[kMaxIters + 1];  // start of iteration i's slice of the hooked list
+    unsigned long long kept_base[kMaxIters + 1];  // host-input chunks: start of chunk i's surviving pairs
     unsigned long long front[kMaxLevels];   // BFS frontier size entering level l
     unsigned long long front_edges[kMaxLevels];  // sum of degrees of that frontier
 };
@@ -146,6 +147,26 @@ __device__ __forceinline__ unsigned long long block_reserve(unsigned long long *
     return r;
 }
 
+
+// Batched form: graph g owns pairs [eo[g], eo[g+1]) and vertices [vo[g], vo[g+1]).
+// The graph of every 2^kTileShift-th pair (and vertex) is precomputed
+// (k_tile_graphs), so a tile starts its forward scan without a search.
+constexpr int kTileShift = 9;
+// largest g in [0, G) with off[g] <= k (skips empty graphs)
+__device__ __forceinline__ int graph_search(const int64_t *off, int G, long long k) {
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int graph_advance(const int64_t *off, int G, long long k, int g) {
+    while (g + 1 < G && off[g + 1] <= k) g++;
+    return g;
+}
 
 // Grid-stride helpers
 __device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }

@@ -8,6 +8,19 @@
 
 namespace ccg {
 
+// Schedule of the batched hook passes: 16-byte vectors per thread per tile
+// and blocks per launch as a multiple of the resident count.
+struct BatchSchedule {
+    int unroll = 2;
+    int grid_mult = 1;
+    const uint32_t *pair_tiles = nullptr;  // graph of every 2^kTileShift-th pair (launch_tile_graphs), required
+};
+
+
+// launch_cfg.cu: min(grid, blocks of `kernel` resident on the current device at once)
+int fit_grid(const void *kernel, int grid, int block, size_t smem = 0);
+
+
 // Scratch of the K-S fit (device arrays, sized for the distinct degrees).
 struct KsScratch {
     uint32_t *xs;                  // distinct degrees >= 1, increasing
@@ -62,6 +75,15 @@ template <typename T>
 void launch_degree_hubs(const void *edges, long long m, vid_t n, uint32_t *deg, unsigned *scratch, DevState *st,
                         int grid, int num_sms, cudaStream_t s);
 size_t degree_hubs_scratch_bytes();
+// the hub-aware pass in two parts, for pairs that arrive in chunks: the hub
+// table from the first degree_hub_prefix() pairs, then any number of counts
+long long degree_hub_prefix();
+template <typename T>
+void launch_degree_hub_prefix(const void *edges, vid_t n, uint32_t *deg, unsigned *scratch, DevState *st, int grid,
+                              cudaStream_t s);
+template <typename T>
+void launch_degree_hub_count(const void *edges, long long m, vid_t n, uint32_t *deg, const unsigned *scratch,
+                             DevState *st, int num_sms, cudaStream_t s);
 void launch_hist(const uint32_t *deg, vid_t n, uint32_t *hist, uint32_t *ovf, unsigned long long ovf_cap,
                  DevState *st, int grid, cudaStream_t s);
 void launch_ks(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf_cap, KsScratch ks, DevState *st,
@@ -80,11 +102,14 @@ void launch_sv_pass(int mode, bool write, bool record, const void *in, long long
 void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid, cudaStream_t s);
 void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
                           vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
-                          cudaStream_t s);
+                          cudaStream_t s, uint32_t *deg = nullptr,
+                          BatchSchedule sch = BatchSchedule());
 void launch_finalize_batch(vid_t *parent, vid_t ntot, const int64_t *vo, int G, int32_t *labels, int grid,
-                           cudaStream_t s);
+                           cudaStream_t s,
+                           const uint32_t *vertex_tiles);
 
 void launch_sv_shortcut(vid_t *parent, const vid_t *hooked_list, DevState *st, int it, int grid, cudaStream_t s);
+void launch_stream_finish(DevState *st, int it, cudaStream_t s);
 // device-driven loop: init before a WHILE node on handle h, body inside it
 void launch_sv_loop_init(DevState *st, int it0, int cur0, int cap, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_sv_loop_body(const uint2 *eb0, const uint2 *eb1, vid_t n, vid_t *parent, vid_t *hooked_list,
@@ -128,5 +153,28 @@ void mlp_infer(const __nv_bfloat16 *Wb, const float *bias, const float *x, DevSt
 // k_probe.cu
 void launch_l2_probe(int kind, uint32_t *table, uint32_t mask, long long ops, uint32_t *sink, int grid,
                      cudaStream_t s);
+
+// k_batch_route.cu: per-graph route prediction of the batched form
+struct KsBatchScratch {  // per block: ks_batch_entries() of each (cum: one more)
+    uint32_t *xs;
+    unsigned long long *cnt, *cum;
+    double *lnx, *Dc, *Ac, *Zc;
+};
+struct KsBatchOut {  // per graph
+    double *D, *alpha;
+    long long *xmin, *ntail, *ncand;
+    int *route, *overflow;
+    unsigned long long *seedkey;  // (degree << 32) | (0xffffffff - local id) of the max-degree vertex
+};
+size_t ks_batch_entries();
+void launch_degree_batch(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G, uint32_t *deg,
+                         DevState *st, int grid, cudaStream_t s, const uint32_t *pair_tiles);
+// out[k] = the graph holding item k << kTileShift of the offsets `off` (G + 1 entries), k < (count >> kTileShift) + 1
+void launch_tile_graphs(const int64_t *off, int G, long long count, uint32_t *out, int grid, cudaStream_t s);
+void launch_ks_batch(const uint32_t *deg, const int64_t *vo, int G, KsBatchScratch sc, KsBatchOut out,
+                     long long min_tail, long long min_distinct, double min_span, double tau, int blocks,
+                     cudaStream_t s);
+void launch_merge_visited(const uint32_t *vis, long long ng, long long base, const DevState *st, vid_t *parent,
+                          int grid, cudaStream_t s);
 
 }  // namespace ccg

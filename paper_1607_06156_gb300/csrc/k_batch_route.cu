@@ -1,0 +1,386 @@
+// Route prediction of the batched form (Algorithm 2 lines 1-3, Section 3.2,
+// for each of G graphs): the degrees of every graph in one pass over the
+// union, then one block per graph for its degree histogram, the power-law
+// fit with the K-S statistic, the route and the max-degree seed. The
+// arithmetic is the single-graph fit's (ks_math.cuh): fp32 screen of every
+// (candidate, degree) term, fp64 refinement of the terms within the screen
+// slack, minimum D over candidates with ties to the smaller xmin.
+//
+//  k_degree_batch   deg[vo[g] + x] = number of pair endpoints equal to local
+//                   id x of graph g (local ids checked against n_g)
+//  k_ks_batch       per graph: the distinct degrees (dense shared-memory bins
+//                   below kBB, a sorted shared-memory list above), candidate
+//                   setup, terms, selection; graphs with more than kBOvf
+//                   vertices of degree >= kBB are flagged for the
+//                   single-graph fit instead
+//  k_merge_visited  after a graph's BFS: every visited vertex takes the
+//                   visited minimum as parent (atomicMin keeps the forest)
+#include "cc_common.cuh"
+#include "cc_kernels.h"
+#include "ks_math.cuh"
+
+namespace ccg {
+
+constexpr int kBB = 4096;          // dense degree bins per graph (degrees 1..kBB-1)
+constexpr int kBOvf = 4096;        // degrees >= kBB held per graph
+constexpr int kBThreads = 256;
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_degree_batch(const int32_t *__restrict__ in, long long m,
+                                                         const int64_t *__restrict__ eo,
+                                                         const int64_t *__restrict__ vo, int G, uint32_t *deg,
+                                                         DevState *st, const uint32_t *__restrict__ tg) {
+    constexpr int U = 2, K = 2 * U;
+    const long long nvec = m / 2;
+    const int4 *ev = reinterpret_cast<const int4 *>(in);
+    bool bad = false;
+    const long long tile = (long long)kBlock * U;
+    const long long ntiles = (nvec + tile - 1) / tile;
+    for (long long t = blockIdx.x; t < ntiles + ((m & 1) ? 1 : 0); t += gridDim.x) {
+        const long long k0 = t < ntiles ? t * tile * 2 : m - 1;
+        const int g0 = (int)tg[k0 >> kTileShift];  // a graph at or before the tile's first pair
+        long long u[K], v[K], k[K];
+        bool valid[K];
+        if (t < ntiles) {
+#pragma unroll
+            for (int r = 0; r < U; r++) {
+                const long long i = t * tile + (long long)r * kBlock + threadIdx.x;
+                const int4 q = i < nvec ? ld_stream(ev + i) : make_int4(0, 0, 0, 0);
+                u[2 * r] = q.x; v[2 * r] = q.y; k[2 * r] = 2 * i;
+                u[2 * r + 1] = q.z; v[2 * r + 1] = q.w; k[2 * r + 1] = 2 * i + 1;
+                valid[2 * r] = valid[2 * r + 1] = i < nvec;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < K; r++) {
+                u[r] = v[r] = 0;
+                k[r] = m - 1;
+                valid[r] = false;
+            }
+            if (threadIdx.x == 0) {
+                u[0] = in[2 * (m - 1)];
+                v[0] = in[2 * (m - 1) + 1];
+                valid[0] = true;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < K; r++) {
+            if (!valid[r]) continue;
+            const int g = graph_advance(eo, G, k[r], g0);
+            const long long base = vo[g], ng = vo[g + 1] - base;
+            if (u[r] < 0 || v[r] < 0 || u[r] >= ng || v[r] >= ng) {
+                bad = true;
+                continue;
+            }
+            atomicAdd(&deg[base + u[r]], 1u);
+            atomicAdd(&deg[base + v[r]], 1u);
+        }
+    }
+    if (bad) set_err(st, kErrInvalidEdge);
+}
+
+// ---------------------------------------------------------------------------
+// Per-graph fit. Scratch per block (global): the distinct degrees xs, their
+// counts, the exclusive prefix cum (cum[nd] = vertices of degree >= 1),
+// ln x, and per candidate D, alpha, Z; kBB + kBOvf entries each.
+__global__ void __launch_bounds__(kBThreads) k_ks_batch(const uint32_t *__restrict__ deg,
+                                                        const int64_t *__restrict__ vo, int G, KsBatchScratch sc,
+                                                        KsBatchOut out, long long min_tail, long long min_distinct,
+                                                        double min_span, double tau) {
+    __shared__ uint32_t hist[kBB];
+    __shared__ uint32_t ovf[kBOvf];
+    __shared__ unsigned long long s64[33];
+    __shared__ int s_novf;
+    __shared__ unsigned long long s_key;
+    __shared__ double sel_D[kBThreads];
+    __shared__ long long sel_I[kBThreads];
+    __shared__ double sdbl[33];
+    __shared__ long long s64l[33];
+    constexpr int kCap = kBB + kBOvf;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBThreads / 32;
+    uint32_t *xs = sc.xs + (size_t)blockIdx.x * kCap;
+    unsigned long long *cnt = sc.cnt + (size_t)blockIdx.x * kCap;
+    unsigned long long *cum = sc.cum + (size_t)blockIdx.x * (kCap + 1);
+    double *lnx = sc.lnx + (size_t)blockIdx.x * kCap;
+    double *Dc = sc.Dc + (size_t)blockIdx.x * kCap;
+    double *Ac = sc.Ac + (size_t)blockIdx.x * kCap;
+    double *Zc = sc.Zc + (size_t)blockIdx.x * kCap;
+    for (int g = blockIdx.x; g < G; g += gridDim.x) {
+        const long long v0 = vo[g], ng = vo[g + 1] - v0;
+        // 1. histogram and argmax key (deg << 32) | ~local id
+        for (int i = tid; i < kBB; i += kBThreads) hist[i] = 0;
+        if (tid == 0) {
+            s_novf = 0;
+            s_key = 0;
+        }
+        __syncthreads();
+        unsigned long long best = 0;
+        for (long long v = tid; v < ng; v += kBThreads) {
+            const uint32_t d = deg[v0 + v];
+            const unsigned long long key = ((unsigned long long)d << 32) | (0xffffffffull - (unsigned long long)v);
+            best = key > best ? key : best;
+            if (d == 0) continue;
+            if (d < (uint32_t)kBB) {
+                atomicAdd(&hist[d], 1u);
+            } else {
+                const int k = atomicAdd(&s_novf, 1);
+                if (k < kBOvf) ovf[k] = d;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long b = __shfl_xor_sync(0xffffffffu, best, o);
+            best = b > best ? b : best;
+        }
+        if (lane == 0 && best) atomicMax(&s_key, best);
+        __syncthreads();
+        const int novf = s_novf;
+        if (tid == 0) {
+            out.seedkey[g] = s_key;
+            out.overflow[g] = novf > kBOvf ? 1 : 0;
+        }
+        if (novf > kBOvf) {  // left to the single-graph fit (block-uniform)
+            __syncthreads();
+            continue;
+        }
+        // 2a. distinct dense degrees, increasing: thread t owns bins [16t, 16t + 16)
+        constexpr int B = kBB / kBThreads;
+        unsigned long long mynz = 0, mymass = 0;
+#pragma unroll
+        for (int k = 0; k < B; k++) {
+            const int d = tid * B + k;
+            const uint32_t h = d > 0 ? hist[d] : 0u;
+            mynz += h ? 1 : 0;
+            mymass += h;
+        }
+        unsigned long long tnz, tmass;
+        unsigned long long o = block_exclusive_scan<unsigned long long>(mynz, s64, tnz);
+        unsigned long long om = block_exclusive_scan<unsigned long long>(mymass, s64, tmass);
+        for (int k = 0; k < B; k++) {
+            const int d = tid * B + k;
+            const uint32_t h = d > 0 ? hist[d] : 0u;
+            if (h) {
+                xs[o] = (uint32_t)d;
+                cnt[o] = h;
+                cum[o] = om;
+                lnx[o] = log((double)d);
+                o++;
+                om += h;
+            }
+        }
+        // 2b. degrees >= kBB: bitonic sort in shared memory, then one entry per run
+        int P = 1;
+        while (P < novf) P <<= 1;
+        for (int i = tid; i < P; i += kBThreads)
+            if (i >= novf) ovf[i] = 0xffffffffu;
+        __syncthreads();
+        for (int size = 2; size <= P; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = tid; i < P; i += kBThreads) {
+                    const int j = i ^ stride;
+                    if (j > i) {
+                        const bool up = (i & size) == 0;
+                        const uint32_t a = ovf[i], b = ovf[j];
+                        if ((a > b) == up) {
+                            ovf[i] = b;
+                            ovf[j] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        unsigned long long outn = 0;
+        for (int r = 0; r < P; r += kBThreads) {
+            const int i = r + tid;
+            const bool head = i < novf && (i == 0 || ovf[i] != ovf[i - 1]);
+            unsigned long long tot;
+            const unsigned long long rank = block_exclusive_scan<unsigned long long>(head ? 1ull : 0ull, s64, tot);
+            if (head) {
+                int e = i + 1;
+                while (e < novf && ovf[e] == ovf[i]) e++;
+                const unsigned long long q = tnz + outn + rank;
+                xs[q] = ovf[i];
+                cnt[q] = (unsigned long long)(e - i);
+                cum[q] = tmass + (unsigned long long)i;
+                lnx[q] = log((double)ovf[i]);
+            }
+            outn += tot;
+        }
+        const long long nd = (long long)(tnz + outn);
+        if (tid == 0) cum[nd] = tmass + (unsigned long long)novf;
+        __syncthreads();
+        // 3. suffix sums SL[i] = sum_{j >= i} cnt[j] ln x[j] (fp64, one reverse
+        //    pass in chunks of the block), kept in Zc: they make every
+        //    candidate's exponent O(1) instead of a sum over its tail
+        const unsigned long long total = nd > 0 ? cum[nd] : 0;
+        const double xmax = nd > 0 ? (double)xs[nd - 1] : 0.0;
+        {
+            double carry = 0.0;  // sum over the entries above the current chunk
+            for (long long c0 = ((nd - 1) / kBThreads) * kBThreads; c0 >= 0; c0 -= kBThreads) {
+                const long long i = c0 + (kBThreads - 1 - tid);  // thread t takes the t-th from the top
+                const double v = i < nd ? (double)cnt[i] * lnx[i] : 0.0;
+                double tot;
+                const double ex = block_exclusive_scan<double>(v, sdbl, tot);
+                if (i < nd) Zc[i] = carry + ex + v;
+                carry += tot;
+            }
+        }
+        __syncthreads();
+        // 4. candidates (one thread each): the tail rules; alpha by Clauset et
+        //    al. eq. 3.7 from the suffix sum: sum_j cnt_j (ln x_j - ln(xmin - 1/2))
+        //    = SL[i] - N ln(xmin - 1/2); marked with Dc = 0 (candidate) or 2
+        long long nc = 0;
+        for (long long i = tid; i < nd; i += kBThreads) {
+            const double xmin = (double)xs[i];
+            const unsigned long long Nt = total - cum[i];
+            if ((long long)Nt < min_tail || nd - i < min_distinct || xmax < min_span * xmin) {
+                Dc[i] = 2.0;
+                continue;
+            }
+            Ac[i] = 1.0 + (double)Nt / (Zc[i] - (double)Nt * log(xmin - 0.5));
+            Dc[i] = 0.0;
+            nc++;
+        }
+        const long long ncand = block_reduce_sum<long long>(nc, s64l);
+        // 5. screen (one warp per candidate): every term in fp32, with the
+        //    normaliser zeta(alpha, xmin) in fp32 too; Dc[i] = the fp32 sup
+        float fmin_t = 2.0f;
+        for (long long i = warp; i < nd; i += nw) {
+            if (Dc[i] > 1.0) continue;  // not a candidate (warp-uniform)
+            const float alpha_f = (float)Ac[i], lnc_f = (float)lnx[i];
+            const float Z_f = zeta_scaled_f(alpha_f, (float)xs[i], lnc_f);
+            const unsigned long long ci = cum[i];
+            const double N = (double)(total - ci);
+            float fm = 0.0f;
+            for (long long j = i + lane; j < nd; j += 32) {
+                const double before = (double)(cum[j] - ci) / N, at = (double)(cum[j + 1] - ci) / N;
+                fm = fmaxf(fm, ks_term_f(alpha_f, Z_f, lnc_f, (float)xs[j], (float)lnx[j], (float)before, (float)at,
+                                         j == i));
+            }
+#pragma unroll
+            for (int o2 = 16; o2 > 0; o2 >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o2));
+            if (lane == 0) Dc[i] = (double)fm;
+            fmin_t = fminf(fmin_t, fm);
+        }
+        const double fmin = block_reduce_min((double)fmin_t, sdbl);
+        // 6. refinement (one warp per contender): only a candidate whose fp32 sup
+        //    is within two screen slacks of the smallest can hold the fp64
+        //    minimum (the fp32 terms are within ~5e-6 of the fp64 ones); its
+        //    normaliser and the terms within one slack of its fp32 sup are
+        //    evaluated in fp64. The others are marked 1.5 (never selected).
+        for (long long i = warp; i < nd; i += nw) {
+            const double df = Dc[i];
+            if (df > 1.0) continue;
+            if (df > fmin + 2.0 * (double)kScreenSlack) {
+                if (lane == 0) Dc[i] = 1.5;
+                continue;
+            }
+            const double alpha = Ac[i], lnc = lnx[i];
+            const double Z = zeta_scaled(alpha, (double)xs[i], lnc);
+            const float alpha_f = (float)alpha, lnc_f = (float)lnc;
+            const float Z_f = zeta_scaled_f(alpha_f, (float)xs[i], lnc_f);
+            const unsigned long long ci = cum[i];
+            const double N = (double)(total - ci);
+            const float cut = (float)df - kScreenSlack;
+            double dm = 0.0;
+            for (long long j = i + lane; j < nd; j += 32) {
+                const double x = (double)xs[j];
+                const double before = (double)(cum[j] - ci) / N, at = (double)(cum[j + 1] - ci) / N;
+                const float d32 = ks_term_f(alpha_f, Z_f, lnc_f, (float)x, (float)lnx[j], (float)before, (float)at,
+                                            j == i);
+                if (d32 >= cut) {
+                    double zb, za;
+                    zeta_pair(alpha, x, lnx[j], lnc, zb, za);
+                    double d = fabs(at - (1.0 - za / Z));
+                    if (j > i) d = fmax(d, fabs(before - (1.0 - zb / Z)));
+                    dm = fmax(dm, d);
+                }
+            }
+#pragma unroll
+            for (int o2 = 16; o2 > 0; o2 >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o2));
+            if (lane == 0) Dc[i] = dm;
+        }
+        __syncthreads();
+        // 5. selection: minimum D, ties to the smaller xmin (per-thread scan, then a block reduction)
+        double bd = 2.0;
+        long long bi = -1;
+        for (long long i = tid; i < nd; i += kBThreads) {
+            const double d = Dc[i];
+            if (d <= 1.0 && d < bd) {  // i increases per thread, so ties keep the smaller i
+                bd = d;
+                bi = i;
+            }
+        }
+        sel_D[tid] = bd;
+        sel_I[tid] = bi;
+        __syncthreads();
+        for (int o2 = kBThreads / 2; o2 > 0; o2 >>= 1) {
+            if (tid < o2) {
+                const double d2 = sel_D[tid + o2];
+                const long long i2 = sel_I[tid + o2];
+                if (i2 >= 0 && (d2 < sel_D[tid] || (d2 == sel_D[tid] && (sel_I[tid] < 0 || i2 < sel_I[tid])))) {
+                    sel_D[tid] = d2;
+                    sel_I[tid] = i2;
+                }
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const long long bi0 = sel_I[0];
+            const double D = bi0 < 0 ? 1.0 : sel_D[0];
+            out.D[g] = D;
+            out.alpha[g] = bi0 < 0 ? 0.0 : Ac[bi0];
+            out.xmin[g] = bi0 < 0 ? 0 : (long long)xs[bi0];
+            out.ntail[g] = bi0 < 0 ? 0 : (long long)(total - cum[bi0]);
+            out.ncand[g] = ncand;
+            out.route[g] = D < tau ? 1 : 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// vis: the BFS's visited bitmap over local ids of graph g; cmin_local: its minimum.
+__global__ void __launch_bounds__(kBlock) k_merge_visited(const uint32_t *__restrict__ vis, long long ng,
+                                                          long long base, const DevState *st, vid_t *parent) {
+    const vid_t c = st->cmin;
+    if ((long long)c >= ng) return;
+    for (long long v = gtid(); v < ng; v += gstride())
+        if ((vis[v >> 5] >> (v & 31)) & 1u) atomicMin(&parent[base + v], (vid_t)(base + c));
+}
+
+// ---------------------------------------------------------------------------
+void launch_degree_batch(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G, uint32_t *deg,
+                         DevState *st, int grid, cudaStream_t s, const uint32_t *pair_tiles) {
+    if (m <= 0) return;
+    k_degree_batch<<<fit_grid((const void *)k_degree_batch, grid, kBlock), kBlock, 0, s>>>(in, m, eo, vo, G, deg, st,
+                                                                                          pair_tiles);
+}
+
+__global__ void __launch_bounds__(kBlock) k_tile_graphs(const int64_t *__restrict__ off, int G, long long ntiles,
+                                                        uint32_t *out) {
+    for (long long k = gtid(); k < ntiles; k += gstride()) out[k] = (uint32_t)graph_search(off, G, k << kTileShift);
+}
+
+void launch_tile_graphs(const int64_t *off, int G, long long count, uint32_t *out, int grid, cudaStream_t s) {
+    const long long ntiles = (count >> kTileShift) + 1;
+    k_tile_graphs<<<grid, kBlock, 0, s>>>(off, G, ntiles, out);
+}
+
+size_t ks_batch_entries() { return (size_t)(kBB + kBOvf); }
+
+void launch_ks_batch(const uint32_t *deg, const int64_t *vo, int G, KsBatchScratch sc, KsBatchOut out,
+                     long long min_tail, long long min_distinct, double min_span, double tau, int blocks,
+                     cudaStream_t s) {
+    if (G <= 0) return;
+    k_ks_batch<<<blocks < G ? blocks : G, kBThreads, 0, s>>>(deg, vo, G, sc, out, min_tail, min_distinct, min_span,
+                                                             tau);
+}
+
+void launch_merge_visited(const uint32_t *vis, long long ng, long long base, const DevState *st, vid_t *parent,
+                          int grid, cudaStream_t s) {
+    if (ng > 0) k_merge_visited<<<grid, kBlock, 0, s>>>(vis, ng, base, st, parent);
+}
+
+}  // namespace ccg

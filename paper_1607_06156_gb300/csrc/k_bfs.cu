@@ -417,8 +417,8 @@ template <typename T>
 void launch_bfs_edges(bool write, const void *in, long long m, vid_t n, uint32_t *vis, const uint32_t *cur,
                       uint32_t *next, uint2 *out, DevState *st, int level, int grid, cudaStream_t s) {
     if (m <= 0) return;
-    if (write) k_bfs_edges<T, true><<<grid, kBlock, 0, s>>>((const T *)in, m, n, vis, cur, next, out, st, level);
-    else k_bfs_edges<T, false><<<grid, kBlock, 0, s>>>((const T *)in, m, n, vis, cur, next, out, st, level);
+    auto kf = write ? k_bfs_edges<T, true> : k_bfs_edges<T, false>;
+    kf<<<fit_grid((const void *)kf, grid, kBlock), kBlock, 0, s>>>((const T *)in, m, n, vis, cur, next, out, st, level);
 }
 template void launch_bfs_edges<int32_t>(bool, const void *, long long, vid_t, uint32_t *, const uint32_t *, uint32_t *,
                                         uint2 *, DevState *, int, int, cudaStream_t);

@@ -14,6 +14,7 @@
 //  k_ks_select     min D over the candidates, route = D < tau.
 #include "cc_common.cuh"
 #include "cc_kernels.h"
+#include "ks_math.cuh"
 
 #include <math.h>
 
@@ -285,34 +286,6 @@ __device__ __forceinline__ long long dense_limit(const DevState *st) {
     return maxdeg + 1 < kHistDense ? (long long)maxdeg + 1 : (long long)kHistDense;
 }
 
-template <typename V>
-__device__ V block_exclusive_scan(V x, V *smem /* >= 32 */, V &total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    V incl = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        V y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) smem[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        V w = lane < nw ? smem[lane] : (V)0;
-        V wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            V y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
-        }
-        if (lane < nw) smem[lane] = wi - w;
-        if (lane == nw - 1) smem[32] = wi;
-    }
-    __syncthreads();
-    V r = smem[warp] + incl - x;
-    total = smem[32];
-    __syncthreads();
-    return r;
-}
 
 __global__ void __launch_bounds__(1024) k_distinct_count(const uint32_t *hist, const DevState *st,
                                                          unsigned long long *chunk_nz, unsigned long long *chunk_mass) {
@@ -447,82 +420,6 @@ __global__ void __launch_bounds__(1024) k_distinct_overflow(const uint32_t *ovf,
     }
 }
 
-// ---------------------------------------------------------------------------
-// Scaled Hurwitz zeta: c^s * zeta(s, q) = sum_{k>=0} ((q+k)/c)^-s, s > 1.
-// Explicit terms until a = q + k reaches max(16, 2s); the remainder by the
-// Euler-Maclaurin formula with six Bernoulli terms. With a >= 2s the ratio
-// of consecutive correction terms is below (s / (2 pi a))^2 <= 1/(16 pi^2),
-// so six terms leave a relative error near 1e-15.
-// Euler-Maclaurin remainder sum_{k>=0} ((a+k)/c)^-s for a >= max(16, 2s),
-// given A = (a/c)^-s.
-__device__ __forceinline__ double zeta_tail(double s, double a, double A) {
-    double acc = A * a / (s - 1.0) + 0.5 * A;
-    const double ia2 = 1.0 / (a * a);
-    // term_k = B_2k/(2k)! * s(s+1)...(s+2k-2) * A * a^-(2k-1)
-    const double coef[6] = {1.0 / 12.0, -1.0 / 720.0, 1.0 / 30240.0, -1.0 / 1209600.0, 1.0 / 47900160.0,
-                            -691.0 / 1307674368000.0};
-    double t = A * s / a;
-    acc += coef[0] * t;
-#pragma unroll
-    for (int k = 1; k < 6; k++) {
-        t *= (s + 2 * k - 1) * (s + 2 * k) * ia2;
-        acc += coef[k] * t;
-    }
-    return acc;
-}
-
-__device__ double zeta_scaled(double s, double q, double lnc) {
-    double acc = 0.0, a = q;
-    const double thr = fmax(16.0, 2.0 * s);
-    while (a < thr) {
-        const double term = exp(-s * (log(a) - lnc));
-        acc += term;
-        a += 1.0;
-        // the rest is below term * (1 + a/(s-1)) (integral bound); stop once it cannot matter
-        if (term * (1.0 + a / (s - 1.0)) < 1e-18 * acc) return acc;
-    }
-    return acc + zeta_tail(s, a, exp(-s * (log(a) - lnc)));
-}
-
-// zeta_scaled at x and at x+1 for an observed degree x with ln x known.
-// For x >= max(16, 2s) one evaluation serves both: the x+1 value is the x
-// value minus its first term (x/c)^-s, and the tail is at least twice that
-// term, so the subtraction loses under two bits.
-__device__ __forceinline__ void zeta_pair(double s, double x, double lnx, double lnc, double &zx, double &zx1) {
-    if (x >= fmax(16.0, 2.0 * s)) {
-        const double A = exp(-s * (lnx - lnc));
-        zx = zeta_tail(s, x, A);
-        zx1 = zx - A;
-    } else {
-        zx = zeta_scaled(s, x, lnc);
-        zx1 = zeta_scaled(s, x + 1.0, lnc);
-    }
-}
-
-template <typename V>
-__device__ V block_reduce_sum(V x, V *smem) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) smem[warp] = x;
-    __syncthreads();
-    V r = 0;
-    for (int w = 0; w < nw; w++) r += smem[w];
-    __syncthreads();
-    return r;
-}
-
-__device__ double block_reduce_max(double x, double *smem) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-    if (lane == 0) smem[warp] = x;
-    __syncthreads();
-    double r = 0.0;
-    for (int w = 0; w < nw; w++) r = fmax(r, smem[w]);
-    __syncthreads();
-    return r;
-}
 
 // Candidate setup, one warp per candidate xmin: the tail rules, the
 // exponent alpha (Clauset et al. eq. 3.7) and the normaliser Z = scaled
@@ -558,58 +455,6 @@ __global__ void __launch_bounds__(256) k_ks_prep(const uint32_t *xs, const unsig
     }
 }
 
-// The sup distance is taken in two passes over (candidate, chunk of
-// kKsTerms terms) blocks. The screen evaluates every term in fp32 and keeps
-// each candidate's fp32 maximum; the refine pass re-evaluates in fp64 only
-// the terms whose fp32 value is within kScreenSlack of that maximum and
-// folds them into D[i] (atomicMax on the bit pattern: non-negative doubles
-// and floats order like their bits). The fp32 terms are within ~3e-6 of the
-// fp64 ones (a few ulp on S, on the zeta ratio and on 1 - ratio), far inside
-// the 1e-4 slack, so the term that attains the fp64 maximum always passes
-// the screen and D[i] is the fp64 sup.
-constexpr int kKsTerms = 1024;
-constexpr float kScreenSlack = 1e-4f;
-
-__device__ __forceinline__ float zeta_tail_f(float s, float a, float A) {
-    float acc = A * a / (s - 1.0f) + 0.5f * A;
-    const float ia2 = 1.0f / (a * a);
-    float t = A * s / a;
-    acc += t * (1.0f / 12.0f);
-    t *= (s + 1.0f) * (s + 2.0f) * ia2;
-    acc -= t * (1.0f / 720.0f);
-    t *= (s + 3.0f) * (s + 4.0f) * ia2;
-    acc += t * (1.0f / 30240.0f);
-    return acc;
-}
-
-__device__ float zeta_scaled_f(float s, float q, float lnc) {
-    float acc = 0.0f, a = q;
-    const float thr = fmaxf(16.0f, 2.0f * s);
-    while (a < thr) {
-        const float term = __expf(-s * (__logf(a) - lnc));
-        acc += term;
-        a += 1.0f;
-        if (term * (1.0f + a / (s - 1.0f)) < 1e-9f * acc) return acc;
-    }
-    return acc + zeta_tail_f(s, a, __expf(-s * (__logf(a) - lnc)));
-}
-
-// fp32 distance of term j of candidate i
-__device__ __forceinline__ float ks_term_f(float alpha, float Z, float lnc, float x, float lnxj, float before,
-                                           float at, bool first) {
-    float zb, za;
-    if (x >= fmaxf(16.0f, 2.0f * alpha)) {
-        const float A = __expf(-alpha * (lnxj - lnc));
-        zb = zeta_tail_f(alpha, x, A);
-        za = zb - A;
-    } else {
-        zb = zeta_scaled_f(alpha, x, lnc);
-        za = zeta_scaled_f(alpha, x + 1.0f, lnc);
-    }
-    float d = fabsf(at - (1.0f - za / Z));
-    if (!first) d = fmaxf(d, fabsf(before - (1.0f - zb / Z)));
-    return d;
-}
 
 template <bool REFINE>
 __global__ void __launch_bounds__(256) k_ks_terms(const uint32_t *xs, const unsigned long long *cum,
@@ -726,7 +571,7 @@ __global__ void __launch_bounds__(1024) k_ks_select(const uint32_t *xs, const un
 template <typename T>
 void launch_degree(const void *edges, long long m, vid_t n, uint32_t *deg, DevState *st, int grid, cudaStream_t s) {
     if (m <= 0) return;
-    k_degree<T><<<grid, kBlock, 0, s>>>((const T *)edges, m, n, deg, st);
+    k_degree<T><<<fit_grid((const void *)k_degree<T>, grid, kBlock), kBlock, 0, s>>>((const T *)edges, m, n, deg, st);
 }
 template void launch_degree<int32_t>(const void *, long long, vid_t, uint32_t *, DevState *, int, cudaStream_t);
 template void launch_degree<int64_t>(const void *, long long, vid_t, uint32_t *, DevState *, int, cudaStream_t);
@@ -744,26 +589,43 @@ size_t degree_hubs_scratch_bytes() { return (size_t)(kHubKeysAt + kHubSlotsMax) 
 // smaller tables that fit two blocks per SM were slower.
 constexpr int kHubSlots = 24576, kHubThreads = 1024, kHubMinBlocks = 1;
 
-// Steps 1-3 above with a table of SLOTS slots (at most SLOTS / 2 hubs) and
-// blocks of THREADS threads, MINB per SM. deg must be zeroed; scratch:
-// degree_hubs_scratch_bytes(), 16-byte aligned.
-template <typename T, int SLOTS, int THREADS, int MINB>
-void launch_degree_hubs_cfg(const void *edges, long long m, vid_t n, uint32_t *deg, unsigned *scratch,
-                            DevState *st, int grid, int num_sms, cudaStream_t s) {
+// Steps 1-2 above (the hub table from the first kHubPrefix pairs) with a
+// table of SLOTS slots (at most SLOTS / 2 hubs). deg must be zeroed;
+// scratch: degree_hubs_scratch_bytes(), 16-byte aligned.
+template <typename T, int SLOTS>
+void launch_hub_prefix_cfg(const void *edges, vid_t n, uint32_t *deg, unsigned *scratch, DevState *st, int grid,
+                           cudaStream_t s) {
     static_assert(SLOTS % 16 == 0 && SLOTS <= kHubSlotsMax, "table size");
-    constexpr size_t smem = (size_t)SLOTS * 8;
-    cudaFuncSetAttribute(k_degree_hubs<T, SLOTS, THREADS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
     cudaMemsetAsync(scratch, 0, (size_t)kHubKeysAt * 4, s);
     cudaMemsetAsync(scratch + kHubKeysAt, 0xff, (size_t)SLOTS * 4, s);
-    // the prefix must end on a 16-byte boundary of the pair array: kHubPrefix pairs of 8 or 16 bytes do
+    // the prefix ends on a 16-byte boundary of the pair array: kHubPrefix pairs of 8 or 16 bytes do
     k_degree<T><<<grid, kBlock, 0, s>>>((const T *)edges, kHubPrefix, n, deg, st);
     k_hub_levels<<<grid, kBlock, 0, s>>>(deg, n, scratch);
     k_hub_threshold<<<1, 1024, 0, s>>>(scratch, (unsigned)(SLOTS / 2));
     k_hub_select<<<grid, kBlock, 0, s>>>(deg, n, scratch, (uint32_t)(SLOTS / 4));
-    k_degree_hubs<T, SLOTS, THREADS, MINB><<<num_sms * MINB, THREADS, smem, s>>>(
-        (const T *)edges + 2 * kHubPrefix, m - kHubPrefix, n, deg, scratch, st);
 }
+
+// Step 3 over m pairs at `edges` (blocks of THREADS threads, MINB per SM).
+template <typename T, int SLOTS, int THREADS, int MINB>
+void launch_hub_count_cfg(const void *edges, long long m, vid_t n, uint32_t *deg, const unsigned *scratch,
+                          DevState *st, int num_sms, cudaStream_t s) {
+    if (m <= 0) return;
+    constexpr size_t smem = (size_t)SLOTS * 8;
+    cudaFuncSetAttribute(k_degree_hubs<T, SLOTS, THREADS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_degree_hubs<T, SLOTS, THREADS, MINB><<<num_sms * MINB, THREADS, smem, s>>>((const T *)edges, m, n, deg, scratch,
+                                                                                 st);
+}
+
+template <typename T, int SLOTS, int THREADS, int MINB>
+void launch_degree_hubs_cfg(const void *edges, long long m, vid_t n, uint32_t *deg, unsigned *scratch,
+                            DevState *st, int grid, int num_sms, cudaStream_t s) {
+    launch_hub_prefix_cfg<T, SLOTS>(edges, n, deg, scratch, st, grid, s);
+    launch_hub_count_cfg<T, SLOTS, THREADS, MINB>((const T *)edges + 2 * kHubPrefix, m - kHubPrefix, n, deg, scratch,
+                                                  st, num_sms, s);
+}
+
+long long degree_hub_prefix() { return kHubPrefix; }
 
 template <typename T>
 void launch_degree_hubs(const void *edges, long long m, vid_t n, uint32_t *deg, unsigned *scratch, DevState *st,
@@ -771,6 +633,26 @@ void launch_degree_hubs(const void *edges, long long m, vid_t n, uint32_t *deg, 
     launch_degree_hubs_cfg<T, kHubSlots, kHubThreads, kHubMinBlocks>(edges, m, n, deg, scratch, st, grid, num_sms,
                                                                      s);
 }
+
+template <typename T>
+void launch_degree_hub_prefix(const void *edges, vid_t n, uint32_t *deg, unsigned *scratch, DevState *st, int grid,
+                              cudaStream_t s) {
+    launch_hub_prefix_cfg<T, kHubSlots>(edges, n, deg, scratch, st, grid, s);
+}
+
+template <typename T>
+void launch_degree_hub_count(const void *edges, long long m, vid_t n, uint32_t *deg, const unsigned *scratch,
+                             DevState *st, int num_sms, cudaStream_t s) {
+    launch_hub_count_cfg<T, kHubSlots, kHubThreads, kHubMinBlocks>(edges, m, n, deg, scratch, st, num_sms, s);
+}
+template void launch_degree_hub_prefix<int32_t>(const void *, vid_t, uint32_t *, unsigned *, DevState *, int,
+                                                cudaStream_t);
+template void launch_degree_hub_prefix<int64_t>(const void *, vid_t, uint32_t *, unsigned *, DevState *, int,
+                                                cudaStream_t);
+template void launch_degree_hub_count<int32_t>(const void *, long long, vid_t, uint32_t *, const unsigned *,
+                                               DevState *, int, cudaStream_t);
+template void launch_degree_hub_count<int64_t>(const void *, long long, vid_t, uint32_t *, const unsigned *,
+                                               DevState *, int, cudaStream_t);
 template void launch_degree_hubs<int32_t>(const void *, long long, vid_t, uint32_t *, unsigned *, DevState *, int,
                                           int, cudaStream_t);
 template void launch_degree_hubs<int64_t>(const void *, long long, vid_t, uint32_t *, unsigned *, DevState *, int,
@@ -779,7 +661,7 @@ template void launch_degree_hubs<int64_t>(const void *, long long, vid_t, uint32
 void launch_hist(const uint32_t *deg, vid_t n, uint32_t *hist, uint32_t *ovf, unsigned long long ovf_cap,
                  DevState *st, int grid, cudaStream_t s) {
     if (n == 0) return;
-    k_hist<<<grid, kBlock, 0, s>>>(deg, n, hist, ovf, ovf_cap, st);
+    k_hist<<<fit_grid((const void *)k_hist, grid, kBlock), kBlock, 0, s>>>(deg, n, hist, ovf, ovf_cap, st);
 }
 
 void launch_ks(const uint32_t *hist, const uint32_t *ovf, unsigned long long ovf_cap, KsScratch ks, DevState *st,

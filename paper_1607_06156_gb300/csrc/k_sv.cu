@@ -31,7 +31,10 @@
 // parent is the identity (no gathers, nothing written); MODE 1 is the first
 // pass after the BFS step (Algorithm 2, lines 8-9: pairs with both ends
 // visited are dropped, a visited end stands for the BFS component's root);
-// MODE 2 gathers parents.
+// MODE 2 gathers parents (one hop: every vertex the pass reads points at a
+// root after the previous shortcut); MODE 3 chases each end to its current
+// root, for pairs read while parents may be one or more hops from their
+// roots (the chunks of the host-input path).
 #include "cc_common.cuh"
 #include "cc_kernels.h"
 
@@ -63,9 +66,14 @@ __device__ __forceinline__ bool sv_pair(long long u, long long v, vid_t n, vid_t
         const bool a = ok && vis_test(vis, u), b = ok && vis_test(vis, v);
         ru = a ? cmin : (vid_t)u;
         rv = b ? cmin : (vid_t)v;
-    } else {
+    } else if (MODE == 2) {
         ru = parent[u];
         rv = parent[v];
+    } else {  // MODE 3: chase to the roots at read time (parents point at smaller ids, so this ends)
+        ru = (vid_t)u;
+        for (vid_t p = parent[ru]; p != ru; p = parent[ru]) ru = p;
+        rv = (vid_t)v;
+        for (vid_t p = parent[rv]; p != rv; p = parent[rv]) rv = p;
     }
     if (ru == rv) return false;
     const vid_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
@@ -79,10 +87,13 @@ __device__ __forceinline__ bool sv_pair(long long u, long long v, vid_t n, vid_t
 template <typename T> struct PassUnroll { static constexpr int U = 2; };
 template <> struct PassUnroll<int64_t> { static constexpr int U = 4; };
 
+// MODE 3 (the chunks of the host-input path) appends its surviving pairs
+// after those of the earlier chunks: at out + kept_base[it].
 template <typename T, int MODE, bool WRITE, bool RECORD>
 __device__ __forceinline__ void sv_pass_body(const T *__restrict__ in, long long m, vid_t n, vid_t *parent,
                                              const uint32_t *__restrict__ vis, vid_t cmin, vid_t *hooked_list,
                                              uint2 *__restrict__ out, DevState *st, int it) {
+    if (MODE == 3 && WRITE) out += st->kept_base[it];
     constexpr int P = PairVec<T>::kPairs;
     constexpr int U = PassUnroll<T>::U;
     constexpr int K = P * U;  // pairs per thread per round
@@ -148,8 +159,13 @@ __device__ __forceinline__ void sv_pass_body(const T *__restrict__ in, long long
     if (bad) set_err(st, kErrInvalidEdge);
 }
 
+// int32 pairs: 8 resident blocks per SM (the grid-stride grid is 8 blocks
+// per SM), so at most 32 registers; the int64 forms need more and run fewer
+template <typename T> struct PassMinBlocks { static constexpr int v = 8; };
+template <> struct PassMinBlocks<int64_t> { static constexpr int v = 1; };
+
 template <typename T, int MODE, bool WRITE, bool RECORD>
-__global__ void __launch_bounds__(kBlock) k_sv_pass(const T *__restrict__ in, long long m, vid_t n, vid_t *parent,
+__global__ void __launch_bounds__(kBlock, PassMinBlocks<T>::v) k_sv_pass(const T *__restrict__ in, long long m, vid_t n, vid_t *parent,
                                                     const uint32_t *__restrict__ vis, vid_t cmin, vid_t *hooked_list,
                                                     uint2 *__restrict__ out, DevState *st, int it) {
     sv_pass_body<T, MODE, WRITE, RECORD>(in, m, n, parent, vis, cmin, hooked_list, out, st, it);
@@ -188,7 +204,7 @@ __global__ void k_sv_loop_init(DevState *st, int it0, int cur0, int cap, cudaGra
     sv_loop_decide(st, it0, h);
 }
 
-__global__ void __launch_bounds__(kBlock) k_sv_pass_loop(const uint2 *eb0, const uint2 *eb1, vid_t n, vid_t *parent,
+__global__ void __launch_bounds__(kBlock, 8) k_sv_pass_loop(const uint2 *eb0, const uint2 *eb1, vid_t n, vid_t *parent,
                                                          vid_t *hooked_list, DevState *st) {
     const int it = st->loop_it, cur = st->loop_cur;
     const long long m = (long long)st->kept[it - 1];
@@ -241,8 +257,15 @@ __global__ void __launch_bounds__(kBlock) k_sv_shortcut(vid_t *parent, const vid
     if (it < 0) it = st->loop_it;
     const unsigned long long base = st->hook_base[it], cnt = st->hooked[it];
     for (long long i = gtid(); i < (long long)cnt; i += gstride()) shortcut_to_root(parent, hooked_list[base + i]);
-    if (gtid() == 0) st->hook_base[it + 1] = base + cnt;
+    if (gtid() == 0) {
+        st->hook_base[it + 1] = base + cnt;
+        st->kept_base[it + 1] = st->kept_base[it] + st->kept[it];
+    }
 }
+
+// After the host-input chunks 1..it: kept[it] becomes the length of the one
+// list they appended to, which the next iteration reads.
+__global__ void k_stream_finish(DevState *st, int it) { st->kept[it] = st->kept_base[it] + st->kept[it]; }
 
 // parent[v] = v, or the BFS component's minimum for visited vertices.
 __global__ void __launch_bounds__(kBlock) k_parent_init(vid_t *parent, vid_t n, const uint32_t *__restrict__ vis,
@@ -290,32 +313,22 @@ __global__ void __launch_bounds__(kBlock) k_finalize(vid_t *parent, vid_t n, T *
 // of the union; the union's components are exactly the graphs' components,
 // and a component's minimum union id is vo[g] plus its minimum local id.
 
-// largest g in [0, G) with off[g] <= k (skips empty graphs)
-__device__ __forceinline__ int graph_search(const int64_t *off, int G, long long k) {
-    int lo = 0, hi = G - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= k) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
-__device__ __forceinline__ int graph_advance(const int64_t *off, int G, long long k, int g) {
-    while (g + 1 < G && off[g + 1] <= k) g++;
-    return g;
-}
-
-template <int MODE, bool WRITE, bool RECORD>
+// DEG: also count both ends of every valid pair into deg (union ids): the
+// degree pass of Section 3.2 fused into the first hook pass, which needs
+// no prediction result (every vertex starts as its own root).
+// U: 16-byte vectors (two pairs each) per thread per tile, the schedule the
+// batched form's tuner picks.
+template <int MODE, bool WRITE, bool RECORD, bool DEG, int U>
 __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restrict__ in, long long m,
                                                           const int64_t *__restrict__ eo,
                                                           const int64_t *__restrict__ vo, int G, vid_t ntot,
                                                           vid_t *parent, vid_t *hooked_list, uint2 *__restrict__ out,
-                                                          DevState *st, int it) {
-    constexpr int U = 2, K = 2 * U;
+                                                          DevState *st, int it, uint32_t *deg,
+                                                          const uint32_t *__restrict__ tg) {
+    constexpr int K = 2 * U;
     __shared__ int sw[32];
     __shared__ unsigned long long sbase;
-    __shared__ int sg;
     const long long nvec = m / 2;
     const int4 *ev = reinterpret_cast<const int4 *>(in);
     const unsigned long long hbase = RECORD ? st->hook_base[it] : 0ull;
@@ -324,9 +337,7 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restr
     const long long ntiles = (nvec + tile - 1) / tile;
     for (long long t = blockIdx.x; t < ntiles + ((m & 1) ? 1 : 0); t += gridDim.x) {
         const long long k0 = t < ntiles ? t * tile * 2 : m - 1;  // first pair of the tile
-        if (threadIdx.x == 0) sg = graph_search(eo, G, k0);
-        __syncthreads();
-        const int g0 = sg;
+        const int g0 = (int)tg[k0 >> kTileShift];  // a graph at or before the tile's first pair
         long long u[K], v[K], k[K];
         bool valid[K];
         if (t < ntiles) {
@@ -363,6 +374,10 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restr
                 bad = true;
                 continue;
             }
+            if (DEG) {
+                atomicAdd(&deg[base + u[r]], 1u);
+                atomicAdd(&deg[base + v[r]], 1u);
+            }
             keep[r] = sv_pair<MODE, RECORD>(base + u[r], base + v[r], ntot, parent, nullptr, 0, ru[r], rv[r], hk[r],
                                             bad);
         }
@@ -384,43 +399,52 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restr
             for (int r = 0; r < K; r++)
                 if (hk[r]) hooked_list[hbase + o++] = ru[r] > rv[r] ? ru[r] : rv[r];
         }
-        __syncthreads();  // sg is rewritten by the next tile
     }
     if (bad) set_err(st, kErrInvalidEdge);
 }
 
 // labels[v] = root(v) - vo[g(v)]: the minimum local id of v's component
 __global__ void __launch_bounds__(kBlock) k_finalize_batch(vid_t *parent, vid_t ntot, const int64_t *__restrict__ vo,
-                                                           int G, int32_t *__restrict__ labels) {
-    __shared__ int sg;
-    const long long tile = kBlock;
-    const long long ntiles = ((long long)ntot + tile - 1) / tile;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        if (threadIdx.x == 0) sg = graph_search(vo, G, t * tile);
-        __syncthreads();
-        const long long v = t * tile + threadIdx.x;
-        if (v < (long long)ntot) {
-            const int g = graph_advance(vo, G, v, sg);
-            labels[v] = (int32_t)((long long)find_root(parent, (vid_t)v) - vo[g]);
-        }
-        __syncthreads();
+                                                           int G, int32_t *__restrict__ labels,
+                                                           const uint32_t *__restrict__ vg) {
+    for (long long v = gtid(); v < (long long)ntot; v += gstride()) {
+        const int g = graph_advance(vo, G, v, (int)vg[v >> kTileShift]);
+        labels[v] = (int32_t)((long long)find_root(parent, (vid_t)v) - vo[g]);
     }
+}
+
+template <int U>
+void launch_sv_pass_batch_u(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
+                            vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
+                            cudaStream_t s, uint32_t *deg, int grid_mult, const uint32_t *sch_tg) {
+    auto kf = mode == 0 && deg ? k_sv_pass_batch<0, false, false, true, U>
+              : mode == 0      ? k_sv_pass_batch<0, false, false, false, U>
+                               : k_sv_pass_batch<2, true, true, false, U>;
+    const int g = fit_grid((const void *)kf, grid, kBlock) * (grid_mult > 0 ? grid_mult : 1);
+    kf<<<g, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, mode == 0 ? deg : nullptr, sch_tg);
 }
 
 void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
                           vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
-                          cudaStream_t s) {
+                          cudaStream_t s, uint32_t *deg, BatchSchedule sch) {
     if (m <= 0) return;
-    if (mode == 0)
-        k_sv_pass_batch<0, false, false><<<grid, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it);
+    const uint32_t *sch_tg = sch.pair_tiles;
+    if (sch.unroll == 1)
+        launch_sv_pass_batch_u<1>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s, deg,
+                                  sch.grid_mult, sch_tg);
+    else if (sch.unroll == 4)
+        launch_sv_pass_batch_u<4>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s, deg,
+                                  sch.grid_mult, sch_tg);
     else
-        k_sv_pass_batch<2, true, true><<<grid, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it);
+        launch_sv_pass_batch_u<2>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s, deg,
+                                  sch.grid_mult, sch_tg);
 }
 
 void launch_finalize_batch(vid_t *parent, vid_t ntot, const int64_t *vo, int G, int32_t *labels, int grid,
-                           cudaStream_t s) {
+                           cudaStream_t s, const uint32_t *vertex_tiles) {
     if (ntot == 0) return;
-    k_finalize_batch<<<grid, kBlock, 0, s>>>(parent, ntot, vo, G, labels);
+    k_finalize_batch<<<fit_grid((const void *)k_finalize_batch, grid, kBlock), kBlock, 0, s>>>(parent, ntot, vo, G,
+                                                                                                labels, vertex_tiles);
 }
 
 // ---------------------------------------------------------------------------
@@ -431,15 +455,22 @@ void launch_sv_pass(int mode, bool write, bool record, const void *in, long long
                     const uint32_t *vis, vid_t cmin, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
                     cudaStream_t s) {
     const T *e = (const T *)in;
-#define SVP(M, W, R) k_sv_pass<T, M, W, R><<<grid, kBlock, 0, s>>>(e, m, n, parent, vis, cmin, hooked_list, out, st, it)
+#define SVP(M, W, R)                                                                                  \
+    do {                                                                                              \
+        auto kf = k_sv_pass<T, M, W, R>;                                                              \
+        kf<<<fit_grid((const void *)kf, grid, kBlock), kBlock, 0, s>>>(e, m, n, parent, vis, cmin,    \
+                                                                       hooked_list, out, st, it);     \
+    } while (0)
     if (mode == 0) {
         if (write) SVP(0, true, false);
         else SVP(0, false, false);
     } else if (mode == 1) {
         SVP(1, true, true);
-    } else {
+    } else if (mode == 2) {
         if (record) SVP(2, true, true);
         else SVP(2, true, false);
+    } else {
+        SVP(3, true, true);
     }
 #undef SVP
 }
@@ -451,11 +482,11 @@ template void launch_sv_pass<uint32_t>(int, bool, bool, const void *, long long,
                                        vid_t, vid_t *, uint2 *, DevState *, int, int, cudaStream_t);
 
 void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid, cudaStream_t s) {
-    k_shortcut_all<<<grid, kBlock, 0, s>>>(parent, n, st, it);
+    k_shortcut_all<<<fit_grid((const void *)k_shortcut_all, grid, kBlock), kBlock, 0, s>>>(parent, n, st, it);
 }
 
 void launch_sv_shortcut(vid_t *parent, const vid_t *hooked_list, DevState *st, int it, int grid, cudaStream_t s) {
-    k_sv_shortcut<<<grid, kBlock, 0, s>>>(parent, hooked_list, st, it);
+    k_sv_shortcut<<<fit_grid((const void *)k_sv_shortcut, grid, kBlock), kBlock, 0, s>>>(parent, hooked_list, st, it);
 }
 
 void launch_sv_loop_init(DevState *st, int it0, int cur0, int cap, cudaGraphConditionalHandle h, cudaStream_t s) {
@@ -464,10 +495,13 @@ void launch_sv_loop_init(DevState *st, int it0, int cur0, int cap, cudaGraphCond
 
 void launch_sv_loop_body(const uint2 *eb0, const uint2 *eb1, vid_t n, vid_t *parent, vid_t *hooked_list,
                          DevState *st, cudaGraphConditionalHandle h, int grid, cudaStream_t s) {
-    k_sv_pass_loop<<<grid, kBlock, 0, s>>>(eb0, eb1, n, parent, hooked_list, st);
-    k_sv_shortcut<<<grid, kBlock, 0, s>>>(parent, hooked_list, st, -1);
+    k_sv_pass_loop<<<fit_grid((const void *)k_sv_pass_loop, grid, kBlock), kBlock, 0, s>>>(eb0, eb1, n, parent,
+                                                                                            hooked_list, st);
+    k_sv_shortcut<<<fit_grid((const void *)k_sv_shortcut, grid, kBlock), kBlock, 0, s>>>(parent, hooked_list, st, -1);
     k_sv_loop_step<<<1, 1, 0, s>>>(st, h);
 }
+
+void launch_stream_finish(DevState *st, int it, cudaStream_t s) { k_stream_finish<<<1, 1, 0, s>>>(st, it); }
 
 void launch_parent_init(vid_t *parent, vid_t n, const uint32_t *vis, vid_t cmin, int grid, cudaStream_t s) {
     if (n == 0) return;
@@ -477,7 +511,7 @@ void launch_parent_init(vid_t *parent, vid_t n, const uint32_t *vis, vid_t cmin,
 template <typename T>
 void launch_finalize(vid_t *parent, vid_t n, void *labels, int grid, cudaStream_t s) {
     if (n == 0) return;
-    k_finalize<T><<<grid, kBlock, 0, s>>>(parent, n, (T *)labels);
+    k_finalize<T><<<fit_grid((const void *)k_finalize<T>, grid, kBlock), kBlock, 0, s>>>(parent, n, (T *)labels);
 }
 template void launch_finalize<int32_t>(vid_t *, vid_t, void *, int, cudaStream_t);
 template void launch_finalize<int64_t>(vid_t *, vid_t, void *, int, cudaStream_t);

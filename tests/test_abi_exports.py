@@ -47,3 +47,34 @@ def test_no_gpu_calls_fail_cleanly():
     assert o.id_bytes == 4 and abs(o.ks_tau - 0.05) < 1e-15 and o.ks_min_tail == 50 and o.ks_min_span == 10.0
     assert cc.strerror(0) == "ok"
     assert "outside" in cc.strerror(2)
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's ctypes structs have the C structs' sizes and field offsets
+    (a C program compiled against the header prints them)."""
+    import shutil
+
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    import paper_1607_06156_gb300 as cc
+
+    checks = {"cc_options": (cc.Options, ["ks_tau", "ks_min_span", "profile", "bfs_mode"]),
+              "cc_stats": (cc.Stats, ["ks_d", "m_active", "ms_degree", "launches", "kernel_ms", "sv_hooks",
+                                      "ms_features", "batch_unroll", "batch_grid_mult"]),
+              "cc_l2_rates": (cc.L2Rates, ["gather", "atom_min", "table_words", "grid"])}
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "cc_gb300.h"', "int main(void) {"]
+    for name, (_, fields) in checks.items():
+        src.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f in fields:
+            src.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    src.append("return 0; }")
+    c = tmp_path / "sizes.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for name, (cls, fields) in checks.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f in fields:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
