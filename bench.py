@@ -440,6 +440,8 @@ def main() -> int:
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ref-pairs", type=int, default=1 << 24, help="pairs per step of the CPU oracle")
     ap.add_argument("--cpu-pairs", type=int, default=1 << 25, help="pairs in the cpu_baseline sample")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer timing")
+    ap.add_argument("--no-l2", action="store_true", help="skip the live L2 rate probe (no l2_roofline)")
     ap.add_argument("--ncu-summary", metavar="CSV",
                     help="print the DRAM traffic summary of an ncu --csv capture of --workload and exit")
     ap.add_argument("--ncu-command", default="", help="the command line of that capture (recorded)")
@@ -548,13 +550,15 @@ def main() -> int:
                    "gbs": (alg_bytes(k, last, w) / (kms[k] / args.steps / 1e3) / 1e9) if kms[k] > 0 else None}
                for k in kms if kla[k]}
     # the scattered-access ceiling: measured L2 random-op rates of this GPU (outside the timed region)
-    rates = eng.l2_rates()
+    rates = None if args.no_l2 else eng.l2_rates()
     for k, kv in kernels.items():
         ops, op = l2_ops(k, last)
-        if ops > 0 and kv["ms_per_step"] > 0:
+        if rates and ops > 0 and kv["ms_per_step"] > 0:
             kv["l2_gops"] = ops / (kv["ms_per_step"] / 1e3) / 1e9
             kv["l2_frac"] = kv["l2_gops"] * 1e9 / rates[op]
     ops, op = l2_ops(dom, last)
+    if rates is None:
+        rates = {"gather": 0.0, "red_add": 0.0, "red_min": 0.0, "atom_min": 0.0}
     l2_roofline = {"bound": "l2_random_ops", "kernel": dom, "op": op,
                    "ops_per_launch": ops / launches_per_call,
                    "achieved": ops / launches_per_call / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0,
@@ -563,13 +567,15 @@ def main() -> int:
                                   "(cc_measure_l2_rates, best of 3)",
                    "rates_gops": {r: rates[r] / 1e9 for r in ("gather", "red_add", "red_min", "atom_min")}}
     l2_roofline["frac"] = l2_roofline["achieved"] / l2_roofline["peak"] if l2_roofline["peak"] else None
+    if args.no_l2:
+        l2_roofline = None
 
     # end to end through host buffers with the public host-input call
     # (cc_labels_host): the H2D copy of the pairs (chunked, overlapped with the
     # passes that stream them) and the D2H copy of the labels are inside the
     # timed region
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e and (rank == 0 or world > 1):
         h_edges = torch.from_numpy(g.edges).pin_memory()
         h_lab = torch.empty(n, dtype=lab.dtype).pin_memory()
         steps_e2e = max(3, min(args.steps, 10))

@@ -738,6 +738,22 @@ struct JoinGuard {
     ~JoinGuard() { join(); }
 };
 
+cc_status ensure_batch_route(cc_ctx *ctx, int G, int blocks = 0);
+
+// The route of a small graph by the one-block fit (the degrees are in ctx->deg).
+cc_status enqueue_small_fit(cc_ctx *ctx, vid_t n, cudaStream_t s) {
+    KsBatchScratch sc{as<uint32_t>(ctx->kb_xs), as<unsigned long long>(ctx->kb_cnt), as<unsigned long long>(ctx->kb_cum),
+                      as<double>(ctx->kb_lnx), as<double>(ctx->kb_Dc), as<double>(ctx->kb_Ac), as<double>(ctx->kb_Zc)};
+    KsBatchOut out{as<double>(ctx->kb_D),     as<double>(ctx->kb_alpha), as<long long>(ctx->kb_xmin),
+                   as<long long>(ctx->kb_ntail), as<long long>(ctx->kb_ncand), as<int>(ctx->kb_route),
+                   as<int>(ctx->kb_ovf),      as<unsigned long long>(ctx->kb_seed)};
+    int64_t *vo = reinterpret_cast<int64_t *>(static_cast<char *>(ctx->counters.p) + 256);
+    Scope sc2(ctx, CC_K_KS, s, 3);
+    launch_fit_one(as<uint32_t>(ctx->deg), n, vo, sc, out, as<DevState>(ctx->st), ctx->opt.ks_min_tail,
+                   ctx->opt.ks_min_distinct, ctx->opt.ks_min_span, ctx->opt.ks_tau, s);
+    return CC_OK;
+}
+
 // Work cc_labels_host has already enqueued while the pairs were copied: the
 // device state zeroed and EV_START recorded, the degrees counted (AUTO), and
 // the first SV pass (parent init, unrecorded hook pass, full shortcut) on the
@@ -836,11 +852,28 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         }
     }
     if (!learned && policy != CC_ROUTE_FORCE_SV && m > 0) {
-        enqueue_degree<T>(ctx, edges, n, m, s, pre && pre->degree_counted);
-        rec(ctx, EV_DEGREE, s);
-        if (policy != CC_ROUTE_FORCE_BFS) {
+        // Small graphs (n <= 2^20, fewer than 4,097 vertices of degree >= 4,096
+        // possible) take the one-block fit of the batched form: the histogram,
+        // the fit and the seed in one launch instead of the grid-wide kernels
+        // sized for 2^20 histogram bins.
+        const bool small = !pre && n <= (1u << 20) && 2 * m < 4096LL * 4097LL && policy != CC_ROUTE_FORCE_BFS;
+        if (small) {
+            CC_TRY(ensure_batch_route(ctx, 1, 1));
+            CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s));
+            {
+                Scope sc(ctx, CC_K_DEGREE, s, m > 0);
+                launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), st, ctx->grid, s);
+            }
+            rec(ctx, EV_DEGREE, s);
             CC_TRY(speculate());
-            enqueue_ks(ctx, s, distinct_degree_bound(ctx, n, m));
+            CC_TRY(enqueue_small_fit(ctx, n, s));
+        } else {
+            enqueue_degree<T>(ctx, edges, n, m, s, pre && pre->degree_counted);
+            rec(ctx, EV_DEGREE, s);
+            if (policy != CC_ROUTE_FORCE_BFS) {
+                CC_TRY(speculate());
+                enqueue_ks(ctx, s, distinct_degree_bound(ctx, n, m));
+            }
         }
         rec(ctx, EV_PREDICT, s);
         CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, kept), cudaMemcpyDeviceToHost, s));
@@ -1088,6 +1121,10 @@ cc_status labels_host_impl(cc_ctx *ctx, const void *edges_host, vid_t n, long lo
         }
         launch_parent_init(parent, n, nullptr, 0, ctx->grid, side);
         pre.launches++;
+        // Whole SV iterations per chunk pay off while the parent array stays in
+        // L2 (their root chases are then L2 hits); above 2^25 vertices each
+        // chunk only takes the first pass, which needs no chase.
+        const bool stream_sv = n <= (1u << 25);
         // the hub table lives in ebuf1: ebuf0 receives the crossing pairs
         const bool hubs = degree_uses_hubs(m) && ctx->ebuf1.bytes >= degree_hubs_scratch_bytes();
         unsigned *scratch = as<unsigned>(ctx->ebuf1);
@@ -1110,22 +1147,34 @@ cc_status labels_host_impl(cc_ctx *ctx, const void *edges_host, vid_t n, long lo
                     pre.launches++;
                 }
             }
-            // SV iteration i + 1 over this chunk, appended after the earlier chunks' surviving pairs
             CU_TRY(cudaStreamWaitEvent(side, ctx->ev_chunk[i], 0));
-            launch_sv_pass<T>(3, true, true, chunk, len, n, parent, nullptr, 0, hooked, list, st, i + 1, ctx->grid,
-                              side);
-            launch_sv_shortcut(parent, hooked, st, i + 1, ctx->grid, side);
-            pre.launches += 2;
+            if (stream_sv) {
+                // SV iteration i + 1 over this chunk, appended after the earlier chunks' surviving pairs
+                launch_sv_pass<T>(3, true, true, chunk, len, n, parent, nullptr, 0, hooked, list, st, i + 1,
+                                  ctx->grid, side);
+                launch_sv_shortcut(parent, hooked, st, i + 1, ctx->grid, side);
+                pre.launches += 2;
+            } else {
+                // the first SV pass (every vertex its own root) over this chunk
+                launch_sv_pass<T>(0, false, false, chunk, len, n, parent, nullptr, 0, hooked, nullptr, st, 0,
+                                  ctx->grid, side);
+                pre.launches++;
+            }
         }
-        launch_shortcut_all(parent, n, st, chunks, ctx->grid, side);
-        launch_stream_finish(st, chunks, side);
-        pre.launches += 2;
+        if (stream_sv) {
+            launch_shortcut_all(parent, n, st, chunks, ctx->grid, side);
+            launch_stream_finish(st, chunks, side);
+        } else {
+            launch_shortcut_all(parent, n, st, 0, ctx->grid, side);
+        }
+        pre.launches += stream_sv ? 2 : 1;
         CU_TRY(cudaEventRecord(ctx->ev_join, side));
         // `s` continues after every chunk has landed (the later passes read all pairs)
         CU_TRY(cudaStreamWaitEvent(s, ctx->ev_chunk[chunks - 1], 0));
         pre.degree_counted = count;
-        pre.streamed = true;
-        pre.it0 = chunks;
+        pre.streamed = stream_sv;
+        pre.first_pass_done = !stream_sv;
+        pre.it0 = stream_sv ? chunks : 0;
         rc = labels_impl<T>(ctx, dev, n, m, ctx->hlabels.p, s, &pre);
     }
     if (rc != CC_OK) return rc;
@@ -1200,8 +1249,10 @@ cc_status tune_batch(cc_ctx *ctx, const int32_t *edges, long long m, const int64
 // vertices of high degree than its shared-memory list holds takes the
 // single-graph fit on its degree slice instead. Outputs stay on the device
 // (kb_*), the routes and seeds are also returned on the host.
-cc_status ensure_batch_route(cc_ctx *ctx, int G) {
-    if (ctx->kb_blocks == 0) ctx->kb_blocks = ctx->num_sms * 3;  // 3 blocks of k_ks_batch fit on an SM
+// blocks: scratch for this many k_ks_batch blocks (0 = a full grid, 3 per SM)
+cc_status ensure_batch_route(cc_ctx *ctx, int G, int blocks) {
+    const int want = blocks > 0 ? blocks : ctx->num_sms * 3;  // 3 blocks of k_ks_batch fit on an SM
+    if (want > ctx->kb_blocks) ctx->kb_blocks = want;
     const size_t E = ks_batch_entries(), B = (size_t)ctx->kb_blocks;
     CC_TRY(buf_reserve(ctx, ctx->kb_xs, B * E * 4));
     CC_TRY(buf_reserve(ctx, ctx->kb_cnt, B * E * 8));
@@ -1468,7 +1519,7 @@ cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int6
     CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)(n > 0 ? n : 1) * 4, s));
     CC_TRY(ensure_tiles(ctx, edge_offsets_dev, vertex_offsets_dev, G, m, n, s));
     launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, as<uint32_t>(ctx->deg),
-                        st, ctx->grid, s, as<uint32_t>(ctx->tile_pairs));
+                        st, ctx->grid, s);
     std::vector<int> route;
     CC_TRY(batch_routes(ctx, vertex_offsets_dev, vertex_offsets_host, G, route, s));
     std::vector<long long> xmin((size_t)G), ncand((size_t)G);
@@ -1552,7 +1603,7 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
             {
                 Scope sc(ctx, CC_K_DEGREE, s, 1);
                 launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G,
-                                    as<uint32_t>(ctx->deg), st, ctx->grid, s, as<uint32_t>(ctx->tile_pairs));
+                                    as<uint32_t>(ctx->deg), st, ctx->grid, s);
             }
             Scope sc(ctx, CC_K_SV_FIRST, s, 1);
             launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,

@@ -152,6 +152,29 @@ __device__ __forceinline__ unsigned long long block_reserve(unsigned long long *
 // The graph of every 2^kTileShift-th pair (and vertex) is precomputed
 // (k_tile_graphs), so a tile starts its forward scan without a search.
 constexpr int kTileShift = 9;
+
+
+// A thread's position in the batch while it walks increasing pair indices:
+// the graph, where its pairs end, its first union id and its vertex count.
+// Offsets are read only when the walk crosses into the next graph.
+struct GraphCursor {
+    int g;
+    long long kend, base, ng;
+    __device__ __forceinline__ void start(const int64_t *eo, const int64_t *vo, int g0) {
+        g = g0;
+        kend = eo[g + 1];
+        base = vo[g];
+        ng = vo[g + 1] - base;
+    }
+    __device__ __forceinline__ void seek(const int64_t *eo, const int64_t *vo, int G, long long k) {
+        while (k >= kend && g + 1 < G) {
+            g++;
+            kend = eo[g + 1];
+            base = vo[g];
+            ng = vo[g + 1] - base;
+        }
+    }
+};
 // largest g in [0, G) with off[g] <= k (skips empty graphs)
 __device__ __forceinline__ int graph_search(const int64_t *off, int G, long long k) {
     int lo = 0, hi = G - 1;

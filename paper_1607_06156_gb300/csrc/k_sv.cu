@@ -364,12 +364,14 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restr
         }
         vid_t ru[K], rv[K];
         bool keep[K], hk[K];
+        GraphCursor gc;
+        gc.start(eo, vo, g0);
 #pragma unroll
         for (int r = 0; r < K; r++) {
             keep[r] = hk[r] = false;
             if (!valid[r]) continue;
-            const int g = graph_advance(eo, G, k[r], g0);
-            const long long base = vo[g], ng = vo[g + 1] - base;
+            gc.seek(eo, vo, G, k[r]);
+            const long long base = gc.base, ng = gc.ng;
             if (u[r] < 0 || v[r] < 0 || u[r] >= ng || v[r] >= ng) {
                 bad = true;
                 continue;

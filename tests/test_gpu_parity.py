@@ -342,3 +342,23 @@ def test_hub_aware_degree_pass_extremes(kind):
     assert np.array_equal(deg.cpu().numpy().astype(np.int64), deg_o)
     assert np.array_equal(hist.cpu().numpy(), oracle.histogram(deg_o))
     eng.close()
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: gg.chung_lu(seed=8, n=1 << 20, avg_degree=6, alpha=2.4),   # n = 2^20: the one-block fit
+    lambda: gg.chung_lu(seed=8, n=(1 << 20) + 1, avg_degree=6, alpha=2.4),  # one more vertex: the grid-wide fit
+    lambda: gg.planted(seed=4),
+])
+def test_small_and_grid_fits_agree_with_oracle(maker):
+    """Graphs of at most 2^20 vertices (and fewer than 4,097 vertices of degree
+    >= 4,096 possible) take the one-block fit inside cc_labels, larger ones the
+    grid-wide kernels; both match the oracle's fit of the same histogram."""
+    g = maker()
+    deg = oracle.degrees(g.edges, g.n)
+    want = oracle.ks_fit(oracle.histogram(deg))
+    got, st = run_engine(g.edges, g.n, route="auto")
+    assert abs(st["ks_d"] - want["D"]) < 1e-9
+    assert st["ks_xmin"] == want["xmin"] and st["ks_ncand"] == want["ncand"]
+    assert st["route"] == int(oracle.route_is_bfs(want["D"]))
+    assert st["max_degree"] == int(deg.max()) and st["seed_vertex"] == int(np.argmax(deg))
+    assert np.array_equal(got, oracle.cc_labels(g.edges, g.n, cross_check=False))
