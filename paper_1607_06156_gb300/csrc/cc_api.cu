@@ -719,7 +719,13 @@ cc_status run_bfs_edges(cc_ctx *ctx, const void *edges, vid_t n, long long m, cu
 }
 
 cc_status ensure_side(cc_ctx *ctx) {
-    if (!ctx->side_s) CU_TRY(cudaStreamCreateWithFlags(&ctx->side_s, cudaStreamNonBlocking));
+    // lowest priority: the prediction on the caller's stream (the K-S fit, a
+    // few small grids) gets the SMs first and the speculative pass fills the rest
+    if (!ctx->side_s) {
+        int least = 0, greatest = 0;
+        CU_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CU_TRY(cudaStreamCreateWithPriority(&ctx->side_s, cudaStreamNonBlocking, least));
+    }
     if (!ctx->ev_fork) CU_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     if (!ctx->ev_join) CU_TRY(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
     return CC_OK;

@@ -191,6 +191,45 @@ __device__ __forceinline__ int graph_advance(const int64_t *off, int G, long lon
     return g;
 }
 
+// block_reserve for two counters at once: a = (count for counter A), b =
+// (count for counter B), each below 2^16 per thread and 2^16 per block; one
+// block-wide scan of a << 16 | b, one atomic per counter. Returns this
+// thread's first slot in each. sbase: two words.
+__device__ __forceinline__ void block_reserve2(unsigned long long *ca, unsigned long long *cb, int a, int b, int *sw,
+                                               unsigned long long *sbase, unsigned long long &oa,
+                                               unsigned long long &ob) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = (a << 16) | b;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sw[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int w = lane < nw ? sw[lane] : 0, wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) sw[lane] = wi - w;
+        if (lane == nw - 1) {
+            const int ta = wi >> 16, tb = wi & 0xffff;
+            sbase[0] = ta ? atomicAdd(ca, (unsigned long long)ta) : 0ull;
+            sbase[1] = tb ? atomicAdd(cb, (unsigned long long)tb) : 0ull;
+        }
+    }
+    __syncthreads();
+    const int ex = sw[warp] + incl - c;
+    oa = sbase[0] + (unsigned long long)(ex >> 16);
+    ob = sbase[1] + (unsigned long long)(ex & 0xffff);
+    __syncthreads();
+}
+
 // Grid-stride helpers
 __device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }

@@ -99,6 +99,7 @@ __device__ __forceinline__ void sv_pass_body(const T *__restrict__ in, long long
     constexpr int K = P * U;  // pairs per thread per round
     __shared__ int sw[32];
     __shared__ unsigned long long sbase;
+    __shared__ unsigned long long sbase2[2];
     const long long nvec = m / P;
     const int4 *ev = reinterpret_cast<const int4 *>(in);
     const unsigned long long hbase = RECORD ? st->hook_base[it] : 0ull;
@@ -137,7 +138,21 @@ __device__ __forceinline__ void sv_pass_body(const T *__restrict__ in, long long
                 keep[0] = sv_pair<MODE, RECORD>(u, v, n, parent, vis, cmin, ru[0], rv[0], hk[0], bad);
             }
         }
-        if (WRITE) {
+        if (WRITE && RECORD) {  // both lists with one block-wide scan
+            int ck = 0, ch = 0;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                ck += keep[k];
+                ch += hk[k];
+            }
+            unsigned long long ok, oh;
+            block_reserve2(&st->kept[it], &st->hooked[it], ck, ch, sw, sbase2, ok, oh);
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                if (keep[k]) out[ok++] = make_uint2(ru[k], rv[k]);
+                if (hk[k]) hooked_list[hbase + oh++] = ru[k] > rv[k] ? ru[k] : rv[k];
+            }
+        } else if (WRITE) {
             int c = 0;
 #pragma unroll
             for (int k = 0; k < K; k++) c += keep[k];
@@ -145,8 +160,7 @@ __device__ __forceinline__ void sv_pass_body(const T *__restrict__ in, long long
 #pragma unroll
             for (int k = 0; k < K; k++)
                 if (keep[k]) out[o++] = make_uint2(ru[k], rv[k]);
-        }
-        if (RECORD) {
+        } else if (RECORD) {
             int c = 0;
 #pragma unroll
             for (int k = 0; k < K; k++) c += hk[k];
@@ -329,6 +343,7 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restr
     constexpr int K = 2 * U;
     __shared__ int sw[32];
     __shared__ unsigned long long sbase;
+    __shared__ unsigned long long sbase2[2];
     const long long nvec = m / 2;
     const int4 *ev = reinterpret_cast<const int4 *>(in);
     const unsigned long long hbase = RECORD ? st->hook_base[it] : 0ull;
@@ -383,7 +398,21 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restr
             keep[r] = sv_pair<MODE, RECORD>(base + u[r], base + v[r], ntot, parent, nullptr, 0, ru[r], rv[r], hk[r],
                                             bad);
         }
-        if (WRITE) {
+        if (WRITE && RECORD) {  // both lists with one block-wide scan
+            int ck = 0, ch = 0;
+#pragma unroll
+            for (int r = 0; r < K; r++) {
+                ck += keep[r];
+                ch += hk[r];
+            }
+            unsigned long long ok, oh;
+            block_reserve2(&st->kept[it], &st->hooked[it], ck, ch, sw, sbase2, ok, oh);
+#pragma unroll
+            for (int r = 0; r < K; r++) {
+                if (keep[r]) out[ok++] = make_uint2(ru[r], rv[r]);
+                if (hk[r]) hooked_list[hbase + oh++] = ru[r] > rv[r] ? ru[r] : rv[r];
+            }
+        } else if (WRITE) {
             int c = 0;
 #pragma unroll
             for (int r = 0; r < K; r++) c += keep[r];
@@ -391,15 +420,6 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restr
 #pragma unroll
             for (int r = 0; r < K; r++)
                 if (keep[r]) out[o++] = make_uint2(ru[r], rv[r]);
-        }
-        if (RECORD) {
-            int c = 0;
-#pragma unroll
-            for (int r = 0; r < K; r++) c += hk[r];
-            unsigned long long o = block_reserve(&st->hooked[it], c, sw, &sbase);
-#pragma unroll
-            for (int r = 0; r < K; r++)
-                if (hk[r]) hooked_list[hbase + o++] = ru[r] > rv[r] ? ru[r] : rv[r];
         }
     }
     if (bad) set_err(st, kErrInvalidEdge);
