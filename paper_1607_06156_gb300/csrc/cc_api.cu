@@ -760,6 +760,14 @@ cc_status enqueue_small_fit(cc_ctx *ctx, vid_t n, cudaStream_t s) {
     return CC_OK;
 }
 
+// Speculation of the single-graph route: kSpecDeep also runs SV iteration 1
+// (the gather pass over the pairs) on the side stream; kSpecEarly forks the
+// side stream before the degree pass instead of after it. Measured on R-MAT
+// 24: shallow 7.82 ms, deep 7.61 ms, deep and early 8.64 ms (the degree pass
+// and the hook passes then contend for the L2 atomics).
+constexpr bool kSpecDeep = true;
+constexpr bool kSpecEarly = false;
+
 // Work cc_labels_host has already enqueued while the pairs were copied: the
 // device state zeroed and EV_START recorded, the degrees counted (AUTO), and
 // the first SV pass (parent init, unrecorded hook pass, full shortcut) on the
@@ -805,6 +813,10 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     JoinGuard spec{ctx, s};
     if (pre && (pre->first_pass_done || pre->streamed)) spec.armed = true;
     const bool streamed = pre && pre->streamed;
+    const int cap = ctx->opt.fault_inject & CC_FAULT_ITER_CAP ? 1
+                    : ctx->opt.max_iters > 0                  ? ctx->opt.max_iters
+                                                              : default_max_iters(n);
+    bool deep_done = false;  // the side stream also ran SV iteration 1
     auto speculate = [&]() -> cc_status {
         if (spec.armed || m <= 0) return CC_OK;
         CC_TRY(ensure_side(ctx));
@@ -824,10 +836,25 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
             Scope sc(ctx, CC_K_SV_SHORTCUT, side, 1);
             launch_shortcut_all(parent, n, st, 0, ctx->grid, side);
         }
+        if (kSpecDeep && cap >= 2) {
+            // SV iteration 1 as well: the gather pass over the pairs, the crossing
+            // pairs into ebuf0 (the degree pass keeps its hub table in ebuf1)
+            {
+                Scope sc(ctx, CC_K_SV_GATHER_INPUT, side, 1);
+                launch_sv_pass<T>(2, true, true, edges, m, n, parent, nullptr, 0, hooked, as<uint2>(ctx->ebuf0), st, 1,
+                                  ctx->grid, side);
+            }
+            {
+                Scope sc(ctx, CC_K_SV_SHORTCUT, side, 1);
+                launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, side);
+            }
+            deep_done = true;
+        }
         CU_TRY(cudaEventRecord(ctx->ev_join, side));
         spec.armed = true;
         return CC_OK;
     };
+    if (kSpecEarly && policy == CC_ROUTE_AUTO) CC_TRY(speculate());
     int cutoff = ctx->opt.bfs_cutoff_levels;
     // Learned route: sampled features + network; a confident prediction skips
     // the exact degree pass and the K-S fit (its BFS is the edge-list BFS,
@@ -871,14 +898,16 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
                 launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), st, ctx->grid, s);
             }
             rec(ctx, EV_DEGREE, s);
-            CC_TRY(speculate());
+            // the fit is queued ahead of the speculative passes so that its few
+            // blocks are not left waiting behind them
             CC_TRY(enqueue_small_fit(ctx, n, s));
+            CC_TRY(speculate());
         } else {
             enqueue_degree<T>(ctx, edges, n, m, s, pre && pre->degree_counted);
             rec(ctx, EV_DEGREE, s);
             if (policy != CC_ROUTE_FORCE_BFS) {
-                CC_TRY(speculate());
                 enqueue_ks(ctx, s, distinct_degree_bound(ctx, n, m));
+                CC_TRY(speculate());
             }
         }
         rec(ctx, EV_PREDICT, s);
@@ -902,14 +931,11 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     const bool edge_bfs = learned || ctx->opt.bfs_mode == 1;
     if (route == 1 && !edge_bfs && 2ull * (unsigned long long)m >= 0xffffffffull) route = 0;
     S.route = route;
-    const int cap = ctx->opt.fault_inject & CC_FAULT_ITER_CAP ? 1
-                    : ctx->opt.max_iters > 0                  ? ctx->opt.max_iters
-                                                              : default_max_iters(n);
     uint2 *eb[2] = {as<uint2>(ctx->ebuf0), as<uint2>(ctx->ebuf1)};
     int it = 0, cur0 = 0;
     unsigned long long m_cur = 0;
     const void *src = nullptr;
-    if (route == 1 && streamed) {
+    if (route == 1 && (streamed || deep_done)) {
         // the BFS route replaces the iterations the host-input path streamed:
         // clear their per-iteration counters (the side stream is joined)
         CU_TRY(cudaMemsetAsync(&st->kept[0], 0, offsetof(DevState, front) - offsetof(DevState, kept), s));
@@ -960,20 +986,23 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         CC_TRY(read_back(ctx, &st->kept[0], 8, s));
         m_cur = ctx->h_st->kept[0];
         src = eb[cur0];
-    } else if (streamed) {
-        // the host-input path ran SV iterations 1..it0 while the pairs were copied
+    } else if (streamed || deep_done) {
+        // SV iterations 1..it0 already ran: per copied chunk (host-input path) or
+        // on the side stream during the prediction; the crossing pairs are in ebuf0
+        const int it0 = streamed ? pre->it0 : 1;
         S.m_active[0] = m;
+        if (deep_done) S.m_active[1] = m;
         if (!ctx->opt.profile) {
             auto pre_none = [&](cudaStream_t) {};
             auto post = [&](cudaStream_t cs) { launch_finalize<T>(parent, n, labels_out, ctx->grid, cs); };
-            const cc_ctx::GraphKey key = graph_key(ctx, (sizeof(T) == 4 ? 0 : 1) | 8 | (pre->it0 << 4), n, m, 0, edges,
+            const cc_ctx::GraphKey key = graph_key(ctx, (sizeof(T) == 4 ? 0 : 1) | 8 | (it0 << 4), n, m, 0, edges,
                                                    nullptr, nullptr, labels_out, cap);
-            CC_TRY(launch_sv_graph(ctx, ctx->g_single, key, n, pre->it0, 0, cap, pre_none, post, s));
+            CC_TRY(launch_sv_graph(ctx, ctx->g_single, key, n, it0, 0, cap, pre_none, post, s));
             rec(ctx, EV_SV, s);
             rec(ctx, EV_END, s);
-            return sv_graph_finish(ctx, pre->it0, 0, s);
+            return sv_graph_finish(ctx, it0, 0, s);
         }
-        it = pre->it0;
+        it = it0;
         CC_TRY(read_back(ctx, &st->kept[it], 8, s));
         m_cur = ctx->h_st->kept[it];
         src = eb[0];
