@@ -91,6 +91,9 @@ def alg_bytes(cls: str, st: dict, w: int) -> float:
     if cls == "finalize":
         return 4 * n + w * n
     if cls == "sv_first":
+        k = st.get("sv_sample_stride", 1) or 1
+        if k > 1:  # front end: two passes over m/k pairs (pre-check; two gathers and a pre-check)
+            return (4 * w + 16) * m / k
         return 2 * w * m + 4 * m
     if cls == "sv_gather_input":
         # read pairs, gather both parents, atomicMin per surviving pair, write survivors
@@ -121,6 +124,9 @@ def l2_ops(cls: str, st: dict) -> tuple[float, str]:
     if cls == "degree":
         return 2.0 * m, "red_add"            # one increment per pair endpoint
     if cls == "sv_first":
+        k = st.get("sv_sample_stride", 1) or 1
+        if k > 1:  # front end on m/k pairs: a pre-check, then two gathers and a pre-check
+            return 4.0 * m / k, "gather"
         return 1.0 * m, "gather"             # pre-check read of parent[max(u, v)]
     if cls == "sv_gather_input":
         kept = act[2] if len(act) > 2 else 0
@@ -160,7 +166,7 @@ def kernel_class(name: str):
     """Kernel class (the engine's profiling scopes) of a kernel name in an ncu list."""
     table = [("k_degree_hubs", "degree"), ("k_hub_", "degree"), ("k_degree<", "degree"), ("k_hist", "hist"),
              ("k_distinct", "ks"), ("k_ks_", "ks"), ("k_parent_init", "parent_init"),
-             ("k_sv_pass<int, 0", "sv_first"), ("k_sv_pass<long, 0", "sv_first"),
+             ("k_sv_pass<int, 0", "sv_first"), ("k_sv_pass<long, 0", "sv_first"), ("k_sv_sample", "sv_first"),
              ("k_sv_pass<int, 2", "sv_gather_input"), ("k_sv_pass<long, 2", "sv_gather_input"),
              ("k_sv_pass<unsigned int, 2", "sv_gather_list"), ("k_shortcut_all", "sv_shortcut"),
              ("k_sv_shortcut", "sv_shortcut"), ("k_finalize", "finalize")]

@@ -88,7 +88,12 @@ typedef struct {
     int bfs_mode;           /* BFS engine: 0 = direction-optimizing BFS on a CSR (default),
                                1 = edge-list BFS (each level one pass over the active pairs, no CSR);
                                the learned route always uses 1 */
-    int reserved[2];
+    int sv_sample_stride;   /* SV front end: before the first pass over all pairs, hook passes over
+                               one block of pairs in k (k = sv_sample_stride, 1..1024) join most of
+                               every large component; 0 = default (from 2^22 pairs: k = the largest
+                               power of two <= 2m/n, at most 64, none if that is below 4), 1 = none;
+                               the labels are the same either way */
+    int reserved[1];
 } cc_options;
 
 /* Kernel classes reported in cc_stats.kernel_ms / kernel_launches. */
@@ -144,6 +149,9 @@ typedef struct {
     float ms_features;                  /* learned policy: device time of features + inference */
     int32_t batch_unroll;               /* batched form: tuned 16-byte vectors per thread per tile of the hook passes */
     int32_t batch_grid_mult;            /* batched form: tuned blocks per launch, in resident-grid multiples */
+    int32_t sv_sample_stride;           /* SV front end: one block of pairs in this many was sampled (1 = no
+                                           front end; 0 = no first pass over the input pairs in this call) */
+    int32_t pad2;
 } cc_stats;
 
 /* Fills *opt with the defaults listed above. */

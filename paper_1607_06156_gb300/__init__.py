@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
         ("ks_min_tail", ctypes.c_int), ("ks_min_distinct", ctypes.c_int), ("max_iters", ctypes.c_int),
         ("bfs_cutoff_levels", ctypes.c_int), ("debug_checks", ctypes.c_int), ("fault_inject", ctypes.c_int),
         ("ks_min_span", ctypes.c_double), ("profile", ctypes.c_int), ("bfs_mode", ctypes.c_int),
-        ("reserved", ctypes.c_int * 2),
+        ("sv_sample_stride", ctypes.c_int), ("reserved", ctypes.c_int * 1),
     ]
 
 
@@ -67,6 +67,7 @@ class Stats(ctypes.Structure):
         ("ms_features", ctypes.c_float),
         ("batch_unroll", ctypes.c_int32),
         ("batch_grid_mult", ctypes.c_int32),
+        ("sv_sample_stride", ctypes.c_int32), ("pad2", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

@@ -99,6 +99,10 @@ template <typename T>
 void launch_sv_pass(int mode, bool write, bool record, const void *in, long long m, vid_t n, vid_t *parent,
                     const uint32_t *vis, vid_t cmin, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
                     cudaStream_t s);
+// hook pass (mode 0 or 2, nothing recorded) over one tile in tstride of the pairs
+template <typename T>
+void launch_sv_sample(int mode, const void *in, long long m, vid_t n, vid_t *parent, DevState *st, int tstride,
+                      int grid, cudaStream_t s);
 void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid, cudaStream_t s);
 void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
                           vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,

@@ -89,10 +89,14 @@ template <> struct PassUnroll<int64_t> { static constexpr int U = 4; };
 
 // MODE 3 (the chunks of the host-input path) appends its surviving pairs
 // after those of the earlier chunks: at out + kept_base[it].
-template <typename T, int MODE, bool WRITE, bool RECORD>
+//
+// SAMPLED passes read one tile in `tstride` (tiles of kBlock * U vectors,
+// whole tiles so the reads stay coalesced) and skip the odd last pair: the
+// sample front end of the SV route.
+template <typename T, int MODE, bool WRITE, bool RECORD, bool SAMPLED = false>
 __device__ __forceinline__ void sv_pass_body(const T *__restrict__ in, long long m, vid_t n, vid_t *parent,
                                              const uint32_t *__restrict__ vis, vid_t cmin, vid_t *hooked_list,
-                                             uint2 *__restrict__ out, DevState *st, int it) {
+                                             uint2 *__restrict__ out, DevState *st, int it, int tstride = 1) {
     if (MODE == 3 && WRITE) out += st->kept_base[it];
     constexpr int P = PairVec<T>::kPairs;
     constexpr int U = PassUnroll<T>::U;
@@ -107,7 +111,9 @@ __device__ __forceinline__ void sv_pass_body(const T *__restrict__ in, long long
     // block-contiguous tiles of kBlock * U vectors, so the block's rounds are uniform
     const long long tile = (long long)kBlock * U;
     const long long ntiles = (nvec + tile - 1) / tile;
-    for (long long t = blockIdx.x; t < ntiles + (P == 2 && (m & 1) ? 1 : 0); t += gridDim.x) {
+    const long long nt = SAMPLED ? (ntiles + tstride - 1) / tstride : ntiles + (P == 2 && (m & 1) ? 1 : 0);
+    for (long long tt = blockIdx.x; tt < nt; tt += gridDim.x) {
+        const long long t = SAMPLED ? tt * tstride : tt;
         vid_t ru[K], rv[K];
         bool keep[K], hk[K];
         if (t < ntiles) {
@@ -183,6 +189,14 @@ __global__ void __launch_bounds__(kBlock, PassMinBlocks<T>::v) k_sv_pass(const T
                                                     const uint32_t *__restrict__ vis, vid_t cmin, vid_t *hooked_list,
                                                     uint2 *__restrict__ out, DevState *st, int it) {
     sv_pass_body<T, MODE, WRITE, RECORD>(in, m, n, parent, vis, cmin, hooked_list, out, st, it);
+}
+
+// The sample passes of the SV front end: MODE 0 (identity parents) or
+// MODE 2 (one-hop gathers), hooks only (no list is written, no hook recorded).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kBlock, PassMinBlocks<T>::v) k_sv_sample(const T *__restrict__ in, long long m, vid_t n,
+                                                                           vid_t *parent, DevState *st, int tstride) {
+    sv_pass_body<T, MODE, false, false, true>(in, m, n, parent, nullptr, 0, nullptr, nullptr, st, 0, tstride);
 }
 
 // ---------------------------------------------------------------------------
@@ -502,6 +516,20 @@ template void launch_sv_pass<int64_t>(int, bool, bool, const void *, long long, 
                                       vid_t, vid_t *, uint2 *, DevState *, int, int, cudaStream_t);
 template void launch_sv_pass<uint32_t>(int, bool, bool, const void *, long long, vid_t, vid_t *, const uint32_t *,
                                        vid_t, vid_t *, uint2 *, DevState *, int, int, cudaStream_t);
+
+// A hook pass of the SV front end over one tile in tstride of the pairs:
+// mode 0 with identity parents, mode 2 with every vertex pointing at a root.
+template <typename T>
+void launch_sv_sample(int mode, const void *in, long long m, vid_t n, vid_t *parent, DevState *st, int tstride,
+                      int grid, cudaStream_t s) {
+    if (m <= 0) return;
+    auto kf = mode == 0 ? k_sv_sample<T, 0> : k_sv_sample<T, 2>;
+    kf<<<fit_grid((const void *)kf, grid, kBlock), kBlock, 0, s>>>((const T *)in, m, n, parent, st, tstride);
+}
+template void launch_sv_sample<int32_t>(int, const void *, long long, vid_t, vid_t *, DevState *, int, int,
+                                        cudaStream_t);
+template void launch_sv_sample<int64_t>(int, const void *, long long, vid_t, vid_t *, DevState *, int, int,
+                                        cudaStream_t);
 
 void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid, cudaStream_t s) {
     k_shortcut_all<<<fit_grid((const void *)k_shortcut_all, grid, kBlock), kBlock, 0, s>>>(parent, n, st, it);

@@ -362,3 +362,54 @@ def test_small_and_grid_fits_agree_with_oracle(maker):
     assert st["route"] == int(oracle.route_is_bfs(want["D"]))
     assert st["max_degree"] == int(deg.max()) and st["seed_vertex"] == int(np.argmax(deg))
     assert np.array_equal(got, oracle.cc_labels(g.edges, g.n, cross_check=False))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("stride", [0, 1, 2, 8, 1024])
+@pytest.mark.parametrize("route", ["auto", "sv"])
+def test_sv_sample_front_end(stride, route):
+    """The SV front end hooks over one tile of pairs in `stride` before the
+    first pass over all pairs (default 8 from 2^22 pairs, 1 = none). Labels
+    are the oracle's for every stride, on the graph-driven and the
+    host-driven (profiled) loop, with an odd number of pairs."""
+    g = gg.rmat(seed=44, scale=18, edge_factor=16, m=(1 << 22) + 3)
+    want = oracle.cc_labels(g.edges, g.n, cross_check=False)
+    for profile in (0, 1):
+        got, st = run_engine(g.edges, g.n, route=route, sv_sample_stride=stride, profile=profile)
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, f"stride={stride} profile={profile}: {bad.size} labels differ, first at {bad[:5]}"
+        # 2m / n = 32: the default samples one block in 32
+        assert st["sv_sample_stride"] == (32 if stride == 0 else stride)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["sorted", "chains64", "planted"])
+def test_sv_sample_front_end_inputs(kind):
+    """Pairs sorted by their first id (a strided sample still covers every
+    vertex range), int64 chain forests (long paths the sample cuts into
+    pieces), and a graph below the default threshold with a forced stride."""
+    if kind == "sorted":
+        g = gg.chung_lu(seed=5, n=1 << 20, avg_degree=10, alpha=2.3)
+        e = g.edges[np.lexsort((g.edges[:, 1], g.edges[:, 0]))]
+        n, strides = g.n, (0, 4)
+    elif kind == "chains64":  # 2m / n ~ 2: no front end by default
+        g = gg.grid_chains(seed=6, W=600, nchains=300_000, id_bytes=8)
+        e, n, strides = g.edges, g.n, (0, 3, 16)
+        _, st = run_engine(e, n, route="sv")
+        assert st["sv_sample_stride"] == 1
+    else:
+        g = gg.planted(seed=7)
+        e, n, strides = g.edges, g.n, (0, 2, 5)
+    want = oracle.cc_labels(e, n, cross_check=False)
+    for k in strides:
+        assert_labels_match(e, n, want=want, routes=("auto", "sv"), sv_sample_stride=k)
+
+
+@pytest.mark.gpu
+def test_sv_sample_stride_validated():
+    torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    for bad in (-1, 1025):
+        with pytest.raises(cc.CCError):
+            cc.Engine(sv_sample_stride=bad)
