@@ -77,6 +77,9 @@ struct cc_ctx {
     // side stream of the speculative first SV pass, with its fork and join events
     cudaStream_t side_s = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // highest-priority stream of the K-S fit while the speculative pass runs, with its join event
+    cudaStream_t fit_s = nullptr;
+    cudaEvent_t ev_fit = nullptr;
     // host-input entry point: device copies of the pairs and labels, the copy
     // stream and one event per copied chunk
     Buf hedges, hlabels;
@@ -732,6 +735,16 @@ cc_status ensure_side(cc_ctx *ctx) {
     return CC_OK;
 }
 
+cc_status ensure_fit_stream(cc_ctx *ctx) {
+    if (!ctx->fit_s) {
+        int least = 0, greatest = 0;
+        CU_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CU_TRY(cudaStreamCreateWithPriority(&ctx->fit_s, cudaStreamNonBlocking, greatest));
+    }
+    if (!ctx->ev_fit) CU_TRY(cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming));
+    return CC_OK;
+}
+
 // Orders all later work on `s` after the side stream's speculative pass, on
 // every exit path (the next call must not reset state the side stream uses).
 struct JoinGuard {
@@ -827,10 +840,17 @@ int enqueue_first_pass(cc_ctx *ctx, const void *edges, vid_t n, long long m, cud
 // Speculation of the single-graph route: kSpecDeep also runs SV iteration 1
 // (the gather pass over the pairs) on the side stream; kSpecEarly forks the
 // side stream before the degree pass instead of after it. Measured on R-MAT
-// 24: shallow 7.82 ms, deep 7.61 ms, deep and early 8.64 ms (the degree pass
-// and the hook passes then contend for the L2 atomics).
+// 24 (before the SV front end): shallow 7.82 ms, deep 7.61 ms, deep and
+// early 8.64 ms (the degree pass and the hook passes then contend for the L2
+// atomics). kSpecBeforeFit forks it before the K-S fit, which then runs on
+// a highest-priority stream while the gather pass launches one block per
+// tile (so the fit's blocks get SMs as gather blocks retire) instead of
+// after the fit. Measured with the front end, R-MAT 24 / 22: after the fit
+// 5.44 / 1.75 ms, before 5.26 / 1.56 ms; forking the front end alone before
+// the degree pass as well: 5.29 / 1.53 ms (not kept).
 constexpr bool kSpecDeep = true;
 constexpr bool kSpecEarly = false;
+constexpr bool kSpecBeforeFit = true;
 
 // Work cc_labels_host has already enqueued while the pairs were copied: the
 // device state zeroed and EV_START recorded, the degrees counted (AUTO), and
@@ -897,8 +917,11 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
             // pairs into ebuf0 (the degree pass keeps its hub table in ebuf1)
             {
                 Scope sc(ctx, CC_K_SV_GATHER_INPUT, side, 1);
-                launch_sv_pass<T>(2, true, true, edges, m, n, parent, nullptr, 0, hooked, as<uint2>(ctx->ebuf0), st, 1,
-                                  ctx->grid, side);
+                if (kSpecBeforeFit)
+                    launch_sv_gather_tiles<T>(edges, m, n, parent, hooked, as<uint2>(ctx->ebuf0), st, 1, side);
+                else
+                    launch_sv_pass<T>(2, true, true, edges, m, n, parent, nullptr, 0, hooked, as<uint2>(ctx->ebuf0),
+                                      st, 1, ctx->grid, side);
             }
             {
                 Scope sc(ctx, CC_K_SV_SHORTCUT, side, 1);
@@ -962,8 +985,21 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
             enqueue_degree<T>(ctx, edges, n, m, s, pre && pre->degree_counted);
             rec(ctx, EV_DEGREE, s);
             if (policy != CC_ROUTE_FORCE_BFS) {
-                enqueue_ks(ctx, s, distinct_degree_bound(ctx, n, m));
-                CC_TRY(speculate());
+                if (kSpecBeforeFit) {
+                    // the fit on a highest-priority stream: the speculative gather
+                    // launches one block per tile, so the fit's blocks are
+                    // scheduled as soon as gather blocks retire
+                    CC_TRY(speculate());
+                    CC_TRY(ensure_fit_stream(ctx));
+                    CU_TRY(cudaEventRecord(ctx->ev_fork, s));
+                    CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
+                    enqueue_ks(ctx, ctx->fit_s, distinct_degree_bound(ctx, n, m));
+                    CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
+                    CU_TRY(cudaStreamWaitEvent(s, ctx->ev_fit, 0));
+                } else {
+                    enqueue_ks(ctx, s, distinct_degree_bound(ctx, n, m));
+                    CC_TRY(speculate());
+                }
             }
         }
         rec(ctx, EV_PREDICT, s);
@@ -1504,6 +1540,8 @@ cc_status cc_destroy(cc_ctx *ctx) {
     if (ctx->copy_s) cudaStreamDestroy(ctx->copy_s);
     for (cudaEvent_t e : ctx->ev_chunk) cudaEventDestroy(e);
     if (ctx->side_s) cudaStreamDestroy(ctx->side_s);
+    if (ctx->fit_s) cudaStreamDestroy(ctx->fit_s);
+    if (ctx->ev_fit) cudaEventDestroy(ctx->ev_fit);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->cap_s) cudaStreamDestroy(ctx->cap_s);

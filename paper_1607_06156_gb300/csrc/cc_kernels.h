@@ -103,6 +103,10 @@ void launch_sv_pass(int mode, bool write, bool record, const void *in, long long
 template <typename T>
 void launch_sv_sample(int mode, const void *in, long long m, vid_t n, vid_t *parent, DevState *st, int tstride,
                       int grid, cudaStream_t s);
+// MODE 2 with record and write, one tile of pairs per block
+template <typename T>
+void launch_sv_gather_tiles(const void *in, long long m, vid_t n, vid_t *parent, vid_t *hooked_list, uint2 *out,
+                            DevState *st, int it, cudaStream_t s);
 void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid, cudaStream_t s);
 void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
                           vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,

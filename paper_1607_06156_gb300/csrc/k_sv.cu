@@ -531,6 +531,27 @@ template void launch_sv_sample<int32_t>(int, const void *, long long, vid_t, vid
 template void launch_sv_sample<int64_t>(int, const void *, long long, vid_t, vid_t *, DevState *, int, int,
                                         cudaStream_t);
 
+// The MODE 2 pass with one tile per block (instead of a resident grid that
+// strides over the tiles): blocks retire all through the pass, so kernels of
+// a higher-priority stream get SMs within a tile's time rather than after
+// the whole pass.
+template <typename T>
+void launch_sv_gather_tiles(const void *in, long long m, vid_t n, vid_t *parent, vid_t *hooked_list, uint2 *out,
+                            DevState *st, int it, cudaStream_t s) {
+    if (m <= 0) return;
+    constexpr int P = PairVec<T>::kPairs;
+    const long long tile = (long long)kBlock * PassUnroll<T>::U;
+    const long long nvec = m / P;
+    long long blocks = (nvec + tile - 1) / tile + (P == 2 && (m & 1) ? 1 : 0);
+    if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
+    k_sv_pass<T, 2, true, true><<<(unsigned)blocks, kBlock, 0, s>>>((const T *)in, m, n, parent, nullptr, 0, hooked_list,
+                                                                    out, st, it);
+}
+template void launch_sv_gather_tiles<int32_t>(const void *, long long, vid_t, vid_t *, vid_t *, uint2 *, DevState *,
+                                              int, cudaStream_t);
+template void launch_sv_gather_tiles<int64_t>(const void *, long long, vid_t, vid_t *, vid_t *, uint2 *, DevState *,
+                                              int, cudaStream_t);
+
 void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid, cudaStream_t s) {
     k_shortcut_all<<<fit_grid((const void *)k_shortcut_all, grid, kBlock), kBlock, 0, s>>>(parent, n, st, it);
 }
