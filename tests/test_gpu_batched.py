@@ -89,3 +89,12 @@ def test_single_graph_batch_equals_cc_labels():
     g = gg.rmat(seed=6, scale=16, edge_factor=8)
     got, _ = _run_batched(torch, g.edges, np.array([0, g.m], np.int64), np.array([0, g.n], np.int64))
     assert np.array_equal(got, oracle.cc_labels(g.edges, g.n))
+
+
+def test_batched_over_2_25_vertices():
+    """A batch of more than 2^25 vertices in all (a parent array larger than L2)."""
+    torch = torch_cuda()
+    b = gg.batch(seed=12, G=40, nmin=800_000, nmax=1_000_000, edge_factor=2)
+    assert b.vertex_offsets[-1] >= 1 << 25
+    got, _ = _run_batched(torch, b.edges, b.edge_offsets, b.vertex_offsets)
+    _check_each(b, got)

@@ -413,3 +413,18 @@ def test_sv_sample_stride_validated():
     for bad in (-1, 1025):
         with pytest.raises(cc.CCError):
             cc.Engine(sv_sample_stride=bad)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("id_bytes", [4, 8])
+def test_sparse_graph_over_2_25_vertices(id_bytes):
+    """n > 2^25 vertices (a parent array larger than L2): mostly isolated
+    vertices (their own roots), random pairs and a long chain (deep trees
+    before the last shortcut), n not a multiple of 4."""
+    n = (1 << 25) + 13
+    rng = np.random.default_rng(71)
+    rand = rng.integers(0, n, size=(1 << 21, 2))
+    chain = rng.permutation(n)[:600_000]
+    e = np.concatenate([rand, np.stack([chain[:-1], chain[1:]], axis=1), [[n - 1, n - 2], [n - 13, 3]]])
+    e = e.astype(np.int32 if id_bytes == 4 else np.int64)
+    assert_labels_match(e, n)
