@@ -742,6 +742,7 @@ cc_status ensure_fit_stream(cc_ctx *ctx) {
         CU_TRY(cudaStreamCreateWithPriority(&ctx->fit_s, cudaStreamNonBlocking, greatest));
     }
     if (!ctx->ev_fit) CU_TRY(cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming));
+    if (!ctx->ev_fork) CU_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     return CC_OK;
 }
 
@@ -1395,19 +1396,29 @@ cc_status ensure_batch_route(cc_ctx *ctx, int G, int blocks) {
 
 // deg holds the union degrees. Fills kb_* for every graph and returns the
 // routes (1 = BFS first) in `route` (host, G entries).
-cc_status batch_routes(cc_ctx *ctx, const int64_t *vo_dev, const int64_t *vo_host, int G, std::vector<int> &route,
-                       cudaStream_t s) {
-    DevState *st = as<DevState>(ctx->st);
+// The batched route: the per-graph fits overlap the first hook pass (on a
+// highest-priority stream, the pass launched one block per tile) instead of
+// following it. Measured on 4,096 graphs: 107 ms with the fits after the
+// pass, 105.7 with the fits beside a resident-grid pass, 103.2 with the
+// pass in tile blocks.
+constexpr bool kBatchFitOverlap = true;
+
+// One K-S fit per graph on stream s (the degrees of every graph are in ctx->deg).
+void enqueue_ks_batch(cc_ctx *ctx, const int64_t *vo_dev, int G, cudaStream_t s) {
     KsBatchScratch sc{as<uint32_t>(ctx->kb_xs), as<unsigned long long>(ctx->kb_cnt), as<unsigned long long>(ctx->kb_cum),
                       as<double>(ctx->kb_lnx), as<double>(ctx->kb_Dc), as<double>(ctx->kb_Ac), as<double>(ctx->kb_Zc)};
     KsBatchOut out{as<double>(ctx->kb_D),     as<double>(ctx->kb_alpha), as<long long>(ctx->kb_xmin),
                    as<long long>(ctx->kb_ntail), as<long long>(ctx->kb_ncand), as<int>(ctx->kb_route),
                    as<int>(ctx->kb_ovf),      as<unsigned long long>(ctx->kb_seed)};
-    {
-        Scope sc2(ctx, CC_K_KS, s, 1);
-        launch_ks_batch(as<uint32_t>(ctx->deg), vo_dev, G, sc, out, ctx->opt.ks_min_tail, ctx->opt.ks_min_distinct,
-                        ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->kb_blocks, s);
-    }
+    Scope sc2(ctx, CC_K_KS, s, 1);
+    launch_ks_batch(as<uint32_t>(ctx->deg), vo_dev, G, sc, out, ctx->opt.ks_min_tail, ctx->opt.ks_min_distinct,
+                    ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->kb_blocks, s);
+}
+
+// The per-graph routes of the fits enqueue_ks_batch queued before the work
+// on s; graphs the batched fit flagged take the single-graph fit here.
+cc_status batch_routes(cc_ctx *ctx, const int64_t *vo_host, int G, std::vector<int> &route, cudaStream_t s) {
+    DevState *st = as<DevState>(ctx->st);
     route.assign((size_t)G, 0);
     std::vector<int> ovf((size_t)G, 0);
     CU_TRY(cudaMemcpyAsync(route.data(), ctx->kb_route.p, (size_t)G * 4, cudaMemcpyDeviceToHost, s));
@@ -1643,7 +1654,8 @@ cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int6
     launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, as<uint32_t>(ctx->deg),
                         st, ctx->grid, s);
     std::vector<int> route;
-    CC_TRY(batch_routes(ctx, vertex_offsets_dev, vertex_offsets_host, G, route, s));
+    enqueue_ks_batch(ctx, vertex_offsets_dev, G, s);
+    CC_TRY(batch_routes(ctx, vertex_offsets_host, G, route, s));
     std::vector<long long> xmin((size_t)G), ncand((size_t)G);
     std::vector<unsigned long long> seed((size_t)G);
     CU_TRY(cudaMemcpyAsync(D_host, ctx->kb_D.p, (size_t)G * 8, cudaMemcpyDeviceToHost, s));
@@ -1727,13 +1739,26 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
                 launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G,
                                     as<uint32_t>(ctx->deg), st, ctx->grid, s);
             }
-            Scope sc(ctx, CC_K_SV_FIRST, s, 1);
-            launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,
-                                 hooked, nullptr, st, 0, ctx->grid, s, nullptr, sch);
+            // the fits on a highest-priority stream, overlapping the first hook
+            // pass, which launches one block per tile so that the fits' blocks
+            // get SMs as its blocks retire
+            CC_TRY(ensure_fit_stream(ctx));
+            CU_TRY(cudaEventRecord(ctx->ev_fork, s));
+            CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
+            enqueue_ks_batch(ctx, vertex_offsets_dev, G, ctx->fit_s);
+            CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
+            {
+                Scope sc(ctx, CC_K_SV_FIRST, s, 1);
+                BatchSchedule first = sch;
+                first.tile_blocks = kBatchFitOverlap;
+                launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt,
+                                     parent, hooked, nullptr, st, 0, ctx->grid, s, nullptr, first);
+            }
+            CU_TRY(cudaStreamWaitEvent(s, ctx->ev_fit, 0));
         }
         rec(ctx, EV_DEGREE, s);
         std::vector<int> route;
-        cc_status rs = batch_routes(ctx, vertex_offsets_dev, vertex_offsets_host, G, route, s);
+        cc_status rs = batch_routes(ctx, vertex_offsets_host, G, route, s);
         if (rs != CC_OK) {
             ctx->last_status = rs;
             return rs;

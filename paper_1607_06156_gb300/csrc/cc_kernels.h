@@ -14,6 +14,7 @@ struct BatchSchedule {
     int unroll = 2;
     int grid_mult = 1;
     const uint32_t *pair_tiles = nullptr;  // graph of every 2^kTileShift-th pair (launch_tile_graphs), required
+    bool tile_blocks = false;              // one block per tile instead of a resident grid
 };
 
 

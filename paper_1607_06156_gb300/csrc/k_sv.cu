@@ -452,12 +452,18 @@ __global__ void __launch_bounds__(kBlock) k_finalize_batch(vid_t *parent, vid_t 
 template <int U>
 void launch_sv_pass_batch_u(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
                             vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
-                            cudaStream_t s, uint32_t *deg, int grid_mult, const uint32_t *sch_tg) {
+                            cudaStream_t s, uint32_t *deg, int grid_mult, const uint32_t *sch_tg, bool tile_blocks) {
     auto kf = mode == 0 && deg ? k_sv_pass_batch<0, false, false, true, U>
               : mode == 0      ? k_sv_pass_batch<0, false, false, false, U>
                                : k_sv_pass_batch<2, true, true, false, U>;
-    const int g = fit_grid((const void *)kf, grid, kBlock) * (grid_mult > 0 ? grid_mult : 1);
-    kf<<<g, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, mode == 0 ? deg : nullptr, sch_tg);
+    long long g = fit_grid((const void *)kf, grid, kBlock) * (grid_mult > 0 ? grid_mult : 1);
+    if (tile_blocks) {  // one block per tile of kBlock * U vectors, plus the odd last pair
+        const long long tile = (long long)kBlock * U;
+        g = (m / 2 + tile - 1) / tile + (m & 1);
+        if (g > 0x7fffffffLL) g = 0x7fffffffLL;
+    }
+    kf<<<(unsigned)g, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, mode == 0 ? deg : nullptr,
+                                      sch_tg);
 }
 
 void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
@@ -467,13 +473,13 @@ void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_
     const uint32_t *sch_tg = sch.pair_tiles;
     if (sch.unroll == 1)
         launch_sv_pass_batch_u<1>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s, deg,
-                                  sch.grid_mult, sch_tg);
+                                  sch.grid_mult, sch_tg, sch.tile_blocks);
     else if (sch.unroll == 4)
         launch_sv_pass_batch_u<4>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s, deg,
-                                  sch.grid_mult, sch_tg);
+                                  sch.grid_mult, sch_tg, sch.tile_blocks);
     else
         launch_sv_pass_batch_u<2>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s, deg,
-                                  sch.grid_mult, sch_tg);
+                                  sch.grid_mult, sch_tg, sch.tile_blocks);
 }
 
 void launch_finalize_batch(vid_t *parent, vid_t ntot, const int64_t *vo, int G, int32_t *labels, int grid,
