@@ -159,7 +159,7 @@ def ncu_traffic(kernel_cls: str, workload: str):
         return None
     if d.get("sources_hash") != sources_hash():
         return None
-    return d.get("traffic_per_launch", {}).get(workload, {}).get(kernel_cls)
+    return d.get("traffic_per_call", {}).get(workload, {}).get(kernel_cls)
 
 
 def kernel_class(name: str):
@@ -177,12 +177,14 @@ def kernel_class(name: str):
 
 
 def ncu_summary(csv_path: str, workload: str, scale_to: dict, command: str) -> dict:
-    """Mean DRAM bytes per launch of each kernel class from an ncu --csv
+    """DRAM bytes per cc_labels call of each kernel class from an ncu --csv
     capture of gpu__time_duration.sum, dram__bytes_read.sum and
-    dram__bytes_write.sum (the same per-launch unit as the roofline's
-    algorithmic bytes: a class's bytes per call / its launches per call).
-    `scale_to` maps another workload to the ratio of its pairs to this one's
-    (the streamed pairs dominate the traffic)."""
+    dram__bytes_write.sum: the class's bytes over all captured launches
+    divided by the calls captured (the histogram kernel runs once per call
+    on the heuristic route). The roofline divides it by the class's timed
+    launches per call, like the algorithmic bytes. `scale_to` maps another
+    workload to the ratio of its pairs to this one's (the streamed pairs
+    dominate the traffic)."""
     import csv
 
     rows = list(csv.reader(open(csv_path)))
@@ -202,13 +204,16 @@ def ncu_summary(csv_path: str, workload: str, scale_to: dict, command: str) -> d
             continue
         tot[cls] = tot.get(cls, 0.0) + L.get("dram__bytes_read.sum", 0.0) + L.get("dram__bytes_write.sum", 0.0)
         cnt[cls] = cnt.get(cls, 0) + 1
-    per = {k: tot[k] / cnt[k] for k in tot}
-    out = {"sources_hash": sources_hash(), "command": command, "launches": cnt,
-           "note": f"mean dram__bytes_read.sum + dram__bytes_write.sum per launch and kernel class, captured on "
+    calls = cnt.get("hist", 0)
+    if calls <= 0:
+        raise SystemExit("no histogram launches in the capture: cannot count the calls")
+    per = {k: tot[k] / calls for k in tot}
+    out = {"sources_hash": sources_hash(), "command": command, "launches": cnt, "calls": calls,
+           "note": f"dram__bytes_read.sum + dram__bytes_write.sum per cc_labels call and kernel class, captured on "
                    f"{workload}" + "".join(f"; {w}: scaled by the pair ratio x{f:g}" for w, f in scale_to.items()),
-           "traffic_per_launch": {workload: per}}
+           "traffic_per_call": {workload: per}}
     for w, f in scale_to.items():
-        out["traffic_per_launch"][w] = {k: v * f for k, v in per.items()}
+        out["traffic_per_call"][w] = {k: v * f for k, v in per.items()}
     return out
 
 
@@ -548,6 +553,8 @@ def main() -> int:
     if not peak:
         peak = 6800.0
     traffic = ncu_traffic(dom, args.workload)
+    if traffic is not None:
+        traffic /= launches_per_call
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
                 "alg_bytes_per_launch": per_call_bytes / launches_per_call, "avg_launch_ms": per_launch_ms,
@@ -597,8 +604,21 @@ def main() -> int:
         b.record(stream)
         torch.cuda.synchronize(dev)
         t_e2e = max_over_ranks(a.elapsed_time(b) / steps_e2e, dist, dev)
+        # the host link alone: the same two copies with no compute, the floor of the e2e time
+        d_edges = torch.empty_like(h_edges, device=dev)
+        d_lab = torch.empty_like(h_lab, device=dev)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        for _ in range(steps_e2e):
+            d_edges.copy_(h_edges, non_blocking=True)
+            h_lab.copy_(d_lab, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        t_link = a.elapsed_time(b) / steps_e2e
+        del d_edges, d_lab
         e2e = {"value": world * m / (t_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(g.edges.nbytes),
                "d2h_bytes_per_step": int(n * lab.element_size()), "ms_per_step": t_e2e,
+               "copies_alone_ms": t_link,
                "call": "cc_labels_host (pinned host buffers)"}
 
     # the forced routes on the same graph (the paper's dynamic-vs-opposite
