@@ -656,6 +656,26 @@ def main() -> int:
                                 "stage_ms": {k2: sd[k2] for k2 in ("ms_degree", "ms_predict", "ms_csr", "ms_bfs",
                                                                    "ms_sv", "ms_finalize")}}
             e.close()
+        # the paper's own SV design (Algorithm 1: tuples grouped by radix sorts)
+        # on the same GPU, one warm-up and one timed call (it is far slower)
+        if n < (1 << 31):
+            e = cc.Engine(id_bytes=w, device=local)
+            e.labels_tuple_sv(edges_d, n, out=lab)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e.labels_tuple_sv(edges_d, n, out=lab)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            t = a.elapsed_time(b)
+            sd = e.stats()
+            e.close()
+            if not torch.equal(lab, ref_lab):
+                raise SystemExit("the sort-based SV changed the labels")
+            route_compare["tuple_sv_alg1"] = {
+                "value": m / (t / 1e3), "ms_per_step": t, "iterations": sd["sv_iters"],
+                "note": "Algorithm 1 on the device: per iteration four radix sorts of the n + 2m tuples "
+                        "(plus temporaries) and segmented minima; no prediction"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

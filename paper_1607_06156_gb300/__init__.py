@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
         L.cc_destroy.argtypes = [_vp]
         L.cc_labels.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp]
         L.cc_labels_host.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp]
+        L.cc_labels_tuple_sv.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp]
         L.cc_ks_statistic_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.cc_labels_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp]
         L.cc_degree_distribution.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp]
@@ -124,7 +125,7 @@ def lib() -> ctypes.CDLL:
                   "cc_labels_batched", "cc_degree_distribution", "cc_ks_statistic", "cc_get_stats",
                   "cc_labels_static", "cc_route_features", "cc_set_predictor", "cc_mlp_forward",
                   "cc_mlp_backward", "cc_mlp_adam", "cc_measure_l2_rates", "cc_labels_host",
-                  "cc_ks_statistic_batched"):
+                  "cc_ks_statistic_batched", "cc_labels_tuple_sv"):
             getattr(L, f).restype = _int
         _lib = L
     return _lib
@@ -206,6 +207,23 @@ class Engine:
         rc = lib().cc_labels(self._h, edges.data_ptr() if m else None, n, m, out.data_ptr() if n else None,
                              _stream_handle(stream, edges.device))
         _check(rc, "cc_labels")
+        return out
+
+    def labels_tuple_sv(self, edges, n: int, out=None, stream=None):
+        """Labels by the paper's sort-based SV (Algorithm 1) on the device
+        (cc_labels_tuple_sv): the same labels as `labels`, for comparison."""
+        import torch
+
+        if edges.dtype.itemsize != self._opt.id_bytes:
+            raise ValueError(f"edges dtype {edges.dtype} does not match id_bytes={self._opt.id_bytes}")
+        if not edges.is_contiguous():
+            raise ValueError("edges must be contiguous")
+        m = edges.shape[0] if edges.numel() else 0
+        if out is None:
+            out = torch.empty(n, dtype=edges.dtype, device=edges.device)
+        rc = lib().cc_labels_tuple_sv(self._h, edges.data_ptr() if m else None, n, m,
+                                      out.data_ptr() if n else None, _stream_handle(stream, edges.device))
+        _check(rc, "cc_labels_tuple_sv")
         return out
 
     def labels_host(self, edges, n: int, out=None, stream=None):

@@ -35,6 +35,9 @@ struct cc_ctx {
     int grid = 0;  // blocks for grid-stride kernels
     // SV / degree workspace
     size_t n_cap = 0, m_cap = 0;
+    // workspace of cc_labels_tuple_sv (the sort-based SV of Algorithm 1)
+    Buf tsv_t32[4], tsv_v0, tsv_v1, tsv_val, tsv_uniq, tsv_agg, tsv_dense, tsv_temp, tsv_cnt;
+    long long tsv_cap = 0;
     Buf deg, parent, hooked, ebuf0, ebuf1, hist, ovf, ks_xs, ks_cnt, ks_cum, ks_lnx, ks_Dc, ks_Ac, ks_Zc, ks_Df, chunk_nz,
         chunk_mass, st, bk_count, bk_off, bk_cursor;
     unsigned long long ovf_cap = 0, ks_cap = 0;
@@ -1544,6 +1547,10 @@ cc_status cc_destroy(cc_ctx *ctx) {
     buf_free(ctx->hlabels);
     buf_free(ctx->tile_pairs);
     buf_free(ctx->tile_verts);
+    for (Buf &b : ctx->tsv_t32) buf_free(b);
+    Buf *tsv[] = {&ctx->tsv_v0,  &ctx->tsv_v1,    &ctx->tsv_val,  &ctx->tsv_uniq,
+                  &ctx->tsv_agg, &ctx->tsv_dense, &ctx->tsv_temp, &ctx->tsv_cnt};
+    for (Buf *b : tsv) buf_free(*b);
     Buf *kb[] = {&ctx->kb_xs, &ctx->kb_cnt, &ctx->kb_cum, &ctx->kb_lnx, &ctx->kb_Dc, &ctx->kb_Ac, &ctx->kb_Zc,
                  &ctx->kb_D, &ctx->kb_alpha, &ctx->kb_xmin, &ctx->kb_ntail, &ctx->kb_ncand, &ctx->kb_route,
                  &ctx->kb_ovf, &ctx->kb_seed};
@@ -1592,6 +1599,75 @@ cc_status cc_labels(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, vo
     ctx->last_status = st;
     ctx->stats.status = st;
     return st;
+}
+
+cc_status cc_labels_tuple_sv(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, void *labels_out_dev,
+                             void *stream) {
+    if (!ctx) return CC_ERR_INVALID_ARG;
+    if (n < 0 || m < 0) return CC_ERR_INVALID_ARG;
+    if (n >= (1LL << 31) || m >= (1LL << 31)) return CC_ERR_UNSUPPORTED;
+    if (n == 0) return m > 0 ? CC_ERR_INVALID_EDGE : CC_OK;
+    if (!labels_out_dev || (m > 0 && !edges_dev)) return CC_ERR_INVALID_ARG;
+    CU_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    CC_TRY(ensure_sv(ctx, (size_t)n, (size_t)m));  // the device state and the events
+    // tuples: n + 2m, plus up to one temporary per partition (at most n)
+    const long long cap = 2 * n + 2 * m + 16;
+    if (cap > ctx->tsv_cap) {
+        for (Buf &b : ctx->tsv_t32) CC_TRY(buf_reserve(ctx, b, (size_t)cap * 4));
+        CC_TRY(buf_reserve(ctx, ctx->tsv_v0, (size_t)cap * 8));
+        CC_TRY(buf_reserve(ctx, ctx->tsv_v1, (size_t)cap * 8));
+        CC_TRY(buf_reserve(ctx, ctx->tsv_val, (size_t)cap * 4));
+        CC_TRY(buf_reserve(ctx, ctx->tsv_uniq, (size_t)cap * 4));
+        CC_TRY(buf_reserve(ctx, ctx->tsv_agg, (size_t)cap * 4));
+        CC_TRY(buf_reserve(ctx, ctx->tsv_cnt, 64));
+        ctx->tsv_cap = cap;
+    }
+    CC_TRY(buf_reserve(ctx, ctx->tsv_dense, (size_t)(n + 4) * 4));
+    // the temporary storage the sorts need depends on the key bits (n) as well
+    const size_t tb = tuple_sv_temp_bytes(ctx->tsv_cap, (vid_t)n);
+    CC_TRY(buf_reserve(ctx, ctx->tsv_temp, tb));
+    TupleSvBufs b;
+    for (int k = 0; k < 4; k++) b.t32[k] = as<uint32_t>(ctx->tsv_t32[k]);
+    b.v0 = as<unsigned long long>(ctx->tsv_v0);
+    b.v1 = as<unsigned long long>(ctx->tsv_v1);
+    b.val = as<uint32_t>(ctx->tsv_val);
+    b.uniq = as<uint32_t>(ctx->tsv_uniq);
+    b.agg = as<uint32_t>(ctx->tsv_agg);
+    b.dense = as<uint32_t>(ctx->tsv_dense);
+    b.counters = as<unsigned long long>(ctx->tsv_cnt);
+    b.temp = ctx->tsv_temp.p;
+    b.temp_bytes = ctx->tsv_temp.bytes;
+    b.cap = ctx->tsv_cap;
+    b.num_sms = ctx->num_sms;
+    DevState *st = as<DevState>(ctx->st);
+    cc_stats &S = ctx->stats;
+    memset(&S, 0, sizeof(S));
+    prof_reset(ctx);
+    for (int e = 0; e < EV_COUNT; e++) ctx->ev_used[e] = false;
+    S.n = n;
+    S.m = m;
+    S.route_source = 2;
+    CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+    rec(ctx, EV_START, s);
+    const int cap_iters = ctx->opt.max_iters > 0 ? ctx->opt.max_iters : default_max_iters((vid_t)n);
+    int iters = 0;
+    const int rc = ctx->opt.id_bytes == 4
+                       ? tuple_sv_run<int32_t>(edges_dev, m, (vid_t)n, labels_out_dev, b, st, cap_iters, &iters, s)
+                       : tuple_sv_run<int64_t>(edges_dev, m, (vid_t)n, labels_out_dev, b, st, cap_iters, &iters, s);
+    rec(ctx, EV_SV, s);
+    rec(ctx, EV_END, s);
+    S.sv_iters = iters;
+    cc_status out = rc == 0 ? CC_OK : rc == 2 ? CC_ERR_NO_CONVERGENCE : CC_ERR_CUDA;
+    if (rc != 1) {
+        CU_TRY(cudaMemcpyAsync(&ctx->h_st->err, &st->err, 4, cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaStreamSynchronize(s));
+        if (ctx->h_st->err) out = device_error(ctx->h_st->err);
+    }
+    ctx->last_status = out;
+    S.status = out;
+    return out;
 }
 
 cc_status cc_labels_host(cc_ctx *ctx, const void *edges_host, int64_t n, int64_t m, void *labels_out_host,
