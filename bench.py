@@ -669,11 +669,17 @@ def main() -> int:
             torch.cuda.synchronize(dev)
             t = a.elapsed_time(b)
             sd = e.stats()
+            # one more call with the sorts timed (events around each sort)
+            e.set_options(profile=1)
+            e.labels_tuple_sv(edges_d, n, out=lab)
+            sp = e.stats()
             e.close()
             if not torch.equal(lab, ref_lab):
                 raise SystemExit("the sort-based SV changed the labels")
             route_compare["tuple_sv_alg1"] = {
                 "value": m / (t / 1e3), "ms_per_step": t, "iterations": sd["sv_iters"],
+                "sorts": sp["kernel_launches"]["tuple_sort"], "sort_ms": sp["kernel_ms"]["tuple_sort"],
+                "sort_share": sp["kernel_ms"]["tuple_sort"] / sp["ms_total"] if sp["ms_total"] > 0 else None,
                 "note": "Algorithm 1 on the device: per iteration four radix sorts of the n + 2m tuples "
                         "(plus temporaries) and segmented minima; no prediction"}
 

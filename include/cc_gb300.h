@@ -113,6 +113,7 @@ enum {
     CC_K_SV_SHORTCUT = 12,
     CC_K_FINALIZE = 13,
     CC_K_PREDICT = 14,      /* sampled route features + network inference */
+    CC_K_TUPLE_SORT = 15,   /* radix sorts of cc_labels_tuple_sv (the rest of its time is ms_total) */
     CC_K_COUNT = 16
 };
 

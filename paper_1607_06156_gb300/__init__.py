@@ -28,7 +28,7 @@ MAX_SV_ITERS_RECORDED = 64
 K_COUNT = 16
 # kernel classes of cc_stats.kernel_ms (CC_K_* in the header)
 KERNELS = ["degree", "hist", "ks", "scan", "csr", "bfs_topdown", "bfs_bottomup", "bfs_aux", "parent_init",
-           "sv_first", "sv_gather_input", "sv_gather_list", "sv_shortcut", "finalize", "predict"]
+           "sv_first", "sv_gather_input", "sv_gather_list", "sv_shortcut", "finalize", "predict", "tuple_sort"]
 MLP_IN, MLP_HIDDEN, MLP_OUT = 69, 128, 3
 MLP_PARAMS = 128 * 69 + 128 + 128 * 128 + 128 + 3 * 128 + 3
 

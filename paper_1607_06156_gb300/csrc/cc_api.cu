@@ -1652,10 +1652,15 @@ cc_status cc_labels_tuple_sv(cc_ctx *ctx, const void *edges_dev, int64_t n, int6
     CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
     rec(ctx, EV_START, s);
     const int cap_iters = ctx->opt.max_iters > 0 ? ctx->opt.max_iters : default_max_iters((vid_t)n);
-    int iters = 0;
-    const int rc = ctx->opt.id_bytes == 4
-                       ? tuple_sv_run<int32_t>(edges_dev, m, (vid_t)n, labels_out_dev, b, st, cap_iters, &iters, s)
-                       : tuple_sv_run<int64_t>(edges_dev, m, (vid_t)n, labels_out_dev, b, st, cap_iters, &iters, s);
+    int iters = 0, sorts = 0;
+    float sort_ms = 0.0f;
+    float *sort_out = ctx->opt.profile ? &sort_ms : nullptr;
+    const int rc = ctx->opt.id_bytes == 4 ? tuple_sv_run<int32_t>(edges_dev, m, (vid_t)n, labels_out_dev, b, st,
+                                                                  cap_iters, &iters, sort_out, &sorts, s)
+                                          : tuple_sv_run<int64_t>(edges_dev, m, (vid_t)n, labels_out_dev, b, st,
+                                                                  cap_iters, &iters, sort_out, &sorts, s);
+    S.kernel_ms[CC_K_TUPLE_SORT] = sort_ms;
+    S.kernel_launches[CC_K_TUPLE_SORT] = sorts;
     rec(ctx, EV_SV, s);
     rec(ctx, EV_END, s);
     S.sv_iters = iters;

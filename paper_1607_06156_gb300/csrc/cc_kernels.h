@@ -111,9 +111,10 @@ struct TupleSvBufs {
 };
 size_t tuple_sv_temp_bytes(long long cap, vid_t n);
 // 0: labels written; 1: CUDA error or capacity; 2: no convergence within max_iters
+// sort_ms (optional): the summed time of the radix sorts, *sorts their number
 template <typename T>
 int tuple_sv_run(const void *edges, long long m, vid_t n, void *labels, TupleSvBufs b, DevState *st, int max_iters,
-                 int *iters_out, cudaStream_t s);
+                 int *iters_out, float *sort_ms, int *sorts, cudaStream_t s);
 
 // k_sv.cu
 template <typename T>

@@ -26,6 +26,8 @@
 #include <cub/device/device_reduce.cuh>
 #include <cub/device/device_select.cuh>
 
+#include <vector>
+
 namespace ccg {
 
 constexpr uint32_t kTmpBit = 0x80000000u, kIdMask = 0x7fffffffu;
@@ -165,13 +167,43 @@ size_t tuple_sv_temp_bytes(long long cap, vid_t n) {
     return mx + 256;
 }
 
+// Optional timing of the radix sorts (CUDA events around each sort).
+struct SortTimer {
+    std::vector<cudaEvent_t> ev;
+    bool on = false;
+    void mark(cudaStream_t s) {
+        if (!on) return;
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            on = false;
+            return;
+        }
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+    }
+    // sum of the (begin, end) pairs after the stream has finished
+    float total_ms() {
+        float t = 0.0f;
+        for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) t += ms;
+            else cudaGetLastError();
+        }
+        return t;
+    }
+    ~SortTimer() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
 // One vertex pass and one partition pass over the len tuples in (R, PT),
 // two of the four 32-bit tuple buffers (the other two are scratch); on
 // return R and PT point at the buffers holding the new tuples. With
 // `append`, the pass's temporaries follow them and len grows by their count.
 // Sets counters[1] when a partition changed.
 static cudaError_t tsv_half(const TupleSvBufs &b, uint32_t *&R, uint32_t *&PT, long long &len, vid_t n, bool append,
-                            cudaStream_t s) {
+                            SortTimer &timer, cudaStream_t s) {
     const int bits = tsv_key_bits(n);
     const int grid = 8 * b.num_sms;
     uint32_t *free_a = nullptr, *free_b = nullptr;
@@ -184,7 +216,9 @@ static cudaError_t tsv_half(const TupleSvBufs &b, uint32_t *&R, uint32_t *&PT, l
     // vertex pass: sort by r, q <- min p per run of equal r
     cub::DoubleBuffer<uint32_t> vk(R, free_a), vv(PT, free_b);
     size_t tb = b.temp_bytes;
+    timer.mark(s);
     if ((e = cub::DeviceRadixSort::SortPairs(b.temp, tb, vk, vv, len, 0, bits, s)) != cudaSuccess) return e;
+    timer.mark(s);
     uint32_t *Rs = vk.Current(), *Ra = vk.Alternate(), *PTs = vv.Current(), *PTa = vv.Alternate();
     k_tsv_low31<<<grid, kBlock, 0, s>>>(PTs, b.val, len);
     tb = b.temp_bytes;
@@ -197,7 +231,9 @@ static cudaError_t tsv_half(const TupleSvBufs &b, uint32_t *&R, uint32_t *&PT, l
     cub::DoubleBuffer<uint32_t> pk(Ra, Rs);
     cub::DoubleBuffer<unsigned long long> pv(b.v0, b.v1);
     tb = b.temp_bytes;
+    timer.mark(s);
     if ((e = cub::DeviceRadixSort::SortPairs(b.temp, tb, pk, pv, len, 0, bits, s)) != cudaSuccess) return e;
+    timer.mark(s);
     uint32_t *P = pk.Current(), *Pa = pk.Alternate();
     unsigned long long *V = pv.Current();
     k_tsv_high32<<<grid, kBlock, 0, s>>>(V, b.val, len);
@@ -223,8 +259,8 @@ static cudaError_t tsv_half(const TupleSvBufs &b, uint32_t *&R, uint32_t *&PT, l
 }
 
 template <typename T>
-int tuple_sv_run(const void *edges, long long m, vid_t n, void *labels, TupleSvBufs b, DevState *st, int max_iters,
-                 int *iters_out, cudaStream_t s) {
+static int tuple_sv_iterate(const void *edges, long long m, vid_t n, void *labels, const TupleSvBufs &b, DevState *st,
+                            int max_iters, int *iters_out, SortTimer &timer, cudaStream_t s) {
     *iters_out = 0;
     const long long T0 = (long long)n + 2 * m;
     if (T0 + (long long)n > b.cap) return 1;
@@ -236,8 +272,8 @@ int tuple_sv_run(const void *edges, long long m, vid_t n, void *labels, TupleSvB
         *iters_out = it;
         if (cudaMemsetAsync(b.counters, 0, 32, s) != cudaSuccess) return 1;
         long long len = T0;
-        if (tsv_half(b, R, PT, len, n, true, s) != cudaSuccess) return 1;
-        if (tsv_half(b, R, PT, len, n, false, s) != cudaSuccess) return 1;
+        if (tsv_half(b, R, PT, len, n, true, timer, s) != cudaSuccess) return 1;
+        if (tsv_half(b, R, PT, len, n, false, timer, s) != cudaSuccess) return 1;
         // erase the temporaries: pack (PT, R), keep the words without the bit
         k_tsv_pack<<<grid, kBlock, 0, s>>>(R, PT, b.v0, len);
         size_t tb = b.temp_bytes;
@@ -255,9 +291,23 @@ int tuple_sv_run(const void *edges, long long m, vid_t n, void *labels, TupleSvB
     }
     return 2;
 }
+template <typename T>
+int tuple_sv_run(const void *edges, long long m, vid_t n, void *labels, TupleSvBufs b, DevState *st, int max_iters,
+                 int *iters_out, float *sort_ms, int *sorts, cudaStream_t s) {
+    SortTimer timer;
+    timer.on = sort_ms != nullptr;
+    const int rc = tuple_sv_iterate<T>(edges, m, n, labels, b, st, max_iters, iters_out, timer, s);
+    if (sort_ms) {
+        cudaStreamSynchronize(s);
+        *sort_ms = timer.total_ms();
+        *sorts = (int)(timer.ev.size() / 2);
+    }
+    return rc;
+}
+
 template int tuple_sv_run<int32_t>(const void *, long long, vid_t, void *, TupleSvBufs, DevState *, int, int *,
-                                   cudaStream_t);
+                                   float *, int *, cudaStream_t);
 template int tuple_sv_run<int64_t>(const void *, long long, vid_t, void *, TupleSvBufs, DevState *, int, int *,
-                                   cudaStream_t);
+                                   float *, int *, cudaStream_t);
 
 }  // namespace ccg

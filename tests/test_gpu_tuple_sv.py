@@ -111,3 +111,12 @@ def test_invalid_id_and_size_limits():
         eng.labels_tuple_sv(e, 1 << 31, out=torch.empty(1, dtype=torch.int32, device="cuda"))
     assert ei.value.status == 7  # CC_ERR_UNSUPPORTED
     eng.close()
+
+
+def test_sort_time_reported_when_profiling():
+    """options.profile = 1 times every radix sort: four per iteration."""
+    g = gg.rmat(seed=11, scale=15, edge_factor=8)
+    got, st = _run(g.edges, g.n, profile=1)
+    assert np.array_equal(got, oracle.cc_labels(g.edges, g.n))
+    assert st["kernel_launches"]["tuple_sort"] == 4 * st["sv_iters"]
+    assert 0.0 < st["kernel_ms"]["tuple_sort"] <= st["ms_total"]
