@@ -57,6 +57,8 @@ def _load():
         lib.gg_batch_sizes.argtypes = [_u64, _i64, _i64, _i64, _int, _dbl, _dbl, _dbl, _ptr, _ptr]
         lib.gg_batch_fill.restype = None
         lib.gg_batch_fill.argtypes = [_u64, _i64, _ptr, _ptr, _int, _dbl, _dbl, _dbl, _dbl, _dbl, _dbl, _ptr]
+        lib.gg_batch_fill_ids.restype = None
+        lib.gg_batch_fill_ids.argtypes = [_u64, _i64, _ptr, _ptr, _ptr, _dbl, _dbl, _dbl, _dbl, _dbl, _dbl, _ptr]
         lib.gg_permute.restype = None
         lib.gg_permute.argtypes = [_u64, _u64, _u64, _ptr, _ptr, _i64]
         lib.gg_chung_lu_fill.restype = None
@@ -182,21 +184,36 @@ class Batch:
         return Graph(e, int(self.vertex_offsets[g + 1] - self.vertex_offsets[g]), f"{self.name}[{g}]")
 
 
-def batch(seed: int = 1, G: int = 4096, nmin: int = 1000, nmax: int = 1_000_000, edge_factor: int = 8,
-          a: float = 0.57, b: float = 0.19, c: float = 0.19, p: float = 0.55, mean_len: float = 20.0,
-          branch_p: float = 0.02) -> Batch:
-    """G graphs with log-uniform vertex counts, cycling R-MAT / grid / chain forest."""
+def batch_sizes(seed: int = 1, G: int = 4096, nmin: int = 1000, nmax: int = 1_000_000, edge_factor: int = 8,
+                p: float = 0.55, mean_len: float = 20.0, branch_p: float = 0.02) -> tuple[np.ndarray, np.ndarray]:
+    """Vertex and pair counts of every graph of a batch (no pairs drawn)."""
     lib = _load()
     ng = np.empty(G, dtype=np.int64)
     mg = np.empty(G, dtype=np.int64)
     lib.gg_batch_sizes(seed, G, nmin, nmax, edge_factor, p, mean_len, branch_p, _p(ng), _p(mg))
-    eoff = np.zeros(G + 1, dtype=np.int64)
+    return ng, mg
+
+
+def batch(seed: int = 1, G: int = 4096, nmin: int = 1000, nmax: int = 1_000_000, edge_factor: int = 8,
+          a: float = 0.57, b: float = 0.19, c: float = 0.19, p: float = 0.55, mean_len: float = 20.0,
+          branch_p: float = 0.02, graphs=None) -> Batch:
+    """G graphs with log-uniform vertex counts, cycling R-MAT / grid / chain forest.
+    `graphs` (graph numbers in [0, G)) keeps only those graphs, in that order,
+    each with exactly the pairs it has in the whole batch."""
+    lib = _load()
+    ng, mg = batch_sizes(seed, G, nmin, nmax, edge_factor, p, mean_len, branch_p)
+    gids = np.arange(G, dtype=np.int64) if graphs is None else np.ascontiguousarray(graphs, dtype=np.int64)
+    if gids.size and (gids.min() < 0 or gids.max() >= G):
+        raise ValueError("graph number outside [0, G)")
+    ng, mg = np.ascontiguousarray(ng[gids]), mg[gids]
+    eoff = np.zeros(gids.size + 1, dtype=np.int64)
     np.cumsum(mg, out=eoff[1:])
-    voff = np.zeros(G + 1, dtype=np.int64)
+    voff = np.zeros(gids.size + 1, dtype=np.int64)
     np.cumsum(ng, out=voff[1:])
     edges = np.empty((int(eoff[-1]), 2), dtype=np.int32)
-    lib.gg_batch_fill(seed, G, _p(ng), _p(eoff), edge_factor, a, b, c, p, mean_len, branch_p, _p(edges))
-    return Batch(edges, eoff, voff, f"batch(G={G},n=[{nmin},{nmax}],seed={seed})")
+    lib.gg_batch_fill_ids(seed, gids.size, _p(gids), _p(ng), _p(eoff), a, b, c, p, mean_len, branch_p, _p(edges))
+    sub = "" if graphs is None else f",{gids.size} of them"
+    return Batch(edges, eoff, voff, f"batch(G={G},n=[{nmin},{nmax}],seed={seed}{sub})")
 
 
 def num_threads() -> int:

@@ -398,55 +398,72 @@ void gg_batch_sizes(uint64_t seed, int64_t G, int64_t nmin, int64_t nmax, int ef
     }
 }
 
+/* Graph number gid of a batch (its type is gid % 3, its draws are keyed by
+ * gid) with ng vertices, written from pair k on. */
+static void batch_fill_one(uint64_t seed, int64_t gid, int64_t ng, int64_t k, double p, double mean_len, double q,
+                           int32_t *edges_out) {
+    int t = (int)(gid % 3);
+    uint64_t s = rnd(seed, 31, (uint64_t)gid);
+    perm_t pv;
+    perm_init(&pv, (uint64_t)ng, s, 24);
+    if (t == 1) {
+        int64_t W = (int64_t)floor(sqrt((double)ng));
+        while ((W + 1) * (W + 1) <= ng) W++;
+        while (W * W > ng) W--;
+        int64_t nb = (W > 1) ? 2 * W * (W - 1) : 0, hb = W * (W - 1);
+        for (int64_t e = 0; e < nb; e++) {
+            if (!bond_kept(s, (uint64_t)e, p)) continue;
+            int64_t tt = e < hb ? e : e - hb;
+            int64_t r = tt / (W - 1), cc = tt % (W - 1);
+            uint64_t x, y;
+            if (e < hb) { x = (uint64_t)(r * W + cc); y = x + 1; }
+            else { x = (uint64_t)(cc * W + r); y = x + (uint64_t)W; }
+            put_edge(edges_out, 4, (uint64_t)k++, perm_apply(&pv, x), perm_apply(&pv, y));
+        }
+    } else {
+        int64_t nch = chain_forest_lengths(s, ng, mean_len, NULL);
+        int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (nch + 1));
+        chain_forest_lengths(s, ng, mean_len, off);
+        for (int64_t j = 0; j < nch; j++)
+            for (int64_t i = off[j]; i + 1 < off[j + 1]; i++)
+                put_edge(edges_out, 4, (uint64_t)k++, perm_apply(&pv, (uint64_t)i), perm_apply(&pv, (uint64_t)(i + 1)));
+        int64_t j = 0;
+        for (int64_t i = 0; i < ng; i++) {
+            while (off[j + 1] <= i) j++;
+            if (!(u01(rnd(s, 23, (uint64_t)i)) < q)) continue;
+            int64_t L = off[j + 1] - off[j];
+            uint64_t tgt = (uint64_t)off[j] + below(rnd(s, 25, (uint64_t)i), (uint64_t)L);
+            put_edge(edges_out, 4, (uint64_t)k++, perm_apply(&pv, (uint64_t)i), perm_apply(&pv, tgt));
+        }
+        free(off);
+    }
+}
+
+/* The graphs gids[0..count) of a batch, graph gids[i] with n_g[i] vertices
+ * written from pair edge_off[i] on: the same pairs as in the whole batch. */
+void gg_batch_fill_ids(uint64_t seed, int64_t count, const int64_t *gids, const int64_t *n_g, const int64_t *edge_off,
+                       double a, double b, double c, double p, double mean_len, double q, int32_t *edges_out) {
+    /* R-MAT graphs are filled with the (internally parallel) R-MAT routine */
+    for (int64_t i = 0; i < count; i++) {
+        if (gids[i] % 3 != 0) continue;
+        uint64_t s = rnd(seed, 31, (uint64_t)gids[i]);
+        gg_rmat_fill(s, ceil_log2(n_g[i] > 1 ? n_g[i] : 2), edge_off[i + 1] - edge_off[i], a, b, c, (uint64_t)n_g[i],
+                     4, edges_out, edge_off[i]);
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < count; i++) {
+        if (gids[i] % 3 == 0) continue;
+        batch_fill_one(seed, gids[i], n_g[i], edge_off[i], p, mean_len, q, edges_out);
+    }
+}
+
 void gg_batch_fill(uint64_t seed, int64_t G, const int64_t *n_g, const int64_t *edge_off, int ef, double a, double b,
                    double c, double p, double mean_len, double q, int32_t *edges_out) {
     (void)ef;
-    /* R-MAT graphs are filled with the (internally parallel) R-MAT routine */
-    for (int64_t g = 0; g < G; g += 3) {
-        uint64_t s = rnd(seed, 31, (uint64_t)g);
-        gg_rmat_fill(s, ceil_log2(n_g[g] > 1 ? n_g[g] : 2), edge_off[g + 1] - edge_off[g], a, b, c, (uint64_t)n_g[g],
-                     4, edges_out, edge_off[g]);
-    }
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t g = 0; g < G; g++) {
-        int t = (int)(g % 3);
-        if (t == 0) continue;
-        uint64_t s = rnd(seed, 31, (uint64_t)g);
-        int64_t ng = n_g[g], k = edge_off[g];
-        perm_t pv;
-        perm_init(&pv, (uint64_t)ng, s, 24);
-        if (t == 1) {
-            int64_t W = (int64_t)floor(sqrt((double)ng));
-            while ((W + 1) * (W + 1) <= ng) W++;
-            while (W * W > ng) W--;
-            int64_t nb = (W > 1) ? 2 * W * (W - 1) : 0, hb = W * (W - 1);
-            for (int64_t e = 0; e < nb; e++) {
-                if (!bond_kept(s, (uint64_t)e, p)) continue;
-                int64_t tt = e < hb ? e : e - hb;
-                int64_t r = tt / (W - 1), cc = tt % (W - 1);
-                uint64_t x, y;
-                if (e < hb) { x = (uint64_t)(r * W + cc); y = x + 1; }
-                else { x = (uint64_t)(cc * W + r); y = x + (uint64_t)W; }
-                put_edge(edges_out, 4, (uint64_t)k++, perm_apply(&pv, x), perm_apply(&pv, y));
-            }
-        } else {
-            int64_t nch = chain_forest_lengths(s, ng, mean_len, NULL);
-            int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (nch + 1));
-            chain_forest_lengths(s, ng, mean_len, off);
-            for (int64_t j = 0; j < nch; j++)
-                for (int64_t i = off[j]; i + 1 < off[j + 1]; i++)
-                    put_edge(edges_out, 4, (uint64_t)k++, perm_apply(&pv, (uint64_t)i), perm_apply(&pv, (uint64_t)(i + 1)));
-            int64_t j = 0;
-            for (int64_t i = 0; i < ng; i++) {
-                while (off[j + 1] <= i) j++;
-                if (!(u01(rnd(s, 23, (uint64_t)i)) < q)) continue;
-                int64_t L = off[j + 1] - off[j];
-                uint64_t tgt = (uint64_t)off[j] + below(rnd(s, 25, (uint64_t)i), (uint64_t)L);
-                put_edge(edges_out, 4, (uint64_t)k++, perm_apply(&pv, (uint64_t)i), perm_apply(&pv, tgt));
-            }
-            free(off);
-        }
-    }
+    int64_t *gids = (int64_t *)malloc(sizeof(int64_t) * (G > 0 ? G : 1));
+    for (int64_t g = 0; g < G; g++) gids[g] = g;
+    gg_batch_fill_ids(seed, G, gids, n_g, edge_off, a, b, c, p, mean_len, q, edges_out);
+    free(gids);
 }
 
 int gg_num_threads(void) {
