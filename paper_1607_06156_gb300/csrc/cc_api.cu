@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -90,7 +91,7 @@ struct cc_ctx {
     std::vector<cudaEvent_t> ev_chunk;
     // per-graph route prediction of the batched form: block scratch, per-graph outputs
     Buf kb_xs, kb_cnt, kb_cum, kb_lnx, kb_Dc, kb_Ac, kb_Zc, kb_D, kb_alpha, kb_xmin, kb_ntail, kb_ncand, kb_route,
-        kb_ovf, kb_seed;
+        kb_ovf, kb_seed, kb_order;
     int kb_blocks = 0;
     // tuned schedules of the batched hook passes, per shape (log2 pairs << 8 | log2 graphs)
     std::vector<std::pair<int, BatchSchedule>> batch_tuned;
@@ -1406,8 +1407,18 @@ cc_status ensure_batch_route(cc_ctx *ctx, int G, int blocks) {
 // pass in tile blocks.
 constexpr bool kBatchFitOverlap = true;
 
-// One K-S fit per graph on stream s (the degrees of every graph are in ctx->deg).
-void enqueue_ks_batch(cc_ctx *ctx, const int64_t *vo_dev, int G, cudaStream_t s) {
+// One K-S fit per graph on stream s (the degrees of every graph are in
+// ctx->deg); the blocks take the graphs largest first.
+cc_status enqueue_ks_batch(cc_ctx *ctx, const int64_t *vo_dev, const int64_t *vo_host, int G, cudaStream_t s) {
+    CC_TRY(buf_reserve(ctx, ctx->kb_order, (size_t)(G > 0 ? G : 1) * 4));
+    std::vector<int> order((size_t)G);
+    for (int g = 0; g < G; g++) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return vo_host[a + 1] - vo_host[a] > vo_host[b + 1] - vo_host[b];
+    });
+    // pageable source: the copy is staged before the call returns
+    CU_TRY(cudaMemcpyAsync(ctx->kb_order.p, order.data(), (size_t)G * 4, cudaMemcpyHostToDevice, s));
+    int *next = reinterpret_cast<int *>(static_cast<char *>(ctx->counters.p) + 1024);
     KsBatchScratch sc{as<uint32_t>(ctx->kb_xs), as<unsigned long long>(ctx->kb_cnt), as<unsigned long long>(ctx->kb_cum),
                       as<double>(ctx->kb_lnx), as<double>(ctx->kb_Dc), as<double>(ctx->kb_Ac), as<double>(ctx->kb_Zc)};
     KsBatchOut out{as<double>(ctx->kb_D),     as<double>(ctx->kb_alpha), as<long long>(ctx->kb_xmin),
@@ -1415,7 +1426,8 @@ void enqueue_ks_batch(cc_ctx *ctx, const int64_t *vo_dev, int G, cudaStream_t s)
                    as<int>(ctx->kb_ovf),      as<unsigned long long>(ctx->kb_seed)};
     Scope sc2(ctx, CC_K_KS, s, 1);
     launch_ks_batch(as<uint32_t>(ctx->deg), vo_dev, G, sc, out, ctx->opt.ks_min_tail, ctx->opt.ks_min_distinct,
-                    ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->kb_blocks, s);
+                    ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->kb_blocks, as<int>(ctx->kb_order), next, s);
+    return CC_OK;
 }
 
 // The per-graph routes of the fits enqueue_ks_batch queued before the work
@@ -1553,7 +1565,7 @@ cc_status cc_destroy(cc_ctx *ctx) {
     for (Buf *b : tsv) buf_free(*b);
     Buf *kb[] = {&ctx->kb_xs, &ctx->kb_cnt, &ctx->kb_cum, &ctx->kb_lnx, &ctx->kb_Dc, &ctx->kb_Ac, &ctx->kb_Zc,
                  &ctx->kb_D, &ctx->kb_alpha, &ctx->kb_xmin, &ctx->kb_ntail, &ctx->kb_ncand, &ctx->kb_route,
-                 &ctx->kb_ovf, &ctx->kb_seed};
+                 &ctx->kb_ovf, &ctx->kb_seed, &ctx->kb_order};
     for (Buf *b : kb) buf_free(*b);
     if (ctx->copy_s) cudaStreamDestroy(ctx->copy_s);
     for (cudaEvent_t e : ctx->ev_chunk) cudaEventDestroy(e);
@@ -1735,7 +1747,7 @@ cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int6
     launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, as<uint32_t>(ctx->deg),
                         st, ctx->grid, s);
     std::vector<int> route;
-    enqueue_ks_batch(ctx, vertex_offsets_dev, G, s);
+    CC_TRY(enqueue_ks_batch(ctx, vertex_offsets_dev, vertex_offsets_host, G, s));
     CC_TRY(batch_routes(ctx, vertex_offsets_host, G, route, s));
     std::vector<long long> xmin((size_t)G), ncand((size_t)G);
     std::vector<unsigned long long> seed((size_t)G);
@@ -1826,7 +1838,7 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
             CC_TRY(ensure_fit_stream(ctx));
             CU_TRY(cudaEventRecord(ctx->ev_fork, s));
             CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
-            enqueue_ks_batch(ctx, vertex_offsets_dev, G, ctx->fit_s);
+            CC_TRY(enqueue_ks_batch(ctx, vertex_offsets_dev, vertex_offsets_host, G, ctx->fit_s));
             CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
             {
                 Scope sc(ctx, CC_K_SV_FIRST, s, 1);

@@ -201,9 +201,11 @@ void launch_degree_batch(const int32_t *in, long long m, const int64_t *eo, cons
                          DevState *st, int grid, cudaStream_t s);
 // out[k] = the graph holding item k << kTileShift of the offsets `off` (G + 1 entries), k < (count >> kTileShift) + 1
 void launch_tile_graphs(const int64_t *off, int G, long long count, uint32_t *out, int grid, cudaStream_t s);
+// order (device, G graph numbers, largest first) and next (device counter) may
+// both be null: then block b takes graphs b, b + blocks, ...
 void launch_ks_batch(const uint32_t *deg, const int64_t *vo, int G, KsBatchScratch sc, KsBatchOut out,
                      long long min_tail, long long min_distinct, double min_span, double tau, int blocks,
-                     cudaStream_t s);
+                     const int *order, int *next, cudaStream_t s);
 // one graph (n vertices, degrees in deg) through the per-graph fit; results into DevState
 // (ks_out, ncand, route, maxkey); vo: 2 int64 of device scratch
 void launch_fit_one(const uint32_t *deg, long long n, int64_t *vo, KsBatchScratch sc, KsBatchOut out, DevState *st,

@@ -90,10 +90,15 @@ __global__ void __launch_bounds__(kBlock) k_degree_batch(const int32_t *__restri
 // Per-graph fit. Scratch per block (global): the distinct degrees xs, their
 // counts, the exclusive prefix cum (cum[nd] = vertices of degree >= 1),
 // ln x, and per candidate D, alpha, Z; kBB + kBOvf entries each.
+// Graphs go to blocks largest first through a shared counter (`order`: the
+// graphs by decreasing vertex count, `next`: zeroed), so the few largest
+// fits start first and the small ones fill the gaps; without `next` block b
+// takes graphs b, b + grid, ...
 __global__ void __launch_bounds__(kBThreads) k_ks_batch(const uint32_t *__restrict__ deg,
                                                         const int64_t *__restrict__ vo, int G, KsBatchScratch sc,
                                                         KsBatchOut out, long long min_tail, long long min_distinct,
-                                                        double min_span, double tau) {
+                                                        double min_span, double tau, const int *__restrict__ order,
+                                                        int *next) {
     __shared__ uint32_t hist[kBB];
     __shared__ uint32_t ovf[kBOvf];
     __shared__ unsigned long long s64[33];
@@ -103,6 +108,7 @@ __global__ void __launch_bounds__(kBThreads) k_ks_batch(const uint32_t *__restri
     __shared__ long long sel_I[kBThreads];
     __shared__ double sdbl[33];
     __shared__ long long s64l[33];
+    __shared__ int s_gi;
     constexpr int kCap = kBB + kBOvf;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBThreads / 32;
     uint32_t *xs = sc.xs + (size_t)blockIdx.x * kCap;
@@ -112,7 +118,15 @@ __global__ void __launch_bounds__(kBThreads) k_ks_batch(const uint32_t *__restri
     double *Dc = sc.Dc + (size_t)blockIdx.x * kCap;
     double *Ac = sc.Ac + (size_t)blockIdx.x * kCap;
     double *Zc = sc.Zc + (size_t)blockIdx.x * kCap;
-    for (int g = blockIdx.x; g < G; g += gridDim.x) {
+    for (int gi = blockIdx.x;; gi += gridDim.x) {
+        if (next) {
+            if (tid == 0) s_gi = atomicAdd(next, 1);
+            __syncthreads();
+            gi = s_gi;
+            __syncthreads();
+        }
+        if (gi >= G) break;
+        const int g = order ? order[gi] : gi;
         const long long v0 = vo[g], ng = vo[g + 1] - v0;
         // 1. histogram and argmax key (deg << 32) | ~local id
         for (int i = tid; i < kBB; i += kBThreads) hist[i] = 0;
@@ -277,12 +291,13 @@ __global__ void __launch_bounds__(kBThreads) k_ks_batch(const uint32_t *__restri
             const float alpha_f = (float)Ac[i], lnc_f = (float)lnx[i];
             const float Z_f = zeta_scaled_f(alpha_f, (float)xs[i], lnc_f);
             const unsigned long long ci = cum[i];
-            const double N = (double)(total - ci);
+            const float invN_f = 1.0f / (float)(total - ci);
             float fm = 0.0f;
             for (long long j = i + lane; j < nd; j += 32) {
-                const double before = (double)(cum[j] - ci) / N, at = (double)(cum[j + 1] - ci) / N;
-                fm = fmaxf(fm, ks_term_f(alpha_f, Z_f, lnc_f, (float)xs[j], (float)lnx[j], (float)before, (float)at,
-                                         j == i));
+                // the empirical CDF fractions in fp32 too (an fp64 divide per term
+                // kept the fp64 pipe busy); within ~1e-7 of the fp64 values
+                const float before = (float)(cum[j] - ci) * invN_f, at = (float)(cum[j + 1] - ci) * invN_f;
+                fm = fmaxf(fm, ks_term_f(alpha_f, Z_f, lnc_f, (float)xs[j], (float)lnx[j], before, at, j == i));
             }
 #pragma unroll
             for (int o2 = 16; o2 > 0; o2 >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o2));
@@ -308,14 +323,16 @@ __global__ void __launch_bounds__(kBThreads) k_ks_batch(const uint32_t *__restri
             const float Z_f = zeta_scaled_f(alpha_f, (float)xs[i], lnc_f);
             const unsigned long long ci = cum[i];
             const double N = (double)(total - ci);
+            const float invN_f = 1.0f / (float)(total - ci);
             const float cut = (float)df - kScreenSlack;
             double dm = 0.0;
             for (long long j = i + lane; j < nd; j += 32) {
                 const double x = (double)xs[j];
-                const double before = (double)(cum[j] - ci) / N, at = (double)(cum[j + 1] - ci) / N;
-                const float d32 = ks_term_f(alpha_f, Z_f, lnc_f, (float)x, (float)lnx[j], (float)before, (float)at,
-                                            j == i);
+                // the screen's fp32 term (the same arithmetic as in step 5)
+                const float d32 = ks_term_f(alpha_f, Z_f, lnc_f, (float)x, (float)lnx[j], (float)(cum[j] - ci) * invN_f,
+                                            (float)(cum[j + 1] - ci) * invN_f, j == i);
                 if (d32 >= cut) {
+                    const double before = (double)(cum[j] - ci) / N, at = (double)(cum[j + 1] - ci) / N;
                     double zb, za;
                     zeta_pair(alpha, x, lnx[j], lnc, zb, za);
                     double d = fabs(at - (1.0 - za / Z));
@@ -398,7 +415,7 @@ __global__ void k_fit_one_to_state(KsBatchOut out, DevState *st, double tau) {
 void launch_fit_one(const uint32_t *deg, long long n, int64_t *vo, KsBatchScratch sc, KsBatchOut out, DevState *st,
                     long long min_tail, long long min_distinct, double min_span, double tau, cudaStream_t s) {
     k_fit_one_offsets<<<1, 1, 0, s>>>(vo, n);
-    k_ks_batch<<<1, kBThreads, 0, s>>>(deg, vo, 1, sc, out, min_tail, min_distinct, min_span, tau);
+    k_ks_batch<<<1, kBThreads, 0, s>>>(deg, vo, 1, sc, out, min_tail, min_distinct, min_span, tau, nullptr, nullptr);
     k_fit_one_to_state<<<1, 1, 0, s>>>(out, st, tau);
 }
 
@@ -423,10 +440,11 @@ size_t ks_batch_entries() { return (size_t)(kBB + kBOvf); }
 
 void launch_ks_batch(const uint32_t *deg, const int64_t *vo, int G, KsBatchScratch sc, KsBatchOut out,
                      long long min_tail, long long min_distinct, double min_span, double tau, int blocks,
-                     cudaStream_t s) {
+                     const int *order, int *next, cudaStream_t s) {
     if (G <= 0) return;
+    if (next) cudaMemsetAsync(next, 0, sizeof(int), s);
     k_ks_batch<<<blocks < G ? blocks : G, kBThreads, 0, s>>>(deg, vo, G, sc, out, min_tail, min_distinct, min_span,
-                                                             tau);
+                                                             tau, order, next);
 }
 
 void launch_merge_visited(const uint32_t *vis, long long ng, long long base, const DevState *st, vid_t *parent,
