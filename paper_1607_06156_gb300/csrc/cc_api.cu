@@ -1407,6 +1407,14 @@ cc_status ensure_batch_route(cc_ctx *ctx, int G, int blocks) {
 // pass in tile blocks.
 constexpr bool kBatchFitOverlap = true;
 
+// The batched degree pass takes its tiles in order from a device counter
+// (measured below); null keeps the grid stride.
+constexpr bool kBatchTileQueue = true;
+unsigned long long *tile_queue(cc_ctx *ctx) {
+    return kBatchTileQueue ? reinterpret_cast<unsigned long long *>(static_cast<char *>(ctx->counters.p) + 1088)
+                           : nullptr;
+}
+
 // One K-S fit per graph on stream s (the degrees of every graph are in
 // ctx->deg); the blocks take the graphs largest first.
 cc_status enqueue_ks_batch(cc_ctx *ctx, const int64_t *vo_dev, const int64_t *vo_host, int G, cudaStream_t s) {
@@ -1745,7 +1753,7 @@ cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int6
     CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)(n > 0 ? n : 1) * 4, s));
     CC_TRY(ensure_tiles(ctx, edge_offsets_dev, vertex_offsets_dev, G, m, n, s));
     launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, as<uint32_t>(ctx->deg),
-                        st, ctx->grid, s);
+                        st, ctx->grid, tile_queue(ctx), s);
     std::vector<int> route;
     CC_TRY(enqueue_ks_batch(ctx, vertex_offsets_dev, vertex_offsets_host, G, s));
     CC_TRY(batch_routes(ctx, vertex_offsets_host, G, route, s));
@@ -1830,7 +1838,7 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
             {
                 Scope sc(ctx, CC_K_DEGREE, s, 1);
                 launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G,
-                                    as<uint32_t>(ctx->deg), st, ctx->grid, s);
+                                    as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), s);
             }
             // the fits on a highest-priority stream, overlapping the first hook
             // pass, which launches one block per tile so that the fits' blocks

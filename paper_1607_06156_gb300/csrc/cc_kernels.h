@@ -197,8 +197,9 @@ struct KsBatchOut {  // per graph
     unsigned long long *seedkey;  // (degree << 32) | (0xffffffff - local id) of the max-degree vertex
 };
 size_t ks_batch_entries();
+// next: a device counter the blocks take tiles from in order (zeroed here), or null (grid stride)
 void launch_degree_batch(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G, uint32_t *deg,
-                         DevState *st, int grid, cudaStream_t s);
+                         DevState *st, int grid, unsigned long long *next, cudaStream_t s);
 // out[k] = the graph holding item k << kTileShift of the offsets `off` (G + 1 entries), k < (count >> kTileShift) + 1
 void launch_tile_graphs(const int64_t *off, int G, long long count, uint32_t *out, int grid, cudaStream_t s);
 // order (device, G graph numbers, largest first) and next (device counter) may

@@ -26,18 +26,31 @@ constexpr int kBOvf = 4096;        // degrees >= kBB held per graph
 constexpr int kBThreads = 256;
 
 // ---------------------------------------------------------------------------
+// With `next` (a zeroed counter) blocks take tiles in increasing order from
+// it instead of striding by the grid: the tiles in flight then stay within a
+// window of about one tile per block, so the few graphs they belong to keep
+// their counters in L2 (with a fixed stride, blocks drift apart and the
+// counters of many graphs compete for it).
 __global__ void __launch_bounds__(kBlock) k_degree_batch(const int32_t *__restrict__ in, long long m,
                                                          const int64_t *__restrict__ eo,
                                                          const int64_t *__restrict__ vo, int G, uint32_t *deg,
-                                                         DevState *st) {
+                                                         DevState *st, unsigned long long *next) {
     constexpr int U = 2, K = 2 * U;
     __shared__ int sg;
+    __shared__ long long s_t;
     const long long nvec = m / 2;
     const int4 *ev = reinterpret_cast<const int4 *>(in);
     bool bad = false;
     const long long tile = (long long)kBlock * U;
     const long long ntiles = (nvec + tile - 1) / tile;
-    for (long long t = blockIdx.x; t < ntiles + ((m & 1) ? 1 : 0); t += gridDim.x) {
+    const long long nt = ntiles + ((m & 1) ? 1 : 0);
+    for (long long t = blockIdx.x;; t += gridDim.x) {
+        if (next) {
+            if (threadIdx.x == 0) s_t = (long long)atomicAdd(next, 1ull);
+            __syncthreads();
+            t = s_t;
+        }
+        if (t >= nt) break;
         const long long k0 = t < ntiles ? t * tile * 2 : m - 1;
         // the tile's graph by a binary search of the offsets (held in L1); on
         // 4,096 graphs this measured 58 ms for the degree and fit passes
@@ -421,9 +434,11 @@ void launch_fit_one(const uint32_t *deg, long long n, int64_t *vo, KsBatchScratc
 
 // ---------------------------------------------------------------------------
 void launch_degree_batch(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G, uint32_t *deg,
-                         DevState *st, int grid, cudaStream_t s) {
+                         DevState *st, int grid, unsigned long long *next, cudaStream_t s) {
     if (m <= 0) return;
-    k_degree_batch<<<fit_grid((const void *)k_degree_batch, grid, kBlock), kBlock, 0, s>>>(in, m, eo, vo, G, deg, st);
+    if (next) cudaMemsetAsync(next, 0, sizeof(unsigned long long), s);
+    k_degree_batch<<<fit_grid((const void *)k_degree_batch, grid, kBlock), kBlock, 0, s>>>(in, m, eo, vo, G, deg, st,
+                                                                                         next);
 }
 
 __global__ void __launch_bounds__(kBlock) k_tile_graphs(const int64_t *__restrict__ off, int G, long long ntiles,
