@@ -1309,6 +1309,17 @@ cc_status labels_host_impl(cc_ctx *ctx, const void *edges_host, vid_t n, long lo
 }
 
 // ---------------------------------------------------------------------------
+// The batched degree pass takes its tiles in order from a device counter;
+// null keeps the grid stride. Measured on 4,096 graphs: degree pass 38.8 ms
+// with the stride, 33.2 ms in order. The batched hook passes keep the
+// stride: with the counter (two more barriers per tile) the gather pass went
+// from 23.9 to 26.7 ms.
+constexpr bool kBatchTileQueue = true;
+unsigned long long *tile_queue(cc_ctx *ctx) {
+    return kBatchTileQueue ? reinterpret_cast<unsigned long long *>(static_cast<char *>(ctx->counters.p) + 1088)
+                           : nullptr;
+}
+
 // Schedule tuner of the batched form. The hook passes over a batch map each
 // tile of pairs to its graph, and how many pairs a thread carries per tile
 // (amortising that lookup and keeping loads in flight) against how many
@@ -1406,14 +1417,6 @@ cc_status ensure_batch_route(cc_ctx *ctx, int G, int blocks) {
 // pass, 105.7 with the fits beside a resident-grid pass, 103.2 with the
 // pass in tile blocks.
 constexpr bool kBatchFitOverlap = true;
-
-// The batched degree pass takes its tiles in order from a device counter
-// (measured below); null keeps the grid stride.
-constexpr bool kBatchTileQueue = true;
-unsigned long long *tile_queue(cc_ctx *ctx) {
-    return kBatchTileQueue ? reinterpret_cast<unsigned long long *>(static_cast<char *>(ctx->counters.p) + 1088)
-                           : nullptr;
-}
 
 // One K-S fit per graph on stream s (the degrees of every graph are in
 // ctx->deg); the blocks take the graphs largest first.
