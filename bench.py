@@ -127,6 +127,8 @@ def l2_ops(cls: str, st: dict) -> tuple[float, str]:
         k = st.get("sv_sample_stride", 1) or 1
         if k > 1:  # front end on m/k pairs: a pre-check, then two gathers and a pre-check
             return 4.0 * m / k, "gather"
+        if 2 * m < 4 * n:  # sparse graphs: an atomicMin per pair, no pre-check read
+            return 1.0 * m, "red_min"
         return 1.0 * m, "gather"             # pre-check read of parent[max(u, v)]
     if cls == "sv_gather_input":
         kept = act[2] if len(act) > 2 else 0

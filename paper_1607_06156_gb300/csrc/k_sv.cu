@@ -28,7 +28,8 @@
 // label of v is its root, the minimum id of its component (Section 3.1.1).
 //
 // Pass variants: MODE 0 is the first pass over the caller's pairs while
-// parent is the identity (no gathers, nothing written); MODE 1 is the first
+// parent is the identity (no gathers, nothing written; MODE 4 is the same
+// without the read of parent[max] before the atomicMin); MODE 1 is the first
 // pass after the BFS step (Algorithm 2, lines 8-9: pairs with both ends
 // visited are dropped, a visited end stands for the BFS component's root);
 // MODE 2 gathers parents (one hop: every vertex the pass reads points at a
@@ -58,9 +59,15 @@ __device__ __forceinline__ bool sv_pair(long long u, long long v, vid_t n, vid_t
         bad = true;
         return false;
     }
-    if (MODE == 0) {
+    if (MODE == 0 || MODE == 4) {
         ru = (vid_t)u;
         rv = (vid_t)v;
+        if (MODE == 4) {  // no pre-check: a fire-and-forget atomicMin
+            if (ru == rv) return false;
+            const vid_t hi = ru > rv ? ru : rv, lo = ru > rv ? rv : ru;
+            atomicMin(&parent[hi], lo);
+            return true;
+        }
     } else if (MODE == 1) {
         const bool ok = cmin < n;
         const bool a = ok && vis_test(vis, u), b = ok && vis_test(vis, v);
@@ -506,6 +513,8 @@ void launch_sv_pass(int mode, bool write, bool record, const void *in, long long
     if (mode == 0) {
         if (write) SVP(0, true, false);
         else SVP(0, false, false);
+    } else if (mode == 4) {
+        SVP(4, false, false);
     } else if (mode == 1) {
         SVP(1, true, true);
     } else if (mode == 2) {
