@@ -28,12 +28,13 @@
  *    `id_bytes` (4: int32, 8: int64) each, vertex ids dense in [0, n).
  *    Self-loops and duplicate pairs are allowed. n must be < 2^32 - 1.
  *    Edge arrays must be 16-byte aligned (the kernels read them with 128-bit
- *    loads); labels are written with the same id width as the edges.
+ *    loads), and so must the label array of cc_labels (written with 128-bit
+ *    stores); labels are written with the same id width as the edges.
  *  - Errors: argument errors are returned immediately and nothing is
  *    enqueued. Errors the device detects (an id outside [0, n), a run that
- *    exceeds the iteration cap) are recorded in the context and returned by
- *    the next cc_get_stats() or, with debug_checks set, by the call itself;
- *    the contents of the outputs are then unspecified.
+ *    exceeds the iteration cap) are recorded in the context. The labelling
+ *    calls synchronise their stream and return them; cc_get_stats() returns
+ *    the last one again. The contents of the outputs are then unspecified.
  *  - A context is not thread safe: use one context per host thread/stream.
  */
 #ifndef CC_GB300_H
@@ -177,7 +178,8 @@ cc_status cc_destroy(cc_ctx *ctx);
  *   edges_dev      [m][2] pairs of id_bytes each (device, 16-byte aligned)
  *   n              vertices, 0 <= n < 2^32 - 1
  *   m              pairs, m >= 0 (m = 0 gives labels_out[v] = v)
- *   labels_out_dev [n] ids of id_bytes each (device); labels_out[v] = min id of v's component
+ *   labels_out_dev [n] ids of id_bytes each (device, 16-byte aligned);
+ *                  labels_out[v] = min id of v's component
  * The call synchronises `stream` internally a few times (to read the route
  * and the active-pair counts); everything else is enqueued. On return the
  * labels are complete on `stream`.
