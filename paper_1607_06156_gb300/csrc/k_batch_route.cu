@@ -24,6 +24,7 @@ namespace ccg {
 constexpr int kBB = 4096;          // dense degree bins per graph (degrees 1..kBB-1)
 constexpr int kBOvf = 4096;        // degrees >= kBB held per graph
 constexpr int kBThreads = 256;
+constexpr int kZTab = 128;         // zeta table entries per warp (the refinement of step 6)
 
 // ---------------------------------------------------------------------------
 // With `next` (a zeroed counter) blocks take tiles in increasing order from
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(kBlock) k_degree_batch(const int32_t *__restri
 // graphs by decreasing vertex count, `next`: zeroed), so the few largest
 // fits start first and the small ones fill the gaps; without `next` block b
 // takes graphs b, b + grid, ...
-__global__ void __launch_bounds__(kBThreads) k_ks_batch(const uint32_t *__restrict__ deg,
+__global__ void __launch_bounds__(kBThreads, 3) k_ks_batch(const uint32_t *__restrict__ deg,
                                                         const int64_t *__restrict__ vo, int G, KsBatchScratch sc,
                                                         KsBatchOut out, long long min_tail, long long min_distinct,
                                                         double min_span, double tau, const int *__restrict__ order,
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(kBThreads) k_ks_batch(const uint32_t *__restri
     __shared__ double sdbl[33];
     __shared__ long long s64l[33];
     __shared__ int s_gi;
+    __shared__ double ztab[kBThreads / 32][kZTab];  // per warp: the zeta table of its contender
     constexpr int kCap = kBB + kBOvf;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBThreads / 32;
     uint32_t *xs = sc.xs + (size_t)blockIdx.x * kCap;
@@ -331,7 +333,13 @@ __global__ void __launch_bounds__(kBThreads) k_ks_batch(const uint32_t *__restri
                 continue;
             }
             const double alpha = Ac[i], lnc = lnx[i];
-            const double Z = zeta_scaled(alpha, (double)xs[i], lnc);
+            const long long xmin = (long long)xs[i];
+            // the zeta terms below the remainder threshold once for this
+            // exponent (one fp64 power per lane) instead of a loop of them per term
+            double tail = 0.0;
+            double *tab = ztab[warp];
+            const long long T = zeta_table_warp(alpha, xmin, lnc, tab, kZTab, tail);
+            const double Z = (T >= 0 && xmin < T) ? tab[0] + tail : zeta_scaled(alpha, (double)xmin, lnc);
             const float alpha_f = (float)alpha, lnc_f = (float)lnc;
             const float Z_f = zeta_scaled_f(alpha_f, (float)xs[i], lnc_f);
             const unsigned long long ci = cum[i];
@@ -347,7 +355,13 @@ __global__ void __launch_bounds__(kBThreads) k_ks_batch(const uint32_t *__restri
                 if (d32 >= cut) {
                     const double before = (double)(cum[j] - ci) / N, at = (double)(cum[j + 1] - ci) / N;
                     double zb, za;
-                    zeta_pair(alpha, x, lnx[j], lnc, zb, za);
+                    const long long xi = (long long)xs[j];
+                    if (T >= 0 && xi < T) {
+                        zb = tab[xi - xmin] + tail;
+                        za = (xi + 1 < T ? tab[xi + 1 - xmin] : 0.0) + tail;
+                    } else {
+                        zeta_pair(alpha, x, lnx[j], lnc, zb, za);
+                    }
                     double d = fabs(at - (1.0 - za / Z));
                     if (j > i) d = fmax(d, fabs(before - (1.0 - zb / Z)));
                     dm = fmax(dm, d);
@@ -356,6 +370,7 @@ __global__ void __launch_bounds__(kBThreads) k_ks_batch(const uint32_t *__restri
 #pragma unroll
             for (int o2 = 16; o2 > 0; o2 >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o2));
             if (lane == 0) Dc[i] = dm;
+            __syncwarp();  // the table is rewritten for the warp's next contender
         }
         __syncthreads();
         // 5. selection: minimum D, ties to the smaller xmin (per-thread scan, then a block reduction)

@@ -90,6 +90,36 @@ __device__ __forceinline__ void zeta_pair(double s, double x, double lnx, double
     }
 }
 
+// The terms of the scaled zeta below its Euler-Maclaurin threshold, summed
+// once per exponent by one warp: T is the first integer >= max(16, 2s);
+// for integers q0 <= x < T, tab[x - q0] = sum_{t=x}^{T-1} (t/c)^-s (suffix
+// sums), and `tail` = the remainder from T on. Then for q0 <= x < T
+// zeta_scaled(s, x, lnc) = tab[x - q0] + tail (the same sum as the direct
+// loop, summed in another order). Returns T, or -1 (warp-uniform) when the
+// table would need more than cap entries. All lanes of the warp call it.
+__device__ __forceinline__ long long zeta_table_warp(double s, long long q0, double lnc, double *tab, int cap,
+                                                     double &tail) {
+    const int lane = threadIdx.x & 31;
+    const long long T = (long long)ceil(fmax(16.0, 2.0 * s));
+    const long long span = T - q0;
+    if (span > cap) return -1;
+    tail = zeta_tail(s, (double)T, exp(-s * (log((double)T) - lnc)));
+    double carry = 0.0;  // the sum of the entries above the current chunk
+    for (long long c0 = span > 0 ? ((span - 1) / 32) * 32 : -1; c0 >= 0; c0 -= 32) {
+        const long long k = c0 + lane;
+        double v = k < span ? exp(-s * (log((double)(q0 + k)) - lnc)) : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {  // inclusive suffix sum over the lanes
+            const double y = __shfl_down_sync(0xffffffffu, v, o);
+            if (lane + o < 32) v += y;
+        }
+        if (k < span) tab[k] = v + carry;
+        carry += __shfl_sync(0xffffffffu, v, 0);
+    }
+    __syncwarp();
+    return T;
+}
+
 template <typename V>
 __device__ V block_reduce_sum(V x, V *smem) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
