@@ -773,9 +773,11 @@ cc_status enqueue_small_fit(cc_ctx *ctx, vid_t n, cudaStream_t s) {
                    as<long long>(ctx->kb_ntail), as<long long>(ctx->kb_ncand), as<int>(ctx->kb_route),
                    as<int>(ctx->kb_ovf),      as<unsigned long long>(ctx->kb_seed)};
     int64_t *vo = reinterpret_cast<int64_t *>(static_cast<char *>(ctx->counters.p) + 256);
-    Scope sc2(ctx, CC_K_KS, s, 3);
+    Scope sc2(ctx, CC_K_KS, s, 4);
+    // the idle degree-histogram buffer (kHistDense words) holds the grid-wide histogram of the small graph
     launch_fit_one(as<uint32_t>(ctx->deg), n, vo, sc, out, as<DevState>(ctx->st), ctx->opt.ks_min_tail,
-                   ctx->opt.ks_min_distinct, ctx->opt.ks_min_span, ctx->opt.ks_tau, s);
+                   ctx->opt.ks_min_distinct, ctx->opt.ks_min_span, ctx->opt.ks_tau, as<uint32_t>(ctx->hist), ctx->grid,
+                   s);
     return CC_OK;
 }
 

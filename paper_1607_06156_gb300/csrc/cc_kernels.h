@@ -208,9 +208,12 @@ void launch_ks_batch(const uint32_t *deg, const int64_t *vo, int G, KsBatchScrat
                      long long min_tail, long long min_distinct, double min_span, double tau, int blocks,
                      const int *order, int *next, cudaStream_t s);
 // one graph (n vertices, degrees in deg) through the per-graph fit; results into DevState
-// (ks_out, ncand, route, maxkey); vo: 2 int64 of device scratch
+// (ks_out, ncand, route, maxkey); vo: 2 int64 of device scratch; hist_scratch: small_hist_words()
+// words (8-byte aligned) for a grid-wide histogram, or null (the fit block builds it)
+size_t small_hist_words();
 void launch_fit_one(const uint32_t *deg, long long n, int64_t *vo, KsBatchScratch sc, KsBatchOut out, DevState *st,
-                    long long min_tail, long long min_distinct, double min_span, double tau, cudaStream_t s);
+                    long long min_tail, long long min_distinct, double min_span, double tau, uint32_t *hist_scratch,
+                    int grid, cudaStream_t s);
 void launch_merge_visited(const uint32_t *vis, long long ng, long long base, const DevState *st, vid_t *parent,
                           int grid, cudaStream_t s);
 

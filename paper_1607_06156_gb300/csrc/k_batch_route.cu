@@ -25,6 +25,7 @@ constexpr int kBB = 4096;          // dense degree bins per graph (degrees 1..kB
 constexpr int kBOvf = 4096;        // degrees >= kBB held per graph
 constexpr int kBThreads = 256;
 constexpr int kZTab = 128;         // zeta table entries per warp (the refinement of step 6)
+constexpr int kSmallHistKeyAt = 2 * kBB + 2;  // word of the argmax key in k_small_hist's output (8-byte aligned)
 
 // ---------------------------------------------------------------------------
 // With `next` (a zeroed counter) blocks take tiles in increasing order from
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_ks_batch(const uint32_t *__res
                                                         const int64_t *__restrict__ vo, int G, KsBatchScratch sc,
                                                         KsBatchOut out, long long min_tail, long long min_distinct,
                                                         double min_span, double tau, const int *__restrict__ order,
-                                                        int *next) {
+                                                        int *next, const uint32_t *__restrict__ pre) {
     __shared__ uint32_t hist[kBB];
     __shared__ uint32_t ovf[kBOvf];
     __shared__ unsigned long long s64[33];
@@ -143,52 +144,63 @@ __global__ void __launch_bounds__(kBThreads, 3) k_ks_batch(const uint32_t *__res
         if (gi >= G) break;
         const int g = order ? order[gi] : gi;
         const long long v0 = vo[g], ng = vo[g + 1] - v0;
-        // 1. histogram and argmax key (deg << 32) | ~local id
-        for (int i = tid; i < kBB; i += kBThreads) hist[i] = 0;
-        if (tid == 0) {
-            s_novf = 0;
-            s_key = 0;
-        }
-        __syncthreads();
-        unsigned long long best = 0;
-        // kHistLoads independent loads in flight per thread (one block walks the
-        // whole graph, so the loop is bound by load latency, not bandwidth); lanes
-        // holding the same degree add to its bin once (degrees of many graphs
-        // are concentrated on a few values, whose bins would serialise the atomics).
-        // The loop runs warp-uniformly so that every lane joins the match.
-        constexpr int kHistLoads = 8;
-        for (long long vb = (long long)(tid & ~31); vb < ng; vb += (long long)kBThreads * kHistLoads) {
-            uint32_t dv[kHistLoads];
-#pragma unroll
-            for (int q = 0; q < kHistLoads; q++) {
-                const long long w = vb + lane + (long long)q * kBThreads;
-                dv[q] = w < ng ? deg[v0 + w] : 0u;
+        if (pre) {  // one graph, histogram built by k_small_hist over the whole grid
+            for (int i = tid; i < kBB; i += kBThreads) hist[i] = pre[i];
+            const unsigned cnt = pre[2 * kBB];
+            for (int i = tid; i < kBOvf && i < (int)cnt; i += kBThreads) ovf[i] = pre[kBB + i];
+            if (tid == 0) {
+                s_novf = (int)(cnt < 0x7fffffffu ? cnt : 0x7fffffffu);
+                s_key = *reinterpret_cast<const unsigned long long *>(pre + kSmallHistKeyAt);
             }
-#pragma unroll
-            for (int q = 0; q < kHistLoads; q++) {
-                const long long w = vb + lane + (long long)q * kBThreads;
-                const uint32_t d = dv[q];
-                if (w < ng) {
-                    const unsigned long long key =
-                        ((unsigned long long)d << 32) | (0xffffffffull - (unsigned long long)w);
-                    best = key > best ? key : best;
+            __syncthreads();
+        } else {
+            // 1. histogram and argmax key (deg << 32) | ~local id
+            for (int i = tid; i < kBB; i += kBThreads) hist[i] = 0;
+            if (tid == 0) {
+                s_novf = 0;
+                s_key = 0;
+            }
+            __syncthreads();
+            unsigned long long best = 0;
+            // kHistLoads independent loads in flight per thread (one block walks the
+            // whole graph, so the loop is bound by load latency, not bandwidth); lanes
+            // holding the same degree add to its bin once (degrees of many graphs
+            // are concentrated on a few values, whose bins would serialise the atomics).
+            // The loop runs warp-uniformly so that every lane joins the match.
+            constexpr int kHistLoads = 8;
+            for (long long vb = (long long)(tid & ~31); vb < ng; vb += (long long)kBThreads * kHistLoads) {
+                uint32_t dv[kHistLoads];
+    #pragma unroll
+                for (int q = 0; q < kHistLoads; q++) {
+                    const long long w = vb + lane + (long long)q * kBThreads;
+                    dv[q] = w < ng ? deg[v0 + w] : 0u;
                 }
-                const uint32_t bin = (w < ng && d != 0 && d < (uint32_t)kBB) ? d : 0xffffffffu;
-                const unsigned peers = __match_any_sync(0xffffffffu, bin);
-                if (bin != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
-                if (w < ng && d >= (uint32_t)kBB) {
-                    const int k = atomicAdd(&s_novf, 1);
-                    if (k < kBOvf) ovf[k] = d;
+    #pragma unroll
+                for (int q = 0; q < kHistLoads; q++) {
+                    const long long w = vb + lane + (long long)q * kBThreads;
+                    const uint32_t d = dv[q];
+                    if (w < ng) {
+                        const unsigned long long key =
+                            ((unsigned long long)d << 32) | (0xffffffffull - (unsigned long long)w);
+                        best = key > best ? key : best;
+                    }
+                    const uint32_t bin = (w < ng && d != 0 && d < (uint32_t)kBB) ? d : 0xffffffffu;
+                    const unsigned peers = __match_any_sync(0xffffffffu, bin);
+                    if (bin != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
+                    if (w < ng && d >= (uint32_t)kBB) {
+                        const int k = atomicAdd(&s_novf, 1);
+                        if (k < kBOvf) ovf[k] = d;
+                    }
                 }
             }
+    #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long b = __shfl_xor_sync(0xffffffffu, best, o);
+                best = b > best ? b : best;
+            }
+            if (lane == 0 && best) atomicMax(&s_key, best);
+            __syncthreads();
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long b = __shfl_xor_sync(0xffffffffu, best, o);
-            best = b > best ? b : best;
-        }
-        if (lane == 0 && best) atomicMax(&s_key, best);
-        __syncthreads();
         const int novf = s_novf;
         if (tid == 0) {
             out.seedkey[g] = s_key;
@@ -440,10 +452,51 @@ __global__ void k_fit_one_to_state(KsBatchOut out, DevState *st, double tau) {
     st->maxkey = out.seedkey[0];
 }
 
+// The one-block fit's histogram over the whole grid (one block walking all
+// n degrees was most of the fit on small graphs): h[d] for degrees 1..kBB-1
+// (privatised per block), the degrees >= kBB listed from h[kBB] on (their
+// count at h[2 kBB]; at most kBOvf kept), the argmax key at kSmallHistKeyAt.
+__global__ void __launch_bounds__(kBlock) k_small_hist(const uint32_t *__restrict__ deg, long long n, uint32_t *h) {
+    __shared__ uint32_t sh[kBB];
+    for (int i = threadIdx.x; i < kBB; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    unsigned long long best = 0;
+    for (long long v = gtid(); v < n; v += gstride()) {
+        const uint32_t d = deg[v];
+        const unsigned long long key = ((unsigned long long)d << 32) | (0xffffffffull - (unsigned long long)v);
+        best = key > best ? key : best;
+        if (d == 0) continue;
+        if (d < (uint32_t)kBB) {
+            atomicAdd(&sh[d], 1u);
+        } else {
+            const unsigned k = atomicAdd(&h[2 * kBB], 1u);
+            if (k < (unsigned)kBOvf) h[kBB + k] = d;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, best, o);
+        best = b > best ? b : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best)
+        atomicMax(reinterpret_cast<unsigned long long *>(h + kSmallHistKeyAt), best);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBB; i += blockDim.x)
+        if (sh[i]) atomicAdd(&h[i], sh[i]);
+}
+
+size_t small_hist_words() { return (size_t)kSmallHistKeyAt + 2; }
+
 void launch_fit_one(const uint32_t *deg, long long n, int64_t *vo, KsBatchScratch sc, KsBatchOut out, DevState *st,
-                    long long min_tail, long long min_distinct, double min_span, double tau, cudaStream_t s) {
+                    long long min_tail, long long min_distinct, double min_span, double tau, uint32_t *hist_scratch,
+                    int grid, cudaStream_t s) {
     k_fit_one_offsets<<<1, 1, 0, s>>>(vo, n);
-    k_ks_batch<<<1, kBThreads, 0, s>>>(deg, vo, 1, sc, out, min_tail, min_distinct, min_span, tau, nullptr, nullptr);
+    if (hist_scratch) {
+        cudaMemsetAsync(hist_scratch, 0, small_hist_words() * 4, s);
+        k_small_hist<<<fit_grid((const void *)k_small_hist, grid, kBlock), kBlock, 0, s>>>(deg, n, hist_scratch);
+    }
+    k_ks_batch<<<1, kBThreads, 0, s>>>(deg, vo, 1, sc, out, min_tail, min_distinct, min_span, tau, nullptr, nullptr,
+                                       hist_scratch);
     k_fit_one_to_state<<<1, 1, 0, s>>>(out, st, tau);
 }
 
@@ -474,7 +527,7 @@ void launch_ks_batch(const uint32_t *deg, const int64_t *vo, int G, KsBatchScrat
     if (G <= 0) return;
     if (next) cudaMemsetAsync(next, 0, sizeof(int), s);
     k_ks_batch<<<blocks < G ? blocks : G, kBThreads, 0, s>>>(deg, vo, G, sc, out, min_tail, min_distinct, min_span,
-                                                             tau, order, next);
+                                                             tau, order, next, nullptr);
 }
 
 void launch_merge_visited(const uint32_t *vis, long long ng, long long base, const DevState *st, vid_t *parent,
