@@ -230,7 +230,6 @@ __global__ void __launch_bounds__(kBThreads, 3) k_ks_batch(const uint32_t *__res
                 xs[o] = (uint32_t)d;
                 cnt[o] = h;
                 cum[o] = om;
-                lnx[o] = log((double)d);
                 o++;
                 om += h;
             }
@@ -270,12 +269,15 @@ __global__ void __launch_bounds__(kBThreads, 3) k_ks_batch(const uint32_t *__res
                 xs[q] = ovf[i];
                 cnt[q] = (unsigned long long)(e - i);
                 cum[q] = tmass + (unsigned long long)i;
-                lnx[q] = log((double)ovf[i]);
             }
             outn += tot;
         }
         const long long nd = (long long)(tnz + outn);
         if (tid == 0) cum[nd] = tmass + (unsigned long long)novf;
+        __syncthreads();
+        // ln x of every distinct degree, one per thread (an owner of many
+        // occupied bins would otherwise run its fp64 logs one after another)
+        for (long long i = tid; i < nd; i += kBThreads) lnx[i] = log((double)xs[i]);
         __syncthreads();
         // 3. suffix sums SL[i] = sum_{j >= i} cnt[j] ln x[j] (fp64, one reverse
         //    pass in chunks of the block), kept in Zc: they make every
