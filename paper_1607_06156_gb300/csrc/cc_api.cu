@@ -1423,12 +1423,14 @@ cc_status ensure_batch_route(cc_ctx *ctx, int G, int blocks) {
 
 // deg holds the union degrees. Fills kb_* for every graph and returns the
 // routes (1 = BFS first) in `route` (host, G entries).
-// The batched route: the per-graph fits overlap the first hook pass (on a
-// highest-priority stream, the pass launched one block per tile) instead of
-// following it. Measured on 4,096 graphs: 107 ms with the fits after the
-// pass, 105.7 with the fits beside a resident-grid pass, 103.2 with the
-// pass in tile blocks.
-constexpr bool kBatchFitOverlap = true;
+// The batched route: the per-graph fits run on a highest-priority stream
+// beside the first hook pass; kBatchFitOverlap launches that pass one block
+// per tile so that the fits get SMs as its blocks retire. Measured on 4,096
+// graphs while the fits took 25 ms: 107 ms with the fits after the pass,
+// 105.7 beside a resident-grid pass, 103.2 beside the tile-block pass. Once
+// the fits took 2.7 ms: 89.8 ms with the tile-block pass, 88.2 with the
+// resident grid (the tile blocks cost more than the overlap saves).
+constexpr bool kBatchFitOverlap = false;
 
 // One K-S fit per graph on stream s (the degrees of every graph are in
 // ctx->deg); the blocks take the graphs largest first.
