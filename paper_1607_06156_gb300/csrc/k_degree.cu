@@ -470,16 +470,21 @@ __global__ void __launch_bounds__(256) k_ks_terms(const uint32_t *xs, const unsi
         const float alpha_f = (float)alpha, Z_f = (float)Z, lnc_f = (float)lnc;
         const unsigned long long ci = cum[i];
         const double N = (double)(cum[nd] - ci);
+        const float invN_f = 1.0f / (float)(cum[nd] - ci);
         const float cut = REFINE ? Df[i] - kScreenSlack : 0.0f;
         float fmax_ = 0.0f;
         double dmax = 0.0;
         for (long long j = j0 + threadIdx.x; j < nd && j < j0 + kKsTerms; j += blockDim.x) {
             const double x = (double)xs[j];
-            const double before = (double)(cum[j] - ci) / N;
-            const double at = (double)(cum[j + 1] - ci) / N;
-            const float d32 = ks_term_f(alpha_f, Z_f, lnc_f, (float)x, (float)lnx[j], (float)before, (float)at, j == i);
+            // the screen in fp32 throughout (CDF fractions included: an fp64
+            // divide per term kept the fp64 pipe busy); fp64 only for the
+            // terms the refinement keeps
+            const float d32 = ks_term_f(alpha_f, Z_f, lnc_f, (float)x, (float)lnx[j], (float)(cum[j] - ci) * invN_f,
+                                        (float)(cum[j + 1] - ci) * invN_f, j == i);
             fmax_ = fmaxf(fmax_, d32);
             if (REFINE && d32 >= cut) {
+                const double before = (double)(cum[j] - ci) / N;
+                const double at = (double)(cum[j + 1] - ci) / N;
                 double zb, za;  // model mass at >= x and at >= x+1 (scaled by xmin^alpha)
                 zeta_pair(alpha, x, lnx[j], lnc, zb, za);
                 double d = fabs(at - (1.0 - za / Z));
