@@ -1830,6 +1830,7 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
     const uint32_t *vtiles = as<uint32_t>(ctx->tile_verts);
     BatchSchedule sch;
     CC_TRY(tune_batch(ctx, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, s, &sch));
+    S.sv_sample_stride = 1;  // the batched form has no SV front end
     S.batch_unroll = sch.unroll;
     S.batch_grid_mult = sch.grid_mult;
     {
