@@ -1,0 +1,97 @@
+"""The bench's roofline accounting (host logic, no GPU): algorithmic bytes and
+scattered L2 operations per kernel class, the ncu kernel-name classes, and
+the DRAM traffic summary built from an ncu CSV."""
+import csv
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _stats(n, m, **kw):
+    st = {"n": n, "m": m, "m_active": [m, m, 1000, 10], "sv_hooks": [0, 500, 40, 2], "bfs_edges_inspected": 0,
+          "sv_sample_stride": 1}
+    st.update(kw)
+    return st
+
+
+def test_degree_and_labels_bytes():
+    st = _stats(1 << 20, 1 << 24)
+    # read every pair (2 ids of w bytes), write n counters
+    assert bench.alg_bytes("degree", st, 4) == 2 * 4 * (1 << 24) + 4 * (1 << 20)
+    assert bench.alg_bytes("degree", st, 8) == 2 * 8 * (1 << 24) + 4 * (1 << 20)
+    # read the parents, write the labels of the id width
+    assert bench.alg_bytes("finalize", st, 8) == 4 * (1 << 20) + 8 * (1 << 20)
+    assert bench.l2_ops("degree", st) == (2.0 * (1 << 24), "red_add")
+
+
+def test_first_pass_variants():
+    n, m = 1 << 20, 1 << 24
+    # plain first pass with the pre-check read (2m/n = 32: hubs)
+    st = _stats(n, m)
+    assert bench.alg_bytes("sv_first", st, 4) == 2 * 4 * m + 4 * m
+    assert bench.l2_ops("sv_first", st) == (1.0 * m, "gather")
+    # sparse graph (2m/n < 4): an atomicMin per pair, no pre-check read
+    sp = _stats(m, m)
+    assert bench.l2_ops("sv_first", sp) == (1.0 * m, "red_min")
+    # the front end: two passes over one tile of pairs in 32
+    fe = _stats(n, m, sv_sample_stride=32)
+    assert bench.alg_bytes("sv_first", fe, 4) == pytest.approx((4 * 4 + 16) * m / 32)
+    assert bench.l2_ops("sv_first", fe) == (4.0 * m / 32, "gather")
+
+
+def test_gather_passes_count_survivors():
+    n, m = 1 << 20, 1 << 24
+    st = _stats(n, m)
+    kept = st["m_active"][2]
+    assert bench.alg_bytes("sv_gather_input", st, 4) == 2 * 4 * m + 8 * m + 12 * kept
+    assert bench.l2_ops("sv_gather_input", st) == (2.0 * m + kept, "gather")
+    # iterations over the list: 16 bytes read per active pair, 12 per survivor
+    assert bench.alg_bytes("sv_gather_list", st, 4) == 16 * 1000 + 12 * 10 + 16 * 10
+    assert bench.alg_bytes("sv_shortcut", st, 4) == 12 * sum(st["sv_hooks"])
+
+
+@pytest.mark.parametrize("name,cls", [
+    ("void ccg::k_degree_hubs<int, 24576, 1024, 1>(const T1 *, long long)", "degree"),
+    ("ccg::k_hub_select(const unsigned int *)", "degree"),
+    ("void ccg::k_degree<long>(const T1 *)", "degree"),
+    ("void ccg::k_sv_sample<int, 2>(const T1 *)", "sv_first"),
+    ("void ccg::k_sv_pass<int, 0, 0, 0>(const T1 *)", "sv_first"),
+    ("void ccg::k_sv_pass<long, 2, 1, 1>(const T1 *)", "sv_gather_input"),
+    ("void ccg::k_sv_pass<unsigned int, 2, 1, 1>(const T1 *)", "sv_gather_list"),
+    ("ccg::k_shortcut_all(unsigned int *)", "sv_shortcut"),
+    ("void ccg::k_finalize<int>(unsigned int *)", "finalize"),
+    ("ccg::k_ks_select(const unsigned int *)", "ks"),
+    ("void at::vectorized_elementwise_kernel<4>(int)", None),
+])
+def test_kernel_classes(name, cls):
+    assert bench.kernel_class(name) == cls
+
+
+def test_traffic_summary_per_call(tmp_path):
+    """Two calls captured: the class bytes are summed and divided by the calls
+    (the histogram kernel runs once per call)."""
+    rows = [["ID", "Kernel Name", "Metric Name", "Metric Value"]]
+    launches = [("ccg::k_hist(x)", 100, 20), ("void ccg::k_degree_hubs<int>(x)", 1000, 10),
+                ("ccg::k_hub_select(x)", 50, 0), ("ccg::k_hist(x)", 100, 20),
+                ("void ccg::k_degree_hubs<int>(x)", 1000, 10), ("ccg::k_hub_select(x)", 50, 0)]
+    for i, (name, rd, wr) in enumerate(launches):
+        rows.append([str(i), name, "dram__bytes_read.sum", str(rd)])
+        rows.append([str(i), name, "dram__bytes_write.sum", str(wr)])
+        rows.append([str(i), name, "gpu__time_duration.sum", "1000"])
+    p = tmp_path / "cap.csv"
+    with open(p, "w", newline="") as f:
+        f.write("==PROF== preamble line\n")
+        csv.writer(f, quoting=csv.QUOTE_ALL).writerows(rows)
+    out = bench.ncu_summary(str(p), "rmat22", {"rmat24": 4.0}, "cmd")
+    assert out["calls"] == 2
+    assert out["traffic_per_call"]["rmat22"]["degree"] == pytest.approx((1000 + 10 + 50) * 2 / 2)
+    assert out["traffic_per_call"]["rmat22"]["hist"] == pytest.approx(120.0)
+    assert out["traffic_per_call"]["rmat24"]["degree"] == pytest.approx(4 * 1060.0)
+    json.dumps(out)
