@@ -27,6 +27,14 @@ struct Buf {
 
 enum Ev { EV_START, EV_DEGREE, EV_PREDICT, EV_CSR, EV_BFS, EV_SV, EV_END, EV_COUNT };
 
+// Byte offsets in the context's small counters buffer.
+constexpr size_t kCtrBfs = 0;           // BFS visited counts (two 64-bit words)
+constexpr size_t kCtrSmallFitVo = 256;  // vertex offsets {0, n} of the one-graph fit (two int64)
+constexpr size_t kCtrKsQueue = 1024;    // next graph of the batched fits (int)
+constexpr size_t kCtrTileQueue = 1088;  // next tile of the batched degree pass (64-bit)
+constexpr size_t kCountersBytes = 4096;
+template <typename P> P *counter_at(Buf &b, size_t off) { return reinterpret_cast<P *>(static_cast<char *>(b.p) + off); }
+
 }  // namespace
 
 struct cc_ctx {
@@ -175,8 +183,8 @@ cc_status ensure_sv(cc_ctx *ctx, size_t n, size_t m) {
     CC_TRY(buf_reserve(ctx, ctx->chunk_nz, (size_t)(ks_num_chunks() + 1) * 8));
     CC_TRY(buf_reserve(ctx, ctx->chunk_mass, (size_t)(ks_num_chunks() + 1) * 8));
     CC_TRY(buf_reserve(ctx, ctx->st, sizeof(DevState)));
-    // BFS visited counts (words 0-1)
-    CC_TRY(buf_reserve(ctx, ctx->counters, 4096));
+    // small device counters (byte offsets kCtr*)
+    CC_TRY(buf_reserve(ctx, ctx->counters, kCountersBytes));
     CC_TRY(buf_reserve(ctx, ctx->bk_count, (size_t)ctx->grid * (bucket_max() + 2) * 4));
     CC_TRY(buf_reserve(ctx, ctx->bk_cursor, (size_t)ctx->grid * (bucket_max() + 2) * 4));
     CC_TRY(buf_reserve(ctx, ctx->bk_off, (size_t)(bucket_max() + 2) * 8));
@@ -565,7 +573,7 @@ cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStre
     CC_TRY(read_back(ctx, &st->front_edges[0], 8, s));
     fe = ctx->h_st->front_edges[0];
     int level = 0;
-    unsigned long long *cnt = as<unsigned long long>(ctx->counters);
+    unsigned long long *cnt = counter_at<unsigned long long>(ctx->counters, kCtrBfs);
     while (f > 0 && level < kMaxLevels - 1) {
         if (cutoff > 0 && level >= cutoff) break;
         const unsigned long long unexplored = total_edges > explored ? total_edges - explored : 0;
@@ -718,7 +726,7 @@ cc_status run_bfs_edges(cc_ctx *ctx, const void *edges, vid_t n, long long m, cu
     *levels_out = level;
     *list_buf = buf;
     *list_len = len;
-    unsigned long long *cnt = as<unsigned long long>(ctx->counters);
+    unsigned long long *cnt = counter_at<unsigned long long>(ctx->counters, kCtrBfs);
     cudaMemsetAsync(cnt + 1, 0, 8, s);
     Scope sc(ctx, CC_K_BFS_AUX, s, 2);
     launch_popcount(vis, nwords, cnt + 1, ctx->grid, s);
@@ -772,7 +780,7 @@ cc_status enqueue_small_fit(cc_ctx *ctx, vid_t n, cudaStream_t s) {
     KsBatchOut out{as<double>(ctx->kb_D),     as<double>(ctx->kb_alpha), as<long long>(ctx->kb_xmin),
                    as<long long>(ctx->kb_ntail), as<long long>(ctx->kb_ncand), as<int>(ctx->kb_route),
                    as<int>(ctx->kb_ovf),      as<unsigned long long>(ctx->kb_seed)};
-    int64_t *vo = reinterpret_cast<int64_t *>(static_cast<char *>(ctx->counters.p) + 256);
+    int64_t *vo = counter_at<int64_t>(ctx->counters, kCtrSmallFitVo);
     Scope sc2(ctx, CC_K_KS, s, 4);
     // the idle degree-histogram buffer (kHistDense words) holds the grid-wide histogram of the small graph
     launch_fit_one(as<uint32_t>(ctx->deg), n, vo, sc, out, as<DevState>(ctx->st), ctx->opt.ks_min_tail,
@@ -1066,7 +1074,8 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         rec(ctx, EV_BFS, s);
         CU_TRY(cudaMemcpyAsync(&ctx->h_st->cmin, &st->cmin, 4, cudaMemcpyDeviceToHost, s));
         unsigned long long visited = 0;
-        CU_TRY(cudaMemcpyAsync(&visited, as<unsigned long long>(ctx->counters) + 1, 8, cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaMemcpyAsync(&visited, counter_at<unsigned long long>(ctx->counters, kCtrBfs) + 1, 8,
+                               cudaMemcpyDeviceToHost, s));
         CU_TRY(cudaStreamSynchronize(s));
         const vid_t cmin = ctx->h_st->cmin;
         S.bfs_levels = levels;
@@ -1328,8 +1337,7 @@ cc_status labels_host_impl(cc_ctx *ctx, const void *edges_host, vid_t n, long lo
 // from 23.9 to 26.7 ms.
 constexpr bool kBatchTileQueue = true;
 unsigned long long *tile_queue(cc_ctx *ctx) {
-    return kBatchTileQueue ? reinterpret_cast<unsigned long long *>(static_cast<char *>(ctx->counters.p) + 1088)
-                           : nullptr;
+    return kBatchTileQueue ? counter_at<unsigned long long>(ctx->counters, kCtrTileQueue) : nullptr;
 }
 
 // Schedule tuner of the batched form. The hook passes over a batch map each
@@ -1443,7 +1451,7 @@ cc_status enqueue_ks_batch(cc_ctx *ctx, const int64_t *vo_dev, const int64_t *vo
     });
     // pageable source: the copy is staged before the call returns
     CU_TRY(cudaMemcpyAsync(ctx->kb_order.p, order.data(), (size_t)G * 4, cudaMemcpyHostToDevice, s));
-    int *next = reinterpret_cast<int *>(static_cast<char *>(ctx->counters.p) + 1024);
+    int *next = counter_at<int>(ctx->counters, kCtrKsQueue);
     KsBatchScratch sc{as<uint32_t>(ctx->kb_xs), as<unsigned long long>(ctx->kb_cnt), as<unsigned long long>(ctx->kb_cum),
                       as<double>(ctx->kb_lnx), as<double>(ctx->kb_Dc), as<double>(ctx->kb_Ac), as<double>(ctx->kb_Zc)};
     KsBatchOut out{as<double>(ctx->kb_D),     as<double>(ctx->kb_alpha), as<long long>(ctx->kb_xmin),
