@@ -49,32 +49,93 @@ def test_no_gpu_calls_fail_cleanly():
     assert "outside" in cc.strerror(2)
 
 
-def test_ctypes_structs_match_the_header(tmp_path):
-    """The binding's ctypes structs have the C structs' sizes and field offsets
-    (a C program compiled against the header prints them)."""
+def _run_c(tmp_path, body: list[str]) -> dict:
+    """Compile a C program against the header and return its "key value" lines."""
     import shutil
 
     if not shutil.which("gcc"):
         pytest.skip("no C compiler")
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "cc_gb300.h"', "int main(void) {"]
+    src += body + ["return 0; }"]
+    c = tmp_path / "probe.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    return dict(line.split() for line in out.splitlines())
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """Every field of the binding's ctypes structs sits at the C struct's
+    offset with the C field's size, and the structs have the C sizes."""
     import paper_1607_06156_gb300 as cc
 
-    checks = {"cc_options": (cc.Options, ["ks_tau", "ks_min_span", "profile", "bfs_mode"]),
-              "cc_stats": (cc.Stats, ["ks_d", "m_active", "ms_degree", "launches", "kernel_ms", "sv_hooks",
-                                      "ms_features", "batch_unroll", "batch_grid_mult"]),
-              "cc_l2_rates": (cc.L2Rates, ["gather", "atom_min", "table_words", "grid"])}
-    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "cc_gb300.h"', "int main(void) {"]
-    for name, (_, fields) in checks.items():
-        src.append(f'printf("{name} %zu\\n", sizeof({name}));')
-        for f in fields:
-            src.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
-    src.append("return 0; }")
-    c = tmp_path / "sizes.c"
-    c.write_text("\n".join(src))
-    exe = tmp_path / "sizes"
-    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
-    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
-                                                       check=True).stdout.splitlines())
-    for name, (cls, fields) in checks.items():
+    structs = {"cc_options": cc.Options, "cc_stats": cc.Stats, "cc_l2_rates": cc.L2Rates}
+    body = []
+    for name, cls in structs.items():
+        body.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            body.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+            body.append(f'printf("{name}.{f}.size %zu\\n", sizeof((({name} *)0)->{f}));')
+    got = _run_c(tmp_path, body)
+    for name, cls in structs.items():
         assert int(got[name]) == ctypes.sizeof(cls), name
-        for f in fields:
-            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
+        for f, _ in cls._fields_:
+            field = getattr(cls, f)
+            assert int(got[f"{name}.{f}"]) == field.offset, (name, f)
+            assert int(got[f"{name}.{f}.size"]) == field.size, (name, f)
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Status codes, route policies, fault bits, array bounds, the kernel-class
+    order and the network sizes the binding mirrors are the header's."""
+    import paper_1607_06156_gb300 as cc
+
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    kclasses = re.findall(r"\bCC_K_(\w+)\s*=\s*(\d+)", text)
+    order = [name.lower() for name, v in sorted(kclasses, key=lambda t: int(t[1])) if name != "COUNT"]
+    assert order == cc.KERNELS
+    consts = {"CC_K_COUNT": cc.K_COUNT, "CC_MAX_SV_ITERS_RECORDED": cc.MAX_SV_ITERS_RECORDED,
+              "CC_MLP_IN": cc.MLP_IN, "CC_MLP_HIDDEN": cc.MLP_HIDDEN, "CC_MLP_OUT": cc.MLP_OUT,
+              "CC_MLP_PARAMS": cc.MLP_PARAMS, "CC_FAULT_ALLOC": cc.FAULT_ALLOC,
+              "CC_FAULT_ITER_CAP": cc.FAULT_ITER_CAP, "CC_ROUTE_AUTO": cc.ROUTES["auto"],
+              "CC_ROUTE_LEARNED": cc.ROUTES["learned"], "CC_ROUTE_FORCE_BFS": cc.ROUTES["bfs"],
+              "CC_ROUTE_FORCE_SV": cc.ROUTES["sv"]}
+    consts.update({name: code for code, name in cc.STATUS.items()})
+    got = _run_c(tmp_path, [f'printf("{k} %lld\\n", (long long)({k}));' for k in consts])
+    for k, v in consts.items():
+        assert int(got[k]) == v, k
+
+
+def _prototypes():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    pat = r"^\s*((?:const\s+)?[A-Za-z_]\w*\s*\**)\s*(cc_\w+)\s*\(([^)]*)\)\s*;"
+    return {m.group(2): (m.group(1).strip(), [p.strip() for p in m.group(3).split(",") if p.strip()])
+            for m in re.finditer(pat, text, flags=re.M)}
+
+
+def test_binding_argtypes_match_the_prototypes():
+    """Each function's ctypes argtypes have the header prototype's arity and,
+    parameter by parameter, the same kind (pointer, 32- or 64-bit integer,
+    float, double); cc_status returns are read as int."""
+    import paper_1607_06156_gb300 as cc
+
+    L = cc.lib()
+    scalar = {"int": ctypes.c_int, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "float": ctypes.c_float,
+              "double": ctypes.c_double, "cc_status": ctypes.c_int}
+    protos = _prototypes()
+    assert set(protos) == set(declared_functions())
+    for name, (ret, params) in protos.items():
+        fn = getattr(L, name)
+        assert len(fn.argtypes) == len(params), name
+        for p, at in zip(params, fn.argtypes):
+            if "*" in p:
+                assert at is ctypes.c_void_p or issubclass(at, ctypes._Pointer), (name, p)
+            else:
+                ctype = p.rsplit(None, 1)[0]
+                assert ctypes.sizeof(at) == ctypes.sizeof(scalar[ctype]), (name, p)
+                assert (at in (ctypes.c_float, ctypes.c_double)) == (ctype in ("float", "double")), (name, p)
+        if ret == "cc_status":
+            assert fn.restype is ctypes.c_int, name
+        else:
+            assert ret.endswith("*") and fn.restype is ctypes.c_char_p, name
