@@ -139,3 +139,51 @@ def test_binding_argtypes_match_the_prototypes():
             assert fn.restype is ctypes.c_int, name
         else:
             assert ret.endswith("*") and fn.restype is ctypes.c_char_p, name
+
+
+def test_argument_errors_return_before_any_device_call():
+    """The boundary's argument checks run on the host before any CUDA call:
+    a null context, negative sizes, ids past the limits, missing pointers and
+    bad options each give their status with no device present."""
+    import paper_1607_06156_gb300 as cc
+
+    L = cc.lib()
+    ARG, EDGE, UNSUP = 1, 2, 7
+    v = ctypes.c_void_p
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.cast(buf, v)
+    assert L.cc_default_options(None) == ARG
+    assert L.cc_create(None, None, 0) == ARG
+    o = cc.default_options()
+    for field, bad in (("id_bytes", 3), ("ks_tau", -1.0), ("route_policy", 9)):
+        o2 = cc.default_options()
+        setattr(o2, field, bad)
+        out = v()
+        assert L.cc_create(ctypes.byref(out), ctypes.byref(o2), 0) == ARG, field
+        assert not out.value
+    assert L.cc_set_options(None, ctypes.byref(o)) == ARG
+    assert L.cc_destroy(None) == 0
+    assert L.cc_get_stats(None, ctypes.byref(cc.Stats())) == ARG
+    for f in (L.cc_labels, L.cc_labels_host, L.cc_labels_tuple_sv):
+        assert f(None, p, 10, 5, p, None) == ARG
+    assert L.cc_labels_batched(None, p, p, p, p, p, 1, p, None) == ARG
+    assert L.cc_ks_statistic_batched(None, p, p, p, p, p, 1, p, p, p, p, p, p, None) == ARG
+    assert L.cc_degree_distribution(None, p, 10, 5, p, p, 4, None) == ARG
+    assert L.cc_ks_statistic(None, p, 4, p, None) == ARG
+    assert L.cc_route_features(None, p, 10, 5, p, None) == ARG
+    assert L.cc_set_predictor(None, p, 0.5) == ARG
+    assert L.cc_measure_l2_rates(None, None, None) == ARG
+    # the library-owned scratch entry point needs no context
+    assert L.cc_labels_static(p, 3, 10, 5, p, None) == ARG
+    assert L.cc_labels_static(p, 4, -1, 5, p, None) == ARG
+    assert L.cc_labels_static(p, 4, 0, 0, p, None) == 0
+    assert L.cc_labels_static(p, 4, 0, 1, p, None) == EDGE
+    assert L.cc_labels_static(p, 4, (1 << 20) + 1, 5, p, None) == UNSUP
+    assert L.cc_labels_static(p, 4, 10, (1 << 21) + 1, p, None) == UNSUP
+    assert L.cc_labels_static(None, 4, 10, 5, p, None) == ARG
+    assert L.cc_mlp_forward(None, p, 4, p, None) == ARG
+    assert L.cc_mlp_forward(p, p, 0, p, None) == ARG
+    assert L.cc_mlp_backward(p, p, p, p, p, 4, ctypes.c_float(0.1), p, p, p, None, None) == ARG
+    assert L.cc_mlp_adam(p, p, p, p, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == ARG
+    for s in range(8):
+        assert cc.strerror(s)
