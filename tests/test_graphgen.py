@@ -55,3 +55,20 @@ def test_batch_offsets_and_local_ids():
         if g % 3 == 0:
             assert gr.m == 8 * gr.n
 
+
+
+def test_batch4096_sizes_follow_the_workload():
+    """The 4,096-graph batch: vertex counts log-uniform in [1K, 1M] (each
+    decade holds about a third of the graphs), R-MAT every third graph with
+    8 pairs per vertex, and the same sizes whichever graphs are kept."""
+    ng, mg = gg.batch_sizes(seed=1, G=4096)
+    assert ng.size == mg.size == 4096
+    assert ng.min() >= 1000 and ng.max() <= 1_000_000
+    dec = np.bincount(np.minimum((np.log10(ng) - 3).astype(int), 2), minlength=3) / 4096
+    assert np.all(np.abs(dec - 1 / 3) < 0.04)
+    assert np.array_equal(mg[0::3], 8 * ng[0::3])
+    assert (mg > 0).all()
+    sub = gg.batch(seed=1, G=30, nmin=1000, nmax=5000, graphs=[29, 3, 17])
+    n30, m30 = gg.batch_sizes(seed=1, G=30, nmin=1000, nmax=5000)
+    assert np.diff(sub.vertex_offsets).tolist() == n30[[29, 3, 17]].tolist()
+    assert np.diff(sub.edge_offsets).tolist() == m30[[29, 3, 17]].tolist()
