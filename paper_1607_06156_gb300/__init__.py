@@ -49,6 +49,9 @@ class Options(ctypes.Structure):
     ]
 
 
+_OPTION_FIELDS = frozenset(f for f, _ in Options._fields_ if f != "reserved")
+
+
 class Stats(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int), ("route", ctypes.c_int), ("route_source", ctypes.c_int),
@@ -150,6 +153,15 @@ def _stream_handle(stream, device) -> int:
     return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
 
 
+def _set_options(o: Options, opts: dict) -> None:
+    """Copy keyword options into a cc_options; a name that is not a field
+    raises instead of landing on a Python attribute the library never sees."""
+    for k, v in opts.items():
+        if k not in _OPTION_FIELDS:
+            raise TypeError(f"unknown option {k!r} (cc_options fields: {', '.join(sorted(_OPTION_FIELDS))})")
+        setattr(o, k, v)
+
+
 class Engine:
     """One cc_ctx: a device workspace plus options (Algorithm 2 route policy)."""
 
@@ -157,8 +169,7 @@ class Engine:
         o = default_options()
         o.id_bytes = id_bytes
         o.route_policy = ROUTES[route]
-        for k, v in opts.items():
-            setattr(o, k, v)
+        _set_options(o, opts)
         self.device = device
         self._opt = o
         h = _vp()
@@ -169,8 +180,7 @@ class Engine:
         o = self._opt
         if route is not None:
             o.route_policy = ROUTES[route]
-        for k, v in opts.items():
-            setattr(o, k, v)
+        _set_options(o, opts)
         _check(lib().cc_set_options(self._h, ctypes.byref(o)), "cc_set_options")
 
     @property

@@ -187,3 +187,17 @@ def test_argument_errors_return_before_any_device_call():
     assert L.cc_mlp_adam(p, p, p, p, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == ARG
     for s in range(8):
         assert cc.strerror(s)
+
+
+def test_unknown_option_names_are_refused():
+    """A misspelt option raises before the context is created instead of
+    being dropped silently."""
+    import paper_1607_06156_gb300 as cc
+
+    with pytest.raises(TypeError, match="profle"):
+        cc.Engine(profle=1)
+    o = cc.default_options()
+    cc._set_options(o, {"profile": 1, "sv_sample_stride": 8})
+    assert o.profile == 1 and o.sv_sample_stride == 8
+    with pytest.raises(TypeError):
+        cc._set_options(o, {"reserved": 0})
