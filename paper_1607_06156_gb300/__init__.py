@@ -153,6 +153,48 @@ def _stream_handle(stream, device) -> int:
     return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
 
 
+def _device_tensor(t, name: str, itemsize: int, floating: bool = False, numel: int = 0, device=None) -> None:
+    """What the library cannot see behind a pointer: a contiguous CUDA tensor
+    of the right element width and kind, holding at least `numel` elements,
+    on the engine's device. A mismatch raises ValueError before the call
+    instead of letting a kernel read or write past the tensor."""
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (it is on {t.device})")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on {t.device}, the engine on cuda:{device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.element_size() != itemsize or t.dtype.is_floating_point != floating or t.dtype.is_complex:
+        kind = "floating-point" if floating else "integer"
+        raise ValueError(f"{name} must hold {itemsize}-byte {kind} elements (it holds {t.dtype})")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, {numel} are needed")
+
+
+def _pairs(edges, itemsize: int, device=None) -> int:
+    """m of a device [m, 2] pair tensor, checked as above."""
+    _device_tensor(edges, "edges", itemsize, device=device)
+    if edges.numel() == 0:
+        return 0
+    if edges.dim() != 2 or edges.shape[1] != 2:
+        raise ValueError(f"edges must have shape [m, 2] (it has {tuple(edges.shape)})")
+    return edges.shape[0]
+
+
+def _offsets(edge_offsets, vertex_offsets, m: int):
+    """Host int64 copies of a batch's offsets ([G + 1] each); the last edge
+    offset may not pass the pairs the edge tensor holds."""
+    import torch
+
+    eo = torch.as_tensor(edge_offsets).cpu().to(torch.int64).contiguous()
+    vo = torch.as_tensor(vertex_offsets).cpu().to(torch.int64).contiguous()
+    if eo.dim() != 1 or vo.dim() != 1 or eo.numel() < 1 or eo.numel() != vo.numel():
+        raise ValueError("edge_offsets and vertex_offsets must be 1-D with G + 1 entries each")
+    if int(eo[-1]) > m:
+        raise ValueError(f"edge_offsets end at pair {int(eo[-1])}, the edges hold {m} pairs")
+    return eo, vo
+
+
 def _set_options(o: Options, opts: dict) -> None:
     """Copy keyword options into a cc_options; a name that is not a field
     raises instead of landing on a Python attribute the library never sees."""
@@ -207,13 +249,10 @@ class Engine:
         """Component labels (min vertex id per component) of a device edge tensor [m, 2]."""
         import torch
 
-        if edges.dtype.itemsize != self._opt.id_bytes:
-            raise ValueError(f"edges dtype {edges.dtype} does not match id_bytes={self._opt.id_bytes}")
-        if not edges.is_contiguous():
-            raise ValueError("edges must be contiguous")
-        m = edges.shape[0] if edges.numel() else 0
+        m = _pairs(edges, self._opt.id_bytes, self.device)
         if out is None:
             out = torch.empty(n, dtype=edges.dtype, device=edges.device)
+        _device_tensor(out, "out", self._opt.id_bytes, numel=n, device=self.device)
         rc = lib().cc_labels(self._h, edges.data_ptr() if m else None, n, m, out.data_ptr() if n else None,
                              _stream_handle(stream, edges.device))
         _check(rc, "cc_labels")
@@ -224,13 +263,10 @@ class Engine:
         (cc_labels_tuple_sv): the same labels as `labels`, for comparison."""
         import torch
 
-        if edges.dtype.itemsize != self._opt.id_bytes:
-            raise ValueError(f"edges dtype {edges.dtype} does not match id_bytes={self._opt.id_bytes}")
-        if not edges.is_contiguous():
-            raise ValueError("edges must be contiguous")
-        m = edges.shape[0] if edges.numel() else 0
+        m = _pairs(edges, self._opt.id_bytes, self.device)
         if out is None:
             out = torch.empty(n, dtype=edges.dtype, device=edges.device)
+        _device_tensor(out, "out", self._opt.id_bytes, numel=n, device=self.device)
         rc = lib().cc_labels_tuple_sv(self._h, edges.data_ptr() if m else None, n, m,
                                       out.data_ptr() if n else None, _stream_handle(stream, edges.device))
         _check(rc, "cc_labels_tuple_sv")
@@ -243,6 +279,10 @@ class Engine:
 
         if edges.device.type != "cpu" or not edges.is_contiguous():
             raise ValueError("edges must be a contiguous CPU tensor")
+        if edges.element_size() != self._opt.id_bytes or edges.dtype.is_floating_point or edges.dtype.is_complex:
+            raise ValueError(f"edges must hold {self._opt.id_bytes}-byte integer ids (it holds {edges.dtype})")
+        if edges.numel() and (edges.dim() != 2 or edges.shape[1] != 2):
+            raise ValueError(f"edges must have shape [m, 2] (it has {tuple(edges.shape)})")
         m = edges.shape[0] if edges.numel() else 0
         dt = torch.int32 if self._opt.id_bytes == 4 else torch.int64
         if out is None:
@@ -258,13 +298,13 @@ class Engine:
         """Local labels of G independent graphs (int32 ids local to each graph)."""
         import torch
 
-        eo_h = edge_offsets.cpu().contiguous()
-        vo_h = vertex_offsets.cpu().contiguous()
-        eo_d = eo_h.to(edges.device)
-        vo_d = vo_h.to(edges.device)
+        eo_h, vo_h = _offsets(edge_offsets, vertex_offsets, _pairs(edges, 4, self.device))
         G = eo_h.numel() - 1
         if out is None:
             out = torch.empty(int(vo_h[-1]), dtype=torch.int32, device=edges.device)
+        _device_tensor(out, "out", 4, numel=int(vo_h[-1]), device=self.device)
+        eo_d = eo_h.to(edges.device)
+        vo_d = vo_h.to(edges.device)
         rc = lib().cc_labels_batched(self._h, edges.data_ptr() if edges.numel() else None, eo_d.data_ptr(),
                                      vo_d.data_ptr(), eo_h.data_ptr(), vo_h.data_ptr(), G,
                                      out.data_ptr() if out.numel() else None, _stream_handle(stream, edges.device))
@@ -277,13 +317,13 @@ class Engine:
         import numpy as np
         import torch
 
-        eo = torch.as_tensor(np.ascontiguousarray(edge_offsets, dtype=np.int64))
-        vo = torch.as_tensor(np.ascontiguousarray(vertex_offsets, dtype=np.int64))
+        m = _pairs(edges, 4, self.device)
+        eo, vo = _offsets(np.ascontiguousarray(edge_offsets, dtype=np.int64),
+                          np.ascontiguousarray(vertex_offsets, dtype=np.int64), m)
         G = eo.numel() - 1
         eo_d, vo_d = eo.to(edges.device), vo.to(edges.device)
         out = {k: np.zeros(G, dtype=dt) for k, dt in (("D", np.float64), ("alpha", np.float64), ("xmin", np.int64),
                                                      ("ncand", np.int64), ("route", np.int32), ("seed", np.int64))}
-        m = edges.shape[0] if edges.numel() else 0
         ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         rc = lib().cc_ks_statistic_batched(self._h, edges.data_ptr() if m else None, eo_d.data_ptr(), vo_d.data_ptr(),
                                            eo.data_ptr(), vo.data_ptr(), G, ptr(out["D"]), ptr(out["alpha"]),
@@ -293,8 +333,18 @@ class Engine:
         return out
 
     def labels_batched_dev(self, edges, eo_dev, vo_dev, eo_host, vo_host, out, stream=None):
-        """cc_labels_batched with offsets already on the device and on the host (no copies)."""
+        """cc_labels_batched with offsets already on the device and on the host (no copies).
+        The device offsets must hold the same values as the host ones."""
+        m = _pairs(edges, 4, self.device)
+        if eo_host.is_cuda or vo_host.is_cuda or eo_host.element_size() != 8 or vo_host.element_size() != 8 \
+                or not (eo_host.is_contiguous() and vo_host.is_contiguous()):
+            raise ValueError("eo_host and vo_host must be contiguous int64 CPU tensors")
         G = eo_host.numel() - 1
+        if G < 0 or vo_host.numel() != G + 1 or int(eo_host[-1]) > m:
+            raise ValueError("eo_host and vo_host must hold G + 1 offsets, the last edge offset within the edges")
+        _device_tensor(eo_dev, "eo_dev", 8, numel=G + 1, device=self.device)
+        _device_tensor(vo_dev, "vo_dev", 8, numel=G + 1, device=self.device)
+        _device_tensor(out, "out", 4, numel=int(vo_host[-1]), device=self.device)
         rc = lib().cc_labels_batched(self._h, edges.data_ptr() if edges.numel() else None, eo_dev.data_ptr(),
                                      vo_dev.data_ptr(), eo_host.data_ptr(), vo_host.data_ptr(), G,
                                      out.data_ptr() if out.numel() else None, _stream_handle(stream, edges.device))
@@ -305,7 +355,7 @@ class Engine:
         """(deg[n] uint32 as int32 tensor, hist[hist_len] uint64 as int64 tensor or None)."""
         import torch
 
-        m = edges.shape[0] if edges.numel() else 0
+        m = _pairs(edges, self._opt.id_bytes, self.device)
         deg = torch.empty(n, dtype=torch.int32, device=edges.device)
         hist = torch.empty(hist_len, dtype=torch.int64, device=edges.device) if hist_len > 0 else None
         rc = lib().cc_degree_distribution(self._h, edges.data_ptr() if m else None, n, m,
@@ -316,6 +366,7 @@ class Engine:
 
     def ks_statistic(self, hist, stream=None) -> dict:
         """Power-law fit + K-S statistic of a device uint64 (int64 tensor) degree histogram."""
+        _device_tensor(hist, "hist", 8, numel=1, device=self.device)
         out = (ctypes.c_double * 5)()
         rc = lib().cc_ks_statistic(self._h, hist.data_ptr(), hist.numel(), out, _stream_handle(stream, hist.device))
         _check(rc, "cc_ks_statistic")
@@ -325,7 +376,7 @@ class Engine:
         """The predictor's CC_MLP_IN features of a device edge tensor (float32 tensor on its device)."""
         import torch
 
-        m = edges.shape[0] if edges.numel() else 0
+        m = _pairs(edges, self._opt.id_bytes, self.device)
         x = torch.empty(MLP_IN, dtype=torch.float32, device=edges.device)
         rc = lib().cc_route_features(self._h, edges.data_ptr() if m else None, n, m, x.data_ptr(),
                                      _stream_handle(stream, edges.device))
@@ -358,14 +409,31 @@ class Engine:
         return s.as_dict()
 
 
+def _mlp_batch(params, X) -> int:
+    """B of a [B, MLP_IN] float32 feature tensor, with the flat parameters checked."""
+    _device_tensor(params, "params", 4, floating=True, numel=MLP_PARAMS)
+    _device_tensor(X, "X", 4, floating=True, device=params.device.index)
+    if X.dim() != 2 or X.shape[1] != MLP_IN:
+        raise ValueError(f"X must have shape [B, {MLP_IN}] (it has {tuple(X.shape)})")
+    return X.shape[0]
+
+
 def mlp_forward(params, X, act, stream=None):
     """cc_mlp_forward on device float32 tensors; act holds B * (2*128 + 3) floats."""
+    B = _mlp_batch(params, X)
+    _device_tensor(act, "act", 4, floating=True, numel=B * (2 * MLP_HIDDEN + MLP_OUT), device=X.device.index)
     _check(lib().cc_mlp_forward(params.data_ptr(), X.data_ptr(), X.shape[0], act.data_ptr(),
                                 _stream_handle(stream, X.device)), "cc_mlp_forward")
 
 
 def mlp_backward(params, X, y, t, w, lam, act, grad, scratch, loss, stream=None):
     """cc_mlp_backward on device tensors (y int32, others float32); adds the batch loss into loss[0]."""
+    B = _mlp_batch(params, X)
+    d = X.device.index
+    _device_tensor(y, "y", 4, numel=B, device=d)
+    for name, t_, k in (("t", t, B), ("w", w, B), ("act", act, B * (2 * MLP_HIDDEN + MLP_OUT)),
+                        ("grad", grad, MLP_PARAMS), ("scratch", scratch, B * (3 + 2 * MLP_HIDDEN)), ("loss", loss, 1)):
+        _device_tensor(t_, name, 4, floating=True, numel=k, device=d)
     _check(lib().cc_mlp_backward(params.data_ptr(), X.data_ptr(), y.data_ptr(), t.data_ptr(), w.data_ptr(),
                                  X.shape[0], lam, act.data_ptr(), grad.data_ptr(), scratch.data_ptr(),
                                  loss.data_ptr(), _stream_handle(stream, X.device)), "cc_mlp_backward")
@@ -373,6 +441,9 @@ def mlp_backward(params, X, y, t, w, lam, act, grad, scratch, loss, stream=None)
 
 def mlp_adam(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     """cc_mlp_adam on device float32 tensors (step >= 1)."""
+    d = params.device.index
+    for name, t_ in (("params", params), ("grad", grad), ("m", m), ("v", v)):
+        _device_tensor(t_, name, 4, floating=True, numel=params.numel(), device=d)
     _check(lib().cc_mlp_adam(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), params.numel(), lr,
                              beta1, beta2, eps, step, _stream_handle(stream, params.device)), "cc_mlp_adam")
 
@@ -385,9 +456,10 @@ def labels_static(edges, n: int, out=None, stream=None):
     """cc_labels_static: labels with the library's built-in scratch (no device allocation by the library)."""
     import torch
 
-    m = edges.shape[0] if edges.numel() else 0
+    m = _pairs(edges, edges.element_size())
     if out is None:
         out = torch.empty(n, dtype=edges.dtype, device=edges.device)
+    _device_tensor(out, "out", edges.element_size(), numel=n, device=edges.device.index)
     rc = lib().cc_labels_static(edges.data_ptr() if m else None, edges.element_size(), n, m,
                                 out.data_ptr() if n else None, _stream_handle(stream, edges.device))
     _check(rc, "cc_labels_static")

@@ -107,9 +107,12 @@ def test_invalid_id_and_size_limits():
     assert ei.value.status == 2  # CC_ERR_INVALID_EDGE
     eng = cc.Engine()
     e = torch.zeros((1, 2), dtype=torch.int32, device="cuda")
-    with pytest.raises(cc.CCError) as ei:
-        eng.labels_tuple_sv(e, 1 << 31, out=torch.empty(1, dtype=torch.int32, device="cuda"))
-    assert ei.value.status == 7  # CC_ERR_UNSUPPORTED
+    small = torch.empty(1, dtype=torch.int32, device="cuda")
+    # the C boundary refuses n >= 2^31 before it touches the output
+    assert cc.lib().cc_labels_tuple_sv(eng._h, e.data_ptr(), 1 << 31, 1, small.data_ptr(), 0) == 7  # UNSUPPORTED
+    # the binding refuses an output shorter than n before the call
+    with pytest.raises(ValueError):
+        eng.labels_tuple_sv(e, 1 << 31, out=small)
     eng.close()
 
 
