@@ -29,6 +29,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -165,13 +166,24 @@ def ncu_traffic(kernel_cls: str, workload: str):
 
 
 def kernel_class(name: str):
-    """Kernel class (the engine's profiling scopes) of a kernel name in an ncu list."""
+    """Kernel class (the engine's profiling scopes) of a kernel name in an ncu list.
+
+    An SV pass is classed by its id type and mode: modes 0, 4 (the first pass
+    over the caller's pairs, with or without the pre-check) and 1 (the first
+    pass after the BFS, over the pairs or the list) are the first pass; mode 2
+    is a gather pass, over the caller's pairs (int / long ids) or over the
+    compacted list (unsigned int); mode 3 belongs to the host-input chunks."""
+    sv = re.search(r"k_sv_pass<(int|long|unsigned int), (\d)", name)
+    if sv:
+        ids, mode = sv.group(1), int(sv.group(2))
+        if mode in (0, 1, 4):
+            return "sv_first"
+        if mode == 2:
+            return "sv_gather_list" if ids == "unsigned int" else "sv_gather_input"
+        return None
     table = [("k_degree_hubs", "degree"), ("k_hub_", "degree"), ("k_degree<", "degree"), ("k_hist", "hist"),
-             ("k_distinct", "ks"), ("k_ks_", "ks"), ("k_parent_init", "parent_init"),
-             ("k_sv_pass<int, 0", "sv_first"), ("k_sv_pass<long, 0", "sv_first"), ("k_sv_sample", "sv_first"),
-             ("k_sv_pass<int, 2", "sv_gather_input"), ("k_sv_pass<long, 2", "sv_gather_input"),
-             ("k_sv_pass<unsigned int, 2", "sv_gather_list"), ("k_shortcut_all", "sv_shortcut"),
-             ("k_sv_shortcut", "sv_shortcut"), ("k_finalize", "finalize")]
+             ("k_distinct", "ks"), ("k_ks_", "ks"), ("k_parent_init", "parent_init"), ("k_sv_sample", "sv_first"),
+             ("k_shortcut_all", "sv_shortcut"), ("k_sv_shortcut", "sv_shortcut"), ("k_finalize", "finalize")]
     for key, cls in table:
         if key in name:
             return cls

@@ -65,6 +65,12 @@ def test_gather_passes_count_survivors():
     ("void ccg::k_sv_pass<int, 0, 0, 0>(const T1 *)", "sv_first"),
     ("void ccg::k_sv_pass<long, 2, 1, 1>(const T1 *)", "sv_gather_input"),
     ("void ccg::k_sv_pass<unsigned int, 2, 1, 1>(const T1 *)", "sv_gather_list"),
+    ("void ccg::k_sv_pass<long, 4, 0, 0>(const T1 *)", "sv_first"),
+    ("void ccg::k_sv_pass<int, 1, 1, 1>(const T1 *)", "sv_first"),
+    ("void ccg::k_sv_pass<unsigned int, 1, 1, 1>(const T1 *)", "sv_first"),
+    ("void ccg::k_sv_pass<int, 3, 1, 1>(const T1 *)", None),
+    ("void ccg::k_sv_pass_batch<0>(const int *)", None),
+    ("void ccg::k_finalize_batch(unsigned int *)", "finalize"),
     ("ccg::k_shortcut_all(unsigned int *)", "sv_shortcut"),
     ("void ccg::k_finalize<int>(unsigned int *)", "finalize"),
     ("ccg::k_ks_select(const unsigned int *)", "ks"),
