@@ -94,16 +94,6 @@ def adam_step(p: dict, g: dict, state: dict, lr: float = 1e-3, b1: float = 0.9, 
         p[k] -= lr * mh / (np.sqrt(vh) + eps)
 
 
-def predict(p: dict, X: np.ndarray) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
-    """(route 0/1, probability of the chosen route, log cutoff) for inputs X."""
-    o = forward(p, X)["o"]
-    logits = o[:, :2]
-    e = np.exp(logits - logits.max(axis=1, keepdims=True))
-    sm = e / e.sum(axis=1, keepdims=True)
-    r = sm.argmax(axis=1)
-    return r, sm[np.arange(len(r)), r], o[:, 2]
-
-
 def route_features(edges: np.ndarray, n: int) -> np.ndarray:
     """The predictor's 69 input features, by their plain definition.
 
