@@ -350,23 +350,29 @@ cc_status cc_labels_static(const void *edges_dev, int id_bytes, int64_t n, int64
 
 /*
  * The paper's own SV design on the GPU, for comparison with cc_labels
- * (Section 3.1, Algorithm 1): the tuple array A_0 (<x,_,x> per vertex,
- * <u,_,v> and <v,_,u> per pair), grouped by radix sorts. Each iteration runs
- * the vertex pass (sort by vertex, q = min partition of the vertex's bucket)
- * and the partition pass (sort by partition, every partition moves to the
- * minimum candidate of its bucket), then both again with one temporary tuple
- * <p_min,_,p_min> per partition (the pointer doubling of Fig. 3), and erases
- * the temporaries. It stops when no partition changed; a vertex's label is
- * then its partition, the minimum id of its component - the labels of
- * cc_labels. No route prediction, BFS or exclusion of finished partitions.
+ * (Section 3.1): the bag of tuples of Section 3.1.1 (one (x, x) per vertex,
+ * (u, v) and (v, u) per pair; a tuple holds a partition and a vertex),
+ * grouped by radix sorts. Every iteration runs two join rounds: grouped by
+ * vertex, each vertex nominates the smallest partition among its tuples;
+ * grouped by partition, each partition moves to the smallest nomination of
+ * its tuples. The second round carries one extra tuple (t, t) per target t
+ * of the first, which moves t on as well (the pointer doubling of Fig. 3).
+ * Completed partitions (Section 3.1.4: every vertex of the partition has
+ * tuples of that partition only) are detected in the first round; their
+ * labels are written and their tuples leave the working set after the
+ * iteration. The run stops after the first iteration in which no partition
+ * moved; a vertex's label is then its partition, the minimum id of its
+ * component - the labels of cc_labels. No route prediction or BFS.
  *   edges_dev      [m][2] pairs of the context's id width, device
  *   n              vertices, n < 2^31 (else CC_ERR_UNSUPPORTED)
  *   labels_out_dev [n] ids of the context's id width, device
  *   stream         cudaStream_t as void*; the call synchronises it once per
  *                  iteration and returns with the labels complete
- * cc_get_stats reports the iterations (sv_iters) and the time (ms_sv,
- * ms_total). The context keeps a workspace of 44 bytes per tuple slot
- * (2n + 2m slots: the n + 2m tuples and up to n temporaries) until cc_destroy.
+ * cc_get_stats reports the iterations (sv_iters), the tuples in the working
+ * set entering each iteration (m_active[i - 1] for iteration i) and the time
+ * (ms_sv, ms_total). The context keeps a workspace of 52 bytes per tuple
+ * slot (2n + 2m slots: the n + 2m tuples and up to n extras) until
+ * cc_destroy.
  * Errors: as cc_labels; CC_ERR_NO_CONVERGENCE past the iteration cap.
  */
 cc_status cc_labels_tuple_sv(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, void *labels_out_dev,

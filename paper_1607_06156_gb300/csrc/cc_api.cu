@@ -45,7 +45,8 @@ struct cc_ctx {
     // SV / degree workspace
     size_t n_cap = 0, m_cap = 0;
     // workspace of cc_labels_tuple_sv (the sort-based SV of Algorithm 1)
-    Buf tsv_t32[4], tsv_v0, tsv_v1, tsv_val, tsv_uniq, tsv_agg, tsv_dense, tsv_temp, tsv_cnt;
+    Buf tsv_t32[4], tsv_v0, tsv_v1, tsv_val, tsv_val2, tsv_uniq, tsv_agg, tsv_dense, tsv_pc, tsv_done, tsv_temp,
+        tsv_cnt;
     long long tsv_cap = 0;
     Buf deg, parent, hooked, ebuf0, ebuf1, hist, ovf, ks_xs, ks_cnt, ks_cum, ks_lnx, ks_Dc, ks_Ac, ks_Zc, ks_Df, chunk_nz,
         chunk_mass, st, bk_count, bk_off, bk_cursor;
@@ -1593,8 +1594,8 @@ cc_status cc_destroy(cc_ctx *ctx) {
     buf_free(ctx->tile_pairs);
     buf_free(ctx->tile_verts);
     for (Buf &b : ctx->tsv_t32) buf_free(b);
-    Buf *tsv[] = {&ctx->tsv_v0,  &ctx->tsv_v1,    &ctx->tsv_val,  &ctx->tsv_uniq,
-                  &ctx->tsv_agg, &ctx->tsv_dense, &ctx->tsv_temp, &ctx->tsv_cnt};
+    Buf *tsv[] = {&ctx->tsv_v0,    &ctx->tsv_v1, &ctx->tsv_val,  &ctx->tsv_val2, &ctx->tsv_uniq, &ctx->tsv_agg,
+                  &ctx->tsv_dense, &ctx->tsv_pc, &ctx->tsv_done, &ctx->tsv_temp, &ctx->tsv_cnt};
     for (Buf *b : tsv) buf_free(*b);
     Buf *kb[] = {&ctx->kb_xs, &ctx->kb_cnt, &ctx->kb_cum, &ctx->kb_lnx, &ctx->kb_Dc, &ctx->kb_Ac, &ctx->kb_Zc,
                  &ctx->kb_D, &ctx->kb_alpha, &ctx->kb_xmin, &ctx->kb_ntail, &ctx->kb_ncand, &ctx->kb_route,
@@ -1664,12 +1665,15 @@ cc_status cc_labels_tuple_sv(cc_ctx *ctx, const void *edges_dev, int64_t n, int6
         CC_TRY(buf_reserve(ctx, ctx->tsv_v0, (size_t)cap * 8));
         CC_TRY(buf_reserve(ctx, ctx->tsv_v1, (size_t)cap * 8));
         CC_TRY(buf_reserve(ctx, ctx->tsv_val, (size_t)cap * 4));
+        CC_TRY(buf_reserve(ctx, ctx->tsv_val2, (size_t)cap * 4));
         CC_TRY(buf_reserve(ctx, ctx->tsv_uniq, (size_t)cap * 4));
         CC_TRY(buf_reserve(ctx, ctx->tsv_agg, (size_t)cap * 4));
         CC_TRY(buf_reserve(ctx, ctx->tsv_cnt, 64));
         ctx->tsv_cap = cap;
     }
     CC_TRY(buf_reserve(ctx, ctx->tsv_dense, (size_t)(n + 4) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->tsv_pc, (size_t)(n + 4) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->tsv_done, (size_t)(n + 4) * 4));
     // the temporary storage the sorts need depends on the key bits (n) as well
     const size_t tb = tuple_sv_temp_bytes(ctx->tsv_cap, (vid_t)n);
     CC_TRY(buf_reserve(ctx, ctx->tsv_temp, tb));
@@ -1678,6 +1682,9 @@ cc_status cc_labels_tuple_sv(cc_ctx *ctx, const void *edges_dev, int64_t n, int6
     b.v0 = as<unsigned long long>(ctx->tsv_v0);
     b.v1 = as<unsigned long long>(ctx->tsv_v1);
     b.val = as<uint32_t>(ctx->tsv_val);
+    b.val2 = as<uint32_t>(ctx->tsv_val2);
+    b.pc = as<uint32_t>(ctx->tsv_pc);
+    b.done = as<uint32_t>(ctx->tsv_done);
     b.uniq = as<uint32_t>(ctx->tsv_uniq);
     b.agg = as<uint32_t>(ctx->tsv_agg);
     b.dense = as<uint32_t>(ctx->tsv_dense);
@@ -1700,10 +1707,13 @@ cc_status cc_labels_tuple_sv(cc_ctx *ctx, const void *edges_dev, int64_t n, int6
     int iters = 0, sorts = 0;
     float sort_ms = 0.0f;
     float *sort_out = ctx->opt.profile ? &sort_ms : nullptr;
-    const int rc = ctx->opt.id_bytes == 4 ? tuple_sv_run<int32_t>(edges_dev, m, (vid_t)n, labels_out_dev, b, st,
-                                                                  cap_iters, &iters, sort_out, &sorts, s)
-                                          : tuple_sv_run<int64_t>(edges_dev, m, (vid_t)n, labels_out_dev, b, st,
-                                                                  cap_iters, &iters, sort_out, &sorts, s);
+    long long active[CC_MAX_SV_ITERS_RECORDED] = {};
+    const int rc = ctx->opt.id_bytes == 4
+                       ? tuple_sv_run<int32_t>(edges_dev, m, (vid_t)n, labels_out_dev, b, st, cap_iters, &iters,
+                                               active, CC_MAX_SV_ITERS_RECORDED, sort_out, &sorts, s)
+                       : tuple_sv_run<int64_t>(edges_dev, m, (vid_t)n, labels_out_dev, b, st, cap_iters, &iters,
+                                               active, CC_MAX_SV_ITERS_RECORDED, sort_out, &sorts, s);
+    for (int i = 0; i < CC_MAX_SV_ITERS_RECORDED; i++) S.m_active[i] = active[i];
     S.kernel_ms[CC_K_TUPLE_SORT] = sort_ms;
     S.kernel_launches[CC_K_TUPLE_SORT] = sorts;
     rec(ctx, EV_SV, s);

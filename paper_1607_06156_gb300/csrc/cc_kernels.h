@@ -95,15 +95,18 @@ void launch_hist_widen(const uint32_t *hist, const uint32_t *ovf, unsigned long 
                        uint64_t *out, long long len, int grid, cudaStream_t s);
 void launch_hist_narrow(const uint64_t *in, long long len, uint32_t *hist, DevState *st, int grid, cudaStream_t s);
 
-// k_tuple_sv.cu: the paper's sort-based SV (Algorithm 1) as an ablation.
-// Tuple buffers hold cap >= n + 2m + n entries (the tuples and the temporaries).
+// k_tuple_sv.cu: the paper's sort-based SV (Section 3.1) as an ablation, with
+// the exclusion of completed partitions (Section 3.1.4).
+// Tuple buffers hold cap >= n + 2m + n entries (the tuples and the extras).
 struct TupleSvBufs {
-    uint32_t *t32[4];              // tuple words: two hold the tuples (r, p | temporary bit), two are scratch
-    unsigned long long *v0, *v1;   // partition-pass values q << 32 | r (double buffer)
-    uint32_t *val;                 // reduce-by-key values
+    uint32_t *t32[4];              // tuple words: two hold the tuples (r, p | extra bit), two are scratch
+    unsigned long long *v0, *v1;   // partition-grouped values (double buffer), then the packed tuples
+    uint32_t *val, *val2;          // reduce-by-key values
     uint32_t *uniq, *agg;          // reduce-by-key outputs
-    uint32_t *dense;               // [n] run minimum by key
-    unsigned long long *counters;  // [4]: runs, changed, kept after erasing the temporaries
+    uint32_t *dense;               // [n] reduced value by key
+    uint32_t *pc;                  // [n] vertex: all its tuples share one partition
+    uint32_t *done;                // [n] partition: completed
+    unsigned long long *counters;  // [4]: runs, moved, tuples kept
     void *temp;
     size_t temp_bytes;
     long long cap;
@@ -111,10 +114,11 @@ struct TupleSvBufs {
 };
 size_t tuple_sv_temp_bytes(long long cap, vid_t n);
 // 0: labels written; 1: CUDA error or capacity; 2: no convergence within max_iters
+// active_out[i - 1] (i <= active_cap): tuples in the working set entering iteration i
 // sort_ms (optional): the summed time of the radix sorts, *sorts their number
 template <typename T>
 int tuple_sv_run(const void *edges, long long m, vid_t n, void *labels, TupleSvBufs b, DevState *st, int max_iters,
-                 int *iters_out, float *sort_ms, int *sorts, cudaStream_t s);
+                 int *iters_out, long long *active_out, int active_cap, float *sort_ms, int *sorts, cudaStream_t s);
 
 // k_sv.cu
 template <typename T>

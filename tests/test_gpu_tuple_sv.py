@@ -36,15 +36,32 @@ def _run(edges: np.ndarray, n: int, id_bytes: int = 4, **opts):
 
 
 @pytest.mark.parametrize("seed", range(6))
-def test_matches_algorithm1_labels_and_iterations(seed):
+def test_matches_algorithm1_labels_iterations_and_working_set(seed):
+    """Labels, iterations, and the tuples left in the working set entering
+    every iteration after completed partitions leave (Section 3.1.4)."""
     rng = np.random.default_rng(500 + seed)
     n = int(rng.integers(1, 300))
     m = int(rng.integers(0, 2 * n + 1))
     e = rng.integers(0, n, size=(m, 2))
-    want_lab, want_it = tuple_sv(n, e.tolist())
+    trace = []
+    want_lab, want_it = tuple_sv(n, e.tolist(), trace=trace)
     got, st = _run(e, n)
     assert got.tolist() == want_lab
     assert st["sv_iters"] == want_it
+    assert st["m_active"][:want_it] == [t["active"] for t in trace]
+
+
+def test_many_small_components_leave_early():
+    """The planted graph's 512 components finish at different iterations:
+    the working set shrinks each iteration exactly as in the oracle."""
+    g = gg.planted(seed=6, n=4096, ncomp=128)
+    trace = []
+    want_lab, want_it = tuple_sv(g.n, g.edges.tolist(), trace=trace)
+    got, st = _run(g.edges, g.n)
+    assert got.tolist() == want_lab
+    active = [t["active"] for t in trace]
+    assert st["m_active"][:want_it] == active
+    assert active[-1] < active[0]
 
 
 def test_long_path_iterations():
