@@ -51,8 +51,8 @@ WORKLOADS = {
     "batch4096": dict(kind="batch", seed=1, G=4096, nmin=1000, nmax=1_000_000),
     "batch512": dict(kind="batch", seed=1, G=512, nmin=1000, nmax=1_000_000),
 }
-KERNEL_FILES = ["cc_common.cuh", "ks_math.cuh", "k_degree.cu", "k_sv.cu", "k_bfs.cu", "k_bucket.cu", "k_batch_route.cu",
-                "cc_api.cu"]
+KERNEL_FILES = ["cc_common.cuh", "ks_math.cuh", "k_degree.cu", "k_degree_part.cu", "k_sv.cu", "k_bfs.cu", "k_bucket.cu",
+                "k_batch_route.cu", "cc_api.cu"]
 
 
 def make_graph(name: str):
@@ -181,7 +181,9 @@ def kernel_class(name: str):
         if mode == 2:
             return "sv_gather_list" if ids == "unsigned int" else "sv_gather_input"
         return None
-    table = [("k_degree_hubs", "degree"), ("k_hub_", "degree"), ("k_degree<", "degree"), ("k_hist", "hist"),
+    if "k_sv_pass_loop" in name:  # the list pass inside the graph's WHILE node
+        return "sv_gather_list"
+    table = [("k_degree_partition", "degree"), ("k_degree_count", "degree"), ("k_degree_hubs", "degree"), ("k_hub_", "degree"), ("k_degree<", "degree"), ("k_hist", "hist"),
              ("k_distinct", "ks"), ("k_ks_", "ks"), ("k_parent_init", "parent_init"), ("k_sv_sample", "sv_first"),
              ("k_shortcut_all", "sv_shortcut"), ("k_sv_shortcut", "sv_shortcut"), ("k_finalize", "finalize")]
     for key, cls in table:
@@ -301,6 +303,63 @@ def cpu_oracle_rate(edges: np.ndarray, n: int, budget_pairs: int) -> tuple[float
     return k / dt, k, dt
 
 
+def cpu_leg(edges: np.ndarray, n: int, gpu_labels: np.ndarray, budget_pairs: int) -> tuple[dict, bool]:
+    """The cpu_baseline leg of one graph (outside every timed region): the
+    oracle's sequential union-find timed on one host core over the whole
+    graph when it has at most `budget_pairs` pairs (else over that prefix,
+    with the whole graph labelled untimed), and the GPU labels compared with
+    the oracle's element by element."""
+    import oracle
+
+    m = edges.shape[0]
+    if m <= budget_pairs:
+        t = time.perf_counter()
+        want = oracle.labels_uf(edges, n)
+        dt = time.perf_counter() - t
+        k = m
+        sample = f"all {m} pairs of the graph ({dt:.1f} s of sequential union-find)"
+    else:
+        rate, k, dt = cpu_oracle_rate(edges, n, budget_pairs)
+        want = oracle.labels_uf(edges, n)
+        sample = f"first {k} of {m} pairs of the same graph, full n ({dt:.1f} s of sequential union-find)"
+    same = bool(np.array_equal(want, np.asarray(gpu_labels).astype(np.int64)))
+    return {"value": k / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}, same
+
+
+def cpu_leg_check(edges: np.ndarray, n: int, gpu_labels: np.ndarray) -> bool:
+    """The cpu_baseline leg's label check alone (untimed): the GPU labels
+    against the oracle's union-find, element by element."""
+    import oracle
+
+    return bool(np.array_equal(oracle.labels_uf(edges, n), np.asarray(gpu_labels).astype(np.int64)))
+
+
+def cpu_leg_batch(b, gpu_labels: np.ndarray, threads: int) -> tuple[dict, bool, int]:
+    """The cpu_baseline leg of a batch: the oracle's union-find on every graph,
+    the graphs spread over `threads` host threads (the oracle releases the
+    interpreter lock), each graph's labels compared with the GPU's. Returns
+    the record, whether every graph matched, and the graphs checked."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    eo, vo = b.edge_offsets, b.vertex_offsets
+    lab = np.asarray(gpu_labels).astype(np.int64)
+
+    def one(g):
+        want = oracle.labels_uf(b.edges[eo[g]:eo[g + 1]], int(vo[g + 1] - vo[g]))
+        return bool(np.array_equal(want, lab[vo[g]:vo[g + 1]]))
+
+    t = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        ok = list(ex.map(one, range(b.G)))
+    dt = time.perf_counter() - t
+    m = int(eo[-1])
+    return ({"value": m / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+             "sample": f"all {b.G} graphs ({m} pairs), union-find per graph on {threads} threads, {dt:.1f} s"},
+            all(ok), len(ok))
+
+
 def max_over_ranks(ms: float, dist, device) -> float:
     """The slowest rank's time (every rank gets it); `dist` None = one rank."""
     if dist is None:
@@ -342,25 +401,126 @@ def run_reference(args, world: int, rank: int):
     return 0
 
 
-def run_batch(args, world: int, rank: int, local: int) -> int:
+def roofline_of(kms: dict, kla: dict, st: dict, w: int, steps: int, workload: str) -> dict:
+    """Dominant kernel class of the profiled calls against the measured HBM
+    copy bandwidth: algorithmic bytes per launch / average launch time."""
+    dom = max(kms, key=lambda k: kms[k])
+    per_call_bytes = alg_bytes(dom, st, w)
+    per_launch_ms = kms[dom] / max(kla[dom], 1)
+    launches_per_call = kla[dom] / steps
+    achieved = per_call_bytes / launches_per_call / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+    pk = peaks()
+    peak = pk.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    if not peak:
+        peak = 6800.0
+    traffic = ncu_traffic(dom, workload)
+    if traffic is not None:
+        traffic /= launches_per_call
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src,
+            "alg_bytes_per_launch": per_call_bytes / launches_per_call, "avg_launch_ms": per_launch_ms,
+            "traffic": traffic}
+
+
+def kernel_table(kms: dict, kla: dict, st: dict, w: int, steps: int) -> dict:
+    return {k: {"ms_per_step": kms[k] / steps, "launches_per_step": kla[k] / steps,
+                "gbs": (alg_bytes(k, st, w) / (kms[k] / steps / 1e3) / 1e9) if kms[k] > 0 else None}
+            for k in kms if kla[k]}
+
+
+def profiled_calls(torch, eng, call, steps: int, stream) -> tuple[dict, dict, dict, float]:
+    """The same calls with per-kernel CUDA events (options.profile = 1, the
+    host-driven SV loop): summed ms and launches per kernel class, the last
+    call's statistics and the ms per call of this region."""
+    eng.set_options(profile=1)
+    call()
+    torch.cuda.synchronize()
+    kms, kla = {}, {}
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    st = None
+    for _ in range(steps):
+        call()
+        st = eng.stats()
+        for k, v in st["kernel_ms"].items():
+            kms[k] = kms.get(k, 0.0) + v
+            kla[k] = kla.get(k, 0) + st["kernel_launches"][k]
+    p1.record(stream)
+    torch.cuda.synchronize()
+    eng.set_options(profile=0)
+    return kms, kla, st, p0.elapsed_time(p1) / steps
+
+
+def timed_calls(torch, eng, call, steps: int, stream, dist=None, device=None) -> tuple[float, int]:
+    """Device time of `steps` back-to-back calls (CUDA events on the launching
+    stream, a synchronise and a barrier on both sides): total ms (max over
+    ranks) and the kernels the calls launched."""
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    e0.record(stream)
+    for _ in range(steps):
+        call()
+        launches += eng.stats()["launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return max_over_ranks(e0.elapsed_time(e1), dist, device), launches
+
+
+def single_record(name: str, args, dev, stream, cpu_budget: int) -> dict:
+    """One config as a sub-record: the heuristic route through cc_labels with
+    the pairs resident in HBM, its dominant kernel against the HBM roofline,
+    and the labels against the oracle."""
+    import torch
+
+    import paper_1607_06156_gb300 as cc
+
+    g = make_graph(name)
+    w, n, m = g.id_bytes, g.n, g.m
+    edges_d = torch.from_numpy(g.edges).to(dev)
+    lab = torch.empty(n, dtype=edges_d.dtype, device=dev)
+    eng = cc.Engine(id_bytes=w, device=dev.index, profile=0)
+    call = lambda: eng.labels(edges_d, n, out=lab)
+    for _ in range(max(args.warmup, 1)):
+        call()
+    torch.cuda.synchronize()
+    ms, launches = timed_calls(torch, eng, call, args.steps, stream)
+    kms, kla, st, ms_prof = profiled_calls(torch, eng, call, args.steps, stream)
+    roof = roofline_of(kms, kla, st, w, args.steps, name)
+    gpu_lab = lab.cpu().numpy()
+    cpu, same = cpu_leg(g.edges, n, gpu_lab, cpu_budget)
+    eng.close()
+    rec = {"config": workload_config(name, g), "ms_per_step": ms / args.steps, "value": m / (ms / args.steps / 1e3),
+           "unit": UNIT, "steps": args.steps, "route_taken": "bfs+sv" if st["route"] else "sv", "ks_d": st["ks_d"],
+           "sv_iters": st["sv_iters"], "gpu_launches": launches, "roofline": roof,
+           "kernels": kernel_table(kms, kla, st, w, args.steps), "labels_vs_oracle": same, "cpu_baseline": cpu,
+           "stage_ms": {k: st[k] for k in ("ms_degree", "ms_predict", "ms_csr", "ms_bfs", "ms_sv", "ms_finalize",
+                                           "ms_total")}}
+    if not same:
+        raise SystemExit(f"{name}: labels differ from the oracle")
+    del edges_d, lab
+    torch.cuda.empty_cache()
+    return rec
+
+
+def batch_record(args, dev, stream, world: int = 1, rank: int = 0, dist=None, workload: str = "batch4096") -> dict:
     """Batched form: one cc_labels_batched call per step over G graphs, against
-    a loop of per-graph cc_labels calls on the same GPU (labels compared).
-    With N ranks the batch holds G x N graphs and every rank labels its own
-    longest-processing-time-first shard of them (about G graphs), with no
-    collective in the data path; the value is all pairs / the slowest rank."""
+    a loop of per-graph cc_labels calls on the same GPU and against the same
+    batch with the route prediction skipped. With N ranks the batch holds
+    G x N graphs and every rank labels its own longest-processing-time-first
+    shard of them (about G graphs), with no collective in the data path; the
+    value is all pairs / the slowest rank."""
     import torch
 
     import graphgen as gg
     import paper_1607_06156_gb300 as cc
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=dev)
-    w = dict(WORKLOADS[args.workload])
+    w = dict(WORKLOADS[workload])
     w.pop("kind")
     if world > 1:
         from paper_1607_06156_gb300.sharding import graph_cost, lpt_shards
@@ -379,110 +539,146 @@ def run_batch(args, world: int, rank: int, local: int) -> int:
     vo_h = torch.from_numpy(b.vertex_offsets)
     eo_d, vo_d = eo_h.to(dev), vo_h.to(dev)
     out = torch.empty(n, dtype=torch.int32, device=dev)
-    eng = cc.Engine(id_bytes=4, device=local, profile=0)  # SV loop as one captured graph
-    stream = torch.cuda.current_stream(dev)
+    eng = cc.Engine(id_bytes=4, device=dev.index, profile=0)  # SV loop as one captured graph
+    call = lambda: eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
     for _ in range(max(args.warmup, 1)):
-        eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
-    torch.cuda.synchronize(dev)
-    sampler = ClockSampler(local) if rank == 0 else None
-    if sampler:
-        sampler.start()
-        time.sleep(0.5)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches = 0
-    e0.record(stream)
-    for _ in range(args.steps):
-        eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
-        launches += eng.stats()["launches"]
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
-    # per-kernel CUDA events in a second region (profiling on: host-driven loop)
-    eng.set_options(profile=1)
-    eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
-    kms, kla = {}, {}
-    for _ in range(args.steps):
-        eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
-        st = eng.stats()
-        for k, v in st["kernel_ms"].items():
-            kms[k] = kms.get(k, 0.0) + v
-            kla[k] = kla.get(k, 0) + st["kernel_launches"][k]
-    clocks = sampler.stop() if sampler else None
-    eng.set_options(profile=0)
-    if world > 1:  # the shards ran; rank 0 reports the job
-        if rank == 0:
-            line = {"metric": METRIC + " [batched form]", "value": m_job / (ms / 1e3), "unit": UNIT,
-                    "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-                    "data": "synthetic",
-                    "config": {"workload": args.workload, "graphs": w["G"], "m": m_job,
-                               "parallelism": f"graph shards (longest processing time first) x{world}, "
-                                              "no collective",
-                               "graph": "log-uniform n_g in [1K, 1M], cycling R-MAT ef 8 / grid p=0.55 / "
-                                        "chain forest", "l2": "inputs larger than L2 (no flush)"},
-                    "rank0_shard": {"graphs": int(b.G), "m": m, "n": n}, "gpu_launches": launches,
-                    "clocks": clocks}
-            print(json.dumps(line), flush=True)
+        call()
+    torch.cuda.synchronize()
+    ms, launches = timed_calls(torch, eng, call, args.steps, stream, dist, dev)
+    ms /= args.steps
+    cfg = {"workload": workload, "graphs": w["G"], "n": n, "m": m_job,
+           "graph": "log-uniform n_g in [1K, 1M], cycling R-MAT ef 8 / grid p=0.55 / chain forest",
+           "l2": "inputs larger than L2 (no flush)"}
+    if world > 1:
+        cfg["parallelism"] = f"graph shards (longest processing time first) x{world}, no collective"
         eng.close()
-        dist.barrier()
-        dist.destroy_process_group()
-        return 0
+        return {"config": cfg, "ms_per_step": ms, "value": m_job / (ms / 1e3), "unit": UNIT,
+                "gpu_launches": launches, "rank0_shard": {"graphs": int(b.G), "m": m, "n": n}}
+    kms, kla, st, _ = profiled_calls(torch, eng, call, args.steps, stream)
+    gpu_lab = out.cpu().numpy()
     # the same graphs one cc_labels call at a time (each graph in its own aligned buffer)
     per = [edges_d[b.edge_offsets[g]:b.edge_offsets[g + 1]].clone() for g in range(b.G)]
     outs = [torch.empty(int(b.vertex_offsets[g + 1] - b.vertex_offsets[g]), dtype=torch.int32, device=dev)
             for g in range(b.G)]
-    one = cc.Engine(id_bytes=4, device=local)
+    one = cc.Engine(id_bytes=4, device=dev.index)
     for g in range(b.G):
         one.labels(per[g], outs[g].numel(), out=outs[g])
-    torch.cuda.synchronize(dev)
-    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
     loops = max(1, min(args.steps, 2))
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(loops):
         for g in range(b.G):
             one.labels(per[g], outs[g].numel(), out=outs[g])
     c.record(stream)
-    torch.cuda.synchronize(dev)
+    torch.cuda.synchronize()
     ms_loop = a.elapsed_time(c) / loops
-    same = all(torch.equal(outs[g], out[b.vertex_offsets[g]:b.vertex_offsets[g + 1]]) for g in range(b.G))
-    if not same:
-        raise SystemExit("batched labels differ from the per-graph calls")
-    dom = max(kms, key=lambda k: kms[k])
-    kernels = {k: {"ms_per_step": kms[k] / args.steps, "launches_per_step": kla[k] / args.steps} for k in kms if kla[k]}
+    same_loop = all(torch.equal(outs[g], out[b.vertex_offsets[g]:b.vertex_offsets[g + 1]]) for g in range(b.G))
+    one.close()
+    del per, outs
     # the same batch with the route prediction skipped (every graph SV only)
-    sv = cc.Engine(id_bytes=4, device=local, route="sv")
+    sv = cc.Engine(id_bytes=4, device=dev.index, route="sv")
     sv.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
-    torch.cuda.synchronize(dev)
+    torch.cuda.synchronize()
     a.record(stream)
     for _ in range(loops):
         sv.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
     c.record(stream)
-    torch.cuda.synchronize(dev)
+    torch.cuda.synchronize()
     ms_sv = a.elapsed_time(c) / loops
+    same_sv = bool(torch.equal(out.cpu(), torch.from_numpy(gpu_lab)))
     sv.close()
-    line = {"metric": METRIC + " [batched form]", "value": m / (ms / 1e3), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": args.workload, "graphs": b.G, "n": n, "m": m,
-                       "graph": "log-uniform n_g in [1K, 1M], cycling R-MAT ef 8 / grid p=0.55 / chain forest",
-                       "l2": "inputs larger than L2 (no flush)"},
-            "vs_per_graph_loop": {"value": m / (ms_loop / 1e3), "ms_per_step": ms_loop,
-                                  "speedup": ms_loop / ms, "labels_identical": same},
+    eng.close()
+    del edges_d, out
+    torch.cuda.empty_cache()
+    cpu, same, checked = cpu_leg_batch(b, gpu_lab, threads=max(1, min(16, os.cpu_count() or 1)))
+    if not (same and same_loop and same_sv):
+        raise SystemExit(f"batched labels: oracle {same}, per-graph loop {same_loop}, SV-only batch {same_sv}")
+    dom = max(kms, key=lambda k: kms[k])
+    return {"config": cfg, "ms_per_step": ms, "value": m / (ms / 1e3), "unit": UNIT, "steps": args.steps,
+            "gpu_launches": launches,
+            "vs_per_graph_loop": {"value": m / (ms_loop / 1e3), "ms_per_step": ms_loop, "speedup": ms_loop / ms,
+                                  "labels_identical": same_loop},
             "sv_only_batched": {"value": m / (ms_sv / 1e3), "ms_per_step": ms_sv,
                                 "note": "route prediction skipped (CC_ROUTE_FORCE_SV)"},
             "route_policy": "auto (a K-S fit per graph)", "graphs_routed_bfs": st["route"],
             "schedule": {"unroll": st["batch_unroll"], "grid_mult": st["batch_grid_mult"]},
-            "dominant_kernel": dom, "kernels": kernels, "gpu_launches": launches, "clocks": clocks,
-            "sv_iters": st["sv_iters"], "m_active": st["m_active"]}
-    print(json.dumps(line), flush=True)
-    eng.close()
-    one.close()
-    return 0
+            "roofline": roofline_of(kms, kla, st, 4, args.steps, workload) | {"kernel": dom},
+            "kernels": kernel_table(kms, kla, st, 4, args.steps), "sv_iters": st["sv_iters"],
+            "m_active": st["m_active"], "labels_vs_oracle": same, "graphs_checked": checked, "cpu_baseline": cpu}
+
+
+def learned_record(args, dev, stream, graphs: int) -> dict | None:
+    """The learned route against the K-S heuristic on a bounded held-out mix
+    (the predictor's five families from a seed not used in training, plus
+    one R-MAT scale 22 and one 4096 x 4096 percolated grid): device time of
+    each route per graph (median of 3), the per-graph best forced route,
+    and every graph's labels against the oracle."""
+    import torch
+
+    import graphgen as gg
+    import paper_1607_06156_gb300 as cc
+    from paper_1607_06156_gb300 import train_predictor as tp
+
+    wpath = tp.default_weights_path()
+    if not os.path.exists(wpath):
+        return None
+    params, n_train = tp.load_params(wpath)
+    timer = tp.Timer(torch, cc)
+    learned = cc.Engine(id_bytes=4, device=dev.index, route="learned")
+    learned.set_predictor(params)
+    rng = np.random.default_rng(7777)
+    plan = [(tp.FAMILIES[i % len(tp.FAMILIES)], None) for i in range(graphs)] + [("rmat", 22), ("grid", 4096)]
+    tot = {"heuristic": 0.0, "learned": 0.0, "best_forced": 0.0, "sv": 0.0}
+    m_tot, same_all, bfs_routes, fams = 0, True, 0, {}
+    for fam, big in plan:
+        if fam == "rmat" and big:
+            g = gg.rmat(seed=int(rng.integers(1, 2 ** 40)), scale=big, edge_factor=16)
+        elif fam == "grid":
+            g = gg.grid_chains(seed=int(rng.integers(1, 2 ** 40)), W=big, p=0.55, nchains=0, id_bytes=4)
+        else:
+            g = tp.make_graph(rng, fam)
+        e = torch.from_numpy(g.edges).to(dev)
+        out = torch.empty(g.n, dtype=torch.int32, device=dev)
+        t_h = timer.time("auto", e, g.n, out)
+        t_l = timer.time(learned, e, g.n, out)
+        st = learned.stats()
+        lab = out.cpu().numpy()
+        t_sv = timer.time("sv", e, g.n, out)
+        t_b = min(timer.time(f"bfs{L}", e, g.n, out) for L in tp.CUTOFFS)
+        same = cpu_leg_check(g.edges, g.n, lab)
+        same_all &= same
+        bfs_routes += int(st["route"])
+        key = fam + (f"_{big}" if big else "")
+        f = fams.setdefault(key, {"graphs": 0, "t_heuristic_ms": 0.0, "t_learned_ms": 0.0, "t_best_forced_ms": 0.0,
+                                  "t_always_sv_ms": 0.0, "learned_bfs": 0})
+        f["graphs"] += 1
+        f["t_heuristic_ms"] += t_h
+        f["t_learned_ms"] += t_l
+        f["t_best_forced_ms"] += min(t_sv, t_b)
+        f["t_always_sv_ms"] += t_sv
+        f["learned_bfs"] += int(st["route"])
+        tot["heuristic"] += t_h
+        tot["learned"] += t_l
+        tot["best_forced"] += min(t_sv, t_b)
+        tot["sv"] += t_sv
+        m_tot += g.m
+        del e, out
+    learned.close()
+    timer.close()
+    torch.cuda.empty_cache()
+    if not same_all:
+        raise SystemExit("learned route: labels differ from the oracle")
+    rate = lambda k: m_tot / (tot[k] / 1e3)
+    return {"config": {"workload": "heldout_mix", "graphs": len(plan), "m": m_tot, "seed": 7777,
+                       "graph": f"{graphs} graphs cycling {', '.join(tp.FAMILIES)} + R-MAT scale 22 + "
+                                "4096^2 grid p=0.55", "predictor_train_graphs": n_train},
+            "value": rate("learned"), "unit": UNIT, "value_heuristic": rate("heuristic"),
+            "value_best_forced": rate("best_forced"), "value_always_sv": rate("sv"),
+            "gain_over_heuristic": tot["heuristic"] / tot["learned"], "learned_routes_bfs": bfs_routes,
+            "per_family": fams, "labels_vs_oracle": same_all,
+            "note": "per graph: median of 3 device-timed cc_labels calls per route; aggregate = sum of pairs / "
+                    "sum of times"}
 
 
 def check_labels(torch, edges_d, lab, n):
@@ -504,11 +700,15 @@ def main() -> int:
     ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
     ap.add_argument("--route", default="auto", choices=["auto", "sv", "bfs"])
     ap.add_argument("--no-compare", action="store_true", help="skip the forced-route comparison")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline and label check")
     ap.add_argument("--ref-pairs", type=int, default=1 << 24, help="pairs per step of the CPU oracle")
-    ap.add_argument("--cpu-pairs", type=int, default=1 << 25, help="pairs in the cpu_baseline sample")
+    ap.add_argument("--cpu-pairs", type=int, default=1 << 29,
+                    help="most pairs the cpu_baseline times (the whole graph when it has fewer)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer timing")
     ap.add_argument("--no-l2", action="store_true", help="skip the live L2 rate probe (no l2_roofline)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the sub-records of the other configs (planted, grid + chains, batch, learned route)")
+    ap.add_argument("--heldout", type=int, default=40, help="small held-out graphs of the learned-route record")
     ap.add_argument("--ncu-summary", metavar="CSV",
                     help="print the DRAM traffic summary of an ncu --csv capture of --workload and exit")
     ap.add_argument("--ncu-command", default="", help="the command line of that capture (recorded)")
@@ -525,8 +725,6 @@ def main() -> int:
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, world, rank)
-    if WORKLOADS[args.workload]["kind"] == "batch":
-        return run_batch(args, world, rank, local)
 
     import torch
 
@@ -534,11 +732,30 @@ def main() -> int:
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
     dist = None
     if world > 1:
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
+
+    if WORKLOADS[args.workload]["kind"] == "batch":
+        sampler = ClockSampler(local) if rank == 0 else None
+        if sampler:
+            sampler.start()
+        rec = batch_record(args, dev, stream, world, rank, dist, args.workload)
+        clocks = sampler.stop() if sampler else None
+        if rank == 0:
+            line = {"metric": METRIC + " [batched form]", "value": rec.pop("value"), "unit": UNIT, "n_gpus": world,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec.pop("ms_per_step"),
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                    "data": "synthetic", "config": rec.pop("config"), "clocks": clocks} | rec
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
     g = make_graph(args.workload)
     cfg = workload_config(args.workload, g)
     w = g.id_bytes
@@ -548,10 +765,10 @@ def main() -> int:
     # the product path: per-kernel profiling off, so the SV loop runs as one
     # captured CUDA graph with a device-driven WHILE node
     eng = cc.Engine(id_bytes=w, route=args.route, device=local, profile=0)
-    stream = torch.cuda.current_stream(dev)
+    call = lambda: eng.labels(edges_d, n, out=lab)
 
     for _ in range(max(args.warmup, 1)):
-        eng.labels(edges_d, n, out=lab)
+        call()
     torch.cuda.synchronize(dev)
     if not check_labels(torch, edges_d, lab, n):
         raise SystemExit("label invariants violated after warm-up")
@@ -560,64 +777,18 @@ def main() -> int:
     if sampler:
         sampler.start()
         time.sleep(0.5)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches = 0
-    e0.record(stream)
-    for _ in range(args.steps):
-        eng.labels(edges_d, n, out=lab)
-        launches += eng.stats()["launches"]
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    ms, launches = timed_calls(torch, eng, call, args.steps, stream, dist, dev)
     value = replica_value(world, m, args.steps, ms)
 
     # second timed region: the same calls with per-kernel CUDA events on the
     # launching stream (host-driven loop), for the kernel breakdown and roofline
-    eng.set_options(profile=1)
-    eng.labels(edges_d, n, out=lab)
-    torch.cuda.synchronize(dev)
-    kms, kla = {}, {}
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    for _ in range(args.steps):
-        eng.labels(edges_d, n, out=lab)
-        st = eng.stats()
-        for k, v in st["kernel_ms"].items():
-            kms[k] = kms.get(k, 0.0) + v
-            kla[k] = kla.get(k, 0) + st["kernel_launches"][k]
-    p1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_profiled = p0.elapsed_time(p1) / args.steps
+    kms, kla, last, ms_profiled = profiled_calls(torch, eng, call, args.steps, stream)
     clocks = sampler.stop() if sampler else None
-    eng.set_options(profile=0)
-    last = st
-
-    # roofline of the dominant kernel class
-    dom = max(kms, key=lambda k: kms[k])
-    per_call_bytes = alg_bytes(dom, last, w)
-    per_launch_ms = kms[dom] / max(kla[dom], 1)
+    roofline = roofline_of(kms, kla, last, w, args.steps, args.workload)
+    dom = roofline["kernel"]
     launches_per_call = kla[dom] / args.steps
-    achieved = per_call_bytes / launches_per_call / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
-    pk = peaks()
-    peak = pk.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
-    if not peak:
-        peak = 6800.0
-    traffic = ncu_traffic(dom, args.workload)
-    if traffic is not None:
-        traffic /= launches_per_call
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src,
-                "alg_bytes_per_launch": per_call_bytes / launches_per_call, "avg_launch_ms": per_launch_ms,
-                "traffic": traffic}
-    kernels = {k: {"ms_per_step": kms[k] / args.steps, "launches_per_step": kla[k] / args.steps,
-                   "gbs": (alg_bytes(k, last, w) / (kms[k] / args.steps / 1e3) / 1e9) if kms[k] > 0 else None}
-               for k in kms if kla[k]}
+    per_launch_ms = kms[dom] / max(kla[dom], 1)
+    kernels = kernel_table(kms, kla, last, w, args.steps)
     # the scattered-access ceiling: measured L2 random-op rates of this GPU (outside the timed region)
     rates = None if args.no_l2 else eng.l2_rates()
     for k, kv in kernels.items():
@@ -625,19 +796,17 @@ def main() -> int:
         if rates and ops > 0 and kv["ms_per_step"] > 0:
             kv["l2_gops"] = ops / (kv["ms_per_step"] / 1e3) / 1e9
             kv["l2_frac"] = kv["l2_gops"] * 1e9 / rates[op]
-    ops, op = l2_ops(dom, last)
-    if rates is None:
-        rates = {"gather": 0.0, "red_add": 0.0, "red_min": 0.0, "atom_min": 0.0}
-    l2_roofline = {"bound": "l2_random_ops", "kernel": dom, "op": op,
-                   "ops_per_launch": ops / launches_per_call,
-                   "achieved": ops / launches_per_call / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0,
-                   "peak": rates[op] / 1e9, "unit": "Gop/s",
-                   "peak_source": "measured in this run: 2^28 random 4-byte ops over a 64 MiB table "
-                                  "(cc_measure_l2_rates, best of 3)",
-                   "rates_gops": {r: rates[r] / 1e9 for r in ("gather", "red_add", "red_min", "atom_min")}}
-    l2_roofline["frac"] = l2_roofline["achieved"] / l2_roofline["peak"] if l2_roofline["peak"] else None
-    if args.no_l2:
-        l2_roofline = None
+    l2_roofline = None
+    if rates:
+        ops, op = l2_ops(dom, last)
+        l2_roofline = {"bound": "l2_random_ops", "kernel": dom, "op": op,
+                       "ops_per_launch": ops / launches_per_call,
+                       "achieved": ops / launches_per_call / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0,
+                       "peak": rates[op] / 1e9, "unit": "Gop/s",
+                       "peak_source": "measured in this run: 2^28 random 4-byte ops over a 64 MiB table "
+                                      "(cc_measure_l2_rates, best of 3)",
+                       "rates_gops": {r: rates[r] / 1e9 for r in ("gather", "red_add", "red_min", "atom_min")}}
+        l2_roofline["frac"] = l2_roofline["achieved"] / l2_roofline["peak"] if l2_roofline["peak"] else None
 
     # end to end through host buffers with the public host-input call
     # (cc_labels_host): the H2D copy of the pairs (chunked, overlapped with the
@@ -671,7 +840,7 @@ def main() -> int:
         b.record(stream)
         torch.cuda.synchronize(dev)
         t_link = a.elapsed_time(b) / steps_e2e
-        del d_edges, d_lab
+        del d_edges, d_lab, h_edges, h_lab
         e2e = {"value": world * m / (t_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(g.edges.nbytes),
                "d2h_bytes_per_step": int(n * lab.element_size()), "ms_per_step": t_e2e,
                "copies_alone_ms": t_link,
@@ -707,12 +876,16 @@ def main() -> int:
             sd = e.stats()
             if not torch.equal(lab, ref_lab):
                 raise SystemExit(f"route {r} changed the labels")
-            route_compare[r] = {"value": m / (t / 1e3), "ms_per_step": t, "route": sd["route"],
-                                "route_source": sd["route_source"],
-                                "stage_ms": {k2: sd[k2] for k2 in ("ms_degree", "ms_predict", "ms_csr", "ms_bfs",
-                                                                   "ms_sv", "ms_finalize")}}
+            rc = {"value": m / (t / 1e3), "ms_per_step": t, "route": sd["route"], "route_source": sd["route_source"],
+                  "stage_ms": {k2: sd[k2] for k2 in ("ms_degree", "ms_predict", "ms_csr", "ms_bfs", "ms_sv",
+                                                     "ms_finalize")}}
+            if r.startswith("bfs"):  # kernel breakdown of the BFS route (profiled calls)
+                pk_ms, pk_la, pst, _ = profiled_calls(torch, e, lambda: e.labels(edges_d, n, out=lab), k, stream)
+                rc["kernels"] = kernel_table(pk_ms, pk_la, pst, w, k)
+                rc["bfs_levels"] = pst["bfs_levels"]
+            route_compare[r] = rc
             e.close()
-        # the paper's own SV design (Algorithm 1: tuples grouped by radix sorts)
+        # the paper's own SV design (Section 3.1: tuples grouped by radix sorts)
         # on the same GPU, one warm-up and one timed call (it is far slower)
         if n < (1 << 31):
             e = cc.Engine(id_bytes=w, device=local)
@@ -732,18 +905,32 @@ def main() -> int:
             e.close()
             if not torch.equal(lab, ref_lab):
                 raise SystemExit("the sort-based SV changed the labels")
-            route_compare["tuple_sv_alg1"] = {
+            route_compare["tuple_sv"] = {
                 "value": m / (t / 1e3), "ms_per_step": t, "iterations": sd["sv_iters"],
+                "tuples_per_iteration": sd["m_active"],
                 "sorts": sp["kernel_launches"]["tuple_sort"], "sort_ms": sp["kernel_ms"]["tuple_sort"],
                 "sort_share": sp["kernel_ms"]["tuple_sort"] / sp["ms_total"] if sp["ms_total"] > 0 else None,
-                "note": "Algorithm 1 on the device: per iteration four radix sorts of the n + 2m tuples "
-                        "(plus temporaries) and segmented minima; no prediction"}
+                "note": "the paper's SV on the device: per iteration four radix sorts of the working set of "
+                        "tuples (plus the extras of the doubling round) and segmented minima; completed "
+                        "partitions leave the working set (Section 3.1.4); no prediction"}
+    gpu_lab = lab.cpu().numpy()
+    eng.close()
+    del edges_d, lab
+    torch.cuda.empty_cache()
 
-    cpu = None
+    cpu, same = None, None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, k, dt = cpu_oracle_rate(g.edges, n, args.cpu_pairs)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {k} of {m} pairs of the same graph, full n ({dt:.1f} s of sequential union-find)"}
+        cpu, same = cpu_leg(g.edges, n, gpu_lab, args.cpu_pairs)
+        if not same:
+            raise SystemExit("labels differ from the oracle")
+
+    configs = None
+    if rank == 0 and world == 1 and not args.no_configs and args.workload == "rmat24":
+        budget = args.cpu_pairs if not args.no_cpu else 0
+        configs = {"planted": single_record("planted", args, dev, stream, budget),
+                   "grid_chains": single_record("grid_chains", args, dev, stream, budget),
+                   "batch4096": batch_record(args, dev, stream),
+                   "learned_route": learned_record(args, dev, stream, args.heldout)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -752,6 +939,7 @@ def main() -> int:
                 "config": cfg | {"route_policy": args.route, "route_taken": "bfs+sv" if last["route"] else "sv",
                                  "ks_d": last["ks_d"], "sv_iters": last["sv_iters"],
                                  "parallelism": "replicas" if world > 1 else "single"},
+                "labels_vs_oracle": same,
                 "roofline": roofline, "l2_roofline": l2_roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks,
                 "gpu_launches": launches,
@@ -761,9 +949,8 @@ def main() -> int:
                 "kernels": kernels, "route_compare": route_compare,
                 "stage_ms": {k: last[k] for k in ("ms_degree", "ms_predict", "ms_csr", "ms_bfs", "ms_sv",
                                                   "ms_finalize", "ms_total")},
-                "m_active": last["m_active"]}
+                "m_active": last["m_active"], "configs": configs}
         print(json.dumps(line), flush=True)
-    eng.close()
     if dist:
         dist.destroy_process_group()
     return 0

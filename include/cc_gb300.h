@@ -214,8 +214,10 @@ cc_status cc_labels_host(cc_ctx *ctx, const void *edges_host, int64_t n, int64_t
  * Labels of G independent graphs in one call (the batched form). Under the
  * K-S policy (and the learned one, which the batch treats the same way)
  * every graph gets its own route prediction, as cc_ks_statistic_batched:
- * the degree pass is fused into the first SV hook pass over all graphs, and
- * each graph routed to BFS runs the BFS step on its own pairs; then the SV
+ * one degree pass over all graphs, then the per-graph fits beside the first
+ * SV hook pass over all graphs (which needs no route: every vertex starts as
+ * its own root); each graph routed to BFS runs the BFS step on its own
+ * pairs; then the SV
  * iterations run over the union of all graphs (one cached CUDA graph with a
  * device-driven loop when per-kernel profiling is off). CC_ROUTE_FORCE_SV
  * skips the prediction; CC_ROUTE_FORCE_BFS sends every graph to BFS.
@@ -336,14 +338,15 @@ cc_status cc_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, fl
  *   labels_out_dev [n] ids of id_bytes each, device, 16-byte aligned
  *   stream         cudaStream_t as void*
  * Errors as cc_labels (CC_ERR_INVALID_EDGE for an id outside [0, n)). The
- * call synchronises `stream` once per SV iteration and returns with the
- * labels complete.
- * The first call on each device looks up the device address of the scratch
- * array (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture. Every call on a device shares the one
- * scratch area and clears the parts that must start at zero; calls that
- * overlap on the GPU (other streams or host threads) race and must be
- * serialised by the caller.
+ * call synchronises `stream` once per SV iteration (it reads the active-pair
+ * count back) and returns with the labels complete, so it cannot be called
+ * while `stream` is being captured into a CUDA graph.
+ * Every call looks up the device address of the scratch array
+ * (cudaGetSymbolAddress) on the current device, so it stays valid across a
+ * device reset. Every call on a device shares the one scratch area and
+ * clears the parts that must start at zero; calls that overlap on the GPU
+ * (other streams or host threads) race and must be serialised by the
+ * caller.
  */
 cc_status cc_labels_static(const void *edges_dev, int id_bytes, int64_t n, int64_t m, void *labels_out_dev,
                            void *stream);

@@ -50,6 +50,7 @@ struct cc_ctx {
     long long tsv_cap = 0;
     Buf deg, parent, hooked, ebuf0, ebuf1, hist, ovf, ks_xs, ks_cnt, ks_cum, ks_lnx, ks_Dc, ks_Ac, ks_Zc, ks_Df, chunk_nz,
         chunk_mass, st, bk_count, bk_off, bk_cursor;
+    Buf dpart;  // endpoints partitioned by vertex bucket (partitioned degree pass)
     unsigned long long ovf_cap = 0, ks_cap = 0;
     // BFS workspace
     size_t bn_cap = 0, bm_cap = 0;
@@ -189,6 +190,8 @@ cc_status ensure_sv(cc_ctx *ctx, size_t n, size_t m) {
     CC_TRY(buf_reserve(ctx, ctx->bk_count, (size_t)ctx->grid * (bucket_max() + 2) * 4));
     CC_TRY(buf_reserve(ctx, ctx->bk_cursor, (size_t)ctx->grid * (bucket_max() + 2) * 4));
     CC_TRY(buf_reserve(ctx, ctx->bk_off, (size_t)(bucket_max() + 2) * 8));
+    if (degree_part_ok((vid_t)(N < 0xffffffffULL ? N : 0xfffffffeULL), (long long)M))
+        CC_TRY(buf_reserve(ctx, ctx->dpart, degree_part_scratch_bytes((vid_t)N, (long long)M)));
     ctx->n_cap = N;
     ctx->m_cap = M;
     return CC_OK;
@@ -322,6 +325,7 @@ cc_status read_back(cc_ctx *ctx, const void *dev_ptr, size_t bytes, cudaStream_t
 cc_status device_error(uint32_t err) {
     if (err & kErrInvalidEdge) return CC_ERR_INVALID_EDGE;
     if (err & kErrNoConvergence) return CC_ERR_NO_CONVERGENCE;
+    if (err & kErrTimeout) return CC_ERR_TIMEOUT;
     if (err & kErrOverflow) return CC_ERR_CUDA;
     return CC_OK;
 }
@@ -491,14 +495,19 @@ void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaSt
         return;
     }
     cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s);
-    cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
-    if (degree_uses_hubs(m) && ctx->ebuf1.bytes >= degree_hubs_scratch_bytes()) {
+    if (degree_part_ok(n, m) && ctx->dpart.bytes >= degree_part_scratch_bytes(n, m)) {
+        Scope sc(ctx, CC_K_DEGREE, s, 2);
+        launch_degree_partitioned<T>(edges, m, n, as<uint32_t>(ctx->deg), ctx->dpart.p, as<DevState>(ctx->st),
+                                     ctx->num_sms, s);
+    } else if (degree_uses_hubs(m) && ctx->ebuf1.bytes >= degree_hubs_scratch_bytes()) {
+        cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
         Scope sc(ctx, CC_K_DEGREE, s, 5);
         // ebuf1 is idle until the second SV iteration over the compacted list; m >= 2^24 makes it far larger
         // than the scratch
         launch_degree_hubs<T>(edges, m, n, as<uint32_t>(ctx->deg), as<unsigned>(ctx->ebuf1), as<DevState>(ctx->st),
                               ctx->grid, ctx->num_sms, s);
     } else {
+        cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
         Scope sc(ctx, CC_K_DEGREE, s, m > 0);
         launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), as<DevState>(ctx->st), ctx->grid, s);
     }
@@ -863,20 +872,17 @@ int enqueue_first_pass(cc_ctx *ctx, const void *edges, vid_t n, long long m, cud
     return 2;
 }
 
-// Speculation of the single-graph route: kSpecDeep also runs SV iteration 1
-// (the gather pass over the pairs) on the side stream; kSpecEarly forks the
-// side stream before the degree pass instead of after it. Measured on R-MAT
-// 24 (before the SV front end): shallow 7.82 ms, deep 7.61 ms, deep and
-// early 8.64 ms (the degree pass and the hook passes then contend for the L2
-// atomics). kSpecBeforeFit forks it before the K-S fit, which then runs on
-// a highest-priority stream while the gather pass launches one block per
-// tile (so the fit's blocks get SMs as gather blocks retire) instead of
-// after the fit. Measured with the front end, R-MAT 24 / 22: after the fit
-// 5.44 / 1.75 ms, before 5.26 / 1.56 ms; forking the front end alone before
-// the degree pass as well: 5.29 / 1.53 ms (not kept).
-constexpr bool kSpecDeep = true;
-constexpr bool kSpecEarly = false;
-constexpr bool kSpecBeforeFit = true;
+// Speculation of the single-graph route: the side stream runs parent init,
+// the first pass and SV iteration 1 (the gather pass over the pairs), forked
+// after the degree pass, while the K-S fit runs on a highest-priority stream
+// and the gather pass launches one block per tile (so the fit's blocks get
+// SMs as gather blocks retire). Measured on R-MAT 24 before the SV front
+// end: the first pass alone speculated 7.82 ms, with the gather pass 7.61
+// ms, both forked before the degree pass 8.64 ms (the degree pass and the
+// hook passes then contend for the L2 atomics). With the front end, R-MAT
+// 24 / 22: fit first and the speculative passes after it 5.44 / 1.75 ms,
+// fit beside them 5.26 / 1.56 ms; forking the front end alone before the
+// degree pass as well 5.29 / 1.53 ms.
 
 // Work cc_labels_host has already enqueued while the pairs were copied: the
 // device state zeroed and EV_START recorded, the degrees counted (AUTO), and
@@ -938,16 +944,12 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
             launch_parent_init(parent, n, nullptr, 0, ctx->grid, side);
         }
         enqueue_first_pass<T>(ctx, edges, n, m, side, true);
-        if (kSpecDeep && cap >= 2) {
+        if (cap >= 2) {
             // SV iteration 1 as well: the gather pass over the pairs, the crossing
             // pairs into ebuf0 (the degree pass keeps its hub table in ebuf1)
             {
                 Scope sc(ctx, CC_K_SV_GATHER_INPUT, side, 1);
-                if (kSpecBeforeFit)
-                    launch_sv_gather_tiles<T>(edges, m, n, parent, hooked, as<uint2>(ctx->ebuf0), st, 1, side);
-                else
-                    launch_sv_pass<T>(2, true, true, edges, m, n, parent, nullptr, 0, hooked, as<uint2>(ctx->ebuf0),
-                                      st, 1, ctx->grid, side);
+                launch_sv_gather_tiles<T>(edges, m, n, parent, hooked, as<uint2>(ctx->ebuf0), st, 1, side);
             }
             {
                 Scope sc(ctx, CC_K_SV_SHORTCUT, side, 1);
@@ -959,7 +961,6 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         spec.armed = true;
         return CC_OK;
     };
-    if (kSpecEarly && policy == CC_ROUTE_AUTO) CC_TRY(speculate());
     int cutoff = ctx->opt.bfs_cutoff_levels;
     // Learned route: sampled features + network; a confident prediction skips
     // the exact degree pass and the K-S fit (its BFS is the edge-list BFS,
@@ -1011,21 +1012,16 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
             enqueue_degree<T>(ctx, edges, n, m, s, pre && pre->degree_counted);
             rec(ctx, EV_DEGREE, s);
             if (policy != CC_ROUTE_FORCE_BFS) {
-                if (kSpecBeforeFit) {
-                    // the fit on a highest-priority stream: the speculative gather
-                    // launches one block per tile, so the fit's blocks are
-                    // scheduled as soon as gather blocks retire
-                    CC_TRY(speculate());
-                    CC_TRY(ensure_fit_stream(ctx));
-                    CU_TRY(cudaEventRecord(ctx->ev_fork, s));
-                    CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
-                    enqueue_ks(ctx, ctx->fit_s, distinct_degree_bound(ctx, n, m));
-                    CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
-                    CU_TRY(cudaStreamWaitEvent(s, ctx->ev_fit, 0));
-                } else {
-                    enqueue_ks(ctx, s, distinct_degree_bound(ctx, n, m));
-                    CC_TRY(speculate());
-                }
+                // the fit on a highest-priority stream: the speculative gather
+                // launches one block per tile, so the fit's blocks are
+                // scheduled as soon as gather blocks retire
+                CC_TRY(speculate());
+                CC_TRY(ensure_fit_stream(ctx));
+                CU_TRY(cudaEventRecord(ctx->ev_fork, s));
+                CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
+                enqueue_ks(ctx, ctx->fit_s, distinct_degree_bound(ctx, n, m));
+                CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
+                CU_TRY(cudaStreamWaitEvent(s, ctx->ev_fit, 0));
             }
         }
         rec(ctx, EV_PREDICT, s);
@@ -1386,7 +1382,7 @@ cc_status tune_batch(cc_ctx *ctx, const int32_t *edges, long long m, const int64
     for (const BatchSchedule &c : cand) {
         launch_parent_init(parent, nt, nullptr, 0, ctx->grid, s);
         CU_TRY(cudaEventRecord(a, s));
-        launch_sv_pass_batch(0, edges, m, eo, vo, G, nt, parent, hooked, nullptr, st, 0, ctx->grid, s, nullptr, c);
+        launch_sv_pass_batch(0, edges, m, eo, vo, G, nt, parent, hooked, nullptr, st, 0, ctx->grid, s, c);
         CU_TRY(cudaEventRecord(b, s));
         CU_TRY(cudaEventSynchronize(b));
         float ms = 0.f;
@@ -1433,13 +1429,12 @@ cc_status ensure_batch_route(cc_ctx *ctx, int G, int blocks) {
 // deg holds the union degrees. Fills kb_* for every graph and returns the
 // routes (1 = BFS first) in `route` (host, G entries).
 // The batched route: the per-graph fits run on a highest-priority stream
-// beside the first hook pass; kBatchFitOverlap launches that pass one block
-// per tile so that the fits get SMs as its blocks retire. Measured on 4,096
-// graphs while the fits took 25 ms: 107 ms with the fits after the pass,
-// 105.7 beside a resident-grid pass, 103.2 beside the tile-block pass. Once
-// the fits took 2.7 ms: 89.8 ms with the tile-block pass, 88.2 with the
-// resident grid (the tile blocks cost more than the overlap saves).
-constexpr bool kBatchFitOverlap = false;
+// beside the first hook pass, which keeps its resident grid. Measured on
+// 4,096 graphs while the fits took 25 ms: 107 ms with the fits after the
+// pass, 105.7 beside a resident-grid pass, 103.2 beside a pass launched one
+// block per tile (so that the fits get SMs as its blocks retire). Once the
+// fits took 2.7 ms: 89.8 ms with the tile-block pass, 88.2 with the resident
+// grid (the tile blocks cost more than the overlap saves).
 
 // One K-S fit per graph on stream s (the degrees of every graph are in
 // ctx->deg); the blocks take the graphs largest first.
@@ -1549,7 +1544,7 @@ cc_status cc_create(cc_ctx **out, const cc_options *opt, int device) {
         return CC_ERR_CUDA;
     }
     ctx->num_sms = prop.multiProcessorCount;
-    if (bucket_kernels_setup() != cudaSuccess) {
+    if (bucket_kernels_setup() != cudaSuccess || degree_part_setup() != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return CC_ERR_CUDA;
@@ -1581,7 +1576,7 @@ cc_status cc_destroy(cc_ctx *ctx) {
                    &ctx->ks_Ac,  &ctx->ks_Zc, &ctx->ks_Df, &ctx->chunk_nz,   &ctx->chunk_mass, &ctx->st,  &ctx->row_ptr, &ctx->col,
                    &ctx->vis,    &ctx->fb,         &ctx->nb,     &ctx->q0,      &ctx->q1,     &ctx->dq,
                    &ctx->off,    &ctx->tsum,       &ctx->counters, &ctx->bk_count, &ctx->bk_off,
-                   &ctx->bk_cursor, &ctx->csr_entries, &ctx->f_sdeg, &ctx->f_counts, &ctx->f_vis,
+                   &ctx->bk_cursor, &ctx->csr_entries, &ctx->dpart, &ctx->f_sdeg, &ctx->f_counts, &ctx->f_vis,
                    &ctx->f_f0,   &ctx->f_f1,       &ctx->f_x,    &ctx->pred_wb, &ctx->pred_bias, &ctx->pred_tmp};
     for (Buf *b : bufs) buf_free(*b);
     for (int e = 0; e < EV_COUNT; e++)
@@ -1855,22 +1850,19 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
         Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
         launch_parent_init(parent, nt, nullptr, 0, ctx->grid, s);
     }
-    // Route prediction per graph (Algorithm 2 lines 1-3): the degree pass
-    // fused into the first hook pass (every vertex starts as its own root,
-    // so that pass needs no route), one K-S fit per graph, then the BFS step
-    // for the graphs routed to it (lines 5-7): their visited vertices take
-    // the visited minimum as parent before the SV passes continue.
+    // Route prediction per graph (Algorithm 2 lines 1-3): the degree pass,
+    // one K-S fit per graph beside the first hook pass (every vertex starts
+    // as its own root, so that pass needs no route), then the BFS step for
+    // the graphs routed to it (lines 5-7): their visited vertices take the
+    // visited minimum as parent before the SV passes continue. Fusing the
+    // degree count into the first hook pass measured 69 ms against 39 + 13
+    // ms for the two passes (4,096 graphs).
     const int policy = ctx->opt.route_policy;
     const bool predict = m > 0 && policy != CC_ROUTE_FORCE_SV;
     if (predict) {
         CC_TRY(ensure_batch_route(ctx, G));
         CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s));
-        constexpr bool kFuseDegree = false;  // measured: fused 69 ms vs 39 + 13 ms split (4,096 graphs)
-        if (kFuseDegree) {
-            Scope sc(ctx, CC_K_SV_FIRST, s, 1);
-            launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,
-                                 hooked, nullptr, st, 0, ctx->grid, s, as<uint32_t>(ctx->deg), sch);
-        } else {
+        {
             {
                 Scope sc(ctx, CC_K_DEGREE, s, 1);
                 launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G,
@@ -1886,10 +1878,8 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
             CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
             {
                 Scope sc(ctx, CC_K_SV_FIRST, s, 1);
-                BatchSchedule first = sch;
-                first.tile_blocks = kBatchFitOverlap;
                 launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt,
-                                     parent, hooked, nullptr, st, 0, ctx->grid, s, nullptr, first);
+                                     parent, hooked, nullptr, st, 0, ctx->grid, s, sch);
             }
             CU_TRY(cudaStreamWaitEvent(s, ctx->ev_fit, 0));
         }
@@ -1928,10 +1918,10 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
         auto pre = [&](cudaStream_t cs) {
             if (!predict)
                 launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt,
-                                     parent, hooked, nullptr, st, 0, ctx->grid, cs, nullptr, sch);
+                                     parent, hooked, nullptr, st, 0, ctx->grid, cs, sch);
             launch_shortcut_all(parent, nt, st, 0, ctx->grid, cs);
             launch_sv_pass_batch(2, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,
-                                 hooked, eb0, st, 1, ctx->grid, cs, nullptr, sch);
+                                 hooked, eb0, st, 1, ctx->grid, cs, sch);
             launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, cs);
         };
         auto post = [&](cudaStream_t cs) {
@@ -1958,7 +1948,7 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
         if (!predict) {
             Scope sc(ctx, CC_K_SV_FIRST, s, 1);
             launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,
-                                 hooked, nullptr, st, 0, ctx->grid, s, nullptr, sch);
+                                 hooked, nullptr, st, 0, ctx->grid, s, sch);
         }
         {
             Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
@@ -1969,7 +1959,7 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
         {
             Scope sc(ctx, CC_K_SV_GATHER_INPUT, s, 1);
             launch_sv_pass_batch(2, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,
-                                 hooked, as<uint2>(ctx->ebuf0), st, 1, ctx->grid, s, nullptr, sch);
+                                 hooked, as<uint2>(ctx->ebuf0), st, 1, ctx->grid, s, sch);
         }
         {
             Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);

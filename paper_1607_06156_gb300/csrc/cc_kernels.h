@@ -14,7 +14,6 @@ struct BatchSchedule {
     int unroll = 2;
     int grid_mult = 1;
     const uint32_t *pair_tiles = nullptr;  // graph of every 2^kTileShift-th pair (launch_tile_graphs), required
-    bool tile_blocks = false;              // one block per tile instead of a resident grid
 };
 
 
@@ -95,6 +94,17 @@ void launch_hist_widen(const uint32_t *hist, const uint32_t *ovf, unsigned long 
                        uint64_t *out, long long len, int grid, cudaStream_t s);
 void launch_hist_narrow(const uint64_t *in, long long len, uint32_t *hist, DevState *st, int grid, cudaStream_t s);
 
+// k_degree_part.cu: degree pass as a partition of the endpoints by vertex
+// bucket (bulk copies into shared memory) and a count per bucket in shared
+// memory; for 2^20 <= m and n <= 2^25. scratch: degree_part_scratch_bytes.
+int degree_part_buckets(vid_t n);
+bool degree_part_ok(vid_t n, long long m);
+size_t degree_part_scratch_bytes(vid_t n, long long m);
+template <typename T>
+void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t *deg, void *scratch, DevState *st,
+                               int num_sms, cudaStream_t s);
+cudaError_t degree_part_setup();
+
 // k_tuple_sv.cu: the paper's sort-based SV (Section 3.1) as an ablation, with
 // the exclusion of completed partitions (Section 3.1.4).
 // Tuple buffers hold cap >= n + 2m + n entries (the tuples and the extras).
@@ -136,8 +146,7 @@ void launch_sv_gather_tiles(const void *in, long long m, vid_t n, vid_t *parent,
 void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid, cudaStream_t s);
 void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
                           vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
-                          cudaStream_t s, uint32_t *deg = nullptr,
-                          BatchSchedule sch = BatchSchedule());
+                          cudaStream_t s, BatchSchedule sch = BatchSchedule());
 void launch_finalize_batch(vid_t *parent, vid_t ntot, const int64_t *vo, int G, int32_t *labels, int grid,
                            cudaStream_t s,
                            const uint32_t *vertex_tiles);

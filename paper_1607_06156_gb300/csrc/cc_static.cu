@@ -14,8 +14,6 @@
 #include <stdint.h>
 #include <string.h>
 
-#include <mutex>
-
 #include "../../include/cc_gb300.h"
 #include "cc_common.cuh"
 #include "cc_kernels.h"
@@ -36,35 +34,23 @@ constexpr size_t kOffList0 = align256(kOffHooked + (kStaticMaxN + 4) * 4);
 constexpr size_t kOffList1 = align256(kOffList0 + (kStaticMaxM + 4) * 8);
 constexpr size_t kScratchBytes = align256(kOffList1 + (kStaticMaxM + 4) * 8);
 
-constexpr int kMaxDevices = 64;
-
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
 namespace {
 
-std::mutex g_setup_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once
-// per device; the host-side symbol is only a stand-in, not a device address).
+// Device address of the scratch array on the current device. The host-side
+// symbol is only a stand-in, not a device address. The lookup is cheap and
+// is repeated on every call, so a device reset (which reloads the module
+// at another address) never leaves a stale pointer behind.
 cc_status scratch_for_current_device(unsigned char **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
         return CC_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return CC_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = reinterpret_cast<unsigned char *>(g_scratch_addr[dev]);
+    *out = reinterpret_cast<unsigned char *>(p);
     return CC_OK;
 }
 

@@ -349,18 +349,14 @@ __global__ void __launch_bounds__(kBlock) k_finalize(vid_t *parent, vid_t n, T *
 // and a component's minimum union id is vo[g] plus its minimum local id.
 
 
-// DEG: also count both ends of every valid pair into deg (union ids): the
-// degree pass of Section 3.2 fused into the first hook pass, which needs
-// no prediction result (every vertex starts as its own root).
 // U: 16-byte vectors (two pairs each) per thread per tile, the schedule the
 // batched form's tuner picks.
-template <int MODE, bool WRITE, bool RECORD, bool DEG, int U>
+template <int MODE, bool WRITE, bool RECORD, int U>
 __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restrict__ in, long long m,
                                                           const int64_t *__restrict__ eo,
                                                           const int64_t *__restrict__ vo, int G, vid_t ntot,
                                                           vid_t *parent, vid_t *hooked_list, uint2 *__restrict__ out,
-                                                          DevState *st, int it, uint32_t *deg,
-                                                          const uint32_t *__restrict__ tg) {
+                                                          DevState *st, int it, const uint32_t *__restrict__ tg) {
     constexpr int K = 2 * U;
     __shared__ int sw[32];
     __shared__ unsigned long long sbase;
@@ -412,10 +408,6 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restr
                 bad = true;
                 continue;
             }
-            if (DEG) {
-                atomicAdd(&deg[base + u[r]], 1u);
-                atomicAdd(&deg[base + v[r]], 1u);
-            }
             keep[r] = sv_pair<MODE, RECORD>(base + u[r], base + v[r], ntot, parent, nullptr, 0, ru[r], rv[r], hk[r],
                                             bad);
         }
@@ -459,34 +451,26 @@ __global__ void __launch_bounds__(kBlock) k_finalize_batch(vid_t *parent, vid_t 
 template <int U>
 void launch_sv_pass_batch_u(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
                             vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
-                            cudaStream_t s, uint32_t *deg, int grid_mult, const uint32_t *sch_tg, bool tile_blocks) {
-    auto kf = mode == 0 && deg ? k_sv_pass_batch<0, false, false, true, U>
-              : mode == 0      ? k_sv_pass_batch<0, false, false, false, U>
-                               : k_sv_pass_batch<2, true, true, false, U>;
-    long long g = fit_grid((const void *)kf, grid, kBlock) * (grid_mult > 0 ? grid_mult : 1);
-    if (tile_blocks) {  // one block per tile of kBlock * U vectors, plus the odd last pair
-        const long long tile = (long long)kBlock * U;
-        g = (m / 2 + tile - 1) / tile + (m & 1);
-        if (g > 0x7fffffffLL) g = 0x7fffffffLL;
-    }
-    kf<<<(unsigned)g, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, mode == 0 ? deg : nullptr,
-                                      sch_tg);
+                            cudaStream_t s, int grid_mult, const uint32_t *sch_tg) {
+    auto kf = mode == 0 ? k_sv_pass_batch<0, false, false, U> : k_sv_pass_batch<2, true, true, U>;
+    const long long g = fit_grid((const void *)kf, grid, kBlock) * (grid_mult > 0 ? grid_mult : 1);
+    kf<<<(unsigned)g, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, sch_tg);
 }
 
 void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
                           vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
-                          cudaStream_t s, uint32_t *deg, BatchSchedule sch) {
+                          cudaStream_t s, BatchSchedule sch) {
     if (m <= 0) return;
     const uint32_t *sch_tg = sch.pair_tiles;
     if (sch.unroll == 1)
-        launch_sv_pass_batch_u<1>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s, deg,
-                                  sch.grid_mult, sch_tg, sch.tile_blocks);
+        launch_sv_pass_batch_u<1>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s,
+                                  sch.grid_mult, sch_tg);
     else if (sch.unroll == 4)
-        launch_sv_pass_batch_u<4>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s, deg,
-                                  sch.grid_mult, sch_tg, sch.tile_blocks);
+        launch_sv_pass_batch_u<4>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s,
+                                  sch.grid_mult, sch_tg);
     else
-        launch_sv_pass_batch_u<2>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s, deg,
-                                  sch.grid_mult, sch_tg, sch.tile_blocks);
+        launch_sv_pass_batch_u<2>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s,
+                                  sch.grid_mult, sch_tg);
 }
 
 void launch_finalize_batch(vid_t *parent, vid_t ntot, const int64_t *vo, int G, int32_t *labels, int grid,

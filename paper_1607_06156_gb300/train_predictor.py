@@ -252,8 +252,13 @@ def predict_routes(params: np.ndarray, X: np.ndarray) -> np.ndarray:
     return (O[:, 1] > O[:, 0]).astype(np.int32)
 
 
-def evaluate(params: np.ndarray, count: int, seed: int, big: int = 0, min_conf: float = 0.75, log=print) -> dict:
-    """Heuristic vs learned route on held-out graphs (labels must agree)."""
+def evaluate(params: np.ndarray, count: int, seed: int, big: int = 0, min_conf: float = 0.75, log=print,
+             check=None) -> dict:
+    """Heuristic vs learned route on held-out graphs (labels must agree).
+
+    `check(edges, n, labels)`, when given, is called with every graph's
+    learned-route labels (host int32) and must return True: the caller's
+    independent reference for the labels (the tests pass the CPU oracle)."""
     import torch
 
     import paper_1607_06156_gb300 as cc
@@ -281,13 +286,15 @@ def evaluate(params: np.ndarray, count: int, seed: int, big: int = 0, min_conf: 
         t_learn = timer.time(learned, e, g.n, out)
         st = learned.stats()
         same = bool(torch.equal(lab_auto, out))
+        if check is not None:
+            same = same and bool(check(g.edges, g.n, out.cpu().numpy()))
         t_sv = timer.time("sv", e, g.n, out)
         t_bfs = timer.time("bfs0", e, g.n, out)
         rows.append({"family": fam, "big": is_big, "n": g.n, "m": g.m, "t_heuristic": t_auto, "t_learned": t_learn,
-                     "t_sv": t_sv, "t_bfs": t_bfs, "learned_route": st["route"], "route_source": st["route_source"],
+                     "t_sv": t_sv, "t_bfs": t_bfs, "checked": check is not None, "learned_route": st["route"], "route_source": st["route_source"],
                      "confidence": st["pred_confidence"], "labels_equal": same})
         if not same:
-            raise SystemExit(f"learned route labels differ from the heuristic route on {g.name}")
+            raise SystemExit(f"learned route labels differ from the heuristic route or the reference on {g.name}")
         del e, out
     learned.close()
     timer.close()

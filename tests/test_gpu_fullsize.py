@@ -6,6 +6,8 @@ grid + chains graph (8192^2 percolated grid at p = 0.55 unioned with 10M
 branched chains, ~267M int64 vertices). The oracle's union-find runs once
 per graph on the host (tens of seconds each).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -60,9 +62,11 @@ def test_grid_chains_full_size():
 
 
 def test_batch4096_full_size():
-    """The 4,096-graph batch: sampled graphs against the oracle, every graph
-    against the label invariants (edge ends share a label, label <= id,
-    labels are fixed points)."""
+    """The 4,096-graph batch: every graph's labels against the oracle's
+    union-find (the graphs are spread over host threads; the oracle releases
+    the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     torch = torch_cuda()
     import paper_1607_06156_gb300 as cc
 
@@ -71,14 +75,14 @@ def test_batch4096_full_size():
     out = eng.labels_batched(torch.from_numpy(b.edges).cuda(), torch.from_numpy(b.edge_offsets),
                              torch.from_numpy(b.vertex_offsets))
     torch.cuda.synchronize()
-    got = out.cpu().numpy()
+    got = out.cpu().numpy().astype(np.int64)
     eng.close()
-    rng = np.random.default_rng(0)
-    sample = set(rng.choice(b.G, 24, replace=False).tolist()) | {0, 1, 2, b.G - 1}
-    for g in range(b.G):
-        lab = got[b.vertex_offsets[g]:b.vertex_offsets[g + 1]].astype(np.int64)
-        e = b.edges[b.edge_offsets[g]:b.edge_offsets[g + 1]]
-        assert (lab[e[:, 0]] == lab[e[:, 1]]).all(), g
-        assert (lab <= np.arange(lab.size)).all() and (lab[lab] == lab).all(), g
-        if g in sample:
-            assert np.array_equal(lab, oracle.cc_labels(e, lab.size)), g
+    eo, vo = b.edge_offsets, b.vertex_offsets
+
+    def mismatch(g):
+        want = oracle.labels_uf(b.edges[eo[g]:eo[g + 1]], int(vo[g + 1] - vo[g]))
+        return not np.array_equal(want, got[vo[g]:vo[g + 1]])
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        bad = [g for g, x in enumerate(ex.map(mismatch, range(b.G))) if x]
+    assert not bad, bad[:10]

@@ -96,6 +96,21 @@ def test_route_features_match_definition(maker):
     assert np.allclose(x, mlp.route_features(g.edges, g.n), atol=1e-6)
 
 
+def test_route_features_on_the_hand_built_graph():
+    """The graph whose features the oracle test checks by hand: sampled and
+    unsampled blocks of pairs, three BFS levels and a fourth that must not
+    count, a self-loop and a duplicated pair."""
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+    from tests.test_oracle_mlp import _feature_graph
+
+    e = _feature_graph().astype(np.int32)
+    eng = cc.Engine(id_bytes=4)
+    x = eng.route_features(torch.from_numpy(e).cuda(), 4096).cpu().numpy()
+    eng.close()
+    assert np.allclose(x, mlp.route_features(e, 4096), atol=1e-6)
+
+
 def test_learned_route_labels_exact_and_fallback():
     torch = torch_cuda()
     import paper_1607_06156_gb300 as cc
@@ -127,13 +142,14 @@ def test_learned_route_labels_exact_and_fallback():
 def test_trained_predictor_gains_over_the_heuristic():
     """The committed network (trained on 20,000 seeded graphs) against the
     K-S heuristic on graphs it was not trained on (another seed): labels
-    identical on every graph, and less total time. The learned route reads a
+    equal to the oracle's on every graph, and less total time. The learned route reads a
     1/16 vertex sample instead of the exact degree pass and K-S fit."""
     torch_cuda()
     from paper_1607_06156_gb300.train_predictor import default_weights_path, evaluate, load_params
 
     params, n_train = load_params(default_weights_path())
     assert n_train >= 20000
-    summ = evaluate(params, count=30, seed=777, big=0, log=lambda *a, **k: None)
-    assert summ["labels_equal"]
+    check = lambda e, n, lab: np.array_equal(oracle.labels_uf(e, n), lab.astype(np.int64))
+    summ = evaluate(params, count=30, seed=777, big=0, log=lambda *a, **k: None, check=check)
+    assert summ["labels_equal"] and all(r["checked"] for r in summ["rows"])
     assert summ["gain_learned_over_heuristic"] > 1.1, summ["gain_learned_over_heuristic"]
