@@ -24,6 +24,7 @@ enum : uint32_t {
     kErrInvalidEdge = 1u,
     kErrOverflow = 2u,     // an internal capacity was exceeded (a bug guard, never expected)
     kErrNoConvergence = 4u,
+    kErrTimeout = 8u,      // a bounded device wait (an mbarrier of a bulk copy) ran out
 };
 
 // Device-resident bookkeeping for one cc_labels call. Zeroed at the start of

@@ -1,0 +1,354 @@
+// Degree pass (Section 3.2, Algorithm 2 line 1) as a partition of the pair
+// endpoints by vertex bucket, then a count per bucket in shared memory.
+//
+// deg[v] = number of pair endpoints equal to v. Counting them with one
+// atomic per endpoint is bound by the rate of scattered L2 atomics (and, once
+// the count array leaves L2, by DRAM read-modify-writes). Here the endpoints
+// are moved instead of counted in place:
+//
+//  k_degree_partition  one CTA per SM streams 64 KB chunks of pairs into
+//                      shared memory with 1-D bulk copies (cp.async.bulk,
+//                      completion on an mbarrier, two buffers in flight).
+//                      Each chunk's endpoints are counting-sorted by bucket
+//                      (2^15 vertices) in shared memory; one global atomic
+//                      per bucket and chunk reserves the bucket's run, and
+//                      the 16-bit ids within the bucket are written as
+//                      contiguous runs. A bucket holds at most `cap`
+//                      entries; endpoints past it (a bucket far above the
+//                      average) are counted with global atomics instead, so
+//                      the counts stay exact for any input.
+//  k_degree_count      one CTA per bucket: 2^15 counters in 128 KB of shared
+//                      memory, the bucket's entries added with shared atomics
+//                      (lanes of a warp that hold the same vertex merged with
+//                      __match_any_sync, so hubs do not serialise), then the
+//                      bucket's slice of deg written once.
+//
+// HBM traffic per call: the pairs once (2wm bytes), the entries written and
+// read back (2 x 4m bytes), deg written (4n).
+#include "cc_common.cuh"
+#include "cc_kernels.h"
+
+namespace ccg {
+
+constexpr int kPartThreads = 1024;
+constexpr int kPartBits = 15;
+constexpr int kPartBucket = 1 << kPartBits;
+constexpr int kPartMaxBuckets = 1024;                           // n <= 2^25
+constexpr int kPartChunkBytes = 1 << 16;
+constexpr int kPartSlots = kPartChunkBytes / 16 / kPartThreads;  // 16-byte vectors per thread and chunk
+constexpr int kPartMaxEnd = kPartChunkBytes / 8 * 2;             // endpoints of a chunk of int32 pairs
+constexpr unsigned long long kWaitNs = 1000000000ull;           // bounded mbarrier waits: 1 s
+
+struct __align__(128) PartShared {
+    int4 buf[2][kPartChunkBytes / 16];  // two chunks of pairs (bulk-copy destinations)
+    uint16_t stage[kPartMaxEnd];        // ids within the bucket, sorted by bucket
+    uint16_t skey[kPartMaxEnd];         // the bucket of each staged id
+    uint32_t hist[kPartMaxBuckets];
+    uint32_t loff[kPartMaxBuckets + 1];
+    unsigned long long base[kPartMaxBuckets];
+    unsigned long long mbar[2];
+    uint32_t wsum[32];
+    int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// 1-D bulk copy global -> shared; `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *b) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(b))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for phase `parity` of the barrier to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity) {
+    if (mbar_try(b, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(b, parity))
+        if (global_ns() - t0 > kWaitNs) return false;
+    return true;
+}
+
+template <typename T>
+__host__ __device__ constexpr long long part_chunk_pairs() {
+    return kPartChunkBytes / (2 * (long long)sizeof(T));
+}
+
+// Pair p of chunk c: from the chunk's shared-memory copy, or (the odd last
+// pair of an int32 chunk, which the 16-byte bulk copy leaves out) from global memory.
+template <typename T>
+__device__ __forceinline__ void chunk_pair(const PartShared &S, int slot, const T *edges, long long c, int sv,
+                                           int j, bool in_smem, long long &u, long long &v) {
+    if (in_smem) vec_pair<T>(S.buf[slot][sv], j, u, v);
+    else scalar_pair<T>(edges, c * part_chunk_pairs<T>() + (long long)sv * PairVec<T>::kPairs + j, u, v);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPartThreads, 1)
+    k_degree_partition(const T *__restrict__ edges, long long m, vid_t n, int nb, unsigned long long cap,
+                       unsigned long long *__restrict__ fill, uint16_t *__restrict__ part, uint32_t *deg, DevState *st) {
+    extern __shared__ __align__(128) unsigned char part_smem[];
+    PartShared &S = *reinterpret_cast<PartShared *>(part_smem);
+    constexpr int P = PairVec<T>::kPairs;
+    constexpr long long CP = part_chunk_pairs<T>();
+    const long long nch = (m + CP - 1) / CP;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const long long G = gridDim.x;
+    auto chunk_len = [&](long long c) { return m - c * CP < CP ? m - c * CP : CP; };
+    bool inflight[2] = {false, false};  // thread 0's view of the bulk copies it issued
+    auto issue = [&](long long c, int slot) {
+        const uint32_t bytes = (uint32_t)(((unsigned long long)chunk_len(c) * 2 * sizeof(T)) & ~15ull);
+        if (bytes) {
+            mbar_arrive_tx(&S.mbar[slot], bytes);
+            bulk_load(S.buf[slot], edges + 2 * c * CP, bytes, &S.mbar[slot]);
+        } else {
+            mbar_arrive(&S.mbar[slot]);
+        }
+        inflight[slot] = true;
+    };
+    if (t == 0) {
+        mbar_init(&S.mbar[0], 1);
+        mbar_init(&S.mbar[1], 1);
+        mbar_fence_init();
+        S.abort = 0;
+    }
+    for (int i = t; i < nb; i += kPartThreads) S.hist[i] = 0;
+    __syncthreads();
+    if (t == 0) {
+        if (blockIdx.x < nch) issue(blockIdx.x, 0);
+        if (blockIdx.x + G < nch) issue(blockIdx.x + G, 1);
+    }
+    uint32_t phase[2] = {0u, 0u};
+    bool bad = false;
+    int slot = 0;
+    for (long long c = blockIdx.x; c < nch; c += G, slot ^= 1) {
+        if (mbar_wait(&S.mbar[slot], phase[slot])) {
+            phase[slot] ^= 1u;
+            if (t == 0) inflight[slot] = false;
+        } else {
+            S.abort = 1;
+        }
+        __syncthreads();
+        if (S.abort) break;
+        const long long np = chunk_len(c);
+        const int full_vecs = (int)(((unsigned long long)np * 2 * sizeof(T)) >> 4);  // vectors the copy filled
+        // ranks of this thread's endpoints within their buckets (packed u | v << 16)
+        uint32_t rk[kPartSlots * P];
+#pragma unroll
+        for (int k = 0; k < kPartSlots; k++) {
+            const int sv = t + k * kPartThreads;
+#pragma unroll
+            for (int j = 0; j < P; j++) {
+                const long long p = (long long)sv * P + j;
+                uint32_t r = 0xffffffffu;
+                if (p < np) {
+                    long long u, v;
+                    chunk_pair<T>(S, slot, edges, c, sv, j, sv < full_vecs, u, v);
+                    if ((unsigned long long)u >= n || (unsigned long long)v >= n) {
+                        bad = true;
+                    } else {
+                        const uint32_t ru = atomicAdd(&S.hist[u >> kPartBits], 1u);
+                        const uint32_t rv = atomicAdd(&S.hist[v >> kPartBits], 1u);
+                        r = ru | (rv << 16);
+                    }
+                }
+                rk[k * P + j] = r;
+            }
+        }
+        __syncthreads();
+        // exclusive scan of the bucket counts, one reservation per bucket, counts cleared
+        {
+            const uint32_t h = t < nb ? S.hist[t] : 0u;
+            uint32_t incl = h;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) S.wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t w = S.wsum[lane];
+                uint32_t wi = w;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                    if (lane >= o) wi += y;
+                }
+                S.wsum[lane] = wi - w;
+            }
+            __syncthreads();
+            const uint32_t ex = S.wsum[warp] + incl - h;
+            if (t < nb) {
+                S.loff[t] = ex;
+                S.base[t] = h ? atomicAdd(&fill[t], (unsigned long long)h) : 0ull;
+                S.hist[t] = 0u;
+            }
+            if (t == nb - 1) S.loff[nb] = ex + h;
+        }
+        __syncthreads();
+        // stage the ids within the bucket in bucket order
+#pragma unroll
+        for (int k = 0; k < kPartSlots; k++) {
+            const int sv = t + k * kPartThreads;
+#pragma unroll
+            for (int j = 0; j < P; j++) {
+                const uint32_t r = rk[k * P + j];
+                if (r == 0xffffffffu) continue;
+                long long u, v;
+                chunk_pair<T>(S, slot, edges, c, sv, j, sv < full_vecs, u, v);
+                const uint32_t bu = (uint32_t)(u >> kPartBits), bv = (uint32_t)(v >> kPartBits);
+                const uint32_t pu = S.loff[bu] + (r & 0xffffu), pv = S.loff[bv] + (r >> 16);
+                S.stage[pu] = (uint16_t)(u & (kPartBucket - 1));
+                S.skey[pu] = (uint16_t)bu;
+                S.stage[pv] = (uint16_t)(v & (kPartBucket - 1));
+                S.skey[pv] = (uint16_t)bv;
+            }
+        }
+        __syncthreads();
+        // this buffer is read: fetch the chunk after next into it
+        if (t == 0 && c + 2 * G < nch) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(c + 2 * G, slot);
+        }
+        const uint32_t total = S.loff[nb];
+        for (uint32_t i = t; i < total; i += kPartThreads) {
+            const uint32_t b = S.skey[i];
+            const unsigned long long o = S.base[b] + (i - S.loff[b]);
+            const uint16_t lid = S.stage[i];
+            if (o < cap) part[(unsigned long long)b * cap + o] = lid;
+            else atomicAdd(&deg[(b << kPartBits) | lid], 1u);
+        }
+        __syncthreads();
+    }
+    if (bad) set_err(st, kErrInvalidEdge);
+    if (S.abort && t == 0) {
+        set_err(st, kErrTimeout);
+        // leave no copy writing into shared memory after the block exits
+        for (int k = 0; k < 2; k++)
+            if (inflight[k]) mbar_wait(&S.mbar[k], phase[k]);
+    }
+}
+
+__global__ void __launch_bounds__(1024, 1)
+    k_degree_count(const uint16_t *__restrict__ part, unsigned long long cap, const unsigned long long *__restrict__ fill,
+                   vid_t n, int nb, uint32_t *deg) {
+    extern __shared__ uint32_t cnt[];  // kPartBucket counters
+    const int lane = threadIdx.x & 31;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        for (int i = threadIdx.x; i < kPartBucket; i += blockDim.x) cnt[i] = 0u;
+        __syncthreads();
+        const unsigned long long f = fill[b], len = f < cap ? f : cap;
+        const uint16_t *src = part + (unsigned long long)b * cap;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        const unsigned long long nv = len / 8;
+        for (unsigned long long w0 = threadIdx.x & ~31u; w0 < nv; w0 += blockDim.x) {
+            const unsigned long long i = w0 + lane;
+            const bool ok = i < nv;
+            const uint4 q = ok ? ld_stream(s4 + i) : make_uint4(0, 0, 0, 0);
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const uint32_t lid = (w[e >> 1] >> (16 * (e & 1))) & 0xffffu;
+                const uint32_t key = ok ? lid : 0x10000u + (uint32_t)lane;  // idle lanes match nobody
+                const unsigned peers = __match_any_sync(0xffffffffu, key);
+                if (ok && lane == __ffs(peers) - 1) atomicAdd(&cnt[lid], (uint32_t)__popc(peers));
+            }
+        }
+        for (unsigned long long i = nv * 8 + threadIdx.x; i < len; i += blockDim.x) atomicAdd(&cnt[src[i]], 1u);
+        __syncthreads();
+        const long long v0 = (long long)b << kPartBits;
+        const long long v1 = v0 + kPartBucket < (long long)n ? v0 + kPartBucket : (long long)n;
+        const bool spilled = f > cap;  // entries past cap were counted into deg directly
+        for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x)
+            deg[v] = cnt[v - v0] + (spilled ? deg[v] : 0u);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+int degree_part_buckets(vid_t n) { return (int)(((long long)n + kPartBucket - 1) >> kPartBits); }
+
+bool degree_part_ok(vid_t n, long long m) {
+    return n > 0 && degree_part_buckets(n) <= kPartMaxBuckets && m >= (1LL << 20);
+}
+
+// A bucket holds up to twice the average entries (8-entry aligned, so every
+// bucket's region starts on a 16-byte boundary).
+static unsigned long long part_cap(vid_t n, long long m) {
+    const int nb = degree_part_buckets(n);
+    const unsigned long long avg = (2ull * (unsigned long long)m + nb - 1) / nb;
+    return (2 * avg + 4096 + 7) & ~7ull;
+}
+
+size_t degree_part_scratch_bytes(vid_t n, long long m) {
+    const int nb = degree_part_buckets(n);
+    return 256 + (size_t)nb * 8 + (size_t)nb * part_cap(n, m) * 2;
+}
+
+template <typename T>
+void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t *deg, void *scratch, DevState *st,
+                               int num_sms, cudaStream_t s) {
+    const int nb = degree_part_buckets(n);
+    const unsigned long long cap = part_cap(n, m);
+    unsigned long long *fill = reinterpret_cast<unsigned long long *>(scratch);
+    uint16_t *part = reinterpret_cast<uint16_t *>(static_cast<char *>(scratch) + 256 + (((size_t)nb * 8 + 255) & ~255ull));
+    cudaMemsetAsync(fill, 0, (size_t)nb * 8, s);
+    cudaMemsetAsync(deg, 0, (size_t)n * 4, s);
+    const long long nch = (m + part_chunk_pairs<T>() - 1) / part_chunk_pairs<T>();
+    const int grid = (int)(nch < num_sms ? nch : num_sms);
+    if (grid > 0)
+        k_degree_partition<T><<<grid, kPartThreads, sizeof(PartShared), s>>>((const T *)edges, m, n, nb, cap, fill,
+                                                                            part, deg, st);
+    const int cgrid = nb < num_sms ? nb : num_sms;
+    k_degree_count<<<cgrid, 1024, kPartBucket * sizeof(uint32_t), s>>>(part, cap, fill, n, nb, deg);
+}
+template void launch_degree_partitioned<int32_t>(const void *, long long, vid_t, uint32_t *, void *, DevState *, int,
+                                                 cudaStream_t);
+template void launch_degree_partitioned<int64_t>(const void *, long long, vid_t, uint32_t *, void *, DevState *, int,
+                                                 cudaStream_t);
+
+cudaError_t degree_part_setup() {
+    cudaError_t e = cudaFuncSetAttribute(k_degree_partition<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(PartShared));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_degree_partition<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(PartShared));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_degree_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kPartBucket * (int)sizeof(uint32_t));
+    return e;
+}
+
+}  // namespace ccg
