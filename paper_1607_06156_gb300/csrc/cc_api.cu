@@ -50,7 +50,7 @@ struct cc_ctx {
     long long tsv_cap = 0;
     Buf deg, parent, hooked, ebuf0, ebuf1, hist, ovf, ks_xs, ks_cnt, ks_cum, ks_lnx, ks_Dc, ks_Ac, ks_Zc, ks_Df, chunk_nz,
         chunk_mass, st, bk_count, bk_off, bk_cursor;
-    Buf dpart;  // endpoints partitioned by vertex bucket (partitioned degree pass)
+    Buf dpart;  // endpoints partitioned into vertex windows (degree pass of graphs with n > 2^25)
     unsigned long long ovf_cap = 0, ks_cap = 0;
     // BFS workspace
     size_t bn_cap = 0, bm_cap = 0;
@@ -496,9 +496,9 @@ void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaSt
     }
     cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s);
     if (degree_part_ok(n, m) && ctx->dpart.bytes >= degree_part_scratch_bytes(n, m)) {
-        Scope sc(ctx, CC_K_DEGREE, s, 2);
+        Scope sc(ctx, CC_K_DEGREE, s, 1 + degree_part_buckets(n));
         launch_degree_partitioned<T>(edges, m, n, as<uint32_t>(ctx->deg), ctx->dpart.p, as<DevState>(ctx->st),
-                                     ctx->num_sms, s);
+                                     ctx->num_sms, ctx->grid, s);
     } else if (degree_uses_hubs(m) && ctx->ebuf1.bytes >= degree_hubs_scratch_bytes()) {
         cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
         Scope sc(ctx, CC_K_DEGREE, s, 5);

@@ -94,15 +94,17 @@ void launch_hist_widen(const uint32_t *hist, const uint32_t *ovf, unsigned long 
                        uint64_t *out, long long len, int grid, cudaStream_t s);
 void launch_hist_narrow(const uint64_t *in, long long len, uint32_t *hist, DevState *st, int grid, cudaStream_t s);
 
-// k_degree_part.cu: degree pass as a partition of the endpoints by vertex
-// bucket (bulk copies into shared memory) and a count per bucket in shared
-// memory; for 2^20 <= m and n <= 2^25. scratch: degree_part_scratch_bytes.
+// k_degree_part.cu: degree pass for n > 2^25 (counts out of L2): the
+// endpoints partitioned into windows of 2^23 vertices (bulk copies into
+// shared memory), then counted window by window with L2 atomics (one launch
+// per window: degree_part_buckets(n) + 1 launches).
+// scratch: degree_part_scratch_bytes; grid: blocks of the window count pass.
 int degree_part_buckets(vid_t n);
 bool degree_part_ok(vid_t n, long long m);
 size_t degree_part_scratch_bytes(vid_t n, long long m);
 template <typename T>
 void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t *deg, void *scratch, DevState *st,
-                               int num_sms, cudaStream_t s);
+                               int num_sms, int grid, cudaStream_t s);
 cudaError_t degree_part_setup();
 
 // k_tuple_sv.cu: the paper's sort-based SV (Section 3.1) as an ablation, with

@@ -1,39 +1,40 @@
-// Degree pass (Section 3.2, Algorithm 2 line 1) as a partition of the pair
-// endpoints by vertex bucket, then a count per bucket in shared memory.
+// Degree pass (Section 3.2, Algorithm 2 line 1) for graphs whose count
+// array does not fit in L2 (n > 2^25: 128 MB of counts and more).
 //
-// deg[v] = number of pair endpoints equal to v. Counting them with one
-// atomic per endpoint is bound by the rate of scattered L2 atomics (and, once
-// the count array leaves L2, by DRAM read-modify-writes). Here the endpoints
-// are moved instead of counted in place:
+// deg[v] = number of pair endpoints equal to v. With one atomic per
+// endpoint, a count array out of L2 turns every endpoint into a DRAM
+// read-modify-write of a 32-byte sector at a random address (measured on
+// GB300: 35 G increments/s). Here the endpoints are first moved into windows
+// of 2^23 vertices, so that each window's counts (32 MB) stay in L2 while
+// they are incremented:
 //
 //  k_degree_partition  one CTA per SM streams 64 KB chunks of pairs into
 //                      shared memory with 1-D bulk copies (cp.async.bulk,
 //                      completion on an mbarrier, two buffers in flight).
-//                      Each chunk's endpoints are counting-sorted by bucket
-//                      (2^15 vertices) in shared memory; one global atomic
-//                      per bucket and chunk reserves the bucket's run, and
-//                      the 16-bit ids within the bucket are written as
-//                      contiguous runs. A bucket holds at most `cap`
-//                      entries; endpoints past it (a bucket far above the
-//                      average) are counted with global atomics instead, so
-//                      the counts stay exact for any input.
-//  k_degree_count      one CTA per bucket: 2^15 counters in 128 KB of shared
-//                      memory, the bucket's entries added with shared atomics
-//                      (lanes of a warp that hold the same vertex merged with
-//                      __match_any_sync, so hubs do not serialise), then the
-//                      bucket's slice of deg written once.
+//                      Each chunk's endpoints are counting-sorted by window
+//                      in shared memory; one global atomic per window and
+//                      chunk reserves the window's run, and each warp writes
+//                      whole runs of the ids within the window (32-bit). A
+//                      window holds at most `cap` entries; endpoints past it
+//                      are counted with global atomics directly, so the
+//                      counts stay exact for any input.
+//  k_degree_window     one launch per window, one L2 atomic (RED) per
+//                      entry: the whole grid works on one window's counts at
+//                      a time. (A single grid-stride sweep over all windows
+//                      in order measured 9.9 ms on the grid + chains graph
+//                      with windows of 2^24: warps drift across window
+//                      boundaries, and two live windows fill the L2.)
 //
 // HBM traffic per call: the pairs once (2wm bytes), the entries written and
-// read back (2 x 4m bytes), deg written (4n).
+// read back (2 x 8m bytes), deg zeroed and written back (8n).
 #include "cc_common.cuh"
 #include "cc_kernels.h"
 
 namespace ccg {
 
 constexpr int kPartThreads = 1024;
-constexpr int kPartBits = 15;
-constexpr int kPartBucket = 1 << kPartBits;
-constexpr int kPartMaxBuckets = 1024;                           // n <= 2^25
+constexpr int kPartBits = 23;                                   // vertices per window: 2^23 (32 MB of counts)
+constexpr int kPartMaxBuckets = 512;                            // n < 2^32
 constexpr int kPartChunkBytes = 1 << 16;
 constexpr int kPartSlots = kPartChunkBytes / 16 / kPartThreads;  // 16-byte vectors per thread and chunk
 constexpr int kPartMaxEnd = kPartChunkBytes / 8 * 2;             // endpoints of a chunk of int32 pairs
@@ -41,8 +42,7 @@ constexpr unsigned long long kWaitNs = 1000000000ull;           // bounded mbarr
 
 struct __align__(128) PartShared {
     int4 buf[2][kPartChunkBytes / 16];  // two chunks of pairs (bulk-copy destinations)
-    uint16_t stage[kPartMaxEnd];        // ids within the bucket, sorted by bucket
-    uint16_t skey[kPartMaxEnd];         // the bucket of each staged id
+    uint32_t stage[kPartMaxEnd];        // ids within the window, sorted by window
     uint32_t hist[kPartMaxBuckets];
     uint32_t loff[kPartMaxBuckets + 1];
     unsigned long long base[kPartMaxBuckets];
@@ -117,11 +117,12 @@ __device__ __forceinline__ void chunk_pair(const PartShared &S, int slot, const 
 template <typename T>
 __global__ void __launch_bounds__(kPartThreads, 1)
     k_degree_partition(const T *__restrict__ edges, long long m, vid_t n, int nb, unsigned long long cap,
-                       unsigned long long *__restrict__ fill, uint16_t *__restrict__ part, uint32_t *deg, DevState *st) {
+                       unsigned long long *__restrict__ fill, uint32_t *__restrict__ part, uint32_t *deg, DevState *st) {
     extern __shared__ __align__(128) unsigned char part_smem[];
     PartShared &S = *reinterpret_cast<PartShared *>(part_smem);
     constexpr int P = PairVec<T>::kPairs;
     constexpr long long CP = part_chunk_pairs<T>();
+    constexpr uint32_t kLow = (1u << kPartBits) - 1u;
     const long long nch = (m + CP - 1) / CP;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const long long G = gridDim.x;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kPartThreads, 1)
         if (S.abort) break;
         const long long np = chunk_len(c);
         const int full_vecs = (int)(((unsigned long long)np * 2 * sizeof(T)) >> 4);  // vectors the copy filled
-        // ranks of this thread's endpoints within their buckets (packed u | v << 16)
+        // ranks of this thread's endpoints within their windows (packed u | v << 16)
         uint32_t rk[kPartSlots * P];
 #pragma unroll
         for (int k = 0; k < kPartSlots; k++) {
@@ -187,8 +188,9 @@ __global__ void __launch_bounds__(kPartThreads, 1)
             }
         }
         __syncthreads();
-        // exclusive scan of the bucket counts, one reservation per bucket, counts cleared
-        {
+        // exclusive scan of the window counts (nb <= 512: the first 16 warps),
+        // one reservation per window, counts cleared
+        if (warp < kPartMaxBuckets / 32) {
             const uint32_t h = t < nb ? S.hist[t] : 0u;
             uint32_t incl = h;
 #pragma unroll
@@ -197,28 +199,28 @@ __global__ void __launch_bounds__(kPartThreads, 1)
                 if (lane >= o) incl += y;
             }
             if (lane == 31) S.wsum[warp] = incl;
-            __syncthreads();
-            if (warp == 0) {
-                const uint32_t w = S.wsum[lane];
-                uint32_t wi = w;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-                    if (lane >= o) wi += y;
-                }
-                S.wsum[lane] = wi - w;
-            }
-            __syncthreads();
-            const uint32_t ex = S.wsum[warp] + incl - h;
+            S.loff[t] = incl - h;  // within the warp; the warp offsets follow
             if (t < nb) {
-                S.loff[t] = ex;
                 S.base[t] = h ? atomicAdd(&fill[t], (unsigned long long)h) : 0ull;
                 S.hist[t] = 0u;
             }
-            if (t == nb - 1) S.loff[nb] = ex + h;
         }
         __syncthreads();
-        // stage the ids within the bucket in bucket order
+        if (warp == 0) {
+            const uint32_t w = lane < kPartMaxBuckets / 32 ? S.wsum[lane] : 0u;
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            if (lane < kPartMaxBuckets / 32) S.wsum[lane] = wi - w;
+            if (lane == kPartMaxBuckets / 32 - 1) S.loff[kPartMaxBuckets] = wi;
+        }
+        __syncthreads();
+        if (t < kPartMaxBuckets) S.loff[t] += S.wsum[warp];
+        __syncthreads();
+        // stage the ids within the window in window order
 #pragma unroll
         for (int k = 0; k < kPartSlots; k++) {
             const int sv = t + k * kPartThreads;
@@ -228,12 +230,8 @@ __global__ void __launch_bounds__(kPartThreads, 1)
                 if (r == 0xffffffffu) continue;
                 long long u, v;
                 chunk_pair<T>(S, slot, edges, c, sv, j, sv < full_vecs, u, v);
-                const uint32_t bu = (uint32_t)(u >> kPartBits), bv = (uint32_t)(v >> kPartBits);
-                const uint32_t pu = S.loff[bu] + (r & 0xffffu), pv = S.loff[bv] + (r >> 16);
-                S.stage[pu] = (uint16_t)(u & (kPartBucket - 1));
-                S.skey[pu] = (uint16_t)bu;
-                S.stage[pv] = (uint16_t)(v & (kPartBucket - 1));
-                S.skey[pv] = (uint16_t)bv;
+                S.stage[S.loff[u >> kPartBits] + (r & 0xffffu)] = (uint32_t)u & kLow;
+                S.stage[S.loff[v >> kPartBits] + (r >> 16)] = (uint32_t)v & kLow;
             }
         }
         __syncthreads();
@@ -242,13 +240,16 @@ __global__ void __launch_bounds__(kPartThreads, 1)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(c + 2 * G, slot);
         }
-        const uint32_t total = S.loff[nb];
-        for (uint32_t i = t; i < total; i += kPartThreads) {
-            const uint32_t b = S.skey[i];
-            const unsigned long long o = S.base[b] + (i - S.loff[b]);
-            const uint16_t lid = S.stage[i];
-            if (o < cap) part[(unsigned long long)b * cap + o] = lid;
-            else atomicAdd(&deg[(b << kPartBits) | lid], 1u);
+        // each warp writes whole runs: windows warp, warp + 32, ...
+        for (int b = warp; b < nb; b += kPartThreads / 32) {
+            const uint32_t r0 = S.loff[b], r1 = S.loff[b + 1];
+            const unsigned long long o0 = S.base[b];
+            for (uint32_t i = r0 + lane; i < r1; i += 32) {
+                const unsigned long long o = o0 + (i - r0);
+                const uint32_t lid = S.stage[i];
+                if (o < cap) part[(unsigned long long)b * cap + o] = lid;
+                else atomicAdd(&deg[((unsigned long long)b << kPartBits) | lid], 1u);
+            }
         }
         __syncthreads();
     }
@@ -261,83 +262,67 @@ __global__ void __launch_bounds__(kPartThreads, 1)
     }
 }
 
-__global__ void __launch_bounds__(1024, 1)
-    k_degree_count(const uint16_t *__restrict__ part, unsigned long long cap, const unsigned long long *__restrict__ fill,
-                   vid_t n, int nb, uint32_t *deg) {
-    extern __shared__ uint32_t cnt[];  // kPartBucket counters
-    const int lane = threadIdx.x & 31;
-    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
-        for (int i = threadIdx.x; i < kPartBucket; i += blockDim.x) cnt[i] = 0u;
-        __syncthreads();
-        const unsigned long long f = fill[b], len = f < cap ? f : cap;
-        const uint16_t *src = part + (unsigned long long)b * cap;
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-        const unsigned long long nv = len / 8;
-        for (unsigned long long w0 = threadIdx.x & ~31u; w0 < nv; w0 += blockDim.x) {
-            const unsigned long long i = w0 + lane;
-            const bool ok = i < nv;
-            const uint4 q = ok ? ld_stream(s4 + i) : make_uint4(0, 0, 0, 0);
-            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int e = 0; e < 8; e++) {
-                const uint32_t lid = (w[e >> 1] >> (16 * (e & 1))) & 0xffffu;
-                const uint32_t key = ok ? lid : 0x10000u + (uint32_t)lane;  // idle lanes match nobody
-                const unsigned peers = __match_any_sync(0xffffffffu, key);
-                if (ok && lane == __ffs(peers) - 1) atomicAdd(&cnt[lid], (uint32_t)__popc(peers));
-            }
-        }
-        for (unsigned long long i = nv * 8 + threadIdx.x; i < len; i += blockDim.x) atomicAdd(&cnt[src[i]], 1u);
-        __syncthreads();
-        const long long v0 = (long long)b << kPartBits;
-        const long long v1 = v0 + kPartBucket < (long long)n ? v0 + kPartBucket : (long long)n;
-        const bool spilled = f > cap;  // entries past cap were counted into deg directly
-        for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x)
-            deg[v] = cnt[v - v0] + (spilled ? deg[v] : 0u);
-        __syncthreads();
+// One RED per entry of window b (its counts stay in L2 during the launch).
+__global__ void __launch_bounds__(kBlock) k_degree_window(const uint32_t *__restrict__ part, unsigned long long cap,
+                                                          const unsigned long long *__restrict__ fill, int b,
+                                                          uint32_t *deg) {
+    const unsigned long long f = fill[b], len = f < cap ? f : cap;
+    const uint4 *p4 = reinterpret_cast<const uint4 *>(part + (unsigned long long)b * cap);
+    uint32_t *d = deg + ((unsigned long long)b << kPartBits);
+    const unsigned long long nv = len / 4;
+    for (unsigned long long k = gtid(); k < nv; k += gstride()) {
+        const uint4 q = ld_stream(p4 + k);
+        atomicAdd(&d[q.x], 1u);
+        atomicAdd(&d[q.y], 1u);
+        atomicAdd(&d[q.z], 1u);
+        atomicAdd(&d[q.w], 1u);
     }
+    const unsigned long long i = nv * 4 + gtid();
+    if (i < len) atomicAdd(&d[part[(unsigned long long)b * cap + i]], 1u);
 }
 
 // ---------------------------------------------------------------------------
-int degree_part_buckets(vid_t n) { return (int)(((long long)n + kPartBucket - 1) >> kPartBits); }
+int degree_part_buckets(vid_t n) { return (int)(((long long)n + (1LL << kPartBits) - 1) >> kPartBits); }
 
-bool degree_part_ok(vid_t n, long long m) {
-    return n > 0 && degree_part_buckets(n) <= kPartMaxBuckets && m >= (1LL << 20);
-}
+bool degree_part_ok(vid_t n, long long m) { return n > (1u << 25) && m >= (1LL << 20); }
 
-// A bucket holds up to twice the average entries (8-entry aligned, so every
-// bucket's region starts on a 16-byte boundary).
+// A window holds up to twice the average entries (a multiple of 4, so every
+// window's region starts on a 16-byte boundary).
 static unsigned long long part_cap(vid_t n, long long m) {
     const int nb = degree_part_buckets(n);
     const unsigned long long avg = (2ull * (unsigned long long)m + nb - 1) / nb;
-    return (2 * avg + 4096 + 7) & ~7ull;
+    return (2 * avg + 4096 + 3) & ~3ull;
 }
+
+// scratch layout: fill[nb] (64-bit reservation counters) at 0, the window
+// regions (nb x cap 32-bit ids) from part_offset(nb)
+static size_t part_offset(int nb) { return 256 + (((size_t)nb * 8 + 255) & ~(size_t)255); }
 
 size_t degree_part_scratch_bytes(vid_t n, long long m) {
     const int nb = degree_part_buckets(n);
-    return 256 + (size_t)nb * 8 + (size_t)nb * part_cap(n, m) * 2;
+    return part_offset(nb) + (size_t)nb * part_cap(n, m) * 4;
 }
 
 template <typename T>
 void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t *deg, void *scratch, DevState *st,
-                               int num_sms, cudaStream_t s) {
+                               int num_sms, int grid, cudaStream_t s) {
     const int nb = degree_part_buckets(n);
     const unsigned long long cap = part_cap(n, m);
     unsigned long long *fill = reinterpret_cast<unsigned long long *>(scratch);
-    uint16_t *part = reinterpret_cast<uint16_t *>(static_cast<char *>(scratch) + 256 + (((size_t)nb * 8 + 255) & ~255ull));
+    uint32_t *part = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + part_offset(nb));
     cudaMemsetAsync(fill, 0, (size_t)nb * 8, s);
     cudaMemsetAsync(deg, 0, (size_t)n * 4, s);
     const long long nch = (m + part_chunk_pairs<T>() - 1) / part_chunk_pairs<T>();
-    const int grid = (int)(nch < num_sms ? nch : num_sms);
-    if (grid > 0)
-        k_degree_partition<T><<<grid, kPartThreads, sizeof(PartShared), s>>>((const T *)edges, m, n, nb, cap, fill,
-                                                                            part, deg, st);
-    const int cgrid = nb < num_sms ? nb : num_sms;
-    k_degree_count<<<cgrid, 1024, kPartBucket * sizeof(uint32_t), s>>>(part, cap, fill, n, nb, deg);
+    const int pgrid = (int)(nch < num_sms ? nch : num_sms);
+    if (pgrid > 0)
+        k_degree_partition<T><<<pgrid, kPartThreads, sizeof(PartShared), s>>>((const T *)edges, m, n, nb, cap, fill,
+                                                                             part, deg, st);
+    for (int b = 0; b < nb; b++) k_degree_window<<<grid, kBlock, 0, s>>>(part, cap, fill, b, deg);
 }
 template void launch_degree_partitioned<int32_t>(const void *, long long, vid_t, uint32_t *, void *, DevState *, int,
-                                                 cudaStream_t);
+                                                 int, cudaStream_t);
 template void launch_degree_partitioned<int64_t>(const void *, long long, vid_t, uint32_t *, void *, DevState *, int,
-                                                 cudaStream_t);
+                                                 int, cudaStream_t);
 
 cudaError_t degree_part_setup() {
     cudaError_t e = cudaFuncSetAttribute(k_degree_partition<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -345,9 +330,6 @@ cudaError_t degree_part_setup() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_degree_partition<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(PartShared));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_degree_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kPartBucket * (int)sizeof(uint32_t));
     return e;
 }
 

@@ -297,26 +297,58 @@ def test_edge_list_bfs_matches_csr_bfs_visited_set():
     assert a["bfs_visited"] == b["bfs_visited"] and a["comp_min"] == b["comp_min"]
 
 
-@pytest.mark.parametrize("id_bytes,extra", [(4, 0), (4, 3), (8, 1)])
-def test_hub_aware_degree_pass(id_bytes, extra):
-    """m >= 2^24 takes the hub-aware degree pass (prefix counts pick the hubs,
-    the rest is counted with hubs in shared memory); counts stay exact."""
+def _degree_check(e, n, id_bytes):
     torch = torch_cuda()
     import paper_1607_06156_gb300 as cc
 
+    deg_o = oracle.degrees(e, n)
+    eng = cc.Engine(id_bytes=id_bytes)
+    deg, hist = eng.degree_distribution(torch.from_numpy(e).cuda(), n, hist_len=int(deg_o.max()) + 1)
+    assert np.array_equal(deg.cpu().numpy().astype(np.int64), deg_o)
+    assert np.array_equal(hist.cpu().numpy(), oracle.histogram(deg_o))
+    eng.close()
+
+
+@pytest.mark.parametrize("id_bytes,m,n", [
+    (4, (1 << 20) + 1, (1 << 25) + 1),        # 5 windows; a last chunk of one int32 pair (a bulk copy of 0 bytes)
+    (4, 1 << 21, 1 << 26),                    # a whole number of 8,192-pair chunks
+    (4, (1 << 21) + 3, (1 << 28) + 7),        # 33 windows of 2^23 vertices, the last one short
+    (8, (1 << 20) + 4097, (1 << 25) + 100003),  # int64: 4,096-pair chunks and a ragged last one
+])
+def test_partitioned_degree_pass_chunks_and_windows(id_bytes, m, n):
+    """The degree pass of graphs with n > 2^25 (endpoints partitioned into
+    windows of 2^23 vertices, then counted window by window): chunk and
+    window boundaries, counts exact."""
+    rng = np.random.default_rng(m % 1000 + n % 1000)
+    e = rng.integers(0, n, size=(m, 2)).astype(np.int32 if id_bytes == 4 else np.int64)
+    e[::97, 1] = e[::97, 0]  # self-loops
+    _degree_check(e, n, id_bytes)
+
+
+def test_partitioned_degree_pass_window_overflow():
+    """One vertex is an endpoint of every pair: its window holds more than
+    twice the average entries, and the entries past its capacity are counted
+    with global atomics."""
+    n, m = (1 << 25) + 1, (1 << 21) + 9
+    rng = np.random.default_rng(43)
+    e = np.stack([np.full(m, 12345), rng.integers(0, n, size=m)], axis=1).astype(np.int32)
+    _degree_check(e, n, 4)
+    assert_labels_match(e, n, routes=("auto",))
+
+
+@pytest.mark.parametrize("id_bytes,extra", [(4, 0), (4, 3), (8, 1)])
+def test_hub_aware_degree_pass(id_bytes, extra):
+    """m >= 2^24 with n <= 2^25 takes the hub-aware degree pass (prefix counts
+    pick the hubs, the rest is counted with hubs in shared memory); counts
+    stay exact."""
     g = gg.rmat(seed=31, scale=20, edge_factor=16, m=(1 << 24) + extra, id_bytes=id_bytes)
     # hubs whose pairs mostly come after the prefix
     hub = np.stack([np.full(300000, 77), np.arange(300000) * 7 % g.n], axis=1).astype(g.edges.dtype)
     e = np.concatenate([g.edges, hub])
-    deg_o = oracle.degrees(e, g.n)
-    eng = cc.Engine(id_bytes=id_bytes)
-    deg, hist = eng.degree_distribution(torch.from_numpy(e).cuda(), g.n, hist_len=int(deg_o.max()) + 1)
-    assert np.array_equal(deg.cpu().numpy().astype(np.int64), deg_o)
-    assert np.array_equal(hist.cpu().numpy(), oracle.histogram(deg_o))
-    eng.close()
+    _degree_check(e, g.n, id_bytes)
     got, st = run_engine(e, g.n, route="auto")
     assert np.array_equal(got, oracle.cc_labels(e, g.n, cross_check=False))
-    assert st["max_degree"] == int(deg_o.max())
+    assert st["max_degree"] == int(oracle.degrees(e, g.n).max())
 
 
 @pytest.mark.gpu
