@@ -460,15 +460,15 @@ def timed_calls(torch, eng, call, steps: int, stream, dist=None, device=None) ->
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches = 0
     e0.record(stream)
     for _ in range(steps):
-        call()
-        launches += eng.stats()["launches"]
+        call()  # stream-ordered: no host wait between the calls
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    # kernels of one call (every call of a step takes the same route), read after the timed region
+    launches = eng.stats()["launches"] * steps
     return max_over_ranks(e0.elapsed_time(e1), dist, device), launches
 
 

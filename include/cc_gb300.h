@@ -32,9 +32,13 @@
  *    stores); labels are written with the same id width as the edges.
  *  - Errors: argument errors are returned immediately and nothing is
  *    enqueued. Errors the device detects (an id outside [0, n), a run that
- *    exceeds the iteration cap) are recorded in the context. The labelling
- *    calls synchronise their stream and return them; cc_get_stats() returns
- *    the last one again. The contents of the outputs are then unspecified.
+ *    exceeds the iteration cap) go to a device status word. cc_labels is
+ *    stream-ordered: the word is copied to pinned host memory at the end of
+ *    the call's stream work, and cc_get_stats() (which waits for the stream)
+ *    returns it; the next cc_labels call returns it once if that work has
+ *    finished by then; with options.debug_checks the call waits and returns
+ *    it. The other labelling calls wait for their stream and return it. The
+ *    contents of the outputs are then unspecified.
  *  - A context is not thread safe: use one context per host thread/stream.
  */
 #ifndef CC_GB300_H
@@ -82,7 +86,7 @@ typedef struct {
     int ks_min_distinct;    /* fewest distinct degrees in a candidate tail; default 3 */
     int max_iters;          /* SV iteration cap; 0 = default 64 + 4*ceil(log2 n) */
     int bfs_cutoff_levels;  /* stop BFS after this many levels; 0 = run to completion */
-    int debug_checks;       /* reserved: cc_labels always returns device-detected errors */
+    int debug_checks;       /* 1: cc_labels waits for its stream and returns the device status */
     int fault_inject;       /* CC_FAULT_* bits */
     double ks_min_span;     /* a candidate tail must reach max degree >= ks_min_span * xmin; default 10 */
     int profile;            /* 1: time every kernel class with CUDA events (cc_stats.kernel_ms) */
@@ -180,9 +184,21 @@ cc_status cc_destroy(cc_ctx *ctx);
  *   m              pairs, m >= 0 (m = 0 gives labels_out[v] = v)
  *   labels_out_dev [n] ids of id_bytes each (device, 16-byte aligned);
  *                  labels_out[v] = min id of v's component
- * The call synchronises `stream` internally a few times (to read the route
- * and the active-pair counts); everything else is enqueued. On return the
- * labels are complete on `stream`.
+ * Stream-ordered (options.profile = 0): every decision of the route - the
+ * K-S route (or the learned one), the BFS levels and their direction, the
+ * SV iterations - is taken on the device by conditional nodes of one CUDA
+ * graph, which the context captures once per set of arguments, options and
+ * workspace and then launches on `stream`. The call returns without waiting
+ * for the device; the labels are complete when `stream` reaches that point.
+ * If `stream` is being captured into a CUDA graph, the work is captured into
+ * the caller's graph instead (replays may change the contents of edges_dev,
+ * not n, m or the pointers); a capture needs a workspace already sized by an
+ * earlier call of at least that size (else CC_ERR_UNSUPPORTED, nothing
+ * enqueued) and options.profile = 0.
+ * With options.profile = 1 the route is driven from the host (it waits on
+ * `stream` to read the route and the active-pair counts) and every kernel
+ * class is timed with CUDA events; the labels are the same.
+ * Device-detected errors: see the conventions above.
  */
 cc_status cc_labels(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, void *labels_out_dev, void *stream);
 
@@ -424,7 +440,8 @@ cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int6
                                   int64_t *xmin_host, int64_t *ncand_host, int32_t *route_host, int64_t *seed_host,
                                   void *stream);
 
-/* Statistics of the last cc_labels call; synchronises its stream. Returns the recorded device status. */
+/* Statistics of the last cc_labels call; waits for its stream. Returns the device status of that call.
+ * After a stream-ordered call the per-stage times other than ms_total are 0 (they need options.profile). */
 cc_status cc_get_stats(cc_ctx *ctx, cc_stats *out);
 
 /* Static, human-readable description of a status. */

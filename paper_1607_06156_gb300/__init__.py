@@ -246,7 +246,11 @@ class Engine:
 
     # ----- torch conveniences -----
     def labels(self, edges, n: int, out=None, stream=None):
-        """Component labels (min vertex id per component) of a device edge tensor [m, 2]."""
+        """Component labels (min vertex id per component) of a device edge tensor [m, 2].
+
+        Stream-ordered: returns once the work is enqueued on `stream` (the
+        current stream by default). Errors found on the device are reported
+        by check() / stats(), or by this call with debug_checks=1."""
         import torch
 
         m = _pairs(edges, self._opt.id_bytes, self.device)
@@ -404,9 +408,18 @@ class Engine:
         return {f: getattr(r, f) for f, _ in L2Rates._fields_}
 
     def stats(self) -> dict:
+        """Statistics of the last call (waits for its stream)."""
         s = Stats()
         lib().cc_get_stats(self._h, ctypes.byref(s))
         return s.as_dict()
+
+    def check(self) -> None:
+        """Waits for the last call and raises its device-detected error, if any
+        (cc_labels is stream-ordered: an id outside [0, n) or a run past the
+        iteration cap is reported here, by the next call, or by the call
+        itself with the debug_checks option)."""
+        s = Stats()
+        _check(lib().cc_get_stats(self._h, ctypes.byref(s)), "cc_labels (device status)")
 
 
 def _mlp_batch(params, X) -> int:

@@ -87,7 +87,26 @@ struct cc_ctx {
         GraphKey key{};
     };
     LoopGraph g_single, g_batch;
-    cudaStream_t cap_s = nullptr, cap_s2 = nullptr;  // private capture streams
+    cudaStream_t cap_s = nullptr, cap_s2 = nullptr, cap_s3 = nullptr;  // private capture streams
+    // stream-ordered cc_labels: the whole route as one cached graph, keyed by
+    // its arguments, workspace and options, with the host-side facts that
+    // turn the device state into statistics
+    struct RouteGraph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<unsigned char> key;
+        long long static_launches = 0;  // kernels outside the conditional bodies
+        long long bfs_launches = 0;     // kernels of the BFS branch outside its level loop
+        long long unsure_launches = 0;  // kernels of the learned policy's exact-prediction branch
+        int level_launches = 0;         // kernels per BFS level
+        int sample_stride = 1;          // SV front end stride
+        bool edge_bfs = false;          // the BFS branch is the edge-list BFS
+    } g_route;
+    RouteGraph g_capture;               // the same facts for a call captured into the caller's graph
+    const RouteGraph *rg_last = nullptr; // the facts of the last graph-mode call
+    cudaEvent_t ev_done = nullptr;      // after the device status word of the last graph-mode call
+    bool async_outstanding = false;     // that call's status word has not been reported yet
+    bool graph_last = false;            // the last labelling call ran the graph path
+    bool capturing = false;             // enqueueing into the caller's capture: no allocation
     // side stream of the speculative first SV pass, with its fork and join events
     cudaStream_t side_s = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -127,6 +146,8 @@ cc_status cuda_status(cudaError_t e) {
 cc_status buf_reserve(cc_ctx *ctx, Buf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return CC_OK;
+    // inside the caller's stream capture the workspace must already be large enough
+    if (ctx->capturing) return CC_ERR_UNSUPPORTED;
     if (b.p) {
         cudaFree(b.p);
         b.p = nullptr;
@@ -1191,6 +1212,387 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
 }
 
 
+// ---------------------------------------------------------------------------
+// Stream-ordered cc_labels (options.profile == 0). The whole route of
+// Algorithm 2 is one CUDA graph in which the device takes every decision the
+// host loop takes in the profiled path:
+//   * the SV passes that need no route (parent init, the first pass or the
+//     sampling front end, SV iteration 1 over the pairs) run speculatively
+//     on a side stream while the degree pass and the K-S fit run (the fit on
+//     a highest-priority stream); the learned policy runs its sampled
+//     features first, and an IF node runs the exact degree pass and the fit
+//     only when the network is unsure;
+//   * k_route_decide sets an IF node: the BFS branch (the CSR build and the
+//     direction-optimizing BFS, or the edge-list BFS, each level one
+//     iteration of a WHILE node; then the visited minimum, the parent
+//     array and the first SV pass over the pairs the BFS left active);
+//   * the SV iterations over the compacted list are a WHILE node that starts
+//     after whichever iteration the route left in DevState;
+//   * the labels, then a copy of the device state (status word, route,
+//     counts) into pinned host memory.
+// No host thread waits. The graph is captured once per key (arguments,
+// workspace, options) on private streams and launched on the caller's
+// stream; if the caller's stream is being captured, the same work is
+// captured straight into the caller's graph.
+
+cc_status ensure_streams(cc_ctx *ctx) {
+    int least = 0, greatest = 0;
+    CU_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    if (!ctx->side_s) CU_TRY(cudaStreamCreateWithPriority(&ctx->side_s, cudaStreamNonBlocking, least));
+    if (!ctx->fit_s) CU_TRY(cudaStreamCreateWithPriority(&ctx->fit_s, cudaStreamNonBlocking, greatest));
+    if (!ctx->cap_s) CU_TRY(cudaStreamCreateWithFlags(&ctx->cap_s, cudaStreamNonBlocking));
+    if (!ctx->cap_s2) CU_TRY(cudaStreamCreateWithFlags(&ctx->cap_s2, cudaStreamNonBlocking));
+    if (!ctx->cap_s3) CU_TRY(cudaStreamCreateWithFlags(&ctx->cap_s3, cudaStreamNonBlocking));
+    cudaEvent_t *evs[] = {&ctx->ev_fork, &ctx->ev_join, &ctx->ev_fit, &ctx->ev_done};
+    for (cudaEvent_t *e : evs)
+        if (!*e) CU_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return CC_OK;
+}
+
+// A conditional handle in the graph `cs` is capturing into.
+cc_status cond_handle(cudaStream_t cs, cudaGraphConditionalHandle *h) {
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    CU_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, &ed, &nd));
+    if (cst != cudaStreamCaptureStatusActive) return CC_ERR_CUDA;
+    CU_TRY(cudaGraphConditionalHandleCreate(h, g, 0, cudaGraphCondAssignDefault));
+    return CC_OK;
+}
+
+// Appends a conditional node (IF or WHILE on handle h) to the work captured
+// on `cs` so far and captures its body on `bs` with body(bs); `cs` then
+// continues after the node.
+template <typename Body>
+cc_status cond_node(cudaStream_t cs, cudaStream_t bs, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                    Body body) {
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    CU_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, &ed, &nd));
+    if (cst != cudaStreamCaptureStatusActive) return CC_ERR_CUDA;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CU_TRY(cudaGraphAddNode(&node, g, deps, ed, nd, &cp));
+    CU_TRY(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CU_TRY(cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed));
+    const cc_status r = body(bs);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(bs, &out);
+    if (r != CC_OK) return r;
+    CU_TRY(e);
+    return CC_OK;
+}
+
+// Whether the small-graph fit (one block) serves a graph (the profiled path's rule).
+bool small_fit(vid_t n, long long m, int policy) {
+    return n <= (1u << 20) && 2 * m < 4096LL * 4097LL && policy != CC_ROUTE_FORCE_BFS;
+}
+
+// Everything the graph depends on besides the device state it reads.
+std::vector<unsigned char> route_key(cc_ctx *ctx, int tbytes, long long n, long long m, const void *edges,
+                                     void *labels, int cap) {
+    struct {
+        long long n, m;
+        const void *edges, *labels;
+        const void *bufs[24];
+        cc_options opt;
+        double min_conf;
+        int tbytes, cap, grid, have_pred;
+    } k;
+    memset(&k, 0, sizeof(k));
+    k.n = n;
+    k.m = m;
+    k.edges = edges;
+    k.labels = labels;
+    const Buf *b[] = {&ctx->deg,  &ctx->parent,  &ctx->hooked, &ctx->ebuf0,   &ctx->ebuf1, &ctx->hist,
+                      &ctx->ovf,  &ctx->st,      &ctx->dpart,  &ctx->row_ptr, &ctx->col,   &ctx->vis,
+                      &ctx->fb,   &ctx->nb,      &ctx->q0,     &ctx->q1,      &ctx->dq,    &ctx->off,
+                      &ctx->tsum, &ctx->f_vis,   &ctx->f_f0,   &ctx->f_f1,    &ctx->kb_D,  &ctx->csr_entries};
+    for (int i = 0; i < 24; i++) k.bufs[i] = b[i]->p;
+    k.opt = ctx->opt;
+    k.min_conf = ctx->pred_min_conf;
+    k.tbytes = tbytes;
+    k.cap = cap;
+    k.grid = ctx->grid;
+    k.have_pred = ctx->have_pred;
+    const unsigned char *p = reinterpret_cast<const unsigned char *>(&k);
+    return std::vector<unsigned char>(p, p + sizeof(k));
+}
+
+// Captures the route onto `cs` (capturing). Fills the host-side facts in `rg`.
+template <typename T>
+cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, void *labels, int cap, cudaStream_t cs,
+                        cc_ctx::RouteGraph &rg) {
+    DevState *st = as<DevState>(ctx->st);
+    vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
+    uint2 *eb0 = as<uint2>(ctx->ebuf0), *eb1 = as<uint2>(ctx->ebuf1);
+    const int policy = ctx->opt.route_policy;
+    const bool learned = policy == CC_ROUTE_LEARNED && ctx->have_pred;
+    const bool edge_bfs = learned || ctx->opt.bfs_mode == 1;
+    const bool bfs_ok = policy != CC_ROUTE_FORCE_SV && (edge_bfs || 2ull * (unsigned long long)m < 0xffffffffull);
+    const bool predict = policy != CC_ROUTE_FORCE_SV;
+    const bool speculate = !(policy == CC_ROUTE_FORCE_BFS && bfs_ok);
+    const bool small = !learned && small_fit(n, m, policy);
+    const float min_conf = (float)ctx->pred_min_conf;
+    const long long before = ctx->stats.launches;
+    long long direct = 0;
+    rg.edge_bfs = edge_bfs;
+    rg.level_launches = edge_bfs ? 4 : 11;
+    rg.bfs_launches = 0;
+    rg.unsure_launches = 0;
+    rg.sample_stride = 1;
+    CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), cs));
+    if (learned) {
+        launch_route_features<T>(edges, m, n, feat_scratch(ctx), st, as<float>(ctx->f_x), ctx->grid, cs);
+        mlp_infer(as<__nv_bfloat16>(ctx->pred_wb), as<float>(ctx->pred_bias), as<float>(ctx->f_x), st, cs);
+        direct += 12;
+    }
+    auto speculative = [&](cudaStream_t ss) {
+        launch_parent_init(parent, n, nullptr, 0, ctx->grid, ss);
+        direct += 1 + enqueue_first_pass<T>(ctx, edges, n, m, ss, false);
+        rg.sample_stride = ctx->stats.sv_sample_stride;
+        launch_sv_gather_tiles<T>(edges, m, n, parent, hooked, eb0, st, 1, ss);
+        launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, ss);
+        direct += 2;
+    };
+    if (speculate && predict) {
+        CU_TRY(cudaEventRecord(ctx->ev_fork, cs));
+        CU_TRY(cudaStreamWaitEvent(ctx->side_s, ctx->ev_fork, 0));
+        speculative(ctx->side_s);
+        CU_TRY(cudaEventRecord(ctx->ev_join, ctx->side_s));
+    } else if (speculate) {
+        speculative(cs);  // forced SV: the same passes, nothing to overlap
+    }
+    if (learned) {
+        cudaGraphConditionalHandle hu;
+        CC_TRY(cond_handle(cs, &hu));
+        launch_pred_unsure(st, hu, min_conf, cs);
+        direct += 1;
+        const long long b0 = ctx->stats.launches;
+        CC_TRY(cond_node(cs, ctx->cap_s2, hu, cudaGraphCondTypeIf, [&](cudaStream_t bs) -> cc_status {
+            enqueue_degree<T>(ctx, edges, n, m, bs);
+            enqueue_ks(ctx, bs, distinct_degree_bound(ctx, n, m));
+            return CC_OK;
+        }));
+        rg.unsure_launches = ctx->stats.launches - b0;
+        ctx->stats.launches = b0;
+    } else if (predict && small) {
+        CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, cs));
+        launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), st, ctx->grid, cs);
+        direct += 1;
+        CC_TRY(enqueue_small_fit(ctx, n, cs));
+    } else if (predict) {
+        enqueue_degree<T>(ctx, edges, n, m, cs);
+        if (policy == CC_ROUTE_AUTO) {
+            CU_TRY(cudaEventRecord(ctx->ev_fork, cs));
+            CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
+            enqueue_ks(ctx, ctx->fit_s, distinct_degree_bound(ctx, n, m));
+            CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
+            CU_TRY(cudaStreamWaitEvent(cs, ctx->ev_fit, 0));
+        }
+    }
+    if (speculate && predict) CU_TRY(cudaStreamWaitEvent(cs, ctx->ev_join, 0));
+    cudaGraphConditionalHandle hr = cudaGraphConditionalHandle();
+    if (bfs_ok) CC_TRY(cond_handle(cs, &hr));  // a handle only where an IF node will use it
+    launch_route_decide(st, bfs_ok ? &hr : nullptr, policy, bfs_ok ? 1 : 0, ctx->opt.bfs_cutoff_levels, min_conf,
+                        learned ? 1 : 0, cs);
+    direct += 1;
+    if (bfs_ok) {
+        CC_TRY(cond_node(cs, ctx->cap_s2, hr, cudaGraphCondTypeIf, [&](cudaStream_t bs) -> cc_status {
+            const long long nwords = ((long long)n + 31) / 32;
+            // the speculative SV iterations' counters start over
+            CU_TRY(cudaMemsetAsync(&st->kept[0], 0, offsetof(DevState, front) - offsetof(DevState, kept), bs));
+            const uint32_t *vis;
+            if (edge_bfs) {
+                uint32_t *fv = as<uint32_t>(ctx->f_vis), *f0 = as<uint32_t>(ctx->f_f0), *f1 = as<uint32_t>(ctx->f_f1);
+                CU_TRY(cudaMemsetAsync(fv, 0, (size_t)nwords * 4, bs));
+                CU_TRY(cudaMemsetAsync(f0, 0, (size_t)nwords * 4, bs));
+                cudaGraphConditionalHandle hb;
+                CC_TRY(cond_handle(bs, &hb));
+                launch_ebfsg_init(fv, f0, n, m, st, hb, bs);
+                CC_TRY(cond_node(bs, ctx->cap_s3, hb, cudaGraphCondTypeWhile, [&](cudaStream_t ls) -> cc_status {
+                    launch_ebfsg_level<T>(edges, m, eb0, eb1, n, fv, f0, f1, st, hb, ctx->grid, ls);
+                    return CC_OK;
+                }));
+                vis = fv;
+            } else {
+                uint32_t *row_ptr = as<uint32_t>(ctx->row_ptr), *deg = as<uint32_t>(ctx->deg);
+                vid_t *col = as<vid_t>(ctx->col);
+                const bool bucketed = bucketed_ok(n, (size_t)m) && ctx->csr_entries.p;
+                launch_scan_u32(deg, n, row_ptr, bucketed ? nullptr : deg, as<unsigned long long>(ctx->tsum), nullptr,
+                                row_ptr + n, bs);
+                if (bucketed)
+                    launch_csr_bucketed<T>(edges, m, n, row_ptr, col, bucket_scratch(ctx),
+                                           as<unsigned long long>(ctx->csr_entries), st, ctx->grid, bs);
+                else
+                    launch_csr_scatter<T>(edges, m, n, deg, col, ctx->grid, bs);
+                rg.bfs_launches += 3 + (bucketed ? 4 : 1);
+                uint32_t *vm = as<uint32_t>(ctx->vis);
+                CU_TRY(cudaMemsetAsync(vm, 0, (size_t)nwords * 4, bs));
+                cudaGraphConditionalHandle hb;
+                CC_TRY(cond_handle(bs, &hb));
+                launch_bfsg_init(row_ptr, n, vm, as<vid_t>(ctx->q0), st, hb, bs);
+                CC_TRY(cond_node(bs, ctx->cap_s3, hb, cudaGraphCondTypeWhile, [&](cudaStream_t ls) -> cc_status {
+                    launch_bfsg_level(n, 2ull * (unsigned long long)m, row_ptr, col, vm, as<vid_t>(ctx->q0),
+                                      as<vid_t>(ctx->q1), as<uint32_t>(ctx->fb), as<uint32_t>(ctx->nb),
+                                      as<uint32_t>(ctx->dq), as<uint32_t>(ctx->off), as<unsigned long long>(ctx->tsum),
+                                      st, hb, ctx->grid, ls);
+                    return CC_OK;
+                }));
+                vis = vm;
+            }
+            launch_popcount(vis, nwords, &st->bfs_visited, ctx->grid, bs);
+            launch_first_visited(vis, nwords, st, ctx->grid, bs);
+            launch_parent_init_st(parent, n, vis, st, ctx->grid, bs);
+            rg.bfs_launches += 1 + 3 + launch_sv_after_bfs<T>(edges, m, eb0, eb1, n, parent, vis, hooked, st, ctx->grid, bs);
+            launch_sv_shortcut(parent, hooked, st, 0, ctx->grid, bs);
+            rg.bfs_launches += 1;
+            return CC_OK;
+        }));
+    }
+    cudaGraphConditionalHandle hs;
+    CC_TRY(cond_handle(cs, &hs));
+    launch_sv_loop_init_st(st, cap, hs, cs);
+    CC_TRY(cond_node(cs, ctx->cap_s2, hs, cudaGraphCondTypeWhile, [&](cudaStream_t bs) -> cc_status {
+        launch_sv_loop_body(eb0, eb1, n, parent, hooked, st, hs, ctx->grid, bs);
+        return CC_OK;
+    }));
+    launch_finalize<T>(parent, n, labels, ctx->grid, cs);
+    direct += 2;
+    CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, hook_base), cudaMemcpyDeviceToHost, cs));
+    rg.static_launches = ctx->stats.launches - before + direct;
+    return CC_OK;
+}
+
+// Workspace of the route for every branch it may take (allocated before any capture).
+cc_status ensure_route(cc_ctx *ctx, vid_t n, long long m) {
+    const int policy = ctx->opt.route_policy;
+    const bool learned = policy == CC_ROUTE_LEARNED && ctx->have_pred;
+    if (learned || ctx->opt.bfs_mode == 1) CC_TRY(ensure_feat(ctx, n));
+    else if (policy != CC_ROUTE_FORCE_SV && 2ull * (unsigned long long)m < 0xffffffffull)
+        CC_TRY(ensure_bfs(ctx, n, (size_t)m));
+    if (!learned && small_fit(n, m, policy) && policy != CC_ROUTE_FORCE_SV) CC_TRY(ensure_batch_route(ctx, 1, 1));
+    return CC_OK;
+}
+
+// Statistics of a graph-mode call from the device state copied to h_st.
+void stats_from_device(cc_ctx *ctx) {
+    const DevState *h = ctx->h_st;
+    const cc_ctx::RouteGraph &rg = ctx->rg_last ? *ctx->rg_last : ctx->g_route;
+    cc_stats &S = ctx->stats;
+    S.route = h->route_taken;
+    S.route_source = h->route_source;
+    S.ks_d = h->ks_out[0];
+    S.ks_alpha = h->ks_out[1];
+    S.ks_xmin = (int64_t)h->ks_out[2];
+    S.ks_ntail = (int64_t)h->ks_out[3];
+    S.ks_ncand = (int64_t)h->ks_out[4];
+    S.max_degree = (int64_t)(h->maxkey >> 32);
+    S.seed_vertex = h->maxkey ? (int64_t)(0xffffffffu - (uint32_t)(h->maxkey & 0xffffffffu)) : 0;
+    if (h->route_source == 2 && h->route_taken) S.ks_d = 0.0;
+    S.pred_route = ctx->opt.route_policy == CC_ROUTE_LEARNED && ctx->have_pred ? h->pred_route : -1;
+    S.pred_confidence = h->pred_conf;
+    S.pred_cutoff = h->pred_cutoff;
+    S.sv_iters = h->loop_done;
+    const int it0 = h->route_taken ? 0 : 1;
+    if (h->route_taken) {
+        S.bfs_levels = h->bfs_level;
+        S.bfs_visited = (int64_t)h->bfs_visited;
+        S.comp_min = h->cmin;
+        S.bfs_edges_inspected = (int64_t)h->bfs_inspected;
+        S.m_active[0] = rg.edge_bfs && h->bfs_list >= 0 ? (int64_t)h->bfs_len : S.m;
+    } else {
+        S.m_active[0] = S.m;
+        S.m_active[1] = S.m;
+    }
+    for (int i = it0 + 1; i < h->loop_done && i < CC_MAX_SV_ITERS_RECORDED; i++) S.m_active[i] = (int64_t)h->kept[i - 1];
+    for (int i = 0; i < h->loop_done && i < CC_MAX_SV_ITERS_RECORDED; i++) S.sv_hooks[i] = (int64_t)h->hooked[i];
+    S.sv_sample_stride = rg.sample_stride;
+    const long long loops = h->loop_done > it0 + 1 ? h->loop_done - it0 - 1 : 0;
+    const bool unsure = h->route_source != 1;  // the learned policy ran the exact prediction
+    S.launches = rg.static_launches + (unsure ? rg.unsure_launches : 0) +
+                 (h->route_taken ? (long long)h->bfs_level * rg.level_launches + rg.bfs_launches : 0) + 3 * loops;
+    S.status = device_error(h->err);
+}
+
+template <typename T>
+cc_status labels_graph(cc_ctx *ctx, const void *edges, vid_t n, long long m, void *labels, cudaStream_t s) {
+    cc_stats &S = ctx->stats;
+    const int cap = ctx->opt.fault_inject & CC_FAULT_ITER_CAP ? 1
+                    : ctx->opt.max_iters > 0                  ? ctx->opt.max_iters
+                                                              : default_max_iters(n);
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    CU_TRY(cudaStreamIsCapturing(s, &cst));
+    const bool user_capture = cst == cudaStreamCaptureStatusActive;
+    cc_status prior = CC_OK;
+    if (!user_capture && ctx->async_outstanding && cudaEventQuery(ctx->ev_done) == cudaSuccess) {
+        prior = device_error(ctx->h_st->err);  // an earlier call's device error, reported once
+        ctx->async_outstanding = false;
+    }
+    cudaGetLastError();
+    memset(&S, 0, sizeof(S));
+    prof_reset(ctx);
+    for (int e = 0; e < EV_COUNT; e++) ctx->ev_used[e] = false;
+    S.n = n;
+    S.m = m;
+    ctx->graph_last = true;
+    if (user_capture) {
+        // captured into the caller's graph: nothing may allocate or wait
+        ctx->capturing = true;
+        cc_status r = ensure_route(ctx, n, m);
+        if (r == CC_OK) r = enqueue_route<T>(ctx, edges, n, m, labels, cap, s, ctx->g_capture);
+        ctx->capturing = false;
+        ctx->rg_last = &ctx->g_capture;
+        return r;
+    }
+    CC_TRY(ensure_route(ctx, n, m));
+    std::vector<unsigned char> key = route_key(ctx, (int)sizeof(T), n, m, edges, labels, cap);
+    cc_ctx::RouteGraph &rg = ctx->g_route;
+    if (!rg.exec || rg.key != key) {
+        if (rg.exec) cudaGraphExecDestroy(rg.exec);
+        rg.exec = nullptr;
+        CU_TRY(cudaStreamBeginCapture(ctx->cap_s, cudaStreamCaptureModeRelaxed));
+        const cc_status r = enqueue_route<T>(ctx, edges, n, m, labels, cap, ctx->cap_s, rg);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ctx->cap_s, &g);
+        if (r != CC_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return r != CC_OK ? r : CC_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&rg.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            cudaGetLastError();
+            rg.exec = nullptr;
+            return CC_ERR_CUDA;
+        }
+        rg.key.swap(key);
+    }
+    ctx->rg_last = &rg;
+    rec(ctx, EV_START, s);
+    CU_TRY(cudaGraphLaunch(rg.exec, s));
+    rec(ctx, EV_END, s);
+    CU_TRY(cudaEventRecord(ctx->ev_done, s));
+    ctx->async_outstanding = true;
+    if (ctx->opt.debug_checks) {
+        CU_TRY(cudaStreamSynchronize(s));
+        ctx->async_outstanding = false;
+        return device_error(ctx->h_st->err);
+    }
+    return prior;
+}
+
 // Host-input form. The pairs are copied in chunks on a copy stream; the
 // host link (about 210 GB/s on GB300) is the bound, so the passes that need
 // only the pairs seen so far run under the copy, each chunk as it lands:
@@ -1544,7 +1946,8 @@ cc_status cc_create(cc_ctx **out, const cc_options *opt, int device) {
         return CC_ERR_CUDA;
     }
     ctx->num_sms = prop.multiProcessorCount;
-    if (bucket_kernels_setup() != cudaSuccess || degree_part_setup() != cudaSuccess) {
+    if (bucket_kernels_setup() != cudaSuccess || degree_part_setup() != cudaSuccess ||
+        degree_hubs_setup() != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return CC_ERR_CUDA;
@@ -1553,6 +1956,11 @@ cc_status cc_create(cc_ctx **out, const cc_options *opt, int device) {
     if (cudaMallocHost(&ctx->h_st, sizeof(DevState)) != cudaSuccess) {
         delete ctx;
         return CC_ERR_OOM;
+    }
+    if (ensure_streams(ctx) != CC_OK) {  // every stream and event up front: none is created during a capture
+        cudaGetLastError();
+        cc_destroy(ctx);
+        return CC_ERR_CUDA;
     }
     memset(ctx->h_st, 0, sizeof(DevState));
     for (int e = 0; e < EV_COUNT; e++) cudaEventCreate(&ctx->ev[e]);
@@ -1605,6 +2013,9 @@ cc_status cc_destroy(cc_ctx *ctx) {
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->cap_s) cudaStreamDestroy(ctx->cap_s);
     if (ctx->cap_s2) cudaStreamDestroy(ctx->cap_s2);
+    if (ctx->cap_s3) cudaStreamDestroy(ctx->cap_s3);
+    if (ctx->g_route.exec) cudaGraphExecDestroy(ctx->g_route.exec);
+    if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
     if (ctx->h_st) cudaFreeHost(ctx->h_st);
     delete ctx;
     return CC_OK;
@@ -1624,13 +2035,40 @@ cc_status cc_labels(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, vo
     CU_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     ctx->last_stream = s;
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    CU_TRY(cudaStreamIsCapturing(s, &cst));
+    const bool user_capture = cst == cudaStreamCaptureStatusActive;
+    if (user_capture && ctx->opt.profile) return CC_ERR_INVALID_ARG;  // profiling waits on the host
     if (ctx->opt.fault_inject & CC_FAULT_ALLOC) ctx->alloc_fail_pending = 1;
+    ctx->capturing = user_capture;  // inside a capture the workspace must already fit
     cc_status st = ensure_sv(ctx, (size_t)n, (size_t)m);
+    ctx->capturing = false;
     ctx->alloc_fail_pending = 0;
     if (st != CC_OK) {
         ctx->last_status = st;
         return st;
     }
+    if (!ctx->opt.profile) {
+        // stream-ordered: enqueued with no host wait (m = 0: every vertex its own label)
+        if (m == 0) {
+            memset(&ctx->stats, 0, sizeof(ctx->stats));
+            ctx->stats.n = n;
+            ctx->graph_last = false;
+            launch_parent_init(as<vid_t>(ctx->parent), (vid_t)n, nullptr, 0, ctx->grid, s);
+            if (ctx->opt.id_bytes == 4) launch_finalize<int32_t>(as<vid_t>(ctx->parent), (vid_t)n, labels_out_dev, ctx->grid, s);
+            else launch_finalize<int64_t>(as<vid_t>(ctx->parent), (vid_t)n, labels_out_dev, ctx->grid, s);
+            ctx->stats.launches = 2;
+            st = cuda_status(cudaGetLastError());
+        } else if (ctx->opt.id_bytes == 4) {
+            st = labels_graph<int32_t>(ctx, edges_dev, (vid_t)n, m, labels_out_dev, s);
+        } else {
+            st = labels_graph<int64_t>(ctx, edges_dev, (vid_t)n, m, labels_out_dev, s);
+        }
+        ctx->last_status = st;
+        ctx->stats.status = st;
+        return st;
+    }
+    ctx->graph_last = false;
     if (ctx->opt.id_bytes == 4) st = labels_impl<int32_t>(ctx, edges_dev, (vid_t)n, m, labels_out_dev, s);
     else st = labels_impl<int64_t>(ctx, edges_dev, (vid_t)n, m, labels_out_dev, s);
     if (st == CC_OK || st == CC_ERR_INVALID_EDGE || st == CC_ERR_NO_CONVERGENCE) {
@@ -2151,6 +2589,15 @@ cc_status cc_get_stats(cc_ctx *ctx, cc_stats *out) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->last_stream);
     cc_stats &S = ctx->stats;
+    if (ctx->graph_last) {  // stream-ordered call: statistics and status from the device state
+        const int64_t n = S.n, m = S.m;
+        memset(&S, 0, sizeof(S));
+        S.n = n;
+        S.m = m;
+        stats_from_device(ctx);
+        ctx->async_outstanding = false;
+        if (ctx->last_status == CC_OK) ctx->last_status = (cc_status)S.status;
+    }
     S.ms_degree = ev_ms(ctx, EV_START, EV_DEGREE);
     S.ms_predict = ev_ms(ctx, EV_DEGREE, EV_PREDICT);
     S.ms_csr = ev_ms(ctx, EV_PREDICT, EV_CSR);

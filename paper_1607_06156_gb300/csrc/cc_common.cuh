@@ -53,6 +53,24 @@ struct DevState {
     int loop_cur;                           // active pairs of iteration loop_it are in ebuf[loop_cur]
     int loop_cap;                           // iteration cap
     int loop_done;                          // iterations run when the loop stopped (0 = not stopped)
+    // graph-driven route (stream-ordered cc_labels): every decision on the device
+    int route_taken;                        // 1 = the BFS branch ran
+    int route_source;                       // 0 = K-S heuristic, 1 = learned predictor, 2 = forced
+    int loop_start_it;                      // the SV loop continues after this iteration,
+    int loop_start_cur;                     // whose active pairs are in ebuf[loop_start_cur]
+    int bfs_level;                          // BFS levels run so far (the level being run)
+    int bfs_par;                            // current frontier: queue / bitmap number bfs_par
+    int bfs_bu;                             // this level runs bottom-up
+    int bfs_queue;                          // the current frontier is held as a queue (else a bitmap)
+    int bfs_conv;                           // this level converts: 1 queue -> bitmap, 2 bitmap -> queue
+    int bfs_list;                           // edge-list BFS: active pairs in the caller's list (-1) or ebuf[bfs_list]
+    int bfs_write;                          // edge-list BFS: this level compacts its active pairs
+    int bfs_cutoff;                         // stop the BFS after this many levels (0 = run to completion)
+    unsigned long long bfs_len;             // edge-list BFS: pairs in the active list
+    unsigned long long bfs_kept_prev;       // edge-list BFS: pairs that stayed active in the previous level
+    unsigned long long bfs_explored;        // CSR BFS: adjacency entries of the levels expanded so far
+    unsigned long long bfs_prev_f;          // CSR BFS: frontier size of the previous level
+    unsigned long long bfs_qcount;          // CSR BFS: bitmap -> queue counter
     unsigned long long kept[kMaxIters];     // active pairs written by SV iteration i
     unsigned long long hooked[kMaxIters];   // roots hooked in SV iteration i
     unsigned long long hook_base[kMaxIters + 1];  // start of iteration i's slice of the hooked list

@@ -94,6 +94,29 @@ void launch_hist_widen(const uint32_t *hist, const uint32_t *ovf, unsigned long 
                        uint64_t *out, long long len, int grid, cudaStream_t s);
 void launch_hist_narrow(const uint64_t *in, long long len, uint32_t *hist, DevState *st, int grid, cudaStream_t s);
 
+// Stream-ordered route (graph-mode cc_labels): decisions taken on the device.
+// launch_*_level return the kernels they launched (one WHILE iteration).
+void launch_bfsg_init(const uint32_t *row_ptr, vid_t n, uint32_t *vis, vid_t *q0, DevState *st,
+                      cudaGraphConditionalHandle h, cudaStream_t s);
+int launch_bfsg_level(vid_t n, unsigned long long total_edges, const uint32_t *row_ptr, const vid_t *col, uint32_t *vis,
+                      vid_t *q0, vid_t *q1, uint32_t *b0, uint32_t *b1, uint32_t *dq, uint32_t *off,
+                      unsigned long long *tsum, DevState *st, cudaGraphConditionalHandle h, int grid, cudaStream_t s);
+void launch_ebfsg_init(uint32_t *vis, uint32_t *b0, vid_t n, long long m, DevState *st, cudaGraphConditionalHandle h,
+                       cudaStream_t s);
+template <typename T>
+int launch_ebfsg_level(const void *caller, long long m, const uint2 *eb0, const uint2 *eb1, vid_t n, uint32_t *vis,
+                       uint32_t *b0, uint32_t *b1, DevState *st, cudaGraphConditionalHandle h, int grid,
+                       cudaStream_t s);
+void launch_parent_init_st(vid_t *parent, vid_t n, const uint32_t *vis, const DevState *st, int grid, cudaStream_t s);
+template <typename T>
+int launch_sv_after_bfs(const void *caller, long long m, const uint2 *eb0, const uint2 *eb1, vid_t n, vid_t *parent,
+                        const uint32_t *vis, vid_t *hooked_list, DevState *st, int grid, cudaStream_t s);
+void launch_sv_loop_init_st(DevState *st, int cap, cudaGraphConditionalHandle h, cudaStream_t s);
+// h: the IF node's handle, or null when there is no BFS branch
+void launch_route_decide(DevState *st, const cudaGraphConditionalHandle *h, int policy, int bfs_ok, int opt_cutoff,
+                         float min_conf, int have_pred, cudaStream_t s);
+void launch_pred_unsure(const DevState *st, cudaGraphConditionalHandle h, float min_conf, cudaStream_t s);
+
 // k_degree_part.cu: degree pass for n > 2^25 (counts out of L2): the
 // endpoints partitioned into windows of 2^23 vertices (bulk copies into
 // shared memory), then counted window by window with L2 atomics (one launch
@@ -106,6 +129,7 @@ template <typename T>
 void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t *deg, void *scratch, DevState *st,
                                int num_sms, int grid, cudaStream_t s);
 cudaError_t degree_part_setup();
+cudaError_t degree_hubs_setup();  // dynamic shared memory of the hub-aware degree pass
 
 // k_tuple_sv.cu: the paper's sort-based SV (Section 3.1) as an ablation, with
 // the exclusion of completed partitions (Section 3.1.4).

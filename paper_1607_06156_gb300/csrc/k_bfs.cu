@@ -484,4 +484,458 @@ void launch_popcount(const uint32_t *bm, long long nwords, unsigned long long *o
     k_popcount<<<grid, kBlock, 0, s>>>(bm, nwords, out);
 }
 
+// ---------------------------------------------------------------------------
+// Device-driven BFS for the stream-ordered cc_labels: the level loop is the
+// body of a CUDA graph WHILE node. Each level's frontier size, direction
+// and buffers are read from DevState, so no level needs the host. The
+// decisions are those of the host loop: Beamer's switching rule (go
+// bottom-up when the frontier's edges exceed 1/14 of the unexplored edges,
+// come back when the frontier holds fewer than n/24 vertices and shrinks),
+// and the same frontier bookkeeping (front[l], front_edges[l]).
+// Frontier buffers come in pairs: queue / bitmap number bfs_par is current.
+
+constexpr double kBeamerAlpha = 14.0, kBeamerBeta = 24.0;
+
+__device__ __forceinline__ bool bfs_continue(const DevState *st, int l, unsigned long long f) {
+    return f > 0 && l < kMaxLevels - 1 && (st->bfs_cutoff <= 0 || l < st->bfs_cutoff);
+}
+
+__global__ void k_bfsg_init(const uint32_t *__restrict__ row_ptr, vid_t n, uint32_t *vis, vid_t *q0, DevState *st,
+                            cudaGraphConditionalHandle h) {
+    vid_t s = 0xffffffffu - (vid_t)(st->maxkey & 0xffffffffull);
+    if (s >= n) s = 0;
+    vis[s >> 5] |= 1u << (s & 31);
+    q0[0] = s;
+    st->front[0] = 1;
+    st->front_edges[0] = row_ptr[s + 1] - row_ptr[s];
+    st->cmin = 0xffffffffu;
+    st->bfs_level = 0;
+    st->bfs_par = 0;
+    st->bfs_bu = 0;
+    st->bfs_queue = 1;
+    st->bfs_list = -1;
+    st->bfs_explored = 0;
+    st->bfs_prev_f = 0;
+    cudaGraphSetConditional(h, bfs_continue(st, 0, 1ull) ? 1u : 0u);
+}
+
+// direction of this level and the frontier conversion it needs
+__global__ void k_bfsg_plan(DevState *st, vid_t n, unsigned long long total_edges) {
+    const int l = st->bfs_level;
+    const unsigned long long f = st->front[l], fe = st->front_edges[l];
+    int bu = st->bfs_bu;
+    const unsigned long long unexplored = total_edges > st->bfs_explored ? total_edges - st->bfs_explored : 0;
+    if (!bu && (double)fe > (double)unexplored / kBeamerAlpha) bu = 1;
+    else if (bu && (double)f < (double)n / kBeamerBeta && f < st->bfs_prev_f) bu = 0;
+    st->bfs_bu = bu;
+    const int conv = bu && st->bfs_queue ? 1 : (!bu && !st->bfs_queue ? 2 : 0);
+    st->bfs_conv = conv;
+    if (conv == 2) st->bfs_qcount = 0;
+}
+
+// queue -> bitmap, first step: clear the current bitmap
+__global__ void __launch_bounds__(kBlock) k_bfsg_q2b_clear(uint32_t *b0, uint32_t *b1, long long nwords,
+                                                           const DevState *st) {
+    if (st->bfs_conv != 1) return;
+    uint32_t *b = st->bfs_par ? b1 : b0;
+    for (long long w = gtid(); w < nwords; w += gstride()) b[w] = 0u;
+}
+
+__global__ void __launch_bounds__(kBlock) k_bfsg_q2b(const vid_t *q0, const vid_t *q1, uint32_t *b0, uint32_t *b1,
+                                                     const DevState *st) {
+    if (st->bfs_conv != 1) return;
+    const int par = st->bfs_par;
+    const vid_t *q = par ? q1 : q0;
+    uint32_t *b = par ? b1 : b0;
+    const long long f = (long long)st->front[st->bfs_level];
+    for (long long i = gtid(); i < f; i += gstride()) atomicOr(&b[q[i] >> 5], 1u << (q[i] & 31));
+}
+
+__global__ void __launch_bounds__(kBlock) k_bfsg_b2q(const uint32_t *b0, const uint32_t *b1, long long nwords,
+                                                     vid_t *q0, vid_t *q1, DevState *st) {
+    if (st->bfs_conv != 2) return;
+    const int par = st->bfs_par;
+    const uint32_t *bm = par ? b1 : b0;
+    vid_t *queue = par ? q1 : q0;
+    const long long stride = gstride();
+    const long long rounds = (nwords + stride - 1) / stride;
+    const int lane = threadIdx.x & 31;
+    for (long long r = 0; r < rounds; r++) {
+        const long long w = gtid() + r * stride;
+        uint32_t bits = w < nwords ? bm[w] : 0u;
+        const int c = __popc(bits);
+        unsigned long long incl = (unsigned long long)c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned long long wtot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 31 && wtot) base = atomicAdd(&st->bfs_qcount, wtot);
+        base = __shfl_sync(0xffffffffu, base, 31) + incl - (unsigned long long)c;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            queue[base++] = (vid_t)(w * 32 + b);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_bfsg_front_degrees(const vid_t *q0, const vid_t *q1,
+                                                               const uint32_t *__restrict__ row_ptr, uint32_t *dq,
+                                                               const DevState *st) {
+    if (st->bfs_bu) return;
+    const vid_t *q = st->bfs_par ? q1 : q0;
+    const long long f = (long long)st->front[st->bfs_level];
+    for (long long i = gtid(); i < f; i += gstride()) dq[i] = row_ptr[q[i] + 1] - row_ptr[q[i]];
+}
+
+// Exclusive scan of dq over the frontier (top-down levels only), tiles
+// taken grid-stride by a fixed grid.
+__global__ void __launch_bounds__(kBlock) k_bfsg_scan_up(const uint32_t *__restrict__ in, unsigned long long *tsum,
+                                                         const DevState *st) {
+    if (st->bfs_bu) return;
+    const long long len = (long long)st->front[st->bfs_level];
+    const long long ntiles = (len + kScanTile - 1) / kScanTile;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        unsigned long long s = 0;
+        for (int k = 0; k < kScanItems; k++) {
+            const long long i = t * kScanTile + (long long)threadIdx.x * kScanItems + k;
+            if (i < len) s += in[i];
+        }
+        unsigned long long tot;
+        block_scan_excl_u64(s, tot);
+        if (threadIdx.x == 0) tsum[t] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_bfsg_scan_mid(unsigned long long *tsum, const DevState *st) {
+    if (st->bfs_bu) return;
+    const long long len = (long long)st->front[st->bfs_level];
+    const long long ntiles = (len + kScanTile - 1) / kScanTile;
+    unsigned long long carry = 0;
+    for (long long r = 0; r < ntiles; r += blockDim.x) {
+        const long long i = r + threadIdx.x;
+        const unsigned long long x = i < ntiles ? tsum[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long e = block_scan_excl_u64(x, tot);
+        if (i < ntiles) tsum[i] = carry + e;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_bfsg_scan_down(const uint32_t *__restrict__ in,
+                                                           const unsigned long long *__restrict__ tsum, uint32_t *out,
+                                                           const DevState *st) {
+    if (st->bfs_bu) return;
+    const long long len = (long long)st->front[st->bfs_level];
+    const long long ntiles = (len + kScanTile - 1) / kScanTile;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        uint32_t v[kScanItems];
+        unsigned long long s = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            const long long i = t * kScanTile + (long long)threadIdx.x * kScanItems + k;
+            v[k] = i < len ? in[i] : 0u;
+            s += v[k];
+        }
+        unsigned long long tot;
+        unsigned long long run = tsum[t] + block_scan_excl_u64(s, tot);
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            const long long i = t * kScanTile + (long long)threadIdx.x * kScanItems + k;
+            if (i < len) out[i] = (uint32_t)run;
+            run += v[k];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_bfsg_topdown(const vid_t *q0, const vid_t *q1,
+                                                         const uint32_t *__restrict__ off,
+                                                         const uint32_t *__restrict__ row_ptr,
+                                                         const vid_t *__restrict__ col, uint32_t *vis, vid_t *nq0,
+                                                         vid_t *nq1, DevState *st) {
+    if (st->bfs_bu) return;
+    const int level = st->bfs_level, par = st->bfs_par;
+    const vid_t *queue = par ? q1 : q0;
+    vid_t *next = par ? nq0 : nq1;
+    const long long f = (long long)st->front[level], total = (long long)st->front_edges[level];
+    const long long stride = gstride();
+    const long long rounds = (total + stride - 1) / stride;
+    unsigned long long new_edges = 0;
+    for (long long r = 0; r < rounds; r++) {
+        const long long e = gtid() + r * stride;
+        bool fresh = false;
+        vid_t w = 0;
+        if (e < total) {
+            long long lo = 0, hi = f - 1;  // largest k with off[k] <= e
+            while (lo < hi) {
+                const long long mid = (lo + hi + 1) >> 1;
+                if ((long long)off[mid] <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            const vid_t v = queue[lo];
+            const uint32_t k = (uint32_t)(e - (long long)off[lo]), b0 = row_ptr[v];
+            if (k < row_ptr[v + 1] - b0) {
+                w = col[b0 + k];
+                const uint32_t bit = 1u << (w & 31);
+                if (!(__ldcg(&vis[w >> 5]) & bit)) {
+                    const uint32_t old = atomicOr(&vis[w >> 5], bit);
+                    fresh = !(old & bit);
+                }
+            }
+        }
+        const unsigned long long k = warp_append(&st->front[level + 1], fresh);
+        if (fresh) {
+            next[k] = w;
+            new_edges += row_ptr[w + 1] - row_ptr[w];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) new_edges += __shfl_xor_sync(0xffffffffu, new_edges, o);
+    if ((threadIdx.x & 31) == 0 && new_edges) atomicAdd(&st->front_edges[level + 1], new_edges);
+    if (gtid() == 0) atomicAdd(&st->bfs_inspected, (unsigned long long)total);
+}
+
+__global__ void __launch_bounds__(kBlock) k_bfsg_bottomup(vid_t n, const uint32_t *__restrict__ row_ptr,
+                                                          const vid_t *__restrict__ col, uint32_t *b0, uint32_t *b1,
+                                                          uint32_t *vis, DevState *st) {
+    if (!st->bfs_bu) return;
+    const int level = st->bfs_level, par = st->bfs_par;
+    const uint32_t *fb = par ? b1 : b0;
+    uint32_t *nb = par ? b0 : b1;
+    const long long nwords = ((long long)n + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const long long warp0 = gtid() >> 5, nwarps = gstride() >> 5;
+    unsigned long long inspected = 0, new_edges = 0, found_total = 0;
+    for (long long w = warp0; w < nwords; w += nwarps) {
+        const uint32_t vword = vis[w];
+        const long long v = w * 32 + lane;
+        bool found = false;
+        uint32_t d = 0;
+        if (v < (long long)n && !((vword >> lane) & 1u)) {
+            const uint32_t b = row_ptr[v], e = row_ptr[v + 1];
+            d = e - b;
+            for (uint32_t k = b; k < e; k++) {
+                const vid_t x = col[k];
+                inspected++;
+                if ((fb[x >> 5] >> (x & 31)) & 1u) {
+                    found = true;
+                    break;
+                }
+            }
+        }
+        const uint32_t fmask = __ballot_sync(0xffffffffu, found);
+        if (found) new_edges += d;
+        if (lane == 0) {
+            nb[w] = fmask;
+            if (fmask) vis[w] = vword | fmask;
+            found_total += __popc(fmask);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        inspected += __shfl_xor_sync(0xffffffffu, inspected, o);
+        new_edges += __shfl_xor_sync(0xffffffffu, new_edges, o);
+    }
+    if (lane == 0) {
+        if (found_total) atomicAdd(&st->front[level + 1], found_total);
+        if (new_edges) atomicAdd(&st->front_edges[level + 1], new_edges);
+        if (inspected) atomicAdd(&st->bfs_inspected, inspected);
+    }
+}
+
+__global__ void k_bfsg_step(DevState *st, cudaGraphConditionalHandle h) {
+    int l = st->bfs_level;
+    st->bfs_explored += st->front_edges[l];
+    st->bfs_prev_f = st->front[l];
+    st->bfs_queue = st->bfs_bu ? 0 : 1;
+    st->bfs_par ^= 1;
+    l++;
+    st->bfs_level = l;
+    cudaGraphSetConditional(h, bfs_continue(st, l, st->front[l]) ? 1u : 0u);
+}
+
+void launch_bfsg_init(const uint32_t *row_ptr, vid_t n, uint32_t *vis, vid_t *q0, DevState *st,
+                      cudaGraphConditionalHandle h, cudaStream_t s) {
+    k_bfsg_init<<<1, 1, 0, s>>>(row_ptr, n, vis, q0, st, h);
+}
+
+int launch_bfsg_level(vid_t n, unsigned long long total_edges, const uint32_t *row_ptr, const vid_t *col, uint32_t *vis,
+                      vid_t *q0, vid_t *q1, uint32_t *b0, uint32_t *b1, uint32_t *dq, uint32_t *off,
+                      unsigned long long *tsum, DevState *st, cudaGraphConditionalHandle h, int grid, cudaStream_t s) {
+    const long long nwords = ((long long)n + 31) / 32;
+    k_bfsg_plan<<<1, 1, 0, s>>>(st, n, total_edges);
+    k_bfsg_q2b_clear<<<grid, kBlock, 0, s>>>(b0, b1, nwords, st);
+    k_bfsg_q2b<<<grid, kBlock, 0, s>>>(q0, q1, b0, b1, st);
+    k_bfsg_b2q<<<grid, kBlock, 0, s>>>(b0, b1, nwords, q0, q1, st);
+    k_bfsg_front_degrees<<<grid, kBlock, 0, s>>>(q0, q1, row_ptr, dq, st);
+    k_bfsg_scan_up<<<grid, kBlock, 0, s>>>(dq, tsum, st);
+    k_bfsg_scan_mid<<<1, kBlock, 0, s>>>(tsum, st);
+    k_bfsg_scan_down<<<grid, kBlock, 0, s>>>(dq, tsum, off, st);
+    k_bfsg_topdown<<<grid, kBlock, 0, s>>>(q0, q1, off, row_ptr, col, vis, q0, q1, st);
+    k_bfsg_bottomup<<<grid, kBlock, 0, s>>>(n, row_ptr, col, b0, b1, vis, st);
+    k_bfsg_step<<<1, 1, 0, s>>>(st, h);
+    return 11;
+}
+
+// Device-driven edge-list BFS (one WHILE iteration per level). The active
+// pairs are the caller's list (bfs_list < 0, read by the T instantiation)
+// or ebuf[bfs_list] (the uint32 instantiation); a level compacts them into
+// the other buffer once they fall to 70% of the list, as the host loop does.
+// Seed: the sampled hub of the learned predictor when it decided the route,
+// else the exact max-degree vertex.
+__global__ void k_ebfsg_init(uint32_t *vis, uint32_t *b0, vid_t n, long long m, DevState *st,
+                             cudaGraphConditionalHandle h) {
+    const unsigned long long key = st->route_source == 1 ? st->pred_seedkey : st->maxkey;
+    vid_t s = 0xffffffffu - (vid_t)(key & 0xffffffffull);
+    if (s >= n) s = 0;
+    vis[s >> 5] |= 1u << (s & 31);
+    b0[s >> 5] |= 1u << (s & 31);
+    st->front[0] = 1;
+    st->cmin = 0xffffffffu;
+    st->bfs_level = 0;
+    st->bfs_par = 0;
+    st->bfs_list = -1;
+    st->bfs_len = (unsigned long long)m;
+    st->bfs_kept_prev = (unsigned long long)m;
+    cudaGraphSetConditional(h, 1u);  // level 0 always runs (a cutoff is at least one level)
+}
+
+// this level: compact or not; the next frontier bitmap cleared
+__global__ void __launch_bounds__(kBlock) k_ebfsg_plan(uint32_t *b0, uint32_t *b1, long long nwords, DevState *st) {
+    const int l = st->bfs_level;
+    if (gtid() == 0) st->bfs_write = l >= 1 && (double)st->bfs_kept_prev <= 0.7 * (double)st->bfs_len;
+    uint32_t *next = st->bfs_par ? b0 : b1;
+    for (long long w = gtid(); w < nwords; w += gstride()) next[w] = 0u;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_ebfsg_level(const T *__restrict__ caller, long long m, const uint2 *eb0,
+                                                        const uint2 *eb1, vid_t n, uint32_t *vis, uint32_t *b0,
+                                                        uint32_t *b1, DevState *st) {
+    constexpr bool kList = sizeof(T) == 4 && T(-1) > T(0);  // uint32_t: the compacted list
+    const int list = st->bfs_list;
+    if (kList != (list >= 0)) return;
+    const T *in = kList ? reinterpret_cast<const T *>(list ? eb1 : eb0) : caller;
+    const long long len = kList ? (long long)st->bfs_len : m;
+    uint2 *out = const_cast<uint2 *>(list == 0 ? eb1 : eb0);
+    const int level = st->bfs_level, par = st->bfs_par;
+    const bool write = st->bfs_write != 0;
+    const uint32_t *cur = par ? b1 : b0;
+    uint32_t *next = par ? b0 : b1;
+    constexpr int P = PairVec<T>::kPairs;
+    constexpr int U = EdgeUnroll<T>::U;
+    constexpr int K = P * U;
+    __shared__ int sw[32];
+    __shared__ unsigned long long sbase;
+    const long long nvec = len / P;
+    const int4 *ev = reinterpret_cast<const int4 *>(in);
+    const long long tile = (long long)kBlock * U;
+    const long long ntiles = (nvec + tile - 1) / tile;
+    unsigned long long claimed = 0, kept_total = 0;
+    for (long long t = blockIdx.x; t < ntiles + (P == 2 && (len & 1) ? 1 : 0); t += gridDim.x) {
+        long long u[K], v[K];
+        bool valid[K];
+        if (t < ntiles) {
+            int4 q[U];
+#pragma unroll
+            for (int k = 0; k < U; k++) {
+                const long long i = t * tile + (long long)k * kBlock + threadIdx.x;
+                q[k] = i < nvec ? ld_stream(ev + i) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int k = 0; k < U; k++) {
+                const long long i = t * tile + (long long)k * kBlock + threadIdx.x;
+#pragma unroll
+                for (int j = 0; j < P; j++) {
+                    vec_pair<T>(q[k], j, u[k * P + j], v[k * P + j]);
+                    valid[k * P + j] = i < nvec;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                u[k] = v[k] = 0;
+                valid[k] = false;
+            }
+            if (threadIdx.x == 0) {
+                scalar_pair<T>(in, len - 1, u[0], v[0]);
+                valid[0] = true;
+            }
+        }
+        bool keep[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            keep[k] = false;
+            if (!valid[k] || (unsigned long long)u[k] >= n || (unsigned long long)v[k] >= n) continue;
+            const bool fu = bit_test(cur, u[k]), fv = bit_test(cur, v[k]);
+            const bool vu0 = fu || bit_test(vis, u[k]), vv0 = fv || bit_test(vis, v[k]);
+            if (fu && !vv0 && claim(vis, next, v[k])) claimed++;
+            if (fv && !vu0 && claim(vis, next, u[k])) claimed++;
+            keep[k] = !((vu0 || fv) && (vv0 || fu));
+        }
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) c += keep[k];
+        kept_total += (unsigned long long)c;
+        if (write) {  // uniform over the grid
+            unsigned long long o = block_reserve(&st->front_edges[level + 1], c, sw, &sbase);
+#pragma unroll
+            for (int k = 0; k < K; k++)
+                if (keep[k]) out[o++] = make_uint2((vid_t)u[k], (vid_t)v[k]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        claimed += __shfl_xor_sync(0xffffffffu, claimed, o);
+        kept_total += __shfl_xor_sync(0xffffffffu, kept_total, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (claimed) atomicAdd(&st->front[level + 1], claimed);
+        if (!write && kept_total) atomicAdd(&st->front_edges[level + 1], kept_total);
+    }
+}
+
+__global__ void k_ebfsg_step(DevState *st, cudaGraphConditionalHandle h) {
+    int l = st->bfs_level;
+    const unsigned long long claimed = st->front[l + 1], kept = st->front_edges[l + 1];
+    if (st->bfs_write) {
+        st->bfs_list = st->bfs_list == 0 ? 1 : 0;
+        st->bfs_len = kept;
+    }
+    st->bfs_kept_prev = kept;
+    st->bfs_par ^= 1;
+    l++;
+    st->bfs_level = l;
+    const bool go = claimed > 0 && l < kMaxLevels - 1 && (st->bfs_cutoff <= 0 || l < st->bfs_cutoff);
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+void launch_ebfsg_init(uint32_t *vis, uint32_t *b0, vid_t n, long long m, DevState *st, cudaGraphConditionalHandle h,
+                       cudaStream_t s) {
+    k_ebfsg_init<<<1, 1, 0, s>>>(vis, b0, n, m, st, h);
+}
+
+template <typename T>
+int launch_ebfsg_level(const void *caller, long long m, const uint2 *eb0, const uint2 *eb1, vid_t n, uint32_t *vis,
+                       uint32_t *b0, uint32_t *b1, DevState *st, cudaGraphConditionalHandle h, int grid,
+                       cudaStream_t s) {
+    const long long nwords = ((long long)n + 31) / 32;
+    k_ebfsg_plan<<<grid, kBlock, 0, s>>>(b0, b1, nwords, st);
+    k_ebfsg_level<T><<<fit_grid((const void *)k_ebfsg_level<T>, grid, kBlock), kBlock, 0, s>>>(
+        (const T *)caller, m, eb0, eb1, n, vis, b0, b1, st);
+    k_ebfsg_level<uint32_t><<<fit_grid((const void *)k_ebfsg_level<uint32_t>, grid, kBlock), kBlock, 0, s>>>(
+        nullptr, 0, eb0, eb1, n, vis, b0, b1, st);
+    k_ebfsg_step<<<1, 1, 0, s>>>(st, h);
+    return 4;
+}
+template int launch_ebfsg_level<int32_t>(const void *, long long, const uint2 *, const uint2 *, vid_t, uint32_t *,
+                                         uint32_t *, uint32_t *, DevState *, cudaGraphConditionalHandle, int,
+                                         cudaStream_t);
+template int launch_ebfsg_level<int64_t>(const void *, long long, const uint2 *, const uint2 *, vid_t, uint32_t *,
+                                         uint32_t *, uint32_t *, DevState *, cudaGraphConditionalHandle, int,
+                                         cudaStream_t);
+
 }  // namespace ccg

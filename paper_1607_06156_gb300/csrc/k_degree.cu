@@ -615,9 +615,7 @@ template <typename T, int SLOTS, int THREADS, int MINB>
 void launch_hub_count_cfg(const void *edges, long long m, vid_t n, uint32_t *deg, const unsigned *scratch,
                           DevState *st, int num_sms, cudaStream_t s) {
     if (m <= 0) return;
-    constexpr size_t smem = (size_t)SLOTS * 8;
-    cudaFuncSetAttribute(k_degree_hubs<T, SLOTS, THREADS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    constexpr size_t smem = (size_t)SLOTS * 8;  // the attribute is set once, by degree_hubs_setup
     k_degree_hubs<T, SLOTS, THREADS, MINB><<<num_sms * MINB, THREADS, smem, s>>>((const T *)edges, m, n, deg, scratch,
                                                                                  st);
 }
@@ -631,6 +629,16 @@ void launch_degree_hubs_cfg(const void *edges, long long m, vid_t n, uint32_t *d
 }
 
 long long degree_hub_prefix() { return kHubPrefix; }
+
+cudaError_t degree_hubs_setup() {
+    const int smem = kHubSlots * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_degree_hubs<int32_t, kHubSlots, kHubThreads, kHubMinBlocks>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_degree_hubs<int64_t, kHubSlots, kHubThreads, kHubMinBlocks>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
 
 template <typename T>
 void launch_degree_hubs(const void *edges, long long m, vid_t n, uint32_t *deg, unsigned *scratch, DevState *st,

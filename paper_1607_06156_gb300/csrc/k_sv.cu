@@ -481,6 +481,119 @@ void launch_finalize_batch(vid_t *parent, vid_t ntot, const int64_t *vo, int G, 
 }
 
 // ---------------------------------------------------------------------------
+// Stream-ordered route (graph-mode cc_labels): the kernels that take the
+// host's decisions on the device.
+
+// parent[v] = v, or the BFS component's minimum (DevState::cmin) for visited v
+__global__ void __launch_bounds__(kBlock) k_parent_init_st(vid_t *parent, vid_t n, const uint32_t *__restrict__ vis,
+                                                           const DevState *st) {
+    const vid_t cmin = st->cmin;
+    for (long long v = gtid(); v < (long long)n; v += gstride()) {
+        vid_t p = (vid_t)v;
+        if (cmin < n && vis_test(vis, v)) p = cmin;
+        parent[v] = p;
+    }
+}
+
+// The first SV pass after the BFS (MODE 1: a pair with both ends visited is
+// dropped, a visited end stands for cmin) over the pairs the BFS left
+// active: the caller's list (bfs_list < 0; the T instantiation runs) or
+// ebuf[bfs_list] (the uint32 instantiation runs). The surviving pairs go to
+// the other buffer, and the SV loop continues after this iteration 0.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_sv_after_bfs(const T *__restrict__ caller, long long m, const uint2 *eb0,
+                                                         const uint2 *eb1, vid_t n, vid_t *parent,
+                                                         const uint32_t *__restrict__ vis, vid_t *hooked_list,
+                                                         DevState *st) {
+    constexpr bool kList = sizeof(T) == 4 && T(-1) > T(0);
+    const int list = st->bfs_list;
+    if (kList != (list >= 0)) return;
+    const T *in = kList ? reinterpret_cast<const T *>(list ? eb1 : eb0) : caller;
+    const long long len = kList ? (long long)st->bfs_len : m;
+    const int cur0 = list == 0 ? 1 : 0;
+    uint2 *out = const_cast<uint2 *>(cur0 ? eb1 : eb0);
+    sv_pass_body<T, 1, true, true>(in, len, n, parent, vis, st->cmin, hooked_list, out, st, 0);
+    if (gtid() == 0) {
+        st->loop_start_it = 0;
+        st->loop_start_cur = cur0;
+    }
+}
+
+__global__ void k_sv_loop_init_st(DevState *st, int cap, cudaGraphConditionalHandle h) {
+    st->loop_cap = cap < kMaxIters ? cap : kMaxIters;
+    st->loop_cur = st->loop_start_cur;
+    sv_loop_decide(st, st->loop_start_it, h);
+}
+
+// Route of Algorithm 2 (policies as CC_ROUTE_*: 0 K-S heuristic, 1 learned,
+// 2 forced BFS, 3 forced SV); sets the IF node's condition (when there is a
+// BFS branch: has_if). The SV route continues after SV iteration 1, which
+// ran speculatively on ebuf0.
+__global__ void k_route_decide(DevState *st, cudaGraphConditionalHandle h, int has_if, int policy, int bfs_ok,
+                               int opt_cutoff, float min_conf, int have_pred) {
+    int route, src;
+    if (policy == 3) {
+        route = 0;
+        src = 2;
+    } else if (policy == 2) {
+        route = 1;
+        src = 2;
+    } else if (policy == 1 && have_pred && st->pred_conf >= min_conf) {
+        route = st->pred_route;
+        src = 1;
+    } else {
+        route = st->route;
+        src = 0;
+    }
+    if (!bfs_ok) route = 0;
+    st->route_taken = route;
+    st->route_source = src;
+    st->bfs_cutoff = opt_cutoff > 0 ? opt_cutoff : (src == 1 && route == 1 ? st->pred_cutoff : 0);
+    st->loop_start_it = 1;
+    st->loop_start_cur = 0;
+    if (has_if) cudaGraphSetConditional(h, route ? 1u : 0u);
+}
+
+// IF condition: the learned prediction is unsure, the exact degree pass and
+// the K-S fit run
+__global__ void k_pred_unsure(const DevState *st, cudaGraphConditionalHandle h, float min_conf) {
+    cudaGraphSetConditional(h, st->pred_conf < min_conf ? 1u : 0u);
+}
+
+void launch_parent_init_st(vid_t *parent, vid_t n, const uint32_t *vis, const DevState *st, int grid, cudaStream_t s) {
+    if (n == 0) return;
+    k_parent_init_st<<<grid, kBlock, 0, s>>>(parent, n, vis, st);
+}
+
+template <typename T>
+int launch_sv_after_bfs(const void *caller, long long m, const uint2 *eb0, const uint2 *eb1, vid_t n, vid_t *parent,
+                        const uint32_t *vis, vid_t *hooked_list, DevState *st, int grid, cudaStream_t s) {
+    k_sv_after_bfs<T><<<fit_grid((const void *)k_sv_after_bfs<T>, grid, kBlock), kBlock, 0, s>>>(
+        (const T *)caller, m, eb0, eb1, n, parent, vis, hooked_list, st);
+    k_sv_after_bfs<uint32_t><<<fit_grid((const void *)k_sv_after_bfs<uint32_t>, grid, kBlock), kBlock, 0, s>>>(
+        nullptr, 0, eb0, eb1, n, parent, vis, hooked_list, st);
+    return 2;
+}
+template int launch_sv_after_bfs<int32_t>(const void *, long long, const uint2 *, const uint2 *, vid_t, vid_t *,
+                                          const uint32_t *, vid_t *, DevState *, int, cudaStream_t);
+template int launch_sv_after_bfs<int64_t>(const void *, long long, const uint2 *, const uint2 *, vid_t, vid_t *,
+                                          const uint32_t *, vid_t *, DevState *, int, cudaStream_t);
+
+void launch_sv_loop_init_st(DevState *st, int cap, cudaGraphConditionalHandle h, cudaStream_t s) {
+    k_sv_loop_init_st<<<1, 1, 0, s>>>(st, cap, h);
+}
+
+void launch_route_decide(DevState *st, const cudaGraphConditionalHandle *h, int policy, int bfs_ok, int opt_cutoff,
+                         float min_conf, int have_pred, cudaStream_t s) {
+    k_route_decide<<<1, 1, 0, s>>>(st, h ? *h : cudaGraphConditionalHandle(), h ? 1 : 0, policy, bfs_ok, opt_cutoff,
+                                   min_conf, have_pred);
+}
+
+void launch_pred_unsure(const DevState *st, cudaGraphConditionalHandle h, float min_conf, cudaStream_t s) {
+    k_pred_unsure<<<1, 1, 0, s>>>(st, h, min_conf);
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers
 
 template <typename T>

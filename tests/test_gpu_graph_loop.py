@@ -57,7 +57,7 @@ def test_iteration_cap_reports_no_convergence(profile):
     n = 1 << 16
     perm = np.random.default_rng(4).permutation(n)
     e = perm[np.stack([np.arange(n - 1), np.arange(1, n)], axis=1)].astype(np.int32)
-    eng = cc.Engine(route="sv", max_iters=2, profile=profile)
+    eng = cc.Engine(route="sv", max_iters=2, profile=profile, debug_checks=1)
     with pytest.raises(cc.CCError) as ei:
         eng.labels(torch.from_numpy(e).cuda(), n)
     assert ei.value.status == 4
@@ -75,7 +75,7 @@ def test_fault_injection_host_side():
 
     g = gg.rmat(seed=7, scale=12, edge_factor=8)
     e = torch.from_numpy(g.edges).cuda()
-    eng = cc.Engine(route="sv", fault_inject=cc.FAULT_ITER_CAP)
+    eng = cc.Engine(route="sv", fault_inject=cc.FAULT_ITER_CAP, debug_checks=1)
     with pytest.raises(cc.CCError) as ei:
         eng.labels(e, g.n)
     assert ei.value.status == 4

@@ -133,12 +133,23 @@ def test_invalid_ids_rejected(route):
 
     for bad, dt in ((_arr([(0, 1), (2, 10)]), np.int32), (_arr([(0, 1), (-1, 2)]), np.int32),
                     (_arr([(0, 1), (3, 1 << 40)], np.int64), np.int64)):
-        eng = cc.Engine(id_bytes=np.dtype(dt).itemsize, route=route)
+        # debug_checks: the call itself waits and returns the device status
+        eng = cc.Engine(id_bytes=np.dtype(dt).itemsize, route=route, debug_checks=1)
         with pytest.raises(cc.CCError) as ei:
             eng.labels(torch.from_numpy(bad).cuda(), 10)
         assert ei.value.status == 2
         # the context stays usable
         ok = eng.labels(torch.from_numpy(_arr([(0, 1)], dt)).cuda(), 3)
+        assert ok.cpu().tolist() == [0, 0, 2]
+        eng.close()
+        # stream-ordered (the default): the error is the stream's, read by check()
+        eng = cc.Engine(id_bytes=np.dtype(dt).itemsize, route=route)
+        eng.labels(torch.from_numpy(bad).cuda(), 10)
+        with pytest.raises(cc.CCError) as ei:
+            eng.check()
+        assert ei.value.status == 2
+        ok = eng.labels(torch.from_numpy(_arr([(0, 1)], dt)).cuda(), 3)
+        eng.check()
         assert ok.cpu().tolist() == [0, 0, 2]
         eng.close()
 
