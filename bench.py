@@ -48,6 +48,7 @@ WORKLOADS = {
     "rmat22": dict(kind="rmat", scale=22, edge_factor=16, seed=1),
     "planted": dict(kind="planted", seed=1),
     "grid_chains": dict(kind="grid_chains", seed=1, W=8192, nchains=10_000_000),
+    "chung_lu24": dict(kind="chung_lu", seed=1, n=1 << 24, avg_degree=16.0),
     "batch4096": dict(kind="batch", seed=1, G=4096, nmin=1000, nmax=1_000_000),
     "batch512": dict(kind="batch", seed=1, G=512, nmin=1000, nmax=1_000_000),
 }
@@ -64,6 +65,8 @@ def make_graph(name: str):
         return gg.rmat(**w)
     if kind == "planted":
         return gg.planted(**w)
+    if kind == "chung_lu":
+        return gg.chung_lu(**w)
     return gg.grid_chains(**w)
 
 
@@ -540,7 +543,7 @@ def batch_record(args, dev, stream, world: int = 1, rank: int = 0, dist=None, wo
     eo_d, vo_d = eo_h.to(dev), vo_h.to(dev)
     out = torch.empty(n, dtype=torch.int32, device=dev)
     eng = cc.Engine(id_bytes=4, device=dev.index, profile=0)  # SV loop as one captured graph
-    call = lambda: eng.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
+    call = lambda: eng.labels_batched_dev(edges_d, eo_d, vo_d, m, n, out)
     for _ in range(max(args.warmup, 1)):
         call()
     torch.cuda.synchronize()
@@ -578,11 +581,11 @@ def batch_record(args, dev, stream, world: int = 1, rank: int = 0, dist=None, wo
     del per, outs
     # the same batch with the route prediction skipped (every graph SV only)
     sv = cc.Engine(id_bytes=4, device=dev.index, route="sv")
-    sv.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
+    sv.labels_batched_dev(edges_d, eo_d, vo_d, m, n, out)
     torch.cuda.synchronize()
     a.record(stream)
     for _ in range(loops):
-        sv.labels_batched_dev(edges_d, eo_d, vo_d, eo_h, vo_h, out)
+        sv.labels_batched_dev(edges_d, eo_d, vo_d, m, n, out)
     c.record(stream)
     torch.cuda.synchronize()
     ms_sv = a.elapsed_time(c) / loops
@@ -929,6 +932,8 @@ def main() -> int:
         budget = args.cpu_pairs if not args.no_cpu else 0
         configs = {"planted": single_record("planted", args, dev, stream, budget),
                    "grid_chains": single_record("grid_chains", args, dev, stream, budget),
+                   # a power-law graph the K-S heuristic sends to BFS first: the CSR build and BFS kernels
+                   "chung_lu": single_record("chung_lu24", args, dev, stream, budget),
                    "batch4096": batch_record(args, dev, stream),
                    "learned_route": learned_record(args, dev, stream, args.heldout)}
 

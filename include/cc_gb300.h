@@ -230,25 +230,33 @@ cc_status cc_labels_host(cc_ctx *ctx, const void *edges_host, int64_t n, int64_t
  * Labels of G independent graphs in one call (the batched form). Under the
  * K-S policy (and the learned one, which the batch treats the same way)
  * every graph gets its own route prediction, as cc_ks_statistic_batched:
- * one degree pass over all graphs, then the per-graph fits beside the first
- * SV hook pass over all graphs (which needs no route: every vertex starts as
- * its own root); each graph routed to BFS runs the BFS step on its own
- * pairs; then the SV
- * iterations run over the union of all graphs (one cached CUDA graph with a
- * device-driven loop when per-kernel profiling is off). CC_ROUTE_FORCE_SV
- * skips the prediction; CC_ROUTE_FORCE_BFS sends every graph to BFS.
+ * one degree pass over all graphs, then the per-graph fits (largest graph
+ * first) beside the first SV hook pass over all graphs (which needs no
+ * route: every vertex starts as its own root); the graphs routed to BFS take
+ * the BFS step together (one edge-list BFS from all their seeds); then the
+ * SV iterations run over the union of all graphs. CC_ROUTE_FORCE_SV skips
+ * the prediction; CC_ROUTE_FORCE_BFS sends every graph to BFS.
  * cc_get_stats: route = number of graphs that took the BFS step.
- *   edges_dev          concatenated int32 pairs with ids local to each graph
+ *   edges_dev          concatenated int32 pairs with ids local to each graph (16-byte aligned)
  *   edge_offsets_dev   [G+1] int64 (device): graph g owns pairs [eo[g], eo[g+1])
  *   vertex_offsets_dev [G+1] int64 (device): graph g owns vertices [vo[g], vo[g+1]) of labels_out
- *   labels_out_dev     [vo[G]] int32 (device): local labels, min local id of each component
- * edge_offsets_host / vertex_offsets_host must hold the same offsets on the
- * host (they drive the schedule; the device copies drive the kernels).
- * Works for id_bytes = 4 only; sum of vertices < 2^31.
+ *   m_total, n_total   eo[G] and vo[G] (the host sizes the workspace from them)
+ *   labels_out_dev     [n_total] int32 (device): local labels, min local id of each component
+ * Stream-ordered like cc_labels (options.profile = 0): the offsets stay on
+ * the device; every decision (the routes, the overflow fallback of the fits,
+ * the BFS levels, the SV iterations) is taken on the device by conditional
+ * nodes of one CUDA graph, captured once per arguments and workspace and
+ * launched on `stream` (or captured into the caller's graph). The offsets
+ * are checked on the device: not non-decreasing from 0 to the totals gives
+ * the device status CC_ERR_INVALID_ARG (no kernel reads unchecked offsets).
+ * The first call of a shape (log2 of pairs and graphs) with m_total >= 2^24
+ * tunes the schedule of the hook passes (it waits on `stream`). With
+ * options.profile = 1 the offsets are read back and the route is driven from
+ * the host. Works for id_bytes = 4 only; n_total < 2^31.
  */
 cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *edge_offsets_dev,
-                            const int64_t *vertex_offsets_dev, const int64_t *edge_offsets_host,
-                            const int64_t *vertex_offsets_host, int G, void *labels_out_dev, void *stream);
+                            const int64_t *vertex_offsets_dev, int G, int64_t m_total, int64_t n_total,
+                            void *labels_out_dev, void *stream);
 
 /*
  * Degree pass and degree distribution (Section 3.2, Algorithm 2 line 1):
@@ -432,13 +440,13 @@ cc_status cc_measure_l2_rates(cc_ctx *ctx, cc_l2_rates *out, void *stream);
  *   xmin_host, ncand_host  selected xmin (0 without a candidate), number of candidates
  *   route_host           1 = BFS first (D < ks_tau), 0 = SV only
  *   seed_host            local id of the max-degree vertex (ties to the smallest id)
- * The call synchronises `stream`. Errors as cc_labels_batched.
+ * The call reads the offsets back, waits for `stream` and returns the
+ * outputs. Errors as cc_labels_batched (offset errors returned directly).
  */
 cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *edge_offsets_dev,
-                                  const int64_t *vertex_offsets_dev, const int64_t *edge_offsets_host,
-                                  const int64_t *vertex_offsets_host, int G, double *D_host, double *alpha_host,
-                                  int64_t *xmin_host, int64_t *ncand_host, int32_t *route_host, int64_t *seed_host,
-                                  void *stream);
+                                  const int64_t *vertex_offsets_dev, int G, int64_t m_total, int64_t n_total,
+                                  double *D_host, double *alpha_host, int64_t *xmin_host, int64_t *ncand_host,
+                                  int32_t *route_host, int64_t *seed_host, void *stream);
 
 /* Statistics of the last cc_labels call; waits for its stream. Returns the device status of that call.
  * After a stream-ordered call the per-stage times other than ms_total are 0 (they need options.profile). */

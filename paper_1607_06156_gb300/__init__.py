@@ -109,8 +109,8 @@ def lib() -> ctypes.CDLL:
         L.cc_labels.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp]
         L.cc_labels_host.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp]
         L.cc_labels_tuple_sv.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp]
-        L.cc_ks_statistic_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
-        L.cc_labels_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp]
+        L.cc_ks_statistic_batched.argtypes = [_vp, _vp, _vp, _vp, _int, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.cc_labels_batched.argtypes = [_vp, _vp, _vp, _vp, _int, _i64, _i64, _vp, _vp]
         L.cc_degree_distribution.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp]
         L.cc_ks_statistic.argtypes = [_vp, _vp, _i64, _vp, _vp]
         L.cc_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
@@ -299,27 +299,21 @@ class Engine:
         return out
 
     def labels_batched(self, edges, edge_offsets, vertex_offsets, out=None, stream=None):
-        """Local labels of G independent graphs (int32 ids local to each graph)."""
+        """Local labels of G independent graphs (int32 ids local to each graph); the
+        offsets are given on the host and copied to the device."""
         import torch
 
         eo_h, vo_h = _offsets(edge_offsets, vertex_offsets, _pairs(edges, 4, self.device))
-        G = eo_h.numel() - 1
         if out is None:
             out = torch.empty(int(vo_h[-1]), dtype=torch.int32, device=edges.device)
         _device_tensor(out, "out", 4, numel=int(vo_h[-1]), device=self.device)
-        eo_d = eo_h.to(edges.device)
-        vo_d = vo_h.to(edges.device)
-        rc = lib().cc_labels_batched(self._h, edges.data_ptr() if edges.numel() else None, eo_d.data_ptr(),
-                                     vo_d.data_ptr(), eo_h.data_ptr(), vo_h.data_ptr(), G,
-                                     out.data_ptr() if out.numel() else None, _stream_handle(stream, edges.device))
-        _check(rc, "cc_labels_batched")
-        return out
+        return self.labels_batched_dev(edges, eo_h.to(edges.device), vo_h.to(edges.device), int(eo_h[-1]),
+                                       int(vo_h[-1]), out, stream)
 
     def ks_statistic_batched(self, edges, edge_offsets, vertex_offsets, stream=None) -> dict:
         """Per-graph route prediction of a batch (cc_ks_statistic_batched): numpy arrays
         D, alpha, xmin, ncand, route, seed of G entries each."""
         import numpy as np
-        import torch
 
         m = _pairs(edges, 4, self.device)
         eo, vo = _offsets(np.ascontiguousarray(edge_offsets, dtype=np.int64),
@@ -330,28 +324,27 @@ class Engine:
                                                      ("ncand", np.int64), ("route", np.int32), ("seed", np.int64))}
         ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         rc = lib().cc_ks_statistic_batched(self._h, edges.data_ptr() if m else None, eo_d.data_ptr(), vo_d.data_ptr(),
-                                           eo.data_ptr(), vo.data_ptr(), G, ptr(out["D"]), ptr(out["alpha"]),
+                                           G, int(eo[-1]), int(vo[-1]), ptr(out["D"]), ptr(out["alpha"]),
                                            ptr(out["xmin"]), ptr(out["ncand"]), ptr(out["route"]), ptr(out["seed"]),
                                            _stream_handle(stream, edges.device))
         _check(rc, "cc_ks_statistic_batched")
         return out
 
-    def labels_batched_dev(self, edges, eo_dev, vo_dev, eo_host, vo_host, out, stream=None):
-        """cc_labels_batched with offsets already on the device and on the host (no copies).
-        The device offsets must hold the same values as the host ones."""
+    def labels_batched_dev(self, edges, eo_dev, vo_dev, m_total: int, n_total: int, out, stream=None):
+        """cc_labels_batched with the offsets on the device ([G + 1] int64 each) and their
+        last entries given as m_total and n_total; stream-ordered like labels()."""
         m = _pairs(edges, 4, self.device)
-        if eo_host.is_cuda or vo_host.is_cuda or eo_host.element_size() != 8 or vo_host.element_size() != 8 \
-                or not (eo_host.is_contiguous() and vo_host.is_contiguous()):
-            raise ValueError("eo_host and vo_host must be contiguous int64 CPU tensors")
-        G = eo_host.numel() - 1
-        if G < 0 or vo_host.numel() != G + 1 or int(eo_host[-1]) > m:
-            raise ValueError("eo_host and vo_host must hold G + 1 offsets, the last edge offset within the edges")
+        G = eo_dev.numel() - 1
+        if G < 0 or vo_dev.numel() != G + 1:
+            raise ValueError("eo_dev and vo_dev must hold G + 1 offsets each")
+        if not 0 <= m_total <= m or n_total < 0:
+            raise ValueError(f"m_total must be within the {m} pairs of edges and n_total >= 0")
         _device_tensor(eo_dev, "eo_dev", 8, numel=G + 1, device=self.device)
         _device_tensor(vo_dev, "vo_dev", 8, numel=G + 1, device=self.device)
-        _device_tensor(out, "out", 4, numel=int(vo_host[-1]), device=self.device)
+        _device_tensor(out, "out", 4, numel=n_total, device=self.device)
         rc = lib().cc_labels_batched(self._h, edges.data_ptr() if edges.numel() else None, eo_dev.data_ptr(),
-                                     vo_dev.data_ptr(), eo_host.data_ptr(), vo_host.data_ptr(), G,
-                                     out.data_ptr() if out.numel() else None, _stream_handle(stream, edges.device))
+                                     vo_dev.data_ptr(), G, m_total, n_total, out.data_ptr() if out.numel() else None,
+                                     _stream_handle(stream, edges.device))
         _check(rc, "cc_labels_batched")
         return out
 

@@ -100,6 +100,7 @@ struct cc_ctx {
         int level_launches = 0;         // kernels per BFS level
         int sample_stride = 1;          // SV front end stride
         bool edge_bfs = false;          // the BFS branch is the edge-list BFS
+        bool batched = false;           // the batched form (route = graphs that took the BFS step)
     } g_route;
     RouteGraph g_capture;               // the same facts for a call captured into the caller's graph
     const RouteGraph *rg_last = nullptr; // the facts of the last graph-mode call
@@ -126,6 +127,10 @@ struct cc_ctx {
     std::vector<std::pair<int, BatchSchedule>> batch_tuned;
     // graph of every 2^kTileShift-th pair and vertex of the current batch
     Buf tile_pairs, tile_verts;
+    // stream-ordered batched form: checked offsets, the fit order, the BFS step's
+    // per-graph pair counts / offsets / visited minima, CUB scratch
+    Buf bo_e, bo_v, kb_keys, kb_keys2, kb_idx, kb_rcnt, kb_roff, kb_cmin, kb_cub;
+    RouteGraph g_batch_route;
 };
 
 namespace {
@@ -347,6 +352,7 @@ cc_status device_error(uint32_t err) {
     if (err & kErrInvalidEdge) return CC_ERR_INVALID_EDGE;
     if (err & kErrNoConvergence) return CC_ERR_NO_CONVERGENCE;
     if (err & kErrTimeout) return CC_ERR_TIMEOUT;
+    if (err & kErrBadOffsets) return CC_ERR_INVALID_ARG;
     if (err & kErrOverflow) return CC_ERR_CUDA;
     return CC_OK;
 }
@@ -1347,6 +1353,7 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
     const long long before = ctx->stats.launches;
     long long direct = 0;
     rg.edge_bfs = edge_bfs;
+    rg.batched = false;
     rg.level_launches = edge_bfs ? 4 : 11;
     rg.bfs_launches = 0;
     rg.unsure_launches = 0;
@@ -1365,14 +1372,18 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
         launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, ss);
         direct += 2;
     };
-    if (speculate && predict) {
+    // the speculative passes fork after the degree pass (both are bound by
+    // scattered L2 operations, so running them together gains nothing) and
+    // run beside the fit; the learned policy forks them before its features
+    auto fork_speculation = [&]() -> cc_status {
         CU_TRY(cudaEventRecord(ctx->ev_fork, cs));
         CU_TRY(cudaStreamWaitEvent(ctx->side_s, ctx->ev_fork, 0));
         speculative(ctx->side_s);
         CU_TRY(cudaEventRecord(ctx->ev_join, ctx->side_s));
-    } else if (speculate) {
-        speculative(cs);  // forced SV: the same passes, nothing to overlap
-    }
+        return CC_OK;
+    };
+    if (!predict && speculate) speculative(cs);  // forced SV: the same passes, nothing to overlap
+    if (learned && speculate) CC_TRY(fork_speculation());
     if (learned) {
         cudaGraphConditionalHandle hu;
         CC_TRY(cond_handle(cs, &hu));
@@ -1390,9 +1401,12 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
         CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, cs));
         launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), st, ctx->grid, cs);
         direct += 1;
+        // the fit's few blocks are queued ahead of the speculative passes
         CC_TRY(enqueue_small_fit(ctx, n, cs));
+        if (speculate) CC_TRY(fork_speculation());
     } else if (predict) {
         enqueue_degree<T>(ctx, edges, n, m, cs);
+        if (speculate) CC_TRY(fork_speculation());
         if (policy == CC_ROUTE_AUTO) {
             CU_TRY(cudaEventRecord(ctx->ev_fork, cs));
             CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
@@ -1504,8 +1518,16 @@ void stats_from_device(cc_ctx *ctx) {
     S.pred_confidence = h->pred_conf;
     S.pred_cutoff = h->pred_cutoff;
     S.sv_iters = h->loop_done;
-    const int it0 = h->route_taken ? 0 : 1;
-    if (h->route_taken) {
+    // the SV loop continues after iteration 0 (BFS route) or 1 (SV route; always in the batched form)
+    const int it0 = h->route_taken && !rg.batched ? 0 : 1;
+    if (rg.batched) {
+        S.route_source = ctx->opt.route_policy == CC_ROUTE_AUTO || ctx->opt.route_policy == CC_ROUTE_LEARNED ? 0 : 2;
+        S.bfs_levels = h->route_taken ? h->bfs_level : 0;
+        S.m_active[0] = S.m;
+        S.m_active[1] = S.m;
+        S.ks_d = 0.0;
+        S.pred_route = -1;
+    } else if (h->route_taken) {
         S.bfs_levels = h->bfs_level;
         S.bfs_visited = (int64_t)h->bfs_visited;
         S.comp_min = h->cmin;
@@ -1909,6 +1931,266 @@ cc_status batch_routes(cc_ctx *ctx, const int64_t *vo_host, int G, std::vector<i
     return CC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Stream-ordered batched form (options.profile == 0): the route prediction of
+// every graph, the BFS step of the graphs routed to it and the SV over the
+// union as one CUDA graph, decided on the device:
+//   checked offsets and the tile tables of the batch; the degree pass; the
+//   per-graph fits (largest first, sorted on the device) on a
+//   highest-priority stream beside the first hook pass; a WHILE node over
+//   the graphs whose large degrees overflow the per-graph fit (the
+//   single-graph fit of each); an IF node for the BFS step when any graph
+//   is routed to it; then the SV iterations (WHILE) and the labels.
+
+cc_status ensure_batch_graph(cc_ctx *ctx, int G, long long n, long long m) {
+    CC_TRY(ensure_batch_route(ctx, G));
+    const size_t g1 = (size_t)G + 1;
+    CC_TRY(buf_reserve(ctx, ctx->bo_e, g1 * 8));
+    CC_TRY(buf_reserve(ctx, ctx->bo_v, g1 * 8));
+    CC_TRY(buf_reserve(ctx, ctx->kb_keys, g1 * 4));
+    CC_TRY(buf_reserve(ctx, ctx->kb_keys2, g1 * 4));
+    CC_TRY(buf_reserve(ctx, ctx->kb_idx, g1 * 4));
+    CC_TRY(buf_reserve(ctx, ctx->kb_order, g1 * 4));
+    CC_TRY(buf_reserve(ctx, ctx->kb_rcnt, g1 * 8));
+    CC_TRY(buf_reserve(ctx, ctx->kb_roff, g1 * 8));
+    CC_TRY(buf_reserve(ctx, ctx->kb_cmin, g1 * 4));
+    CC_TRY(buf_reserve(ctx, ctx->kb_cub, batch_cub_bytes(G > 0 ? G : 1)));
+    CC_TRY(buf_reserve(ctx, ctx->tile_pairs, (size_t)((m >> kTileShift) + 2) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->tile_verts, (size_t)((n >> kTileShift) + 2) * 4));
+    CC_TRY(ensure_feat(ctx, (size_t)n));
+    return CC_OK;
+}
+
+// checked offsets and the tile tables (also run before the schedule tuner)
+void enqueue_batch_tables(cc_ctx *ctx, const int64_t *eo_u, const int64_t *vo_u, int G, long long m, long long n,
+                          cudaStream_t cs) {
+    int64_t *eo = as<int64_t>(ctx->bo_e), *vo = as<int64_t>(ctx->bo_v);
+    launch_batch_offsets(eo_u, vo_u, G, m, n, eo, vo, as<DevState>(ctx->st), cs);
+    launch_tile_graphs(eo, G, m, as<uint32_t>(ctx->tile_pairs), ctx->grid, cs);
+    launch_tile_graphs(vo, G, n, as<uint32_t>(ctx->tile_verts), ctx->grid, cs);
+}
+
+cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *eo_u, const int64_t *vo_u, int G,
+                              long long m, long long n, int32_t *labels, int cap, BatchSchedule sch, cudaStream_t cs,
+                              cc_ctx::RouteGraph &rg) {
+    DevState *st = as<DevState>(ctx->st);
+    vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
+    uint2 *eb0 = as<uint2>(ctx->ebuf0), *eb1 = as<uint2>(ctx->ebuf1);
+    int64_t *eo = as<int64_t>(ctx->bo_e), *vo = as<int64_t>(ctx->bo_v);
+    const vid_t nt = (vid_t)n;
+    const int policy = ctx->opt.route_policy;
+    const bool predict = policy != CC_ROUTE_FORCE_SV;
+    const uint32_t *ptiles = as<uint32_t>(ctx->tile_pairs), *vtiles = as<uint32_t>(ctx->tile_verts);
+    sch.pair_tiles = ptiles;
+    const long long before = ctx->stats.launches;
+    long long direct = 0;
+    rg.edge_bfs = true;
+    rg.batched = true;
+    rg.level_launches = 4;
+    rg.bfs_launches = 0;
+    rg.unsure_launches = 0;
+    rg.sample_stride = 1;
+    CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), cs));
+    enqueue_batch_tables(ctx, eo_u, vo_u, G, m, n, cs);
+    launch_parent_init(parent, nt, nullptr, 0, ctx->grid, cs);
+    direct += 4;
+    KsBatchScratch sc{as<uint32_t>(ctx->kb_xs), as<unsigned long long>(ctx->kb_cnt), as<unsigned long long>(ctx->kb_cum),
+                      as<double>(ctx->kb_lnx), as<double>(ctx->kb_Dc), as<double>(ctx->kb_Ac), as<double>(ctx->kb_Zc)};
+    KsBatchOut out{as<double>(ctx->kb_D),     as<double>(ctx->kb_alpha), as<long long>(ctx->kb_xmin),
+                   as<long long>(ctx->kb_ntail), as<long long>(ctx->kb_ncand), as<int>(ctx->kb_route),
+                   as<int>(ctx->kb_ovf),      as<unsigned long long>(ctx->kb_seed)};
+    if (predict) {
+        CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, cs));
+        launch_degree_batch(edges, m, eo, vo, G, as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), cs);
+        // the fits (largest graph first) on the highest-priority stream beside the first hook pass
+        CU_TRY(cudaEventRecord(ctx->ev_fork, cs));
+        CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
+        CU_TRY(launch_batch_order(vo, G, as<uint32_t>(ctx->kb_keys), as<uint32_t>(ctx->kb_keys2),
+                                  as<int>(ctx->kb_idx), as<int>(ctx->kb_order), ctx->kb_cub.p, ctx->kb_cub.bytes,
+                                  ctx->grid, ctx->fit_s));
+        launch_ks_batch(as<uint32_t>(ctx->deg), vo, G, sc, out, ctx->opt.ks_min_tail, ctx->opt.ks_min_distinct,
+                        ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->kb_blocks, as<int>(ctx->kb_order),
+                        counter_at<int>(ctx->counters, kCtrKsQueue), ctx->fit_s);
+        CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
+        launch_sv_pass_batch(0, edges, m, eo, vo, G, nt, parent, hooked, nullptr, st, 0, ctx->grid, cs, sch);
+        CU_TRY(cudaStreamWaitEvent(cs, ctx->ev_fit, 0));
+        direct += 6;
+        // graphs with more large degrees than the per-graph fit holds: the single-graph fit, one per iteration
+        KsScratch ks{as<uint32_t>(ctx->ks_xs), as<unsigned long long>(ctx->ks_cnt), as<unsigned long long>(ctx->ks_cum),
+                     as<double>(ctx->ks_lnx), as<double>(ctx->ks_Dc), as<double>(ctx->ks_Ac), as<double>(ctx->ks_Zc),
+                     as<float>(ctx->ks_Df), as<unsigned long long>(ctx->chunk_nz),
+                     as<unsigned long long>(ctx->chunk_mass), ctx->ks_cap};
+        cudaGraphConditionalHandle ho;
+        CC_TRY(cond_handle(cs, &ho));
+        launch_ovf_seek(as<int>(ctx->kb_ovf), G, vo, st, ho, 1, cs);
+        direct += 1;
+        CC_TRY(cond_node(cs, ctx->cap_s2, ho, cudaGraphCondTypeWhile, [&](cudaStream_t bs) -> cc_status {
+            CU_TRY(cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, bs));
+            launch_hist_slice(as<uint32_t>(ctx->deg), as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap, st,
+                              ctx->grid, bs);
+            launch_ks(as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap, ks, st, ctx->opt.ks_min_tail,
+                      ctx->opt.ks_min_distinct, ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->ks_cap, ctx->grid, bs);
+            launch_ovf_store(out, st, bs);
+            launch_ovf_seek(as<int>(ctx->kb_ovf), G, vo, st, ho, 0, bs);
+            return CC_OK;
+        }));
+        // the BFS step of the graphs routed to it (all of them under the forced-BFS policy)
+        cudaGraphConditionalHandle hb;
+        CC_TRY(cond_handle(cs, &hb));
+        CU_TRY(launch_batch_bfs_plan(as<int>(ctx->kb_route), eo, vo, G, policy == CC_ROUTE_FORCE_BFS ? 1 : 0,
+                                     as<unsigned long long>(ctx->kb_rcnt), as<unsigned long long>(ctx->kb_roff),
+                                     ctx->kb_cub.p, ctx->kb_cub.bytes, st, hb, ctx->grid, cs));
+        direct += 3;
+        CC_TRY(cond_node(cs, ctx->cap_s2, hb, cudaGraphCondTypeIf, [&](cudaStream_t bs) -> cc_status {
+            const long long nwords = (n + 31) / 32;
+            uint32_t *fv = as<uint32_t>(ctx->f_vis), *f0 = as<uint32_t>(ctx->f_f0), *f1 = as<uint32_t>(ctx->f_f1);
+            CU_TRY(cudaMemsetAsync(fv, 0, (size_t)nwords * 4, bs));
+            CU_TRY(cudaMemsetAsync(f0, 0, (size_t)nwords * 4, bs));
+            launch_batch_bfs_start(edges, m, eo, vo, G, ptiles, as<unsigned long long>(ctx->kb_rcnt),
+                                   as<unsigned long long>(ctx->kb_roff), as<unsigned long long>(ctx->kb_seed), eb0, fv,
+                                   f0, st, ctx->grid, bs);
+            cudaGraphConditionalHandle hl;
+            CC_TRY(cond_handle(bs, &hl));
+            launch_set_cond(hl, 1u, bs);
+            CC_TRY(cond_node(bs, ctx->cap_s3, hl, cudaGraphCondTypeWhile, [&](cudaStream_t ls) -> cc_status {
+                launch_ebfsg_level<int32_t>(nullptr, 0, eb0, eb1, nt, fv, f0, f1, st, hl, ctx->grid, ls);
+                return CC_OK;
+            }));
+            launch_batch_bfs_finish(fv, n, vo, G, vtiles, as<uint32_t>(ctx->kb_cmin), parent, ctx->grid, bs);
+            rg.bfs_launches = 2 + 1 + 2;
+            return CC_OK;
+        }));
+    } else {
+        launch_sv_pass_batch(0, edges, m, eo, vo, G, nt, parent, hooked, nullptr, st, 0, ctx->grid, cs, sch);
+        direct += 1;
+    }
+    launch_shortcut_all(parent, nt, st, 0, ctx->grid, cs);
+    launch_sv_pass_batch(2, edges, m, eo, vo, G, nt, parent, hooked, eb0, st, 1, ctx->grid, cs, sch);
+    launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, cs);
+    cudaGraphConditionalHandle hs;
+    CC_TRY(cond_handle(cs, &hs));
+    launch_sv_loop_init(st, 1, 0, cap, hs, cs);
+    CC_TRY(cond_node(cs, ctx->cap_s2, hs, cudaGraphCondTypeWhile, [&](cudaStream_t bs) -> cc_status {
+        launch_sv_loop_body(eb0, eb1, nt, parent, hooked, st, hs, ctx->grid, bs);
+        return CC_OK;
+    }));
+    launch_finalize_batch(parent, nt, vo, G, labels, ctx->grid, cs, vtiles);
+    direct += 5;
+    CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, hook_base), cudaMemcpyDeviceToHost, cs));
+    rg.static_launches = ctx->stats.launches - before + direct;
+    return CC_OK;
+}
+
+cc_status labels_batched_graph(cc_ctx *ctx, const int32_t *edges, const int64_t *eo_u, const int64_t *vo_u, int G,
+                               long long m, long long n, int32_t *labels, cudaStream_t s) {
+    cc_stats &S = ctx->stats;
+    const int cap = ctx->opt.max_iters > 0 ? ctx->opt.max_iters : default_max_iters(n);
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    CU_TRY(cudaStreamIsCapturing(s, &cst));
+    const bool user_capture = cst == cudaStreamCaptureStatusActive;
+    cc_status prior = CC_OK;
+    if (!user_capture && ctx->async_outstanding && cudaEventQuery(ctx->ev_done) == cudaSuccess) {
+        prior = device_error(ctx->h_st->err);
+        ctx->async_outstanding = false;
+    }
+    cudaGetLastError();
+    memset(&S, 0, sizeof(S));
+    prof_reset(ctx);
+    for (int e = 0; e < EV_COUNT; e++) ctx->ev_used[e] = false;
+    S.n = n;
+    S.m = m;
+    ctx->graph_last = true;
+    ctx->capturing = user_capture;
+    cc_status r = ensure_sv(ctx, (size_t)n, (size_t)m);
+    if (r == CC_OK) r = ensure_batch_graph(ctx, G, n, m);
+    ctx->capturing = false;
+    CC_TRY(r);
+    // the schedule of the hook passes: tuned on the first call of a shape (outside any capture)
+    BatchSchedule sch;
+    sch.pair_tiles = as<uint32_t>(ctx->tile_pairs);
+    if (!user_capture && m >= (1LL << 24)) {
+        const int key = (ilog2_ceil(m) << 8) | ilog2_ceil(G);
+        bool known = false;
+        for (const auto &e : ctx->batch_tuned) known |= e.first == key;
+        if (!known) {
+            CU_TRY(cudaMemsetAsync(ctx->st.p, 0, sizeof(DevState), s));
+            enqueue_batch_tables(ctx, eo_u, vo_u, G, m, n, s);
+        }
+        CC_TRY(tune_batch(ctx, edges, m, as<int64_t>(ctx->bo_e), as<int64_t>(ctx->bo_v), G, (vid_t)n, s, &sch));
+    } else if (m >= (1LL << 24)) {
+        const int key = (ilog2_ceil(m) << 8) | ilog2_ceil(G);
+        for (const auto &e : ctx->batch_tuned)
+            if (e.first == key) sch = e.second;
+    }
+    S.batch_unroll = sch.unroll;
+    S.batch_grid_mult = sch.grid_mult;
+    S.sv_sample_stride = 1;
+    if (user_capture) {
+        ctx->capturing = true;
+        r = enqueue_batch_route(ctx, edges, eo_u, vo_u, G, m, n, labels, cap, sch, s, ctx->g_capture);
+        ctx->capturing = false;
+        ctx->rg_last = &ctx->g_capture;
+        return r;
+    }
+    std::vector<unsigned char> key = route_key(ctx, 4, n, m, edges, labels, cap);
+    const long long extra[] = {G, sch.unroll, sch.grid_mult, (long long)(uintptr_t)eo_u, (long long)(uintptr_t)vo_u,
+                               (long long)(uintptr_t)ctx->bo_e.p, (long long)(uintptr_t)ctx->kb_route.p,
+                               (long long)(uintptr_t)ctx->tile_pairs.p, (long long)(uintptr_t)ctx->kb_cub.p};
+    key.insert(key.end(), reinterpret_cast<const unsigned char *>(extra),
+               reinterpret_cast<const unsigned char *>(extra) + sizeof(extra));
+    cc_ctx::RouteGraph &rg = ctx->g_batch_route;
+    if (!rg.exec || rg.key != key) {
+        if (rg.exec) cudaGraphExecDestroy(rg.exec);
+        rg.exec = nullptr;
+        CU_TRY(cudaStreamBeginCapture(ctx->cap_s, cudaStreamCaptureModeRelaxed));
+        const cc_status rr = enqueue_batch_route(ctx, edges, eo_u, vo_u, G, m, n, labels, cap, sch, ctx->cap_s, rg);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ctx->cap_s, &g);
+        if (rr != CC_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rr != CC_OK ? rr : CC_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&rg.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            cudaGetLastError();
+            rg.exec = nullptr;
+            return CC_ERR_CUDA;
+        }
+        rg.key.swap(key);
+    }
+    ctx->rg_last = &rg;
+    rec(ctx, EV_START, s);
+    CU_TRY(cudaGraphLaunch(rg.exec, s));
+    rec(ctx, EV_END, s);
+    CU_TRY(cudaEventRecord(ctx->ev_done, s));
+    ctx->async_outstanding = true;
+    if (ctx->opt.debug_checks) {
+        CU_TRY(cudaStreamSynchronize(s));
+        ctx->async_outstanding = false;
+        return device_error(ctx->h_st->err);
+    }
+    return prior;
+}
+
+// The caller's device offsets on the host (the profiled and the statistics
+// entry points wait on the host anyway).
+cc_status offsets_to_host(const int64_t *eo_dev, const int64_t *vo_dev, int G, long long m, long long n,
+                          std::vector<int64_t> &eo, std::vector<int64_t> &vo, cudaStream_t s) {
+    eo.assign((size_t)G + 1, 0);
+    vo.assign((size_t)G + 1, 0);
+    CU_TRY(cudaMemcpyAsync(eo.data(), eo_dev, ((size_t)G + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaMemcpyAsync(vo.data(), vo_dev, ((size_t)G + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    if (eo[0] != 0 || vo[0] != 0 || eo[G] != m || vo[G] != n) return CC_ERR_INVALID_ARG;
+    for (int g = 0; g < G; g++)
+        if (eo[g + 1] < eo[g] || vo[g + 1] < vo[g]) return CC_ERR_INVALID_ARG;
+    for (int g = 0; g < G; g++)  // pairs in a graph without vertices cannot be valid
+        if (vo[g + 1] == vo[g] && eo[g + 1] > eo[g]) return CC_ERR_INVALID_EDGE;
+    return CC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1996,6 +2278,10 @@ cc_status cc_destroy(cc_ctx *ctx) {
     buf_free(ctx->hlabels);
     buf_free(ctx->tile_pairs);
     buf_free(ctx->tile_verts);
+    Buf *bg[] = {&ctx->bo_e, &ctx->bo_v, &ctx->kb_keys, &ctx->kb_keys2, &ctx->kb_idx,
+                 &ctx->kb_rcnt, &ctx->kb_roff, &ctx->kb_cmin, &ctx->kb_cub};
+    for (Buf *b : bg) buf_free(*b);
+    if (ctx->g_batch_route.exec) cudaGraphExecDestroy(ctx->g_batch_route.exec);
     for (Buf &b : ctx->tsv_t32) buf_free(b);
     Buf *tsv[] = {&ctx->tsv_v0,    &ctx->tsv_v1, &ctx->tsv_val,  &ctx->tsv_val2, &ctx->tsv_uniq, &ctx->tsv_agg,
                   &ctx->tsv_dense, &ctx->tsv_pc, &ctx->tsv_done, &ctx->tsv_temp, &ctx->tsv_cnt};
@@ -2193,27 +2479,22 @@ cc_status cc_labels_host(cc_ctx *ctx, const void *edges_host, int64_t n, int64_t
 }
 
 cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *edge_offsets_dev,
-                                  const int64_t *vertex_offsets_dev, const int64_t *edge_offsets_host,
-                                  const int64_t *vertex_offsets_host, int G, double *D_host, double *alpha_host,
-                                  int64_t *xmin_host, int64_t *ncand_host, int32_t *route_host, int64_t *seed_host,
-                                  void *stream) {
-    if (!ctx || G < 0) return CC_ERR_INVALID_ARG;
-    if (G == 0) return CC_OK;
-    if (!edge_offsets_dev || !vertex_offsets_dev || !edge_offsets_host || !vertex_offsets_host || !D_host ||
-        !alpha_host || !xmin_host || !ncand_host || !route_host || !seed_host)
+                                  const int64_t *vertex_offsets_dev, int G, int64_t m_total, int64_t n_total,
+                                  double *D_host, double *alpha_host, int64_t *xmin_host, int64_t *ncand_host,
+                                  int32_t *route_host, int64_t *seed_host, void *stream) {
+    if (!ctx || G < 0 || m_total < 0 || n_total < 0) return CC_ERR_INVALID_ARG;
+    if (G == 0) return m_total || n_total ? CC_ERR_INVALID_ARG : CC_OK;
+    if (!edge_offsets_dev || !vertex_offsets_dev || !D_host || !alpha_host || !xmin_host || !ncand_host ||
+        !route_host || !seed_host)
         return CC_ERR_INVALID_ARG;
-    if (edge_offsets_host[0] != 0 || vertex_offsets_host[0] != 0) return CC_ERR_INVALID_ARG;
-    for (int g = 0; g < G; g++)
-        if (edge_offsets_host[g + 1] < edge_offsets_host[g] || vertex_offsets_host[g + 1] < vertex_offsets_host[g])
-            return CC_ERR_INVALID_ARG;
-    const long long m = edge_offsets_host[G], n = vertex_offsets_host[G];
+    const long long m = m_total, n = n_total;
     if (n >= (1LL << 31) || m >= (1LL << 31)) return CC_ERR_UNSUPPORTED;
-    for (int g = 0; g < G; g++)
-        if (vertex_offsets_host[g + 1] == vertex_offsets_host[g] && edge_offsets_host[g + 1] > edge_offsets_host[g])
-            return CC_ERR_INVALID_EDGE;
     if ((m > 0 && !edges_dev) || ((uintptr_t)edges_dev & 15)) return CC_ERR_INVALID_ARG;
     CU_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> eo_h, vo_h;  // the schedule is built on the host here: the call waits anyway
+    CC_TRY(offsets_to_host(edge_offsets_dev, vertex_offsets_dev, G, m, n, eo_h, vo_h, s));
+    const int64_t *edge_offsets_host = eo_h.data(), *vertex_offsets_host = vo_h.data();
     CC_TRY(ensure_sv(ctx, (size_t)(n > 0 ? n : 1), (size_t)m));
     CC_TRY(ensure_batch_route(ctx, G));
     DevState *st = as<DevState>(ctx->st);
@@ -2242,27 +2523,14 @@ cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int6
     return CC_OK;
 }
 
-cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *edge_offsets_dev,
-                            const int64_t *vertex_offsets_dev, const int64_t *edge_offsets_host,
-                            const int64_t *vertex_offsets_host, int G, void *labels_out_dev, void *stream) {
-    if (!ctx || G < 0) return CC_ERR_INVALID_ARG;
-    if (G == 0) return CC_OK;
-    if (!edge_offsets_dev || !vertex_offsets_dev || !edge_offsets_host || !vertex_offsets_host)
-        return CC_ERR_INVALID_ARG;
-    if (edge_offsets_host[0] != 0 || vertex_offsets_host[0] != 0) return CC_ERR_INVALID_ARG;
-    for (int g = 0; g < G; g++)
-        if (edge_offsets_host[g + 1] < edge_offsets_host[g] || vertex_offsets_host[g + 1] < vertex_offsets_host[g])
-            return CC_ERR_INVALID_ARG;
+// The profiled batched form (options.profile = 1): the same route driven
+// from the host, with every kernel class timed; the offsets are on both sides.
+static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, const int64_t *edge_offsets_dev,
+                                         const int64_t *vertex_offsets_dev, const int64_t *edge_offsets_host,
+                                         const int64_t *vertex_offsets_host, int G, void *labels_out_dev,
+                                         cudaStream_t s) {
     const long long m = edge_offsets_host[G], n = vertex_offsets_host[G];
-    if (n >= (1LL << 31) || m >= (1LL << 31)) return CC_ERR_UNSUPPORTED;
-    for (int g = 0; g < G; g++)  // pairs in a graph without vertices cannot be valid
-        if (vertex_offsets_host[g + 1] == vertex_offsets_host[g] && edge_offsets_host[g + 1] > edge_offsets_host[g])
-            return CC_ERR_INVALID_EDGE;
-    if (n == 0) return CC_OK;
-    if (!labels_out_dev || (m > 0 && !edges_dev) || ((uintptr_t)edges_dev & 15)) return CC_ERR_INVALID_ARG;
-    CU_TRY(cudaSetDevice(ctx->device));
-    cudaStream_t s = (cudaStream_t)stream;
-    ctx->last_stream = s;
+    ctx->graph_last = false;
     CC_TRY(ensure_sv(ctx, (size_t)n, (size_t)m));
     DevState *st = as<DevState>(ctx->st);
     cc_stats &S = ctx->stats;
@@ -2429,6 +2697,38 @@ cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *e
     ctx->last_status = stt;
     S.status = stt;
     return stt;
+}
+
+cc_status cc_labels_batched(cc_ctx *ctx, const void *edges_dev, const int64_t *edge_offsets_dev,
+                            const int64_t *vertex_offsets_dev, int G, int64_t m_total, int64_t n_total,
+                            void *labels_out_dev, void *stream) {
+    if (!ctx || G < 0 || m_total < 0 || n_total < 0) return CC_ERR_INVALID_ARG;
+    if (G == 0) return m_total || n_total ? CC_ERR_INVALID_ARG : CC_OK;
+    if (!edge_offsets_dev || !vertex_offsets_dev) return CC_ERR_INVALID_ARG;
+    if (n_total >= (1LL << 31) || m_total >= (1LL << 31)) return CC_ERR_UNSUPPORTED;
+    if (n_total == 0) return m_total > 0 ? CC_ERR_INVALID_EDGE : CC_OK;
+    if (!labels_out_dev || (m_total > 0 && !edges_dev) || ((uintptr_t)edges_dev & 15)) return CC_ERR_INVALID_ARG;
+    if (ctx->opt.id_bytes != 4) return CC_ERR_INVALID_ARG;
+    CU_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    cc_status st;
+    if (ctx->opt.profile) {
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        CU_TRY(cudaStreamIsCapturing(s, &cst));
+        if (cst == cudaStreamCaptureStatusActive) return CC_ERR_INVALID_ARG;  // profiling waits on the host
+        std::vector<int64_t> eo, vo;
+        st = offsets_to_host(edge_offsets_dev, vertex_offsets_dev, G, m_total, n_total, eo, vo, s);
+        if (st == CC_OK)
+            st = labels_batched_profiled(ctx, edges_dev, edge_offsets_dev, vertex_offsets_dev, eo.data(), vo.data(), G,
+                                         labels_out_dev, s);
+    } else {
+        st = labels_batched_graph(ctx, (const int32_t *)edges_dev, edge_offsets_dev, vertex_offsets_dev, G, m_total,
+                                  n_total, (int32_t *)labels_out_dev, s);
+    }
+    ctx->last_status = st;
+    ctx->stats.status = st;
+    return st;
 }
 
 cc_status cc_degree_distribution(cc_ctx *ctx, const void *edges_dev, int64_t n, int64_t m, uint32_t *deg_out_dev,

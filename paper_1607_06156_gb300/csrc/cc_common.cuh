@@ -25,6 +25,7 @@ enum : uint32_t {
     kErrOverflow = 2u,     // an internal capacity was exceeded (a bug guard, never expected)
     kErrNoConvergence = 4u,
     kErrTimeout = 8u,      // a bounded device wait (an mbarrier of a bulk copy) ran out
+    kErrBadOffsets = 16u,  // batched form: offsets not non-decreasing from 0 to the totals
 };
 
 // Device-resident bookkeeping for one cc_labels call. Zeroed at the start of
@@ -71,6 +72,10 @@ struct DevState {
     unsigned long long bfs_explored;        // CSR BFS: adjacency entries of the levels expanded so far
     unsigned long long bfs_prev_f;          // CSR BFS: frontier size of the previous level
     unsigned long long bfs_qcount;          // CSR BFS: bitmap -> queue counter
+    // graph-driven batched form
+    int batch_g;                            // graph of the current single-graph fit (G: none left)
+    int batch_pad;
+    long long batch_base, batch_ng;         // its first union id and vertex count
     unsigned long long kept[kMaxIters];     // active pairs written by SV iteration i
     unsigned long long hooked[kMaxIters];   // roots hooked in SV iteration i
     unsigned long long hook_base[kMaxIters + 1];  // start of iteration i's slice of the hooked list

@@ -256,4 +256,26 @@ void launch_fit_one(const uint32_t *deg, long long n, int64_t *vo, KsBatchScratc
 void launch_merge_visited(const uint32_t *vis, long long ng, long long base, const DevState *st, vid_t *parent,
                           int grid, cudaStream_t s);
 
+// k_batch_graph.cu: the batched form's prediction and BFS step on the device.
+void launch_hist_slice(const uint32_t *deg, uint32_t *hist, uint32_t *ovf, unsigned long long ovf_cap, DevState *st,
+                       int grid, cudaStream_t s);
+size_t batch_cub_bytes(int G);
+void launch_set_cond(cudaGraphConditionalHandle h, unsigned v, cudaStream_t s);
+void launch_batch_offsets(const int64_t *eo, const int64_t *vo, int G, long long m, long long n, int64_t *eo_v,
+                          int64_t *vo_v, DevState *st, cudaStream_t s);
+cudaError_t launch_batch_order(const int64_t *vo, int G, uint32_t *keys, uint32_t *keys_sorted, int *idx, int *order,
+                               void *tmp, size_t tmp_bytes, int grid, cudaStream_t s);
+void launch_ovf_seek(const int *flag, int G, const int64_t *vo, DevState *st, cudaGraphConditionalHandle h, int first,
+                     cudaStream_t s);
+void launch_ovf_store(KsBatchOut out, const DevState *st, cudaStream_t s);
+cudaError_t launch_batch_bfs_plan(const int *route, const int64_t *eo, const int64_t *vo, int G, int force_all,
+                                  unsigned long long *cnt, unsigned long long *off, void *tmp, size_t tmp_bytes,
+                                  DevState *st, cudaGraphConditionalHandle h, int grid, cudaStream_t s);
+void launch_batch_bfs_start(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
+                            const uint32_t *tg, const unsigned long long *cnt, const unsigned long long *off,
+                            const unsigned long long *seedkey, uint2 *list, uint32_t *vis, uint32_t *cur, DevState *st,
+                            int grid, cudaStream_t s);
+void launch_batch_bfs_finish(const uint32_t *vis, long long n, const int64_t *vo, int G, const uint32_t *vtg,
+                             uint32_t *cmin, vid_t *parent, int grid, cudaStream_t s);
+
 }  // namespace ccg

@@ -272,6 +272,35 @@ __global__ void __launch_bounds__(kBlock) k_hist(const uint32_t *__restrict__ de
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
+// k_hist over the degree slice of one graph of a batch (DevState::batch_base,
+// batch_ng; ids local to that graph): the single-graph fit of a graph whose
+// large degrees overflow the per-graph fit.
+__global__ void __launch_bounds__(kBlock) k_hist_slice(const uint32_t *__restrict__ deg, uint32_t *hist, uint32_t *ovf,
+                                                       unsigned long long ovf_cap, DevState *st) {
+    if (st->batch_ng <= 0) return;
+    __shared__ uint32_t sh[kHistSmem];
+    for (int i = threadIdx.x; i < (int)kHistSmem; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint32_t *d = deg + st->batch_base;
+    const long long n = st->batch_ng;
+    unsigned long long best = 0;
+    for (long long v = gtid(); v < n; v += gstride()) hist_one(d[v], (vid_t)v, sh, hist, ovf, ovf_cap, st, best);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long b = __shfl_xor_sync(0xffffffffu, best, o);
+        best = b > best ? b : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(&st->maxkey, best);
+    __syncthreads();
+    for (int i = threadIdx.x; i < (int)kHistSmem; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+void launch_hist_slice(const uint32_t *deg, uint32_t *hist, uint32_t *ovf, unsigned long long ovf_cap, DevState *st,
+                       int grid, cudaStream_t s) {
+    k_hist_slice<<<grid, kBlock, 0, s>>>(deg, hist, ovf, ovf_cap, st);
+}
+
 // ---------------------------------------------------------------------------
 // Distinct degrees. The dense bins [1, min(maxdeg+1, kHistDense)) are split
 // into chunks of kChunk; k_distinct_count counts nonzero bins and their mass

@@ -166,8 +166,8 @@ def test_argument_errors_return_before_any_device_call():
     assert L.cc_get_stats(None, ctypes.byref(cc.Stats())) == ARG
     for f in (L.cc_labels, L.cc_labels_host, L.cc_labels_tuple_sv):
         assert f(None, p, 10, 5, p, None) == ARG
-    assert L.cc_labels_batched(None, p, p, p, p, p, 1, p, None) == ARG
-    assert L.cc_ks_statistic_batched(None, p, p, p, p, p, 1, p, p, p, p, p, p, None) == ARG
+    assert L.cc_labels_batched(None, p, p, p, 1, 10, 10, p, None) == ARG
+    assert L.cc_ks_statistic_batched(None, p, p, p, 1, 10, 10, p, p, p, p, p, p, None) == ARG
     assert L.cc_degree_distribution(None, p, 10, 5, p, p, 4, None) == ARG
     assert L.cc_ks_statistic(None, p, 4, p, None) == ARG
     assert L.cc_route_features(None, p, 10, 5, p, None) == ARG

@@ -115,17 +115,16 @@ def test_batched_checks():
             eng.labels_batched(edges, torch.as_tensor(eoff), torch.as_tensor(voff), out=Dev((149,)), stream=0)
     with pytest.raises(ValueError, match="the edges hold 30"):
         eng.ks_statistic_batched(e, np.array([0, 40]), np.array([0, 5]), stream=0)
-    eo_h, vo_h = torch.as_tensor(eo), torch.as_tensor(vo)
-    _reaches_the_boundary(lambda: eng.labels_batched_dev(e, Dev((3,), torch.int64), Dev((3,), torch.int64), eo_h,
-                                                         vo_h, Dev((150,)), stream=0))
-    for eod, vod, eoh, voh, o, msg in (
-            (Dev((2,), torch.int64), Dev((3,), torch.int64), eo_h, vo_h, Dev((150,)), "eo_dev holds 2"),
-            (Dev((3,)), Dev((3,), torch.int64), eo_h, vo_h, Dev((150,)), "8-byte"),
-            (Dev((3,), torch.int64), Dev((3,), torch.int64), eo_h.int(), vo_h, Dev((150,)), "int64 CPU"),
-            (Dev((3,), torch.int64), Dev((3,), torch.int64), eo_h, vo_h[:2], Dev((150,)), "G \\+ 1"),
-            (Dev((3,), torch.int64), Dev((3,), torch.int64), eo_h, vo_h, Dev((100,)), "150 are needed")):
+    _reaches_the_boundary(lambda: eng.labels_batched_dev(e, Dev((3,), torch.int64), Dev((3,), torch.int64), 30, 150,
+                                                         Dev((150,)), stream=0))
+    for eod, vod, m_tot, n_tot, o, msg in (
+            (Dev((2,), torch.int64), Dev((3,), torch.int64), 30, 150, Dev((150,)), "G \\+ 1"),
+            (Dev((3,)), Dev((3,), torch.int64), 30, 150, Dev((150,)), "8-byte"),
+            (Dev((3,), torch.int64), Dev((3,), torch.int64), 31, 150, Dev((150,)), "within the 30 pairs"),
+            (Dev((3,), torch.int64), Dev((3,), torch.int64), 30, -1, Dev((150,)), "n_total"),
+            (Dev((3,), torch.int64), Dev((3,), torch.int64), 30, 150, Dev((100,)), "150 are needed")):
         with pytest.raises(ValueError, match=msg):
-            eng.labels_batched_dev(e, eod, vod, eoh, voh, o, stream=0)
+            eng.labels_batched_dev(e, eod, vod, m_tot, n_tot, o, stream=0)
 
 
 def test_degree_ks_and_feature_checks():

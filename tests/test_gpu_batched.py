@@ -80,7 +80,7 @@ def test_local_id_out_of_its_graph_is_rejected():
     eoff = np.array([0, 1, 3], dtype=np.int64)
     voff = np.array([0, 10, 13], dtype=np.int64)
     with pytest.raises(cc.CCError) as ei:
-        _run_batched(torch, edges, eoff, voff)
+        _run_batched(torch, edges, eoff, voff, debug_checks=1)
     assert ei.value.status == 2
 
 
