@@ -195,7 +195,7 @@ def kernel_class(name: str):
     return None
 
 
-def ncu_summary(csv_path: str, workload: str, scale_to: dict, command: str) -> dict:
+def ncu_summary(csv_path: str, workload: str, scale_to: dict, command: str, calls: int = 0) -> dict:
     """DRAM bytes per cc_labels call of each kernel class from an ncu --csv
     capture of gpu__time_duration.sum, dram__bytes_read.sum and
     dram__bytes_write.sum: the class's bytes over all captured launches
@@ -223,9 +223,10 @@ def ncu_summary(csv_path: str, workload: str, scale_to: dict, command: str) -> d
             continue
         tot[cls] = tot.get(cls, 0.0) + L.get("dram__bytes_read.sum", 0.0) + L.get("dram__bytes_write.sum", 0.0)
         cnt[cls] = cnt.get(cls, 0) + 1
-    calls = cnt.get("hist", 0)
+    if calls <= 0:  # a capture of every kernel: the histogram kernel runs once per call
+        calls = cnt.get("hist", 0)
     if calls <= 0:
-        raise SystemExit("no histogram launches in the capture: cannot count the calls")
+        raise SystemExit("no histogram launches in the capture: give the number of calls captured")
     per = {k: tot[k] / calls for k in tot}
     out = {"sources_hash": sources_hash(), "command": command, "launches": cnt, "calls": calls,
            "note": f"dram__bytes_read.sum + dram__bytes_write.sum per cc_labels call and kernel class, captured on "
@@ -715,13 +716,16 @@ def main() -> int:
     ap.add_argument("--ncu-summary", metavar="CSV",
                     help="print the DRAM traffic summary of an ncu --csv capture of --workload and exit")
     ap.add_argument("--ncu-command", default="", help="the command line of that capture (recorded)")
+    ap.add_argument("--ncu-calls", type=int, default=0,
+                    help="cc_labels calls the capture covers (needed when it holds one kernel class, -k)")
     args = ap.parse_args()
     if args.ncu_summary:
         w = WORKLOADS[args.workload]
         scale = {}
         if w["kind"] == "rmat" and w["scale"] < 24:
             scale["rmat24"] = float(2 ** (24 - w["scale"]))
-        print(json.dumps(ncu_summary(args.ncu_summary, args.workload, scale, args.ncu_command), indent=1))
+        print(json.dumps(ncu_summary(args.ncu_summary, args.workload, scale, args.ncu_command, args.ncu_calls),
+                         indent=1))
         return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

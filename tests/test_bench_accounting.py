@@ -101,3 +101,18 @@ def test_traffic_summary_per_call(tmp_path):
     assert out["traffic_per_call"]["rmat22"]["hist"] == pytest.approx(120.0)
     assert out["traffic_per_call"]["rmat24"]["degree"] == pytest.approx(4 * 1060.0)
     json.dumps(out)
+
+
+def test_traffic_summary_of_one_kernel_class(tmp_path):
+    """A capture of one class (ncu -k): the calls are given, not counted."""
+    rows = [["ID", "Kernel Name", "Metric Name", "Metric Value"]]
+    for i in range(3):
+        rows.append([str(i), "void ccg::k_degree_hubs<int>(x)", "dram__bytes_read.sum", "900"])
+        rows.append([str(i), "void ccg::k_degree_hubs<int>(x)", "dram__bytes_write.sum", "30"])
+    p = tmp_path / "cap.csv"
+    with open(p, "w", newline="") as f:
+        csv.writer(f, quoting=csv.QUOTE_ALL).writerows(rows)
+    with pytest.raises(SystemExit):
+        bench.ncu_summary(str(p), "rmat22", {}, "cmd")
+    out = bench.ncu_summary(str(p), "rmat22", {}, "cmd", calls=3)
+    assert out["traffic_per_call"]["rmat22"]["degree"] == pytest.approx(930.0)
