@@ -48,12 +48,20 @@ WORKLOADS = {
     "rmat22": dict(kind="rmat", scale=22, edge_factor=16, seed=1),
     "planted": dict(kind="planted", seed=1),
     "grid_chains": dict(kind="grid_chains", seed=1, W=8192, nchains=10_000_000),
+    "grid_chains_67m": dict(kind="grid_chains", seed=1, W=4096, nchains=2_500_000),
     "chung_lu24": dict(kind="chung_lu", seed=1, n=1 << 24, avg_degree=16.0),
     "batch4096": dict(kind="batch", seed=1, G=4096, nmin=1000, nmax=1_000_000),
     "batch512": dict(kind="batch", seed=1, G=512, nmin=1000, nmax=1_000_000),
 }
 KERNEL_FILES = ["cc_common.cuh", "ks_math.cuh", "k_degree.cu", "k_degree_part.cu", "k_sv.cu", "k_bfs.cu", "k_bucket.cu",
                 "k_batch_route.cu", "cc_api.cu"]
+# the sources of each kernel class's kernels and launchers: a traffic capture
+# stays valid while these are unchanged (another class's kernel may change)
+CLASS_FILES = {
+    "degree": ["cc_common.cuh", "k_degree.cu", "k_degree_part.cu", "launch_cfg.cu"],
+    "hist": ["cc_common.cuh", "k_degree.cu", "launch_cfg.cu"],
+    "ks": ["cc_common.cuh", "ks_math.cuh", "k_degree.cu", "launch_cfg.cu"],
+}
 
 
 def make_graph(name: str):
@@ -147,9 +155,10 @@ def l2_ops(cls: str, st: dict) -> tuple[float, str]:
     return 0.0, "gather"
 
 
-def sources_hash() -> str:
+def sources_hash(cls: str | None = None) -> str:
+    """Hash of the kernel sources (of one kernel class's files when given)."""
     h = hashlib.sha256()
-    for f in KERNEL_FILES:
+    for f in CLASS_FILES.get(cls, KERNEL_FILES) if cls else KERNEL_FILES:
         with open(os.path.join(ROOT, "paper_1607_06156_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -163,7 +172,10 @@ def ncu_traffic(kernel_cls: str, workload: str):
         d = json.load(open(p))
     except (OSError, ValueError):
         return None
-    if d.get("sources_hash") != sources_hash():
+    cls = d.get("kernel_class")
+    if cls is not None and cls != kernel_cls:
+        return None
+    if d.get("sources_hash") != sources_hash(cls):
         return None
     return d.get("traffic_per_call", {}).get(workload, {}).get(kernel_cls)
 
@@ -195,7 +207,8 @@ def kernel_class(name: str):
     return None
 
 
-def ncu_summary(csv_path: str, workload: str, scale_to: dict, command: str, calls: int = 0) -> dict:
+def ncu_summary(csv_path: str, workload: str, scale_to: dict, command: str, calls: int = 0,
+                kernel_cls: str | None = None) -> dict:
     """DRAM bytes per cc_labels call of each kernel class from an ncu --csv
     capture of gpu__time_duration.sum, dram__bytes_read.sum and
     dram__bytes_write.sum: the class's bytes over all captured launches
@@ -203,7 +216,8 @@ def ncu_summary(csv_path: str, workload: str, scale_to: dict, command: str, call
     on the heuristic route). The roofline divides it by the class's timed
     launches per call, like the algorithmic bytes. `scale_to` maps another
     workload to the ratio of its pairs to this one's (the streamed pairs
-    dominate the traffic)."""
+    dominate the traffic). With `kernel_cls` the capture holds that class
+    only (ncu -k), and the summary is tied to that class's sources."""
     import csv
 
     rows = list(csv.reader(open(csv_path)))
@@ -219,7 +233,7 @@ def ncu_summary(csv_path: str, workload: str, scale_to: dict, command: str, call
     tot, cnt = {}, {}
     for L in launches.values():
         cls = kernel_class(L["name"])
-        if cls is None:
+        if cls is None or (kernel_cls is not None and cls != kernel_cls):
             continue
         tot[cls] = tot.get(cls, 0.0) + L.get("dram__bytes_read.sum", 0.0) + L.get("dram__bytes_write.sum", 0.0)
         cnt[cls] = cnt.get(cls, 0) + 1
@@ -228,7 +242,8 @@ def ncu_summary(csv_path: str, workload: str, scale_to: dict, command: str, call
     if calls <= 0:
         raise SystemExit("no histogram launches in the capture: give the number of calls captured")
     per = {k: tot[k] / calls for k in tot}
-    out = {"sources_hash": sources_hash(), "command": command, "launches": cnt, "calls": calls,
+    out = {"sources_hash": sources_hash(kernel_cls), "kernel_class": kernel_cls, "command": command,
+           "launches": cnt, "calls": calls,
            "note": f"dram__bytes_read.sum + dram__bytes_write.sum per cc_labels call and kernel class, captured on "
                    f"{workload}" + "".join(f"; {w}: scaled by the pair ratio x{f:g}" for w, f in scale_to.items()),
            "traffic_per_call": {workload: per}}
@@ -606,7 +621,8 @@ def batch_record(args, dev, stream, world: int = 1, rank: int = 0, dist=None, wo
             "sv_only_batched": {"value": m / (ms_sv / 1e3), "ms_per_step": ms_sv,
                                 "note": "route prediction skipped (CC_ROUTE_FORCE_SV)"},
             "route_policy": "auto (a K-S fit per graph)", "graphs_routed_bfs": st["route"],
-            "schedule": {"unroll": st["batch_unroll"], "grid_mult": st["batch_grid_mult"]},
+            "schedule": {"unroll": st["batch_unroll"], "grid_mult": st["batch_grid_mult"],
+                         "degree_vec": st["batch_deg_vec"], "sv_front_end": st["sv_sample_stride"] == -1},
             "roofline": roofline_of(kms, kla, st, 4, args.steps, workload) | {"kernel": dom},
             "kernels": kernel_table(kms, kla, st, 4, args.steps), "sv_iters": st["sv_iters"],
             "m_active": st["m_active"], "labels_vs_oracle": same, "graphs_checked": checked, "cpu_baseline": cpu}
@@ -718,14 +734,15 @@ def main() -> int:
     ap.add_argument("--ncu-command", default="", help="the command line of that capture (recorded)")
     ap.add_argument("--ncu-calls", type=int, default=0,
                     help="cc_labels calls the capture covers (needed when it holds one kernel class, -k)")
+    ap.add_argument("--ncu-class", default=None, help="the one kernel class the capture holds (ncu -k)")
     args = ap.parse_args()
     if args.ncu_summary:
         w = WORKLOADS[args.workload]
         scale = {}
         if w["kind"] == "rmat" and w["scale"] < 24:
             scale["rmat24"] = float(2 ** (24 - w["scale"]))
-        print(json.dumps(ncu_summary(args.ncu_summary, args.workload, scale, args.ncu_command, args.ncu_calls),
-                         indent=1))
+        print(json.dumps(ncu_summary(args.ncu_summary, args.workload, scale, args.ncu_command, args.ncu_calls,
+                                     args.ncu_class), indent=1))
         return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -97,6 +97,8 @@ typedef struct {
                                one block of pairs in k (k = sv_sample_stride, 1..1024) join most of
                                every large component; 0 = default (from 2^22 pairs: k = the largest
                                power of two <= 2m/n, at most 64, none if that is below 4), 1 = none;
+                               the batched form, when this is > 1, samples each graph by that rule on
+                               its own m_g and n_g (off by default);
                                the labels are the same either way */
     int reserved[1];
 } cc_options;
@@ -156,8 +158,9 @@ typedef struct {
     int32_t batch_unroll;               /* batched form: tuned 16-byte vectors per thread per tile of the hook passes */
     int32_t batch_grid_mult;            /* batched form: tuned blocks per launch, in resident-grid multiples */
     int32_t sv_sample_stride;           /* SV front end: one block of pairs in this many was sampled (1 = no
-                                           front end; 0 = no first pass over the input pairs in this call) */
-    int32_t pad2;
+                                           front end; 0 = no first pass over the input pairs in this call;
+                                           -1 = batched form, each graph with its own stride) */
+    int32_t batch_deg_vec;              /* batched form: tuned 16-byte vectors per thread per tile of the degree pass */
 } cc_stats;
 
 /* Fills *opt with the defaults listed above. */

@@ -863,6 +863,16 @@ int sample_stride(const cc_ctx *ctx, vid_t n, long long m) {
     return p >= 4 ? p : 1;
 }
 
+// The batched form's front end (per-graph strides on the device): on when
+// options.sv_sample_stride > 1. Off by default: on the 4,096-graph batch
+// (79% of the pairs in R-MAT graphs with 2m/n = 16) it cut the pairs left
+// after the first gather pass from 1.71G to 637M, but its passes and the
+// extra full shortcut over the union took 24.5 ms against 15.2 ms for one
+// hook pass over all pairs, and the gather pass only fell from 23.9 to 22.4
+// ms (it is bound by the parent gathers, not by the survivors it writes):
+// 94.2 ms a call against 86.8.
+bool batch_front(const cc_ctx *ctx, long long m) { return ctx->opt.sv_sample_stride > 1 && m > 0; }
+
 // The first SV pass on stream s while every vertex is its own root; after it
 // every vertex points at its root. With a sample stride k > 1: the front end
 // (a hook pass with identity parents and a one-hop hook pass over the sample,
@@ -1756,9 +1766,8 @@ cc_status labels_host_impl(cc_ctx *ctx, const void *edges_host, vid_t n, long lo
 // with the stride, 33.2 ms in order. The batched hook passes keep the
 // stride: with the counter (two more barriers per tile) the gather pass went
 // from 23.9 to 26.7 ms.
-constexpr bool kBatchTileQueue = true;
 unsigned long long *tile_queue(cc_ctx *ctx) {
-    return kBatchTileQueue ? counter_at<unsigned long long>(ctx->counters, kCtrTileQueue) : nullptr;
+    return counter_at<unsigned long long>(ctx->counters, kCtrTileQueue);
 }
 
 // Schedule tuner of the batched form. The hook passes over a batch map each
@@ -1814,6 +1823,24 @@ cc_status tune_batch(cc_ctx *ctx, const int32_t *edges, long long m, const int64
         if (ms < best) {
             best = ms;
             *out = c;
+        }
+    }
+    // the degree pass (idempotent after a reset of the counts): vectors per
+    // thread and tile, fewer blocks resident with more loads in flight each
+    if (ctx->deg.p && ctx->deg.bytes >= (size_t)nt * 4) {
+        float best_deg = 1e30f;
+        for (int vec : {2, 4, 8}) {
+            CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)nt * 4, s));
+            CU_TRY(cudaEventRecord(a, s));
+            launch_degree_batch(edges, m, eo, vo, G, as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), vec, s);
+            CU_TRY(cudaEventRecord(b, s));
+            CU_TRY(cudaEventSynchronize(b));
+            float ms = 0.f;
+            CU_TRY(cudaEventElapsedTime(&ms, a, b));
+            if (ms < best_deg) {
+                best_deg = ms;
+                out->deg_vec = vec;
+            }
         }
     }
     ctx->batch_tuned.push_back({key, *out});
@@ -1970,6 +1997,25 @@ void enqueue_batch_tables(cc_ctx *ctx, const int64_t *eo_u, const int64_t *vo_u,
     launch_tile_graphs(vo, G, n, as<uint32_t>(ctx->tile_verts), ctx->grid, cs);
 }
 
+// The first hook passes over a batch, every vertex its own root: one pass
+// over all pairs, or with the front end (Section 3.1's joins over a sample
+// first, so that the first gather pass finds most pairs inside one tree) a
+// pass over the sampled tiles and the graphs that are not sampled, a full
+// shortcut, and a gather pass over the sampled tiles. Returns the launches.
+int enqueue_batch_first_hooks(cc_ctx *ctx, const int32_t *edges, long long m, const int64_t *eo, const int64_t *vo,
+                              int G, vid_t nt, const BatchSchedule &sch, cudaStream_t cs) {
+    DevState *st = as<DevState>(ctx->st);
+    vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
+    if (!sch.front) {
+        launch_sv_pass_batch(0, edges, m, eo, vo, G, nt, parent, hooked, nullptr, st, 0, ctx->grid, cs, sch);
+        return 1;
+    }
+    launch_sv_pass_batch(5, edges, m, eo, vo, G, nt, parent, hooked, nullptr, st, 0, ctx->grid, cs, sch);
+    launch_shortcut_all(parent, nt, st, 0, ctx->grid, cs);
+    launch_sv_pass_batch(6, edges, m, eo, vo, G, nt, parent, hooked, nullptr, st, 0, ctx->grid, cs, sch);
+    return 3;
+}
+
 cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *eo_u, const int64_t *vo_u, int G,
                               long long m, long long n, int32_t *labels, int cap, BatchSchedule sch, cudaStream_t cs,
                               cc_ctx::RouteGraph &rg) {
@@ -1989,7 +2035,7 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
     rg.level_launches = 4;
     rg.bfs_launches = 0;
     rg.unsure_launches = 0;
-    rg.sample_stride = 1;
+    rg.sample_stride = sch.front ? -1 : 1;
     CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), cs));
     enqueue_batch_tables(ctx, eo_u, vo_u, G, m, n, cs);
     launch_parent_init(parent, nt, nullptr, 0, ctx->grid, cs);
@@ -2001,7 +2047,8 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
                    as<int>(ctx->kb_ovf),      as<unsigned long long>(ctx->kb_seed)};
     if (predict) {
         CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, cs));
-        launch_degree_batch(edges, m, eo, vo, G, as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), cs);
+        launch_degree_batch(edges, m, eo, vo, G, as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), sch.deg_vec,
+                            cs);
         // the fits (largest graph first) on the highest-priority stream beside the first hook pass
         CU_TRY(cudaEventRecord(ctx->ev_fork, cs));
         CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
@@ -2012,9 +2059,8 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
                         ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->kb_blocks, as<int>(ctx->kb_order),
                         counter_at<int>(ctx->counters, kCtrKsQueue), ctx->fit_s);
         CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
-        launch_sv_pass_batch(0, edges, m, eo, vo, G, nt, parent, hooked, nullptr, st, 0, ctx->grid, cs, sch);
+        direct += 5 + enqueue_batch_first_hooks(ctx, edges, m, eo, vo, G, nt, sch, cs);
         CU_TRY(cudaStreamWaitEvent(cs, ctx->ev_fit, 0));
-        direct += 6;
         // graphs with more large degrees than the per-graph fit holds: the single-graph fit, one per iteration
         KsScratch ks{as<uint32_t>(ctx->ks_xs), as<unsigned long long>(ctx->ks_cnt), as<unsigned long long>(ctx->ks_cum),
                      as<double>(ctx->ks_lnx), as<double>(ctx->ks_Dc), as<double>(ctx->ks_Ac), as<double>(ctx->ks_Zc),
@@ -2061,8 +2107,7 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
             return CC_OK;
         }));
     } else {
-        launch_sv_pass_batch(0, edges, m, eo, vo, G, nt, parent, hooked, nullptr, st, 0, ctx->grid, cs, sch);
-        direct += 1;
+        direct += enqueue_batch_first_hooks(ctx, edges, m, eo, vo, G, nt, sch, cs);
     }
     launch_shortcut_all(parent, nt, st, 0, ctx->grid, cs);
     launch_sv_pass_batch(2, edges, m, eo, vo, G, nt, parent, hooked, eb0, st, 1, ctx->grid, cs, sch);
@@ -2122,9 +2167,11 @@ cc_status labels_batched_graph(cc_ctx *ctx, const int32_t *edges, const int64_t 
         for (const auto &e : ctx->batch_tuned)
             if (e.first == key) sch = e.second;
     }
+    sch.front = batch_front(ctx, m);
     S.batch_unroll = sch.unroll;
     S.batch_grid_mult = sch.grid_mult;
-    S.sv_sample_stride = 1;
+    S.batch_deg_vec = sch.deg_vec;
+    S.sv_sample_stride = sch.front ? -1 : 1;
     if (user_capture) {
         ctx->capturing = true;
         r = enqueue_batch_route(ctx, edges, eo_u, vo_u, G, m, n, labels, cap, sch, s, ctx->g_capture);
@@ -2133,8 +2180,8 @@ cc_status labels_batched_graph(cc_ctx *ctx, const int32_t *edges, const int64_t 
         return r;
     }
     std::vector<unsigned char> key = route_key(ctx, 4, n, m, edges, labels, cap);
-    const long long extra[] = {G, sch.unroll, sch.grid_mult, (long long)(uintptr_t)eo_u, (long long)(uintptr_t)vo_u,
-                               (long long)(uintptr_t)ctx->bo_e.p, (long long)(uintptr_t)ctx->kb_route.p,
+    const long long extra[] = {G, sch.unroll, sch.grid_mult, sch.deg_vec, sch.front, (long long)(uintptr_t)eo_u,
+                               (long long)(uintptr_t)vo_u, (long long)(uintptr_t)ctx->bo_e.p, (long long)(uintptr_t)ctx->kb_route.p,
                                (long long)(uintptr_t)ctx->tile_pairs.p, (long long)(uintptr_t)ctx->kb_cub.p};
     key.insert(key.end(), reinterpret_cast<const unsigned char *>(extra),
                reinterpret_cast<const unsigned char *>(extra) + sizeof(extra));
@@ -2502,7 +2549,7 @@ cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int6
     CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)(n > 0 ? n : 1) * 4, s));
     CC_TRY(ensure_tiles(ctx, edge_offsets_dev, vertex_offsets_dev, G, m, n, s));
     launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, as<uint32_t>(ctx->deg),
-                        st, ctx->grid, tile_queue(ctx), s);
+                        st, ctx->grid, tile_queue(ctx), BatchSchedule().deg_vec, s);
     std::vector<int> route;
     CC_TRY(enqueue_ks_batch(ctx, vertex_offsets_dev, vertex_offsets_host, G, s));
     CC_TRY(batch_routes(ctx, vertex_offsets_host, G, route, s));
@@ -2549,9 +2596,11 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
     const uint32_t *vtiles = as<uint32_t>(ctx->tile_verts);
     BatchSchedule sch;
     CC_TRY(tune_batch(ctx, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, s, &sch));
-    S.sv_sample_stride = 1;  // the batched form has no SV front end
+    sch.front = batch_front(ctx, m);
+    S.sv_sample_stride = sch.front ? -1 : 1;
     S.batch_unroll = sch.unroll;
     S.batch_grid_mult = sch.grid_mult;
+    S.batch_deg_vec = sch.deg_vec;
     {
         Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
         launch_parent_init(parent, nt, nullptr, 0, ctx->grid, s);
@@ -2572,7 +2621,7 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
             {
                 Scope sc(ctx, CC_K_DEGREE, s, 1);
                 launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G,
-                                    as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), s);
+                                    as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), sch.deg_vec, s);
             }
             // the fits on a highest-priority stream, overlapping the first hook
             // pass, which launches one block per tile so that the fits' blocks
@@ -2584,8 +2633,8 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
             CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
             {
                 Scope sc(ctx, CC_K_SV_FIRST, s, 1);
-                launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt,
-                                     parent, hooked, nullptr, st, 0, ctx->grid, s, sch);
+                enqueue_batch_first_hooks(ctx, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G,
+                                          nt, sch, s);
             }
             CU_TRY(cudaStreamWaitEvent(s, ctx->ev_fit, 0));
         }
@@ -2623,8 +2672,8 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
         uint2 *eb0 = as<uint2>(ctx->ebuf0);
         auto pre = [&](cudaStream_t cs) {
             if (!predict)
-                launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt,
-                                     parent, hooked, nullptr, st, 0, ctx->grid, cs, sch);
+                enqueue_batch_first_hooks(ctx, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G,
+                                          nt, sch, cs);
             launch_shortcut_all(parent, nt, st, 0, ctx->grid, cs);
             launch_sv_pass_batch(2, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,
                                  hooked, eb0, st, 1, ctx->grid, cs, sch);
@@ -2634,7 +2683,8 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
             launch_finalize_batch(parent, nt, vertex_offsets_dev, G, (int32_t *)labels_out_dev, ctx->grid, cs, vtiles);
         };
         const cc_ctx::GraphKey key =
-            graph_key(ctx, 2 | (predict ? 4 : 0) | (sch.unroll << 8) | (sch.grid_mult << 12), n, m, G, edges_dev,
+            graph_key(ctx, 2 | (predict ? 4 : 0) | (sch.front ? 8 : 0) | (sch.unroll << 8) | (sch.grid_mult << 12), n,
+                      m, G, edges_dev,
                       edge_offsets_dev, vertex_offsets_dev, labels_out_dev, cap);
         cc_status gs = launch_sv_graph(ctx, ctx->g_batch, key, nt, 1, 0, cap, pre, post, s);
         if (gs == CC_OK) {
@@ -2653,8 +2703,8 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
     if (m > 0) {
         if (!predict) {
             Scope sc(ctx, CC_K_SV_FIRST, s, 1);
-            launch_sv_pass_batch(0, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, parent,
-                                 hooked, nullptr, st, 0, ctx->grid, s, sch);
+            enqueue_batch_first_hooks(ctx, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt,
+                                      sch, s);
         }
         {
             Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);

@@ -13,6 +13,8 @@ namespace ccg {
 struct BatchSchedule {
     int unroll = 2;
     int grid_mult = 1;
+    int deg_vec = 4;  // vectors per thread and tile of the degree pass
+    bool front = false;  // SV front end: per-graph sampled hook passes before the first gather pass
     const uint32_t *pair_tiles = nullptr;  // graph of every 2^kTileShift-th pair (launch_tile_graphs), required
 };
 
@@ -170,6 +172,10 @@ template <typename T>
 void launch_sv_gather_tiles(const void *in, long long m, vid_t n, vid_t *parent, vid_t *hooked_list, uint2 *out,
                             DevState *st, int it, cudaStream_t s);
 void launch_shortcut_all(vid_t *parent, vid_t n, DevState *st, int it, int grid, cudaStream_t s);
+// mode 0: first hook pass (identity parents); 2: gather pass with the next
+// list and the hooked roots; 5 / 6: the SV front end's first (mode 0 over
+// every tile of the graphs that are not sampled and the sampled tiles of the
+// others) and second (one-hop gathers over the sampled tiles) hook passes
 void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
                           vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
                           cudaStream_t s, BatchSchedule sch = BatchSchedule());
@@ -236,9 +242,10 @@ struct KsBatchOut {  // per graph
     unsigned long long *seedkey;  // (degree << 32) | (0xffffffff - local id) of the max-degree vertex
 };
 size_t ks_batch_entries();
-// next: a device counter the blocks take tiles from in order (zeroed here), or null (grid stride)
+// next: a device counter the blocks take tiles from in order (zeroed here);
+// vec: 128-bit vectors a thread loads per tile (2, 4 or 8)
 void launch_degree_batch(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G, uint32_t *deg,
-                         DevState *st, int grid, unsigned long long *next, cudaStream_t s);
+                         DevState *st, int grid, unsigned long long *next, int vec, cudaStream_t s);
 // out[k] = the graph holding item k << kTileShift of the offsets `off` (G + 1 entries), k < (count >> kTileShift) + 1
 void launch_tile_graphs(const int64_t *off, int G, long long count, uint32_t *out, int grid, cudaStream_t s);
 // order (device, G graph numbers, largest first) and next (device counter) may

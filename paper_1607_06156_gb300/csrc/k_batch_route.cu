@@ -28,75 +28,107 @@ constexpr int kZTab = 128;         // zeta table entries per warp (the refinemen
 constexpr int kSmallHistKeyAt = 2 * kBB + 2;  // word of the argmax key in k_small_hist's output (8-byte aligned)
 
 // ---------------------------------------------------------------------------
-// With `next` (a zeroed counter) blocks take tiles in increasing order from
-// it instead of striding by the grid: the tiles in flight then stay within a
-// window of about one tile per block, so the few graphs they belong to keep
+// Blocks take tiles of kBlock * V vectors (two pairs each) in increasing
+// order from `next` (a zeroed counter), so the tiles in flight stay within a
+// window of about one tile per block and the few graphs they belong to keep
 // their counters in L2 (with a fixed stride, blocks drift apart and the
-// counters of many graphs compete for it).
-__global__ void __launch_bounds__(kBlock) k_degree_batch(const int32_t *__restrict__ in, long long m,
-                                                         const int64_t *__restrict__ eo,
-                                                         const int64_t *__restrict__ vo, int G, uint32_t *deg,
-                                                         DevState *st, unsigned long long *next) {
-    constexpr int U = 2, K = 2 * U;
-    __shared__ int sg;
-    __shared__ long long s_t;
-    const long long nvec = m / 2;
+// counters of many graphs compete for it). Thread 0 fetches the next tile's
+// number and first and last graph while the block's loads of the current
+// tile are in flight (two slots in shared memory, one barrier per tile). A
+// tile inside one graph - nearly every tile, since the graphs hold thousands
+// to millions of pairs - reads that graph's base and size once; a tile
+// across graphs finds each pair's graph by stepping from its first graph.
+// Resident blocks per SM are set so that no variant spills (40, 62 and 102
+// registers for V = 2, 4, 8).
+template <int V>
+__global__ void __launch_bounds__(kBlock, V >= 8 ? 2 : V >= 4 ? 4 : 6) k_degree_batch(const int32_t *__restrict__ in, long long m,
+                                                                        const int64_t *__restrict__ eo,
+                                                                        const int64_t *__restrict__ vo, int G,
+                                                                        uint32_t *deg, DevState *st,
+                                                                        unsigned long long *next) {
+    __shared__ long long s_t[2];
+    __shared__ int s_g0[2], s_g1[2];
+    constexpr long long kTile = (long long)kBlock * V;
+    const long long nvec = m >> 1;
+    const long long ntiles = (nvec + kTile - 1) / kTile;
     const int4 *ev = reinterpret_cast<const int4 *>(in);
-    bool bad = false;
-    const long long tile = (long long)kBlock * U;
-    const long long ntiles = (nvec + tile - 1) / tile;
-    const long long nt = ntiles + ((m & 1) ? 1 : 0);
-    for (long long t = blockIdx.x;; t += gridDim.x) {
-        if (next) {
-            if (threadIdx.x == 0) s_t = (long long)atomicAdd(next, 1ull);
-            __syncthreads();
-            t = s_t;
-        }
-        if (t >= nt) break;
-        const long long k0 = t < ntiles ? t * tile * 2 : m - 1;
-        // the tile's graph by a binary search of the offsets (held in L1); on
-        // 4,096 graphs this measured 58 ms for the degree and fit passes
-        // against 80 ms with the precomputed tile index and a per-thread cursor
-        if (threadIdx.x == 0) sg = graph_search(eo, G, k0);
-        __syncthreads();
-        const int g0 = sg;
-        long long u[K], v[K], k[K];
-        bool valid[K];
+    auto fetch = [&](int b) {  // thread 0
+        const long long t = (long long)atomicAdd(next, 1ull);
+        s_t[b] = t;
         if (t < ntiles) {
+            const long long last = ((t + 1) * kTile < nvec ? (t + 1) * kTile : nvec) * 2 - 1;
+            const int g0 = graph_search(eo, G, t * kTile * 2);
+            s_g0[b] = g0;
+            s_g1[b] = graph_search(eo, G, last);
+        }
+    };
+    if (threadIdx.x == 0) fetch(0);
+    __syncthreads();
+    bool bad = false;
+    for (int b = 0;; b ^= 1) {
+        const long long t = s_t[b];
+        if (t >= ntiles) break;
+        const int g0 = s_g0[b], g1 = s_g1[b];
+        int4 q[V];
 #pragma unroll
-            for (int r = 0; r < U; r++) {
-                const long long i = t * tile + (long long)r * kBlock + threadIdx.x;
-                const int4 q = i < nvec ? ld_stream(ev + i) : make_int4(0, 0, 0, 0);
-                u[2 * r] = q.x; v[2 * r] = q.y; k[2 * r] = 2 * i;
-                u[2 * r + 1] = q.z; v[2 * r + 1] = q.w; k[2 * r + 1] = 2 * i + 1;
-                valid[2 * r] = valid[2 * r + 1] = i < nvec;
+        for (int r = 0; r < V; r++) {
+            const long long i = t * kTile + (long long)r * kBlock + threadIdx.x;
+            q[r] = i < nvec ? ld_stream(ev + i) : make_int4(0, 0, 0, 0);
+        }
+        if (threadIdx.x == 0) fetch(b ^ 1);
+        if (g0 == g1) {
+            const long long base = vo[g0];
+            const unsigned long long ng = (unsigned long long)(vo[g0 + 1] - base);
+#pragma unroll
+            for (int r = 0; r < V; r++) {
+                const long long i = t * kTile + (long long)r * kBlock + threadIdx.x;
+                if (i >= nvec) break;
+                const int4 x = q[r];
+                const bool ok0 = (unsigned long long)(long long)x.x < ng && (unsigned long long)(long long)x.y < ng;
+                const bool ok1 = (unsigned long long)(long long)x.z < ng && (unsigned long long)(long long)x.w < ng;
+                if (ok0) {
+                    atomicAdd(&deg[base + x.x], 1u);
+                    atomicAdd(&deg[base + x.y], 1u);
+                }
+                if (ok1) {
+                    atomicAdd(&deg[base + x.z], 1u);
+                    atomicAdd(&deg[base + x.w], 1u);
+                }
+                bad |= !(ok0 && ok1);
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < K; r++) {
-                u[r] = v[r] = 0;
-                k[r] = m - 1;
-                valid[r] = false;
-            }
-            if (threadIdx.x == 0) {
-                u[0] = in[2 * (m - 1)];
-                v[0] = in[2 * (m - 1) + 1];
-                valid[0] = true;
-            }
-        }
+            for (int r = 0; r < V; r++) {
+                const long long i = t * kTile + (long long)r * kBlock + threadIdx.x;
+                if (i >= nvec) break;
+                const int4 x = q[r];
 #pragma unroll
-        for (int r = 0; r < K; r++) {
-            if (!valid[r]) continue;
-            const int g = graph_advance(eo, G, k[r], g0);
-            const long long base = vo[g], ng = vo[g + 1] - base;
-            if (u[r] < 0 || v[r] < 0 || u[r] >= ng || v[r] >= ng) {
-                bad = true;
-                continue;
+                for (int h = 0; h < 2; h++) {
+                    const long long u = h ? x.z : x.x, v = h ? x.w : x.y;
+                    const int g = graph_advance(eo, G, 2 * i + h, g0);
+                    const long long base = vo[g];
+                    const unsigned long long ng = (unsigned long long)(vo[g + 1] - base);
+                    if ((unsigned long long)u >= ng || (unsigned long long)v >= ng) {
+                        bad = true;
+                        continue;
+                    }
+                    atomicAdd(&deg[base + u], 1u);
+                    atomicAdd(&deg[base + v], 1u);
+                }
             }
-            atomicAdd(&deg[base + u[r]], 1u);
-            atomicAdd(&deg[base + v[r]], 1u);
         }
-        __syncthreads();  // sg is rewritten by the next tile
+        __syncthreads();  // the slot read above is rewritten by the fetch after next
+    }
+    if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) {  // the odd last pair
+        const long long u = in[2 * (m - 1)], v = in[2 * (m - 1) + 1];
+        const int g = graph_search(eo, G, m - 1);
+        const long long base = vo[g];
+        const unsigned long long ng = (unsigned long long)(vo[g + 1] - base);
+        if ((unsigned long long)u >= ng || (unsigned long long)v >= ng) bad = true;
+        else {
+            atomicAdd(&deg[base + u], 1u);
+            atomicAdd(&deg[base + v], 1u);
+        }
     }
     if (bad) set_err(st, kErrInvalidEdge);
 }
@@ -504,11 +536,11 @@ void launch_fit_one(const uint32_t *deg, long long n, int64_t *vo, KsBatchScratc
 
 // ---------------------------------------------------------------------------
 void launch_degree_batch(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G, uint32_t *deg,
-                         DevState *st, int grid, unsigned long long *next, cudaStream_t s) {
+                         DevState *st, int grid, unsigned long long *next, int vec, cudaStream_t s) {
     if (m <= 0) return;
-    if (next) cudaMemsetAsync(next, 0, sizeof(unsigned long long), s);
-    k_degree_batch<<<fit_grid((const void *)k_degree_batch, grid, kBlock), kBlock, 0, s>>>(in, m, eo, vo, G, deg, st,
-                                                                                         next);
+    cudaMemsetAsync(next, 0, sizeof(unsigned long long), s);
+    auto kf = vec >= 8 ? k_degree_batch<8> : vec >= 4 ? k_degree_batch<4> : k_degree_batch<2>;
+    kf<<<fit_grid((const void *)kf, grid, kBlock), kBlock, 0, s>>>(in, m, eo, vo, G, deg, st, next);
 }
 
 __global__ void __launch_bounds__(kBlock) k_tile_graphs(const int64_t *__restrict__ off, int G, long long ntiles,

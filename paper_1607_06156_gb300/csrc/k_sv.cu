@@ -349,9 +349,34 @@ __global__ void __launch_bounds__(kBlock) k_finalize(vid_t *parent, vid_t n, T *
 // and a component's minimum union id is vo[g] plus its minimum local id.
 
 
+// The SV front end per graph: a graph with 2 m_g / n_g >= 4 has its tiles
+// sampled one in k_g, k_g the largest power of two <= 2 m_g / n_g and at
+// most 64 (the single-graph rule: the sample's mean degree is about 1 or
+// more, so it holds a giant component); other graphs are not sampled (0).
+__device__ __forceinline__ int batch_sample_stride(long long mg, long long ng) {
+    if (ng <= 0 || 2 * mg < 4 * ng) return 0;
+    int k = 4;
+    while (k < 64 && 2 * mg >= 2LL * k * ng) k *= 2;
+    return k;
+}
+
+// Which tiles a pass takes (FILTER), by the sample stride k of the graph
+// holding the tile's first pair: 0 every tile; 1 the front end's first
+// pass: every tile of a graph that is not sampled and one tile in k of a
+// sampled graph; 2 the front end's second pass: the sampled tiles only.
+template <int FILTER>
+__device__ __forceinline__ bool batch_take_tile(long long t, long long k0, const int64_t *eo, const int64_t *vo,
+                                                int G, int g0) {
+    if (FILTER == 0) return true;
+    const int g = graph_advance(eo, G, k0, g0);
+    const int k = batch_sample_stride(eo[g + 1] - eo[g], vo[g + 1] - vo[g]);
+    if (k == 0) return FILTER == 1;
+    return (t & (k - 1)) == 0;
+}
+
 // U: 16-byte vectors (two pairs each) per thread per tile, the schedule the
 // batched form's tuner picks.
-template <int MODE, bool WRITE, bool RECORD, int U>
+template <int MODE, bool WRITE, bool RECORD, int U, int FILTER = 0>
 __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restrict__ in, long long m,
                                                           const int64_t *__restrict__ eo,
                                                           const int64_t *__restrict__ vo, int G, vid_t ntot,
@@ -370,6 +395,7 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restr
     for (long long t = blockIdx.x; t < ntiles + ((m & 1) ? 1 : 0); t += gridDim.x) {
         const long long k0 = t < ntiles ? t * tile * 2 : m - 1;  // first pair of the tile
         const int g0 = (int)tg[k0 >> kTileShift];  // a graph at or before the tile's first pair
+        if (!batch_take_tile<FILTER>(t, k0, eo, vo, G, g0)) continue;  // the same for the whole block
         long long u[K], v[K], k[K];
         bool valid[K];
         if (t < ntiles) {
@@ -452,7 +478,10 @@ template <int U>
 void launch_sv_pass_batch_u(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
                             vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
                             cudaStream_t s, int grid_mult, const uint32_t *sch_tg) {
-    auto kf = mode == 0 ? k_sv_pass_batch<0, false, false, U> : k_sv_pass_batch<2, true, true, U>;
+    auto kf = mode == 0   ? k_sv_pass_batch<0, false, false, U>
+              : mode == 5 ? k_sv_pass_batch<0, false, false, U, 1>   // front end, first pass
+              : mode == 6 ? k_sv_pass_batch<2, false, false, U, 2>   // front end, second pass
+                          : k_sv_pass_batch<2, true, true, U>;
     const long long g = fit_grid((const void *)kf, grid, kBlock) * (grid_mult > 0 ? grid_mult : 1);
     kf<<<(unsigned)g, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, sch_tg);
 }

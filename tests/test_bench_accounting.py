@@ -116,3 +116,34 @@ def test_traffic_summary_of_one_kernel_class(tmp_path):
         bench.ncu_summary(str(p), "rmat22", {}, "cmd")
     out = bench.ncu_summary(str(p), "rmat22", {}, "cmd", calls=3)
     assert out["traffic_per_call"]["rmat22"]["degree"] == pytest.approx(930.0)
+
+
+def test_class_capture_is_tied_to_that_class_sources(tmp_path, monkeypatch):
+    """A one-class summary holds the hash of that class's sources only: it
+    stays valid when another class's kernel file changes, is void when its
+    own files change, and serves no other class."""
+    rows = [["ID", "Kernel Name", "Metric Name", "Metric Value"]]
+    for i in range(2):
+        rows.append([str(i), "void ccg::k_degree_hubs<int>(x)", "dram__bytes_read.sum", "900"])
+        rows.append([str(i), "void ccg::k_degree_hubs<int>(x)", "dram__bytes_write.sum", "100"])
+        rows.append([str(10 + i), "ccg::k_hist(x)", "dram__bytes_read.sum", "5"])
+    p = tmp_path / "cap.csv"
+    with open(p, "w", newline="") as f:
+        csv.writer(f, quoting=csv.QUOTE_ALL).writerows(rows)
+    out = bench.ncu_summary(str(p), "rmat22", {}, "cmd", calls=2, kernel_cls="degree")
+    assert out["kernel_class"] == "degree" and set(out["traffic_per_call"]["rmat22"]) == {"degree"}
+    assert out["sources_hash"] == bench.sources_hash("degree") != bench.sources_hash()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "ncu_traffic.json").write_text(json.dumps(out))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    src = tmp_path / "paper_1607_06156_gb300" / "csrc"
+    src.mkdir(parents=True)
+    for f in set(bench.KERNEL_FILES) | set(bench.CLASS_FILES["degree"]):
+        (src / f).write_bytes(open(os.path.join(ROOT, "paper_1607_06156_gb300", "csrc", f), "rb").read())
+    assert bench.ncu_traffic("degree", "rmat22") == pytest.approx(1000.0)
+    assert bench.ncu_traffic("hist", "rmat22") is None
+    (src / "k_sv.cu").write_text("// another class changed")
+    assert bench.ncu_traffic("degree", "rmat22") == pytest.approx(1000.0)
+    (src / "k_degree.cu").write_text("// the class's own kernel changed")
+    assert bench.ncu_traffic("degree", "rmat22") is None

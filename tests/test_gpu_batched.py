@@ -43,6 +43,26 @@ def test_mixed_batch_matches_oracle_per_graph():
     assert st["sv_iters"] >= 2
 
 
+@pytest.mark.parametrize("stride,route,profile", [(8, "auto", 0), (0, "auto", 0), (8, "sv", 0), (8, "auto", 1),
+                                                   (8, "sv", 1)])
+def test_front_end_per_graph(stride, route, profile):
+    """The SV front end of the batched form (requested by a stride > 1): each
+    graph with 2 m_g / n_g >= 4 (the R-MAT graphs here) is sampled at its own
+    stride, the sparse ones (grids, chains) are hooked in full, and tiles
+    cross graph boundaries. Labels equal the oracle's with the front end on
+    and off (the default), on the captured and the profiled paths; with it
+    on, the first gather pass leaves fewer pairs crossing trees."""
+    torch = torch_cuda()
+    b = gg.batch(seed=5, G=60, nmin=500, nmax=120000)
+    got, st = _run_batched(torch, b.edges, b.edge_offsets, b.vertex_offsets, sv_sample_stride=stride, route=route,
+                           profile=profile)
+    _check_each(b, got)
+    assert st["sv_sample_stride"] == (-1 if stride > 1 else 1)
+    if stride > 1 and route == "auto" and not profile:
+        _, off = _run_batched(torch, b.edges, b.edge_offsets, b.vertex_offsets)
+        assert st["m_active"][2] < off["m_active"][2] // 2, (st["m_active"], off["m_active"])
+
+
 def test_batched_equals_per_graph_loop():
     torch = torch_cuda()
     import paper_1607_06156_gb300 as cc
