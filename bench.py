@@ -50,6 +50,8 @@ WORKLOADS = {
     "grid_chains": dict(kind="grid_chains", seed=1, W=8192, nchains=10_000_000),
     "grid_chains_67m": dict(kind="grid_chains", seed=1, W=4096, nchains=2_500_000),
     "chung_lu24": dict(kind="chung_lu", seed=1, n=1 << 24, avg_degree=16.0),
+    # many mid-size power-law components: 200 Chung-Lu graphs, n log-uniform in [2^14, 2^18]
+    "chung_lu_union": dict(kind="union", seed=1, parts=200, nmin=1 << 14, nmax=1 << 18, avg_degree=16.0),
     "batch4096": dict(kind="batch", seed=1, G=4096, nmin=1000, nmax=1_000_000),
     "batch512": dict(kind="batch", seed=1, G=512, nmin=1000, nmax=1_000_000),
 }
@@ -75,6 +77,15 @@ def make_graph(name: str):
         return gg.planted(**w)
     if kind == "chung_lu":
         return gg.chung_lu(**w)
+    if kind == "union":
+        rng = np.random.default_rng(w["seed"])
+        sizes = np.exp(rng.uniform(np.log(w["nmin"]), np.log(w["nmax"]), size=w["parts"])).astype(np.int64)
+        parts = [gg.chung_lu(seed=w["seed"] * 1000 + i, n=int(s), avg_degree=w["avg_degree"])
+                 for i, s in enumerate(sizes)]
+        g = gg.union(parts, seed=w["seed"])
+        g.name = f"union of {w['parts']} Chung-Lu graphs (n log-uniform in [{w['nmin']}, {w['nmax']}], " \
+                 f"avg degree {w['avg_degree']:g}, seed {w['seed']})"
+        return g
     return gg.grid_chains(**w)
 
 
@@ -628,6 +639,70 @@ def batch_record(args, dev, stream, world: int = 1, rank: int = 0, dist=None, wo
             "m_active": st["m_active"], "labels_vs_oracle": same, "graphs_checked": checked, "cpu_baseline": cpu}
 
 
+def multi_start_record(args, dev, stream, name: str = "chung_lu_union", starts=(64, 1024)) -> dict:
+    """The multi-start BFS step (several traversals at once) on many mid-size
+    power-law components, against one BFS tree (Algorithm 2) and against SV
+    only: device time of each through cc_labels, what the trees reached, and
+    every route's labels against the oracle."""
+    import torch
+
+    import oracle
+    import paper_1607_06156_gb300 as cc
+    from oracle import multi_bfs
+
+    g = make_graph(name)
+    w, n, m = g.id_bytes, g.n, g.m
+    edges_d = torch.from_numpy(g.edges).to(dev)
+    lab = torch.empty(n, dtype=edges_d.dtype, device=dev)
+    want = oracle.labels_uf(g.edges, n)
+    runs = {"one_tree": {}, "sv_only": {"route": "sv"}}
+    for k in starts:
+        runs[f"starts_{k}"] = {"bfs_starts": k}
+    out = {"config": {"workload": name, "n": int(n), "m": int(m), "id_bytes": int(w), "graph": g.name,
+                      "l2": "inputs larger than L2 (no flush)" if m * 2 * w > 129e6 else "L2-resident inputs"}}
+    same_all = True
+    for key, opts in runs.items():
+        eng = cc.Engine(id_bytes=w, device=dev.index, profile=0, **opts)
+        call = lambda: eng.labels(edges_d, n, out=lab)
+        for _ in range(max(args.warmup, 1)):
+            call()
+        torch.cuda.synchronize()
+        ms, launches = timed_calls(torch, eng, call, args.steps, stream)
+        st = eng.stats()
+        same = bool(np.array_equal(lab.cpu().numpy().astype(np.int64), want))
+        same_all &= same
+        rec = {"ms_per_step": ms / args.steps, "value": m / (ms / args.steps / 1e3), "unit": UNIT,
+               "route_taken": "bfs+sv" if st["route"] else "sv", "sv_iters": st["sv_iters"],
+               "gpu_launches": launches, "labels_vs_oracle": same}
+        if st["route"]:
+            rec |= {"bfs_starts": st["bfs_starts"], "bfs_levels": st["bfs_levels"], "bfs_visited": st["bfs_visited"],
+                    "pairs_left_for_sv": st["m_active"][0]}
+            k = opts.get("bfs_starts", 1)
+            if k > 1:
+                s0, reached = multi_bfs.multi_bfs_reached(g.edges, n, k)
+                rec["visited_vs_oracle"] = bool(st["bfs_visited"] == int(reached.sum()) and
+                                                st["bfs_starts"] == len(s0))
+                kms, kla, pst, _ = profiled_calls(torch, eng, call, max(1, min(args.steps, 3)), stream)
+                rec["kernels"] = kernel_table(kms, kla, pst, w, max(1, min(args.steps, 3)))
+                bfs_ms = kms.get("bfs_bottomup", 0.0) / max(1, min(args.steps, 3))
+                if bfs_ms > 0:
+                    # each level streams the active pairs (both 4-byte ends of each)
+                    gbs = 4.0 * pst["bfs_edges_inspected"] / (bfs_ms / 1e3) / 1e9
+                    pk = peaks().get("hbm_gbs") or 6800.0
+                    rec["bfs_levels_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": pk, "unit": "GB/s",
+                                                  "frac": gbs / pk, "bytes": 4.0 * pst["bfs_edges_inspected"]}
+        out[key] = rec
+        eng.close()
+    best = min((v["ms_per_step"], k) for k, v in out.items() if k != "config")
+    out["fastest"] = best[1]
+    out["labels_vs_oracle"] = same_all
+    del edges_d, lab
+    torch.cuda.empty_cache()
+    if not same_all:
+        raise SystemExit(f"{name}: labels differ from the oracle")
+    return out
+
+
 def learned_record(args, dev, stream, graphs: int) -> dict | None:
     """The learned route against the K-S heuristic on a bounded held-out mix
     (the predictor's five families from a seed not used in training, plus
@@ -956,6 +1031,7 @@ def main() -> int:
                    # a power-law graph the K-S heuristic sends to BFS first: the CSR build and BFS kernels
                    "chung_lu": single_record("chung_lu24", args, dev, stream, budget),
                    "batch4096": batch_record(args, dev, stream),
+                   "multi_start": multi_start_record(args, dev, stream),
                    "learned_route": learned_record(args, dev, stream, args.heldout)}
 
     if rank == 0:

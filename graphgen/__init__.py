@@ -216,5 +216,25 @@ def batch(seed: int = 1, G: int = 4096, nmin: int = 1000, nmax: int = 1_000_000,
     return Batch(edges, eoff, voff, f"batch(G={G},n=[{nmin},{nmax}],seed={seed}{sub})")
 
 
+def union(parts: list, seed: int = 1, id_bytes: int = 4) -> Graph:
+    """Disjoint union of graphs: graph i's ids are shifted past those of
+    graphs 0..i-1, then every id goes through one seeded random permutation
+    of [0, n) and the pairs are put in a seeded random order, so that no
+    component sits in a contiguous id range or a contiguous run of pairs.
+    ``meta['comp_of_part']`` gives, per vertex, the part it came from."""
+    rng = np.random.default_rng(seed)
+    sizes = [int(g.n) for g in parts]
+    base = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(base[-1])
+    e = np.concatenate([g.edges.astype(np.int64) + base[i] for i, g in enumerate(parts)]) if parts else \
+        np.zeros((0, 2), np.int64)
+    perm = rng.permutation(n).astype(np.int64)
+    e = perm[e][rng.permutation(e.shape[0])]
+    part = np.empty(n, dtype=np.int32)
+    part[perm] = np.repeat(np.arange(len(parts), dtype=np.int32), sizes)
+    return Graph(np.ascontiguousarray(e.astype(_dtype(id_bytes))), n,
+                 f"union({len(parts)} parts,seed={seed})", {"comp_of_part": part})
+
+
 def num_threads() -> int:
     return int(_load().gg_num_threads())

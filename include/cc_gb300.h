@@ -100,7 +100,14 @@ typedef struct {
                                the batched form, when this is > 1, samples each graph by that rule on
                                its own m_g and n_g (off by default);
                                the labels are the same either way */
-    int reserved[1];
+    int bfs_starts;         /* BFS starts: 0 or 1 = one tree from the max-degree vertex (Algorithm 2);
+                               k in 2..4096 = the multi-start BFS: [0, n) is cut into k ranges
+                               [j n / k, (j + 1) n / k) and each range's max-degree vertex (ties to
+                               the smallest id) starts a tree unless its degree is 0; the trees grow
+                               together on the edge-list engine, pairs inside one tree leave the
+                               active list and each tree's vertices take its smallest vertex as
+                               parent before SV. Used by the K-S heuristic and forced routes (the
+                               learned route keeps one sampled start); the labels are the same */
 } cc_options;
 
 /* Kernel classes reported in cc_stats.kernel_ms / kernel_launches. */
@@ -161,6 +168,8 @@ typedef struct {
                                            front end; 0 = no first pass over the input pairs in this call;
                                            -1 = batched form, each graph with its own stride) */
     int32_t batch_deg_vec;              /* batched form: tuned 16-byte vectors per thread per tile of the degree pass */
+    int32_t bfs_starts;                 /* BFS trees started (0 if the BFS did not run) */
+    int32_t pad3;
 } cc_stats;
 
 /* Fills *opt with the defaults listed above. */

@@ -51,6 +51,7 @@ struct cc_ctx {
     Buf deg, parent, hooked, ebuf0, ebuf1, hist, ovf, ks_xs, ks_cnt, ks_cum, ks_lnx, ks_Dc, ks_Ac, ks_Zc, ks_Df, chunk_nz,
         chunk_mass, st, bk_count, bk_off, bk_cursor;
     Buf dpart;  // endpoints partitioned into vertex windows (degree pass of graphs with n > 2^25)
+    Buf bfs_own, bfs_tmin;  // multi-start BFS: the tree of every vertex, the minimum of every tree
     unsigned long long ovf_cap = 0, ks_cap = 0;
     // BFS workspace
     size_t bn_cap = 0, bm_cap = 0;
@@ -262,6 +263,20 @@ cc_status ensure_feat(cc_ctx *ctx, size_t n) {
     return CC_OK;
 }
 
+// The multi-start BFS runs on the K-S heuristic and forced routes, which
+// count the exact degrees its starts are chosen from (the learned route
+// keeps its single sampled hub).
+bool multi_start(const cc_ctx *ctx) {
+    return ctx->opt.bfs_starts > 1 && !(ctx->opt.route_policy == CC_ROUTE_LEARNED && ctx->have_pred);
+}
+
+cc_status ensure_mbfs(cc_ctx *ctx, size_t n) {
+    CC_TRY(ensure_feat(ctx, n));
+    CC_TRY(buf_reserve(ctx, ctx->bfs_own, (n + 4) * 4));
+    CC_TRY(buf_reserve(ctx, ctx->bfs_tmin, (size_t)kMaxBfsStarts * 4));
+    return CC_OK;
+}
+
 FeatScratch feat_scratch(cc_ctx *ctx) {
     return FeatScratch{as<uint32_t>(ctx->f_sdeg), as<unsigned>(ctx->f_counts), as<uint32_t>(ctx->f_vis),
                        as<uint32_t>(ctx->f_f0), as<uint32_t>(ctx->f_f1)};
@@ -277,6 +292,7 @@ cc_status check_options(const cc_options *o) {
     if (o->max_iters > kMaxIters - 1) return CC_ERR_INVALID_ARG;
     if (o->bfs_mode < 0 || o->bfs_mode > 1) return CC_ERR_INVALID_ARG;
     if (o->sv_sample_stride < 0 || o->sv_sample_stride > 1024) return CC_ERR_INVALID_ARG;
+    if (o->bfs_starts < 0 || o->bfs_starts > kMaxBfsStarts) return CC_ERR_INVALID_ARG;
     return CC_OK;
 }
 
@@ -771,6 +787,50 @@ cc_status run_bfs_edges(cc_ctx *ctx, const void *edges, vid_t n, long long m, cu
     return CC_OK;
 }
 
+// The multi-start BFS with the host driving the levels (options.profile):
+// the graph route's kernels, each level timed. Leaves the active pairs'
+// buffer and length as run_bfs_edges does, the visited count in the BFS
+// counter, and the parents of the trees' vertices set to the tree minima.
+template <typename T>
+cc_status run_mbfs_edges(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s, int cutoff,
+                         int *levels_out, int *list_buf, unsigned long long *list_len) {
+    DevState *st = as<DevState>(ctx->st);
+    CC_TRY(ensure_mbfs(ctx, n));
+    const long long nwords = ((long long)n + 31) / 32;
+    uint32_t *vis = as<uint32_t>(ctx->f_vis), *b0 = as<uint32_t>(ctx->f_f0), *b1 = as<uint32_t>(ctx->f_f1);
+    uint32_t *own = as<uint32_t>(ctx->bfs_own), *tmin = as<uint32_t>(ctx->bfs_tmin);
+    uint2 *eb0 = as<uint2>(ctx->ebuf0), *eb1 = as<uint2>(ctx->ebuf1);
+    {
+        Scope sc(ctx, CC_K_BFS_AUX, s, 2);
+        launch_mbfs_start(as<uint32_t>(ctx->deg), n, m, ctx->opt.bfs_starts, vis, b0, own, tmin, st, nullptr, s);
+    }
+    int level = 0;
+    while (level < kMaxLevels - 1 && (cutoff <= 0 || level < cutoff)) {
+        {
+            Scope sc(ctx, CC_K_BFS_BOTTOMUP, s, 4);
+            launch_ebfsg_level<T>(edges, m, eb0, eb1, n, vis, b0, b1, st, cudaGraphConditionalHandle(), ctx->grid, s,
+                                  own, false);
+        }
+        CC_TRY(read_back(ctx, &st->front[level + 1], 8, s));
+        level++;
+        if (ctx->h_st->front[level] == 0) break;
+    }
+    CU_TRY(cudaMemcpyAsync(&ctx->h_st->bfs_starts, &st->bfs_starts, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaMemcpyAsync(&ctx->h_st->bfs_len, &st->bfs_len, 8, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaMemcpyAsync(&ctx->h_st->bfs_inspected, &st->bfs_inspected, 8, cudaMemcpyDeviceToHost, s));
+    CC_TRY(read_back(ctx, &st->bfs_list, sizeof(int), s));
+    *levels_out = level;
+    *list_buf = ctx->h_st->bfs_list;
+    *list_len = *list_buf < 0 ? (unsigned long long)m : ctx->h_st->bfs_len;
+    unsigned long long *cnt = counter_at<unsigned long long>(ctx->counters, kCtrBfs);
+    cudaMemsetAsync(cnt + 1, 0, 8, s);
+    Scope sc(ctx, CC_K_BFS_AUX, s, 4);
+    launch_popcount(vis, nwords, cnt + 1, ctx->grid, s);
+    launch_first_visited(vis, nwords, st, ctx->grid, s);
+    launch_mbfs_finish(own, tmin, n, as<vid_t>(ctx->parent), ctx->grid, s);
+    return CC_OK;
+}
+
 cc_status ensure_side(cc_ctx *ctx) {
     // lowest priority: the prediction on the caller's stream (the K-S fit, a
     // few small grids) gets the SMs first and the speculative pass fills the rest
@@ -1079,7 +1139,8 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
     spec.join();  // later work on `s` sees the speculative pass complete
     // the learned route always takes the edge-list BFS (it needs no exact
     // degrees); the CSR uses 32-bit offsets, so the CSR BFS needs 2m < 2^32
-    const bool edge_bfs = learned || ctx->opt.bfs_mode == 1;
+    const bool multi = multi_start(ctx);
+    const bool edge_bfs = learned || multi || ctx->opt.bfs_mode == 1;
     if (route == 1 && !edge_bfs && 2ull * (unsigned long long)m >= 0xffffffffull) route = 0;
     S.route = route;
     uint2 *eb[2] = {as<uint2>(ctx->ebuf0), as<uint2>(ctx->ebuf1)};
@@ -1095,7 +1156,10 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         int levels = 0, list_buf = -1;
         unsigned long long list_len = (unsigned long long)m;
         const uint32_t *vis = nullptr;
-        if (edge_bfs) {
+        if (multi) {
+            CC_TRY(run_mbfs_edges<T>(ctx, edges, n, m, s, cutoff, &levels, &list_buf, &list_len));
+            vis = as<uint32_t>(ctx->f_vis);
+        } else if (edge_bfs) {
             // seed: the exact max-degree vertex when the degree pass ran, else the sampled hub
             const unsigned long long *key = learned ? &st->pred_seedkey : &st->maxkey;
             CC_TRY(run_bfs_edges<T>(ctx, edges, n, m, s, cutoff, key, &levels, &list_buf, &list_len));
@@ -1115,20 +1179,24 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         S.bfs_levels = levels;
         S.bfs_visited = (int64_t)visited;
         S.comp_min = cmin;
-        {
+        S.bfs_starts = multi ? ctx->h_st->bfs_starts : 1;
+        if (multi) S.bfs_edges_inspected = (int64_t)ctx->h_st->bfs_inspected;
+        if (!multi) {  // the multi-start BFS set the trees' parents itself
             Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
             launch_parent_init(parent, n, vis, cmin, ctx->grid, s);
         }
-        // first SV pass over the pairs the BFS left active (Algorithm 2 lines 8-9)
+        // first SV pass over the pairs the BFS left active (Algorithm 2 lines 8-9): MODE 1
+        // after one tree, MODE 2 (one-hop gathers) after several
+        const int mode = multi ? 2 : 1;
         cur0 = list_buf == 0 ? 1 : 0;
         {
             Scope sc(ctx, CC_K_SV_FIRST, s, 1);
             if (list_buf < 0)
-                launch_sv_pass<T>(1, true, true, edges, m, n, parent, vis, cmin, hooked, eb[cur0], st, 0, ctx->grid,
-                                  s);
+                launch_sv_pass<T>(mode, true, true, edges, m, n, parent, vis, cmin, hooked, eb[cur0], st, 0,
+                                  ctx->grid, s);
             else
-                launch_sv_pass<uint32_t>(1, true, true, eb[list_buf], (long long)list_len, n, parent, vis, cmin, hooked,
-                                         eb[cur0], st, 0, ctx->grid, s);
+                launch_sv_pass<uint32_t>(mode, true, true, eb[list_buf], (long long)list_len, n, parent, vis, cmin,
+                                         hooked, eb[cur0], st, 0, ctx->grid, s);
         }
         {
             Scope sc(ctx, CC_K_SV_SHORTCUT, s, 1);
@@ -1320,7 +1388,7 @@ std::vector<unsigned char> route_key(cc_ctx *ctx, int tbytes, long long n, long 
     struct {
         long long n, m;
         const void *edges, *labels;
-        const void *bufs[24];
+        const void *bufs[26];
         cc_options opt;
         double min_conf;
         int tbytes, cap, grid, have_pred;
@@ -1333,8 +1401,9 @@ std::vector<unsigned char> route_key(cc_ctx *ctx, int tbytes, long long n, long 
     const Buf *b[] = {&ctx->deg,  &ctx->parent,  &ctx->hooked, &ctx->ebuf0,   &ctx->ebuf1, &ctx->hist,
                       &ctx->ovf,  &ctx->st,      &ctx->dpart,  &ctx->row_ptr, &ctx->col,   &ctx->vis,
                       &ctx->fb,   &ctx->nb,      &ctx->q0,     &ctx->q1,      &ctx->dq,    &ctx->off,
-                      &ctx->tsum, &ctx->f_vis,   &ctx->f_f0,   &ctx->f_f1,    &ctx->kb_D,  &ctx->csr_entries};
-    for (int i = 0; i < 24; i++) k.bufs[i] = b[i]->p;
+                      &ctx->tsum, &ctx->f_vis,   &ctx->f_f0,   &ctx->f_f1,    &ctx->kb_D,  &ctx->csr_entries,
+                      &ctx->bfs_own, &ctx->bfs_tmin};
+    for (int i = 0; i < 26; i++) k.bufs[i] = b[i]->p;
     k.opt = ctx->opt;
     k.min_conf = ctx->pred_min_conf;
     k.tbytes = tbytes;
@@ -1354,7 +1423,8 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
     uint2 *eb0 = as<uint2>(ctx->ebuf0), *eb1 = as<uint2>(ctx->ebuf1);
     const int policy = ctx->opt.route_policy;
     const bool learned = policy == CC_ROUTE_LEARNED && ctx->have_pred;
-    const bool edge_bfs = learned || ctx->opt.bfs_mode == 1;
+    const bool multi = multi_start(ctx);
+    const bool edge_bfs = learned || multi || ctx->opt.bfs_mode == 1;
     const bool bfs_ok = policy != CC_ROUTE_FORCE_SV && (edge_bfs || 2ull * (unsigned long long)m < 0xffffffffull);
     const bool predict = policy != CC_ROUTE_FORCE_SV;
     const bool speculate = !(policy == CC_ROUTE_FORCE_BFS && bfs_ok);
@@ -1437,15 +1507,23 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
             // the speculative SV iterations' counters start over
             CU_TRY(cudaMemsetAsync(&st->kept[0], 0, offsetof(DevState, front) - offsetof(DevState, kept), bs));
             const uint32_t *vis;
+            uint32_t *own = multi ? as<uint32_t>(ctx->bfs_own) : nullptr;
             if (edge_bfs) {
                 uint32_t *fv = as<uint32_t>(ctx->f_vis), *f0 = as<uint32_t>(ctx->f_f0), *f1 = as<uint32_t>(ctx->f_f1);
-                CU_TRY(cudaMemsetAsync(fv, 0, (size_t)nwords * 4, bs));
-                CU_TRY(cudaMemsetAsync(f0, 0, (size_t)nwords * 4, bs));
                 cudaGraphConditionalHandle hb;
                 CC_TRY(cond_handle(bs, &hb));
-                launch_ebfsg_init(fv, f0, n, m, st, hb, bs);
+                if (multi) {
+                    launch_mbfs_start(as<uint32_t>(ctx->deg), n, m, ctx->opt.bfs_starts, fv, f0, own,
+                                      as<uint32_t>(ctx->bfs_tmin), st, &hb, bs);
+                    rg.bfs_launches += 2;
+                } else {
+                    CU_TRY(cudaMemsetAsync(fv, 0, (size_t)nwords * 4, bs));
+                    CU_TRY(cudaMemsetAsync(f0, 0, (size_t)nwords * 4, bs));
+                    launch_ebfsg_init(fv, f0, n, m, st, hb, bs);
+                    rg.bfs_launches += 1;
+                }
                 CC_TRY(cond_node(bs, ctx->cap_s3, hb, cudaGraphCondTypeWhile, [&](cudaStream_t ls) -> cc_status {
-                    launch_ebfsg_level<T>(edges, m, eb0, eb1, n, fv, f0, f1, st, hb, ctx->grid, ls);
+                    launch_ebfsg_level<T>(edges, m, eb0, eb1, n, fv, f0, f1, st, hb, ctx->grid, ls, own);
                     return CC_OK;
                 }));
                 vis = fv;
@@ -1460,7 +1538,7 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
                                            as<unsigned long long>(ctx->csr_entries), st, ctx->grid, bs);
                 else
                     launch_csr_scatter<T>(edges, m, n, deg, col, ctx->grid, bs);
-                rg.bfs_launches += 3 + (bucketed ? 4 : 1);
+                rg.bfs_launches += 3 + (bucketed ? 4 : 1) + 1;  // the scan, the CSR, the BFS state
                 uint32_t *vm = as<uint32_t>(ctx->vis);
                 CU_TRY(cudaMemsetAsync(vm, 0, (size_t)nwords * 4, bs));
                 cudaGraphConditionalHandle hb;
@@ -1477,8 +1555,11 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
             }
             launch_popcount(vis, nwords, &st->bfs_visited, ctx->grid, bs);
             launch_first_visited(vis, nwords, st, ctx->grid, bs);
-            launch_parent_init_st(parent, n, vis, st, ctx->grid, bs);
-            rg.bfs_launches += 1 + 3 + launch_sv_after_bfs<T>(edges, m, eb0, eb1, n, parent, vis, hooked, st, ctx->grid, bs);
+            if (multi) launch_mbfs_finish(own, as<uint32_t>(ctx->bfs_tmin), n, parent, ctx->grid, bs);
+            else launch_parent_init_st(parent, n, vis, st, ctx->grid, bs);
+            rg.bfs_launches += 2 + (multi ? 2 : 1) +
+                               launch_sv_after_bfs<T>(edges, m, eb0, eb1, n, parent, vis, hooked, st, ctx->grid, bs,
+                                                      multi);
             launch_sv_shortcut(parent, hooked, st, 0, ctx->grid, bs);
             rg.bfs_launches += 1;
             return CC_OK;
@@ -1502,7 +1583,8 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
 cc_status ensure_route(cc_ctx *ctx, vid_t n, long long m) {
     const int policy = ctx->opt.route_policy;
     const bool learned = policy == CC_ROUTE_LEARNED && ctx->have_pred;
-    if (learned || ctx->opt.bfs_mode == 1) CC_TRY(ensure_feat(ctx, n));
+    if (multi_start(ctx) && policy != CC_ROUTE_FORCE_SV) CC_TRY(ensure_mbfs(ctx, n));
+    else if (learned || ctx->opt.bfs_mode == 1) CC_TRY(ensure_feat(ctx, n));
     else if (policy != CC_ROUTE_FORCE_SV && 2ull * (unsigned long long)m < 0xffffffffull)
         CC_TRY(ensure_bfs(ctx, n, (size_t)m));
     if (!learned && small_fit(n, m, policy) && policy != CC_ROUTE_FORCE_SV) CC_TRY(ensure_batch_route(ctx, 1, 1));
@@ -1539,6 +1621,7 @@ void stats_from_device(cc_ctx *ctx) {
         S.pred_route = -1;
     } else if (h->route_taken) {
         S.bfs_levels = h->bfs_level;
+        S.bfs_starts = h->bfs_starts > 0 ? h->bfs_starts : 1;
         S.bfs_visited = (int64_t)h->bfs_visited;
         S.comp_min = h->cmin;
         S.bfs_edges_inspected = (int64_t)h->bfs_inspected;

@@ -16,6 +16,8 @@ typedef uint32_t vid_t;
 constexpr int kBlock = 256;            // threads per block for the streaming kernels
 constexpr int kMaxIters = 256;         // SV iteration slots recorded on the device
 constexpr int kMaxLevels = 4096;       // BFS level slots recorded on the device
+constexpr uint32_t kNoOwner = 0xffffffffu;  // multi-start BFS: a vertex no tree reached
+constexpr int kMaxBfsStarts = 4096;    // multi-start BFS: most ranges (options.bfs_starts)
 constexpr uint32_t kHistDense = 1u << 20;   // degrees below this get a dense histogram bin
 constexpr uint32_t kHistSmem = 4096;        // bins privatised in shared memory
 
@@ -41,7 +43,7 @@ struct DevState {
     unsigned long long bfs_inspected;       // adjacency entries read by the BFS
     double ks_out[5];                       // D, alpha, xmin, ntail, ncand
     int route;                              // 1 = BFS first
-    int pad;
+    int bfs_starts;                         // multi-start BFS: trees started (ranges with a vertex of degree > 0)
     // learned route predictor
     unsigned long long pred_seedkey;        // (sampled degree << 32) | (0xffffffff - v): probe seed
     unsigned long long pred_probe[3];       // new vertices at probe levels 1..3

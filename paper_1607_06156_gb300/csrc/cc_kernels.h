@@ -105,14 +105,26 @@ int launch_bfsg_level(vid_t n, unsigned long long total_edges, const uint32_t *r
                       unsigned long long *tsum, DevState *st, cudaGraphConditionalHandle h, int grid, cudaStream_t s);
 void launch_ebfsg_init(uint32_t *vis, uint32_t *b0, vid_t n, long long m, DevState *st, cudaGraphConditionalHandle h,
                        cudaStream_t s);
+// own: the multi-start form's owner array (null: one tree); has_h = false
+// runs the level without a WHILE node (the host-driven loop)
 template <typename T>
 int launch_ebfsg_level(const void *caller, long long m, const uint2 *eb0, const uint2 *eb1, vid_t n, uint32_t *vis,
                        uint32_t *b0, uint32_t *b1, DevState *st, cudaGraphConditionalHandle h, int grid,
-                       cudaStream_t s);
+                       cudaStream_t s, uint32_t *own = nullptr, bool has_h = true);
+// Multi-start BFS: the bitmaps, owners (kNoOwner), tree minima and level
+// counters cleared, the starts of k ranges seeded from deg (one block per
+// range) and the BFS state set; h (or null) gets "level 0 runs". Then
+// launch_ebfsg_level with own, and launch_mbfs_finish: the tree minima and
+// parent[v] = the minimum of v's tree (v if no tree reached it).
+void launch_mbfs_start(const uint32_t *deg, vid_t n, long long m, int k, uint32_t *vis, uint32_t *b0, uint32_t *own,
+                       uint32_t *tmin, DevState *st, const cudaGraphConditionalHandle *h, cudaStream_t s);
+void launch_mbfs_finish(const uint32_t *own, uint32_t *tmin, vid_t n, vid_t *parent, int grid, cudaStream_t s);
 void launch_parent_init_st(vid_t *parent, vid_t n, const uint32_t *vis, const DevState *st, int grid, cudaStream_t s);
 template <typename T>
+// trees: after the multi-start BFS (parents already point at the tree minima)
 int launch_sv_after_bfs(const void *caller, long long m, const uint2 *eb0, const uint2 *eb1, vid_t n, vid_t *parent,
-                        const uint32_t *vis, vid_t *hooked_list, DevState *st, int grid, cudaStream_t s);
+                        const uint32_t *vis, vid_t *hooked_list, DevState *st, int grid, cudaStream_t s,
+                        bool trees = false);
 void launch_sv_loop_init_st(DevState *st, int cap, cudaGraphConditionalHandle h, cudaStream_t s);
 // h: the IF node's handle, or null when there is no BFS branch
 void launch_route_decide(DevState *st, const cudaGraphConditionalHandle *h, int policy, int bfs_ok, int opt_cutoff,

@@ -811,10 +811,18 @@ __global__ void __launch_bounds__(kBlock) k_ebfsg_plan(uint32_t *b0, uint32_t *b
     for (long long w = gtid(); w < nwords; w += gstride()) next[w] = 0u;
 }
 
-template <typename T>
+// OWN: the multi-start form. own[v] is the tree (start number) that claimed
+// v, kNoOwner before; a vertex claimed from u takes own[u]. A pair leaves
+// the active list only when its ends are known to be in one tree: the pair
+// that claimed one end from the other, or ends whose owners are both
+// written and equal. Owners are written once, so a value read is final and
+// an end claimed by another pair in this level is at worst read as
+// kNoOwner, which keeps the pair for a later level or for SV (where equal
+// roots drop it).
+template <typename T, bool OWN>
 __global__ void __launch_bounds__(kBlock) k_ebfsg_level(const T *__restrict__ caller, long long m, const uint2 *eb0,
                                                         const uint2 *eb1, vid_t n, uint32_t *vis, uint32_t *b0,
-                                                        uint32_t *b1, DevState *st) {
+                                                        uint32_t *b1, DevState *st, uint32_t *own) {
     constexpr bool kList = sizeof(T) == 4 && T(-1) > T(0);  // uint32_t: the compacted list
     const int list = st->bfs_list;
     if (kList != (list >= 0)) return;
@@ -872,9 +880,29 @@ __global__ void __launch_bounds__(kBlock) k_ebfsg_level(const T *__restrict__ ca
             if (!valid[k] || (unsigned long long)u[k] >= n || (unsigned long long)v[k] >= n) continue;
             const bool fu = bit_test(cur, u[k]), fv = bit_test(cur, v[k]);
             const bool vu0 = fu || bit_test(vis, u[k]), vv0 = fv || bit_test(vis, v[k]);
-            if (fu && !vv0 && claim(vis, next, v[k])) claimed++;
-            if (fv && !vu0 && claim(vis, next, u[k])) claimed++;
-            keep[k] = !((vu0 || fv) && (vv0 || fu));
+            if (OWN) {
+                bool joined = false;
+                if (fu && !vv0 && claim(vis, next, v[k])) {
+                    own[v[k]] = __ldcg(&own[u[k]]);
+                    claimed++;
+                    joined = true;
+                }
+                if (fv && !vu0 && claim(vis, next, u[k])) {
+                    own[u[k]] = __ldcg(&own[v[k]]);
+                    claimed++;
+                    joined = true;
+                }
+                if (joined) keep[k] = false;
+                else if (vu0 && vv0) {
+                    const uint32_t ou = __ldcg(&own[u[k]]), ov = __ldcg(&own[v[k]]);
+                    keep[k] = !(ou != kNoOwner && ou == ov);
+                } else
+                    keep[k] = true;
+            } else {
+                if (fu && !vv0 && claim(vis, next, v[k])) claimed++;
+                if (fv && !vu0 && claim(vis, next, u[k])) claimed++;
+                keep[k] = !((vu0 || fv) && (vv0 || fu));
+            }
         }
         int c = 0;
 #pragma unroll
@@ -898,8 +926,9 @@ __global__ void __launch_bounds__(kBlock) k_ebfsg_level(const T *__restrict__ ca
     }
 }
 
-__global__ void k_ebfsg_step(DevState *st, cudaGraphConditionalHandle h) {
+__global__ void k_ebfsg_step(DevState *st, cudaGraphConditionalHandle h, int has_h) {
     int l = st->bfs_level;
+    st->bfs_inspected += 2ull * st->bfs_len;  // the level read both ends of every active pair
     const unsigned long long claimed = st->front[l + 1], kept = st->front_edges[l + 1];
     if (st->bfs_write) {
         st->bfs_list = st->bfs_list == 0 ? 1 : 0;
@@ -910,7 +939,98 @@ __global__ void k_ebfsg_step(DevState *st, cudaGraphConditionalHandle h) {
     l++;
     st->bfs_level = l;
     const bool go = claimed > 0 && l < kMaxLevels - 1 && (st->bfs_cutoff <= 0 || l < st->bfs_cutoff);
-    cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (has_h) cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Multi-start BFS (the BFS step of Section 3.2 run as several traversals at
+// once): the id range [0, n) is cut into k ranges [j n / k, (j + 1) n / k),
+// and the vertex of largest degree of range j (ties to the smallest id)
+// starts tree j unless that degree is 0. One block per range.
+__global__ void __launch_bounds__(kBlock) k_mbfs_starts(const uint32_t *__restrict__ deg, vid_t n, int k,
+                                                        uint32_t *vis, uint32_t *b0, uint32_t *own, DevState *st) {
+    __shared__ unsigned long long sbest[kBlock / 32];
+    const int j = blockIdx.x;
+    const long long lo = (long long)n * j / k, hi = (long long)n * (j + 1) / k;
+    unsigned long long best = 0;  // (degree << 32) | (0xffffffff - v): the larger key wins
+    for (long long v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        const unsigned long long key = ((unsigned long long)deg[v] << 32) | (0xffffffffull - (unsigned long long)v);
+        best = key > best ? key : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(0xffffffffu, best, o);
+        best = x > best ? x : best;
+    }
+    if ((threadIdx.x & 31) == 0) sbest[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kBlock / 32; w++) best = sbest[w] > best ? sbest[w] : best;
+        if ((best >> 32) > 0) {
+            const vid_t v = (vid_t)(0xffffffffull - (best & 0xffffffffull));
+            atomicOr(&vis[v >> 5], 1u << (v & 31));
+            atomicOr(&b0[v >> 5], 1u << (v & 31));
+            own[v] = (uint32_t)j;
+            atomicAdd(&st->front[0], 1ull);
+            atomicAdd(&st->bfs_starts, 1);
+        }
+    }
+}
+
+// the BFS state once the starts are seeded; level 0 runs if there is a start
+__global__ void k_mbfsg_init(long long m, DevState *st, cudaGraphConditionalHandle h, int has_h) {
+    st->cmin = 0xffffffffu;
+    st->bfs_level = 0;
+    st->bfs_par = 0;
+    st->bfs_list = -1;
+    st->bfs_len = (unsigned long long)m;
+    st->bfs_kept_prev = (unsigned long long)m;
+    if (has_h) cudaGraphSetConditional(h, st->front[0] > 0 ? 1u : 0u);
+}
+
+// tmin[j] = the smallest vertex of tree j: the lanes of a warp with the same
+// owner reduce their ids first, so a large tree costs one atomic per warp
+__global__ void __launch_bounds__(kBlock) k_mbfs_tree_min(const uint32_t *__restrict__ own, vid_t n,
+                                                          uint32_t *tmin) {
+    const int lane = threadIdx.x & 31;
+    for (long long base = gtid() - lane; base < (long long)n; base += gstride()) {
+        const long long v = base + lane;
+        const uint32_t o = v < (long long)n ? own[v] : kNoOwner;
+        const unsigned act = __ballot_sync(0xffffffffu, o != kNoOwner);
+        if (o != kNoOwner) {
+            const unsigned grp = __match_any_sync(act, o);
+            const unsigned mn = __reduce_min_sync(grp, (unsigned)v);
+            if (lane == __ffs(grp) - 1) atomicMin(&tmin[o], mn);
+        }
+    }
+}
+
+// every vertex a tree reached takes the tree's smallest vertex as parent (a
+// root: it is in the tree, so its own parent is itself); the rest are roots
+__global__ void __launch_bounds__(kBlock) k_mbfs_parents(const uint32_t *__restrict__ own,
+                                                         const uint32_t *__restrict__ tmin, vid_t n, vid_t *parent) {
+    for (long long v = gtid(); v < (long long)n; v += gstride()) {
+        const uint32_t o = own[v];
+        parent[v] = o == kNoOwner ? (vid_t)v : tmin[o];
+    }
+}
+
+void launch_mbfs_start(const uint32_t *deg, vid_t n, long long m, int k, uint32_t *vis, uint32_t *b0, uint32_t *own,
+                       uint32_t *tmin, DevState *st, const cudaGraphConditionalHandle *h, cudaStream_t s) {
+    const long long nwords = ((long long)n + 31) / 32;
+    cudaMemsetAsync(vis, 0, (size_t)nwords * 4, s);
+    cudaMemsetAsync(b0, 0, (size_t)nwords * 4, s);
+    cudaMemsetAsync(own, 0xff, (size_t)n * 4, s);
+    cudaMemsetAsync(tmin, 0xff, (size_t)k * 4, s);
+    cudaMemsetAsync(&st->front[0], 0, sizeof(st->front) + sizeof(st->front_edges), s);
+    cudaMemsetAsync(&st->bfs_starts, 0, sizeof(st->bfs_starts), s);
+    k_mbfs_starts<<<k, kBlock, 0, s>>>(deg, n, k, vis, b0, own, st);
+    k_mbfsg_init<<<1, 1, 0, s>>>(m, st, h ? *h : cudaGraphConditionalHandle(), h ? 1 : 0);
+}
+
+void launch_mbfs_finish(const uint32_t *own, uint32_t *tmin, vid_t n, vid_t *parent, int grid, cudaStream_t s) {
+    k_mbfs_tree_min<<<grid, kBlock, 0, s>>>(own, n, tmin);
+    k_mbfs_parents<<<grid, kBlock, 0, s>>>(own, tmin, n, parent);
 }
 
 void launch_ebfsg_init(uint32_t *vis, uint32_t *b0, vid_t n, long long m, DevState *st, cudaGraphConditionalHandle h,
@@ -918,24 +1038,32 @@ void launch_ebfsg_init(uint32_t *vis, uint32_t *b0, vid_t n, long long m, DevSta
     k_ebfsg_init<<<1, 1, 0, s>>>(vis, b0, n, m, st, h);
 }
 
+template <typename T, bool OWN>
+void launch_ebfsg_level_k(const void *caller, long long m, const uint2 *eb0, const uint2 *eb1, vid_t n, uint32_t *vis,
+                          uint32_t *b0, uint32_t *b1, DevState *st, int grid, cudaStream_t s, uint32_t *own) {
+    auto kc = k_ebfsg_level<T, OWN>;
+    auto kl = k_ebfsg_level<uint32_t, OWN>;
+    kc<<<fit_grid((const void *)kc, grid, kBlock), kBlock, 0, s>>>((const T *)caller, m, eb0, eb1, n, vis, b0, b1, st,
+                                                                     own);
+    kl<<<fit_grid((const void *)kl, grid, kBlock), kBlock, 0, s>>>(nullptr, 0, eb0, eb1, n, vis, b0, b1, st, own);
+}
+
 template <typename T>
 int launch_ebfsg_level(const void *caller, long long m, const uint2 *eb0, const uint2 *eb1, vid_t n, uint32_t *vis,
                        uint32_t *b0, uint32_t *b1, DevState *st, cudaGraphConditionalHandle h, int grid,
-                       cudaStream_t s) {
+                       cudaStream_t s, uint32_t *own, bool has_h) {
     const long long nwords = ((long long)n + 31) / 32;
     k_ebfsg_plan<<<grid, kBlock, 0, s>>>(b0, b1, nwords, st);
-    k_ebfsg_level<T><<<fit_grid((const void *)k_ebfsg_level<T>, grid, kBlock), kBlock, 0, s>>>(
-        (const T *)caller, m, eb0, eb1, n, vis, b0, b1, st);
-    k_ebfsg_level<uint32_t><<<fit_grid((const void *)k_ebfsg_level<uint32_t>, grid, kBlock), kBlock, 0, s>>>(
-        nullptr, 0, eb0, eb1, n, vis, b0, b1, st);
-    k_ebfsg_step<<<1, 1, 0, s>>>(st, h);
+    if (own) launch_ebfsg_level_k<T, true>(caller, m, eb0, eb1, n, vis, b0, b1, st, grid, s, own);
+    else launch_ebfsg_level_k<T, false>(caller, m, eb0, eb1, n, vis, b0, b1, st, grid, s, nullptr);
+    k_ebfsg_step<<<1, 1, 0, s>>>(st, h, has_h ? 1 : 0);
     return 4;
 }
 template int launch_ebfsg_level<int32_t>(const void *, long long, const uint2 *, const uint2 *, vid_t, uint32_t *,
                                          uint32_t *, uint32_t *, DevState *, cudaGraphConditionalHandle, int,
-                                         cudaStream_t);
+                                         cudaStream_t, uint32_t *, bool);
 template int launch_ebfsg_level<int64_t>(const void *, long long, const uint2 *, const uint2 *, vid_t, uint32_t *,
                                          uint32_t *, uint32_t *, DevState *, cudaGraphConditionalHandle, int,
-                                         cudaStream_t);
+                                         cudaStream_t, uint32_t *, bool);
 
 }  // namespace ccg

@@ -524,12 +524,14 @@ __global__ void __launch_bounds__(kBlock) k_parent_init_st(vid_t *parent, vid_t 
     }
 }
 
-// The first SV pass after the BFS (MODE 1: a pair with both ends visited is
-// dropped, a visited end stands for cmin) over the pairs the BFS left
-// active: the caller's list (bfs_list < 0; the T instantiation runs) or
-// ebuf[bfs_list] (the uint32 instantiation runs). The surviving pairs go to
-// the other buffer, and the SV loop continues after this iteration 0.
-template <typename T>
+// The first SV pass after the BFS over the pairs the BFS left active: the
+// caller's list (bfs_list < 0; the T instantiation runs) or ebuf[bfs_list]
+// (the uint32 instantiation runs). MODE 1 after one tree (a pair with both
+// ends visited is dropped, a visited end stands for cmin); MODE 2 after the
+// multi-start BFS, whose trees already point at their minima (one-hop
+// gathers). The surviving pairs go to the other buffer, and the SV loop
+// continues after this iteration 0.
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kBlock) k_sv_after_bfs(const T *__restrict__ caller, long long m, const uint2 *eb0,
                                                          const uint2 *eb1, vid_t n, vid_t *parent,
                                                          const uint32_t *__restrict__ vis, vid_t *hooked_list,
@@ -541,7 +543,7 @@ __global__ void __launch_bounds__(kBlock) k_sv_after_bfs(const T *__restrict__ c
     const long long len = kList ? (long long)st->bfs_len : m;
     const int cur0 = list == 0 ? 1 : 0;
     uint2 *out = const_cast<uint2 *>(cur0 ? eb1 : eb0);
-    sv_pass_body<T, 1, true, true>(in, len, n, parent, vis, st->cmin, hooked_list, out, st, 0);
+    sv_pass_body<T, MODE, true, true>(in, len, n, parent, vis, st->cmin, hooked_list, out, st, 0);
     if (gtid() == 0) {
         st->loop_start_it = 0;
         st->loop_start_cur = cur0;
@@ -594,19 +596,29 @@ void launch_parent_init_st(vid_t *parent, vid_t n, const uint32_t *vis, const De
     k_parent_init_st<<<grid, kBlock, 0, s>>>(parent, n, vis, st);
 }
 
+template <typename T, int MODE>
+void launch_sv_after_bfs_m(const void *caller, long long m, const uint2 *eb0, const uint2 *eb1, vid_t n,
+                           vid_t *parent, const uint32_t *vis, vid_t *hooked_list, DevState *st, int grid,
+                           cudaStream_t s) {
+    auto kc = k_sv_after_bfs<T, MODE>;
+    auto kl = k_sv_after_bfs<uint32_t, MODE>;
+    kc<<<fit_grid((const void *)kc, grid, kBlock), kBlock, 0, s>>>((const T *)caller, m, eb0, eb1, n, parent, vis,
+                                                                     hooked_list, st);
+    kl<<<fit_grid((const void *)kl, grid, kBlock), kBlock, 0, s>>>(nullptr, 0, eb0, eb1, n, parent, vis, hooked_list,
+                                                                     st);
+}
+
 template <typename T>
 int launch_sv_after_bfs(const void *caller, long long m, const uint2 *eb0, const uint2 *eb1, vid_t n, vid_t *parent,
-                        const uint32_t *vis, vid_t *hooked_list, DevState *st, int grid, cudaStream_t s) {
-    k_sv_after_bfs<T><<<fit_grid((const void *)k_sv_after_bfs<T>, grid, kBlock), kBlock, 0, s>>>(
-        (const T *)caller, m, eb0, eb1, n, parent, vis, hooked_list, st);
-    k_sv_after_bfs<uint32_t><<<fit_grid((const void *)k_sv_after_bfs<uint32_t>, grid, kBlock), kBlock, 0, s>>>(
-        nullptr, 0, eb0, eb1, n, parent, vis, hooked_list, st);
+                        const uint32_t *vis, vid_t *hooked_list, DevState *st, int grid, cudaStream_t s, bool trees) {
+    if (trees) launch_sv_after_bfs_m<T, 2>(caller, m, eb0, eb1, n, parent, vis, hooked_list, st, grid, s);
+    else launch_sv_after_bfs_m<T, 1>(caller, m, eb0, eb1, n, parent, vis, hooked_list, st, grid, s);
     return 2;
 }
 template int launch_sv_after_bfs<int32_t>(const void *, long long, const uint2 *, const uint2 *, vid_t, vid_t *,
-                                          const uint32_t *, vid_t *, DevState *, int, cudaStream_t);
+                                          const uint32_t *, vid_t *, DevState *, int, cudaStream_t, bool);
 template int launch_sv_after_bfs<int64_t>(const void *, long long, const uint2 *, const uint2 *, vid_t, vid_t *,
-                                          const uint32_t *, vid_t *, DevState *, int, cudaStream_t);
+                                          const uint32_t *, vid_t *, DevState *, int, cudaStream_t, bool);
 
 void launch_sv_loop_init_st(DevState *st, int cap, cudaGraphConditionalHandle h, cudaStream_t s) {
     k_sv_loop_init_st<<<1, 1, 0, s>>>(st, cap, h);

@@ -72,3 +72,20 @@ def test_batch4096_sizes_follow_the_workload():
     n30, m30 = gg.batch_sizes(seed=1, G=30, nmin=1000, nmax=5000)
     assert np.diff(sub.vertex_offsets).tolist() == n30[[29, 3, 17]].tolist()
     assert np.diff(sub.edge_offsets).tolist() == m30[[29, 3, 17]].tolist()
+
+
+def test_union_keeps_each_part_a_separate_set_of_components():
+    """The union relabels by one permutation: each part's pairs stay within
+    that part's vertices, and the parts' vertex sets partition [0, n)."""
+    parts = [gg.chung_lu(seed=3 + i, n=500 + 100 * i, avg_degree=6) for i in range(4)]
+    u = gg.union(parts, seed=9)
+    assert u.n == sum(p.n for p in parts) and u.m == sum(p.m for p in parts)
+    part = u.meta["comp_of_part"]
+    assert np.array_equal(np.bincount(part), [p.n for p in parts])
+    assert np.array_equal(part[u.edges[:, 0]], part[u.edges[:, 1]])
+    # the degree sequence of each part survives the relabelling
+    deg = np.bincount(u.edges.ravel(), minlength=u.n)
+    for i, p in enumerate(parts):
+        want = np.sort(np.bincount(p.edges.ravel(), minlength=p.n))
+        assert np.array_equal(np.sort(deg[part == i]), want)
+    assert np.array_equal(gg.union(parts, seed=9).edges, u.edges)
