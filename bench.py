@@ -50,8 +50,8 @@ WORKLOADS = {
     "grid_chains": dict(kind="grid_chains", seed=1, W=8192, nchains=10_000_000),
     "grid_chains_67m": dict(kind="grid_chains", seed=1, W=4096, nchains=2_500_000),
     "chung_lu24": dict(kind="chung_lu", seed=1, n=1 << 24, avg_degree=16.0),
-    # many mid-size power-law components: 200 Chung-Lu graphs, n log-uniform in [2^14, 2^18]
-    "chung_lu_union": dict(kind="union", seed=1, parts=200, nmin=1 << 14, nmax=1 << 18, avg_degree=16.0),
+    # many mid-size power-law components: 200 Chung-Lu graphs, n log-uniform in [2^13, 2^17]
+    "chung_lu_union": dict(kind="union", seed=1, parts=200, nmin=1 << 13, nmax=1 << 17, avg_degree=16.0),
     "batch4096": dict(kind="batch", seed=1, G=4096, nmin=1000, nmax=1_000_000),
     "batch512": dict(kind="batch", seed=1, G=512, nmin=1000, nmax=1_000_000),
 }
@@ -639,6 +639,20 @@ def batch_record(args, dev, stream, world: int = 1, rank: int = 0, dist=None, wo
             "m_active": st["m_active"], "labels_vs_oracle": same, "graphs_checked": checked, "cpu_baseline": cpu}
 
 
+def cpu_leg_multi(g, starts) -> tuple[np.ndarray, dict]:
+    """The oracle's labels of g, and per start count k the oracle's number of
+    trees and of reached vertices of a k-start BFS (outside any timed region)."""
+    import oracle
+    from oracle import multi_bfs
+
+    want = oracle.labels_uf(g.edges, g.n)
+    reach = {}
+    for k in starts:
+        s0, reached = multi_bfs.multi_bfs_reached(g.edges, g.n, k)
+        reach[k] = (len(s0), int(reached.sum()))
+    return want, reach
+
+
 def multi_start_record(args, dev, stream, name: str = "chung_lu_union", starts=(64, 1024)) -> dict:
     """The multi-start BFS step (several traversals at once) on many mid-size
     power-law components, against one BFS tree (Algorithm 2) and against SV
@@ -646,15 +660,13 @@ def multi_start_record(args, dev, stream, name: str = "chung_lu_union", starts=(
     every route's labels against the oracle."""
     import torch
 
-    import oracle
     import paper_1607_06156_gb300 as cc
-    from oracle import multi_bfs
 
     g = make_graph(name)
     w, n, m = g.id_bytes, g.n, g.m
+    want, reach = cpu_leg_multi(g, starts)
     edges_d = torch.from_numpy(g.edges).to(dev)
     lab = torch.empty(n, dtype=edges_d.dtype, device=dev)
-    want = oracle.labels_uf(g.edges, n)
     runs = {"one_tree": {}, "sv_only": {"route": "sv"}}
     for k in starts:
         runs[f"starts_{k}"] = {"bfs_starts": k}
@@ -679,9 +691,8 @@ def multi_start_record(args, dev, stream, name: str = "chung_lu_union", starts=(
                     "pairs_left_for_sv": st["m_active"][0]}
             k = opts.get("bfs_starts", 1)
             if k > 1:
-                s0, reached = multi_bfs.multi_bfs_reached(g.edges, n, k)
-                rec["visited_vs_oracle"] = bool(st["bfs_visited"] == int(reached.sum()) and
-                                                st["bfs_starts"] == len(s0))
+                nstarts, nreached = reach[k]
+                rec["visited_vs_oracle"] = bool(st["bfs_visited"] == nreached and st["bfs_starts"] == nstarts)
                 kms, kla, pst, _ = profiled_calls(torch, eng, call, max(1, min(args.steps, 3)), stream)
                 rec["kernels"] = kernel_table(kms, kla, pst, w, max(1, min(args.steps, 3)))
                 bfs_ms = kms.get("bfs_bottomup", 0.0) / max(1, min(args.steps, 3))

@@ -66,6 +66,8 @@ def _load():
         lib.oracle_hurwitz_zeta.argtypes = [_dbl, _dbl]
         lib.oracle_ks_fit.restype = None
         lib.oracle_ks_fit.argtypes = [_ptr, _i64, _i64, _i64, _dbl, _ptr]
+        lib.oracle_multi_bfs.restype = _int
+        lib.oracle_multi_bfs.argtypes = [_ptr, _int, _i64, _i64, _ptr, _i64, _i64, _ptr]
         _lib = lib
     return _lib
 
@@ -120,6 +122,22 @@ def cc_labels(edges: np.ndarray, n: int, cross_check: bool | None = None) -> np.
         if not np.array_equal(lab, lab2):
             raise AssertionError("union-find and BFS labellers disagree")
     return lab
+
+
+def multi_bfs_distances(edges: np.ndarray, n: int, starts: np.ndarray, cutoff: int = 0) -> np.ndarray:
+    """dist[v] = least number of pairs from any start to v (-1: not
+    reached), BFS from all starts at once, stopping after `cutoff` levels
+    when cutoff > 0 (Section 3.2, the BFS step)."""
+    e, w, m = _edges(edges)
+    st = np.ascontiguousarray(starts, dtype=np.int64)
+    out = np.empty(max(n, 1), dtype=np.int64)
+    rc = _load().oracle_multi_bfs(e.ctypes.data_as(_ptr), w, n, m, st.ctypes.data_as(_ptr), st.size, int(cutoff),
+                                  out.ctypes.data_as(_ptr))
+    if rc == 1:
+        raise ValueError("id out of range [0, n)")
+    if rc != 0:
+        raise RuntimeError(f"oracle_multi_bfs failed with code {rc}")
+    return out[:n]
 
 
 def degrees(edges: np.ndarray, n: int) -> np.ndarray:

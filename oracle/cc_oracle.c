@@ -140,6 +140,61 @@ int oracle_bfs_labels(const void *edges, int id_bytes, int64_t n, int64_t m, int
     return 0;
 }
 
+/* ---------------- multi-source BFS distances ---------------- */
+/*
+ * The BFS step of Section 3.2 from several starts at once: dist[v] = the
+ * least number of pairs on a path from any start to v, -1 if no start
+ * reaches v. A queue holds the vertices in increasing distance; with
+ * cutoff > 0 vertices at distance cutoff are not expanded (the traversal
+ * stops after `cutoff` levels). Returns 0, 1 for an id outside [0, n), 2
+ * when memory runs out.
+ */
+int oracle_multi_bfs(const void *edges, int id_bytes, int64_t n, int64_t m, const int64_t *starts, int64_t nstarts,
+                     int64_t cutoff, int64_t *dist) {
+    if (oracle_check_ids(edges, id_bytes, n, m)) return 1;
+    for (int64_t i = 0; i < nstarts; i++)
+        if (starts[i] < 0 || starts[i] >= n) return 1;
+    int64_t *start = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t *adj = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * m + 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!start || !adj || !fill || !queue) {
+        free(start); free(adj); free(fill); free(queue);
+        return 2;
+    }
+    for (int64_t i = 0; i < m; i++) {
+        start[edge_at(edges, id_bytes, 2 * i) + 1]++;
+        start[edge_at(edges, id_bytes, 2 * i + 1) + 1]++;
+    }
+    for (int64_t v = 0; v < n; v++) start[v + 1] += start[v];
+    memcpy(fill, start, sizeof(int64_t) * (size_t)n);
+    for (int64_t i = 0; i < m; i++) {
+        int64_t u = edge_at(edges, id_bytes, 2 * i), v = edge_at(edges, id_bytes, 2 * i + 1);
+        adj[fill[u]++] = v;
+        adj[fill[v]++] = u;
+    }
+    for (int64_t v = 0; v < n; v++) dist[v] = -1;
+    int64_t head = 0, tail = 0;
+    for (int64_t i = 0; i < nstarts; i++)
+        if (dist[starts[i]] < 0) {
+            dist[starts[i]] = 0;
+            queue[tail++] = starts[i];
+        }
+    while (head < tail) {
+        int64_t x = queue[head++];
+        if (cutoff > 0 && dist[x] >= cutoff) continue;
+        for (int64_t k = start[x]; k < start[x + 1]; k++) {
+            int64_t y = adj[k];
+            if (dist[y] < 0) {
+                dist[y] = dist[x] + 1;
+                queue[tail++] = y;
+            }
+        }
+    }
+    free(start); free(adj); free(fill); free(queue);
+    return 0;
+}
+
 /* ---------------- transitive closure (tiny n) ---------------- */
 int oracle_closure_labels(const void *edges, int id_bytes, int64_t n, int64_t m, int64_t *labels) {
     if (n > 256) return 3;

@@ -25,6 +25,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import degrees
+from . import multi_bfs_distances as _distances
 
 
 def bfs_starts(edges: np.ndarray, n: int, k: int) -> np.ndarray:
@@ -47,31 +48,9 @@ def multi_bfs_distances(edges: np.ndarray, n: int, starts: np.ndarray, cutoff: i
     """Level-synchronous BFS from all starts at once: dist[v] = the smallest
     number of pairs on a path from a start to v, -1 if v is not reached.
     With cutoff L > 0 the traversal stops after L levels, so only distances
-    <= L are found (cutoff 0: run to completion)."""
-    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
-    # both directions of every pair, grouped by source (the adjacency lists)
-    src = np.concatenate([e[:, 0], e[:, 1]])
-    dst = np.concatenate([e[:, 1], e[:, 0]])
-    order = np.argsort(src, kind="stable")
-    src, dst = src[order], dst[order]
-    row = np.searchsorted(src, np.arange(n + 1))
-    dist = np.full(n, -1, dtype=np.int64)
-    frontier = np.unique(np.asarray(starts, dtype=np.int64))
-    dist[frontier] = 0
-    level = 0
-    while frontier.size and (cutoff <= 0 or level < cutoff):
-        lens = row[frontier + 1] - row[frontier]
-        total = int(lens.sum())
-        if total == 0:
-            break
-        first = np.repeat(row[frontier], lens)
-        within = np.arange(total) - np.repeat(np.cumsum(lens) - lens, lens)
-        nbrs = dst[first + within]
-        new = np.unique(nbrs[dist[nbrs] < 0])
-        dist[new] = level + 1
-        frontier = new
-        level += 1
-    return dist
+    <= L are found (cutoff 0: run to completion). The queue BFS of the
+    oracle's C library."""
+    return _distances(edges, n, starts, cutoff)
 
 
 def multi_bfs_reached(edges: np.ndarray, n: int, k: int, cutoff: int = 0) -> tuple[np.ndarray, np.ndarray]:

@@ -53,7 +53,7 @@ def test_bench_uses_the_oracle_only_in_its_cpu_legs():
     (the timed oracle and the label check); the timing helpers never call
     them, so no oracle work sits inside a timed region."""
     path = os.path.join(ROOT, "bench.py")
-    legs = {"cpu_oracle_rate", "cpu_leg", "cpu_leg_check", "cpu_leg_batch"}
+    legs = {"cpu_oracle_rate", "cpu_leg", "cpu_leg_check", "cpu_leg_batch", "cpu_leg_multi"}
     assert {fn for m, fn in _imports(path) if m == "oracle"} <= legs
     tree = ast.parse(open(path).read())
     callers = {}
@@ -62,5 +62,6 @@ def test_bench_uses_the_oracle_only_in_its_cpu_legs():
             for node in ast.walk(fn):
                 if isinstance(node, ast.Call) and getattr(node.func, "id", None) in legs:
                     callers.setdefault(fn.name, set()).add(node.func.id)
-    assert set(callers) <= {"run_reference", "main", "cpu_leg", "single_record", "batch_record", "learned_record"}
+    assert set(callers) <= {"run_reference", "main", "cpu_leg", "single_record", "batch_record", "learned_record",
+                            "multi_start_record"}
     assert "timed_calls" not in callers and "profiled_calls" not in callers
