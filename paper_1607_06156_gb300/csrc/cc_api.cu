@@ -32,6 +32,7 @@ constexpr size_t kCtrBfs = 0;           // BFS visited counts (two 64-bit words)
 constexpr size_t kCtrSmallFitVo = 256;  // vertex offsets {0, n} of the one-graph fit (two int64)
 constexpr size_t kCtrKsQueue = 1024;    // next graph of the batched fits (int)
 constexpr size_t kCtrTileQueue = 1088;  // next tile of the batched degree pass (64-bit)
+constexpr size_t kCtrCsrQueue = 1096;   // next tile of the CSR placement (64-bit)
 constexpr size_t kCountersBytes = 4096;
 template <typename P> P *counter_at(Buf &b, size_t off) { return reinterpret_cast<P *>(static_cast<char *>(b.p) + off); }
 
@@ -49,7 +50,7 @@ struct cc_ctx {
         tsv_cnt;
     long long tsv_cap = 0;
     Buf deg, parent, hooked, ebuf0, ebuf1, hist, ovf, ks_xs, ks_cnt, ks_cum, ks_lnx, ks_Dc, ks_Ac, ks_Zc, ks_Df, chunk_nz,
-        chunk_mass, st, bk_count, bk_off, bk_cursor;
+        chunk_mass, st, bk_off;
     Buf dpart;  // endpoints partitioned into vertex windows (degree pass of graphs with n > 2^25)
     Buf bfs_own, bfs_tmin;  // multi-start BFS: the tree of every vertex, the minimum of every tree
     unsigned long long ovf_cap = 0, ks_cap = 0;
@@ -214,8 +215,6 @@ cc_status ensure_sv(cc_ctx *ctx, size_t n, size_t m) {
     CC_TRY(buf_reserve(ctx, ctx->st, sizeof(DevState)));
     // small device counters (byte offsets kCtr*)
     CC_TRY(buf_reserve(ctx, ctx->counters, kCountersBytes));
-    CC_TRY(buf_reserve(ctx, ctx->bk_count, (size_t)ctx->grid * (bucket_max() + 2) * 4));
-    CC_TRY(buf_reserve(ctx, ctx->bk_cursor, (size_t)ctx->grid * (bucket_max() + 2) * 4));
     CC_TRY(buf_reserve(ctx, ctx->bk_off, (size_t)(bucket_max() + 2) * 8));
     if (degree_part_ok((vid_t)(N < 0xffffffffULL ? N : 0xfffffffeULL), (long long)M))
         CC_TRY(buf_reserve(ctx, ctx->dpart, degree_part_scratch_bytes((vid_t)N, (long long)M)));
@@ -515,7 +514,7 @@ cc_status sv_graph_finish(cc_ctx *ctx, int it0, int prefix_launches, cudaStream_
 }
 
 BucketScratch bucket_scratch(cc_ctx *ctx) {
-    return BucketScratch{as<uint32_t>(ctx->bk_count), as<uint32_t>(ctx->bk_cursor), as<unsigned long long>(ctx->bk_off)};
+    return BucketScratch{as<unsigned long long>(ctx->bk_off), counter_at<unsigned long long>(ctx->counters, kCtrCsrQueue)};
 }
 
 float ev_ms(cc_ctx *ctx, Ev a, Ev b) {
@@ -596,14 +595,13 @@ cc_status run_bfs(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStre
     const bool bucketed = bucketed_ok(n, (size_t)m) && ctx->csr_entries.p;
     {
         Scope sc(ctx, CC_K_SCAN, s, 3);
-        // the direct scatter uses deg as its cursor
-        launch_scan_u32(deg, n, row_ptr, bucketed ? nullptr : deg, as<unsigned long long>(ctx->tsum), nullptr,
-                        row_ptr + n, s);
+        // both CSR builds use a copy of row_ptr in deg as their cursors
+        launch_scan_u32(deg, n, row_ptr, deg, as<unsigned long long>(ctx->tsum), nullptr, row_ptr + n, s);
     }
     if (bucketed) {
-        Scope sc(ctx, CC_K_CSR, s, 4);
-        launch_csr_bucketed<T>(edges, m, n, row_ptr, col, bucket_scratch(ctx), as<unsigned long long>(ctx->csr_entries),
-                               st, ctx->grid, s);
+        Scope sc(ctx, CC_K_CSR, s, 2);
+        launch_csr_bucketed<T>(edges, m, n, row_ptr, deg, col, bucket_scratch(ctx),
+                               as<unsigned long long>(ctx->csr_entries), st, ctx->grid, s);
     } else {
         Scope sc(ctx, CC_K_CSR, s, 1);
         launch_csr_scatter<T>(edges, m, n, deg, col, ctx->grid, s);
@@ -1531,14 +1529,13 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
                 uint32_t *row_ptr = as<uint32_t>(ctx->row_ptr), *deg = as<uint32_t>(ctx->deg);
                 vid_t *col = as<vid_t>(ctx->col);
                 const bool bucketed = bucketed_ok(n, (size_t)m) && ctx->csr_entries.p;
-                launch_scan_u32(deg, n, row_ptr, bucketed ? nullptr : deg, as<unsigned long long>(ctx->tsum), nullptr,
-                                row_ptr + n, bs);
+                launch_scan_u32(deg, n, row_ptr, deg, as<unsigned long long>(ctx->tsum), nullptr, row_ptr + n, bs);
                 if (bucketed)
-                    launch_csr_bucketed<T>(edges, m, n, row_ptr, col, bucket_scratch(ctx),
+                    launch_csr_bucketed<T>(edges, m, n, row_ptr, deg, col, bucket_scratch(ctx),
                                            as<unsigned long long>(ctx->csr_entries), st, ctx->grid, bs);
                 else
                     launch_csr_scatter<T>(edges, m, n, deg, col, ctx->grid, bs);
-                rg.bfs_launches += 3 + (bucketed ? 4 : 1) + 1;  // the scan, the CSR, the BFS state
+                rg.bfs_launches += 3 + (bucketed ? 2 : 1) + 1;  // the scan, the CSR, the BFS state
                 uint32_t *vm = as<uint32_t>(ctx->vis);
                 CU_TRY(cudaMemsetAsync(vm, 0, (size_t)nwords * 4, bs));
                 cudaGraphConditionalHandle hb;
@@ -2358,8 +2355,7 @@ cc_status cc_create(cc_ctx **out, const cc_options *opt, int device) {
         return CC_ERR_CUDA;
     }
     ctx->num_sms = prop.multiProcessorCount;
-    if (bucket_kernels_setup() != cudaSuccess || degree_part_setup() != cudaSuccess ||
-        degree_hubs_setup() != cudaSuccess) {
+    if (degree_part_setup() != cudaSuccess || degree_hubs_setup() != cudaSuccess || csr_kernels_setup() != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return CC_ERR_CUDA;
@@ -2395,9 +2391,10 @@ cc_status cc_destroy(cc_ctx *ctx) {
                    &ctx->ovf,    &ctx->ks_xs,      &ctx->ks_cnt, &ctx->ks_cum,  &ctx->ks_lnx, &ctx->ks_Dc,
                    &ctx->ks_Ac,  &ctx->ks_Zc, &ctx->ks_Df, &ctx->chunk_nz,   &ctx->chunk_mass, &ctx->st,  &ctx->row_ptr, &ctx->col,
                    &ctx->vis,    &ctx->fb,         &ctx->nb,     &ctx->q0,      &ctx->q1,     &ctx->dq,
-                   &ctx->off,    &ctx->tsum,       &ctx->counters, &ctx->bk_count, &ctx->bk_off,
-                   &ctx->bk_cursor, &ctx->csr_entries, &ctx->dpart, &ctx->f_sdeg, &ctx->f_counts, &ctx->f_vis,
-                   &ctx->f_f0,   &ctx->f_f1,       &ctx->f_x,    &ctx->pred_wb, &ctx->pred_bias, &ctx->pred_tmp};
+                   &ctx->off,    &ctx->tsum,       &ctx->counters, &ctx->bk_off, &ctx->csr_entries,
+                   &ctx->dpart,  &ctx->f_sdeg,     &ctx->f_counts, &ctx->f_vis,
+                   &ctx->f_f0,   &ctx->f_f1,       &ctx->f_x,    &ctx->pred_wb, &ctx->pred_bias, &ctx->pred_tmp,
+                   &ctx->bfs_own, &ctx->bfs_tmin};
     for (Buf *b : bufs) buf_free(*b);
     for (int e = 0; e < EV_COUNT; e++)
         if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);

@@ -38,18 +38,18 @@ struct KsScratch {
 
 // Scratch of the vertex-block partitioned CSR build (k_bucket.cu).
 struct BucketScratch {
-    uint32_t *counts;             // [grid][buckets] entries of each grid block's chunks per vertex block
-    uint32_t *off;                // [grid][buckets] private write offsets
-    unsigned long long *boff;     // [buckets + 1] (unused by the CSR build)
+    unsigned long long *fill;     // [vertex blocks] entries reserved so far in each block's CSR range
+    unsigned long long *queue;    // the placement's tile counter
 };
 
 // k_bucket.cu
 int bucket_count_for(vid_t n);
 int bucket_max();
 template <typename T>
-void launch_csr_bucketed(const void *edges, long long m, vid_t n, const uint32_t *row_ptr, vid_t *col,
-                         BucketScratch bs, unsigned long long *entries, DevState *st, int grid, cudaStream_t s);
-cudaError_t bucket_kernels_setup();
+void launch_csr_bucketed(const void *edges, long long m, vid_t n, const uint32_t *row_ptr, uint32_t *cursor,
+                         vid_t *col, BucketScratch bs, unsigned long long *entries, DevState *st, int grid,
+                         cudaStream_t s);
+cudaError_t csr_kernels_setup();
 
 // Scratch of the sampled route features (k_mlp.cu).
 struct FeatScratch {

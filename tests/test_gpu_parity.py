@@ -271,7 +271,32 @@ def test_partitioned_degree_and_csr_paths(id_bytes):
     assert np.array_equal(deg.cpu().numpy().astype(np.int64), deg_o)
     assert np.array_equal(hist.cpu().numpy()[:-1], oracle.histogram(deg_o))
     eng.close()
-    assert_labels_match(e, g.n, routes=("auto", "bfs"))
+    st = assert_labels_match(e, g.n, routes=("auto", "bfs"))["bfs"]
+    _check_bfs_reach(e, g.n, st)
+
+
+def _check_bfs_reach(e, n, st):
+    """The CSR BFS from the max-degree vertex reached exactly that vertex's
+    component: a missing or a wrong adjacency entry changes the count."""
+    from oracle import multi_bfs
+
+    starts, reached = multi_bfs.multi_bfs_reached(e, n, 1)
+    assert st["route"] == 1 and st["bfs_visited"] == int(reached.sum()), (st["bfs_visited"], int(reached.sum()))
+
+
+def test_csr_placement_of_a_vertex_block_with_a_hub():
+    """One vertex of degree 2^21 makes its vertex block hold far more entries
+    than the average: the placement merges the lanes that hit it. The BFS
+    from it must reach exactly its component."""
+    rng = np.random.default_rng(11)
+    n = 1 << 20
+    leaves = rng.choice(n, size=1 << 21)
+    star = np.stack([np.full(leaves.size, 777), leaves], axis=1)
+    noise = rng.integers(0, n, size=(1 << 19, 2))
+    e = np.concatenate([star, noise]).astype(np.int32)
+    e = e[rng.permutation(len(e))]
+    st = assert_labels_match(e, n, routes=("bfs",))["bfs"]
+    _check_bfs_reach(e, n, st)
 
 
 def test_partitioned_paths_many_vertex_blocks():
@@ -279,7 +304,8 @@ def test_partitioned_paths_many_vertex_blocks():
     n = (1 << 25) - 5
     rng = np.random.default_rng(8)
     e = rng.integers(0, n, size=((1 << 21) + 1, 2)).astype(np.int32)
-    assert_labels_match(e, n, routes=("bfs",))
+    st = assert_labels_match(e, n, routes=("bfs",))["bfs"]
+    _check_bfs_reach(e, n, st)
 
 
 @pytest.mark.parametrize("seed", list(range(12)))
