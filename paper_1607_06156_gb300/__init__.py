@@ -70,7 +70,7 @@ class Stats(ctypes.Structure):
         ("ms_features", ctypes.c_float),
         ("batch_unroll", ctypes.c_int32),
         ("batch_grid_mult", ctypes.c_int32),
-        ("sv_sample_stride", ctypes.c_int32), ("batch_deg_vec", ctypes.c_int32),
+        ("sv_sample_stride", ctypes.c_int32), ("batch_deg_regions", ctypes.c_int32),
         ("bfs_starts", ctypes.c_int32), ("pad3", ctypes.c_int32),
     ]
 

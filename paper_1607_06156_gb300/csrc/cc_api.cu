@@ -103,6 +103,7 @@ struct cc_ctx {
         int sample_stride = 1;          // SV front end stride
         bool edge_bfs = false;          // the BFS branch is the edge-list BFS
         bool batched = false;           // the batched form (route = graphs that took the BFS step)
+        int batch_unroll = 0, batch_grid_mult = 0, batch_deg_regions = 0;  // the batched form's tuned schedule
     } g_route;
     RouteGraph g_capture;               // the same facts for a call captured into the caller's graph
     const RouteGraph *rg_last = nullptr; // the facts of the last graph-mode call
@@ -1610,6 +1611,9 @@ void stats_from_device(cc_ctx *ctx) {
     // the SV loop continues after iteration 0 (BFS route) or 1 (SV route; always in the batched form)
     const int it0 = h->route_taken && !rg.batched ? 0 : 1;
     if (rg.batched) {
+        S.batch_unroll = rg.batch_unroll;
+        S.batch_grid_mult = rg.batch_grid_mult;
+        S.batch_deg_regions = rg.batch_deg_regions;
         S.route_source = ctx->opt.route_policy == CC_ROUTE_AUTO || ctx->opt.route_policy == CC_ROUTE_LEARNED ? 0 : 2;
         S.bfs_levels = h->route_taken ? h->bfs_level : 0;
         S.m_active[0] = S.m;
@@ -1905,21 +1909,22 @@ cc_status tune_batch(cc_ctx *ctx, const int32_t *edges, long long m, const int64
             *out = c;
         }
     }
-    // the degree pass (idempotent after a reset of the counts): vectors per
-    // thread and tile, fewer blocks resident with more loads in flight each
+    // the degree pass (idempotent after a reset of the counts): regions of
+    // the pairs worked on side by side
     if (ctx->deg.p && ctx->deg.bytes >= (size_t)nt * 4) {
         float best_deg = 1e30f;
-        for (int vec : {2, 4, 8}) {
+        for (int regions : {1, 8, 32}) {
             CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)nt * 4, s));
             CU_TRY(cudaEventRecord(a, s));
-            launch_degree_batch(edges, m, eo, vo, G, as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), vec, s);
+            launch_degree_batch(edges, m, eo, vo, G, as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), regions,
+                                s);
             CU_TRY(cudaEventRecord(b, s));
             CU_TRY(cudaEventSynchronize(b));
             float ms = 0.f;
             CU_TRY(cudaEventElapsedTime(&ms, a, b));
             if (ms < best_deg) {
                 best_deg = ms;
-                out->deg_vec = vec;
+                out->deg_regions = regions;
             }
         }
     }
@@ -2116,6 +2121,9 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
     rg.bfs_launches = 0;
     rg.unsure_launches = 0;
     rg.sample_stride = sch.front ? -1 : 1;
+    rg.batch_unroll = sch.unroll;
+    rg.batch_grid_mult = sch.grid_mult;
+    rg.batch_deg_regions = sch.deg_regions;
     CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), cs));
     enqueue_batch_tables(ctx, eo_u, vo_u, G, m, n, cs);
     launch_parent_init(parent, nt, nullptr, 0, ctx->grid, cs);
@@ -2127,8 +2135,8 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
                    as<int>(ctx->kb_ovf),      as<unsigned long long>(ctx->kb_seed)};
     if (predict) {
         CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, cs));
-        launch_degree_batch(edges, m, eo, vo, G, as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), sch.deg_vec,
-                            cs);
+        launch_degree_batch(edges, m, eo, vo, G, as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx),
+                            sch.deg_regions, cs);
         // the fits (largest graph first) on the highest-priority stream beside the first hook pass
         CU_TRY(cudaEventRecord(ctx->ev_fork, cs));
         CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
@@ -2250,7 +2258,7 @@ cc_status labels_batched_graph(cc_ctx *ctx, const int32_t *edges, const int64_t 
     sch.front = batch_front(ctx, m);
     S.batch_unroll = sch.unroll;
     S.batch_grid_mult = sch.grid_mult;
-    S.batch_deg_vec = sch.deg_vec;
+    S.batch_deg_regions = sch.deg_regions;
     S.sv_sample_stride = sch.front ? -1 : 1;
     if (user_capture) {
         ctx->capturing = true;
@@ -2260,8 +2268,9 @@ cc_status labels_batched_graph(cc_ctx *ctx, const int32_t *edges, const int64_t 
         return r;
     }
     std::vector<unsigned char> key = route_key(ctx, 4, n, m, edges, labels, cap);
-    const long long extra[] = {G, sch.unroll, sch.grid_mult, sch.deg_vec, sch.front, (long long)(uintptr_t)eo_u,
-                               (long long)(uintptr_t)vo_u, (long long)(uintptr_t)ctx->bo_e.p, (long long)(uintptr_t)ctx->kb_route.p,
+    const long long extra[] = {G, sch.unroll, sch.grid_mult, sch.deg_regions, sch.front,
+                               (long long)(uintptr_t)eo_u, (long long)(uintptr_t)vo_u,
+                               (long long)(uintptr_t)ctx->bo_e.p, (long long)(uintptr_t)ctx->kb_route.p,
                                (long long)(uintptr_t)ctx->tile_pairs.p, (long long)(uintptr_t)ctx->kb_cub.p};
     key.insert(key.end(), reinterpret_cast<const unsigned char *>(extra),
                reinterpret_cast<const unsigned char *>(extra) + sizeof(extra));
@@ -2629,7 +2638,7 @@ cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int6
     CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)(n > 0 ? n : 1) * 4, s));
     CC_TRY(ensure_tiles(ctx, edge_offsets_dev, vertex_offsets_dev, G, m, n, s));
     launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, as<uint32_t>(ctx->deg),
-                        st, ctx->grid, tile_queue(ctx), BatchSchedule().deg_vec, s);
+                        st, ctx->grid, tile_queue(ctx), BatchSchedule().deg_regions, s);
     std::vector<int> route;
     CC_TRY(enqueue_ks_batch(ctx, vertex_offsets_dev, vertex_offsets_host, G, s));
     CC_TRY(batch_routes(ctx, vertex_offsets_host, G, route, s));
@@ -2680,7 +2689,7 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
     S.sv_sample_stride = sch.front ? -1 : 1;
     S.batch_unroll = sch.unroll;
     S.batch_grid_mult = sch.grid_mult;
-    S.batch_deg_vec = sch.deg_vec;
+    S.batch_deg_regions = sch.deg_regions;
     {
         Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
         launch_parent_init(parent, nt, nullptr, 0, ctx->grid, s);
@@ -2701,7 +2710,7 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
             {
                 Scope sc(ctx, CC_K_DEGREE, s, 1);
                 launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G,
-                                    as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), sch.deg_vec, s);
+                                    as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), sch.deg_regions, s);
             }
             // the fits on a highest-priority stream, overlapping the first hook
             // pass, which launches one block per tile so that the fits' blocks

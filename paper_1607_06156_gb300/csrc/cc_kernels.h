@@ -13,7 +13,7 @@ namespace ccg {
 struct BatchSchedule {
     int unroll = 2;
     int grid_mult = 1;
-    int deg_vec = 4;  // vectors per thread and tile of the degree pass
+    int deg_regions = 1;  // regions of the pairs the degree pass works on side by side
     bool front = false;  // SV front end: per-graph sampled hook passes before the first gather pass
     const uint32_t *pair_tiles = nullptr;  // graph of every 2^kTileShift-th pair (launch_tile_graphs), required
 };
@@ -254,10 +254,10 @@ struct KsBatchOut {  // per graph
     unsigned long long *seedkey;  // (degree << 32) | (0xffffffff - local id) of the max-degree vertex
 };
 size_t ks_batch_entries();
-// next: a device counter the blocks take tiles from in order (zeroed here);
-// vec: 128-bit vectors a thread loads per tile (2, 4 or 8)
+// next: a device counter the blocks take tiles from (zeroed here); regions:
+// contiguous regions of the pairs worked on side by side, each in order
 void launch_degree_batch(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G, uint32_t *deg,
-                         DevState *st, int grid, unsigned long long *next, int vec, cudaStream_t s);
+                         DevState *st, int grid, unsigned long long *next, int regions, cudaStream_t s);
 // out[k] = the graph holding item k << kTileShift of the offsets `off` (G + 1 entries), k < (count >> kTileShift) + 1
 void launch_tile_graphs(const int64_t *off, int G, long long count, uint32_t *out, int grid, cudaStream_t s);
 // order (device, G graph numbers, largest first) and next (device counter) may

@@ -28,37 +28,45 @@ constexpr int kZTab = 128;         // zeta table entries per warp (the refinemen
 constexpr int kSmallHistKeyAt = 2 * kBB + 2;  // word of the argmax key in k_small_hist's output (8-byte aligned)
 
 // ---------------------------------------------------------------------------
-// Blocks take tiles of kBlock * V vectors (two pairs each) in increasing
-// order from `next` (a zeroed counter), so the tiles in flight stay within a
-// window of about one tile per block and the few graphs they belong to keep
-// their counters in L2 (with a fixed stride, blocks drift apart and the
-// counters of many graphs compete for it). Thread 0 fetches the next tile's
-// number and first and last graph while the block's loads of the current
-// tile are in flight (two slots in shared memory, one barrier per tile). A
-// tile inside one graph - nearly every tile, since the graphs hold thousands
-// to millions of pairs - reads that graph's base and size once; a tile
-// across graphs finds each pair's graph by stepping from its first graph.
-// Resident blocks per SM are set so that no variant spills (40, 62 and 102
-// registers for V = 2, 4, 8).
-template <int V>
-__global__ void __launch_bounds__(kBlock, V >= 8 ? 2 : V >= 4 ? 4 : 6) k_degree_batch(const int32_t *__restrict__ in, long long m,
-                                                                        const int64_t *__restrict__ eo,
-                                                                        const int64_t *__restrict__ vo, int G,
-                                                                        uint32_t *deg, DevState *st,
-                                                                        unsigned long long *next) {
+// Blocks take tiles of kBlock * kDegVec vectors (two pairs each) from `next`
+// (a zeroed counter). The pairs are cut into R contiguous regions worked on
+// side by side: fetch f takes tile f / R of region f % R. Within a region
+// the tiles go in increasing order, so the tiles in flight stay within a
+// window of a few graphs per region and their counters stay in L2 (with a
+// fixed stride, blocks drift apart and the counters of many graphs compete
+// for it). With R = 1 every SM works on the same graph at once, and the
+// increments of that graph's hubs queue on a few L2 lines: on 512 graphs
+// (R-MAT, grids, chains) the pass ran at 50% of the L2 atomic rate, its
+// blocks stalled on their loads and their barrier whatever their vectors
+// per thread (2, 4 or 8 measured 4.25-4.31 ms); with R = 8 it took 2.91 ms.
+// Thread 0 fetches the next tile's number and first and last graph while
+// the block's loads of the current tile are in flight (two slots in shared
+// memory, one barrier per tile). A tile inside one graph - nearly every
+// tile, since the graphs hold thousands to millions of pairs - reads that
+// graph's base and size once; a tile across graphs finds each pair's graph
+// by stepping from its first graph.
+constexpr int kDegVec = 2;
+__global__ void __launch_bounds__(kBlock, 6) k_degree_batch(const int32_t *__restrict__ in, long long m,
+                                                            const int64_t *__restrict__ eo,
+                                                            const int64_t *__restrict__ vo, int G, uint32_t *deg,
+                                                            DevState *st, unsigned long long *next, int regions) {
+    constexpr int V = kDegVec;
     __shared__ long long s_t[2];
     __shared__ int s_g0[2], s_g1[2];
     constexpr long long kTile = (long long)kBlock * V;
     const long long nvec = m >> 1;
     const long long ntiles = (nvec + kTile - 1) / kTile;
+    const long long per = (ntiles + regions - 1) / regions;  // tiles per region
+    const long long nfetch = per * regions;
     const int4 *ev = reinterpret_cast<const int4 *>(in);
-    auto fetch = [&](int b) {  // thread 0
-        const long long t = (long long)atomicAdd(next, 1ull);
+    auto fetch = [&](int b) {  // thread 0; s_t: the tile, ntiles to skip a fetch past the last tile, -1 when done
+        const long long f = (long long)atomicAdd(next, 1ull);
+        long long t = f >= nfetch ? -1 : (f % regions) * per + f / regions;
+        if (t >= ntiles) t = ntiles;
         s_t[b] = t;
-        if (t < ntiles) {
+        if (t >= 0 && t < ntiles) {
             const long long last = ((t + 1) * kTile < nvec ? (t + 1) * kTile : nvec) * 2 - 1;
-            const int g0 = graph_search(eo, G, t * kTile * 2);
-            s_g0[b] = g0;
+            s_g0[b] = graph_search(eo, G, t * kTile * 2);
             s_g1[b] = graph_search(eo, G, last);
         }
     };
@@ -67,7 +75,12 @@ __global__ void __launch_bounds__(kBlock, V >= 8 ? 2 : V >= 4 ? 4 : 6) k_degree_
     bool bad = false;
     for (int b = 0;; b ^= 1) {
         const long long t = s_t[b];
-        if (t >= ntiles) break;
+        if (t < 0) break;
+        if (t >= ntiles) {  // a fetch past the end of the last region: nothing to count
+            if (threadIdx.x == 0) fetch(b ^ 1);
+            __syncthreads();
+            continue;
+        }
         const int g0 = s_g0[b], g1 = s_g1[b];
         int4 q[V];
 #pragma unroll
@@ -536,11 +549,11 @@ void launch_fit_one(const uint32_t *deg, long long n, int64_t *vo, KsBatchScratc
 
 // ---------------------------------------------------------------------------
 void launch_degree_batch(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G, uint32_t *deg,
-                         DevState *st, int grid, unsigned long long *next, int vec, cudaStream_t s) {
+                         DevState *st, int grid, unsigned long long *next, int regions, cudaStream_t s) {
     if (m <= 0) return;
     cudaMemsetAsync(next, 0, sizeof(unsigned long long), s);
-    auto kf = vec >= 8 ? k_degree_batch<8> : vec >= 4 ? k_degree_batch<4> : k_degree_batch<2>;
-    kf<<<fit_grid((const void *)kf, grid, kBlock), kBlock, 0, s>>>(in, m, eo, vo, G, deg, st, next);
+    k_degree_batch<<<fit_grid((const void *)k_degree_batch, grid, kBlock), kBlock, 0, s>>>(
+        in, m, eo, vo, G, deg, st, next, regions > 0 ? regions : 1);
 }
 
 __global__ void __launch_bounds__(kBlock) k_tile_graphs(const int64_t *__restrict__ off, int G, long long ntiles,

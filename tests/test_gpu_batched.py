@@ -41,6 +41,8 @@ def test_mixed_batch_matches_oracle_per_graph():
     got, st = _run_batched(torch, b.edges, b.edge_offsets, b.vertex_offsets)
     _check_each(b, got)
     assert st["sv_iters"] >= 2
+    # the schedule the call used (the default below the tuner's size)
+    assert (st["batch_unroll"], st["batch_grid_mult"], st["batch_deg_regions"]) == (2, 1, 1)
 
 
 @pytest.mark.parametrize("stride,route,profile", [(8, "auto", 0), (0, "auto", 0), (8, "sv", 0), (8, "auto", 1),
