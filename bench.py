@@ -633,7 +633,8 @@ def batch_record(args, dev, stream, world: int = 1, rank: int = 0, dist=None, wo
                                 "note": "route prediction skipped (CC_ROUTE_FORCE_SV)"},
             "route_policy": "auto (a K-S fit per graph)", "graphs_routed_bfs": st["route"],
             "schedule": {"unroll": st["batch_unroll"], "grid_mult": st["batch_grid_mult"],
-                         "degree_regions": st["batch_deg_regions"], "sv_front_end": st["sv_sample_stride"] == -1},
+                         "degree_regions": st["batch_deg_regions"], "hook_regions": st["batch_sv_regions"],
+                         "sv_front_end": st["sv_sample_stride"] == -1},
             "roofline": roofline_of(kms, kla, st, 4, args.steps, workload) | {"kernel": dom},
             "kernels": kernel_table(kms, kla, st, 4, args.steps), "sv_iters": st["sv_iters"],
             "m_active": st["m_active"], "labels_vs_oracle": same, "graphs_checked": checked, "cpu_baseline": cpu}

@@ -108,6 +108,10 @@ typedef struct {
                                active list and each tree's vertices take its smallest vertex as
                                parent before SV. Used by the K-S heuristic and forced routes (the
                                learned route keeps one sampled start); the labels are the same */
+    int batch_hook_regions; /* batched form, tile order of the hook passes over the pairs: 0 = the tuner's
+                               choice (default), -1 = a grid stride, k > 0 = k contiguous regions of the
+                               pairs worked on side by side, each in order */
+    int reserved;
 } cc_options;
 
 /* Kernel classes reported in cc_stats.kernel_ms / kernel_launches. */
@@ -169,7 +173,8 @@ typedef struct {
                                            -1 = batched form, each graph with its own stride) */
     int32_t batch_deg_regions;          /* batched form: tuned regions of the pairs the degree pass works on side by side */
     int32_t bfs_starts;                 /* BFS trees started (0 if the BFS did not run) */
-    int32_t pad3;
+    int32_t batch_sv_regions;           /* batched form: tuned tile order of the hook passes (0 = grid stride,
+                                           else regions of the pairs worked on side by side) */
 } cc_stats;
 
 /* Fills *opt with the defaults listed above. */

@@ -46,10 +46,11 @@ class Options(ctypes.Structure):
         ("bfs_cutoff_levels", ctypes.c_int), ("debug_checks", ctypes.c_int), ("fault_inject", ctypes.c_int),
         ("ks_min_span", ctypes.c_double), ("profile", ctypes.c_int), ("bfs_mode", ctypes.c_int),
         ("sv_sample_stride", ctypes.c_int), ("bfs_starts", ctypes.c_int),
+        ("batch_hook_regions", ctypes.c_int), ("reserved", ctypes.c_int),
     ]
 
 
-_OPTION_FIELDS = frozenset(f for f, _ in Options._fields_)
+_OPTION_FIELDS = frozenset(f for f, _ in Options._fields_ if f != "reserved")
 
 
 class Stats(ctypes.Structure):
@@ -71,7 +72,7 @@ class Stats(ctypes.Structure):
         ("batch_unroll", ctypes.c_int32),
         ("batch_grid_mult", ctypes.c_int32),
         ("sv_sample_stride", ctypes.c_int32), ("batch_deg_regions", ctypes.c_int32),
-        ("bfs_starts", ctypes.c_int32), ("pad3", ctypes.c_int32),
+        ("bfs_starts", ctypes.c_int32), ("batch_sv_regions", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

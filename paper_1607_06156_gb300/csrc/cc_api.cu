@@ -33,6 +33,7 @@ constexpr size_t kCtrSmallFitVo = 256;  // vertex offsets {0, n} of the one-grap
 constexpr size_t kCtrKsQueue = 1024;    // next graph of the batched fits (int)
 constexpr size_t kCtrTileQueue = 1088;  // next tile of the batched degree pass (64-bit)
 constexpr size_t kCtrCsrQueue = 1096;   // next tile of the CSR placement (64-bit)
+constexpr size_t kCtrSvQueue = 1104;    // next tile of a batched hook pass in region order (64-bit)
 constexpr size_t kCountersBytes = 4096;
 template <typename P> P *counter_at(Buf &b, size_t off) { return reinterpret_cast<P *>(static_cast<char *>(b.p) + off); }
 
@@ -103,7 +104,7 @@ struct cc_ctx {
         int sample_stride = 1;          // SV front end stride
         bool edge_bfs = false;          // the BFS branch is the edge-list BFS
         bool batched = false;           // the batched form (route = graphs that took the BFS step)
-        int batch_unroll = 0, batch_grid_mult = 0, batch_deg_regions = 0;  // the batched form's tuned schedule
+        int batch_unroll = 0, batch_grid_mult = 0, batch_deg_regions = 0, batch_sv_regions = 0;  // its schedule
     } g_route;
     RouteGraph g_capture;               // the same facts for a call captured into the caller's graph
     const RouteGraph *rg_last = nullptr; // the facts of the last graph-mode call
@@ -293,6 +294,7 @@ cc_status check_options(const cc_options *o) {
     if (o->bfs_mode < 0 || o->bfs_mode > 1) return CC_ERR_INVALID_ARG;
     if (o->sv_sample_stride < 0 || o->sv_sample_stride > 1024) return CC_ERR_INVALID_ARG;
     if (o->bfs_starts < 0 || o->bfs_starts > kMaxBfsStarts) return CC_ERR_INVALID_ARG;
+    if (o->batch_hook_regions < -1 || o->batch_hook_regions > 1024) return CC_ERR_INVALID_ARG;
     return CC_OK;
 }
 
@@ -1614,6 +1616,7 @@ void stats_from_device(cc_ctx *ctx) {
         S.batch_unroll = rg.batch_unroll;
         S.batch_grid_mult = rg.batch_grid_mult;
         S.batch_deg_regions = rg.batch_deg_regions;
+        S.batch_sv_regions = rg.batch_sv_regions;
         S.route_source = ctx->opt.route_policy == CC_ROUTE_AUTO || ctx->opt.route_policy == CC_ROUTE_LEARNED ? 0 : 2;
         S.bfs_levels = h->route_taken ? h->bfs_level : 0;
         S.m_active[0] = S.m;
@@ -1878,10 +1881,19 @@ int ilog2_ceil(long long x) {
     return l;
 }
 
+// options.batch_hook_regions overrides the tuned tile order of the hook passes
+void hook_order(cc_ctx *ctx, BatchSchedule *sch) {
+    const int k = ctx->opt.batch_hook_regions;
+    if (k == 0) return;
+    sch->sv_regions = k > 0 ? k : 0;
+    sch->queue = counter_at<unsigned long long>(ctx->counters, kCtrSvQueue);
+}
+
 cc_status tune_batch(cc_ctx *ctx, const int32_t *edges, long long m, const int64_t *eo, const int64_t *vo, int G,
                      vid_t nt, cudaStream_t s, BatchSchedule *out) {
     *out = BatchSchedule();
     out->pair_tiles = as<uint32_t>(ctx->tile_pairs);
+    out->queue = counter_at<unsigned long long>(ctx->counters, kCtrSvQueue);
     if (m < (1LL << 24)) return CC_OK;
     const int key = (ilog2_ceil(m) << 8) | ilog2_ceil(G);
     for (const auto &e : ctx->batch_tuned)
@@ -1889,17 +1901,36 @@ cc_status tune_batch(cc_ctx *ctx, const int32_t *edges, long long m, const int64
             *out = e.second;
             return CC_OK;
         }
-    BatchSchedule cand[] = {{1, 1}, {2, 1}, {4, 1}, {1, 2}, {2, 2}, {4, 2}};
-    for (BatchSchedule &c : cand) c.pair_tiles = as<uint32_t>(ctx->tile_pairs);
+    // (unroll, grid multiple, regions): grid-stride schedules, and tiles in
+    // region order from a counter (the grid multiple does not apply there)
+    const int cand_spec[][3] = {{1, 1, 0}, {2, 1, 0}, {4, 1, 0}, {1, 2, 0}, {2, 2, 0},
+                                {4, 2, 0}, {2, 1, 8}, {2, 1, 32}, {4, 1, 8}};
+    std::vector<BatchSchedule> cand;
+    for (const auto &c : cand_spec) {
+        BatchSchedule b;
+        b.unroll = c[0];
+        b.grid_mult = c[1];
+        b.sv_regions = c[2];
+        b.queue = counter_at<unsigned long long>(ctx->counters, kCtrSvQueue);
+        b.pair_tiles = as<uint32_t>(ctx->tile_pairs);
+        cand.push_back(b);
+    }
     DevState *st = as<DevState>(ctx->st);
     vid_t *parent = as<vid_t>(ctx->parent), *hooked = as<vid_t>(ctx->hooked);
+    uint2 *eb0 = as<uint2>(ctx->ebuf0);
     cudaEvent_t a = pool_event(ctx), b = pool_event(ctx);
     if (!a || !b) return CC_OK;
     float best = 1e30f;
+    // each candidate runs the first two passes of the route (idempotent after
+    // a reset of the parents and the device state): the hook pass over all
+    // pairs, the full shortcut and the gather pass that writes the survivors
     for (const BatchSchedule &c : cand) {
         launch_parent_init(parent, nt, nullptr, 0, ctx->grid, s);
+        CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
         CU_TRY(cudaEventRecord(a, s));
         launch_sv_pass_batch(0, edges, m, eo, vo, G, nt, parent, hooked, nullptr, st, 0, ctx->grid, s, c);
+        launch_shortcut_all(parent, nt, st, 0, ctx->grid, s);
+        launch_sv_pass_batch(2, edges, m, eo, vo, G, nt, parent, hooked, eb0, st, 1, ctx->grid, s, c);
         CU_TRY(cudaEventRecord(b, s));
         CU_TRY(cudaEventSynchronize(b));
         float ms = 0.f;
@@ -1928,6 +1959,7 @@ cc_status tune_batch(cc_ctx *ctx, const int32_t *edges, long long m, const int64
             }
         }
     }
+    CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
     ctx->batch_tuned.push_back({key, *out});
     return CC_OK;
 }
@@ -2124,6 +2156,7 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
     rg.batch_unroll = sch.unroll;
     rg.batch_grid_mult = sch.grid_mult;
     rg.batch_deg_regions = sch.deg_regions;
+    rg.batch_sv_regions = sch.sv_regions;
     CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), cs));
     enqueue_batch_tables(ctx, eo_u, vo_u, G, m, n, cs);
     launch_parent_init(parent, nt, nullptr, 0, ctx->grid, cs);
@@ -2256,9 +2289,11 @@ cc_status labels_batched_graph(cc_ctx *ctx, const int32_t *edges, const int64_t 
             if (e.first == key) sch = e.second;
     }
     sch.front = batch_front(ctx, m);
+    hook_order(ctx, &sch);
     S.batch_unroll = sch.unroll;
     S.batch_grid_mult = sch.grid_mult;
     S.batch_deg_regions = sch.deg_regions;
+    S.batch_sv_regions = sch.sv_regions;
     S.sv_sample_stride = sch.front ? -1 : 1;
     if (user_capture) {
         ctx->capturing = true;
@@ -2268,7 +2303,7 @@ cc_status labels_batched_graph(cc_ctx *ctx, const int32_t *edges, const int64_t 
         return r;
     }
     std::vector<unsigned char> key = route_key(ctx, 4, n, m, edges, labels, cap);
-    const long long extra[] = {G, sch.unroll, sch.grid_mult, sch.deg_regions, sch.front,
+    const long long extra[] = {G, sch.unroll, sch.grid_mult, sch.deg_regions, sch.sv_regions, sch.front,
                                (long long)(uintptr_t)eo_u, (long long)(uintptr_t)vo_u,
                                (long long)(uintptr_t)ctx->bo_e.p, (long long)(uintptr_t)ctx->kb_route.p,
                                (long long)(uintptr_t)ctx->tile_pairs.p, (long long)(uintptr_t)ctx->kb_cub.p};
@@ -2686,10 +2721,12 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
     BatchSchedule sch;
     CC_TRY(tune_batch(ctx, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, s, &sch));
     sch.front = batch_front(ctx, m);
+    hook_order(ctx, &sch);
     S.sv_sample_stride = sch.front ? -1 : 1;
     S.batch_unroll = sch.unroll;
     S.batch_grid_mult = sch.grid_mult;
     S.batch_deg_regions = sch.deg_regions;
+    S.batch_sv_regions = sch.sv_regions;
     {
         Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
         launch_parent_init(parent, nt, nullptr, 0, ctx->grid, s);
@@ -2772,9 +2809,10 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
             launch_finalize_batch(parent, nt, vertex_offsets_dev, G, (int32_t *)labels_out_dev, ctx->grid, cs, vtiles);
         };
         const cc_ctx::GraphKey key =
-            graph_key(ctx, 2 | (predict ? 4 : 0) | (sch.front ? 8 : 0) | (sch.unroll << 8) | (sch.grid_mult << 12), n,
-                      m, G, edges_dev,
-                      edge_offsets_dev, vertex_offsets_dev, labels_out_dev, cap);
+            graph_key(ctx,
+                      2 | (predict ? 4 : 0) | (sch.front ? 8 : 0) | (sch.unroll << 8) | (sch.grid_mult << 12) |
+                          (sch.sv_regions << 16),
+                      n, m, G, edges_dev, edge_offsets_dev, vertex_offsets_dev, labels_out_dev, cap);
         cc_status gs = launch_sv_graph(ctx, ctx->g_batch, key, nt, 1, 0, cap, pre, post, s);
         if (gs == CC_OK) {
             rec(ctx, EV_SV, s);

@@ -14,6 +14,8 @@ struct BatchSchedule {
     int unroll = 2;
     int grid_mult = 1;
     int deg_regions = 1;  // regions of the pairs the degree pass works on side by side
+    int sv_regions = 0;   // the hook passes: 0 = grid stride, else regions of the pairs side by side
+    unsigned long long *queue = nullptr;  // the hook passes' tile counter (with sv_regions > 0)
     bool front = false;  // SV front end: per-graph sampled hook passes before the first gather pass
     const uint32_t *pair_tiles = nullptr;  // graph of every 2^kTileShift-th pair (launch_tile_graphs), required
 };

@@ -374,14 +374,18 @@ __device__ __forceinline__ bool batch_take_tile(long long t, long long k0, const
     return (t & (k - 1)) == 0;
 }
 
-// U: 16-byte vectors (two pairs each) per thread per tile, the schedule the
+// U: 16-byte vectors (two pairs each) per thread per tile, and the tile
+// order: a grid stride (regions = 0), or tiles from `next` (a zeroed counter)
+// over `regions` contiguous regions of the pairs worked on side by side
+// (fetch f takes tile f / regions of region f % regions) - the schedule the
 // batched form's tuner picks.
 template <int MODE, bool WRITE, bool RECORD, int U, int FILTER = 0>
 __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restrict__ in, long long m,
                                                           const int64_t *__restrict__ eo,
                                                           const int64_t *__restrict__ vo, int G, vid_t ntot,
                                                           vid_t *parent, vid_t *hooked_list, uint2 *__restrict__ out,
-                                                          DevState *st, int it, const uint32_t *__restrict__ tg) {
+                                                          DevState *st, int it, const uint32_t *__restrict__ tg,
+                                                          int regions, unsigned long long *next) {
     constexpr int K = 2 * U;
     __shared__ int sw[32];
     __shared__ unsigned long long sbase;
@@ -392,7 +396,26 @@ __global__ void __launch_bounds__(kBlock) k_sv_pass_batch(const int32_t *__restr
     bool bad = false;
     const long long tile = (long long)kBlock * U;
     const long long ntiles = (nvec + tile - 1) / tile;
-    for (long long t = blockIdx.x; t < ntiles + ((m & 1) ? 1 : 0); t += gridDim.x) {
+    const long long nt_all = ntiles + ((m & 1) ? 1 : 0);  // the odd last pair is a tile of its own
+    const long long per = regions > 0 ? (nt_all + regions - 1) / regions : 0;
+    const long long nfetch = per * regions;
+    __shared__ long long s_f;
+    long long slot = blockIdx.x;
+    for (;;) {
+        long long t;
+        if (regions > 0) {
+            __syncthreads();  // every thread has read the previous fetch
+            if (threadIdx.x == 0) s_f = (long long)atomicAdd(next, 1ull);
+            __syncthreads();
+            const long long f = s_f;
+            if (f >= nfetch) break;
+            t = (f % regions) * per + f / regions;
+            if (t >= nt_all) continue;  // past the end of the last region
+        } else {
+            t = slot;
+            slot += gridDim.x;
+            if (t >= nt_all) break;
+        }
         const long long k0 = t < ntiles ? t * tile * 2 : m - 1;  // first pair of the tile
         const int g0 = (int)tg[k0 >> kTileShift];  // a graph at or before the tile's first pair
         if (!batch_take_tile<FILTER>(t, k0, eo, vo, G, g0)) continue;  // the same for the whole block
@@ -477,13 +500,17 @@ __global__ void __launch_bounds__(kBlock) k_finalize_batch(vid_t *parent, vid_t 
 template <int U>
 void launch_sv_pass_batch_u(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
                             vid_t ntot, vid_t *parent, vid_t *hooked_list, uint2 *out, DevState *st, int it, int grid,
-                            cudaStream_t s, int grid_mult, const uint32_t *sch_tg) {
+                            cudaStream_t s, int grid_mult, const uint32_t *sch_tg, int regions,
+                            unsigned long long *next) {
     auto kf = mode == 0   ? k_sv_pass_batch<0, false, false, U>
               : mode == 5 ? k_sv_pass_batch<0, false, false, U, 1>   // front end, first pass
               : mode == 6 ? k_sv_pass_batch<2, false, false, U, 2>   // front end, second pass
                           : k_sv_pass_batch<2, true, true, U>;
-    const long long g = fit_grid((const void *)kf, grid, kBlock) * (grid_mult > 0 ? grid_mult : 1);
-    kf<<<(unsigned)g, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, sch_tg);
+    const bool ordered = regions > 0 && next;
+    const long long g = fit_grid((const void *)kf, grid, kBlock) * (!ordered && grid_mult > 0 ? grid_mult : 1);
+    if (ordered) cudaMemsetAsync(next, 0, sizeof(unsigned long long), s);
+    kf<<<(unsigned)g, kBlock, 0, s>>>(in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, sch_tg,
+                                      ordered ? regions : 0, next);
 }
 
 void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G,
@@ -493,13 +520,13 @@ void launch_sv_pass_batch(int mode, const int32_t *in, long long m, const int64_
     const uint32_t *sch_tg = sch.pair_tiles;
     if (sch.unroll == 1)
         launch_sv_pass_batch_u<1>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s,
-                                  sch.grid_mult, sch_tg);
+                                  sch.grid_mult, sch_tg, sch.sv_regions, sch.queue);
     else if (sch.unroll == 4)
         launch_sv_pass_batch_u<4>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s,
-                                  sch.grid_mult, sch_tg);
+                                  sch.grid_mult, sch_tg, sch.sv_regions, sch.queue);
     else
         launch_sv_pass_batch_u<2>(mode, in, m, eo, vo, G, ntot, parent, hooked_list, out, st, it, grid, s,
-                                  sch.grid_mult, sch_tg);
+                                  sch.grid_mult, sch_tg, sch.sv_regions, sch.queue);
 }
 
 void launch_finalize_batch(vid_t *parent, vid_t ntot, const int64_t *vo, int G, int32_t *labels, int grid,

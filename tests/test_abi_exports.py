@@ -200,4 +200,4 @@ def test_unknown_option_names_are_refused():
     cc._set_options(o, {"profile": 1, "sv_sample_stride": 8})
     assert o.profile == 1 and o.sv_sample_stride == 8
     with pytest.raises(TypeError):
-        cc._set_options(o, {"pad3": 0})
+        cc._set_options(o, {"reserved": 0})

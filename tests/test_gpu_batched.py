@@ -65,6 +65,25 @@ def test_front_end_per_graph(stride, route, profile):
         assert st["m_active"][2] < off["m_active"][2] // 2, (st["m_active"], off["m_active"])
 
 
+@pytest.mark.parametrize("regions,profile", [(-1, 0), (1, 0), (8, 0), (32, 0), (8, 1), (1000, 0)])
+def test_hook_passes_in_region_order(regions, profile):
+    """The batched hook passes with their tiles taken from a counter over
+    contiguous regions of the pairs (the tuner's other tile order): every
+    tile exactly once, the odd last pair included, whatever the number of
+    regions (more regions than tiles leave fetches with nothing to do)."""
+    torch = torch_cuda()
+    b = gg.batch(seed=6, G=40, nmin=500, nmax=80000)
+    edges, eo, vo = b.edges, b.edge_offsets, b.vertex_offsets
+    if eo[-1] % 2 == 0:  # an odd number of pairs: drop the last pair of the last graph
+        edges, eo = edges[:-1], eo.copy()
+        eo[-1] -= 1
+    got, st = _run_batched(torch, edges, eo, vo, batch_hook_regions=regions, profile=profile)
+    for g in range(b.G):
+        want = oracle.cc_labels(np.ascontiguousarray(edges[eo[g]:eo[g + 1]]), int(vo[g + 1] - vo[g]))
+        assert np.array_equal(got[vo[g]:vo[g + 1]], want), g
+    assert st["batch_sv_regions"] == max(regions, 0)
+
+
 def test_batched_equals_per_graph_loop():
     torch = torch_cuda()
     import paper_1607_06156_gb300 as cc
