@@ -136,47 +136,99 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_csr_partition(const T *__re
 // col[cursor[x]++] = y for every entry, in the order of the partitioned
 // array: tiles of kPlaceTile entries taken from `next` (a zeroed counter) in
 // increasing order, the next tile fetched while the current one is placed.
-// The lanes of a warp that hit one vertex take their slots with a single
-// atomic (__match_any_sync); without the match (only in the vertex blocks
-// far above the average size) the placement of a Chung-Lu 2^24 graph took
-// 4.89 ms instead of 3.5: its many vertices of degree in the thousands
-// collide within warps in every vertex block. Placing 16 regions of the
-// array side by side, to spread the atomics over more cursor lines, measured
-// the same (3.43 ms) with 1.4x the DRAM traffic.
-constexpr int kPlaceVec = 4;  // entries per thread per tile
-constexpr long long kPlaceTile = (long long)kBlock * kPlaceVec;
+// The entries of a tile that fall in the vertex block of its first entry
+// (all but the few tiles that straddle two blocks) are counted per vertex in
+// shared memory (a dense array over the block's 2^15 vertices): each entry
+// gets its rank among the tile's entries of its vertex, the first entry of
+// each vertex appends the vertex to a list, and one global atomic per
+// listed vertex reserves its slots. Measured on R-MAT scale 22, a tile of
+// 8,192 entries holds 0.31 distinct vertices per entry (a warp of 32: 0.94),
+// Chung-Lu 0.7 (0.98). The other entries take their slots with one atomic
+// per vertex and warp (__match_any_sync).
+constexpr int kPlaceThreads = 1024;
+constexpr int kPlaceVec = 8;  // entries per thread per tile
+constexpr long long kPlaceTile = (long long)kPlaceThreads * kPlaceVec;
+// per vertex of the tile's block: the count, then the reserved base; the list of the tile's vertices
+constexpr size_t kPlaceSmem = (size_t)kBucketSize * sizeof(uint32_t) + (size_t)kPlaceTile * sizeof(uint32_t);
 
-__global__ void __launch_bounds__(kBlock) k_csr_place(const unsigned long long *__restrict__ entries,
-                                                      unsigned long long total, uint32_t *cursor, vid_t *col,
-                                                      unsigned long long *next) {
+__global__ void __launch_bounds__(kPlaceThreads, 1) k_csr_place(const unsigned long long *__restrict__ entries,
+                                                                unsigned long long total, uint32_t *cursor,
+                                                                vid_t *col, unsigned long long *next) {
+    extern __shared__ uint32_t place_smem[];
+    uint32_t *cnt = place_smem, *touched = place_smem + kBucketSize;
     __shared__ unsigned long long s_t[2];
+    __shared__ uint32_t s_blk[2];
+    __shared__ uint32_t s_nt;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const unsigned long long ntiles = (total + kPlaceTile - 1) / kPlaceTile;
-    if (threadIdx.x == 0) s_t[0] = atomicAdd(next, 1ull);
+    for (int i = threadIdx.x; i < kBucketSize; i += kPlaceThreads) cnt[i] = 0u;
+    if (threadIdx.x == 0) s_nt = 0u;
+    auto fetch = [&](int b) {  // thread 0: the tile and its first entry's vertex block
+        const unsigned long long t = atomicAdd(next, 1ull);
+        s_t[b] = t;
+        if (t < ntiles) s_blk[b] = (uint32_t)(entries[t * kPlaceTile] >> 32) >> kBucketBits;
+    };
+    if (threadIdx.x == 0) fetch(0);
     __syncthreads();
     for (int b = 0;; b ^= 1) {
         const unsigned long long t = s_t[b];
         if (t >= ntiles) break;
+        const uint32_t blk = s_blk[b], v0 = blk << kBucketBits;
         unsigned long long ent[kPlaceVec];
+        uint32_t rank[kPlaceVec];
 #pragma unroll
         for (int r = 0; r < kPlaceVec; r++) {
-            const unsigned long long i = t * kPlaceTile + (unsigned long long)r * kBlock + threadIdx.x;
+            const unsigned long long i = t * kPlaceTile + (unsigned long long)r * kPlaceThreads + threadIdx.x;
             ent[r] = i < total ? __ldcs(entries + i) : ~0ull;
         }
-        if (threadIdx.x == 0) s_t[b ^ 1] = atomicAdd(next, 1ull);
+        if (threadIdx.x == 0) fetch(b ^ 1);
+        // entries of the tile's block: ranks among the tile's entries of their vertex; the
+        // first entry of each vertex lists it (one list append per warp)
 #pragma unroll
         for (int r = 0; r < kPlaceVec; r++) {
-            const bool ok = ent[r] != ~0ull;
             const uint32_t x = (uint32_t)(ent[r] >> 32);
-            const unsigned peers = __match_any_sync(0xffffffffu, ok ? x : 0xffffffffu);
+            const bool mine = ent[r] != ~0ull && (x >> kBucketBits) == blk;
+            rank[r] = mine ? atomicAdd(&cnt[x - v0], 1u) : 1u;
+            const unsigned first = __ballot_sync(0xffffffffu, rank[r] == 0u);
+            if (first) {
+                uint32_t at = 0;
+                if (lane == 0) at = atomicAdd(&s_nt, (uint32_t)__popc(first));
+                at = __shfl_sync(0xffffffffu, at, 0);
+                if (rank[r] == 0u) touched[at + __popc(first & lt)] = x - v0;
+            }
+        }
+        // the other entries (a tile that straddles two blocks): one atomic per vertex and warp
+#pragma unroll
+        for (int r = 0; r < kPlaceVec; r++) {
+            const uint32_t x = (uint32_t)(ent[r] >> 32);
+            const bool other = ent[r] != ~0ull && (x >> kBucketBits) != blk;
+            if (!__any_sync(0xffffffffu, other)) continue;
+            const unsigned peers = __match_any_sync(0xffffffffu, other ? x : 0xffffffffu);
             const int leader = __ffs(peers) - 1;
             uint32_t base = 0;
-            if (ok && lane == leader) base = atomicAdd(&cursor[x], (uint32_t)__popc(peers));
+            if (other && lane == leader) base = atomicAdd(&cursor[x], (uint32_t)__popc(peers));
             base = __shfl_sync(0xffffffffu, base, leader);
-            if (ok) col[base + __popc(peers & lt)] = (vid_t)(ent[r] & 0xffffffffull);
+            if (other) col[base + __popc(peers & lt)] = (vid_t)(ent[r] & 0xffffffffull);
         }
-        __syncthreads();  // the slot read above is rewritten by the fetch after next
+        __syncthreads();
+        // one reservation per listed vertex; its count becomes its base
+        const uint32_t nt = s_nt;
+        for (uint32_t i = threadIdx.x; i < nt; i += kPlaceThreads) {
+            const uint32_t lx = touched[i];
+            cnt[lx] = atomicAdd(&cursor[v0 + lx], cnt[lx]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kPlaceVec; r++) {
+            const uint32_t x = (uint32_t)(ent[r] >> 32);
+            if (ent[r] != ~0ull && (x >> kBucketBits) == blk)
+                col[cnt[x - v0] + rank[r]] = (vid_t)(ent[r] & 0xffffffffull);
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nt; i += kPlaceThreads) cnt[touched[i]] = 0u;
+        if (threadIdx.x == 0) s_nt = 0u;
+        __syncthreads();  // the reset before the next tile's counts
     }
 }
 
@@ -194,8 +246,8 @@ void launch_csr_bucketed(const void *edges, long long m, vid_t n, const uint32_t
     auto kp = k_csr_partition<T>;
     kp<<<fit_grid((const void *)kp, grid, kPartThreads, kCsrPartSmem), kPartThreads, kCsrPartSmem, s>>>(
         (const T *)edges, m, n, nb, row_ptr, bs.fill, entries, st);
-    k_csr_place<<<fit_grid((const void *)k_csr_place, grid, kBlock), kBlock, 0, s>>>(
-        entries, 2ull * (unsigned long long)m, cursor, col, bs.queue);
+    k_csr_place<<<fit_grid((const void *)k_csr_place, grid, kPlaceThreads, kPlaceSmem), kPlaceThreads, kPlaceSmem,
+                  s>>>(entries, 2ull * (unsigned long long)m, cursor, col, bs.queue);
 }
 template void launch_csr_bucketed<int32_t>(const void *, long long, vid_t, const uint32_t *, uint32_t *, vid_t *,
                                            BucketScratch, unsigned long long *, DevState *, int, cudaStream_t);
@@ -205,6 +257,8 @@ template void launch_csr_bucketed<int64_t>(const void *, long long, vid_t, const
 cudaError_t csr_kernels_setup() {
     cudaError_t e = cudaFuncSetAttribute(k_csr_partition<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kCsrPartSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_csr_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPlaceSmem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_csr_partition<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kCsrPartSmem);
