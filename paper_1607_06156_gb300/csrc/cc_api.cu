@@ -219,7 +219,7 @@ cc_status ensure_sv(cc_ctx *ctx, size_t n, size_t m) {
     CC_TRY(buf_reserve(ctx, ctx->counters, kCountersBytes));
     CC_TRY(buf_reserve(ctx, ctx->bk_off, (size_t)(bucket_max() + 2) * 8));
     if (degree_part_ok((vid_t)(N < 0xffffffffULL ? N : 0xfffffffeULL), (long long)M))
-        CC_TRY(buf_reserve(ctx, ctx->dpart, degree_part_scratch_bytes((vid_t)N, (long long)M)));
+        CC_TRY(buf_reserve(ctx, ctx->dpart, degree_part_scratch_bytes((vid_t)N, (long long)M, true)));
     ctx->n_cap = N;
     ctx->m_cap = M;
     return CC_OK;
@@ -532,7 +532,10 @@ float ev_ms(cc_ctx *ctx, Ev a, Ev b) {
 
 // Degree pass + histogram (Algorithm 2 line 1).
 template <typename T>
-void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s, bool counted = false) {
+// hook: the parent array, every vertex its own root, when the windowed pass
+// is to apply the first SV hook pass too (fused_hooks); null otherwise.
+void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s, bool counted = false,
+                    vid_t *hook = nullptr) {
     if (counted) {  // the pairs were counted as they arrived (cc_labels_host): histogram only
         Scope sc(ctx, CC_K_HIST, s, 1);
         launch_hist(as<uint32_t>(ctx->deg), n, as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap,
@@ -540,9 +543,9 @@ void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaSt
         return;
     }
     cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s);
-    if (degree_part_ok(n, m) && ctx->dpart.bytes >= degree_part_scratch_bytes(n, m)) {
+    if (degree_part_ok(n, m) && ctx->dpart.bytes >= degree_part_scratch_bytes(n, m, hook != nullptr)) {
         Scope sc(ctx, CC_K_DEGREE, s, 1 + degree_part_buckets(n));
-        launch_degree_partitioned<T>(edges, m, n, as<uint32_t>(ctx->deg), ctx->dpart.p, as<DevState>(ctx->st),
+        launch_degree_partitioned<T>(edges, m, n, as<uint32_t>(ctx->deg), hook, ctx->dpart.p, as<DevState>(ctx->st),
                                      ctx->num_sms, ctx->grid, s);
     } else if (degree_uses_hubs(m) && ctx->ebuf1.bytes >= degree_hubs_scratch_bytes()) {
         cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
@@ -934,6 +937,15 @@ int sample_stride(const cc_ctx *ctx, vid_t n, long long m) {
 // 94.2 ms a call against 86.8.
 bool batch_front(const cc_ctx *ctx, long long m) { return ctx->opt.sv_sample_stride > 1 && m > 0; }
 
+// The first hook pass over all pairs rides on the windowed degree pass (its
+// window pass applies atomicMin(parent[max], min) while the window's parents
+// are in L2) when that pass runs (n > 2^25) and the SV front end does not
+// (the sample passes come before any pass over all pairs).
+bool fused_hooks(const cc_ctx *ctx, vid_t n, long long m) {
+    return degree_part_ok(n, m) && sample_stride(ctx, n, m) == 1 &&
+           ctx->dpart.bytes >= degree_part_scratch_bytes(n, m, true);
+}
+
 // The first SV pass on stream s while every vertex is its own root; after it
 // every vertex points at its root. With a sample stride k > 1: the front end
 // (a hook pass with identity parents and a one-hop hook pass over the sample,
@@ -1031,17 +1043,26 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
                     : ctx->opt.max_iters > 0                  ? ctx->opt.max_iters
                                                               : default_max_iters(n);
     bool deep_done = false;  // the side stream also ran SV iteration 1
+    // the first hook pass inside the windowed degree pass (parent init first), as on the graph route
+    const bool fused = !pre && policy != CC_ROUTE_FORCE_SV && policy != CC_ROUTE_FORCE_BFS &&
+                       !(policy == CC_ROUTE_LEARNED && ctx->have_pred) && m > 0 && fused_hooks(ctx, n, m);
     auto speculate = [&]() -> cc_status {
         if (spec.armed || m <= 0) return CC_OK;
         CC_TRY(ensure_side(ctx));
         cudaStream_t side = ctx->side_s;
         CU_TRY(cudaEventRecord(ctx->ev_fork, s));
         CU_TRY(cudaStreamWaitEvent(side, ctx->ev_fork, 0));
-        {
-            Scope sc(ctx, CC_K_PARENT_INIT, side, 1);
-            launch_parent_init(parent, n, nullptr, 0, ctx->grid, side);
+        if (fused) {  // parents initialised and hooked by the degree pass: the full shortcut remains
+            Scope sc(ctx, CC_K_SV_SHORTCUT, side, 1);
+            launch_shortcut_all(parent, n, st, 0, ctx->grid, side);
+            ctx->stats.sv_sample_stride = 1;
+        } else {
+            {
+                Scope sc(ctx, CC_K_PARENT_INIT, side, 1);
+                launch_parent_init(parent, n, nullptr, 0, ctx->grid, side);
+            }
+            enqueue_first_pass<T>(ctx, edges, n, m, side, true);
         }
-        enqueue_first_pass<T>(ctx, edges, n, m, side, true);
         if (cap >= 2) {
             // SV iteration 1 as well: the gather pass over the pairs, the crossing
             // pairs into ebuf0 (the degree pass keeps its hub table in ebuf1)
@@ -1107,7 +1128,11 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
             CC_TRY(enqueue_small_fit(ctx, n, s));
             CC_TRY(speculate());
         } else {
-            enqueue_degree<T>(ctx, edges, n, m, s, pre && pre->degree_counted);
+            if (fused) {
+                Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
+                launch_parent_init(parent, n, nullptr, 0, ctx->grid, s);
+            }
+            enqueue_degree<T>(ctx, edges, n, m, s, pre && pre->degree_counted, fused ? parent : nullptr);
             rec(ctx, EV_DEGREE, s);
             if (policy != CC_ROUTE_FORCE_BFS) {
                 // the fit on a highest-priority stream: the speculative gather
@@ -1430,6 +1455,8 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
     const bool predict = policy != CC_ROUTE_FORCE_SV;
     const bool speculate = !(policy == CC_ROUTE_FORCE_BFS && bfs_ok);
     const bool small = !learned && small_fit(n, m, policy);
+    // the first hook pass inside the windowed degree pass (parent init first)
+    const bool fused = predict && !learned && !small && speculate && fused_hooks(ctx, n, m);
     const float min_conf = (float)ctx->pred_min_conf;
     const long long before = ctx->stats.launches;
     long long direct = 0;
@@ -1446,8 +1473,14 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
         direct += 12;
     }
     auto speculative = [&](cudaStream_t ss) {
-        launch_parent_init(parent, n, nullptr, 0, ctx->grid, ss);
-        direct += 1 + enqueue_first_pass<T>(ctx, edges, n, m, ss, false);
+        if (fused) {  // parents initialised and hooked by the degree pass: the full shortcut remains
+            launch_shortcut_all(parent, n, st, 0, ctx->grid, ss);
+            ctx->stats.sv_sample_stride = 1;
+            direct += 1;
+        } else {
+            launch_parent_init(parent, n, nullptr, 0, ctx->grid, ss);
+            direct += 1 + enqueue_first_pass<T>(ctx, edges, n, m, ss, false);
+        }
         rg.sample_stride = ctx->stats.sv_sample_stride;
         launch_sv_gather_tiles<T>(edges, m, n, parent, hooked, eb0, st, 1, ss);
         launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, ss);
@@ -1486,7 +1519,11 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
         CC_TRY(enqueue_small_fit(ctx, n, cs));
         if (speculate) CC_TRY(fork_speculation());
     } else if (predict) {
-        enqueue_degree<T>(ctx, edges, n, m, cs);
+        if (fused) {
+            launch_parent_init(parent, n, nullptr, 0, ctx->grid, cs);
+            direct += 1;
+        }
+        enqueue_degree<T>(ctx, edges, n, m, cs, false, fused ? parent : nullptr);
         if (speculate) CC_TRY(fork_speculation());
         if (policy == CC_ROUTE_AUTO) {
             CU_TRY(cudaEventRecord(ctx->ev_fork, cs));

@@ -138,12 +138,15 @@ void launch_pred_unsure(const DevState *st, cudaGraphConditionalHandle h, float 
 // shared memory), then counted window by window with L2 atomics (one launch
 // per window: degree_part_buckets(n) + 1 launches).
 // scratch: degree_part_scratch_bytes; grid: blocks of the window count pass.
+// hook: the parent array with every vertex its own root, or null; with it the
+// window pass also hooks every pair (atomicMin(parent[max], min), the first
+// SV hook pass) while the window's parents are in L2.
 int degree_part_buckets(vid_t n);
 bool degree_part_ok(vid_t n, long long m);
-size_t degree_part_scratch_bytes(vid_t n, long long m);
+size_t degree_part_scratch_bytes(vid_t n, long long m, bool hook);
 template <typename T>
-void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t *deg, void *scratch, DevState *st,
-                               int num_sms, int grid, cudaStream_t s);
+void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t *deg, vid_t *hook, void *scratch,
+                               DevState *st, int num_sms, int grid, cudaStream_t s);
 cudaError_t degree_part_setup();
 cudaError_t degree_hubs_setup();  // dynamic shared memory of the hub-aware degree pass
 

@@ -27,6 +27,15 @@
 //
 // HBM traffic per call: the pairs once (2wm bytes), the entries written and
 // read back (2 x 8m bytes), deg zeroed and written back (8n).
+//
+// With `hook` (the parent array, every vertex its own root) each entry also
+// carries the endpoint's partner (64-bit entries, partner << 32 | id within
+// the window), and the window pass applies the first SV hook of Section 3.1
+// as well: for the entry of the larger end, atomicMin(parent[hi], lo) - the
+// first hook pass over all pairs, done while the window's parents are in L2.
+// Out of L2 that pass costs a DRAM read-modify-write per pair (grid + chains:
+// 8.1 ms for 268M int64 pairs). The entries double in size (16m bytes more
+// written and read back).
 #include "cc_common.cuh"
 #include "cc_kernels.h"
 
@@ -35,14 +44,21 @@ namespace ccg {
 constexpr int kPartThreads = 1024;
 constexpr int kPartBits = 23;                                   // vertices per window: 2^23 (32 MB of counts)
 constexpr int kPartMaxBuckets = 512;                            // n < 2^32
-constexpr int kPartChunkBytes = 1 << 16;
-constexpr int kPartSlots = kPartChunkBytes / 16 / kPartThreads;  // 16-byte vectors per thread and chunk
-constexpr int kPartMaxEnd = kPartChunkBytes / 8 * 2;             // endpoints of a chunk of int32 pairs
 constexpr unsigned long long kWaitNs = 1000000000ull;           // bounded mbarrier waits: 1 s
 
+// E: the entry type (uint32_t: the id within the window; unsigned long long:
+// partner << 32 | id within the window). Chunks of 64 KB of pairs, 32 KB
+// with the wider entries, so that both fit in shared memory.
+template <typename E> struct PartCfg {
+    static constexpr int kChunkBytes = sizeof(E) == 4 ? (1 << 16) : (1 << 15);
+    static constexpr int kSlots = kChunkBytes / 16 / kPartThreads;  // 16-byte vectors per thread and chunk
+    static constexpr int kMaxEnd = kChunkBytes / 8 * 2;            // endpoints of a chunk of int32 pairs
+};
+
+template <typename E>
 struct __align__(128) PartShared {
-    int4 buf[2][kPartChunkBytes / 16];  // two chunks of pairs (bulk-copy destinations)
-    uint32_t stage[kPartMaxEnd];        // ids within the window, sorted by window
+    int4 buf[2][PartCfg<E>::kChunkBytes / 16];  // two chunks of pairs (bulk-copy destinations)
+    E stage[PartCfg<E>::kMaxEnd];               // entries sorted by window
     uint32_t hist[kPartMaxBuckets];
     uint32_t loff[kPartMaxBuckets + 1];
     unsigned long long base[kPartMaxBuckets];
@@ -100,28 +116,53 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity
     return true;
 }
 
-template <typename T>
+template <typename T, typename E>
 __host__ __device__ constexpr long long part_chunk_pairs() {
-    return kPartChunkBytes / (2 * (long long)sizeof(T));
+    return PartCfg<E>::kChunkBytes / (2 * (long long)sizeof(T));
 }
 
 // Pair p of chunk c: from the chunk's shared-memory copy, or (the odd last
 // pair of an int32 chunk, which the 16-byte bulk copy leaves out) from global memory.
-template <typename T>
-__device__ __forceinline__ void chunk_pair(const PartShared &S, int slot, const T *edges, long long c, int sv,
+template <typename T, typename E>
+__device__ __forceinline__ void chunk_pair(const PartShared<E> &S, int slot, const T *edges, long long c, int sv,
                                            int j, bool in_smem, long long &u, long long &v) {
     if (in_smem) vec_pair<T>(S.buf[slot][sv], j, u, v);
-    else scalar_pair<T>(edges, c * part_chunk_pairs<T>() + (long long)sv * PairVec<T>::kPairs + j, u, v);
+    else scalar_pair<T>(edges, c * part_chunk_pairs<T, E>() + (long long)sv * PairVec<T>::kPairs + j, u, v);
 }
 
-template <typename T>
+// The entry of endpoint x with partner y.
+template <typename E>
+__device__ __forceinline__ E part_entry(long long x, long long y);
+template <>
+__device__ __forceinline__ uint32_t part_entry<uint32_t>(long long x, long long) {
+    return (uint32_t)x & ((1u << kPartBits) - 1u);
+}
+template <>
+__device__ __forceinline__ unsigned long long part_entry<unsigned long long>(long long x, long long y) {
+    return ((unsigned long long)y << 32) | ((unsigned long long)x & ((1ull << kPartBits) - 1ull));
+}
+
+// Count (and with a partner, hook) one entry of window b directly in global memory.
+template <typename E>
+__device__ __forceinline__ void part_direct(E e, int b, uint32_t *deg, vid_t *parent) {
+    const uint32_t x = ((uint32_t)b << kPartBits) | ((uint32_t)e & ((1u << kPartBits) - 1u));
+    atomicAdd(&deg[x], 1u);
+    if (sizeof(E) == 8) {
+        const uint32_t y = (uint32_t)((unsigned long long)e >> 32);
+        if (y < x) atomicMin(&parent[x], y);
+    }
+}
+
+template <typename T, typename E>
 __global__ void __launch_bounds__(kPartThreads, 1)
     k_degree_partition(const T *__restrict__ edges, long long m, vid_t n, int nb, unsigned long long cap,
-                       unsigned long long *__restrict__ fill, uint32_t *__restrict__ part, uint32_t *deg, DevState *st) {
+                       unsigned long long *__restrict__ fill, E *__restrict__ part, uint32_t *deg, vid_t *parent,
+                       DevState *st) {
     extern __shared__ __align__(128) unsigned char part_smem[];
-    PartShared &S = *reinterpret_cast<PartShared *>(part_smem);
+    PartShared<E> &S = *reinterpret_cast<PartShared<E> *>(part_smem);
     constexpr int P = PairVec<T>::kPairs;
-    constexpr long long CP = part_chunk_pairs<T>();
+    constexpr int kPartSlots = PartCfg<E>::kSlots;
+    constexpr long long CP = part_chunk_pairs<T, E>();
     constexpr uint32_t kLow = (1u << kPartBits) - 1u;
     const long long nch = (m + CP - 1) / CP;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -175,7 +216,7 @@ __global__ void __launch_bounds__(kPartThreads, 1)
                 uint32_t r = 0xffffffffu;
                 if (p < np) {
                     long long u, v;
-                    chunk_pair<T>(S, slot, edges, c, sv, j, sv < full_vecs, u, v);
+                    chunk_pair<T, E>(S, slot, edges, c, sv, j, sv < full_vecs, u, v);
                     if ((unsigned long long)u >= n || (unsigned long long)v >= n) {
                         bad = true;
                     } else {
@@ -229,9 +270,9 @@ __global__ void __launch_bounds__(kPartThreads, 1)
                 const uint32_t r = rk[k * P + j];
                 if (r == 0xffffffffu) continue;
                 long long u, v;
-                chunk_pair<T>(S, slot, edges, c, sv, j, sv < full_vecs, u, v);
-                S.stage[S.loff[u >> kPartBits] + (r & 0xffffu)] = (uint32_t)u & kLow;
-                S.stage[S.loff[v >> kPartBits] + (r >> 16)] = (uint32_t)v & kLow;
+                chunk_pair<T, E>(S, slot, edges, c, sv, j, sv < full_vecs, u, v);
+                S.stage[S.loff[u >> kPartBits] + (r & 0xffffu)] = part_entry<E>(u, v);
+                S.stage[S.loff[v >> kPartBits] + (r >> 16)] = part_entry<E>(v, u);
             }
         }
         __syncthreads();
@@ -246,9 +287,9 @@ __global__ void __launch_bounds__(kPartThreads, 1)
             const unsigned long long o0 = S.base[b];
             for (uint32_t i = r0 + lane; i < r1; i += 32) {
                 const unsigned long long o = o0 + (i - r0);
-                const uint32_t lid = S.stage[i];
-                if (o < cap) part[(unsigned long long)b * cap + o] = lid;
-                else atomicAdd(&deg[((unsigned long long)b << kPartBits) | lid], 1u);
+                const E e = S.stage[i];
+                if (o < cap) part[(unsigned long long)b * cap + o] = e;
+                else part_direct<E>(e, b, deg, parent);
             }
         }
         __syncthreads();
@@ -281,56 +322,101 @@ __global__ void __launch_bounds__(kBlock) k_degree_window(const uint32_t *__rest
     if (i < len) atomicAdd(&d[part[(unsigned long long)b * cap + i]], 1u);
 }
 
+// The same with partners: one RED per entry on the counts, and for the entry
+// of the larger end of a pair, a RED atomicMin on its parent (both windows
+// of 32 MB stay in L2 during the launch).
+__global__ void __launch_bounds__(kBlock) k_degree_window_hook(const unsigned long long *__restrict__ part,
+                                                               unsigned long long cap,
+                                                               const unsigned long long *__restrict__ fill, int b,
+                                                               uint32_t *deg, vid_t *parent) {
+    const unsigned long long f = fill[b], len = f < cap ? f : cap;
+    const ulonglong2 *p2 = reinterpret_cast<const ulonglong2 *>(part + (unsigned long long)b * cap);
+    uint32_t *d = deg + ((unsigned long long)b << kPartBits);
+    vid_t *pa = parent + ((unsigned long long)b << kPartBits);
+    const uint32_t x0 = (uint32_t)b << kPartBits;
+    auto one = [&](unsigned long long e) {
+        const uint32_t lx = (uint32_t)e & ((1u << kPartBits) - 1u), y = (uint32_t)(e >> 32);
+        atomicAdd(&d[lx], 1u);
+        if (y < x0 + lx) atomicMin(&pa[lx], y);
+    };
+    const unsigned long long nv = len / 2;
+    for (unsigned long long k = gtid(); k < nv; k += gstride()) {
+        const ulonglong2 q = __ldcs(p2 + k);
+        one(q.x);
+        one(q.y);
+    }
+    const unsigned long long i = nv * 2 + gtid();
+    if (i < len) one(part[(unsigned long long)b * cap + i]);
+}
+
 // ---------------------------------------------------------------------------
 int degree_part_buckets(vid_t n) { return (int)(((long long)n + (1LL << kPartBits) - 1) >> kPartBits); }
 
 bool degree_part_ok(vid_t n, long long m) { return n > (1u << 25) && m >= (1LL << 20); }
 
-// A window holds up to twice the average entries (a multiple of 4, so every
-// window's region starts on a 16-byte boundary).
+// A window holds up to 1.5 times the average entries (a multiple of 4, so
+// every window's region starts on a 16-byte boundary); the ids are permuted
+// in every workload here, so windows hold the average to within a fraction
+// of a percent, and entries past the cap are counted directly (exact either way).
 static unsigned long long part_cap(vid_t n, long long m) {
     const int nb = degree_part_buckets(n);
     const unsigned long long avg = (2ull * (unsigned long long)m + nb - 1) / nb;
-    return (2 * avg + 4096 + 3) & ~3ull;
+    return (avg + avg / 2 + 4096 + 3) & ~3ull;
 }
 
 // scratch layout: fill[nb] (64-bit reservation counters) at 0, the window
-// regions (nb x cap 32-bit ids) from part_offset(nb)
+// regions (nb x cap entries of 8 bytes with partners, else 4) from part_offset(nb)
 static size_t part_offset(int nb) { return 256 + (((size_t)nb * 8 + 255) & ~(size_t)255); }
 
-size_t degree_part_scratch_bytes(vid_t n, long long m) {
+size_t degree_part_scratch_bytes(vid_t n, long long m, bool hook) {
     const int nb = degree_part_buckets(n);
-    return part_offset(nb) + (size_t)nb * part_cap(n, m) * 4;
+    return part_offset(nb) + (size_t)nb * part_cap(n, m) * (hook ? 8 : 4);
 }
 
 template <typename T>
-void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t *deg, void *scratch, DevState *st,
-                               int num_sms, int grid, cudaStream_t s) {
+void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t *deg, vid_t *hook, void *scratch,
+                               DevState *st, int num_sms, int grid, cudaStream_t s) {
     const int nb = degree_part_buckets(n);
     const unsigned long long cap = part_cap(n, m);
     unsigned long long *fill = reinterpret_cast<unsigned long long *>(scratch);
-    uint32_t *part = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + part_offset(nb));
+    void *part = static_cast<char *>(scratch) + part_offset(nb);
     cudaMemsetAsync(fill, 0, (size_t)nb * 8, s);
     cudaMemsetAsync(deg, 0, (size_t)n * 4, s);
-    const long long nch = (m + part_chunk_pairs<T>() - 1) / part_chunk_pairs<T>();
-    const int pgrid = (int)(nch < num_sms ? nch : num_sms);
-    if (pgrid > 0)
-        k_degree_partition<T><<<pgrid, kPartThreads, sizeof(PartShared), s>>>((const T *)edges, m, n, nb, cap, fill,
-                                                                             part, deg, st);
-    for (int b = 0; b < nb; b++) k_degree_window<<<grid, kBlock, 0, s>>>(part, cap, fill, b, deg);
+    if (hook) {
+        using E = unsigned long long;
+        const long long nch = (m + part_chunk_pairs<T, E>() - 1) / part_chunk_pairs<T, E>();
+        const int pgrid = (int)(nch < num_sms ? nch : num_sms);
+        if (pgrid > 0)
+            k_degree_partition<T, E><<<pgrid, kPartThreads, sizeof(PartShared<E>), s>>>(
+                (const T *)edges, m, n, nb, cap, fill, (E *)part, deg, hook, st);
+        for (int b = 0; b < nb; b++) k_degree_window_hook<<<grid, kBlock, 0, s>>>((E *)part, cap, fill, b, deg, hook);
+    } else {
+        using E = uint32_t;
+        const long long nch = (m + part_chunk_pairs<T, E>() - 1) / part_chunk_pairs<T, E>();
+        const int pgrid = (int)(nch < num_sms ? nch : num_sms);
+        if (pgrid > 0)
+            k_degree_partition<T, E><<<pgrid, kPartThreads, sizeof(PartShared<E>), s>>>(
+                (const T *)edges, m, n, nb, cap, fill, (E *)part, deg, nullptr, st);
+        for (int b = 0; b < nb; b++) k_degree_window<<<grid, kBlock, 0, s>>>((E *)part, cap, fill, b, deg);
+    }
 }
-template void launch_degree_partitioned<int32_t>(const void *, long long, vid_t, uint32_t *, void *, DevState *, int,
-                                                 int, cudaStream_t);
-template void launch_degree_partitioned<int64_t>(const void *, long long, vid_t, uint32_t *, void *, DevState *, int,
-                                                 int, cudaStream_t);
+template void launch_degree_partitioned<int32_t>(const void *, long long, vid_t, uint32_t *, vid_t *, void *,
+                                                 DevState *, int, int, cudaStream_t);
+template void launch_degree_partitioned<int64_t>(const void *, long long, vid_t, uint32_t *, vid_t *, void *,
+                                                 DevState *, int, int, cudaStream_t);
 
 cudaError_t degree_part_setup() {
-    cudaError_t e = cudaFuncSetAttribute(k_degree_partition<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(PartShared));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_degree_partition<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(PartShared));
-    return e;
+    const void *ks[] = {(const void *)k_degree_partition<int32_t, uint32_t>,
+                        (const void *)k_degree_partition<int64_t, uint32_t>,
+                        (const void *)k_degree_partition<int32_t, unsigned long long>,
+                        (const void *)k_degree_partition<int64_t, unsigned long long>};
+    const int sm[] = {(int)sizeof(PartShared<uint32_t>), (int)sizeof(PartShared<uint32_t>),
+                      (int)sizeof(PartShared<unsigned long long>), (int)sizeof(PartShared<unsigned long long>)};
+    for (int i = 0; i < 4; i++) {
+        const cudaError_t e = cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, sm[i]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace ccg

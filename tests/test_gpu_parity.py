@@ -362,6 +362,32 @@ def test_partitioned_degree_pass_chunks_and_windows(id_bytes, m, n):
     _degree_check(e, n, id_bytes)
 
 
+@pytest.mark.parametrize("id_bytes,m,n", [
+    (4, (1 << 20) + 1, (1 << 25) + 1),
+    (8, (1 << 20) + 4097, (1 << 25) + 100003),
+])
+@pytest.mark.parametrize("profile", [0, 1])
+def test_first_hooks_inside_the_windowed_degree_pass(id_bytes, m, n, profile):
+    """With n > 2^25 and no SV front end the window pass also applies the first
+    hook pass (atomicMin on the parent of each pair's larger end) while the
+    window's parents are in L2: labels exact on the heuristic route (the hooks
+    fused) and on the forced routes (not fused), with chains so that the
+    hooks build deep trees, self-loops and duplicated pairs."""
+    rng = np.random.default_rng(7 + id_bytes)
+    dt = np.int32 if id_bytes == 4 else np.int64
+    e = rng.integers(0, n, size=(m, 2))
+    perm = rng.permutation(n)
+    k = m // 4  # a few long paths through random vertices
+    e[:k, 0] = perm[:k]
+    e[:k, 1] = perm[1:k + 1]
+    e[k:k + 1000] = e[:1000]  # duplicates
+    e[::101, 1] = e[::101, 0]  # self-loops
+    e = np.ascontiguousarray(e[rng.permutation(m)].astype(dt))
+    want = oracle.cc_labels(e, n, cross_check=False)
+    out = assert_labels_match(e, n, want=want, routes=("auto", "sv", "bfs"), profile=profile)
+    assert out["auto"]["route"] == 0 and out["auto"]["sv_sample_stride"] == 1
+
+
 def test_partitioned_degree_pass_window_overflow():
     """One vertex is an endpoint of every pair: its window holds more than
     twice the average entries, and the entries past its capacity are counted
