@@ -2203,10 +2203,13 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
     KsBatchOut out{as<double>(ctx->kb_D),     as<double>(ctx->kb_alpha), as<long long>(ctx->kb_xmin),
                    as<long long>(ctx->kb_ntail), as<long long>(ctx->kb_ncand), as<int>(ctx->kb_route),
                    as<int>(ctx->kb_ovf),      as<unsigned long long>(ctx->kb_seed)};
+    // without the front end the degree pass applies the first hook pass as well, and the fits
+    // run beside the full shortcut that follows it
+    const bool fused = predict && !sch.front;
     if (predict) {
         CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, cs));
         launch_degree_batch(edges, m, eo, vo, G, as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx),
-                            sch.deg_regions, cs);
+                            sch.deg_regions, cs, fused ? parent : nullptr);
         // the fits (largest graph first) on the highest-priority stream beside the first hook pass
         CU_TRY(cudaEventRecord(ctx->ev_fork, cs));
         CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
@@ -2217,7 +2220,12 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
                         ctx->opt.ks_min_span, ctx->opt.ks_tau, ctx->kb_blocks, as<int>(ctx->kb_order),
                         counter_at<int>(ctx->counters, kCtrKsQueue), ctx->fit_s);
         CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
-        direct += 5 + enqueue_batch_first_hooks(ctx, edges, m, eo, vo, G, nt, sch, cs);
+        if (fused) {
+            launch_shortcut_all(parent, nt, st, 0, ctx->grid, cs);
+            direct += 6;
+        } else {
+            direct += 5 + enqueue_batch_first_hooks(ctx, edges, m, eo, vo, G, nt, sch, cs);
+        }
         CU_TRY(cudaStreamWaitEvent(cs, ctx->ev_fit, 0));
         // graphs with more large degrees than the per-graph fit holds: the single-graph fit, one per iteration
         KsScratch ks{as<uint32_t>(ctx->ks_xs), as<unsigned long long>(ctx->ks_cnt), as<unsigned long long>(ctx->ks_cum),
@@ -2262,12 +2270,19 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
             }));
             launch_batch_bfs_finish(fv, n, vo, G, vtiles, as<uint32_t>(ctx->kb_cmin), parent, ctx->grid, bs);
             rg.bfs_launches = 2 + 1 + 2;
+            if (fused) {  // the merge left visited vertices two hops from their roots
+                launch_shortcut_all(parent, nt, st, 0, ctx->grid, bs);
+                rg.bfs_launches += 1;
+            }
             return CC_OK;
         }));
     } else {
         direct += enqueue_batch_first_hooks(ctx, edges, m, eo, vo, G, nt, sch, cs);
     }
-    launch_shortcut_all(parent, nt, st, 0, ctx->grid, cs);
+    if (!fused) {
+        launch_shortcut_all(parent, nt, st, 0, ctx->grid, cs);
+        direct += 1;
+    }
     launch_sv_pass_batch(2, edges, m, eo, vo, G, nt, parent, hooked, eb0, st, 1, ctx->grid, cs, sch);
     launch_sv_shortcut(parent, hooked, st, 1, ctx->grid, cs);
     cudaGraphConditionalHandle hs;
@@ -2278,7 +2293,7 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
         return CC_OK;
     }));
     launch_finalize_batch(parent, nt, vo, G, labels, ctx->grid, cs, vtiles);
-    direct += 5;
+    direct += 4;
     CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, hook_base), cudaMemcpyDeviceToHost, cs));
     rg.static_launches = ctx->stats.launches - before + direct;
     return CC_OK;
@@ -2768,13 +2783,12 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
         Scope sc(ctx, CC_K_PARENT_INIT, s, 1);
         launch_parent_init(parent, nt, nullptr, 0, ctx->grid, s);
     }
-    // Route prediction per graph (Algorithm 2 lines 1-3): the degree pass,
-    // one K-S fit per graph beside the first hook pass (every vertex starts
-    // as its own root, so that pass needs no route), then the BFS step for
-    // the graphs routed to it (lines 5-7): their visited vertices take the
-    // visited minimum as parent before the SV passes continue. Fusing the
-    // degree count into the first hook pass measured 69 ms against 39 + 13
-    // ms for the two passes (4,096 graphs).
+    // Route prediction per graph (Algorithm 2 lines 1-3): the degree pass
+    // (with the first hook pass fused in unless the SV front end runs: every
+    // vertex starts as its own root, so that pass needs no route), one K-S fit
+    // per graph, then the BFS step for the graphs routed to it (lines 5-7):
+    // their visited vertices take the visited minimum as parent before the SV
+    // passes continue.
     const int policy = ctx->opt.route_policy;
     const bool predict = m > 0 && policy != CC_ROUTE_FORCE_SV;
     if (predict) {
@@ -2784,7 +2798,8 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
             {
                 Scope sc(ctx, CC_K_DEGREE, s, 1);
                 launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G,
-                                    as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), sch.deg_regions, s);
+                                    as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), sch.deg_regions, s,
+                                    sch.front ? nullptr : parent);
             }
             // the fits on a highest-priority stream, overlapping the first hook
             // pass, which launches one block per tile so that the fits' blocks
@@ -2794,7 +2809,7 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
             CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
             CC_TRY(enqueue_ks_batch(ctx, vertex_offsets_dev, vertex_offsets_host, G, ctx->fit_s));
             CU_TRY(cudaEventRecord(ctx->ev_fit, ctx->fit_s));
-            {
+            if (sch.front) {  // without the front end the degree pass applied the first hook pass
                 Scope sc(ctx, CC_K_SV_FIRST, s, 1);
                 enqueue_batch_first_hooks(ctx, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G,
                                           nt, sch, s);

@@ -260,9 +260,12 @@ struct KsBatchOut {  // per graph
 };
 size_t ks_batch_entries();
 // next: a device counter the blocks take tiles from (zeroed here); regions:
-// contiguous regions of the pairs worked on side by side, each in order
+// contiguous regions of the pairs worked on side by side, each in order;
+// hook: the parent array with every vertex its own root, to apply the first
+// SV hook pass (atomicMin(parent[max], min)) in the same pass, or null
 void launch_degree_batch(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G, uint32_t *deg,
-                         DevState *st, int grid, unsigned long long *next, int regions, cudaStream_t s);
+                         DevState *st, int grid, unsigned long long *next, int regions, cudaStream_t s,
+                         vid_t *hook = nullptr);
 // out[k] = the graph holding item k << kTileShift of the offsets `off` (G + 1 entries), k < (count >> kTileShift) + 1
 void launch_tile_graphs(const int64_t *off, int G, long long count, uint32_t *out, int grid, cudaStream_t s);
 // order (device, G graph numbers, largest first) and next (device counter) may

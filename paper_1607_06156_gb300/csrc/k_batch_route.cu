@@ -45,11 +45,23 @@ constexpr int kSmallHistKeyAt = 2 * kBB + 2;  // word of the argmax key in k_sma
 // tile, since the graphs hold thousands to millions of pairs - reads that
 // graph's base and size once; a tile across graphs finds each pair's graph
 // by stepping from its first graph.
+//
+// With `hook` (the parent array, every vertex its own root) the pass also
+// applies the first SV hook pass of Section 3.1 to every pair:
+// atomicMin(parent[max], min) in union ids, while the graphs in flight have
+// their parents in L2 beside their counts.
 constexpr int kDegVec = 2;
+__device__ __forceinline__ void batch_hook(vid_t *hook, long long a, long long b) {
+    if (a == b) return;
+    const vid_t hi = (vid_t)(a > b ? a : b), lo = (vid_t)(a > b ? b : a);
+    atomicMin(&hook[hi], lo);
+}
+
 __global__ void __launch_bounds__(kBlock, 6) k_degree_batch(const int32_t *__restrict__ in, long long m,
                                                             const int64_t *__restrict__ eo,
                                                             const int64_t *__restrict__ vo, int G, uint32_t *deg,
-                                                            DevState *st, unsigned long long *next, int regions) {
+                                                            DevState *st, unsigned long long *next, int regions,
+                                                            vid_t *hook) {
     constexpr int V = kDegVec;
     __shared__ long long s_t[2];
     __shared__ int s_g0[2], s_g1[2];
@@ -102,10 +114,12 @@ __global__ void __launch_bounds__(kBlock, 6) k_degree_batch(const int32_t *__res
                 if (ok0) {
                     atomicAdd(&deg[base + x.x], 1u);
                     atomicAdd(&deg[base + x.y], 1u);
+                    if (hook) batch_hook(hook, base + x.x, base + x.y);
                 }
                 if (ok1) {
                     atomicAdd(&deg[base + x.z], 1u);
                     atomicAdd(&deg[base + x.w], 1u);
+                    if (hook) batch_hook(hook, base + x.z, base + x.w);
                 }
                 bad |= !(ok0 && ok1);
             }
@@ -127,6 +141,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_degree_batch(const int32_t *__res
                     }
                     atomicAdd(&deg[base + u], 1u);
                     atomicAdd(&deg[base + v], 1u);
+                    if (hook) batch_hook(hook, base + u, base + v);
                 }
             }
         }
@@ -141,6 +156,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_degree_batch(const int32_t *__res
         else {
             atomicAdd(&deg[base + u], 1u);
             atomicAdd(&deg[base + v], 1u);
+            if (hook) batch_hook(hook, base + u, base + v);
         }
     }
     if (bad) set_err(st, kErrInvalidEdge);
@@ -549,11 +565,11 @@ void launch_fit_one(const uint32_t *deg, long long n, int64_t *vo, KsBatchScratc
 
 // ---------------------------------------------------------------------------
 void launch_degree_batch(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G, uint32_t *deg,
-                         DevState *st, int grid, unsigned long long *next, int regions, cudaStream_t s) {
+                         DevState *st, int grid, unsigned long long *next, int regions, cudaStream_t s, vid_t *hook) {
     if (m <= 0) return;
     cudaMemsetAsync(next, 0, sizeof(unsigned long long), s);
     k_degree_batch<<<fit_grid((const void *)k_degree_batch, grid, kBlock), kBlock, 0, s>>>(
-        in, m, eo, vo, G, deg, st, next, regions > 0 ? regions : 1);
+        in, m, eo, vo, G, deg, st, next, regions > 0 ? regions : 1, hook);
 }
 
 __global__ void __launch_bounds__(kBlock) k_tile_graphs(const int64_t *__restrict__ off, int G, long long ntiles,
