@@ -54,9 +54,7 @@ constexpr int kDegVec = 2;
 __device__ __forceinline__ void batch_hook(vid_t *hook, long long a, long long b) {
     if (a == b) return;
     const vid_t hi = (vid_t)(a > b ? a : b), lo = (vid_t)(a > b ? b : a);
-    // a plain read first: parents only decrease, so a value <= lo read now
-    // means the atomic could not lower it
-    if (__ldcg(&hook[hi]) > lo) atomicMin(&hook[hi], lo);
+    atomicMin(&hook[hi], lo);
 }
 
 __global__ void __launch_bounds__(kBlock, 6) k_degree_batch(const int32_t *__restrict__ in, long long m,
