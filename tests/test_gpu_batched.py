@@ -139,3 +139,13 @@ def test_batched_over_2_25_vertices():
     assert b.vertex_offsets[-1] >= 1 << 25
     got, _ = _run_batched(torch, b.edges, b.edge_offsets, b.vertex_offsets)
     _check_each(b, got)
+
+
+@pytest.mark.parametrize("bad", [-2, 1025])
+def test_hook_regions_option_is_checked(bad):
+    torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    with pytest.raises(cc.CCError) as ei:
+        cc.Engine(batch_hook_regions=bad)
+    assert ei.value.status == 1
