@@ -380,8 +380,7 @@ cc_status cc_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, fl
  *   stream         cudaStream_t as void*
  * Errors as cc_labels (CC_ERR_INVALID_EDGE for an id outside [0, n)). The
  * call synchronises `stream` once per SV iteration (it reads the active-pair
- * count back) and returns with the labels complete, so it cannot be called
- * while `stream` is being captured into a CUDA graph.
+ * count back) and returns with the labels complete.
  * Every call looks up the device address of the scratch array
  * (cudaGetSymbolAddress) on the current device, so it stays valid across a
  * device reset. Every call on a device shares the one scratch area and
