@@ -209,7 +209,7 @@ def kernel_class(name: str):
         return None
     if "k_sv_pass_loop" in name:  # the list pass inside the graph's WHILE node
         return "sv_gather_list"
-    table = [("k_degree_partition", "degree"), ("k_degree_count", "degree"), ("k_degree_hubs", "degree"), ("k_hub_", "degree"), ("k_degree<", "degree"), ("k_hist", "hist"),
+    table = [("k_degree_partition", "degree"), ("k_degree_window", "degree"), ("k_degree_count", "degree"), ("k_degree_hubs", "degree"), ("k_hub_", "degree"), ("k_degree<", "degree"), ("k_hist", "hist"),
              ("k_distinct", "ks"), ("k_ks_", "ks"), ("k_parent_init", "parent_init"), ("k_sv_sample", "sv_first"),
              ("k_shortcut_all", "sv_shortcut"), ("k_sv_shortcut", "sv_shortcut"), ("k_finalize", "finalize")]
     for key, cls in table:
@@ -1063,7 +1063,7 @@ def main() -> int:
                 "kernels": kernels, "route_compare": route_compare,
                 "stage_ms": {k: last[k] for k in ("ms_degree", "ms_predict", "ms_csr", "ms_bfs", "ms_sv",
                                                   "ms_finalize", "ms_total")},
-                "m_active": last["m_active"], "configs": configs}
+                "m_active": last["m_active"], "degree_form": last["degree_form"], "configs": configs}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -143,7 +143,10 @@ typedef struct {
     int route_source;       /* 0 = K-S heuristic, 1 = learned predictor, 2 = forced */
     int bfs_levels;         /* BFS levels run */
     int sv_iters;           /* SV iterations run */
-    int pad0;
+    int degree_form;        /* exact degree pass of a single-graph call: 0 = none ran, 1 = one L2
+                               atomic per endpoint, 2 = hub table, 3 = windows of 2^23 vertices
+                               counted in L2 (n > 2^25), 4 = windows counted in shared memory
+                               (2^20 <= n <= 2^24) */
     double ks_d;            /* K-S statistic (min over xmin); 1.0 if no candidate */
     double ks_alpha;        /* power-law exponent at the chosen xmin */
     int64_t ks_xmin;        /* chosen xmin; 0 if no candidate */

@@ -56,7 +56,7 @@ _OPTION_FIELDS = frozenset(f for f, _ in Options._fields_ if f != "reserved")
 class Stats(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int), ("route", ctypes.c_int), ("route_source", ctypes.c_int),
-        ("bfs_levels", ctypes.c_int), ("sv_iters", ctypes.c_int), ("pad0", ctypes.c_int),
+        ("bfs_levels", ctypes.c_int), ("sv_iters", ctypes.c_int), ("degree_form", ctypes.c_int),
         ("ks_d", ctypes.c_double), ("ks_alpha", ctypes.c_double), ("ks_xmin", ctypes.c_int64),
         ("ks_ntail", ctypes.c_int64), ("ks_ncand", ctypes.c_int64), ("n", ctypes.c_int64), ("m", ctypes.c_int64),
         ("max_degree", ctypes.c_int64), ("seed_vertex", ctypes.c_int64), ("bfs_visited", ctypes.c_int64),

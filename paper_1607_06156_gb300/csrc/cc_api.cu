@@ -105,6 +105,7 @@ struct cc_ctx {
         bool edge_bfs = false;          // the BFS branch is the edge-list BFS
         bool batched = false;           // the batched form (route = graphs that took the BFS step)
         int batch_unroll = 0, batch_grid_mult = 0, batch_deg_regions = 0, batch_sv_regions = 0;  // its schedule
+        int degree_form = 0;            // the exact degree pass captured (cc_stats.degree_form)
     } g_route;
     RouteGraph g_capture;               // the same facts for a call captured into the caller's graph
     const RouteGraph *rg_last = nullptr; // the facts of the last graph-mode call
@@ -537,6 +538,7 @@ template <typename T>
 void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaStream_t s, bool counted = false,
                     vid_t *hook = nullptr) {
     if (counted) {  // the pairs were counted as they arrived (cc_labels_host): histogram only
+        ctx->stats.degree_form = 1;
         Scope sc(ctx, CC_K_HIST, s, 1);
         launch_hist(as<uint32_t>(ctx->deg), n, as<uint32_t>(ctx->hist), as<uint32_t>(ctx->ovf), ctx->ovf_cap,
                     as<DevState>(ctx->st), ctx->grid, s);
@@ -544,10 +546,19 @@ void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaSt
     }
     cudaMemsetAsync(ctx->hist.p, 0, (size_t)kHistDense * 4, s);
     if (degree_part_ok(n, m) && ctx->dpart.bytes >= degree_part_scratch_bytes(n, m, hook != nullptr)) {
+        ctx->stats.degree_form = 3;
         Scope sc(ctx, CC_K_DEGREE, s, 1 + degree_part_buckets(n));
         launch_degree_partitioned<T>(edges, m, n, as<uint32_t>(ctx->deg), hook, ctx->dpart.p, as<DevState>(ctx->st),
                                      ctx->num_sms, ctx->grid, s);
+    } else if (degree_smem_ok(n, m) && ctx->ebuf1.bytes >= degree_smem_scratch_bytes(n, m)) {
+        // ebuf1 (8m bytes) is idle until the second SV iteration; the 16-bit
+        // entries take about 6m
+        ctx->stats.degree_form = 4;
+        Scope sc(ctx, CC_K_DEGREE, s, 2);
+        launch_degree_smem<T>(edges, m, n, as<uint32_t>(ctx->deg), ctx->ebuf1.p, as<DevState>(ctx->st), ctx->num_sms,
+                              s);
     } else if (degree_uses_hubs(m) && ctx->ebuf1.bytes >= degree_hubs_scratch_bytes()) {
+        ctx->stats.degree_form = 2;
         cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
         Scope sc(ctx, CC_K_DEGREE, s, 5);
         // ebuf1 is idle until the second SV iteration over the compacted list; m >= 2^24 makes it far larger
@@ -555,6 +566,7 @@ void enqueue_degree(cc_ctx *ctx, const void *edges, vid_t n, long long m, cudaSt
         launch_degree_hubs<T>(edges, m, n, as<uint32_t>(ctx->deg), as<unsigned>(ctx->ebuf1), as<DevState>(ctx->st),
                               ctx->grid, ctx->num_sms, s);
     } else {
+        ctx->stats.degree_form = 1;
         cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s);
         Scope sc(ctx, CC_K_DEGREE, s, m > 0);
         launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), as<DevState>(ctx->st), ctx->grid, s);
@@ -1118,6 +1130,7 @@ cc_status labels_impl(cc_ctx *ctx, const void *edges, vid_t n, long long m, void
         if (small) {
             CC_TRY(ensure_batch_route(ctx, 1, 1));
             CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, s));
+            ctx->stats.degree_form = 1;
             {
                 Scope sc(ctx, CC_K_DEGREE, s, m > 0);
                 launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), st, ctx->grid, s);
@@ -1466,6 +1479,7 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
     rg.bfs_launches = 0;
     rg.unsure_launches = 0;
     rg.sample_stride = 1;
+    ctx->stats.degree_form = 0;
     CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), cs));
     if (learned) {
         launch_route_features<T>(edges, m, n, feat_scratch(ctx), st, as<float>(ctx->f_x), ctx->grid, cs);
@@ -1512,6 +1526,7 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
         rg.unsure_launches = ctx->stats.launches - b0;
         ctx->stats.launches = b0;
     } else if (predict && small) {
+        ctx->stats.degree_form = 1;
         CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, cs));
         launch_degree<T>(edges, m, n, as<uint32_t>(ctx->deg), st, ctx->grid, cs);
         direct += 1;
@@ -1612,6 +1627,7 @@ cc_status enqueue_route(cc_ctx *ctx, const void *edges, vid_t n, long long m, vo
     launch_finalize<T>(parent, n, labels, ctx->grid, cs);
     direct += 2;
     CU_TRY(cudaMemcpyAsync(ctx->h_st, st, offsetof(DevState, hook_base), cudaMemcpyDeviceToHost, cs));
+    rg.degree_form = ctx->stats.degree_form;
     rg.static_launches = ctx->stats.launches - before + direct;
     return CC_OK;
 }
@@ -1674,6 +1690,7 @@ void stats_from_device(cc_ctx *ctx) {
     for (int i = it0 + 1; i < h->loop_done && i < CC_MAX_SV_ITERS_RECORDED; i++) S.m_active[i] = (int64_t)h->kept[i - 1];
     for (int i = 0; i < h->loop_done && i < CC_MAX_SV_ITERS_RECORDED; i++) S.sv_hooks[i] = (int64_t)h->hooked[i];
     S.sv_sample_stride = rg.sample_stride;
+    S.degree_form = rg.batched || h->route_source == 1 ? 0 : rg.degree_form;
     const long long loops = h->loop_done > it0 + 1 ? h->loop_done - it0 - 1 : 0;
     const bool unsure = h->route_source != 1;  // the learned policy ran the exact prediction
     S.launches = rg.static_launches + (unsure ? rg.unsure_launches : 0) +
@@ -2186,6 +2203,7 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
     long long direct = 0;
     rg.edge_bfs = true;
     rg.batched = true;
+    rg.degree_form = 0;
     rg.level_launches = 4;
     rg.bfs_launches = 0;
     rg.unsure_launches = 0;

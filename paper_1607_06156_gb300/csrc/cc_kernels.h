@@ -147,6 +147,14 @@ size_t degree_part_scratch_bytes(vid_t n, long long m, bool hook);
 template <typename T>
 void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t *deg, vid_t *hook, void *scratch,
                                DevState *st, int num_sms, int grid, cudaStream_t s);
+// The same for 2^20 <= n <= 2^24 with windows of at most 2^15 vertices whose
+// counts stay in shared memory (16-bit entries; two launches). Scratch:
+// degree_smem_scratch_bytes.
+bool degree_smem_ok(vid_t n, long long m);
+size_t degree_smem_scratch_bytes(vid_t n, long long m);
+template <typename T>
+void launch_degree_smem(const void *edges, long long m, vid_t n, uint32_t *deg, void *scratch, DevState *st,
+                        int num_sms, cudaStream_t s);
 cudaError_t degree_part_setup();
 cudaError_t degree_hubs_setup();  // dynamic shared memory of the hub-aware degree pass
 

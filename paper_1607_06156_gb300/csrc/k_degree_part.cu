@@ -130,22 +130,22 @@ __device__ __forceinline__ void chunk_pair(const PartShared<E> &S, int slot, con
     else scalar_pair<T>(edges, c * part_chunk_pairs<T, E>() + (long long)sv * PairVec<T>::kPairs + j, u, v);
 }
 
-// The entry of endpoint x with partner y.
+// The entry of endpoint x with partner y; windows of 2^wb vertices.
 template <typename E>
-__device__ __forceinline__ E part_entry(long long x, long long y);
+__device__ __forceinline__ E part_entry(long long x, long long y, int wb);
 template <>
-__device__ __forceinline__ uint32_t part_entry<uint32_t>(long long x, long long) {
-    return (uint32_t)x & ((1u << kPartBits) - 1u);
+__device__ __forceinline__ uint32_t part_entry<uint32_t>(long long x, long long, int wb) {
+    return (uint32_t)x & ((1u << wb) - 1u);
 }
 template <>
-__device__ __forceinline__ unsigned long long part_entry<unsigned long long>(long long x, long long y) {
-    return ((unsigned long long)y << 32) | ((unsigned long long)x & ((1ull << kPartBits) - 1ull));
+__device__ __forceinline__ unsigned long long part_entry<unsigned long long>(long long x, long long y, int wb) {
+    return ((unsigned long long)y << 32) | ((unsigned long long)x & ((1ull << wb) - 1ull));
 }
 
 // Count (and with a partner, hook) one entry of window b directly in global memory.
 template <typename E>
-__device__ __forceinline__ void part_direct(E e, int b, uint32_t *deg, vid_t *parent) {
-    const uint32_t x = ((uint32_t)b << kPartBits) | ((uint32_t)e & ((1u << kPartBits) - 1u));
+__device__ __forceinline__ void part_direct(E e, int b, int wb, uint32_t *deg, vid_t *parent) {
+    const uint32_t x = ((uint32_t)b << wb) | ((uint32_t)e & ((1u << wb) - 1u));
     atomicAdd(&deg[x], 1u);
     if (sizeof(E) == 8) {
         const uint32_t y = (uint32_t)((unsigned long long)e >> 32);
@@ -155,7 +155,7 @@ __device__ __forceinline__ void part_direct(E e, int b, uint32_t *deg, vid_t *pa
 
 template <typename T, typename E>
 __global__ void __launch_bounds__(kPartThreads, 1)
-    k_degree_partition(const T *__restrict__ edges, long long m, vid_t n, int nb, unsigned long long cap,
+    k_degree_partition(const T *__restrict__ edges, long long m, vid_t n, int nb, int wb, unsigned long long cap,
                        unsigned long long *__restrict__ fill, E *__restrict__ part, uint32_t *deg, vid_t *parent,
                        DevState *st) {
     extern __shared__ __align__(128) unsigned char part_smem[];
@@ -163,7 +163,6 @@ __global__ void __launch_bounds__(kPartThreads, 1)
     constexpr int P = PairVec<T>::kPairs;
     constexpr int kPartSlots = PartCfg<E>::kSlots;
     constexpr long long CP = part_chunk_pairs<T, E>();
-    constexpr uint32_t kLow = (1u << kPartBits) - 1u;
     const long long nch = (m + CP - 1) / CP;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const long long G = gridDim.x;
@@ -220,8 +219,8 @@ __global__ void __launch_bounds__(kPartThreads, 1)
                     if ((unsigned long long)u >= n || (unsigned long long)v >= n) {
                         bad = true;
                     } else {
-                        const uint32_t ru = atomicAdd(&S.hist[u >> kPartBits], 1u);
-                        const uint32_t rv = atomicAdd(&S.hist[v >> kPartBits], 1u);
+                        const uint32_t ru = atomicAdd(&S.hist[u >> wb], 1u);
+                        const uint32_t rv = atomicAdd(&S.hist[v >> wb], 1u);
                         r = ru | (rv << 16);
                     }
                 }
@@ -271,8 +270,8 @@ __global__ void __launch_bounds__(kPartThreads, 1)
                 if (r == 0xffffffffu) continue;
                 long long u, v;
                 chunk_pair<T, E>(S, slot, edges, c, sv, j, sv < full_vecs, u, v);
-                S.stage[S.loff[u >> kPartBits] + (r & 0xffffu)] = part_entry<E>(u, v);
-                S.stage[S.loff[v >> kPartBits] + (r >> 16)] = part_entry<E>(v, u);
+                S.stage[S.loff[u >> wb] + (r & 0xffffu)] = part_entry<E>(u, v, wb);
+                S.stage[S.loff[v >> wb] + (r >> 16)] = part_entry<E>(v, u, wb);
             }
         }
         __syncthreads();
@@ -289,7 +288,7 @@ __global__ void __launch_bounds__(kPartThreads, 1)
                 const unsigned long long o = o0 + (i - r0);
                 const E e = S.stage[i];
                 if (o < cap) part[(unsigned long long)b * cap + o] = e;
-                else part_direct<E>(e, b, deg, parent);
+                else part_direct<E>(e, b, wb, deg, parent);
             }
         }
         __syncthreads();
@@ -349,6 +348,294 @@ __global__ void __launch_bounds__(kBlock) k_degree_window_hook(const unsigned lo
     if (i < len) one(part[(unsigned long long)b * cap + i]);
 }
 
+// Shared-memory windows (n <= 2^24). Two launches:
+//
+//  k_degree_split      two CTAs of 512 threads per SM stream 32 KB chunks of
+//                      pairs into shared memory (bulk copies, two in flight).
+//                      Each thread keeps its chunk's endpoints in registers,
+//                      takes their ranks within their windows with shared
+//                      atomics, and after one scan of the window counts and
+//                      one reservation per window and chunk stages the ids
+//                      within the windows, with their window numbers, in
+//                      window order; the block then writes the staged ids out
+//                      in that order, so each window's run is one coalesced
+//                      store. Four barriers per chunk, and the next copy into
+//                      the buffer is issued as soon as the pairs are in
+//                      registers; two CTAs per SM overlap one's reservation
+//                      round trip with the other's work.
+//  k_degree_window_smem one CTA per window of 2^wb vertices counts the
+//                      window's ids in shared memory. A vertex that holds a
+//                      large share of its window's entries (an R-MAT hub: up
+//                      to 41% of one window at scale 24) would serialise the
+//                      warps' shared atomics on one address, so the CTA first
+//                      counts a sample of the window (its first
+//                      kSmemSampleVecs * 8 entries), takes the vertex with the
+//                      largest sample count as the window's hub, and then
+//                      counts the hub's entries in registers (one shared
+//                      atomic per warp at the end) and every other entry with
+//                      a shared atomic. The counts are written to deg once,
+//                      coalesced; entries of a window past its capacity were
+//                      counted in deg directly by the split, so such a window
+//                      adds.
+//
+// HBM traffic per call: the pairs once (2wm), the ids written and read back
+// (2 x 4m), deg zeroed and written (8n).
+constexpr int kSplitThreads = 512;
+constexpr int kSplitChunk = 1 << 15;                  // bytes of pairs per chunk
+constexpr int kSplitVecs = kSplitChunk / 16;          // 16-byte vectors per chunk
+constexpr int kSplitSlots = kSplitVecs / kSplitThreads;
+constexpr int kSplitMaxEnd = kSplitChunk / 8 * 2;     // endpoints of a chunk of int32 pairs
+constexpr int kSmemThreads = 1024;
+constexpr int kSmemSampleVecs = 2048;                 // 16,384 entries
+constexpr int kSmemMaxBits = 15;                      // 128 KB of counts per CTA
+constexpr int kSmemMinBits = 11;
+
+struct __align__(128) SplitShared {
+    int4 buf[2][kSplitVecs];        // two chunks of pairs (bulk-copy destinations)
+    uint32_t stage[kSplitMaxEnd];   // window << 16 | id within the window, in window order
+    uint32_t hist[kPartMaxBuckets];
+    unsigned long long goff[kPartMaxBuckets];  // the window's region + its reservation - its first stage slot
+    uint32_t loff[kPartMaxBuckets];  // the window's first stage slot
+    uint32_t gend[kPartMaxBuckets];  // the end of its stage slots that fit in the region
+    unsigned long long mbar[2];
+    uint32_t wsum[kSplitThreads / 32];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kSplitThreads, 2)
+    k_degree_split(const T *__restrict__ edges, long long m, vid_t n, int nb, int wb, uint32_t cap,
+                   uint32_t *__restrict__ fill, uint16_t *__restrict__ part, uint32_t *deg, DevState *st) {
+    extern __shared__ __align__(128) unsigned char split_smem[];
+    SplitShared &S = *reinterpret_cast<SplitShared *>(split_smem);
+    constexpr int P = PairVec<T>::kPairs;
+    constexpr long long CP = kSplitChunk / (2 * (long long)sizeof(T));
+    constexpr int NE = kSplitSlots * P;  // pairs per thread and chunk
+    const long long nch = (m + CP - 1) / CP;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const long long G = gridDim.x;
+    const uint32_t low = (1u << wb) - 1u;
+    auto chunk_len = [&](long long c) { return m - c * CP < CP ? m - c * CP : CP; };
+    bool inflight[2] = {false, false};  // thread 0's view of the bulk copies it issued
+    auto issue = [&](long long c, int slot) {
+        const uint32_t bytes = (uint32_t)(((unsigned long long)chunk_len(c) * 2 * sizeof(T)) & ~15ull);
+        if (bytes) {
+            mbar_arrive_tx(&S.mbar[slot], bytes);
+            bulk_load(S.buf[slot], edges + 2 * c * CP, bytes, &S.mbar[slot]);
+        } else {
+            mbar_arrive(&S.mbar[slot]);
+        }
+        inflight[slot] = true;
+    };
+    if (t == 0) {
+        mbar_init(&S.mbar[0], 1);
+        mbar_init(&S.mbar[1], 1);
+        mbar_fence_init();
+    }
+    for (int i = t; i < kPartMaxBuckets; i += kSplitThreads) S.hist[i] = 0;
+    __syncthreads();
+    if (t == 0) {
+        if (blockIdx.x < nch) issue(blockIdx.x, 0);
+        if (blockIdx.x + G < nch) issue(blockIdx.x + G, 1);
+    }
+    uint32_t phase[2] = {0u, 0u};
+    bool bad = false, timed_out = false;
+    int slot = 0;
+    for (long long c = blockIdx.x; c < nch; c += G, slot ^= 1) {
+        const bool ok = mbar_wait(&S.mbar[slot], phase[slot]);
+        if (ok) phase[slot] ^= 1u;
+        const int np = (int)chunk_len(c);  // <= CP
+        const int full_vecs = (int)(((unsigned)np * 2 * sizeof(T)) >> 4);  // vectors the copy filled
+        uint32_t pu[NE], pv[NE], rk[NE];
+#pragma unroll
+        for (int k = 0; k < kSplitSlots; k++) {
+            const int sv = t + k * kSplitThreads;
+#pragma unroll
+            for (int j = 0; j < P; j++) {
+                const int p = sv * P + j;
+                uint32_t r = 0xffffffffu;
+                if (ok && p < np) {
+                    long long u, v;
+                    if (sv < full_vecs) vec_pair<T>(S.buf[slot][sv], j, u, v);
+                    else scalar_pair<T>(edges, c * CP + p, u, v);  // the odd last int32 pair
+                    // ids of int32 pairs compared as 32-bit: a negative id is above n
+                    const bool out = sizeof(T) == 4 ? ((uint32_t)u >= n || (uint32_t)v >= n)
+                                                    : ((unsigned long long)u >= n || (unsigned long long)v >= n);
+                    if (out) {
+                        bad = true;
+                    } else {
+                        pu[k * P + j] = (uint32_t)u;
+                        pv[k * P + j] = (uint32_t)v;
+                        r = atomicAdd(&S.hist[(uint32_t)u >> wb], 1u) | (atomicAdd(&S.hist[(uint32_t)v >> wb], 1u) << 16);
+                    }
+                }
+                rk[k * P + j] = r;
+            }
+        }
+        // barrier 1: the counts are complete and the buffer is read
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        if (t == 0) {
+            inflight[slot] = false;
+            if (c + 2 * G < nch) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(c + 2 * G, slot);
+            }
+        }
+        // exclusive scan of the window counts (nb <= 512 = the block), one
+        // reservation per window, counts cleared
+        uint32_t h = 0u, incl = 0u, bt = 0u;
+        if (t < nb) {
+            h = S.hist[t];
+            S.hist[t] = 0u;
+            if (h) bt = atomicAdd(&fill[t], h);
+        }
+        incl = h;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) S.wsum[warp] = incl;
+        __syncthreads();  // barrier 2
+        uint32_t w = lane < kSplitThreads / 32 ? S.wsum[lane] : 0u, wi = w;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, wi, kSplitThreads / 32 - 1);
+        const uint32_t wbase = __shfl_sync(0xffffffffu, wi - w, warp);
+        const uint32_t lo = wbase + incl - h;
+        const uint32_t fit = bt >= cap ? 0u : (cap - bt < h ? cap - bt : h);
+        S.loff[t] = lo;
+        S.gend[t] = lo + fit;
+        S.goff[t] = (unsigned long long)t * cap + bt - lo;  // mod 2^64; t < nb where h > 0
+        // barrier 3; `over`: a window of this chunk runs past its capacity
+        const int over = __syncthreads_or(fit < h);
+#pragma unroll
+        for (int k = 0; k < NE; k++) {
+            const uint32_t r = rk[k];
+            if (r == 0xffffffffu) continue;
+            const uint32_t bu = pu[k] >> wb, bv = pv[k] >> wb;
+            S.stage[S.loff[bu] + (r & 0xffffu)] = (bu << 16) | (pu[k] & low);
+            S.stage[S.loff[bv] + (r >> 16)] = (bv << 16) | (pv[k] & low);
+        }
+        __syncthreads();  // barrier 4
+        if (!over) {
+            for (uint32_t i = t; i < tot; i += kSplitThreads) {
+                const uint32_t x = S.stage[i];
+                part[S.goff[x >> 16] + i] = (uint16_t)x;
+            }
+        } else {
+            for (uint32_t i = t; i < tot; i += kSplitThreads) {
+                const uint32_t x = S.stage[i], b = x >> 16;
+                if (i < S.gend[b]) part[S.goff[b] + i] = (uint16_t)x;
+                else atomicAdd(&deg[(b << wb) | (x & 0xffffu)], 1u);
+            }
+        }
+        // the next chunk's counts go to S.hist (cleared before barrier 2);
+        // its scan rewrites loff / gend / goff only after its barrier 1
+    }
+    if (bad) set_err(st, kErrInvalidEdge);
+    if (timed_out && t == 0) {
+        set_err(st, kErrTimeout);
+        // leave no copy writing into shared memory after the block exits
+        for (int k = 0; k < 2; k++)
+            if (inflight[k]) mbar_wait(&S.mbar[k], phase[k]);
+    }
+}
+
+__device__ __forceinline__ void smem_count8(uint32_t *cnt, uint4 q) {
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        atomicAdd(&cnt[w[i] & 0xffffu], 1u);
+        atomicAdd(&cnt[w[i] >> 16], 1u);
+    }
+}
+
+__device__ __forceinline__ void smem_count8_hub(uint32_t *cnt, uint4 q, uint32_t hub, uint32_t &hc) {
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const uint32_t a = w[i] & 0xffffu, b = w[i] >> 16;
+        if (a == hub) hc++;
+        else atomicAdd(&cnt[a], 1u);
+        if (b == hub) hc++;
+        else atomicAdd(&cnt[b], 1u);
+    }
+}
+
+__global__ void __launch_bounds__(kSmemThreads, 1)
+    k_degree_window_smem(const uint16_t *__restrict__ part, uint32_t cap, const uint32_t *__restrict__ fill, int wb,
+                         vid_t n, uint32_t *deg) {
+    extern __shared__ __align__(16) uint32_t cnt[];  // 2^wb counts, then 32 words of reduction
+    uint32_t *red = cnt + (1u << wb);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int b = blockIdx.x;
+    const uint32_t W = 1u << wb;
+    for (uint32_t i = t; i < W; i += kSmemThreads) cnt[i] = 0u;
+    __syncthreads();
+    const unsigned long long f = fill[b], len = f < cap ? f : cap;
+    const uint16_t *p = part + (unsigned long long)b * cap;  // 16-byte aligned: cap is a multiple of 8
+    const uint4 *p4 = reinterpret_cast<const uint4 *>(p);
+    const unsigned long long nv = len >> 3;
+    const unsigned long long ns = nv < (unsigned long long)kSmemSampleVecs ? nv : (unsigned long long)kSmemSampleVecs;
+    for (unsigned long long k = t; k < ns; k += kSmemThreads) smem_count8(cnt, __ldcs(p4 + k));
+    __syncthreads();
+    // the hub: the largest sample count (< 2^15 + 1), as count << 16 | id
+    uint32_t key = 0u;
+    for (uint32_t i = t; i < W; i += kSmemThreads) {
+        const uint32_t c = cnt[i];
+        const uint32_t k2 = (c << 16) | i;
+        if (c && k2 > key) key = k2;
+    }
+    key = __reduce_max_sync(0xffffffffu, key);
+    if (lane == 0) red[warp] = key;
+    __syncthreads();
+    if (warp == 0) {
+        key = __reduce_max_sync(0xffffffffu, red[lane]);
+        if (lane == 0) red[0] = key;
+    }
+    __syncthreads();
+    key = red[0];
+    const uint32_t hub = key ? (key & 0xffffu) : 0x10000u;  // no entry equals 0x10000
+    uint32_t hc = 0u;
+    constexpr int U = 8;
+    for (unsigned long long k = ns + t; k < nv; k += (unsigned long long)U * kSmemThreads) {
+        uint4 q[U];
+#pragma unroll
+        for (int j = 0; j < U; j++) {
+            const unsigned long long kk = k + (unsigned long long)j * kSmemThreads;
+            if (kk < nv) q[j] = __ldcs(p4 + kk);
+        }
+#pragma unroll
+        for (int j = 0; j < U; j++)
+            if (k + (unsigned long long)j * kSmemThreads < nv) smem_count8_hub(cnt, q[j], hub, hc);
+    }
+    {
+        const unsigned long long i = nv * 8 + t;  // the last len % 8 entries
+        if (i < len) {
+            const uint32_t e = p[i];
+            if (e == hub) hc++;
+            else atomicAdd(&cnt[e], 1u);
+        }
+    }
+    hc = __reduce_add_sync(0xffffffffu, hc);
+    if (lane == 0 && hc) atomicAdd(&cnt[hub], hc);
+    __syncthreads();
+    const unsigned long long x0 = (unsigned long long)b << wb;
+    const uint32_t lim = (unsigned long long)n - x0 < W ? (uint32_t)((unsigned long long)n - x0) : W;
+    uint32_t *d = deg + x0;
+    if (f > cap) {
+        for (uint32_t i = t; i < lim; i += kSmemThreads) d[i] += cnt[i];
+    } else {
+        for (uint32_t i = t; i < lim; i += kSmemThreads) d[i] = cnt[i];
+    }
+}
+
 // ---------------------------------------------------------------------------
 int degree_part_buckets(vid_t n) { return (int)(((long long)n + (1LL << kPartBits) - 1) >> kPartBits); }
 
@@ -388,7 +675,7 @@ void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t
         const int pgrid = (int)(nch < num_sms ? nch : num_sms);
         if (pgrid > 0)
             k_degree_partition<T, E><<<pgrid, kPartThreads, sizeof(PartShared<E>), s>>>(
-                (const T *)edges, m, n, nb, cap, fill, (E *)part, deg, hook, st);
+                (const T *)edges, m, n, nb, kPartBits, cap, fill, (E *)part, deg, hook, st);
         for (int b = 0; b < nb; b++) k_degree_window_hook<<<grid, kBlock, 0, s>>>((E *)part, cap, fill, b, deg, hook);
     } else {
         using E = uint32_t;
@@ -396,7 +683,7 @@ void launch_degree_partitioned(const void *edges, long long m, vid_t n, uint32_t
         const int pgrid = (int)(nch < num_sms ? nch : num_sms);
         if (pgrid > 0)
             k_degree_partition<T, E><<<pgrid, kPartThreads, sizeof(PartShared<E>), s>>>(
-                (const T *)edges, m, n, nb, cap, fill, (E *)part, deg, nullptr, st);
+                (const T *)edges, m, n, nb, kPartBits, cap, fill, (E *)part, deg, nullptr, st);
         for (int b = 0; b < nb; b++) k_degree_window<<<grid, kBlock, 0, s>>>((E *)part, cap, fill, b, deg);
     }
 }
@@ -405,14 +692,70 @@ template void launch_degree_partitioned<int32_t>(const void *, long long, vid_t,
 template void launch_degree_partitioned<int64_t>(const void *, long long, vid_t, uint32_t *, vid_t *, void *,
                                                  DevState *, int, int, cudaStream_t);
 
+// Shared-memory windows: the smallest window of at least 2^11 vertices that
+// gives at most kPartMaxBuckets windows (n <= 2^24: 2^15 vertices at most).
+bool degree_smem_ok(vid_t n, long long m) {
+    return n >= (1u << 20) && n <= (1u << 24) && m >= (1LL << 22);
+}
+
+static int smem_window_bits(vid_t n) {
+    int wb = kSmemMinBits;
+    while (wb < kSmemMaxBits && (((long long)n + (1LL << wb) - 1) >> wb) > kPartMaxBuckets) wb++;
+    return wb;
+}
+
+static int smem_buckets(vid_t n) {
+    const int wb = smem_window_bits(n);
+    return (int)(((long long)n + (1LL << wb) - 1) >> wb);
+}
+
+// As part_cap, a multiple of 8 (16 bytes of 16-bit entries).
+static unsigned long long smem_cap(vid_t n, long long m) {
+    const int nb = smem_buckets(n);
+    const unsigned long long avg = (2ull * (unsigned long long)m + nb - 1) / nb;
+    return (avg + avg / 2 + 4096 + 7) & ~7ull;
+}
+
+size_t degree_smem_scratch_bytes(vid_t n, long long m) {
+    const int nb = smem_buckets(n);
+    return part_offset(nb) + (size_t)nb * smem_cap(n, m) * 2;
+}
+
+template <typename T>
+void launch_degree_smem(const void *edges, long long m, vid_t n, uint32_t *deg, void *scratch, DevState *st,
+                        int num_sms, cudaStream_t s) {
+    const int wb = smem_window_bits(n), nb = smem_buckets(n);
+    const uint32_t cap = (uint32_t)smem_cap(n, m);
+    uint32_t *fill = reinterpret_cast<uint32_t *>(scratch);
+    uint16_t *part = reinterpret_cast<uint16_t *>(static_cast<char *>(scratch) + part_offset(nb));
+    cudaMemsetAsync(fill, 0, (size_t)nb * 4, s);
+    cudaMemsetAsync(deg, 0, (size_t)n * 4, s);
+    constexpr long long CP = kSplitChunk / (2 * (long long)sizeof(T));
+    const long long nch = (m + CP - 1) / CP;
+    const int pgrid = (int)(nch < 2LL * num_sms ? nch : 2LL * num_sms);
+    if (pgrid > 0)
+        k_degree_split<T><<<pgrid, kSplitThreads, sizeof(SplitShared), s>>>((const T *)edges, m, n, nb, wb, cap, fill,
+                                                                             part, deg, st);
+    k_degree_window_smem<<<nb, kSmemThreads, (4u << wb) + 128, s>>>(part, cap, fill, wb, n, deg);
+}
+template void launch_degree_smem<int32_t>(const void *, long long, vid_t, uint32_t *, void *, DevState *, int,
+                                          cudaStream_t);
+template void launch_degree_smem<int64_t>(const void *, long long, vid_t, uint32_t *, void *, DevState *, int,
+                                          cudaStream_t);
+
 cudaError_t degree_part_setup() {
     const void *ks[] = {(const void *)k_degree_partition<int32_t, uint32_t>,
                         (const void *)k_degree_partition<int64_t, uint32_t>,
                         (const void *)k_degree_partition<int32_t, unsigned long long>,
-                        (const void *)k_degree_partition<int64_t, unsigned long long>};
-    const int sm[] = {(int)sizeof(PartShared<uint32_t>), (int)sizeof(PartShared<uint32_t>),
-                      (int)sizeof(PartShared<unsigned long long>), (int)sizeof(PartShared<unsigned long long>)};
-    for (int i = 0; i < 4; i++) {
+                        (const void *)k_degree_partition<int64_t, unsigned long long>,
+                        (const void *)k_degree_split<int32_t>,
+                        (const void *)k_degree_split<int64_t>,
+                        (const void *)k_degree_window_smem};
+    const int sm[] = {(int)sizeof(PartShared<uint32_t>),           (int)sizeof(PartShared<uint32_t>),
+                      (int)sizeof(PartShared<unsigned long long>), (int)sizeof(PartShared<unsigned long long>),
+                      (int)sizeof(SplitShared),                    (int)sizeof(SplitShared),
+                      (4 << kSmemMaxBits) + 128};
+    for (int i = 0; i < 7; i++) {
         const cudaError_t e = cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, sm[i]);
         if (e != cudaSuccess) return e;
     }

@@ -61,6 +61,9 @@ def test_gather_passes_count_survivors():
     ("void ccg::k_degree_hubs<int, 24576, 1024, 1>(const T1 *, long long)", "degree"),
     ("ccg::k_hub_select(const unsigned int *)", "degree"),
     ("void ccg::k_degree<long>(const T1 *)", "degree"),
+    ("void ccg::k_degree_partition<int, unsigned short>(const T1 *, long long)", "degree"),
+    ("ccg::k_degree_window_smem(const unsigned short *, unsigned long long)", "degree"),
+    ("ccg::k_degree_window_hook(const unsigned long long *, unsigned long long)", "degree"),
     ("void ccg::k_sv_sample<int, 2>(const T1 *)", "sv_first"),
     ("void ccg::k_sv_pass<int, 0, 0, 0>(const T1 *)", "sv_first"),
     ("void ccg::k_sv_pass<long, 2, 1, 1>(const T1 *)", "sv_gather_input"),

@@ -343,7 +343,9 @@ def _degree_check(e, n, id_bytes):
     deg, hist = eng.degree_distribution(torch.from_numpy(e).cuda(), n, hist_len=int(deg_o.max()) + 1)
     assert np.array_equal(deg.cpu().numpy().astype(np.int64), deg_o)
     assert np.array_equal(hist.cpu().numpy(), oracle.histogram(deg_o))
+    st = eng.stats()
     eng.close()
+    return st
 
 
 @pytest.mark.parametrize("id_bytes,m,n", [
@@ -359,7 +361,7 @@ def test_partitioned_degree_pass_chunks_and_windows(id_bytes, m, n):
     rng = np.random.default_rng(m % 1000 + n % 1000)
     e = rng.integers(0, n, size=(m, 2)).astype(np.int32 if id_bytes == 4 else np.int64)
     e[::97, 1] = e[::97, 0]  # self-loops
-    _degree_check(e, n, id_bytes)
+    assert _degree_check(e, n, id_bytes)["degree_form"] == 3
 
 
 @pytest.mark.parametrize("id_bytes,m,n", [
@@ -401,17 +403,18 @@ def test_partitioned_degree_pass_window_overflow():
 
 @pytest.mark.parametrize("id_bytes,extra", [(4, 0), (4, 3), (8, 1)])
 def test_hub_aware_degree_pass(id_bytes, extra):
-    """m >= 2^24 with n <= 2^25 takes the hub-aware degree pass (prefix counts
-    pick the hubs, the rest is counted with hubs in shared memory); counts
-    stay exact."""
-    g = gg.rmat(seed=31, scale=20, edge_factor=16, m=(1 << 24) + extra, id_bytes=id_bytes)
+    """m >= 2^24 with n < 2^20 (or 2^24 < n <= 2^25) takes the hub-aware
+    degree pass (prefix counts pick the hubs, the rest is counted with hubs in
+    shared memory); counts stay exact."""
+    g = gg.rmat(seed=31, scale=19, edge_factor=32, m=(1 << 24) + extra, id_bytes=id_bytes)
     # hubs whose pairs mostly come after the prefix
     hub = np.stack([np.full(300000, 77), np.arange(300000) * 7 % g.n], axis=1).astype(g.edges.dtype)
     e = np.concatenate([g.edges, hub])
-    _degree_check(e, g.n, id_bytes)
+    assert _degree_check(e, g.n, id_bytes)["degree_form"] == 2
     got, st = run_engine(e, g.n, route="auto")
     assert np.array_equal(got, oracle.cc_labels(e, g.n, cross_check=False))
     assert st["max_degree"] == int(oracle.degrees(e, g.n).max())
+    assert st["degree_form"] == 2
 
 
 @pytest.mark.gpu
@@ -426,17 +429,59 @@ def test_hub_aware_degree_pass_extremes(kind):
     m = (1 << 24) + 5
     rng = np.random.default_rng(41)
     if kind == "uniform":
-        n = 1 << 23
+        n = (1 << 24) + 12345
         e = rng.integers(0, n, size=(m, 2), dtype=np.int64).astype(np.int32)
     else:
-        n = 1 << 20
+        n = (1 << 20) - 1
         e = np.stack([np.full(m, 12345), rng.integers(0, n, size=m)], axis=1).astype(np.int32)
     deg_o = oracle.degrees(e, n)
     eng = cc.Engine(id_bytes=4)
     deg, hist = eng.degree_distribution(torch.from_numpy(e).cuda(), n, hist_len=int(deg_o.max()) + 1)
     assert np.array_equal(deg.cpu().numpy().astype(np.int64), deg_o)
     assert np.array_equal(hist.cpu().numpy(), oracle.histogram(deg_o))
+    assert eng.stats()["degree_form"] == 2
     eng.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("id_bytes,m,n", [
+    (4, (1 << 22) + 7, 1 << 24),          # 512 windows of 2^15 vertices, a ragged last chunk
+    (8, (1 << 22) + 4097, 3_000_001),     # int64; 367 windows of 2^13, the last one short
+    (4, (1 << 22) + 1, 1 << 20),          # 512 windows of 2^11 (the smallest)
+])
+def test_shared_window_degree_pass(id_bytes, m, n):
+    """2^20 <= n <= 2^24 with m >= 2^22: the endpoints are partitioned into at
+    most 512 windows of at most 2^15 vertices (16-bit entries) and each window
+    is counted in shared memory, its sampled hub in registers. Counts exact
+    with a hub that holds about 30% of its window (within the window's
+    capacity), a second heavy vertex in the same window, a star vertex whose
+    window runs far past its capacity (the rest counted in global memory), and
+    self-loops; labels exact on the heuristic route through that pass."""
+    rng = np.random.default_rng(n % 997 + m % 991)
+    dt = np.int32 if id_bytes == 4 else np.int64
+    e = rng.integers(0, n, size=(m, 2))
+    wb = 11
+    while (n + (1 << wb) - 1) >> wb > 512:
+        wb += 1
+    avg = 2 * m // ((n + (1 << wb) - 1) >> wb)
+    h1 = (n // 2) | 5
+    h2 = h1 ^ 3  # the same window
+    star = 7
+    rows = rng.permutation(m)
+    k1, k2, k3 = int(0.45 * avg), avg // 10, m // 8  # h1 and h2 stay within 1.5x the average
+    e[rows[:k1], 0] = h1
+    e[rows[k1:k1 + k2], 1] = h2
+    e[rows[k1 + k2:k1 + k2 + k3], 0] = star
+    e[::97, 1] = e[::97, 0]
+    e = np.ascontiguousarray(e.astype(dt))
+    assert _degree_check(e, n, id_bytes)["degree_form"] == 4
+    want = oracle.cc_labels(e, n, cross_check=False)
+    # graphs of at most 2^20 vertices and 2m < 4096 * 4097 take the one-block
+    # fit, whose degree pass is one atomic per endpoint
+    form = 1 if n <= (1 << 20) and 2 * m < 4096 * 4097 else 4
+    for profile in (0, 1):
+        out = assert_labels_match(e, n, want=want, routes=("auto",), profile=profile)
+        assert out["auto"]["degree_form"] == form
 
 
 @pytest.mark.parametrize("maker", [
