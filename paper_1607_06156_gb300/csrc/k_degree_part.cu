@@ -390,26 +390,33 @@ constexpr int kSmemSampleVecs = 2048;                 // 16,384 entries
 constexpr int kSmemMaxBits = 15;                      // 128 KB of counts per CTA
 constexpr int kSmemMinBits = 11;
 
+constexpr int kSplitWpt = kPartMaxBuckets / kSplitThreads;  // windows per thread in the scan
+
+// I: the type of a window's offset into the regions (uint32_t when all the
+// regions hold fewer than 2^32 entries).
+template <typename I>
 struct __align__(128) SplitShared {
     int4 buf[2][kSplitVecs];        // two chunks of pairs (bulk-copy destinations)
-    uint32_t stage[kSplitMaxEnd];   // window << 16 | id within the window, in window order
+    uint32_t stage[kSplitMaxEnd + kPartMaxBuckets];  // window << 16 | id within the window, in window order
+                                                     // (each window's run padded to even length)
     uint32_t hist[kPartMaxBuckets];
-    unsigned long long goff[kPartMaxBuckets];  // the window's region + its reservation - its first stage slot
-    uint32_t loff[kPartMaxBuckets];  // the window's first stage slot
-    uint32_t gend[kPartMaxBuckets];  // the end of its stage slots that fit in the region
+    I goff[kPartMaxBuckets];        // the window's region + its reservation - its first stage slot
+    uint32_t loff[kPartMaxBuckets]; // the window's first stage slot
+    uint32_t gend[kPartMaxBuckets]; // the end of its stage slots that fit in the region
     unsigned long long mbar[2];
     uint32_t wsum[kSplitThreads / 32];
 };
 
-template <typename T>
+template <typename T, typename I>
 __global__ void __launch_bounds__(kSplitThreads, 2)
     k_degree_split(const T *__restrict__ edges, long long m, vid_t n, int nb, int wb, uint32_t cap,
                    uint32_t *__restrict__ fill, uint16_t *__restrict__ part, uint32_t *deg, DevState *st) {
     extern __shared__ __align__(128) unsigned char split_smem[];
-    SplitShared &S = *reinterpret_cast<SplitShared *>(split_smem);
+    SplitShared<I> &S = *reinterpret_cast<SplitShared<I> *>(split_smem);
     constexpr int P = PairVec<T>::kPairs;
     constexpr long long CP = kSplitChunk / (2 * (long long)sizeof(T));
     constexpr int NE = kSplitSlots * P;  // pairs per thread and chunk
+    constexpr int NW = kSplitThreads / 32;
     const long long nch = (m + CP - 1) / CP;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const long long G = gridDim.x;
@@ -483,15 +490,26 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
                 issue(c + 2 * G, slot);
             }
         }
-        // exclusive scan of the window counts (nb <= 512 = the block), one
-        // reservation per window, counts cleared
-        uint32_t h = 0u, incl = 0u, bt = 0u;
-        if (t < nb) {
-            h = S.hist[t];
-            S.hist[t] = 0u;
-            if (h) bt = atomicAdd(&fill[t], h);
+        // exclusive scan of the window counts (thread t: windows t * kSplitWpt
+        // and on), one reservation per window, counts cleared
+        // A window's run is padded to an even length with the id 2^wb (a
+        // count slot past the window's counts), so that every run starts on
+        // an even stage slot and an even region offset: the runs are written
+        // two ids per 32-bit store.
+        uint32_t h[kSplitWpt], bt[kSplitWpt], hs = 0u;
+#pragma unroll
+        for (int q = 0; q < kSplitWpt; q++) {
+            const int b = t * kSplitWpt + q;
+            h[q] = 0u;
+            bt[q] = 0u;
+            if (b < nb) {
+                h[q] = S.hist[b];
+                S.hist[b] = 0u;
+                if (h[q]) bt[q] = atomicAdd(&fill[b], (h[q] + 1u) & ~1u);
+            }
+            hs += (h[q] + 1u) & ~1u;
         }
-        incl = h;
+        uint32_t incl = hs;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -499,21 +517,29 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
         }
         if (lane == 31) S.wsum[warp] = incl;
         __syncthreads();  // barrier 2
-        uint32_t w = lane < kSplitThreads / 32 ? S.wsum[lane] : 0u, wi = w;
+        uint32_t w = lane < NW ? S.wsum[lane] : 0u, wi = w;
 #pragma unroll
-        for (int o = 1; o < 16; o <<= 1) {
+        for (int o = 1; o < NW; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
             if (lane >= o) wi += y;
         }
-        const uint32_t tot = __shfl_sync(0xffffffffu, wi, kSplitThreads / 32 - 1);
-        const uint32_t wbase = __shfl_sync(0xffffffffu, wi - w, warp);
-        const uint32_t lo = wbase + incl - h;
-        const uint32_t fit = bt >= cap ? 0u : (cap - bt < h ? cap - bt : h);
-        S.loff[t] = lo;
-        S.gend[t] = lo + fit;
-        S.goff[t] = (unsigned long long)t * cap + bt - lo;  // mod 2^64; t < nb where h > 0
+        const uint32_t tot = __shfl_sync(0xffffffffu, wi, NW - 1);
+        uint32_t lo = __shfl_sync(0xffffffffu, wi - w, warp) + incl - hs;
+        bool short_fit = false;
+#pragma unroll
+        for (int q = 0; q < kSplitWpt; q++) {
+            const int b = t * kSplitWpt + q;
+            const uint32_t hp = (h[q] + 1u) & ~1u;
+            const uint32_t fit = bt[q] >= cap ? 0u : (cap - bt[q] < hp ? cap - bt[q] : hp);  // even: cap, bt even
+            S.loff[b] = lo;
+            S.gend[b] = lo + fit;
+            S.goff[b] = (I)((unsigned long long)b * cap + bt[q] - lo);  // mod 2^bits; read only where h > 0
+            if (h[q] & 1u) S.stage[lo + h[q]] = ((uint32_t)b << 16) | (1u << wb);  // the pad
+            short_fit |= fit < hp;
+            lo += hp;
+        }
         // barrier 3; `over`: a window of this chunk runs past its capacity
-        const int over = __syncthreads_or(fit < h);
+        const int over = __syncthreads_or(short_fit);
 #pragma unroll
         for (int k = 0; k < NE; k++) {
             const uint32_t r = rk[k];
@@ -523,16 +549,22 @@ __global__ void __launch_bounds__(kSplitThreads, 2)
             S.stage[S.loff[bv] + (r >> 16)] = (bv << 16) | (pv[k] & low);
         }
         __syncthreads();  // barrier 4
+        // stage slots 2i and 2i + 1 hold ids of one window (tot is even)
         if (!over) {
-            for (uint32_t i = t; i < tot; i += kSplitThreads) {
-                const uint32_t x = S.stage[i];
-                part[S.goff[x >> 16] + i] = (uint16_t)x;
+            for (uint32_t i = 2 * t; i < tot; i += 2 * kSplitThreads) {
+                const uint2 x = *reinterpret_cast<const uint2 *>(&S.stage[i]);
+                *reinterpret_cast<uint32_t *>(&part[S.goff[x.x >> 16] + (I)i]) = (x.x & 0xffffu) | (x.y << 16);
             }
         } else {
-            for (uint32_t i = t; i < tot; i += kSplitThreads) {
-                const uint32_t x = S.stage[i], b = x >> 16;
-                if (i < S.gend[b]) part[S.goff[b] + i] = (uint16_t)x;
-                else atomicAdd(&deg[(b << wb) | (x & 0xffffu)], 1u);
+            for (uint32_t i = 2 * t; i < tot; i += 2 * kSplitThreads) {
+                const uint2 x = *reinterpret_cast<const uint2 *>(&S.stage[i]);
+                const uint32_t b = x.x >> 16;
+                if (i < S.gend[b]) {
+                    *reinterpret_cast<uint32_t *>(&part[S.goff[b] + (I)i]) = (x.x & 0xffffu) | (x.y << 16);
+                } else {  // past the region: counted here (a pad counts nothing)
+                    atomicAdd(&deg[(b << wb) | (x.x & 0xffffu)], 1u);
+                    if ((x.y & 0xffffu) >> wb == 0u) atomicAdd(&deg[(b << wb) | (x.y & 0xffffu)], 1u);
+                }
             }
         }
         // the next chunk's counts go to S.hist (cleared before barrier 2);
@@ -571,12 +603,12 @@ __device__ __forceinline__ void smem_count8_hub(uint32_t *cnt, uint4 q, uint32_t
 __global__ void __launch_bounds__(kSmemThreads, 1)
     k_degree_window_smem(const uint16_t *__restrict__ part, uint32_t cap, const uint32_t *__restrict__ fill, int wb,
                          vid_t n, uint32_t *deg) {
-    extern __shared__ __align__(16) uint32_t cnt[];  // 2^wb counts, then 32 words of reduction
-    uint32_t *red = cnt + (1u << wb);
+    extern __shared__ __align__(16) uint32_t cnt[];  // 2^wb counts, the pads' slot, then 32 words of reduction
+    uint32_t *red = cnt + (1u << wb) + 32;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int b = blockIdx.x;
     const uint32_t W = 1u << wb;
-    for (uint32_t i = t; i < W; i += kSmemThreads) cnt[i] = 0u;
+    for (uint32_t i = t; i <= W; i += kSmemThreads) cnt[i] = 0u;
     __syncthreads();
     const unsigned long long f = fill[b], len = f < cap ? f : cap;
     const uint16_t *p = part + (unsigned long long)b * cap;  // 16-byte aligned: cap is a multiple of 8
@@ -733,10 +765,15 @@ void launch_degree_smem(const void *edges, long long m, vid_t n, uint32_t *deg, 
     constexpr long long CP = kSplitChunk / (2 * (long long)sizeof(T));
     const long long nch = (m + CP - 1) / CP;
     const int pgrid = (int)(nch < 2LL * num_sms ? nch : 2LL * num_sms);
-    if (pgrid > 0)
-        k_degree_split<T><<<pgrid, kSplitThreads, sizeof(SplitShared), s>>>((const T *)edges, m, n, nb, wb, cap, fill,
-                                                                             part, deg, st);
-    k_degree_window_smem<<<nb, kSmemThreads, (4u << wb) + 128, s>>>(part, cap, fill, wb, n, deg);
+    if (pgrid > 0) {
+        if ((unsigned long long)nb * cap < (1ull << 32))
+            k_degree_split<T, uint32_t><<<pgrid, kSplitThreads, sizeof(SplitShared<uint32_t>), s>>>(
+                (const T *)edges, m, n, nb, wb, cap, fill, part, deg, st);
+        else
+            k_degree_split<T, unsigned long long><<<pgrid, kSplitThreads, sizeof(SplitShared<unsigned long long>), s>>>(
+                (const T *)edges, m, n, nb, wb, cap, fill, part, deg, st);
+    }
+    k_degree_window_smem<<<nb, kSmemThreads, (4u << wb) + 256, s>>>(part, cap, fill, wb, n, deg);
 }
 template void launch_degree_smem<int32_t>(const void *, long long, vid_t, uint32_t *, void *, DevState *, int,
                                           cudaStream_t);
@@ -748,14 +785,17 @@ cudaError_t degree_part_setup() {
                         (const void *)k_degree_partition<int64_t, uint32_t>,
                         (const void *)k_degree_partition<int32_t, unsigned long long>,
                         (const void *)k_degree_partition<int64_t, unsigned long long>,
-                        (const void *)k_degree_split<int32_t>,
-                        (const void *)k_degree_split<int64_t>,
+                        (const void *)k_degree_split<int32_t, uint32_t>,
+                        (const void *)k_degree_split<int64_t, uint32_t>,
+                        (const void *)k_degree_split<int32_t, unsigned long long>,
+                        (const void *)k_degree_split<int64_t, unsigned long long>,
                         (const void *)k_degree_window_smem};
     const int sm[] = {(int)sizeof(PartShared<uint32_t>),           (int)sizeof(PartShared<uint32_t>),
                       (int)sizeof(PartShared<unsigned long long>), (int)sizeof(PartShared<unsigned long long>),
-                      (int)sizeof(SplitShared),                    (int)sizeof(SplitShared),
-                      (4 << kSmemMaxBits) + 128};
-    for (int i = 0; i < 7; i++) {
+                      (int)sizeof(SplitShared<uint32_t>),          (int)sizeof(SplitShared<uint32_t>),
+                      (int)sizeof(SplitShared<unsigned long long>), (int)sizeof(SplitShared<unsigned long long>),
+                      (4 << kSmemMaxBits) + 256};
+    for (int i = 0; i < 9; i++) {
         const cudaError_t e = cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, sm[i]);
         if (e != cudaSuccess) return e;
     }
