@@ -63,6 +63,7 @@ CLASS_FILES = {
     "degree": ["cc_common.cuh", "k_degree.cu", "k_degree_part.cu", "launch_cfg.cu"],
     "hist": ["cc_common.cuh", "k_degree.cu", "launch_cfg.cu"],
     "ks": ["cc_common.cuh", "ks_math.cuh", "k_degree.cu", "launch_cfg.cu"],
+    "sv_gather_input": ["cc_common.cuh", "k_sv.cu", "launch_cfg.cu"],
 }
 
 
@@ -183,6 +184,10 @@ def ncu_traffic(kernel_cls: str, workload: str):
         d = json.load(open(p))
     except (OSError, ValueError):
         return None
+    if "classes" in d:  # one capture per kernel class
+        d = d["classes"].get(kernel_cls)
+        if d is None:
+            return None
     cls = d.get("kernel_class")
     if cls is not None and cls != kernel_cls:
         return None
@@ -209,7 +214,7 @@ def kernel_class(name: str):
         return None
     if "k_sv_pass_loop" in name:  # the list pass inside the graph's WHILE node
         return "sv_gather_list"
-    table = [("k_degree_partition", "degree"), ("k_degree_window", "degree"), ("k_degree_count", "degree"), ("k_degree_hubs", "degree"), ("k_hub_", "degree"), ("k_degree<", "degree"), ("k_hist", "hist"),
+    table = [("k_degree_partition", "degree"), ("k_degree_split", "degree"), ("k_degree_window", "degree"), ("k_degree_count", "degree"), ("k_degree_hubs", "degree"), ("k_hub_", "degree"), ("k_degree<", "degree"), ("k_hist", "hist"),
              ("k_distinct", "ks"), ("k_ks_", "ks"), ("k_parent_init", "parent_init"), ("k_sv_sample", "sv_first"),
              ("k_shortcut_all", "sv_shortcut"), ("k_sv_shortcut", "sv_shortcut"), ("k_finalize", "finalize")]
     for key, cls in table:

@@ -63,6 +63,7 @@ def test_gather_passes_count_survivors():
     ("void ccg::k_degree<long>(const T1 *)", "degree"),
     ("void ccg::k_degree_partition<int, unsigned short>(const T1 *, long long)", "degree"),
     ("ccg::k_degree_window_smem(const unsigned short *, unsigned long long)", "degree"),
+    ("void ccg::k_degree_split<int, unsigned int>(const T1 *, long long)", "degree"),
     ("ccg::k_degree_window_hook(const unsigned long long *, unsigned long long)", "degree"),
     ("void ccg::k_sv_sample<int, 2>(const T1 *)", "sv_first"),
     ("void ccg::k_sv_pass<int, 0, 0, 0>(const T1 *)", "sv_first"),
@@ -150,3 +151,33 @@ def test_class_capture_is_tied_to_that_class_sources(tmp_path, monkeypatch):
     assert bench.ncu_traffic("degree", "rmat22") == pytest.approx(1000.0)
     (src / "k_degree.cu").write_text("// the class's own kernel changed")
     assert bench.ncu_traffic("degree", "rmat22") is None
+
+
+def test_traffic_file_with_one_record_per_class(tmp_path, monkeypatch):
+    """A traffic file may hold one capture per kernel class ("classes"): each
+    class is served from its own record and voided by its own sources only."""
+    recs = {}
+    for cls, name, rd in (("degree", "void ccg::k_degree_split<int, unsigned int>(x)", 700),
+                          ("sv_gather_input", "void ccg::k_sv_pass<int, 2, 1, 1>(x)", 400)):
+        rows = [["ID", "Kernel Name", "Metric Name", "Metric Value"]]
+        for i in range(2):
+            rows.append([str(i), name, "dram__bytes_read.sum", str(rd)])
+            rows.append([str(i), name, "dram__bytes_write.sum", "100"])
+        p = tmp_path / f"{cls}.csv"
+        with open(p, "w", newline="") as f:
+            csv.writer(f, quoting=csv.QUOTE_ALL).writerows(rows)
+        recs[cls] = bench.ncu_summary(str(p), "rmat24", {}, "cmd", calls=2, kernel_cls=cls)
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "ncu_traffic.json").write_text(json.dumps({"classes": recs}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    src = tmp_path / "paper_1607_06156_gb300" / "csrc"
+    src.mkdir(parents=True)
+    for f in set(bench.KERNEL_FILES) | set(bench.CLASS_FILES["degree"]) | set(bench.CLASS_FILES["sv_gather_input"]):
+        (src / f).write_bytes(open(os.path.join(ROOT, "paper_1607_06156_gb300", "csrc", f), "rb").read())
+    assert bench.ncu_traffic("degree", "rmat24") == pytest.approx(800.0)
+    assert bench.ncu_traffic("sv_gather_input", "rmat24") == pytest.approx(500.0)
+    assert bench.ncu_traffic("hist", "rmat24") is None
+    (src / "k_sv.cu").write_text("// the gather pass changed")
+    assert bench.ncu_traffic("sv_gather_input", "rmat24") is None
+    assert bench.ncu_traffic("degree", "rmat24") == pytest.approx(800.0)
