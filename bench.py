@@ -146,6 +146,8 @@ def l2_ops(cls: str, st: dict) -> tuple[float, str]:
     n, m = st["n"], st["m"]
     act = st["m_active"]
     if cls == "degree":
+        if st.get("degree_form") == 4:      # the increments are in shared memory, not L2
+            return 0.0, "red_add"
         return 2.0 * m, "red_add"            # one increment per pair endpoint
     if cls == "sv_first":
         k = st.get("sv_sample_stride", 1) or 1
@@ -913,8 +915,8 @@ def main() -> int:
             kv["l2_gops"] = ops / (kv["ms_per_step"] / 1e3) / 1e9
             kv["l2_frac"] = kv["l2_gops"] * 1e9 / rates[op]
     l2_roofline = None
-    if rates:
-        ops, op = l2_ops(dom, last)
+    ops, op = l2_ops(dom, last)
+    if rates and ops > 0:
         l2_roofline = {"bound": "l2_random_ops", "kernel": dom, "op": op,
                        "ops_per_launch": ops / launches_per_call,
                        "achieved": ops / launches_per_call / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0,

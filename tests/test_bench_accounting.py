@@ -29,6 +29,9 @@ def test_degree_and_labels_bytes():
     # read the parents, write the labels of the id width
     assert bench.alg_bytes("finalize", st, 8) == 4 * (1 << 20) + 8 * (1 << 20)
     assert bench.l2_ops("degree", st) == (2.0 * (1 << 24), "red_add")
+    # the shared-memory form makes no L2 increments
+    assert bench.l2_ops("degree", dict(st, degree_form=4))[0] == 0.0
+    assert bench.l2_ops("degree", dict(st, degree_form=3))[0] == 2.0 * (1 << 24)
 
 
 def test_first_pass_variants():
