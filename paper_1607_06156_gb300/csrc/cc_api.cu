@@ -53,6 +53,7 @@ struct cc_ctx {
     Buf deg, parent, hooked, ebuf0, ebuf1, hist, ovf, ks_xs, ks_cnt, ks_cum, ks_lnx, ks_Dc, ks_Ac, ks_Zc, ks_Df, chunk_nz,
         chunk_mass, st, bk_off;
     Buf dpart;  // endpoints partitioned into vertex windows (degree pass of graphs with n > 2^25)
+    Buf bwin;   // the batched degree pass's window tables and regions
     Buf bfs_own, bfs_tmin;  // multi-start BFS: the tree of every vertex, the minimum of every tree
     unsigned long long ovf_cap = 0, ks_cap = 0;
     // BFS workspace
@@ -1427,7 +1428,7 @@ std::vector<unsigned char> route_key(cc_ctx *ctx, int tbytes, long long n, long 
     struct {
         long long n, m;
         const void *edges, *labels;
-        const void *bufs[26];
+        const void *bufs[27];
         cc_options opt;
         double min_conf;
         int tbytes, cap, grid, have_pred;
@@ -1441,8 +1442,8 @@ std::vector<unsigned char> route_key(cc_ctx *ctx, int tbytes, long long n, long 
                       &ctx->ovf,  &ctx->st,      &ctx->dpart,  &ctx->row_ptr, &ctx->col,   &ctx->vis,
                       &ctx->fb,   &ctx->nb,      &ctx->q0,     &ctx->q1,      &ctx->dq,    &ctx->off,
                       &ctx->tsum, &ctx->f_vis,   &ctx->f_f0,   &ctx->f_f1,    &ctx->kb_D,  &ctx->csr_entries,
-                      &ctx->bfs_own, &ctx->bfs_tmin};
-    for (int i = 0; i < 26; i++) k.bufs[i] = b[i]->p;
+                      &ctx->bfs_own, &ctx->bfs_tmin, &ctx->bwin};
+    for (int i = 0; i < 27; i++) k.bufs[i] = b[i]->p;
     k.opt = ctx->opt;
     k.min_conf = ctx->pred_min_conf;
     k.tbytes = tbytes;
@@ -1911,6 +1912,31 @@ unsigned long long *tile_queue(cc_ctx *ctx) {
     return counter_at<unsigned long long>(ctx->counters, kCtrTileQueue);
 }
 
+// The degree pass of a batch in shared-memory windows when its scratch is
+// reserved (ensure_batch_win, before any capture), else one L2 atomic per
+// endpoint (k_degree_batch, `regions` of the pairs side by side). With `hook`
+// either applies the first hook pass as well. Returns true for the windows.
+bool batch_win(const cc_ctx *ctx, long long m, long long n, int G) {
+    return degree_batch_win_ok(m, n) && ctx->bwin.bytes >= batch_win_scratch_bytes(m, n, G);
+}
+
+cc_status ensure_batch_win(cc_ctx *ctx, long long m, long long n, int G) {
+    if (!degree_batch_win_ok(m, n)) return CC_OK;
+    return buf_reserve(ctx, ctx->bwin, batch_win_scratch_bytes(m, n, G));
+}
+
+bool enqueue_batch_degree(cc_ctx *ctx, const int32_t *edges, long long m, const int64_t *eo, const int64_t *vo, int G,
+                          long long n, int regions, cudaStream_t s, vid_t *hook) {
+    DevState *st = as<DevState>(ctx->st);
+    if (batch_win(ctx, m, n, G)) {
+        launch_degree_batch_win(edges, m, eo, vo, G, n, as<uint32_t>(ctx->tile_pairs), as<uint32_t>(ctx->deg), st,
+                                ctx->bwin.p, ctx->num_sms, s, hook);
+        return true;
+    }
+    launch_degree_batch(edges, m, eo, vo, G, as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), regions, s, hook);
+    return false;
+}
+
 // Schedule tuner of the batched form. The hook passes over a batch map each
 // tile of pairs to its graph, and how many pairs a thread carries per tile
 // (amortising that lookup and keeping loads in flight) against how many
@@ -1995,8 +2021,10 @@ cc_status tune_batch(cc_ctx *ctx, const int32_t *edges, long long m, const int64
         }
     }
     // the degree pass (idempotent after a reset of the counts): regions of
-    // the pairs worked on side by side
-    if (ctx->deg.p && ctx->deg.bytes >= (size_t)nt * 4) {
+    // the pairs worked on side by side (the windowed pass has no regions: 0)
+    if (batch_win(ctx, m, nt, G)) {
+        out->deg_regions = 0;
+    } else if (ctx->deg.p && ctx->deg.bytes >= (size_t)nt * 4) {
         float best_deg = 1e30f;
         for (int regions : {1, 8, 32}) {
             CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)nt * 4, s));
@@ -2156,6 +2184,8 @@ cc_status ensure_batch_graph(cc_ctx *ctx, int G, long long n, long long m) {
     CC_TRY(buf_reserve(ctx, ctx->tile_pairs, (size_t)((m >> kTileShift) + 2) * 4));
     CC_TRY(buf_reserve(ctx, ctx->tile_verts, (size_t)((n >> kTileShift) + 2) * 4));
     CC_TRY(ensure_feat(ctx, (size_t)n));
+    // inside the caller's capture a missing window scratch means the L2 degree pass
+    if (!ctx->capturing && ctx->opt.route_policy != CC_ROUTE_FORCE_SV) CC_TRY(ensure_batch_win(ctx, m, n, G));
     return CC_OK;
 }
 
@@ -2226,8 +2256,7 @@ cc_status enqueue_batch_route(cc_ctx *ctx, const int32_t *edges, const int64_t *
     const bool fused = predict && !sch.front;
     if (predict) {
         CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)n * 4, cs));
-        launch_degree_batch(edges, m, eo, vo, G, as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx),
-                            sch.deg_regions, cs, fused ? parent : nullptr);
+        enqueue_batch_degree(ctx, edges, m, eo, vo, G, n, sch.deg_regions, cs, fused ? parent : nullptr);
         // the fits (largest graph first) on the highest-priority stream beside the first hook pass
         CU_TRY(cudaEventRecord(ctx->ev_fork, cs));
         CU_TRY(cudaStreamWaitEvent(ctx->fit_s, ctx->ev_fork, 0));
@@ -2360,6 +2389,7 @@ cc_status labels_batched_graph(cc_ctx *ctx, const int32_t *edges, const int64_t 
     }
     sch.front = batch_front(ctx, m);
     hook_order(ctx, &sch);
+    if (batch_win(ctx, m, n, G)) sch.deg_regions = 0;  // the windowed degree pass has no regions
     S.batch_unroll = sch.unroll;
     S.batch_grid_mult = sch.grid_mult;
     S.batch_deg_regions = sch.deg_regions;
@@ -2469,7 +2499,8 @@ cc_status cc_create(cc_ctx **out, const cc_options *opt, int device) {
         return CC_ERR_CUDA;
     }
     ctx->num_sms = prop.multiProcessorCount;
-    if (degree_part_setup() != cudaSuccess || degree_hubs_setup() != cudaSuccess || csr_kernels_setup() != cudaSuccess) {
+    if (degree_part_setup() != cudaSuccess || degree_hubs_setup() != cudaSuccess || csr_kernels_setup() != cudaSuccess ||
+        batch_win_setup() != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return CC_ERR_CUDA;
@@ -2508,7 +2539,7 @@ cc_status cc_destroy(cc_ctx *ctx) {
                    &ctx->off,    &ctx->tsum,       &ctx->counters, &ctx->bk_off, &ctx->csr_entries,
                    &ctx->dpart,  &ctx->f_sdeg,     &ctx->f_counts, &ctx->f_vis,
                    &ctx->f_f0,   &ctx->f_f1,       &ctx->f_x,    &ctx->pred_wb, &ctx->pred_bias, &ctx->pred_tmp,
-                   &ctx->bfs_own, &ctx->bfs_tmin};
+                   &ctx->bfs_own, &ctx->bfs_tmin, &ctx->bwin};
     for (Buf *b : bufs) buf_free(*b);
     for (int e = 0; e < EV_COUNT; e++)
         if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
@@ -2738,12 +2769,13 @@ cc_status cc_ks_statistic_batched(cc_ctx *ctx, const void *edges_dev, const int6
     const int64_t *edge_offsets_host = eo_h.data(), *vertex_offsets_host = vo_h.data();
     CC_TRY(ensure_sv(ctx, (size_t)(n > 0 ? n : 1), (size_t)m));
     CC_TRY(ensure_batch_route(ctx, G));
+    CC_TRY(ensure_batch_win(ctx, m, n, G));
     DevState *st = as<DevState>(ctx->st);
     CU_TRY(cudaMemsetAsync(st, 0, sizeof(DevState), s));
     CU_TRY(cudaMemsetAsync(ctx->deg.p, 0, (size_t)(n > 0 ? n : 1) * 4, s));
     CC_TRY(ensure_tiles(ctx, edge_offsets_dev, vertex_offsets_dev, G, m, n, s));
-    launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, as<uint32_t>(ctx->deg),
-                        st, ctx->grid, tile_queue(ctx), BatchSchedule().deg_regions, s);
+    enqueue_batch_degree(ctx, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, n,
+                         BatchSchedule().deg_regions, s, nullptr);
     std::vector<int> route;
     CC_TRY(enqueue_ks_batch(ctx, vertex_offsets_dev, vertex_offsets_host, G, s));
     CC_TRY(batch_routes(ctx, vertex_offsets_host, G, route, s));
@@ -2788,10 +2820,12 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
     const int cap = ctx->opt.max_iters > 0 ? ctx->opt.max_iters : default_max_iters(n);
     CC_TRY(ensure_tiles(ctx, edge_offsets_dev, vertex_offsets_dev, G, m, n, s));
     const uint32_t *vtiles = as<uint32_t>(ctx->tile_verts);
+    if (m > 0 && ctx->opt.route_policy != CC_ROUTE_FORCE_SV) CC_TRY(ensure_batch_win(ctx, m, n, G));
     BatchSchedule sch;
     CC_TRY(tune_batch(ctx, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, nt, s, &sch));
     sch.front = batch_front(ctx, m);
     hook_order(ctx, &sch);
+    if (batch_win(ctx, m, n, G)) sch.deg_regions = 0;  // the windowed degree pass has no regions
     S.sv_sample_stride = sch.front ? -1 : 1;
     S.batch_unroll = sch.unroll;
     S.batch_grid_mult = sch.grid_mult;
@@ -2815,9 +2849,8 @@ static cc_status labels_batched_profiled(cc_ctx *ctx, const void *edges_dev, con
         {
             {
                 Scope sc(ctx, CC_K_DEGREE, s, 1);
-                launch_degree_batch((const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G,
-                                    as<uint32_t>(ctx->deg), st, ctx->grid, tile_queue(ctx), sch.deg_regions, s,
-                                    sch.front ? nullptr : parent);
+                enqueue_batch_degree(ctx, (const int32_t *)edges_dev, m, edge_offsets_dev, vertex_offsets_dev, G, n,
+                                     sch.deg_regions, s, sch.front ? nullptr : parent);
             }
             // the fits on a highest-priority stream, overlapping the first hook
             // pass, which launches one block per tile so that the fits' blocks

@@ -155,6 +155,16 @@ size_t degree_smem_scratch_bytes(vid_t n, long long m);
 template <typename T>
 void launch_degree_smem(const void *edges, long long m, vid_t n, uint32_t *deg, void *scratch, DevState *st,
                         int num_sms, cudaStream_t s);
+// k_batch_degree.cu: the batched degree pass (with the first hook pass when
+// `hook`) counted in shared-memory windows of 4,096 vertices per graph; four
+// launches. Scratch: batch_win_scratch_bytes(m, n, G) bytes; tile_pairs: the
+// graph of every 2^kTileShift-th pair of the batch (launch_tile_graphs).
+bool degree_batch_win_ok(long long m, long long n);
+size_t batch_win_scratch_bytes(long long m, long long n, int G);
+void launch_degree_batch_win(const int32_t *in, long long m, const int64_t *eo, const int64_t *vo, int G, long long n,
+                             const uint32_t *tile_pairs, uint32_t *deg, DevState *st, void *scratch, int num_sms,
+                             cudaStream_t s, vid_t *hook);
+cudaError_t batch_win_setup();
 cudaError_t degree_part_setup();
 cudaError_t degree_hubs_setup();  // dynamic shared memory of the hub-aware degree pass
 

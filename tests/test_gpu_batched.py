@@ -41,8 +41,11 @@ def test_mixed_batch_matches_oracle_per_graph():
     got, st = _run_batched(torch, b.edges, b.edge_offsets, b.vertex_offsets)
     _check_each(b, got)
     assert st["sv_iters"] >= 2
-    # the schedule the call used (the default below the tuner's size)
-    assert (st["batch_unroll"], st["batch_grid_mult"], st["batch_deg_regions"]) == (2, 1, 1)
+    # the schedule the call used (the default below the tuner's size); the
+    # degree pass of a batch of 2^20 pairs or more counts in shared-memory
+    # windows, which have no regions (0)
+    assert b.edge_offsets[-1] >= 1 << 20
+    assert (st["batch_unroll"], st["batch_grid_mult"], st["batch_deg_regions"]) == (2, 1, 0)
 
 
 @pytest.mark.parametrize("stride,route,profile", [(8, "auto", 0), (0, "auto", 0), (8, "sv", 0), (8, "auto", 1),
@@ -149,3 +152,71 @@ def test_hook_regions_option_is_checked(bad):
     with pytest.raises(cc.CCError) as ei:
         cc.Engine(batch_hook_regions=bad)
     assert ei.value.status == 1
+
+
+def _window_edge_case_batch():
+    """A batch for the windowed degree pass (windows of 4,096 vertices per
+    graph, 2^20 pairs or more in all) with each of its exact fallbacks:
+    a graph of more than 2^20 vertices (counted and hooked with global
+    atomics), 1,500 graphs of three pairs and two windows each (their chunks
+    span more than 512 windows), a star whose window runs far past its
+    capacity, an R-MAT graph with hubs and a long path."""
+    rng = np.random.default_rng(77)
+    gs = []
+    n_big = (1 << 20) + 3
+    gs.append((rng.integers(0, n_big, size=(400_000, 2)), n_big))
+    for k in range(700):
+        n = 4097 + k % 3
+        gs.append((rng.integers(0, n, size=(3, 2)), n))
+    n = 50_000
+    star = np.stack([np.full(300_000, 7), rng.integers(0, n, size=300_000)], axis=1)
+    star[::5] = star[::5, ::-1]
+    gs.append((star, n))
+    r = gg.rmat(seed=78, scale=17, edge_factor=8)
+    gs.append((r.edges.astype(np.int64), r.n))
+    for k in range(800):
+        n = 4097 + k % 5
+        gs.append((rng.integers(0, n, size=(3, 2)), n))
+    n = 200_000
+    perm = rng.permutation(n)
+    gs.append((np.stack([perm[:-1], perm[1:]], axis=1), n))
+    gs.append((np.array([[0, 0], [1, 1], [2, 1]]), 3))  # self-loops
+    eo = np.zeros(len(gs) + 1, np.int64)
+    vo = np.zeros(len(gs) + 1, np.int64)
+    for i, (e, n) in enumerate(gs):
+        eo[i + 1] = eo[i] + len(e)
+        vo[i + 1] = vo[i] + n
+    edges = np.ascontiguousarray(np.concatenate([e for e, _ in gs]).astype(np.int32))
+    assert eo[-1] >= 1 << 20
+    return gs, edges, eo, vo
+
+
+def test_windowed_degree_pass_fallbacks_per_graph_fit():
+    """The batched degree pass in shared-memory windows against the oracle:
+    every graph's fit (which depends on every degree) and max-degree seed."""
+    torch = torch_cuda()
+    import paper_1607_06156_gb300 as cc
+
+    gs, edges, eo, vo = _window_edge_case_batch()
+    eng = cc.Engine()
+    r = eng.ks_statistic_batched(torch.from_numpy(edges).cuda(), eo, vo)
+    eng.close()
+    for i, (e, n) in enumerate(gs):
+        deg = oracle.degrees(e, n)
+        want = oracle.ks_fit(oracle.histogram(deg))
+        assert r["ncand"][i] == want["ncand"] and r["xmin"][i] == want["xmin"], (i, want)
+        assert abs(r["D"][i] - want["D"]) < 1e-9, (i, r["D"][i], want)
+        assert r["seed"][i] == int(np.argmax(deg)), i
+
+
+@pytest.mark.parametrize("profile,stride", [(0, 0), (1, 0), (0, 8)])
+def test_windowed_degree_pass_fallbacks_labels(profile, stride):
+    """Labels per graph with the first hook pass inside the windowed degree
+    pass (profile 0 and 1), and with the front end, whose degree pass hooks
+    nothing (stride 8)."""
+    torch = torch_cuda()
+    gs, edges, eo, vo = _window_edge_case_batch()
+    got, st = _run_batched(torch, edges, eo, vo, profile=profile, sv_sample_stride=stride)
+    assert st["batch_deg_regions"] == 0
+    for i, (e, n) in enumerate(gs):
+        assert np.array_equal(got[vo[i]:vo[i + 1]], oracle.cc_labels(e.astype(np.int32), n)), i
