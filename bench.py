@@ -54,6 +54,8 @@ WORKLOADS = {
     "chung_lu_union": dict(kind="union", seed=1, parts=200, nmin=1 << 13, nmax=1 << 17, avg_degree=16.0),
     "batch4096": dict(kind="batch", seed=1, G=4096, nmin=1000, nmax=1_000_000),
     "batch512": dict(kind="batch", seed=1, G=512, nmin=1000, nmax=1_000_000),
+    # a small batch of the same graph mix, for captures of the batched kernels
+    "batch64": dict(kind="batch", seed=1, G=64, nmin=1000, nmax=1_000_000),
 }
 KERNEL_FILES = ["cc_common.cuh", "ks_math.cuh", "k_degree.cu", "k_degree_part.cu", "k_sv.cu", "k_bfs.cu", "k_bucket.cu",
                 "k_batch_route.cu", "cc_api.cu"]

@@ -17,8 +17,9 @@
 //                     Each endpoint x of graph g (local ids) becomes the
 //                     32-bit entry (x mod 4096) | partner << 12 of window
 //                     wo[g] + x / 4096; the chunk's entries are counting-
-//                     sorted by window in shared memory, one reservation per
-//                     window and chunk, and written out run by run
+//                     sorted by window in shared memory (staged as window <<
+//                     32 | entry, one 8-byte access each way), one reservation
+//                     per window and chunk, and written out run by run
 //  k_degree_window_batch  one CTA per window counts its entries and hooks its
 //                     vertices in shared memory (the window's sampled hub in
 //                     registers), then writes deg and parent once
@@ -194,8 +195,7 @@ __global__ void __launch_bounds__(kBlock) k_bwin_graphs(const uint32_t *__restri
 
 struct __align__(128) BSplitShared {
     int4 buf[2][kBSplitVecs];        // two chunks of pairs (bulk-copy destinations)
-    uint32_t se[kBSplitMaxEnd];      // staged entries, in window order
-    uint16_t sb[kBSplitMaxEnd];      // their windows within the chunk's range
+    unsigned long long se[kBSplitMaxEnd];  // window within the chunk's range << 32 | entry, in window order
     uint32_t hist[kBMaxWin];
     unsigned long long goff[kBMaxWin];  // the window's region + its reservation - its first stage slot
     uint32_t loff[kBMaxWin];         // the window's first stage slot
@@ -303,7 +303,9 @@ __global__ void __launch_bounds__(kBSplitThreads, 2)
         const int g0 = S.g0[slot], g1 = S.g1[slot];
         const uint32_t wlo = wo[g0], nbw = wo[g1 + 1] - wlo;
         const bool direct = nbw > (uint32_t)kBMaxWin;  // block-uniform
-        // the chunk's first graph (most chunks lie in one graph)
+        // the chunk's first graph (most chunks lie in one graph: their windows
+        // start at wlo, so a window is x / 4096 and no offset is read per pair)
+        const bool one = g0 == g1;
         const long long vb0 = vo[g0];
         const long long ng0 = vo[g0 + 1] - vb0;
         uint32_t pe[2 * NE], rk[NE];
@@ -321,10 +323,12 @@ __global__ void __launch_bounds__(kBSplitThreads, 2)
                     else scalar_pair<int32_t>(edges, c * CP + p, u, v);  // the odd last pair
                     int g = g0;
                     long long vb = vb0, ng = ng0;
-                    if (g0 != g1) {
+                    uint32_t wg0 = 0u;  // the graph's first window - wlo
+                    if (!one) {
                         g = graph_advance(eo, G, c * CP + p, g0);
                         vb = vo[g];
                         ng = vo[g + 1] - vb;
+                        wg0 = wo[g] - wlo;
                     }
                     if ((unsigned long long)u >= (unsigned long long)ng ||
                         (unsigned long long)v >= (unsigned long long)ng) {
@@ -336,7 +340,6 @@ __global__ void __launch_bounds__(kBSplitThreads, 2)
                             atomicOr(&dirty[wo[g] + ((uint32_t)v >> kBWinBits)], 1u);
                         }
                     } else {
-                        const uint32_t wg0 = wo[g] - wlo;
                         const uint32_t bu = wg0 + ((uint32_t)u >> kBWinBits), bv = wg0 + ((uint32_t)v >> kBWinBits);
                         pe[2 * (k * 2 + j)] = ((uint32_t)u & kLow) | ((uint32_t)v << kBWinBits);
                         pe[2 * (k * 2 + j) + 1] = ((uint32_t)v & kLow) | ((uint32_t)u << kBWinBits);
@@ -417,18 +420,19 @@ __global__ void __launch_bounds__(kBSplitThreads, 2)
             const uint32_t r = rk[k];
             if (r == 0xffffffffu) continue;
             const uint32_t bu = pb[2 * k], bv = pb[2 * k + 1];
-            const uint32_t iu = S.loff[bu] + (r & 0xffffu), iv = S.loff[bv] + (r >> 16);
-            S.se[iu] = pe[2 * k];
-            S.sb[iu] = (uint16_t)bu;
-            S.se[iv] = pe[2 * k + 1];
-            S.sb[iv] = (uint16_t)bv;
+            S.se[S.loff[bu] + (r & 0xffffu)] = ((unsigned long long)bu << 32) | pe[2 * k];
+            S.se[S.loff[bv] + (r >> 16)] = ((unsigned long long)bv << 32) | pe[2 * k + 1];
         }
         __syncthreads();  // barrier 4
         if (!over) {
-            for (uint32_t i = t; i < tot; i += kBSplitThreads) part[S.goff[S.sb[i]] + i] = S.se[i];
+            for (uint32_t i = t; i < tot; i += kBSplitThreads) {
+                const unsigned long long x = S.se[i];
+                part[S.goff[x >> 32] + i] = (uint32_t)x;
+            }
         } else {
             for (uint32_t i = t; i < tot; i += kBSplitThreads) {
-                const uint32_t b = S.sb[i], e = S.se[i];
+                const unsigned long long x = S.se[i];
+                const uint32_t b = (uint32_t)(x >> 32), e = (uint32_t)x;
                 if (i < S.gend[b]) {
                     part[S.goff[b] + i] = e;
                 } else {  // past the region: counted and hooked here
