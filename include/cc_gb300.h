@@ -174,7 +174,8 @@ typedef struct {
     int32_t sv_sample_stride;           /* SV front end: one block of pairs in this many was sampled (1 = no
                                            front end; 0 = no first pass over the input pairs in this call;
                                            -1 = batched form, each graph with its own stride) */
-    int32_t batch_deg_regions;          /* batched form: tuned regions of the pairs the degree pass works on side by side */
+    int32_t batch_deg_regions;          /* batched form: tuned regions of the pairs the degree pass works on side by side;
+                                           0 = the degree pass counted in shared-memory windows (2^20 pairs or more) */
     int32_t bfs_starts;                 /* BFS trees started (0 if the BFS did not run) */
     int32_t batch_sv_regions;           /* batched form: tuned tile order of the hook passes (0 = grid stride,
                                            else regions of the pairs worked on side by side) */
