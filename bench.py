@@ -58,7 +58,7 @@ WORKLOADS = {
     "batch64": dict(kind="batch", seed=1, G=64, nmin=1000, nmax=1_000_000),
 }
 KERNEL_FILES = ["cc_common.cuh", "ks_math.cuh", "k_degree.cu", "k_degree_part.cu", "k_sv.cu", "k_bfs.cu", "k_bucket.cu",
-                "k_batch_route.cu", "cc_api.cu"]
+                "k_batch_route.cu", "k_batch_degree.cu", "cc_api.cu"]
 # the sources of each kernel class's kernels and launchers: a traffic capture
 # stays valid while these are unchanged (another class's kernel may change)
 CLASS_FILES = {
@@ -218,7 +218,7 @@ def kernel_class(name: str):
         return None
     if "k_sv_pass_loop" in name:  # the list pass inside the graph's WHILE node
         return "sv_gather_list"
-    table = [("k_degree_partition", "degree"), ("k_degree_split", "degree"), ("k_degree_window", "degree"), ("k_degree_count", "degree"), ("k_degree_hubs", "degree"), ("k_hub_", "degree"), ("k_degree<", "degree"), ("k_hist", "hist"),
+    table = [("k_degree_partition", "degree"), ("k_degree_split", "degree"), ("k_degree_window", "degree"), ("k_bwin_", "degree"), ("k_degree_count", "degree"), ("k_degree_hubs", "degree"), ("k_hub_", "degree"), ("k_degree<", "degree"), ("k_hist", "hist"),
              ("k_distinct", "ks"), ("k_ks_", "ks"), ("k_parent_init", "parent_init"), ("k_sv_sample", "sv_first"),
              ("k_shortcut_all", "sv_shortcut"), ("k_sv_shortcut", "sv_shortcut"), ("k_finalize", "finalize")]
     for key, cls in table:

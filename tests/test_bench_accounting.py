@@ -67,6 +67,9 @@ def test_gather_passes_count_survivors():
     ("void ccg::k_degree_partition<int, unsigned short>(const T1 *, long long)", "degree"),
     ("ccg::k_degree_window_smem(const unsigned short *, unsigned long long)", "degree"),
     ("void ccg::k_degree_split<int, unsigned int>(const T1 *, long long)", "degree"),
+    ("ccg::k_degree_split_batch(const int *, long long)", "degree"),
+    ("ccg::k_degree_window_batch(const unsigned int *, const long *)", "degree"),
+    ("ccg::k_bwin_plan(const long *, const long *, int)", "degree"),
     ("ccg::k_degree_window_hook(const unsigned long long *, unsigned long long)", "degree"),
     ("void ccg::k_sv_sample<int, 2>(const T1 *)", "sv_first"),
     ("void ccg::k_sv_pass<int, 0, 0, 0>(const T1 *)", "sv_first"),
