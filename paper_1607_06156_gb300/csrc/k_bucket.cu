@@ -28,11 +28,11 @@ constexpr int kBucketBits = 15;  // 32768 vertices per block: 128 KB of uint32 c
 constexpr int kBucketSize = 1 << kBucketBits;
 constexpr int kMaxBuckets = 1024;  // n <= 2^25 takes this path
 constexpr int kPartThreads = 512;
-constexpr int kPartPairs = 16;  // pairs per thread per tile
-constexpr int kPartTile = kPartThreads * kPartPairs * 2;  // directed entries per tile (16,384)
+constexpr int kPartPairs = 8;  // pairs per thread per tile (two blocks per SM: Chung-Lu 2^24 CSR 4.71 ms, 4.82 with 16 and one)
+constexpr int kPartTile = kPartThreads * kPartPairs * 2;  // directed entries per tile (8,192)
 
 struct CsrPartShared {
-    unsigned long long stage[kPartTile];  // the tile's entries in vertex-block order (128 KB)
+    unsigned long long stage[kPartTile];  // the tile's entries in vertex-block order (64 KB)
     uint16_t key[kPartTile];              // the vertex block of each staged entry
     uint32_t hist[kMaxBuckets];
     uint32_t loff[kMaxBuckets + 1];
@@ -41,7 +41,7 @@ struct CsrPartShared {
 constexpr size_t kCsrPartSmem = sizeof(CsrPartShared);
 
 template <typename T>
-__global__ void __launch_bounds__(kPartThreads, 1) k_csr_partition(const T *__restrict__ edges, long long m, vid_t n,
+__global__ void __launch_bounds__(kPartThreads, 2) k_csr_partition(const T *__restrict__ edges, long long m, vid_t n,
                                                                    int nb, const uint32_t *__restrict__ row_ptr,
                                                                    unsigned long long *fill,
                                                                    unsigned long long *out, DevState *st) {
