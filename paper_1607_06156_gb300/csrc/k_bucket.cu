@@ -37,7 +37,9 @@ struct CsrPartShared {
     uint32_t hist[kMaxBuckets];
     uint32_t loff[kMaxBuckets + 1];
     unsigned long long base[kMaxBuckets];
+    uint32_t wsum[kPartThreads / 32];
 };
+constexpr int kPartWpt = kMaxBuckets / kPartThreads;  // vertex blocks per thread in the scan
 constexpr size_t kCsrPartSmem = sizeof(CsrPartShared);
 
 template <typename T>
@@ -57,55 +59,79 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_csr_partition(const T *__re
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         for (int i = threadIdx.x; i < nb; i += kPartThreads) S.hist[i] = 0;
         __syncthreads();
-        unsigned long long ent[2 * kPartPairs];
-        uint32_t rank[2 * kPartPairs];
+        // the thread's pairs (ids below n <= 2^25; an invalid pair is marked by pu = ~0)
+        // and the ranks of both directed entries within their vertex blocks (16 bits each)
+        uint32_t pu[kPartPairs], pv[kPartPairs], rank[kPartPairs];
 #pragma unroll
         for (int k = 0; k < V; k++) {
             const long long i = t * tvec + (long long)k * kPartThreads + threadIdx.x;
             const int4 q = i < nvec ? ld_stream(ev + i) : make_int4(0, 0, 0, 0);
 #pragma unroll
             for (int j = 0; j < P; j++) {
-                const int e = (k * P + j) * 2;
+                const int e = k * P + j;
                 long long u, v;
                 vec_pair<T>(q, j, u, v);
                 const bool ok = i < nvec && (unsigned long long)u < n && (unsigned long long)v < n;
                 bad |= i < nvec && !ok;
-                ent[e] = ok ? ((unsigned long long)u << 32) | (unsigned long long)v : ~0ull;
-                ent[e + 1] = ok ? ((unsigned long long)v << 32) | (unsigned long long)u : ~0ull;
+                pu[e] = ok ? (uint32_t)u : ~0u;
+                pv[e] = (uint32_t)v;
             }
         }
 #pragma unroll
-        for (int e = 0; e < 2 * kPartPairs; e++)
-            rank[e] = ent[e] != ~0ull ? atomicAdd(&S.hist[(uint32_t)(ent[e] >> 32) >> kBucketBits], 1u) : 0u;
+        for (int e = 0; e < kPartPairs; e++)
+            rank[e] = pu[e] != ~0u ? atomicAdd(&S.hist[pu[e] >> kBucketBits], 1u) |
+                                         (atomicAdd(&S.hist[pv[e] >> kBucketBits], 1u) << 16)
+                                   : 0u;
         __syncthreads();
-        if (threadIdx.x < 32) {  // warp-parallel exclusive scan of the nb counts
-            uint32_t carry = 0;
-            for (int b0 = 0; b0 < nb; b0 += 32) {
-                const int b = b0 + threadIdx.x;
-                const uint32_t c = b < nb ? S.hist[b] : 0u;
-                uint32_t incl = c;
+        {  // block-wide exclusive scan of the nb counts (thread t: blocks t * kPartWpt and on),
+           // one reservation per vertex block
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            constexpr int NW = kPartThreads / 32;
+            uint32_t h[kPartWpt], hs = 0u;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t w = __shfl_up_sync(0xffffffffu, incl, o);
-                    if ((int)threadIdx.x >= o) incl += w;
-                }
-                if (b < nb) S.loff[b] = carry + incl - c;
-                carry += __shfl_sync(0xffffffffu, incl, 31);
+            for (int q = 0; q < kPartWpt; q++) {
+                const int b = threadIdx.x * kPartWpt + q;
+                h[q] = b < nb ? S.hist[b] : 0u;
+                hs += h[q];
+                if (h[q])
+                    S.base[b] = (unsigned long long)row_ptr[(long long)b << kBucketBits] +
+                                atomicAdd(&fill[b], (unsigned long long)h[q]);
             }
-            if (threadIdx.x == 0) S.loff[nb] = carry;
+            uint32_t incl = hs;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t w = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += w;
+            }
+            if (lane == 31) S.wsum[warp] = incl;
+            __syncthreads();
+            const uint32_t w = lane < NW ? S.wsum[lane] : 0u;
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < NW; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            uint32_t lo = __shfl_sync(0xffffffffu, wi - w, warp) + incl - hs;
+#pragma unroll
+            for (int q = 0; q < kPartWpt; q++) {
+                const int b = threadIdx.x * kPartWpt + q;
+                if (b < nb) S.loff[b] = lo;
+                lo += h[q];
+            }
+            const uint32_t tot = __shfl_sync(0xffffffffu, wi, NW - 1);
+            if (threadIdx.x == 0) S.loff[nb] = tot;
         }
-        for (int b = threadIdx.x; b < nb; b += kPartThreads)
-            if (S.hist[b]) {
-                const long long v0 = (long long)b << kBucketBits;
-                S.base[b] = (unsigned long long)row_ptr[v0] + atomicAdd(&fill[b], (unsigned long long)S.hist[b]);
-            }
         __syncthreads();
 #pragma unroll
-        for (int e = 0; e < 2 * kPartPairs; e++)
-            if (ent[e] != ~0ull) {
-                const uint32_t b = (uint32_t)(ent[e] >> 32) >> kBucketBits, pos = S.loff[b] + rank[e];
-                S.stage[pos] = ent[e];
-                S.key[pos] = (uint16_t)b;
+        for (int e = 0; e < kPartPairs; e++)
+            if (pu[e] != ~0u) {
+                const uint32_t bu = pu[e] >> kBucketBits, bv = pv[e] >> kBucketBits;
+                const uint32_t iu = S.loff[bu] + (rank[e] & 0xffffu), iv = S.loff[bv] + (rank[e] >> 16);
+                S.stage[iu] = ((unsigned long long)pu[e] << 32) | pv[e];
+                S.key[iu] = (uint16_t)bu;
+                S.stage[iv] = ((unsigned long long)pv[e] << 32) | pu[e];
+                S.key[iv] = (uint16_t)bv;
             }
         __syncthreads();
         const uint32_t total = S.loff[nb];
