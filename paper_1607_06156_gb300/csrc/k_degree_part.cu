@@ -1,5 +1,8 @@
-// Degree pass (Section 3.2, Algorithm 2 line 1) for graphs whose count
-// array does not fit in L2 (n > 2^25: 128 MB of counts and more).
+// Degree pass (Section 3.2, Algorithm 2 line 1) with the endpoints moved
+// into vertex windows first, in two forms: windows of 2^23 vertices counted
+// with L2 atomics, for graphs whose count array does not fit in L2 (n > 2^25:
+// 128 MB of counts and more); and windows of at most 2^15 vertices counted in
+// shared memory, for 2^20 <= n <= 2^24 (the second half of this file).
 //
 // deg[v] = number of pair endpoints equal to v. With one atomic per
 // endpoint, a count array out of L2 turns every endpoint into a DRAM
